@@ -1,0 +1,154 @@
+/*
+ * p2 — PARAFAC2-ALS (SPARTan formulation) on one NVIDIA GB300 GPU.
+ *
+ * C ABI of libp2.so.  All compute runs in the library's own CUDA kernels
+ * (sm_103a); there is no CPU fallback.  Paper references are to Perros et
+ * al., "SPARTan: Scalable PARAFAC2 for Large & Sparse Data", KDD 2017
+ * (arXiv:1703.04219).
+ *
+ * Problem (Section 3.1-3.2): a collection of sparse slices X_k (I_k x J),
+ * k = 0..K-1, is modelled as X_k ~ Q_k H S_k V^T with Q_k^T Q_k = I,
+ * H (R x R), V (J x R) and S_k = diag(W(k,:)), W (K x R).  One iteration is
+ * Algorithm 2's loop body: the Procrustes Q-step for every k, then a single
+ * CP-ALS sweep (Algorithm 1) on the implicit tensor Y with slices
+ * Y_k = Q_k^T X_k, whose MTTKRPs are Algorithm 3's.
+ *
+ * Conventions shared by every call:
+ *  - Return value: P2_OK (0) or one of the P2_E* codes; a human readable
+ *    message for the last failure on the calling thread is p2_last_error().
+ *  - Matrices are row-major, indices 0-based, FP32 unless stated.
+ *  - Inputs are copied; the caller keeps ownership of every buffer it passes.
+ *    Outputs go to caller-allocated buffers.
+ *  - Device work is enqueued on the context's stream.  Calls that return
+ *    host data (p2_load_slices, p2_iterate with fit_out, p2_fit,
+ *    p2_get_*) synchronise that stream before returning.
+ *  - A context is not thread safe: one host thread at a time.
+ */
+#ifndef P2_H
+#define P2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    P2_OK = 0,
+    P2_EINVAL = 1,     /* invalid argument or malformed slices */
+    P2_ENOMEM = 2,     /* device or host allocation failed */
+    P2_ECUDA = 3,      /* a CUDA runtime call failed */
+    P2_ENUMERIC = 4,   /* non-finite value or fixed-point overflow detected */
+    P2_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    P2_ESTATE = 6      /* call out of order (e.g. p2_iterate before p2_init) */
+};
+
+enum { P2_FP32 = 0, P2_BF16 = 1 };
+
+typedef struct p2_ctx p2_ctx;
+
+typedef struct {
+    int32_t R;            /* target rank, 1 <= R <= 64 */
+    int32_t precision;    /* P2_FP32 (P2_BF16 is reserved and rejected for now) */
+    int32_t device;       /* CUDA device ordinal */
+    int32_t use_graph;    /* non-zero: one iteration is captured in a CUDA graph and replayed */
+    double rank_rtol;     /* Procrustes rank cut: singular values <= rank_rtol * sigma_1 of
+                             X_k V S_k H^T are dropped; <= 0 selects the default 1e-5 */
+    void *stream;         /* cudaStream_t to enqueue on; NULL: the context creates its own */
+} p2_options;
+
+/* Fill *opt with defaults for rank R (precision FP32, device 0, graph on,
+ * rank_rtol 1e-5, own stream). */
+void p2_default_options(p2_options *opt, int32_t R);
+
+/* Create a context on opt->device.  *out receives the handle (NULL on error).
+ * The context owns every device allocation it makes. */
+int p2_create(p2_ctx **out, const p2_options *opt);
+
+/* Free the context and all its device memory.  NULL is accepted. */
+int p2_destroy(p2_ctx *ctx);
+
+/*
+ * Load the collection {X_k} (Algorithm 2, REQUIRE: X_k in R^{I_k x J}).
+ *   K         number of subjects, K >= 1
+ *   J         number of variables (columns), 1 <= J <= 65535
+ *   subj_ptr  int64[K+1]: rows of X_k are subj_ptr[k] .. subj_ptr[k+1]-1 of
+ *             the stacked row list; subj_ptr[0] = 0, non-decreasing
+ *   row_ptr   int64[N+1], N = subj_ptr[K]: CSR row pointers into col/val;
+ *             row_ptr[0] = 0, non-decreasing, at most 65535 entries per row
+ *   col       int32[nnz]: column ids in [0, J), strictly increasing in a row
+ *   val       float[nnz]: finite values
+ *   location  0: all four pointers are host memory; 1: device memory
+ * Empty rows and subjects with no rows are allowed (they add nothing to the
+ * model; Section 3.3 notes zero rows can be dropped without effect).  Limits:
+ * N < 2^31, nnz < 2^31.  Malformed input returns P2_EINVAL and leaves any
+ * previously loaded data in place.  The columns are relabelled internally by
+ * decreasing frequency; every factor the API returns is in the caller's
+ * column order.  Synchronises.
+ */
+int p2_load_slices(p2_ctx *ctx, int64_t K, int32_t J, const int64_t *subj_ptr,
+                   const int64_t *row_ptr, const int32_t *col, const float *val,
+                   int32_t location);
+
+/*
+ * Set the initial factors (Algorithm 2, "Initialize H, V, {S_k}") and run the
+ * first Q-step so that p2_iterate can start.  H0: R x R, V0: J x R (caller's
+ * column order), W0: K x R; host memory, FP32, none may be NULL.
+ */
+int p2_init(p2_ctx *ctx, const float *H0, const float *V0, const float *W0);
+
+/*
+ * Run n_iter >= 0 iterations of PARAFAC2-ALS (Algorithm 2 loop body: Q-step,
+ * one CP-ALS sweep on Y with Algorithm 3's MTTKRPs, S_k = diag(W(k,:))).
+ * fit_out (nullable, host): fit after the last iteration, as p2_fit.
+ * Returns P2_ENUMERIC if a non-finite loss or a fixed-point overflow was
+ * detected during these iterations.
+ */
+int p2_iterate(p2_ctx *ctx, int32_t n_iter, double *fit_out);
+
+/*
+ * Loss and fit of the last completed iteration (the objective of Section 3.2):
+ *   loss = sum_k ||X_k||^2 - 2 <Y_k, H S_k V^T> + ||H S_k V^T||_F^2
+ *        = ||X||^2 - 2 <W, M3> + 1^T (W^TW * H^TH * V^TV) 1,
+ *   fit  = 1 - sqrt(max(loss, 0)) / ||X||_F.
+ * Either pointer may be NULL.  P2_ESTATE before the first iteration.
+ */
+int p2_fit(p2_ctx *ctx, double *fit, double *loss);
+
+/* Current factors into host buffers (any may be NULL): H R x R, V J x R in
+ * the caller's column order, W K x R (W carries the scale; S_k = diag(W(k,:))). */
+int p2_get_factors(p2_ctx *ctx, float *H, float *V, float *W);
+
+/*
+ * Replace the current factors (host FP32; same layouts as p2_get_factors) and
+ * redo the Q-step for them, exactly as p2_init.  Used to resume from a
+ * checkpoint.
+ */
+int p2_set_factors(p2_ctx *ctx, const float *H, const float *V, const float *W);
+
+/*
+ * MTTKRPs of the last completed iteration (Algorithm 3), into host FP64
+ * buffers: mode 1 -> R x R (M1, with the Y and W of that iteration's H step),
+ * mode 2 -> J x R (M2, caller's column order), mode 3 -> K x R (M3).
+ */
+int p2_get_mttkrp(p2_ctx *ctx, int32_t mode, double *out);
+
+/*
+ * Per-subject Procrustes transform of the current Q-step, into a host FP32
+ * buffer of (k1 - k0) x R x R: T_k = C_k H S_k, where Q_k = X_k V T_k^T and
+ * C_k is the pseudo-inverse square root of (X_k V S_k H^T)^T (X_k V S_k H^T)
+ * (polar factor of Section 3.2's Procrustes problem).  0 <= k0 <= k1 <= K.
+ */
+int p2_get_procrustes(p2_ctx *ctx, int64_t k0, int64_t k1, float *T);
+
+/* Bytes of device memory the context holds now. */
+int p2_device_bytes(p2_ctx *ctx, int64_t *bytes);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *p2_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* P2_H */

@@ -1,0 +1,231 @@
+"""p2: PARAFAC2-ALS in SPARTan's formulation on one GB300 GPU.
+
+Thin ctypes binding of ``libp2.so`` (C ABI declared in ``include/p2.h``).
+The functions below carry the C names and only marshal arguments; every
+step of the computation runs in the library's CUDA kernels.  There is no
+CPU fallback: importing this package fails if ``libp2.so`` has not been
+built (``python paper_1703_04219_gb300/build.py`` or
+``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libp2.so")
+
+P2_OK, P2_EINVAL, P2_ENOMEM, P2_ECUDA, P2_ENUMERIC, P2_ETIMEOUT, P2_ESTATE = range(7)
+P2_FP32, P2_BF16 = 0, 1
+_NAMES = {0: "P2_OK", 1: "P2_EINVAL", 2: "P2_ENOMEM", 3: "P2_ECUDA", 4: "P2_ENUMERIC",
+          5: "P2_ETIMEOUT", 6: "P2_ESTATE"}
+
+# every symbol include/p2.h declares
+EXPORTED = ("p2_default_options", "p2_create", "p2_destroy", "p2_load_slices", "p2_init",
+            "p2_iterate", "p2_fit", "p2_get_factors", "p2_set_factors", "p2_get_mttkrp",
+            "p2_get_procrustes", "p2_device_bytes", "p2_last_error")
+
+
+class p2_options(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("rank_rtol", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+class P2Error(RuntimeError):
+    def __init__(self, code, where, msg):
+        super().__init__(f"{where}: {_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libp2.so not found at {LIB_PATH}: build it first "
+                          "(python paper_1703_04219_gb300/build.py); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "p2_default_options": ([ctypes.POINTER(p2_options), i32], None),
+        "p2_create": ([ctypes.POINTER(vp), ctypes.POINTER(p2_options)], ctypes.c_int),
+        "p2_destroy": ([vp], ctypes.c_int),
+        "p2_load_slices": ([vp, i64, i32, vp, vp, vp, vp, i32], ctypes.c_int),
+        "p2_init": ([vp, vp, vp, vp], ctypes.c_int),
+        "p2_iterate": ([vp, i32, ctypes.POINTER(dbl)], ctypes.c_int),
+        "p2_fit": ([vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)], ctypes.c_int),
+        "p2_get_factors": ([vp, vp, vp, vp], ctypes.c_int),
+        "p2_set_factors": ([vp, vp, vp, vp], ctypes.c_int),
+        "p2_get_mttkrp": ([vp, i32, vp], ctypes.c_int),
+        "p2_get_procrustes": ([vp, i64, i64, vp], ctypes.c_int),
+        "p2_device_bytes": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "p2_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def p2_last_error() -> str:
+    return lib.p2_last_error().decode(errors="replace")
+
+
+def _check(rc, where):
+    if rc != P2_OK:
+        raise P2Error(rc, where, p2_last_error())
+
+
+def _ptr(a):
+    """Address of a contiguous numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def p2_default_options(R: int) -> p2_options:
+    o = p2_options()
+    lib.p2_default_options(ctypes.byref(o), R)
+    return o
+
+
+def p2_create(opt: p2_options):
+    h = ctypes.c_void_p()
+    _check(lib.p2_create(ctypes.byref(h), ctypes.byref(opt)), "p2_create")
+    return h
+
+
+def p2_destroy(ctx):
+    _check(lib.p2_destroy(ctx), "p2_destroy")
+
+
+def p2_load_slices(ctx, K, J, subj_ptr, row_ptr, col, val, location=None):
+    if location is None:
+        location = 1 if hasattr(subj_ptr, "is_cuda") and subj_ptr.is_cuda else 0
+    if location == 0:
+        subj_ptr = np.ascontiguousarray(subj_ptr, np.int64)
+        row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+        col = np.ascontiguousarray(col, np.int32)
+        val = np.ascontiguousarray(val, np.float32)
+    _check(lib.p2_load_slices(ctx, int(K), int(J), _ptr(subj_ptr), _ptr(row_ptr), _ptr(col),
+                              _ptr(val), int(location)), "p2_load_slices")
+
+
+def p2_init(ctx, H0, V0, W0):
+    H0, V0, W0 = (np.ascontiguousarray(a, np.float32) for a in (H0, V0, W0))
+    _check(lib.p2_init(ctx, _ptr(H0), _ptr(V0), _ptr(W0)), "p2_init")
+
+
+def p2_set_factors(ctx, H, V, W):
+    H, V, W = (np.ascontiguousarray(a, np.float32) for a in (H, V, W))
+    _check(lib.p2_set_factors(ctx, _ptr(H), _ptr(V), _ptr(W)), "p2_set_factors")
+
+
+def p2_iterate(ctx, n_iter: int, want_fit: bool = True):
+    f = ctypes.c_double()
+    _check(lib.p2_iterate(ctx, int(n_iter), ctypes.byref(f) if want_fit else None), "p2_iterate")
+    return f.value if want_fit else None
+
+
+def p2_fit(ctx):
+    f, l = ctypes.c_double(), ctypes.c_double()
+    _check(lib.p2_fit(ctx, ctypes.byref(f), ctypes.byref(l)), "p2_fit")
+    return f.value, l.value
+
+
+def p2_get_factors(ctx, R, J, K):
+    H = np.empty((R, R), np.float32)
+    V = np.empty((J, R), np.float32)
+    W = np.empty((K, R), np.float32)
+    _check(lib.p2_get_factors(ctx, _ptr(H), _ptr(V), _ptr(W)), "p2_get_factors")
+    return H, V, W
+
+
+def p2_get_mttkrp(ctx, mode, R, J, K):
+    shape = {1: (R, R), 2: (J, R), 3: (K, R)}[mode]
+    out = np.empty(shape, np.float64)
+    _check(lib.p2_get_mttkrp(ctx, int(mode), _ptr(out)), "p2_get_mttkrp")
+    return out
+
+
+def p2_get_procrustes(ctx, k0, k1, R):
+    out = np.empty((k1 - k0, R, R), np.float32)
+    _check(lib.p2_get_procrustes(ctx, int(k0), int(k1), _ptr(out)), "p2_get_procrustes")
+    return out
+
+
+def p2_device_bytes(ctx) -> int:
+    b = ctypes.c_int64()
+    _check(lib.p2_device_bytes(ctx, ctypes.byref(b)), "p2_device_bytes")
+    return b.value
+
+
+class Parafac2:
+    """Owning wrapper of one context: load, init, iterate, read back."""
+
+    def __init__(self, R: int, device: int = 0, use_graph: bool = True, rank_rtol: float = 1e-5,
+                 stream=None):
+        opt = p2_default_options(R)
+        opt.device = device
+        opt.use_graph = 1 if use_graph else 0
+        opt.rank_rtol = rank_rtol
+        opt.stream = stream
+        self.R = R
+        self.ctx = p2_create(opt)
+        self.K = self.J = 0
+
+    def close(self):
+        if self.ctx is not None:
+            p2_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, slices, location=None):
+        p2_load_slices(self.ctx, slices.K, slices.J, slices.subj_ptr, slices.row_ptr, slices.col,
+                       slices.val, location)
+        self.K, self.J = int(slices.K), int(slices.J)
+
+    def init(self, H0, V0, W0):
+        p2_init(self.ctx, H0, V0, W0)
+
+    def set_factors(self, H, V, W):
+        p2_set_factors(self.ctx, H, V, W)
+
+    def iterate(self, n: int, want_fit: bool = True):
+        return p2_iterate(self.ctx, n, want_fit)
+
+    def fit(self):
+        return p2_fit(self.ctx)
+
+    def factors(self):
+        return p2_get_factors(self.ctx, self.R, self.J, self.K)
+
+    def mttkrp(self, mode: int):
+        return p2_get_mttkrp(self.ctx, mode, self.R, self.J, self.K)
+
+    def procrustes(self, k0=0, k1=None):
+        return p2_get_procrustes(self.ctx, k0, self.K if k1 is None else k1, self.R)
+
+    def device_bytes(self) -> int:
+        return p2_device_bytes(self.ctx)

@@ -1,0 +1,451 @@
+// C ABI of libp2.so: context, memory, call order, CUDA graph replay.
+// Every numerical step runs in the kernels of p2_kernels.cu / p2_load.cu.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "p2_internal.cuh"
+
+namespace p2 {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+static int fail(int code, const char *msg) {
+    set_error("%s", msg);
+    return code;
+}
+
+template <class T>
+static int dalloc(p2_ctx *c, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %zu bytes failed: %s", sizeof(T) * count, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? P2_ENOMEM : P2_ECUDA;
+    }
+    c->dev_bytes += sizeof(T) * count;
+    return P2_OK;
+}
+
+template <class T>
+static void dfree(p2_ctx *c, T **p, size_t count) {
+    if (*p) {
+        cudaFree(*p);
+        if (count == 0) count = 1;
+        c->dev_bytes -= sizeof(T) * count;
+    }
+    *p = nullptr;
+}
+
+#define P2_TRY(x)                   \
+    do {                            \
+        int _rc = (x);              \
+        if (_rc != P2_OK) return _rc; \
+    } while (0)
+
+static void free_data(p2_ctx *c) {
+    const size_t K = (size_t)c->X.K, J = (size_t)c->X.J, N = (size_t)c->X.N,
+                 nnz = (size_t)c->X.nnz, R = (size_t)c->R, P = (size_t)c->P;
+    dfree(c, &c->X.subj_row, K + 1);
+    dfree(c, &c->X.subj_nnz, K + 1);
+    dfree(c, &c->X.row_len, N);
+    dfree(c, &c->X.col, nnz);
+    dfree(c, &c->X.val, nnz);
+    dfree(c, &c->d_perm_old2new, J);
+    dfree(c, &c->d_colcount, J);
+    dfree(c, &c->d_V, J * R);
+    dfree(c, &c->d_Vprev, J * R);
+    dfree(c, &c->d_Vun, J * R);
+    dfree(c, &c->d_M2, J * R);
+    dfree(c, &c->d_m2acc, J * R);
+    dfree(c, &c->d_W, K * R);
+    dfree(c, &c->d_M3, K * R);
+    dfree(c, &c->d_T, K * R * R);
+    dfree(c, &c->d_G, K * P);
+    delete[] c->h_perm_new2old;
+    delete[] c->h_perm_old2new;
+    c->h_perm_new2old = c->h_perm_old2new = nullptr;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    c->X = DevX{};
+    c->loaded = false;
+    c->inited = false;
+    c->iters_done = 0;
+}
+
+static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
+    const size_t R = (size_t)c->R, P = (size_t)c->P;
+    c->X.K = K;
+    c->X.J = J;
+    c->X.N = N;
+    c->X.nnz = nnz;
+    P2_TRY(dalloc(c, &c->X.subj_row, (size_t)K + 1));
+    P2_TRY(dalloc(c, &c->X.subj_nnz, (size_t)K + 1));
+    P2_TRY(dalloc(c, &c->X.row_len, (size_t)N));
+    P2_TRY(dalloc(c, &c->X.col, (size_t)nnz));
+    P2_TRY(dalloc(c, &c->X.val, (size_t)nnz));
+    P2_TRY(dalloc(c, &c->d_perm_old2new, (size_t)J));
+    P2_TRY(dalloc(c, &c->d_colcount, (size_t)J));
+    P2_TRY(dalloc(c, &c->d_V, (size_t)J * R));
+    P2_TRY(dalloc(c, &c->d_Vprev, (size_t)J * R));
+    P2_TRY(dalloc(c, &c->d_Vun, (size_t)J * R));
+    P2_TRY(dalloc(c, &c->d_M2, (size_t)J * R));
+    P2_TRY(dalloc(c, &c->d_m2acc, (size_t)J * R));
+    P2_TRY(dalloc(c, &c->d_W, (size_t)K * R));
+    P2_TRY(dalloc(c, &c->d_M3, (size_t)K * R));
+    P2_TRY(dalloc(c, &c->d_T, (size_t)K * R * R));
+    P2_TRY(dalloc(c, &c->d_G, (size_t)K * P));
+    P2_CUDA_TRY(cudaMemsetAsync(c->d_m2acc, 0, sizeof(unsigned long long) * (size_t)J * R, c->stream));
+    P2_CUDA_TRY(cudaMemsetAsync(c->d_M3, 0, sizeof(float) * (size_t)K * R, c->stream));
+    c->h_perm_new2old = new int32_t[J];
+    c->h_perm_old2new = new int32_t[J];
+    return P2_OK;
+}
+
+static int check_ready(p2_ctx *c, bool need_init) {
+    if (!c) return fail(P2_EINVAL, "NULL context");
+    if (!c->loaded) return fail(P2_ESTATE, "no slices loaded (call p2_load_slices first)");
+    if (need_init && !c->inited) return fail(P2_ESTATE, "factors not initialised (call p2_init first)");
+    return P2_OK;
+}
+
+static int read_flags(p2_ctx *c, int *flags) {
+    P2_CUDA_TRY(cudaMemcpyAsync(flags, &c->d_s->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    P2_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return P2_OK;
+}
+
+static int flags_status(int flags) {
+    if (flags & (FLAG_FIXED_OVF | FLAG_NONFINITE)) {
+        set_error("numeric problem detected on the device (flags 0x%x: %s%s)", flags,
+                  (flags & FLAG_FIXED_OVF) ? "mode-2 fixed-point range exceeded; " : "",
+                  (flags & FLAG_NONFINITE) ? "non-finite loss; " : "");
+        return P2_ENUMERIC;
+    }
+    return P2_OK;
+}
+
+static int set_factors_impl(p2_ctx *c, const float *H, const float *V, const float *W) {
+    const int R = c->R;
+    const int32_t J = c->X.J;
+    const int64_t K = c->X.K;
+    std::vector<float> Vp((size_t)J * R);
+    for (int32_t j = 0; j < J; ++j)
+        memcpy(&Vp[(size_t)c->h_perm_old2new[j] * R], V + (size_t)j * R, sizeof(float) * R);
+    P2_CUDA_TRY(cudaMemcpyAsync(c->d_H, H, sizeof(float) * R * R, cudaMemcpyHostToDevice, c->stream));
+    P2_CUDA_TRY(cudaMemcpyAsync(c->d_V, Vp.data(), sizeof(float) * (size_t)J * R,
+                                cudaMemcpyHostToDevice, c->stream));
+    P2_CUDA_TRY(cudaMemcpyAsync(c->d_W, W, sizeof(float) * (size_t)K * R, cudaMemcpyHostToDevice,
+                                c->stream));
+    int zero = 0;
+    P2_CUDA_TRY(cudaMemcpyAsync(&c->d_s->flags, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    P2_TRY(enqueue_factor_stats(c));
+    P2_TRY(enqueue_prologue(c));
+    int flags = 0;
+    P2_TRY(read_flags(c, &flags));   // also keeps Vp alive until the copy finished
+    c->inited = true;
+    c->iters_done = 0;
+    return P2_OK;
+}
+
+}  // namespace p2
+
+using namespace p2;
+
+extern "C" {
+
+void p2_default_options(p2_options *opt, int32_t R) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->R = R;
+    opt->precision = P2_FP32;
+    opt->device = 0;
+    opt->use_graph = 1;
+    opt->rank_rtol = 1e-5;
+    opt->stream = nullptr;
+}
+
+int p2_create(p2_ctx **out, const p2_options *opt) {
+    if (!out || !opt) return fail(P2_EINVAL, "p2_create: NULL argument");
+    *out = nullptr;
+    if (opt->R < 1 || opt->R > P2_RMAX) return fail(P2_EINVAL, "p2_create: R must be in [1, 64]");
+    if (opt->precision != P2_FP32)
+        return fail(P2_EINVAL, "p2_create: only P2_FP32 storage is implemented");
+    int ndev = 0;
+    P2_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (opt->device < 0 || opt->device >= ndev) return fail(P2_EINVAL, "p2_create: bad device");
+    P2_CUDA_TRY(cudaSetDevice(opt->device));
+    p2_ctx *c = new p2_ctx();
+    c->opt = *opt;
+    if (!(c->opt.rank_rtol > 0.0)) c->opt.rank_rtol = 1e-5;
+    c->R = opt->R;
+    c->P = opt->R * (opt->R + 1) / 2;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, opt->device);
+    if (e != cudaSuccess) {
+        delete c;
+        set_error("cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+        return P2_ECUDA;
+    }
+    c->geo.nsm = prop.multiProcessorCount;
+    c->geo.smem_optin = (int)prop.sharedMemPerBlockOptin;
+    c->geo.red_blocks = 2 * prop.multiProcessorCount;
+    if (opt->stream) {
+        c->stream = (cudaStream_t)opt->stream;
+        c->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            set_error("cudaStreamCreate: %s", cudaGetErrorString(e));
+            return P2_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    int rc = dalloc(c, &c->d_s, 1);
+    if (rc == P2_OK) rc = dalloc(c, &c->d_H, (size_t)c->R * c->R);
+    const size_t part_stride = (size_t)c->R * c->R + 2 * (size_t)c->R + 8;
+    if (rc == P2_OK) rc = dalloc(c, &c->d_part, (size_t)c->geo.red_blocks * part_stride);
+    if (rc == P2_OK) rc = dalloc(c, &c->d_part2, (size_t)c->geo.red_blocks * part_stride);
+    if (rc == P2_OK) rc = configure_kernels(c);
+    if (rc == P2_OK) {
+        if (cudaMemsetAsync(c->d_s, 0, sizeof(SmallState), c->stream) != cudaSuccess) rc = P2_ECUDA;
+    }
+    if (rc != P2_OK) {
+        p2_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return P2_OK;
+}
+
+int p2_destroy(p2_ctx *c) {
+    if (!c) return P2_OK;
+    cudaSetDevice(c->opt.device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_data(c);
+    dfree(c, &c->d_s, 1);
+    dfree(c, &c->d_H, (size_t)c->R * c->R);
+    const size_t part_stride = (size_t)c->R * c->R + 2 * (size_t)c->R + 8;
+    dfree(c, &c->d_part, (size_t)c->geo.red_blocks * part_stride);
+    dfree(c, &c->d_part2, (size_t)c->geo.red_blocks * part_stride);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return P2_OK;
+}
+
+int p2_load_slices(p2_ctx *c, int64_t K, int32_t J, const int64_t *subj_ptr,
+                   const int64_t *row_ptr, const int32_t *col, const float *val,
+                   int32_t location) {
+    if (!c) return fail(P2_EINVAL, "NULL context");
+    if (K < 1) return fail(P2_EINVAL, "p2_load_slices: K must be >= 1");
+    if (J < 1 || J > 65535) return fail(P2_EINVAL, "p2_load_slices: J must be in [1, 65535]");
+    if (!subj_ptr || !row_ptr) return fail(P2_EINVAL, "p2_load_slices: NULL pointer array");
+    if (location != 0 && location != 1) return fail(P2_EINVAL, "p2_load_slices: location must be 0 or 1");
+    P2_CUDA_TRY(cudaSetDevice(c->opt.device));
+    cudaStream_t s = c->stream;
+    const cudaMemcpyKind kind = location == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    // endpoints: subj_ptr[0] = 0, N = subj_ptr[K]; row_ptr[0] = 0, nnz = row_ptr[N]
+    int64_t s0 = 0, N = 0, r0 = 0, nnz = 0;
+    if (location == 0) {
+        s0 = subj_ptr[0];
+        N = subj_ptr[K];
+    } else {
+        P2_CUDA_TRY(cudaMemcpy(&s0, subj_ptr, 8, cudaMemcpyDeviceToHost));
+        P2_CUDA_TRY(cudaMemcpy(&N, subj_ptr + K, 8, cudaMemcpyDeviceToHost));
+    }
+    if (s0 != 0 || N < 0 || N >= (1LL << 31))
+        return fail(P2_EINVAL, "p2_load_slices: subj_ptr[0] must be 0 and 0 <= subj_ptr[K] < 2^31");
+    if (location == 0) {
+        r0 = row_ptr[0];
+        nnz = row_ptr[N];
+    } else {
+        P2_CUDA_TRY(cudaMemcpy(&r0, row_ptr, 8, cudaMemcpyDeviceToHost));
+        P2_CUDA_TRY(cudaMemcpy(&nnz, row_ptr + N, 8, cudaMemcpyDeviceToHost));
+    }
+    if (r0 != 0 || nnz < 0 || nnz >= (1LL << 31))
+        return fail(P2_EINVAL, "p2_load_slices: row_ptr[0] must be 0 and 0 <= row_ptr[N] < 2^31");
+    if (nnz > 0 && (!col || !val)) return fail(P2_EINVAL, "p2_load_slices: NULL col/val");
+    free_data(c);
+    P2_TRY(alloc_data(c, K, J, N, nnz));
+    // raw copies of the caller's arrays (subject pointers land in place)
+    int64_t *d_row_ptr = nullptr;
+    int32_t *d_col = nullptr;
+    P2_TRY(dalloc(c, &d_row_ptr, (size_t)N + 1));
+    int rc = dalloc(c, &d_col, (size_t)nnz);
+    if (rc != P2_OK) {
+        dfree(c, &d_row_ptr, (size_t)N + 1);
+        free_data(c);
+        return rc;
+    }
+    int64_t *d_subj = nullptr;
+    rc = dalloc(c, &d_subj, (size_t)K + 1);
+    cudaError_t e = cudaSuccess;
+    if (rc == P2_OK) {
+        e = cudaMemcpyAsync(d_subj, subj_ptr, 8 * ((size_t)K + 1), kind, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_row_ptr, row_ptr, 8 * ((size_t)N + 1), kind, s);
+        if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(d_col, col, 4 * (size_t)nnz, kind, s);
+        if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(c->X.val, val, 4 * (size_t)nnz, kind, s);
+        if (e != cudaSuccess) {
+            set_error("p2_load_slices: copy failed: %s", cudaGetErrorString(e));
+            rc = P2_ECUDA;
+        }
+    }
+    if (rc == P2_OK) rc = launch_load(c, d_subj, d_row_ptr, d_col, c->X.val, K, J, N, nnz);
+    cudaStreamSynchronize(s);
+    dfree(c, &d_subj, (size_t)K + 1);
+    dfree(c, &d_row_ptr, (size_t)N + 1);
+    dfree(c, &d_col, (size_t)nnz);
+    if (rc != P2_OK) {
+        free_data(c);
+        return rc;
+    }
+    c->loaded = true;
+    return P2_OK;
+}
+
+int p2_init(p2_ctx *c, const float *H0, const float *V0, const float *W0) {
+    P2_TRY(check_ready(c, false));
+    if (!H0 || !V0 || !W0) return fail(P2_EINVAL, "p2_init: NULL factor");
+    P2_CUDA_TRY(cudaSetDevice(c->opt.device));
+    return set_factors_impl(c, H0, V0, W0);
+}
+
+int p2_set_factors(p2_ctx *c, const float *H, const float *V, const float *W) {
+    P2_TRY(check_ready(c, false));
+    if (!H || !V || !W) return fail(P2_EINVAL, "p2_set_factors: NULL factor");
+    P2_CUDA_TRY(cudaSetDevice(c->opt.device));
+    return set_factors_impl(c, H, V, W);
+}
+
+int p2_iterate(p2_ctx *c, int32_t n_iter, double *fit_out) {
+    P2_TRY(check_ready(c, true));
+    if (n_iter < 0) return fail(P2_EINVAL, "p2_iterate: n_iter < 0");
+    P2_CUDA_TRY(cudaSetDevice(c->opt.device));
+    if (n_iter > 0 && c->opt.use_graph && !c->graph) {
+        cudaGraph_t g = nullptr;
+        P2_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_iteration(c);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc != P2_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) {
+            set_error("graph capture failed: %s", cudaGetErrorString(e));
+            return P2_ECUDA;
+        }
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->graph = nullptr;
+            set_error("graph instantiate failed: %s", cudaGetErrorString(e));
+            return P2_ECUDA;
+        }
+    }
+    for (int32_t i = 0; i < n_iter; ++i) {
+        if (c->opt.use_graph) {
+            P2_CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
+        } else {
+            P2_TRY(enqueue_iteration(c));
+        }
+    }
+    c->iters_done += n_iter;
+    if (fit_out) {
+        int flags = 0;
+        P2_TRY(read_flags(c, &flags));
+        P2_TRY(flags_status(flags));
+        P2_CUDA_TRY(cudaMemcpy(fit_out, &c->d_s->fit, sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return P2_OK;
+}
+
+int p2_fit(p2_ctx *c, double *fit, double *loss) {
+    P2_TRY(check_ready(c, true));
+    if (c->iters_done == 0) return fail(P2_ESTATE, "p2_fit: no iteration completed yet");
+    P2_CUDA_TRY(cudaSetDevice(c->opt.device));
+    int flags = 0;
+    P2_TRY(read_flags(c, &flags));
+    P2_TRY(flags_status(flags));
+    if (fit) P2_CUDA_TRY(cudaMemcpy(fit, &c->d_s->fit, sizeof(double), cudaMemcpyDeviceToHost));
+    if (loss) P2_CUDA_TRY(cudaMemcpy(loss, &c->d_s->loss, sizeof(double), cudaMemcpyDeviceToHost));
+    return P2_OK;
+}
+
+int p2_get_factors(p2_ctx *c, float *H, float *V, float *W) {
+    P2_TRY(check_ready(c, true));
+    P2_CUDA_TRY(cudaSetDevice(c->opt.device));
+    const int R = c->R;
+    P2_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (H) P2_CUDA_TRY(cudaMemcpy(H, c->d_H, sizeof(float) * R * R, cudaMemcpyDeviceToHost));
+    if (V) {
+        std::vector<float> Vp((size_t)c->X.J * R);
+        P2_CUDA_TRY(cudaMemcpy(Vp.data(), c->d_V, sizeof(float) * Vp.size(), cudaMemcpyDeviceToHost));
+        for (int32_t j = 0; j < c->X.J; ++j)
+            memcpy(V + (size_t)j * R, &Vp[(size_t)c->h_perm_old2new[j] * R], sizeof(float) * R);
+    }
+    if (W) P2_CUDA_TRY(cudaMemcpy(W, c->d_W, sizeof(float) * (size_t)c->X.K * R, cudaMemcpyDeviceToHost));
+    return P2_OK;
+}
+
+int p2_get_mttkrp(p2_ctx *c, int32_t mode, double *out) {
+    P2_TRY(check_ready(c, true));
+    if (!out) return fail(P2_EINVAL, "p2_get_mttkrp: NULL out");
+    if (c->iters_done == 0) return fail(P2_ESTATE, "p2_get_mttkrp: no iteration completed yet");
+    P2_CUDA_TRY(cudaSetDevice(c->opt.device));
+    P2_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const int R = c->R;
+    if (mode == 1) {
+        P2_CUDA_TRY(cudaMemcpy(out, c->d_s->M1, sizeof(double) * R * R, cudaMemcpyDeviceToHost));
+    } else if (mode == 2) {
+        std::vector<double> M((size_t)c->X.J * R);
+        P2_CUDA_TRY(cudaMemcpy(M.data(), c->d_M2, sizeof(double) * M.size(), cudaMemcpyDeviceToHost));
+        for (int32_t j = 0; j < c->X.J; ++j)
+            memcpy(out + (size_t)j * R, &M[(size_t)c->h_perm_old2new[j] * R], sizeof(double) * R);
+    } else if (mode == 3) {
+        std::vector<float> M((size_t)c->X.K * R);
+        P2_CUDA_TRY(cudaMemcpy(M.data(), c->d_M3, sizeof(float) * M.size(), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < M.size(); ++i) out[i] = (double)M[i];
+    } else {
+        return fail(P2_EINVAL, "p2_get_mttkrp: mode must be 1, 2 or 3");
+    }
+    return P2_OK;
+}
+
+int p2_get_procrustes(p2_ctx *c, int64_t k0, int64_t k1, float *T) {
+    P2_TRY(check_ready(c, true));
+    if (k0 < 0 || k1 < k0 || k1 > c->X.K) return fail(P2_EINVAL, "p2_get_procrustes: bad range");
+    if (k1 > k0 && !T) return fail(P2_EINVAL, "p2_get_procrustes: NULL out");
+    P2_CUDA_TRY(cudaSetDevice(c->opt.device));
+    P2_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const size_t RR = (size_t)c->R * c->R;
+    if (k1 > k0)
+        P2_CUDA_TRY(cudaMemcpy(T, c->d_T + (size_t)k0 * RR, sizeof(float) * RR * (size_t)(k1 - k0),
+                               cudaMemcpyDeviceToHost));
+    return P2_OK;
+}
+
+int p2_device_bytes(p2_ctx *c, int64_t *bytes) {
+    if (!c || !bytes) return fail(P2_EINVAL, "NULL argument");
+    *bytes = (int64_t)c->dev_bytes;
+    return P2_OK;
+}
+
+const char *p2_last_error(void) { return g_err; }
+
+}  // extern "C"

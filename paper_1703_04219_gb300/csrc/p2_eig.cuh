@@ -1,0 +1,194 @@
+// Symmetric eigen-decomposition of one small FP64 matrix by one thread.
+//
+// Used by the Procrustes step (Section 3.2): with one GPU lane per subject,
+// the R x R matrix A_k^T A_k is decomposed as Z diag(d) Z^T so that the
+// polar factor's pseudo-inverse square root can be formed.
+//
+// Method (Golub & Van Loan, "Matrix Computations", 4th ed., Algorithms
+// 5.1.1, 8.3.1 and 8.3.2): Householder reduction to tridiagonal form with
+// backward accumulation of the orthogonal factor, then implicit symmetric QR
+// steps with the Wilkinson shift and deflation, rotations accumulated into
+// the eigenvector matrix.  Cost ~ (4/3) n^3 + O(n^2) rotations, versus the
+// ~6 n^3 per sweep of cyclic Jacobi: FP64 issue slots are the scarce resource
+// on this GPU, so the cheaper method wins.
+//
+// The matrix and vectors are reached through small accessor objects so the
+// same code runs on interleaved shared memory (element e of thread t at
+// base[e * stride + t]) on the GPU and on plain arrays on the host.
+#pragma once
+
+#ifndef P2_HD
+#define P2_HD __host__ __device__ __forceinline__
+#endif
+
+#include <math.h>
+
+namespace p2 {
+
+struct MatView {
+    double *base;
+    int stride;
+    int n;
+    P2_HD double &operator()(int i, int j) const { return base[(size_t)(i * n + j) * stride]; }
+};
+
+struct VecView {
+    double *base;
+    int stride;
+    P2_HD double &operator[](int i) const { return base[(size_t)i * stride]; }
+};
+
+// Reduce the symmetric matrix held in the lower triangle of A (n x n) to
+// tridiagonal form T = Q^T A Q, then overwrite A with Q (full storage).
+// On return d[0..n) is diag(T) and e[0..n-1) its sub-diagonal.
+// beta and t are work vectors of length n.
+P2_HD void tridiagonalize(int n, MatView A, VecView d, VecView e, VecView beta, VecView t) {
+    for (int k = 0; k + 2 < n; ++k) {
+        // Householder vector for x = A[k+1:n, k]
+        double sigma = 0.0;
+        for (int i = k + 2; i < n; ++i) sigma = fma(A(i, k), A(i, k), sigma);
+        double x0 = A(k + 1, k);
+        if (sigma == 0.0) {
+            beta[k] = 0.0;
+            e[k] = x0;
+            continue;
+        }
+        double mu = sqrt(x0 * x0 + sigma);
+        double v0 = (x0 <= 0.0) ? (x0 - mu) : (-sigma / (x0 + mu));
+        double b = 2.0 * v0 * v0 / (sigma + v0 * v0);
+        double inv_v0 = 1.0 / v0;
+        for (int i = k + 2; i < n; ++i) A(i, k) *= inv_v0;     // v = [1, A(k+2:n,k)]
+        beta[k] = b;
+        e[k] = mu;
+        // p = b * A22 v  (A22 symmetric, lower triangle stored), K = b/2 p^T v
+        double pv = 0.0;
+        for (int i = k + 1; i < n; ++i) {
+            double s = 0.0;
+            for (int j = k + 1; j < n; ++j) {
+                double vj = (j == k + 1) ? 1.0 : A(j, k);
+                double aij = (j <= i) ? A(i, j) : A(j, i);
+                s = fma(aij, vj, s);
+            }
+            s *= b;
+            t[i] = s;
+            double vi = (i == k + 1) ? 1.0 : A(i, k);
+            pv = fma(s, vi, pv);
+        }
+        double Kc = 0.5 * b * pv;
+        for (int i = k + 1; i < n; ++i) {                      // w = p - K v
+            double vi = (i == k + 1) ? 1.0 : A(i, k);
+            t[i] = fma(-Kc, vi, t[i]);
+        }
+        for (int i = k + 1; i < n; ++i) {                      // A22 -= v w^T + w v^T
+            double vi = (i == k + 1) ? 1.0 : A(i, k);
+            double wi = t[i];
+            for (int j = k + 1; j <= i; ++j) {
+                double vj = (j == k + 1) ? 1.0 : A(j, k);
+                A(i, j) = A(i, j) - vi * t[j] - wi * vj;
+            }
+        }
+    }
+    if (n >= 2) e[n - 2] = A(n - 1, n - 2);
+    for (int i = 0; i < n; ++i) d[i] = A(i, i);
+
+    // Backward accumulation Q = P_0 P_1 ... P_{n-3}, in place.
+    if (n >= 2) {
+        A(n - 1, n - 1) = 1.0;
+        A(n - 2, n - 2) = 1.0;
+        A(n - 1, n - 2) = 0.0;
+        A(n - 2, n - 1) = 0.0;
+    } else if (n == 1) {
+        A(0, 0) = 1.0;
+        return;
+    }
+    for (int k = n - 3; k >= 0; --k) {
+        A(k + 1, k + 1) = 1.0;
+        for (int j = k + 2; j < n; ++j) {
+            A(k + 1, j) = 0.0;
+            A(j, k + 1) = 0.0;
+        }
+        double b = beta[k];
+        if (b == 0.0) continue;
+        for (int c = k + 1; c < n; ++c) {
+            double s = A(k + 1, c);
+            for (int i = k + 2; i < n; ++i) s = fma(A(i, k), A(i, c), s);
+            s *= b;
+            A(k + 1, c) -= s;
+            for (int i = k + 2; i < n; ++i) A(i, c) = fma(-s, A(i, k), A(i, c));
+        }
+    }
+    A(0, 0) = 1.0;
+    for (int j = 1; j < n; ++j) {
+        A(0, j) = 0.0;
+        A(j, 0) = 0.0;
+    }
+}
+
+// Implicit symmetric QR with Wilkinson shift on the tridiagonal (d, e);
+// rotations are accumulated into the columns of Z (n x n).  Returns the
+// number of QR steps taken, or -1 if max_steps was exceeded (d then holds
+// the current, partly converged, diagonal).
+P2_HD int tridiagonal_qr(int n, MatView Z, VecView d, VecView e, int max_steps) {
+    const double eps = 2.220446049250313e-16;
+    double anorm = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double r = fabs(d[i]) + ((i + 1 < n) ? fabs(e[i]) : 0.0) + ((i > 0) ? fabs(e[i - 1]) : 0.0);
+        anorm = fmax(anorm, r);
+    }
+    const double tiny = eps * anorm;
+    int steps = 0;
+    int q = n - 1;
+    while (q > 0) {
+        double eq = e[q - 1];
+        if (fabs(eq) <= eps * (fabs(d[q - 1]) + fabs(d[q])) || fabs(eq) <= tiny) {
+            e[q - 1] = 0.0;
+            --q;
+            continue;
+        }
+        int p = q - 1;
+        while (p > 0) {
+            double ep = e[p - 1];
+            if (fabs(ep) <= eps * (fabs(d[p - 1]) + fabs(d[p])) || fabs(ep) <= tiny) {
+                e[p - 1] = 0.0;
+                break;
+            }
+            --p;
+        }
+        if (++steps > max_steps) return -1;
+        // Wilkinson shift from the trailing 2 x 2 block
+        double dd = 0.5 * (d[q - 1] - d[q]);
+        double h = sqrt(dd * dd + eq * eq);
+        double mu = d[q] - eq * eq / (dd + (dd >= 0.0 ? h : -h));
+        double x = d[p] - mu;
+        double z = e[p];
+        for (int k = p; k < q; ++k) {
+            double r = sqrt(x * x + z * z);
+            double c = 1.0, s = 0.0;
+            if (r > 0.0) {
+                double ir = 1.0 / r;
+                c = x * ir;
+                s = -z * ir;
+            }
+            if (k > p) e[k - 1] = r;
+            double a = d[k], bb = d[k + 1], g = e[k];
+            double cc = c * c, ss = s * s, cs = c * s;
+            d[k] = cc * a - 2.0 * cs * g + ss * bb;
+            d[k + 1] = ss * a + 2.0 * cs * g + cc * bb;
+            e[k] = cs * (a - bb) + (cc - ss) * g;
+            if (k + 1 < q) {
+                double en = e[k + 1];
+                z = -s * en;
+                e[k + 1] = c * en;
+                x = e[k];
+            }
+            for (int i = 0; i < n; ++i) {
+                double zk = Z(i, k), zk1 = Z(i, k + 1);
+                Z(i, k) = c * zk - s * zk1;
+                Z(i, k + 1) = s * zk + c * zk1;
+            }
+        }
+    }
+    return steps;
+}
+
+}  // namespace p2

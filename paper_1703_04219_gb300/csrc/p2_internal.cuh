@@ -1,0 +1,126 @@
+// Internal declarations shared by the translation units of libp2.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/p2.h"
+
+#define P2_RMAX 64
+
+namespace p2 {
+
+// error flags raised by kernels (bit mask in ctx device memory)
+enum : int {
+    FLAG_BAD_PTR = 1,        // non-monotone subject/row pointers or row longer than 65535
+    FLAG_BAD_COL = 2,        // column out of range or not strictly increasing in a row
+    FLAG_BAD_VAL = 4,        // non-finite value
+    FLAG_EIG_NOCONV = 8,     // an eigen iteration hit its step limit
+    FLAG_FIXED_OVF = 16,     // mode-2 fixed-point term out of range
+    FLAG_NONFINITE = 32,     // non-finite loss / factor
+};
+
+void set_error(const char *fmt, ...);
+
+#define P2_CUDA_TRY(call)                                                                  \
+    do {                                                                                   \
+        cudaError_t _e = (call);                                                           \
+        if (_e != cudaSuccess) {                                                           \
+            ::p2::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e),      \
+                            __FILE__, __LINE__);                                           \
+            return P2_ECUDA;                                                               \
+        }                                                                                  \
+    } while (0)
+
+// Small FP64 state that lives in device memory (one copy per context).
+struct SmallState {
+    double M1[P2_RMAX * P2_RMAX];       // mode-1 MTTKRP used by the last H solve
+    double WtW[P2_RMAX * P2_RMAX];
+    double VtV[P2_RMAX * P2_RMAX];
+    double HtH[P2_RMAX * P2_RMAX];
+    double H64[P2_RMAX * P2_RMAX];      // FP32 H widened to FP64
+    double P2inv[P2_RMAX * P2_RMAX];    // (W^TW * H^TH)^+ for the V solve
+    double G3inv[P2_RMAX * P2_RMAX];    // (V^TV * H^TH)^+ for the W solve
+    double wmax[P2_RMAX];               // max_k |W(k, s)|
+    double colnorm[P2_RMAX];            // column norms of the unnormalised V
+    float m2scale[P2_RMAX];             // 2^E_s: fixed-point scale of mode-2 terms
+    float pad_[P2_RMAX];
+    double m2inv[P2_RMAX];              // 2^-E_s
+    double wm3;                          // <W, M3>
+    double loss;
+    double fit;
+    double normx2;                       // ||X||_F^2
+    double xbound;                       // max column nnz count * max |x|
+    int flags;
+    int iter;
+};
+
+// Device-resident sparse slices in the internal format.
+struct DevX {
+    int64_t K = 0, N = 0, nnz = 0;
+    int32_t J = 0;
+    int64_t *subj_row = nullptr;   // [K+1] row offsets
+    int64_t *subj_nnz = nullptr;   // [K+1] non-zero offsets
+    uint16_t *row_len = nullptr;   // [N]
+    uint16_t *col = nullptr;       // [nnz] relabelled column ids
+    float *val = nullptr;          // [nnz]
+};
+
+// Launch geometry decided once per context.
+struct Geometry {
+    int nsm = 0;
+    int smem_optin = 0;
+    int red_blocks = 0;     // blocks of the grid reductions (fixed => deterministic)
+};
+
+// kernel launchers (defined in the .cu files)
+int launch_load(struct ::p2_ctx *ctx, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
+                const int32_t *d_col, const float *d_val, int64_t K, int32_t J, int64_t N,
+                int64_t nnz);
+
+}  // namespace p2
+
+struct p2_ctx {
+    p2_options opt;
+    int R = 0;
+    int P = 0;                      // R(R+1)/2
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    p2::Geometry geo;
+
+    p2::DevX X;
+    bool loaded = false;
+    int32_t *d_perm_old2new = nullptr;   // [J]
+    int32_t *h_perm_new2old = nullptr;   // host [J]
+    int32_t *h_perm_old2new = nullptr;   // host [J]
+
+    // factors and per-subject state
+    float *d_H = nullptr;       // R x R
+    float *d_V = nullptr;       // J x R (relabelled rows)
+    float *d_Vprev = nullptr;   // J x R
+    float *d_W = nullptr;       // K x R
+    float *d_T = nullptr;       // K x R x R
+    double *d_G = nullptr;      // K x P (packed lower Gram of Z_k)
+    float *d_M3 = nullptr;      // K x R
+    double *d_M2 = nullptr;     // J x R (relabelled rows)
+    double *d_Vun = nullptr;    // J x R unnormalised V
+    unsigned long long *d_m2acc = nullptr;  // J x R fixed-point accumulators
+    p2::SmallState *d_s = nullptr;
+    double *d_part = nullptr;   // reduction partials (red_blocks x (R*R + 2R + 2))
+    double *d_part2 = nullptr;  // second partial buffer
+    int *d_colcount = nullptr;  // [J] (load time)
+
+    bool inited = false;
+    int iters_done = 0;
+    cudaGraphExec_t graph = nullptr;
+    size_t dev_bytes = 0;
+};
+
+namespace p2 {
+// per-iteration pieces (p2_kernels.cu)
+int enqueue_prologue(p2_ctx *c);     // Q-step + mode-1 MTTKRP for the current (H, V, W)
+int enqueue_iteration(p2_ctx *c);    // one ALS iteration
+int enqueue_factor_stats(p2_ctx *c); // HtH, VtV, WtW, wmax for freshly set factors
+int configure_kernels(p2_ctx *c);    // smem attributes etc.
+}  // namespace p2

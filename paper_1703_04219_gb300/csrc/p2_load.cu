@@ -1,0 +1,182 @@
+// Loading {X_k}: validation and conversion to the internal streaming format,
+// on the device.
+//
+// Internal format (what the passes stream): per subject int64 row and
+// non-zero offsets, per row a uint16 length, per non-zero a uint16 column id
+// (relabelled by decreasing column frequency so that the hottest columns are
+// the smallest ids) and an FP32 value: 6 bytes per non-zero + 2 per row.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "p2_internal.cuh"
+
+namespace p2 {
+
+struct LoadScratch {
+    int flags;
+    int maxabs_bits;
+};
+
+__global__ void k_check_subjects(const int64_t *__restrict__ subj_ptr,
+                                 const int64_t *__restrict__ row_ptr, int64_t K, int64_t N,
+                                 int64_t *subj_row, int64_t *subj_nnz, LoadScratch *ls) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = subj_ptr[k];
+        subj_row[k] = a;
+        if (a < 0 || a > N) {
+            atomicOr(&ls->flags, FLAG_BAD_PTR);
+            subj_nnz[k] = 0;
+            continue;
+        }
+        subj_nnz[k] = row_ptr[a];
+        if (k < K && subj_ptr[k + 1] < a) atomicOr(&ls->flags, FLAG_BAD_PTR);
+    }
+}
+
+__global__ void k_check_rows(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                             const float *__restrict__ val, int64_t N, int64_t nnz, int32_t J,
+                             uint16_t *row_len, int *colcount, LoadScratch *ls) {
+    int fl = 0;
+    int mx = 0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = row_ptr[r], e = row_ptr[r + 1];
+        const int64_t len = e - b;
+        if (b < 0 || e > nnz || len < 0 || len > 65535) {
+            fl |= FLAG_BAD_PTR;
+            row_len[r] = 0;
+            continue;
+        }
+        row_len[r] = (uint16_t)len;
+        int prev = -1;
+        for (int64_t i = b; i < e; ++i) {
+            const int j = col[i];
+            const float x = val[i];
+            if (j < 0 || j >= J || j <= prev) {
+                fl |= FLAG_BAD_COL;
+            } else {
+                atomicAdd(&colcount[j], 1);
+            }
+            prev = j;
+            if (!isfinite(x)) fl |= FLAG_BAD_VAL;
+            else mx = max(mx, __float_as_int(fabsf(x)));
+        }
+    }
+    if (fl) atomicOr(&ls->flags, fl);
+    atomicMax(&ls->maxabs_bits, mx);
+}
+
+// deterministic partial sums of x^2 over fixed non-zero ranges
+__global__ void k_sumsq(const float *__restrict__ val, int64_t nnz, double *part) {
+    __shared__ double red[256];
+    const int64_t per = (nnz + gridDim.x - 1) / gridDim.x;
+    const int64_t a = (int64_t)blockIdx.x * per;
+    const int64_t b = (a + per < nnz) ? (a + per) : nnz;
+    double s = 0.0;
+    for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+        const double x = (double)val[i];
+        s = fma(x, x, s);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_relabel(const int32_t *__restrict__ col, const int32_t *__restrict__ perm,
+                          int64_t nnz, uint16_t *col16) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz;
+         i += (int64_t)gridDim.x * blockDim.x)
+        col16[i] = (uint16_t)perm[col[i]];
+}
+
+int launch_load(p2_ctx *c, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
+                const int32_t *d_col, const float *d_val, int64_t K, int32_t J, int64_t N,
+                int64_t nnz) {
+    cudaStream_t s = c->stream;
+    const int nsm = c->geo.nsm;
+    LoadScratch *ls = nullptr;
+    P2_CUDA_TRY(cudaMallocAsync(&ls, sizeof(LoadScratch), s));
+    P2_CUDA_TRY(cudaMemsetAsync(ls, 0, sizeof(LoadScratch), s));
+    P2_CUDA_TRY(cudaMemsetAsync(c->d_colcount, 0, sizeof(int) * (size_t)J, s));
+    k_check_subjects<<<4 * nsm, 256, 0, s>>>(d_subj_ptr, d_row_ptr, K, N, c->X.subj_row,
+                                             c->X.subj_nnz, ls);
+    if (N > 0)
+        k_check_rows<<<8 * nsm, 256, 0, s>>>(d_row_ptr, d_col, d_val, N, nnz, J, c->X.row_len,
+                                             c->d_colcount, ls);
+    const int nb = c->geo.red_blocks;
+    k_sumsq<<<nb, 256, 0, s>>>(d_val, nnz, c->d_part);
+    P2_CUDA_TRY(cudaGetLastError());
+    LoadScratch h{};
+    P2_CUDA_TRY(cudaMemcpyAsync(&h, ls, sizeof(h), cudaMemcpyDeviceToHost, s));
+    double *hp = new double[nb];
+    int *cc = new int[J];
+    cudaError_t e1 = cudaMemcpyAsync(hp, c->d_part, sizeof(double) * nb, cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaMemcpyAsync(cc, c->d_colcount, sizeof(int) * (size_t)J,
+                                     cudaMemcpyDeviceToHost, s);
+    cudaError_t e3 = cudaStreamSynchronize(s);
+    cudaFreeAsync(ls, s);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        delete[] hp;
+        delete[] cc;
+        set_error("load: device copy failed: %s",
+                  cudaGetErrorString(e3 != cudaSuccess ? e3 : (e1 != cudaSuccess ? e1 : e2)));
+        return P2_ECUDA;
+    }
+    if (h.flags) {
+        delete[] hp;
+        delete[] cc;
+        set_error("p2_load_slices: malformed input (%s%s%s)",
+                  (h.flags & FLAG_BAD_PTR) ? "bad subject/row pointers or row longer than 65535; " : "",
+                  (h.flags & FLAG_BAD_COL) ? "column out of range or not strictly increasing in a row; " : "",
+                  (h.flags & FLAG_BAD_VAL) ? "non-finite value; " : "");
+        return P2_EINVAL;
+    }
+    double nx2 = 0.0;
+    for (int b = 0; b < nb; ++b) nx2 += hp[b];
+    delete[] hp;
+    // relabel: decreasing frequency, ties by original id
+    int maxcount = 0;
+    for (int j = 0; j < J; ++j) maxcount = cc[j] > maxcount ? cc[j] : maxcount;
+    {
+        int32_t *order = c->h_perm_new2old;
+        for (int j = 0; j < J; ++j) order[j] = j;
+        // bottom-up stable merge sort on count, descending
+        int32_t *tmp = new int32_t[J];
+        for (int w = 1; w < J; w <<= 1) {
+            for (int lo = 0; lo < J; lo += 2 * w) {
+                int mid = lo + w < J ? lo + w : J, hi = lo + 2 * w < J ? lo + 2 * w : J;
+                int a = lo, b = mid, o = lo;
+                while (a < mid && b < hi) {
+                    if (cc[order[b]] > cc[order[a]]) tmp[o++] = order[b++];
+                    else tmp[o++] = order[a++];
+                }
+                while (a < mid) tmp[o++] = order[a++];
+                while (b < hi) tmp[o++] = order[b++];
+            }
+            for (int j = 0; j < J; ++j) order[j] = tmp[j];
+        }
+        delete[] tmp;
+        for (int r = 0; r < J; ++r) c->h_perm_old2new[order[r]] = r;
+    }
+    delete[] cc;
+    P2_CUDA_TRY(cudaMemcpyAsync(c->d_perm_old2new, c->h_perm_old2new, sizeof(int32_t) * (size_t)J,
+                                cudaMemcpyHostToDevice, s));
+    if (nnz > 0) k_relabel<<<8 * nsm, 256, 0, s>>>(d_col, c->d_perm_old2new, nnz, c->X.col);
+    P2_CUDA_TRY(cudaGetLastError());
+    float maxabs;
+    memcpy(&maxabs, &h.maxabs_bits, sizeof(float));
+    const double xbound = (double)maxcount * (double)maxabs;
+    P2_CUDA_TRY(cudaMemcpyAsync(&c->d_s->normx2, &nx2, sizeof(double), cudaMemcpyHostToDevice, s));
+    P2_CUDA_TRY(cudaMemcpyAsync(&c->d_s->xbound, &xbound, sizeof(double), cudaMemcpyHostToDevice, s));
+    P2_CUDA_TRY(cudaStreamSynchronize(s));
+    return P2_OK;
+}
+
+}  // namespace p2

@@ -1,0 +1,122 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: factors and MTTKRPs within relative Frobenius 1e-5 of the FP64
+oracle for the FP32 path, fit within 1e-4 after a fixed number of
+iterations.  The one-step tests start both sides from the same FP32-exact
+state, so they isolate kernel error from ALS trajectory divergence.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import parafac2 as P
+from tests.helpers import rel_fro, slices_from_dense
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+FIT_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def p2():
+    import paper_1703_04219_gb300 as mod
+    return mod
+
+
+def _one_step(p2, X, R, seed):
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=seed)
+    with p2.Parafac2(R) as m:
+        m.load(X)
+        m.init(H0, V0, W0)
+        fit = m.iterate(1)
+        H, V, W = m.factors()
+        M = {n: m.mttkrp(n) for n in (1, 2, 3)}
+    blocks = P.all_blocks(X)
+    ref = P.als_iteration(blocks, H0.astype(np.float64), V0.astype(np.float64),
+                          W0.astype(np.float64))
+    nx2 = P.norm_x_sq(blocks)
+    return dict(fit=fit, H=H, V=V, W=W, M=M, ref=ref, ref_fit=P.fit_from_loss(ref["loss"], nx2))
+
+
+@pytest.mark.parametrize("name,K,R", [("tiny", 200, 5), ("tiny", 200, 1), ("tiny", 97, 8),
+                                      ("c63m", 3000, 10), ("c250m", 400, 40)])
+def test_one_step_parity(p2, name, K, R):
+    X = synth.generate(name, K=K)
+    out = _one_step(p2, X, R, seed=11)
+    ref = out["ref"]
+    for mode, key in ((1, "M1"), (2, "M2"), (3, "M3")):
+        assert rel_fro(out["M"][mode], ref[key]) < TOL, (key, rel_fro(out["M"][mode], ref[key]))
+    for key in ("H", "V", "W"):
+        assert rel_fro(out[key], ref[key]) < TOL, (key, rel_fro(out[key], ref[key]))
+    assert abs(out["fit"] - out["ref_fit"]) < FIT_TOL
+
+
+def test_tiny_ten_iterations(p2):
+    """The tiny workload (K=200, J=100, R=5), 10 iterations from the same start."""
+    X = synth.generate("tiny")
+    R = 5
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=20170314)
+    with p2.Parafac2(R) as m:
+        m.load(X)
+        m.init(H0, V0, W0)
+        fits = [m.iterate(1) for _ in range(10)]
+        H, V, W = m.factors()
+    ref = P.parafac2_als(X, H0, V0, W0, n_iter=10)
+    ref_fits = [h["fit"] for h in ref["history"]]
+    assert max(abs(a - b) for a, b in zip(fits, ref_fits)) < FIT_TOL
+    for key, got in (("H", H), ("V", V), ("W", W)):
+        assert rel_fro(got, ref[key]) < 1e-4, (key, rel_fro(got, ref[key]))
+
+
+def test_graph_and_eager_agree_bitwise(p2):
+    X = synth.generate("c63m", K=1500)
+    R = 10
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=3)
+    outs = []
+    for graph in (True, False, True):
+        with p2.Parafac2(R, use_graph=graph) as m:
+            m.load(X)
+            m.init(H0, V0, W0)
+            m.iterate(3)
+            outs.append(m.factors())
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+    for a, b in zip(outs[0], outs[2]):
+        assert np.array_equal(a, b)
+
+
+def test_edge_cases_empty_rows_and_small_subjects(p2):
+    rng = np.random.default_rng(0)
+    J, R = 12, 4
+    mats = []
+    for k in range(30):
+        I = int(rng.integers(1, 7))
+        m = rng.random((I, J)) * (rng.random((I, J)) < 0.4)
+        if k % 5 == 0:
+            m[0, :] = 0.0                      # an empty row
+        if k % 7 == 0:
+            m = np.vstack([m, 2.0 * m[:1]])    # proportional rows: rank deficient
+        mats.append(m)
+    X = slices_from_dense(mats, J)
+    out = _one_step(p2, X, R, seed=5)
+    ref = out["ref"]
+    for key in ("H", "V", "W"):
+        assert rel_fro(out[key], ref[key]) < TOL, (key, rel_fro(out[key], ref[key]))
+
+
+def test_invalid_input_rejected(p2):
+    X = synth.generate("tiny", K=10)
+    with p2.Parafac2(3) as m:
+        bad = X.col.copy()
+        bad[0] = X.J + 5
+        with pytest.raises(p2.P2Error) as ei:
+            p2.p2_load_slices(m.ctx, X.K, X.J, X.subj_ptr, X.row_ptr, bad, X.val)
+        assert ei.value.code == p2.P2_EINVAL
+        badv = X.val.copy()
+        badv[3] = np.nan
+        with pytest.raises(p2.P2Error):
+            p2.p2_load_slices(m.ctx, X.K, X.J, X.subj_ptr, X.row_ptr, X.col, badv)
+        with pytest.raises(p2.P2Error) as ei:
+            p2.p2_iterate(m.ctx, 1)
+        assert ei.value.code == p2.P2_ESTATE

@@ -1,0 +1,389 @@
+"""Benchmark: PARAFAC2-ALS iterations (SPARTan formulation) on GB300.
+
+One step = one full ALS iteration of Algorithm 2 (Q-step for every subject,
+the three MTTKRPs of Algorithm 3, the H/V/W solves and the fit) over the
+whole synthetic collection, replayed from a CUDA graph with the data
+resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c63m]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+
+Multi-GPU: the path has per-iteration reductions over all subjects, and no
+run here uses more than one GPU, so N ranks run N independent replicas of
+the workload (weak scaling); the only cross-rank step is the timing barrier.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+# the oracle's per-subject numpy work runs single-threaded; state it, do not vary it
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "PARAFAC2-ALS s/iter & nnz/s, 63M-500M nnz, R=10/40; HBM roofline fraction"
+UNIT = "nnz/s"
+FP64_PEAK_TFLOPS = 1.25        # GB300 FP64 (nominal; measured 1.19 with an FMA loop)
+PHASES = ("h_solve", "beta_mode2", "v_solve", "alpha_mode3_w_gram", "w_stats_fit",
+          "procrustes", "mode1")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _workload_desc(w, X):
+    cols = "uniform" if w.col_mode == 0 else f"Zipf({w.zipf_s}) via seeded permutation"
+    return (f"{w.name}: K={w.K:,} subjects, J={w.J:,}, I_k~U{{{w.imin}..{w.imax}}}, "
+            f"Poisson({w.lam})+1 nnz/row, {cols} columns, values 1+Poisson(1), "
+            f"R={w.R}, nnz={X.nnz:,}")
+
+
+def _bytes_model(X, R):
+    """Algorithmic HBM bytes per launch of each kernel group."""
+    K, N, nnz = X.K, X.n_rows, X.nnz
+    P = R * (R + 1) // 2
+    xb = 6 * nnz + 2 * N + 16 * (K + 1)          # u16 col + f32 val, u16 row length, 2 int64 offsets
+    return {
+        "beta_mode2": xb + K * (4 * R * R + 4 * R),
+        "alpha_mode3_w_gram": xb + K * (4 * R * R + 8 * P + 8 * R),
+        "procrustes": K * (8 * P + 4 * R + 4 * R * R),
+        "mode1": K * (4 * R * R + 8 * P + 4 * R),
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = str(gpu_id)
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_id], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        h = hashlib.sha1()
+        csrc = os.path.join(ROOT, "paper_1703_04219_gb300", "csrc")
+        for name in sorted(os.listdir(csrc)):
+            with open(os.path.join(csrc, name), "rb") as g:
+                h.update(g.read())
+        ent = d.get(workload, {}).get(kernel)
+        if ent and ent.get("sources_sha1") == h.hexdigest():
+            return ent["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(w, X, H0, V0, W0, target_s=12.0):
+    """The FP64 oracle, as it stands, on a bounded prefix of the same workload."""
+    import oracle
+    n_pilot = min(X.K, 300)
+    Xs = X.take(range(n_pilot))
+    t = time.perf_counter()
+    oracle.parafac2_als(Xs, H0, V0, W0[:n_pilot], n_iter=1)
+    per = (time.perf_counter() - t) / max(Xs.nnz, 1)
+    n = n_pilot
+    if per > 0:
+        want_nnz = target_s / per
+        n = int(min(X.K, max(n_pilot, n_pilot * want_nnz / max(Xs.nnz, 1))))
+    Xs = X.take(range(n))
+    t = time.perf_counter()
+    oracle.parafac2_als(Xs, H0, V0, W0[:n], n_iter=1)
+    dt = time.perf_counter() - t
+    return {"value": Xs.nnz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n:,} subjects of {w.name} ({Xs.nnz:,} nnz), 1 iteration, "
+                      f"{dt:.1f} s, numpy FP64 single-threaded"}
+
+
+def run_reference(args, w):
+    """--impl reference: the FP64 oracle, bounded sample per step."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import synth
+    import oracle
+    X = synth.generate(w)
+    H0, V0, W0 = synth.init_factors(w.R, X.J, X.K, seed=w.seed)
+    # size the per-step sample so that (warmup + steps) steps take ~2 minutes
+    n_pilot = min(X.K, 200)
+    Xp = X.take(range(n_pilot))
+    t = time.perf_counter()
+    oracle.parafac2_als(Xp, H0, V0, W0[:n_pilot], n_iter=1)
+    per_nnz = (time.perf_counter() - t) / max(Xp.nnz, 1)
+    budget = 120.0 / max(args.steps + args.warmup, 1)
+    n = int(min(X.K, max(n_pilot, n_pilot * (budget / per_nnz) / max(Xp.nnz, 1))))
+    Xs = X.take(range(n))
+    blocks = oracle.all_blocks(Xs)
+    H, V, Wk = (np.asarray(a, np.float64) for a in (H0, V0, W0[:n]))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        out = oracle.als_iteration(blocks, H, V, Wk)
+        dt = time.perf_counter() - t
+        H, V, Wk = out["H"], out["V"], out["W"]
+        if i >= args.warmup:
+            times.append(dt)
+    step = statistics.mean(times)
+    value = Xs.nnz / step
+    sample = (f"first {n:,} subjects of {w.name} ({Xs.nnz:,} nnz) per step, "
+              f"numpy FP64 single-threaded")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": _workload_desc(w, X), "sample_subjects": n,
+                       "sample_nnz": int(Xs.nnz)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_p2(args, w):
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    import synth
+    import paper_1703_04219_gb300 as p2
+
+    X = synth.generate(w)
+    R = w.R
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=w.seed)
+    stream = torch.cuda.Stream()
+    m = p2.Parafac2(R, device=local, stream=stream.cuda_stream, timing=True)
+    m.load(X)
+    m.init(H0, V0, W0)
+    for _ in range(args.warmup):
+        m.iterate(1, want_fit=False)
+    stream.synchronize()
+
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = getattr(props, "uuid", None)
+    gpu_id = f"GPU-{gpu_id}" if gpu_id is not None and not str(gpu_id).startswith("GPU-") else \
+        (str(gpu_id) if gpu_id is not None else local)
+    clocks = ClockSampler(gpu_id)
+    st0 = m.stats()
+    phase_sum = {k: 0.0 for k in PHASES}
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        m.iterate(1, want_fit=False)
+        st = m.stats()                  # synchronises the stream; reads this step's phase events
+        for k in PHASES:
+            phase_sum[k] += st["phase_ms"].get(k, 0.0)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    st1 = m.stats()
+    fit, loss = m.fit()
+    if pg:
+        t = torch.tensor([ms_total], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * X.nnz * args.steps / (ms_total / 1e3)
+    phase_ms = {k: v / args.steps for k, v in phase_sum.items()}
+    launches = st1["kernel_launches"] - st0["kernel_launches"]
+
+    # roofline of the dominant kernel group
+    dom = max(phase_ms, key=phase_ms.get)
+    bmodel = _bytes_model(X, R)
+    hbm_peak, hbm_src = _peaks()
+    if dom == "procrustes":
+        flops = (st1["polar_fp64_flops"] - st0["polar_fp64_flops"]) / args.steps
+        ach = flops / (phase_ms[dom] / 1e3) / 1e12
+        roof = {"kernel": "k_polar (FP64 Procrustes, lane per subject)", "bound": "alu",
+                "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "FP64 nominal 1.25 TFLOP/s "
+                "(recipe table); measured FMA loop 1.19",
+                "algorithmic_flops_per_launch": flops,
+                "traffic": _traffic("k_polar", w.name)}
+    else:
+        by = bmodel.get(dom, 0)
+        ach = by / (phase_ms[dom] / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "peak_source": hbm_src,
+                "algorithmic_bytes_per_launch": by, "traffic": _traffic(dom, w.name)}
+    sparse = {}
+    for k in ("beta_mode2", "alpha_mode3_w_gram"):
+        gbs = bmodel[k] / (phase_ms[k] / 1e3) / 1e9 if phase_ms[k] > 0 else None
+        sparse[k] = {"ms": phase_ms[k], "algorithmic_GBps": gbs,
+                     "hbm_frac": gbs / hbm_peak if gbs else None}
+
+    # end-to-end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(m, X, H0, V0, W0, args.e2e_steps, world, pg)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w, X, H0, V0, W0)
+    m.close()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "s_per_iter": ms_step / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 storage/SpMM, f64 Gram, Procrustes and solves", "data": "synthetic",
+            "config": {"workload": _workload_desc(w, X), "K": X.K, "J": X.J, "R": R,
+                       "nnz": int(X.nnz), "rows": int(X.n_rows),
+                       "l2": "inputs larger than L2: X (~6 B/nnz) streamed twice per step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "graph": True, "fit_after_steps": fit},
+            "phase_ms": phase_ms, "sparse_passes": sparse, "roofline": roof,
+            "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def run_e2e(m, X, H0, V0, W0, steps, world, pg):
+    """Per step: p2_load_slices from pinned host memory + p2_init + one iteration
+    + the fit read back (device -> host)."""
+    import torch
+    import paper_1703_04219_gb300 as p2
+    arrs = [X.subj_ptr, X.row_ptr, X.col, X.val]
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in arrs]
+    fac = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (H0, V0, W0)]
+    h2d = sum(t.numel() * t.element_size() for t in pinned + fac)
+    times = []
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        t = time.perf_counter()
+        p2.p2_load_slices(m.ctx, X.K, X.J, *pinned, location=0)
+        lib = p2.lib
+        rc = lib.p2_init(m.ctx, p2._ptr(fac[0]), p2._ptr(fac[1]), p2._ptr(fac[2]))
+        p2._check(rc, "p2_init")
+        fit = m.iterate(1, want_fit=True)
+        dt = time.perf_counter() - t
+        if i > 0:                      # first one warms the allocator
+            times.append(dt)
+    step = statistics.mean(times)
+    if pg:
+        t = torch.tensor([step], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        step = float(t.item())
+    return {"value": world * X.nnz / step, "unit": UNIT, "s_per_step": step,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8,
+            "step": "p2_load_slices (host, pinned) + p2_init + p2_iterate(1) + fit read-back",
+            "fit": fit}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="p2", choices=["p2", "reference"])
+    ap.add_argument("--workload", default="c63m")
+    ap.add_argument("--K", type=int, default=None, help="override the number of subjects")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    import synth
+    w = synth.WORKLOADS[args.workload]
+    if args.K:
+        w = w.scaled(args.K)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_p2(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

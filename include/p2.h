@@ -55,10 +55,24 @@ typedef struct {
     double rank_rtol;     /* Procrustes rank cut: singular values <= rank_rtol * sigma_1 of
                              X_k V S_k H^T are dropped; <= 0 selects the default 1e-5 */
     void *stream;         /* cudaStream_t to enqueue on; NULL: the context creates its own */
+    int32_t timing;       /* non-zero: CUDA events around each phase of an iteration (p2_stats) */
 } p2_options;
 
+/* Counters and timings of a context (p2_stats). */
+typedef struct {
+    int64_t kernel_launches;    /* kernels this context has enqueued (graph replays included) */
+    int64_t iterations;         /* ALS iterations completed */
+    double polar_fp64_flops;    /* FP64 flops executed by the Procrustes kernel so far
+                                   (fused multiply-add = 2), counted from the operations the
+                                   kernel performed, including its data-dependent QR steps */
+    int32_t n_phases;           /* 7 when timing is on, else 0 */
+    float phase_ms[8];          /* last iteration: H solve, pass beta (mode 2), V solve,
+                                   pass alpha (mode 3 + W + Gram), W statistics + fit,
+                                   Procrustes, mode-1 reduction */
+} p2_stats_t;
+
 /* Fill *opt with defaults for rank R (precision FP32, device 0, graph on,
- * rank_rtol 1e-5, own stream). */
+ * rank_rtol 1e-5, own stream, timing off). */
 void p2_default_options(p2_options *opt, int32_t R);
 
 /* Create a context on opt->device.  *out receives the handle (NULL on error).
@@ -81,8 +95,8 @@ int p2_destroy(p2_ctx *ctx);
  *   location  0: all four pointers are host memory; 1: device memory
  * Empty rows and subjects with no rows are allowed (they add nothing to the
  * model; Section 3.3 notes zero rows can be dropped without effect).  Limits:
- * N < 2^31, nnz < 2^31.  Malformed input returns P2_EINVAL and leaves any
- * previously loaded data in place.  The columns are relabelled internally by
+ * N < 2^31, nnz < 2^31.  Malformed input returns P2_EINVAL; after any
+ * failure the context holds no slices (load again).  The columns are relabelled internally by
  * decreasing frequency; every factor the API returns is in the caller's
  * column order.  Synchronises.
  */
@@ -100,9 +114,10 @@ int p2_init(p2_ctx *ctx, const float *H0, const float *V0, const float *W0);
 /*
  * Run n_iter >= 0 iterations of PARAFAC2-ALS (Algorithm 2 loop body: Q-step,
  * one CP-ALS sweep on Y with Algorithm 3's MTTKRPs, S_k = diag(W(k,:))).
- * fit_out (nullable, host): fit after the last iteration, as p2_fit.
- * Returns P2_ENUMERIC if a non-finite loss or a fixed-point overflow was
- * detected during these iterations.
+ * fit_out (nullable, host): fit after the last iteration, as p2_fit.  With
+ * fit_out == NULL the call only enqueues and returns; with fit_out it
+ * synchronises and returns P2_ENUMERIC if a non-finite loss or a fixed-point
+ * overflow was detected (p2_fit reports the same later otherwise).
  */
 int p2_iterate(p2_ctx *ctx, int32_t n_iter, double *fit_out);
 
@@ -140,6 +155,9 @@ int p2_get_mttkrp(p2_ctx *ctx, int32_t mode, double *out);
  * (polar factor of Section 3.2's Procrustes problem).  0 <= k0 <= k1 <= K.
  */
 int p2_get_procrustes(p2_ctx *ctx, int64_t k0, int64_t k1, float *T);
+
+/* Counters and the last iteration's phase timings.  Synchronises. */
+int p2_stats(p2_ctx *ctx, p2_stats_t *out);
 
 /* Bytes of device memory the context holds now. */
 int p2_device_bytes(p2_ctx *ctx, int64_t *bytes);

@@ -25,13 +25,23 @@ _NAMES = {0: "P2_OK", 1: "P2_EINVAL", 2: "P2_ENOMEM", 3: "P2_ECUDA", 4: "P2_ENUM
 # every symbol include/p2.h declares
 EXPORTED = ("p2_default_options", "p2_create", "p2_destroy", "p2_load_slices", "p2_init",
             "p2_iterate", "p2_fit", "p2_get_factors", "p2_set_factors", "p2_get_mttkrp",
-            "p2_get_procrustes", "p2_device_bytes", "p2_last_error")
+            "p2_get_procrustes", "p2_stats", "p2_device_bytes", "p2_last_error")
 
 
 class p2_options(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("rank_rtol", ctypes.c_double),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("timing", ctypes.c_int32)]
+
+
+class p2_stats_t(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("iterations", ctypes.c_int64),
+                ("polar_fp64_flops", ctypes.c_double), ("n_phases", ctypes.c_int32),
+                ("phase_ms", ctypes.c_float * 8)]
+
+
+PHASES = ("h_solve", "beta_mode2", "v_solve", "alpha_mode3_w_gram", "w_stats_fit",
+          "procrustes", "mode1")
 
 
 class P2Error(RuntimeError):
@@ -58,6 +68,7 @@ def _load():
         "p2_set_factors": ([vp, vp, vp, vp], ctypes.c_int),
         "p2_get_mttkrp": ([vp, i32, vp], ctypes.c_int),
         "p2_get_procrustes": ([vp, i64, i64, vp], ctypes.c_int),
+        "p2_stats": ([vp, ctypes.POINTER(p2_stats_t)], ctypes.c_int),
         "p2_device_bytes": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
         "p2_last_error": ([], ctypes.c_char_p),
     }
@@ -113,10 +124,10 @@ def p2_load_slices(ctx, K, J, subj_ptr, row_ptr, col, val, location=None):
     if location is None:
         location = 1 if hasattr(subj_ptr, "is_cuda") and subj_ptr.is_cuda else 0
     if location == 0:
-        subj_ptr = np.ascontiguousarray(subj_ptr, np.int64)
-        row_ptr = np.ascontiguousarray(row_ptr, np.int64)
-        col = np.ascontiguousarray(col, np.int32)
-        val = np.ascontiguousarray(val, np.float32)
+        def host(a, dt):
+            return a if hasattr(a, "data_ptr") else np.ascontiguousarray(a, dt)
+        subj_ptr, row_ptr = host(subj_ptr, np.int64), host(row_ptr, np.int64)
+        col, val = host(col, np.int32), host(val, np.float32)
     _check(lib.p2_load_slices(ctx, int(K), int(J), _ptr(subj_ptr), _ptr(row_ptr), _ptr(col),
                               _ptr(val), int(location)), "p2_load_slices")
 
@@ -164,6 +175,14 @@ def p2_get_procrustes(ctx, k0, k1, R):
     return out
 
 
+def p2_stats(ctx) -> dict:
+    st = p2_stats_t()
+    _check(lib.p2_stats(ctx, ctypes.byref(st)), "p2_stats")
+    return dict(kernel_launches=st.kernel_launches, iterations=st.iterations,
+                polar_fp64_flops=st.polar_fp64_flops,
+                phase_ms={PHASES[i]: st.phase_ms[i] for i in range(st.n_phases)})
+
+
 def p2_device_bytes(ctx) -> int:
     b = ctypes.c_int64()
     _check(lib.p2_device_bytes(ctx, ctypes.byref(b)), "p2_device_bytes")
@@ -174,12 +193,13 @@ class Parafac2:
     """Owning wrapper of one context: load, init, iterate, read back."""
 
     def __init__(self, R: int, device: int = 0, use_graph: bool = True, rank_rtol: float = 1e-5,
-                 stream=None):
+                 stream=None, timing: bool = False):
         opt = p2_default_options(R)
         opt.device = device
         opt.use_graph = 1 if use_graph else 0
         opt.rank_rtol = rank_rtol
         opt.stream = stream
+        opt.timing = 1 if timing else 0
         self.R = R
         self.ctx = p2_create(opt)
         self.K = self.J = 0
@@ -226,6 +246,9 @@ class Parafac2:
 
     def procrustes(self, k0=0, k1=None):
         return p2_get_procrustes(self.ctx, k0, self.K if k1 is None else k1, self.R)
+
+    def stats(self) -> dict:
+        return p2_stats(self.ctx)
 
     def device_bytes(self) -> int:
         return p2_device_bytes(self.ctx)

@@ -178,6 +178,7 @@ void p2_default_options(p2_options *opt, int32_t R) {
     opt->use_graph = 1;
     opt->rank_rtol = 1e-5;
     opt->stream = nullptr;
+    opt->timing = 0;
 }
 
 int p2_create(p2_ctx **out, const p2_options *opt) {
@@ -217,6 +218,15 @@ int p2_create(p2_ctx **out, const p2_options *opt) {
         }
         c->own_stream = true;
     }
+    if (c->opt.timing) {
+        for (int i = 0; i < 8; ++i) {
+            if (cudaEventCreate(&c->ev[i]) != cudaSuccess) {
+                set_error("cudaEventCreate failed");
+                p2_destroy(c);
+                return P2_ECUDA;
+            }
+        }
+    }
     int rc = dalloc(c, &c->d_s, 1);
     if (rc == P2_OK) rc = dalloc(c, &c->d_H, (size_t)c->R * c->R);
     const size_t part_stride = (size_t)c->R * c->R + 2 * (size_t)c->R + 8;
@@ -244,6 +254,8 @@ int p2_destroy(p2_ctx *c) {
     const size_t part_stride = (size_t)c->R * c->R + 2 * (size_t)c->R + 8;
     dfree(c, &c->d_part, (size_t)c->geo.red_blocks * part_stride);
     dfree(c, &c->d_part2, (size_t)c->geo.red_blocks * part_stride);
+    for (int i = 0; i < 8; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return P2_OK;
@@ -340,7 +352,10 @@ int p2_iterate(p2_ctx *c, int32_t n_iter, double *fit_out) {
     if (n_iter > 0 && c->opt.use_graph && !c->graph) {
         cudaGraph_t g = nullptr;
         P2_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        const int64_t before = c->enqueued;
         int rc = enqueue_iteration(c);
+        c->graph_kernels = c->enqueued - before;
+        c->enqueued = before;                  // captured, not yet run
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (rc != P2_OK) {
             if (g) cudaGraphDestroy(g);
@@ -361,6 +376,7 @@ int p2_iterate(p2_ctx *c, int32_t n_iter, double *fit_out) {
     for (int32_t i = 0; i < n_iter; ++i) {
         if (c->opt.use_graph) {
             P2_CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
+            c->enqueued += c->graph_kernels;
         } else {
             P2_TRY(enqueue_iteration(c));
         }
@@ -437,6 +453,32 @@ int p2_get_procrustes(p2_ctx *c, int64_t k0, int64_t k1, float *T) {
     if (k1 > k0)
         P2_CUDA_TRY(cudaMemcpy(T, c->d_T + (size_t)k0 * RR, sizeof(float) * RR * (size_t)(k1 - k0),
                                cudaMemcpyDeviceToHost));
+    return P2_OK;
+}
+
+int p2_stats(p2_ctx *c, p2_stats_t *out) {
+    if (!c || !out) return fail(P2_EINVAL, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    P2_CUDA_TRY(cudaSetDevice(c->opt.device));
+    P2_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    out->kernel_launches = c->enqueued;
+    out->iterations = c->iters_done;
+    if (c->d_s) {
+        unsigned long long fl = 0;
+        P2_CUDA_TRY(cudaMemcpy(&fl, &c->d_s->polar_flops, sizeof(fl), cudaMemcpyDeviceToHost));
+        out->polar_fp64_flops = (double)fl;
+    }
+    if (c->opt.timing && c->iters_done > 0) {
+        out->n_phases = 7;
+        for (int i = 0; i < 7; ++i) {
+            float ms = -1.f;
+            if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) != cudaSuccess) {
+                cudaGetLastError();
+                ms = -1.f;
+            }
+            out->phase_ms[i] = ms;
+        }
+    }
     return P2_OK;
 }
 

@@ -127,8 +127,10 @@ P2_HD void tridiagonalize(int n, MatView A, VecView d, VecView e, VecView beta, 
 // Implicit symmetric QR with Wilkinson shift on the tridiagonal (d, e);
 // rotations are accumulated into the columns of Z (n x n).  Returns the
 // number of QR steps taken, or -1 if max_steps was exceeded (d then holds
-// the current, partly converged, diagonal).
-P2_HD int tridiagonal_qr(int n, MatView Z, VecView d, VecView e, int max_steps) {
+// the current, partly converged, diagonal).  *rotations (if given) is
+// incremented by the number of Givens rotations applied.
+P2_HD int tridiagonal_qr(int n, MatView Z, VecView d, VecView e, int max_steps,
+                         int *rotations = nullptr) {
     const double eps = 2.220446049250313e-16;
     double anorm = 0.0;
     for (int i = 0; i < n; ++i) {
@@ -155,6 +157,7 @@ P2_HD int tridiagonal_qr(int n, MatView Z, VecView d, VecView e, int max_steps) 
             --p;
         }
         if (++steps > max_steps) return -1;
+        if (rotations) *rotations += q - p;
         // Wilkinson shift from the trailing 2 x 2 block
         double dd = 0.5 * (d[q - 1] - d[q]);
         double h = sqrt(dd * dd + eq * eq);

@@ -52,6 +52,7 @@ struct SmallState {
     double fit;
     double normx2;                       // ||X||_F^2
     double xbound;                       // max column nnz count * max |x|
+    unsigned long long polar_flops;     // FP64 flops executed by k_polar (running total)
     int flags;
     int iter;
 };
@@ -114,6 +115,9 @@ struct p2_ctx {
     bool inited = false;
     int iters_done = 0;
     cudaGraphExec_t graph = nullptr;
+    int64_t graph_kernels = 0;      // kernels in one captured iteration
+    int64_t enqueued = 0;           // kernels enqueued (eager launches and graph replays)
+    cudaEvent_t ev[8] = {};         // phase boundaries when opt.timing
     size_t dev_bytes = 0;
 };
 

@@ -334,10 +334,28 @@ __global__ void k_m2_finalize(unsigned long long *m2acc, double *M2, const Small
 // d_i > rtol2 * max(d) else 0, T_k = Z diag(f) Z^T H S  (stored FP32).
 // Per-thread matrices live in interleaved shared memory.
 // ---------------------------------------------------------------------------
+// FP64 flops of the Procrustes kernel for one subject (fused multiply-add =
+// 2; sqrt and division = 1), counted from the operations it performs: the
+// fixed part below plus 11 per QR step and 29 + 6R per Givens rotation.
+static __host__ __device__ unsigned long long polar_fixed_flops(int R) {
+    unsigned long long f = 0;
+    const unsigned long long r = (unsigned long long)R, P = r * (r + 1) / 2;
+    f += 2 * P;                                     // S G S
+    f += 2 * r * r * r + r * r * (r + 1);           // M = H (S G S) H^T, lower triangle
+    for (unsigned long long m = 2; m + 1 <= r; ++m) {
+        f += 4 * m * m + 10 * m + 10;               // Householder step on an m-vector
+        f += m * (4 * m - 2);                       // backward accumulation of that step
+    }
+    f += 3 * r;                                     // QR scale estimate
+    f += 3 * r + 1;                                 // eigenvalue cut and d^-1/2
+    f += 4 * r * r * r + 2 * r * r;                 // T = Z diag(f) Z^T H S
+    return f;
+}
+
 __global__ void __launch_bounds__(128) k_polar(const double *__restrict__ G,
                                                const float *__restrict__ W,
-                                               const SmallState *__restrict__ st, float *T,
-                                               int64_t K, int R, double rtol2, int *flags) {
+                                               SmallState *st, float *T,
+                                               int64_t K, int R, double rtol2) {
     extern __shared__ __align__(16) double sm[];
     const int NT = blockDim.x;
     const int t = threadIdx.x;
@@ -347,57 +365,65 @@ __global__ void __launch_bounds__(128) k_polar(const double *__restrict__ G,
     for (int i = t; i < R * R; i += NT) Hs[i] = st->H64[i];
     __syncthreads();
     const int64_t k = (int64_t)blockIdx.x * NT + t;
-    if (k >= K) return;
+    unsigned long long flops = 0;
+    if (k < K) {
+        MatView A{th + t, NT, R};
+        double *gp = th + (size_t)R * R * NT + t;          // packed scaled Gram, stride NT
+        VecView d{gp + (size_t)P * NT, NT};
+        VecView e{gp + (size_t)(P + R) * NT, NT};
+        VecView bt{gp + (size_t)(P + 2 * R) * NT, NT};
+        VecView tv{gp + (size_t)(P + 3 * R) * NT, NT};
+        VecView w{gp + (size_t)(P + 4 * R) * NT, NT};
 
-    MatView A{th + t, NT, R};
-    double *gp = th + (size_t)R * R * NT + t;          // packed scaled Gram, stride NT
-    VecView d{gp + (size_t)P * NT, NT};
-    VecView e{gp + (size_t)(P + R) * NT, NT};
-    VecView bt{gp + (size_t)(P + 2 * R) * NT, NT};
-    VecView tv{gp + (size_t)(P + 3 * R) * NT, NT};
-    VecView w{gp + (size_t)(P + 4 * R) * NT, NT};
-
-    const float *Wk = W + (size_t)k * R;
-    for (int i = 0; i < R; ++i) w[i] = (double)Wk[i];
-    const double *Gk = G + (size_t)k * P;
-    for (int i = 0, p = 0; i < R; ++i)
-        for (int j = 0; j <= i; ++j, ++p) gp[(size_t)p * NT] = Gk[p] * w[i] * w[j];
-    // M = H Gs H^T, lower triangle, column by column
-    for (int c = 0; c < R; ++c) {
-        for (int i = 0; i < R; ++i) {
-            double s = 0.0;
-            for (int j = 0; j < R; ++j) {
-                const int p = (j <= i) ? (i * (i + 1) / 2 + j) : (j * (j + 1) / 2 + i);
-                s = fma(gp[(size_t)p * NT], Hs[c * R + j], s);
+        const float *Wk = W + (size_t)k * R;
+        for (int i = 0; i < R; ++i) w[i] = (double)Wk[i];
+        const double *Gk = G + (size_t)k * P;
+        for (int i = 0, p = 0; i < R; ++i)
+            for (int j = 0; j <= i; ++j, ++p) gp[(size_t)p * NT] = Gk[p] * w[i] * w[j];
+        // M = H Gs H^T, lower triangle, column by column
+        for (int c = 0; c < R; ++c) {
+            for (int i = 0; i < R; ++i) {
+                double s = 0.0;
+                for (int j = 0; j < R; ++j) {
+                    const int p = (j <= i) ? (i * (i + 1) / 2 + j) : (j * (j + 1) / 2 + i);
+                    s = fma(gp[(size_t)p * NT], Hs[c * R + j], s);
+                }
+                tv[i] = s;
             }
-            tv[i] = s;
+            for (int r = c; r < R; ++r) {
+                double s = 0.0;
+                for (int i = 0; i < R; ++i) s = fma(Hs[r * R + i], tv[i], s);
+                A(r, c) = s;
+            }
         }
-        for (int r = c; r < R; ++r) {
-            double s = 0.0;
-            for (int i = 0; i < R; ++i) s = fma(Hs[r * R + i], tv[i], s);
-            A(r, c) = s;
+        tridiagonalize(R, A, d, e, bt, tv);
+        int rot = 0;
+        const int steps = tridiagonal_qr(R, A, d, e, 30 * R, &rot);
+        if (steps < 0) atomicOr(&st->flags, FLAG_EIG_NOCONV);
+        double lmax = 0.0;
+        for (int i = 0; i < R; ++i) lmax = fmax(lmax, d[i]);
+        const double cut = rtol2 * lmax;
+        for (int i = 0; i < R; ++i) d[i] = (lmax > 0.0 && d[i] > cut) ? 1.0 / sqrt(d[i]) : 0.0;
+        float *Tk = T + (size_t)k * R * R;
+        for (int c = 0; c < R; ++c) {
+            const double wc = w[c];
+            for (int i = 0; i < R; ++i) {
+                double s = 0.0;
+                for (int u = 0; u < R; ++u) s = fma(A(u, i), Hs[u * R + c], s);
+                tv[i] = s * d[i] * wc;
+            }
+            for (int r = 0; r < R; ++r) {
+                double s = 0.0;
+                for (int i = 0; i < R; ++i) s = fma(A(r, i), tv[i], s);
+                Tk[r * R + c] = (float)s;
+            }
         }
+        flops = polar_fixed_flops(R) + 11ull * (unsigned long long)(steps > 0 ? steps : 0) +
+                (29ull + 6ull * R) * (unsigned long long)rot;
     }
-    tridiagonalize(R, A, d, e, bt, tv);
-    if (tridiagonal_qr(R, A, d, e, 30 * R) < 0) atomicOr(flags, FLAG_EIG_NOCONV);
-    double lmax = 0.0;
-    for (int i = 0; i < R; ++i) lmax = fmax(lmax, d[i]);
-    const double cut = rtol2 * lmax;
-    for (int i = 0; i < R; ++i) d[i] = (lmax > 0.0 && d[i] > cut) ? 1.0 / sqrt(d[i]) : 0.0;
-    float *Tk = T + (size_t)k * R * R;
-    for (int c = 0; c < R; ++c) {
-        const double wc = w[c];
-        for (int i = 0; i < R; ++i) {
-            double s = 0.0;
-            for (int u = 0; u < R; ++u) s = fma(A(u, i), Hs[u * R + c], s);
-            tv[i] = s * d[i] * wc;
-        }
-        for (int r = 0; r < R; ++r) {
-            double s = 0.0;
-            for (int i = 0; i < R; ++i) s = fma(A(r, i), tv[i], s);
-            Tk[r * R + c] = (float)s;
-        }
-    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) flops += __shfl_down_sync(FULLMASK, flops, o);
+    if ((t & 31) == 0 && flops) atomicAdd(&st->polar_flops, flops);
 }
 
 // ---------------------------------------------------------------------------
@@ -904,7 +930,14 @@ static int check_launch(const char *what) {
     do {                                              \
         int _rc = check_launch(name);                 \
         if (_rc != P2_OK) return _rc;                 \
+        c->enqueued += 1;                             \
     } while (0)
+
+// Phase boundary event; recorded as an event-record node when the stream is
+// being captured into the iteration graph.
+static void mark(p2_ctx *c, int i) {
+    if (c->opt.timing) cudaEventRecordWithFlags(c->ev[i], c->stream, cudaEventRecordExternal);
+}
 
 static int enqueue_qstep(p2_ctx *c, const Launch &L) {
     const int R = c->R;
@@ -915,9 +948,10 @@ static int enqueue_qstep(p2_ctx *c, const Launch &L) {
     if (K > 0) {
         const int nblk = (int)((K + L.polar_nt - 1) / L.polar_nt);
         k_polar<<<nblk, L.polar_nt, L.polar_smem, s>>>(c->d_G, c->d_W, c->d_s, c->d_T, K, R,
-                                                       rtol2, &c->d_s->flags);
+                                                       rtol2);
         P2_LAUNCH_CHECK("k_polar");
     }
+    mark(c, 6);
     const size_t m1_smem = ((size_t)2 * R * R + R) * 4;
     k_mode1<<<nb, 256, m1_smem, s>>>(c->d_T, c->d_G, c->d_W, c->d_part, K, R);
     P2_LAUNCH_CHECK("k_mode1");
@@ -963,9 +997,11 @@ int enqueue_iteration(p2_ctx *c) {
     XView X = xview(c);
     const size_t sm_pinv = (size_t)4 * R * R * 8;
     // H step (Algorithm 1 line 3 with U = H; mode-1 MTTKRP from the previous pass)
+    mark(c, 0);
     k_solve_h<<<1, 256, sm_pinv, s>>>(c->d_part, nb, c->d_s, c->d_H, R);
     P2_LAUNCH_CHECK("k_solve_h");
     // pass beta: mode-2 MTTKRP
+    mark(c, 1);
     k_beta<<<nsm, L.beta_warps * 32, L.beta_smem, s>>>(X, c->d_V, c->d_H, c->d_T, c->d_W, c->d_s,
                                                        c->d_m2acc, R, L.beta_hc);
     P2_LAUNCH_CHECK("k_beta");
@@ -974,6 +1010,7 @@ int enqueue_iteration(p2_ctx *c) {
     k_m2_finalize<<<fb, 256, 0, s>>>(c->d_m2acc, c->d_M2, c->d_s, nJR, R);
     P2_LAUNCH_CHECK("k_m2_finalize");
     // V step (Algorithm 1 line 5)
+    mark(c, 2);
     k_solve_v_pinv<<<1, 256, sm_pinv, s>>>(c->d_s, R);
     P2_LAUNCH_CHECK("k_solve_v_pinv");
     k_solve_v_rows<<<nb, 256, ((size_t)R * R + 256) * 8, s>>>(c->d_M2, c->d_s, c->d_Vun,
@@ -988,15 +1025,20 @@ int enqueue_iteration(p2_ctx *c) {
     k_fin_v<<<1, 256, sm_pinv, s>>>(c->d_part2, nb, c->d_s, R, 1);
     P2_LAUNCH_CHECK("k_fin_v");
     // pass alpha: mode-3 MTTKRP + W step (Algorithm 1 line 7) + Gram for the next Q-step
+    mark(c, 3);
     k_alpha<true><<<nsm, L.alpha_warps * 32, L.alpha_smem, s>>>(
         X, c->d_Vprev, c->d_V, c->d_H, c->d_T, c->d_s, c->d_G, c->d_W, c->d_M3, R);
     P2_LAUNCH_CHECK("k_alpha<true>");
+    mark(c, 4);
     k_gram_w<<<nb, 256, 0, s>>>(c->d_W, c->d_M3, c->d_part2, K, R, 1);
     P2_LAUNCH_CHECK("k_gram_w");
     k_fin_w<<<1, 256, 0, s>>>(c->d_part2, nb, c->d_s, R, 1);
     P2_LAUNCH_CHECK("k_fin_w");
-    // next Q-step (Algorithm 2, lines for the SVD) and its mode-1 MTTKRP
-    return enqueue_qstep(c, L);
+    // next Q-step (Algorithm 2's SVD loop) and its mode-1 MTTKRP
+    mark(c, 5);
+    int rc = enqueue_qstep(c, L);
+    mark(c, 7);
+    return rc;
 }
 
 }  // namespace p2

@@ -36,8 +36,8 @@ import numpy as np  # noqa: E402
 METRIC = "PARAFAC2-ALS s/iter & nnz/s, 63M-500M nnz, R=10/40; HBM roofline fraction"
 UNIT = "nnz/s"
 FP64_PEAK_TFLOPS = 1.25        # GB300 FP64 (nominal; measured 1.19 with an FMA loop)
-PHASES = ("h_solve", "beta_mode2", "v_solve", "alpha_mode3_w_gram", "w_stats_fit",
-          "procrustes", "mode1")
+PHASES = ("h_solve", "beta_mode2", "v_solve", "alpha_mode3_w_gram", "procrustes",
+          "subject_stats_mode1", "fit")
 
 
 def _peaks():
@@ -65,7 +65,7 @@ def _bytes_model(X, R):
         "beta_mode2": xb + K * (4 * R * R + 4 * R),
         "alpha_mode3_w_gram": xb + K * (4 * R * R + 8 * P + 8 * R),
         "procrustes": K * (8 * P + 4 * R + 4 * R * R),
-        "mode1": K * (4 * R * R + 8 * P + 4 * R),
+        "subject_stats_mode1": K * (4 * R * R + 8 * P + 8 * R),
     }
 
 
@@ -283,7 +283,8 @@ def run_p2(args, w):
     if dom == "procrustes":
         flops = (st1["polar_fp64_flops"] - st0["polar_fp64_flops"]) / args.steps
         ach = flops / (phase_ms[dom] / 1e3) / 1e12
-        roof = {"kernel": "k_polar (FP64 Procrustes, lane per subject)", "bound": "alu",
+        roof = {"kernel": "k_polar_reg/k_polar_smem (FP64 Procrustes, lane per subject)",
+                "bound": "alu",
                 "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "FP64 nominal 1.25 TFLOP/s "
                 "(recipe table); measured FMA loop 1.19",

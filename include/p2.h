@@ -67,8 +67,8 @@ typedef struct {
                                    kernel performed, including its data-dependent QR steps */
     int32_t n_phases;           /* 7 when timing is on, else 0 */
     float phase_ms[8];          /* last iteration: H solve, pass beta (mode 2), V solve,
-                                   pass alpha (mode 3 + W + Gram), W statistics + fit,
-                                   Procrustes, mode-1 reduction */
+                                   pass alpha (mode 3 + W + Gram), Procrustes,
+                                   subject statistics (mode 1, W^TW), fit */
 } p2_stats_t;
 
 /* Fill *opt with defaults for rank R (precision FP32, device 0, graph on,

@@ -40,8 +40,8 @@ class p2_stats_t(ctypes.Structure):
                 ("phase_ms", ctypes.c_float * 8)]
 
 
-PHASES = ("h_solve", "beta_mode2", "v_solve", "alpha_mode3_w_gram", "w_stats_fit",
-          "procrustes", "mode1")
+PHASES = ("h_solve", "beta_mode2", "v_solve", "alpha_mode3_w_gram", "procrustes",
+          "subject_stats_mode1", "fit")
 
 
 class P2Error(RuntimeError):

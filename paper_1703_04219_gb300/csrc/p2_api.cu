@@ -70,7 +70,12 @@ static void free_data(p2_ctx *c) {
     dfree(c, &c->d_Vprev, J * R);
     dfree(c, &c->d_Vun, J * R);
     dfree(c, &c->d_M2, J * R);
-    dfree(c, &c->d_m2acc, J * R);
+    dfree(c, &c->d_P, N * R);
+    dfree(c, &c->X.csc_row, nnz);
+    dfree(c, &c->X.csc_val, nnz);
+    dfree(c, &c->X.seg_start, (size_t)c->X.nseg + 1);
+    dfree(c, &c->X.col_seg, J + 1);
+    dfree(c, &c->d_segpart, (size_t)c->X.nseg * R);
     dfree(c, &c->d_W, K * R);
     dfree(c, &c->d_M3, K * R);
     dfree(c, &c->d_T, K * R * R);
@@ -105,12 +110,11 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
     P2_TRY(dalloc(c, &c->d_Vprev, (size_t)J * R));
     P2_TRY(dalloc(c, &c->d_Vun, (size_t)J * R));
     P2_TRY(dalloc(c, &c->d_M2, (size_t)J * R));
-    P2_TRY(dalloc(c, &c->d_m2acc, (size_t)J * R));
+    P2_TRY(dalloc(c, &c->d_P, (size_t)N * R));
     P2_TRY(dalloc(c, &c->d_W, (size_t)K * R));
     P2_TRY(dalloc(c, &c->d_M3, (size_t)K * R));
     P2_TRY(dalloc(c, &c->d_T, (size_t)K * R * R));
     P2_TRY(dalloc(c, &c->d_G, (size_t)K * P));
-    P2_CUDA_TRY(cudaMemsetAsync(c->d_m2acc, 0, sizeof(unsigned long long) * (size_t)J * R, c->stream));
     P2_CUDA_TRY(cudaMemsetAsync(c->d_M3, 0, sizeof(float) * (size_t)K * R, c->stream));
     c->h_perm_new2old = new int32_t[J];
     c->h_perm_old2new = new int32_t[J];

@@ -38,36 +38,50 @@ struct VecView {
     P2_HD double &operator[](int i) const { return base[(size_t)i * stride]; }
 };
 
+P2_HD double p2_rsqrt(double x) {
+#ifdef __CUDA_ARCH__
+    return rsqrt(x);
+#else
+    return 1.0 / sqrt(x);
+#endif
+}
+
 // Reduce the symmetric matrix held in the lower triangle of A (n x n) to
 // tridiagonal form T = Q^T A Q, then overwrite A with Q (full storage).
-// On return d[0..n) is diag(T) and e[0..n-1) its sub-diagonal.
-// beta and t are work vectors of length n.
-P2_HD void tridiagonalize(int n, MatView A, VecView d, VecView e, VecView beta, VecView t) {
+// On return d[0..n) is diag(T) and e[0..n-1) its sub-diagonal.  Work space:
+// d doubles as the Householder work vector during the reduction, and the
+// Householder scalars beta_k are kept in the (unused) upper triangle at
+// A(k, k+1) until the backward accumulation consumes them.
+// N > 0 fixes n at compile time (n_rt is then ignored).
+template <int N>
+P2_HD void tridiagonalize(int n_rt, MatView A, VecView d, VecView e) {
+    const int n = N > 0 ? N : n_rt;
+    VecView t = d;
     for (int k = 0; k + 2 < n; ++k) {
         // Householder vector for x = A[k+1:n, k]
         double sigma = 0.0;
         for (int i = k + 2; i < n; ++i) sigma = fma(A(i, k), A(i, k), sigma);
         double x0 = A(k + 1, k);
         if (sigma == 0.0) {
-            beta[k] = 0.0;
+            A(k, k + 1) = 0.0;      // beta_k
             e[k] = x0;
             continue;
         }
         double mu = sqrt(x0 * x0 + sigma);
         double v0 = (x0 <= 0.0) ? (x0 - mu) : (-sigma / (x0 + mu));
-        double b = 2.0 * v0 * v0 / (sigma + v0 * v0);
+        double v02 = v0 * v0;
+        double b = 2.0 * v02 / (sigma + v02);
         double inv_v0 = 1.0 / v0;
         for (int i = k + 2; i < n; ++i) A(i, k) *= inv_v0;     // v = [1, A(k+2:n,k)]
-        beta[k] = b;
+        A(k, k + 1) = b;
         e[k] = mu;
         // p = b * A22 v  (A22 symmetric, lower triangle stored), K = b/2 p^T v
         double pv = 0.0;
         for (int i = k + 1; i < n; ++i) {
-            double s = 0.0;
-            for (int j = k + 1; j < n; ++j) {
-                double vj = (j == k + 1) ? 1.0 : A(j, k);
+            double s = A(i, k + 1);                           // v_{k+1} = 1
+            for (int j = k + 2; j < n; ++j) {
                 double aij = (j <= i) ? A(i, j) : A(j, i);
-                s = fma(aij, vj, s);
+                s = fma(aij, A(j, k), s);
             }
             s *= b;
             t[i] = s;
@@ -84,7 +98,7 @@ P2_HD void tridiagonalize(int n, MatView A, VecView d, VecView e, VecView beta, 
             double wi = t[i];
             for (int j = k + 1; j <= i; ++j) {
                 double vj = (j == k + 1) ? 1.0 : A(j, k);
-                A(i, j) = A(i, j) - vi * t[j] - wi * vj;
+                A(i, j) = fma(-vi, t[j], fma(-wi, vj, A(i, j)));
             }
         }
     }
@@ -92,22 +106,21 @@ P2_HD void tridiagonalize(int n, MatView A, VecView d, VecView e, VecView beta, 
     for (int i = 0; i < n; ++i) d[i] = A(i, i);
 
     // Backward accumulation Q = P_0 P_1 ... P_{n-3}, in place.
-    if (n >= 2) {
-        A(n - 1, n - 1) = 1.0;
-        A(n - 2, n - 2) = 1.0;
-        A(n - 1, n - 2) = 0.0;
-        A(n - 2, n - 1) = 0.0;
-    } else if (n == 1) {
+    if (n == 1) {
         A(0, 0) = 1.0;
         return;
     }
+    A(n - 1, n - 1) = 1.0;
+    A(n - 2, n - 2) = 1.0;
+    A(n - 1, n - 2) = 0.0;
+    A(n - 2, n - 1) = 0.0;
     for (int k = n - 3; k >= 0; --k) {
+        const double b = A(k, k + 1);
         A(k + 1, k + 1) = 1.0;
         for (int j = k + 2; j < n; ++j) {
             A(k + 1, j) = 0.0;
             A(j, k + 1) = 0.0;
         }
-        double b = beta[k];
         if (b == 0.0) continue;
         for (int c = k + 1; c < n; ++c) {
             double s = A(k + 1, c);
@@ -128,9 +141,13 @@ P2_HD void tridiagonalize(int n, MatView A, VecView d, VecView e, VecView beta, 
 // rotations are accumulated into the columns of Z (n x n).  Returns the
 // number of QR steps taken, or -1 if max_steps was exceeded (d then holds
 // the current, partly converged, diagonal).  *rotations (if given) is
-// incremented by the number of Givens rotations applied.
-P2_HD int tridiagonal_qr(int n, MatView Z, VecView d, VecView e, int max_steps,
+// incremented by the number of Givens rotations applied.  Each rotation is
+// formed from one reciprocal square root: c = x / r, s = -z / r, r = t / sqrt(t)
+// with t = x^2 + z^2.
+template <int N>
+P2_HD int tridiagonal_qr(int n_rt, MatView Z, VecView d, VecView e, int max_steps,
                          int *rotations = nullptr) {
+    const int n = N > 0 ? N : n_rt;
     const double eps = 2.220446049250313e-16;
     double anorm = 0.0;
     for (int i = 0; i < n; ++i) {
@@ -165,19 +182,21 @@ P2_HD int tridiagonal_qr(int n, MatView Z, VecView d, VecView e, int max_steps,
         double x = d[p] - mu;
         double z = e[p];
         for (int k = p; k < q; ++k) {
-            double r = sqrt(x * x + z * z);
-            double c = 1.0, s = 0.0;
-            if (r > 0.0) {
-                double ir = 1.0 / r;
+            const double tt = fma(x, x, z * z);
+            double c = 1.0, s = 0.0, r = 0.0;
+            if (tt > 0.0) {
+                const double ir = p2_rsqrt(tt);
                 c = x * ir;
                 s = -z * ir;
+                r = tt * ir;
             }
             if (k > p) e[k - 1] = r;
             double a = d[k], bb = d[k + 1], g = e[k];
             double cc = c * c, ss = s * s, cs = c * s;
-            d[k] = cc * a - 2.0 * cs * g + ss * bb;
-            d[k + 1] = ss * a + 2.0 * cs * g + cc * bb;
-            e[k] = cs * (a - bb) + (cc - ss) * g;
+            double cs2g = 2.0 * cs * g;
+            d[k] = fma(cc, a, fma(ss, bb, -cs2g));
+            d[k + 1] = fma(ss, a, fma(cc, bb, cs2g));
+            e[k] = fma(cs, a - bb, (cc - ss) * g);
             if (k + 1 < q) {
                 double en = e[k + 1];
                 z = -s * en;
@@ -186,8 +205,8 @@ P2_HD int tridiagonal_qr(int n, MatView Z, VecView d, VecView e, int max_steps,
             }
             for (int i = 0; i < n; ++i) {
                 double zk = Z(i, k), zk1 = Z(i, k + 1);
-                Z(i, k) = c * zk - s * zk1;
-                Z(i, k + 1) = s * zk + c * zk1;
+                Z(i, k) = fma(c, zk, -s * zk1);
+                Z(i, k + 1) = fma(s, zk, c * zk1);
             }
         }
     }

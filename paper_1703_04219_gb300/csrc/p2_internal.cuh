@@ -66,7 +66,15 @@ struct DevX {
     uint16_t *row_len = nullptr;   // [N]
     uint16_t *col = nullptr;       // [nnz] relabelled column ids
     float *val = nullptr;          // [nnz]
+    // column-major copy for the mode-2 reduction (built once at load)
+    uint32_t *csc_row = nullptr;   // [nnz] stacked row id of each non-zero, column-major
+    float *csc_val = nullptr;      // [nnz]
+    int64_t nseg = 0;              // column segments of at most P2_SEG non-zeros
+    int64_t *seg_start = nullptr;  // [nseg+1] offsets into csc_*
+    int64_t *col_seg = nullptr;    // [J+1] first segment of each (relabelled) column
 };
+
+#define P2_SEG 1024
 
 // Launch geometry decided once per context.
 struct Geometry {
@@ -105,8 +113,9 @@ struct p2_ctx {
     double *d_G = nullptr;      // K x P (packed lower Gram of Z_k)
     float *d_M3 = nullptr;      // K x R
     double *d_M2 = nullptr;     // J x R (relabelled rows)
+    float *d_P = nullptr;       // N x R rows of P_k = Z_k F_k (mode-2 pass)
+    double *d_segpart = nullptr; // nseg x R partial sums of the mode-2 reduction
     double *d_Vun = nullptr;    // J x R unnormalised V
-    unsigned long long *d_m2acc = nullptr;  // J x R fixed-point accumulators
     p2::SmallState *d_s = nullptr;
     double *d_part = nullptr;   // reduction partials (red_blocks x (R*R + 2R + 2))
     double *d_part2 = nullptr;  // second partial buffer
@@ -127,4 +136,8 @@ int enqueue_prologue(p2_ctx *c);     // Q-step + mode-1 MTTKRP for the current (
 int enqueue_iteration(p2_ctx *c);    // one ALS iteration
 int enqueue_factor_stats(p2_ctx *c); // HtH, VtV, WtW, wmax for freshly set factors
 int configure_kernels(p2_ctx *c);    // smem attributes etc.
+// Procrustes step (p2_polar.cu)
+int polar_configure(p2_ctx *c);
+cudaError_t launch_polar(p2_ctx *c);
+__host__ __device__ unsigned long long polar_fixed_flops(int R);
 }  // namespace p2

@@ -100,7 +100,10 @@ static __device__ __forceinline__ void gather_rows(const XView &X, int nr, int64
 }
 
 // ---------------------------------------------------------------------------
-// Pass alpha: for each subject, Gram of Z'_k = X_k V (FP64, packed lower)
+// Pass alpha: for each subject, Gram of Z'_k = X_k V (packed lower; every
+// product z_r z_s is split exactly into p + e with an FMA (Dekker's
+// TwoProduct) and summed into an unevaluated float pair with Knuth's TwoSum,
+// so the Gram carries ~2^-48 relative error without using the FP64 pipe)
 // and, with MODE3, the mode-3 MTTKRP row M3(k,:) = coldot(H, T_k Z_k^T Z'_k)
 // with Z_k = X_k Vprev, followed by W(k,:) = M3(k,:) (V^TV * H^TH)^+.
 // ---------------------------------------------------------------------------
@@ -124,8 +127,9 @@ __global__ void __launch_bounds__(512) k_alpha(XView X, const float *__restrict_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const size_t warp_bytes = (size_t)P * 8 + ((size_t)64 * R + 2 * (size_t)R * R) * 4;
     unsigned char *wb = smem_raw + cta_bytes + warp * warp_bytes;
-    double *Gacc = reinterpret_cast<double *>(wb);
-    float *zo = reinterpret_cast<float *>(Gacc + P);   // 32 R  (zo and zn contiguous: 64 R scratch)
+    float *Ghi = reinterpret_cast<float *>(wb);
+    float *Glo = Ghi + P;
+    float *zo = Glo + P;                                // 32 R  (zo and zn contiguous: 64 R scratch)
     float *zn = zo + 32 * R;                            // 32 R
     float *Tk = zn + 32 * R;                            // R R
     float *Cacc = Tk + R * R;                           // R R
@@ -147,7 +151,10 @@ __global__ void __launch_bounds__(512) k_alpha(XView X, const float *__restrict_
     for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; k < X.K; k += nwarps) {
         const int64_t r0 = X.subj_row[k], r1 = X.subj_row[k + 1];
         int64_t base = X.subj_nnz[k];
-        for (int p = lane; p < P; p += 32) Gacc[p] = 0.0;
+        for (int p = lane; p < P; p += 32) {
+            Ghi[p] = 0.f;
+            Glo[p] = 0.f;
+        }
         if (MODE3)
             for (int e = lane; e < R * R; e += 32) Cacc[e] = 0.f;
         for (int64_t cr = r0; cr < r1; cr += 32) {
@@ -171,16 +178,25 @@ __global__ void __launch_bounds__(512) k_alpha(XView X, const float *__restrict_
             }
             for (int p = lane; p < P; p += 32) {
                 const int r = pr[p], s = pc[p];
-                double acc = 0.0;
-                for (int i = 0; i < nr; ++i)
-                    acc = fma((double)zn[i * R + r], (double)zn[i * R + s], acc);
-                Gacc[p] += acc;
+                float sh = Ghi[p], sl = Glo[p];
+                for (int i = 0; i < nr; ++i) {
+                    const float a = zn[i * R + r], b = zn[i * R + s];
+                    const float pa = a * b;
+                    const float pe = fmaf(a, b, -pa);           // a*b = pa + pe exactly
+                    const float t = sh + pa;                    // TwoSum(sh, pa)
+                    const float bv = t - sh;
+                    const float er = (sh - (t - bv)) + (pa - bv);
+                    sh = t;
+                    sl += er + pe;
+                }
+                Ghi[p] = sh;
+                Glo[p] = sl;
             }
             __syncwarp();
             base += tot;
         }
         double *Gk = G + (size_t)k * P;
-        for (int p = lane; p < P; p += 32) Gk[p] = Gacc[p];
+        for (int p = lane; p < P; p += 32) Gk[p] = (double)Ghi[p] + (double)Glo[p];
         if (MODE3) {
             const float *Tg = T + (size_t)k * R * R;
             for (int e = lane; e < R * R; e += 32) Tk[e] = Tg[e];
@@ -211,39 +227,28 @@ __global__ void __launch_bounds__(512) k_alpha(XView X, const float *__restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Pass beta: mode-2 MTTKRP M2 = sum_k X_k^T (Z_k F_k), F_k = T_k^T H S_k.
-// Terms are rounded to 64-bit fixed point with a per-component power-of-two
-// scale and added with integer atomics (order independent).  Columns below
-// Hc (the most frequent after relabelling) accumulate in shared memory first.
+// Pass beta, part 1: rows of P_k = Z_k F_k with F_k = T_k^T H S_k, so that
+// mode 2 (Eq. mttkrp2_3) is M2 = sum_k Y_k^T H S_k = sum_k X_k^T P_k.
+// One warp per subject; the rows go to P (N x R) in stacked-row order.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_beta(XView X, const float *__restrict__ V,
-                                              const float *__restrict__ H,
-                                              const float *__restrict__ T,
-                                              const float *__restrict__ W,
-                                              SmallState *st, unsigned long long *m2acc,
-                                              int R, int Hc) {
+static __host__ __device__ size_t beta_warp_bytes(int R) { return ((size_t)64 * R + 2 * (size_t)R * R + R) * 4; }
+
+__global__ void __launch_bounds__(512) k_beta_p(XView X, const float *__restrict__ V,
+                                                const float *__restrict__ H,
+                                                const float *__restrict__ T,
+                                                const float *__restrict__ W, float *Pout, int R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int LPR = R < 32 ? R : 32;
     const int RPP = 32 / LPR;
-    unsigned long long *hot = reinterpret_cast<unsigned long long *>(smem_raw);
-    float *Hs = reinterpret_cast<float *>(hot + (size_t)Hc * R);
-    float *scale = Hs + R * R;
-    size_t cta_bytes = ((size_t)Hc * R * 8 + (size_t)R * R * 4 + (size_t)R * 4 + 15) & ~(size_t)15;
+    float *Hs = reinterpret_cast<float *>(smem_raw);
+    const size_t cta_bytes = ((size_t)R * R * 4 + 15) & ~(size_t)15;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t warp_bytes = ((size_t)64 * R + 2 * (size_t)R * R + R) * 4;
-    float *zo = reinterpret_cast<float *>(smem_raw + cta_bytes + warp * warp_bytes);
-    float *pp = zo + 32 * R;
-    float *Tk = pp + 32 * R;
+    float *zo = reinterpret_cast<float *>(smem_raw + cta_bytes + warp * beta_warp_bytes(R));
+    float *Tk = zo + 64 * R;
     float *Fk = Tk + R * R;
     float *wk = Fk + R * R;
-
-    for (int i = threadIdx.x; i < Hc * R; i += blockDim.x) hot[i] = 0ull;
     for (int i = threadIdx.x; i < R * R; i += blockDim.x) Hs[i] = H[i];
-    for (int i = threadIdx.x; i < R; i += blockDim.x) scale[i] = st->m2scale[i];
     __syncthreads();
-    const float lim = 4.0e18f;   // < 2^62
-    bool ovf = false;
-
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; k < X.K; k += nwarps) {
         const int64_t r0 = X.subj_row[k], r1 = X.subj_row[k + 1];
@@ -267,266 +272,195 @@ __global__ void __launch_bounds__(512) k_beta(XView X, const float *__restrict__
             const int tot = __shfl_sync(FULLMASK, off + len, 31);
             gather_rows<false>(X, nr, base, len, off, V, nullptr, zo, nullptr, R, LPR, RPP, lane);
             __syncwarp();
+            float *Pr = Pout + (size_t)cr * R;
             for (int e = lane; e < nr * R; e += 32) {
                 const int i = e / R, s = e - i * R;
                 float p = 0.f;
                 for (int u = 0; u < R; ++u) p = fmaf(zo[i * R + u], Fk[u * R + s], p);
-                pp[e] = p;
-            }
-            __syncwarp();
-            const int g = lane / LPR, sub = lane - g * LPR;
-            for (int i0 = 0; i0 < nr; i0 += RPP) {
-                const int i = i0 + g;
-                const int src = (i < 32) ? i : 31;
-                const int ro = __shfl_sync(FULLMASK, off, src);
-                const int rl = __shfl_sync(FULLMASK, len, src);
-                if ((g < RPP) && (i < nr)) {
-                    for (int e = 0; e < rl; ++e) {
-                        const int64_t idx = base + ro + e;
-                        const int j = X.col[idx];
-                        const float x = X.val[idx];
-#pragma unroll
-                        for (int t = 0; t < 2; ++t) {
-                            const int c = sub + t * LPR;
-                            if (c < R) {
-                                float v = x * pp[i * R + c] * scale[c];
-                                if (!(fabsf(v) < lim)) {
-                                    ovf = true;
-                                    v = (v != v) ? 0.f : copysignf(lim, v);
-                                }
-                                const long long q = __float2ll_rn(v);
-                                if (q != 0) {
-                                    if (j < Hc)
-                                        atomicAdd(&hot[(size_t)j * R + c], (unsigned long long)q);
-                                    else
-                                        atomicAdd(&m2acc[(size_t)j * R + c], (unsigned long long)q);
-                                }
-                            }
-                        }
-                    }
-                }
+                Pr[e] = p;
             }
             __syncwarp();
             base += tot;
         }
     }
-    if (ovf) atomicOr(&st->flags, FLAG_FIXED_OVF);
-    __syncthreads();
-    for (int i = threadIdx.x; i < Hc * R; i += blockDim.x)
-        if (hot[i] != 0ull) atomicAdd(&m2acc[i], hot[i]);
 }
 
-// M2 = fixed-point sums scaled back to FP64; accumulators reset for next use.
-__global__ void k_m2_finalize(unsigned long long *m2acc, double *M2, const SmallState *st,
-                              int64_t n, int R) {
+// ---------------------------------------------------------------------------
+// Pass beta, part 2: M2(j, :) = sum over the non-zeros x of column j of
+// x * P(row, :), read column-major.  One warp per column segment (at most
+// P2_SEG non-zeros); lanes accumulate with Kahan-compensated FP32; the lane
+// groups are combined in FP64 in a fixed order.  No atomics: deterministic.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_m2_segments(const uint32_t *__restrict__ csc_row,
+                                                     const float *__restrict__ csc_val,
+                                                     const int64_t *__restrict__ seg_start,
+                                                     int64_t nseg, const float *__restrict__ Pin,
+                                                     double *segpart, int R) {
+    __shared__ double red[8][64];
+    const int LPR = R < 32 ? R : 32;
+    const int RPP = 32 / LPR;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane / LPR, sub = lane - g * LPR;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t sg = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; sg < nseg; sg += nwarps) {
+        const int64_t a = seg_start[sg], b = seg_start[sg + 1];
+        float hi[2] = {0.f, 0.f}, cp[2] = {0.f, 0.f};
+        if (g < RPP) {
+            for (int64_t e = a + g; e < b; e += RPP) {
+                const uint32_t row = csc_row[e];
+                const float x = csc_val[e];
+                const float *pr = Pin + (size_t)row * R;
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const int c = sub + t * LPR;
+                    if (c < R) {
+                        const float y = x * __ldg(pr + c) - cp[t];
+                        const float tt = hi[t] + y;
+                        cp[t] = (tt - hi[t]) - y;
+                        hi[t] = tt;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int c = sub + t * LPR;
+            if (g < RPP && c < R) red[warp][lane + 32 * t] = (double)hi[t] - (double)cp[t];
+        }
+        __syncwarp();
+        for (int c = lane; c < R; c += 32) {
+            const int cs = c % LPR, ct = c / LPR;
+            double acc = 0.0;
+            for (int gg = 0; gg < RPP; ++gg) acc += red[warp][gg * LPR + cs + 32 * ct];
+            segpart[(size_t)sg * R + c] = acc;
+        }
+        __syncwarp();
+    }
+}
+
+// M2(j, :) = sum of column j's segment partials, in segment order (FP64).
+__global__ void k_m2_columns(const double *__restrict__ segpart, const int64_t *__restrict__ col_seg,
+                             double *M2, int32_t J, int R) {
+    const int64_t n = (int64_t)J * R;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int s = (int)(e % R);
-        const long long q = (long long)m2acc[e];
-        M2[e] = (double)q * st->m2inv[s];
-        m2acc[e] = 0ull;
+        const int64_t j = e / R;
+        const int c = (int)(e - j * R);
+        double acc = 0.0;
+        for (int64_t sg = col_seg[j]; sg < col_seg[j + 1]; ++sg) acc += segpart[(size_t)sg * R + c];
+        M2[e] = acc;
     }
 }
 
 // ---------------------------------------------------------------------------
-// Procrustes step, one GPU lane per subject, FP64.
-// M = H S G S H^T (= A_k^T A_k), M = Z diag(d) Z^T, f_i = d_i^{-1/2} for
-// d_i > rtol2 * max(d) else 0, T_k = Z diag(f) Z^T H S  (stored FP32).
-// Per-thread matrices live in interleaved shared memory.
+// Per-subject statistics after the Q-step, in one pass over the subjects:
+//   mode 1 (Eq. mttkrp1_3): M1 = sum_k (T_k G_k) * 1 W(k,:)   (Y_k V = T_k G_k),
+//   W^TW, max_k |W(k, s)| and <W, M3>.
+// One block per fixed contiguous subject range and one warp per subject at a
+// time (no block barriers in the loop).  M1 products in FP32, accumulation in
+// FP64 (W^TW products of FP32 values are exact in FP64).  Block partials,
+// layout [R*R M1][R*R WtW][R wmax][1 wm3], summed later in block order.
 // ---------------------------------------------------------------------------
-// FP64 flops of the Procrustes kernel for one subject (fused multiply-add =
-// 2; sqrt and division = 1), counted from the operations it performs: the
-// fixed part below plus 11 per QR step and 29 + 6R per Givens rotation.
-static __host__ __device__ unsigned long long polar_fixed_flops(int R) {
-    unsigned long long f = 0;
-    const unsigned long long r = (unsigned long long)R, P = r * (r + 1) / 2;
-    f += 2 * P;                                     // S G S
-    f += 2 * r * r * r + r * r * (r + 1);           // M = H (S G S) H^T, lower triangle
-    for (unsigned long long m = 2; m + 1 <= r; ++m) {
-        f += 4 * m * m + 10 * m + 10;               // Householder step on an m-vector
-        f += m * (4 * m - 2);                       // backward accumulation of that step
-    }
-    f += 3 * r;                                     // QR scale estimate
-    f += 3 * r + 1;                                 // eigenvalue cut and d^-1/2
-    f += 4 * r * r * r + 2 * r * r;                 // T = Z diag(f) Z^T H S
-    return f;
+static __host__ __device__ size_t stats_warp_bytes(int R) {   // multiple of 16: FP64 first
+    return ((size_t)R * R * 16 + ((size_t)2 * R * R + R) * 4 + 15) & ~(size_t)15;
 }
 
-__global__ void __launch_bounds__(128) k_polar(const double *__restrict__ G,
-                                               const float *__restrict__ W,
-                                               SmallState *st, float *T,
-                                               int64_t K, int R, double rtol2) {
-    extern __shared__ __align__(16) double sm[];
-    const int NT = blockDim.x;
-    const int t = threadIdx.x;
-    const int P = R * (R + 1) / 2;
-    double *Hs = sm;                       // R*R, H64
-    double *th = sm + R * R;
-    for (int i = t; i < R * R; i += NT) Hs[i] = st->H64[i];
-    __syncthreads();
-    const int64_t k = (int64_t)blockIdx.x * NT + t;
-    unsigned long long flops = 0;
-    if (k < K) {
-        MatView A{th + t, NT, R};
-        double *gp = th + (size_t)R * R * NT + t;          // packed scaled Gram, stride NT
-        VecView d{gp + (size_t)P * NT, NT};
-        VecView e{gp + (size_t)(P + R) * NT, NT};
-        VecView bt{gp + (size_t)(P + 2 * R) * NT, NT};
-        VecView tv{gp + (size_t)(P + 3 * R) * NT, NT};
-        VecView w{gp + (size_t)(P + 4 * R) * NT, NT};
-
-        const float *Wk = W + (size_t)k * R;
-        for (int i = 0; i < R; ++i) w[i] = (double)Wk[i];
-        const double *Gk = G + (size_t)k * P;
-        for (int i = 0, p = 0; i < R; ++i)
-            for (int j = 0; j <= i; ++j, ++p) gp[(size_t)p * NT] = Gk[p] * w[i] * w[j];
-        // M = H Gs H^T, lower triangle, column by column
-        for (int c = 0; c < R; ++c) {
-            for (int i = 0; i < R; ++i) {
-                double s = 0.0;
-                for (int j = 0; j < R; ++j) {
-                    const int p = (j <= i) ? (i * (i + 1) / 2 + j) : (j * (j + 1) / 2 + i);
-                    s = fma(gp[(size_t)p * NT], Hs[c * R + j], s);
-                }
-                tv[i] = s;
-            }
-            for (int r = c; r < R; ++r) {
-                double s = 0.0;
-                for (int i = 0; i < R; ++i) s = fma(Hs[r * R + i], tv[i], s);
-                A(r, c) = s;
-            }
-        }
-        tridiagonalize(R, A, d, e, bt, tv);
-        int rot = 0;
-        const int steps = tridiagonal_qr(R, A, d, e, 30 * R, &rot);
-        if (steps < 0) atomicOr(&st->flags, FLAG_EIG_NOCONV);
-        double lmax = 0.0;
-        for (int i = 0; i < R; ++i) lmax = fmax(lmax, d[i]);
-        const double cut = rtol2 * lmax;
-        for (int i = 0; i < R; ++i) d[i] = (lmax > 0.0 && d[i] > cut) ? 1.0 / sqrt(d[i]) : 0.0;
-        float *Tk = T + (size_t)k * R * R;
-        for (int c = 0; c < R; ++c) {
-            const double wc = w[c];
-            for (int i = 0; i < R; ++i) {
-                double s = 0.0;
-                for (int u = 0; u < R; ++u) s = fma(A(u, i), Hs[u * R + c], s);
-                tv[i] = s * d[i] * wc;
-            }
-            for (int r = 0; r < R; ++r) {
-                double s = 0.0;
-                for (int i = 0; i < R; ++i) s = fma(A(r, i), tv[i], s);
-                Tk[r * R + c] = (float)s;
-            }
-        }
-        flops = polar_fixed_flops(R) + 11ull * (unsigned long long)(steps > 0 ? steps : 0) +
-                (29ull + 6ull * R) * (unsigned long long)rot;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) flops += __shfl_down_sync(FULLMASK, flops, o);
-    if ((t & 31) == 0 && flops) atomicAdd(&st->polar_flops, flops);
-}
-
-// ---------------------------------------------------------------------------
-// Mode 1: partials of M1 = sum_k (T_k G_k) * 1 W(k,:), one block per fixed
-// contiguous subject range; FP32 products, FP64 accumulation.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_mode1(const float *__restrict__ T,
-                                               const double *__restrict__ G,
-                                               const float *__restrict__ W, double *part,
-                                               int64_t K, int R) {
+__global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__ T,
+                                                       const double *__restrict__ G,
+                                                       const float *__restrict__ W,
+                                                       const float *__restrict__ M3, double *part,
+                                                       int64_t K, int R, int with_m3) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red_wm3[8];
+    __shared__ float red_wmax[8][P2_RMAX];
     const int P = R * (R + 1) / 2;
-    float *Ts = reinterpret_cast<float *>(smem_raw);
-    float *Gs = Ts + R * R;   // full R x R in FP32
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *pr = smem_raw;
+    uint8_t *pc = pr + P;
+    const size_t cta_bytes = (2 * (size_t)P + 15) & ~(size_t)15;
+    const size_t wbytes = stats_warp_bytes(R);
+    unsigned char *wb = smem_raw + cta_bytes + warp * wbytes;
+    double *aM1 = reinterpret_cast<double *>(wb);
+    double *aW = aM1 + R * R;
+    float *Ts = reinterpret_cast<float *>(aW + R * R);
+    float *Gs = Ts + R * R;
     float *ws = Gs + R * R;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        int r = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+        while ((r + 1) * (r + 2) / 2 <= p) ++r;
+        while (r * (r + 1) / 2 > p) --r;
+        pr[p] = (uint8_t)r;
+        pc[p] = (uint8_t)(p - r * (r + 1) / 2);
+    }
+    for (int e = lane; e < R * R; e += 32) {
+        aM1[e] = 0.0;
+        aW[e] = 0.0;
+    }
+    __syncthreads();
     const int64_t per = (K + gridDim.x - 1) / gridDim.x;
     const int64_t k0 = (int64_t)blockIdx.x * per;
     const int64_t k1 = (k0 + per < K) ? (k0 + per) : K;
-    double acc[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
-    for (int64_t k = k0; k < k1; ++k) {
+    double wm3 = 0.0;
+    float wmx[2] = {0.f, 0.f};
+    for (int64_t k = k0 + warp; k < k1; k += nw) {
         const float *Tg = T + (size_t)k * R * R;
         const double *Gg = G + (size_t)k * P;
-        for (int e = threadIdx.x; e < R * R; e += blockDim.x) Ts[e] = Tg[e];
-        for (int p = threadIdx.x; p < P; p += blockDim.x) {
-            int r = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
-            while ((r + 1) * (r + 2) / 2 <= p) ++r;
-            while (r * (r + 1) / 2 > p) --r;
-            const int s = p - r * (r + 1) / 2;
+        for (int e = lane; e < R * R; e += 32) Ts[e] = Tg[e];
+        for (int p = lane; p < P; p += 32) {
             const float g = (float)Gg[p];
-            Gs[r * R + s] = g;
-            Gs[s * R + r] = g;
+            const int r = pr[p], c = pc[p];
+            Gs[r * R + c] = g;
+            Gs[c * R + r] = g;
         }
-        for (int s = threadIdx.x; s < R; s += blockDim.x) ws[s] = W[(size_t)k * R + s];
-        __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int e = threadIdx.x + q * blockDim.x;
-            if (e < R * R) {
-                const int r = e / R, c = e - r * R;
-                float s = 0.f;
-                for (int u = 0; u < R; ++u) s = fmaf(Ts[r * R + u], Gs[u * R + c], s);
-                acc[q] += (double)(s * ws[c]);
+        for (int t = 0; t < 2; ++t) {
+            const int s = lane + 32 * t;
+            if (s < R) {
+                const float v = W[(size_t)k * R + s];
+                ws[s] = v;
+                wmx[t] = fmaxf(wmx[t], fabsf(v));
+                if (with_m3) wm3 = fma((double)v, (double)M3[(size_t)k * R + s], wm3);
             }
         }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        const int e = threadIdx.x + q * blockDim.x;
-        if (e < R * R) part[(size_t)blockIdx.x * R * R + e] = acc[q];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Partials of W^TW, <W, M3> and max |W(:, s)| over fixed subject ranges.
-// part layout per block: [R*R WtW][R wmax][1 wm3]
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gram_w(const float *__restrict__ W,
-                                                const float *__restrict__ M3, double *part,
-                                                int64_t K, int R, int with_m3) {
-    const int64_t per = (K + gridDim.x - 1) / gridDim.x;
-    const int64_t k0 = (int64_t)blockIdx.x * per;
-    const int64_t k1 = (k0 + per < K) ? (k0 + per) : K;
-    const size_t stride = (size_t)R * R + R + 1;
-    double *out = part + (size_t)blockIdx.x * stride;
-    double acc[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
-    double wm3 = 0.0;
-    float wmx = 0.f;
-    for (int64_t k = k0; k < k1; ++k) {
-        const float *wk = W + (size_t)k * R;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int e = threadIdx.x + q * blockDim.x;
-            if (e < R * R) {
-                const int r = e / R, s = e - r * R;
-                acc[q] = fma((double)wk[r], (double)wk[s], acc[q]);
-            }
+        __syncwarp();
+        for (int e = lane; e < R * R; e += 32) {
+            const int r = e / R, c = e - r * R;
+            float sacc = 0.f;
+            for (int u = 0; u < R; ++u) sacc = fmaf(Ts[r * R + u], Gs[u * R + c], sacc);
+            aM1[e] += (double)(sacc * ws[c]);
+            aW[e] = fma((double)ws[r], (double)ws[c], aW[e]);
         }
-        if (threadIdx.x < R) {
-            const float v = wk[threadIdx.x];
-            wmx = fmaxf(wmx, fabsf(v));
-            if (with_m3) wm3 = fma((double)v, (double)M3[(size_t)k * R + threadIdx.x], wm3);
-        }
+        __syncwarp();
     }
+    // fixed-order reductions: lanes, then warps in index order
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        const int e = threadIdx.x + q * blockDim.x;
-        if (e < R * R) out[e] = acc[q];
-    }
-    __shared__ double sw[P2_RMAX];
-    if (threadIdx.x < R) {
-        out[R * R + threadIdx.x] = (double)wmx;
-        sw[threadIdx.x] = wm3;
-    }
+    for (int o = 16; o > 0; o >>= 1) wm3 += __shfl_down_sync(FULLMASK, wm3, o);
+    if (lane == 0) red_wm3[warp] = wm3;
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+        if (lane + 32 * t < P2_RMAX) red_wmax[warp][lane + 32 * t] = wmx[t];
     __syncthreads();
+    const size_t stride = 2 * (size_t)R * R + R + 1;
+    double *out = part + (size_t)blockIdx.x * stride;
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+        double m = 0.0, w2 = 0.0;
+        for (int q = 0; q < nw; ++q) {
+            const double *aq = reinterpret_cast<const double *>(smem_raw + cta_bytes + q * wbytes);
+            m += aq[e];
+            w2 += aq[R * R + e];
+        }
+        out[e] = m;
+        out[R * R + e] = w2;
+    }
+    for (int s = threadIdx.x; s < R; s += blockDim.x) {
+        float m = 0.f;
+        for (int q = 0; q < nw; ++q) m = fmaxf(m, red_wmax[q][s]);
+        out[2 * R * R + s] = (double)m;
+    }
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < R; ++i) s += sw[i];
-        out[R * R + R] = s;
+        double t = 0.0;
+        for (int q = 0; q < nw; ++q) t += red_wm3[q];
+        out[2 * R * R + R] = t;
     }
 }
 
@@ -671,7 +605,7 @@ __global__ void __launch_bounds__(256) k_solve_h(const double *__restrict__ part
     __shared__ double nrm[P2_RMAX];
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
         double s = 0.0;
-        for (int b = 0; b < nparts; ++b) s += part[(size_t)b * R * R + e];
+        for (int b = 0; b < nparts; ++b) s += part[(size_t)b * (2 * (size_t)R * R + R + 1) + e];
         st->M1[e] = s;
         A[e] = st->WtW[e] * st->VtV[e];
     }
@@ -796,35 +730,24 @@ __global__ void __launch_bounds__(256) k_fin_v(const double *__restrict__ part, 
     if (with_g3) cta_pinv(A, U, st->G3inv, R, &st->flags);
 }
 
-// Sum the W partials; loss / fit; fixed-point scales for the next mode-2 pass.
+// Sum the subject-statistics partials: W^TW, max |W|, <W, M3>; loss / fit.
+// (M1 stays in the partials; the H solve sums it.)
 __global__ void k_fin_w(const double *__restrict__ part, int nparts, SmallState *st, int R,
                         int with_fit) {
-    const size_t stride = (size_t)R * R + R + 1;
+    const size_t stride = 2 * (size_t)R * R + R + 1;
     __shared__ double red[256];
     double lsum = 0.0;
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
         double s = 0.0;
-        for (int b = 0; b < nparts; ++b) s += part[(size_t)b * stride + e];
+        for (int b = 0; b < nparts; ++b) s += part[(size_t)b * stride + R * R + e];
         st->WtW[e] = s;
         lsum += s * st->HtH[e] * st->VtV[e];
     }
     red[threadIdx.x] = lsum;
     for (int s = threadIdx.x; s < R; s += blockDim.x) {
         double mx = 0.0;
-        for (int b = 0; b < nparts; ++b) mx = fmax(mx, part[(size_t)b * stride + R * R + s]);
+        for (int b = 0; b < nparts; ++b) mx = fmax(mx, part[(size_t)b * stride + 2 * R * R + s]);
         st->wmax[s] = mx;
-        // |term| <= xbound * wmax: choose 2^E with xbound * wmax * 2^E < 2^61
-        const double bound = st->xbound * mx;
-        int E = 0;
-        if (bound > 0.0) {
-            int ex;
-            frexp(bound, &ex);          // bound < 2^ex
-            E = 61 - ex;
-            if (E > 120) E = 120;
-            if (E < -120) E = -120;
-        }
-        st->m2scale[s] = ldexpf(1.0f, E);
-        st->m2inv[s] = ldexp(1.0, -E);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -832,7 +755,7 @@ __global__ void k_fin_w(const double *__restrict__ part, int nparts, SmallState 
         for (int i = 0; i < (int)blockDim.x; ++i) t += red[i];
         if (with_fit) {
             double wm3 = 0.0;
-            for (int b = 0; b < nparts; ++b) wm3 += part[(size_t)b * stride + R * R + R];
+            for (int b = 0; b < nparts; ++b) wm3 += part[(size_t)b * stride + 2 * R * R + R];
             st->wm3 = wm3;
             const double loss = st->normx2 - 2.0 * wm3 + t;
             st->loss = loss;
@@ -854,12 +777,20 @@ static size_t alpha_warp_bytes(int R) {
     const int P = R * (R + 1) / 2;
     return (size_t)P * 8 + ((size_t)64 * R + 2 * (size_t)R * R) * 4;
 }
-static size_t beta_warp_bytes(int R) { return ((size_t)64 * R + 2 * (size_t)R * R + R) * 4; }
 
 struct Launch {
-    int alpha_warps, beta_warps, beta_hc, polar_nt;
-    size_t alpha_smem, beta_smem, polar_smem;
+    int alpha_warps, beta_warps, alpha_blocks, beta_blocks;
+    size_t alpha_smem, beta_smem;
 };
+
+// CTAs of this shape that fit on one SM (shared memory and 2048 threads).
+static int blocks_per_sm(const p2_ctx *c, size_t smem, int threads) {
+    const size_t usable = 233472;   // per-SM shared memory (228 KB) on this GPU
+    int b = smem > 0 ? (int)(usable / (smem + 1024)) : 32;
+    if (b > 2048 / threads) b = 2048 / threads;
+    if (b > (int)((size_t)c->geo.smem_optin / (smem > 0 ? smem : 1))) b = (int)((size_t)c->geo.smem_optin / (smem > 0 ? smem : 1));
+    return b < 1 ? 1 : b;
+}
 
 static Launch plan(const p2_ctx *c) {
     Launch L{};
@@ -869,24 +800,13 @@ static Launch plan(const p2_ctx *c) {
     while (aw > 1 && alpha_cta_bytes(R) + aw * alpha_warp_bytes(R) > cap) --aw;
     L.alpha_warps = aw;
     L.alpha_smem = alpha_cta_bytes(R) + aw * alpha_warp_bytes(R);
-    int bw = R <= 16 ? 8 : 4;
+    int bw = 16;
+    const size_t bcta = ((size_t)R * R * 4 + 15) & ~(size_t)15;
+    while (bw > 1 && bcta + bw * beta_warp_bytes(R) > cap) --bw;
     L.beta_warps = bw;
-    size_t fixed = (size_t)R * R * 4 + (size_t)R * 4 + 16 + bw * beta_warp_bytes(R);
-    int hc = (int)((cap - fixed) / (8 * (size_t)R));
-    if (hc > c->X.J) hc = c->X.J;
-    if (hc < 0) hc = 0;
-    L.beta_hc = hc;
-    L.beta_smem = (((size_t)hc * R * 8 + (size_t)R * R * 4 + (size_t)R * 4 + 15) & ~(size_t)15) +
-                  bw * beta_warp_bytes(R);
-    const int P = R * (R + 1) / 2;
-    const size_t per_thread = ((size_t)R * R + P + 5 * (size_t)R) * 8;
-    const size_t avail = cap - (size_t)R * R * 8;
-    int nt = (int)(avail / per_thread);
-    if (nt > 128) nt = 128;
-    if (nt >= 32) nt = (nt / 32) * 32;
-    if (nt < 1) nt = 1;
-    L.polar_nt = nt;
-    L.polar_smem = (size_t)R * R * 8 + (size_t)nt * per_thread;
+    L.beta_smem = bcta + bw * beta_warp_bytes(R);
+    L.alpha_blocks = blocks_per_sm(c, L.alpha_smem, L.alpha_warps * 32);
+    L.beta_blocks = blocks_per_sm(c, L.beta_smem, L.beta_warps * 32);
     return L;
 }
 
@@ -909,11 +829,12 @@ int configure_kernels(p2_ctx *c) {
     int rc = P2_OK;
     if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<true>, cap, "k_alpha<true>");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<false>, cap, "k_alpha<false>");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta, cap, "k_beta");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_polar, cap, "k_polar");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p, cap, "k_beta_p");
+    if (rc == P2_OK) rc = polar_configure(c);
     if (rc == P2_OK) rc = allow_dynamic_smem(k_solve_h, cap, "k_solve_h");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_solve_v_pinv, cap, "k_solve_v_pinv");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_fin_v, cap, "k_fin_v");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_subject_stats, cap, "k_subject_stats");
     return rc;
 }
 
@@ -936,25 +857,44 @@ static int check_launch(const char *what) {
 // Phase boundary event; recorded as an event-record node when the stream is
 // being captured into the iteration graph.
 static void mark(p2_ctx *c, int i) {
-    if (c->opt.timing) cudaEventRecordWithFlags(c->ev[i], c->stream, cudaEventRecordExternal);
+    if (!c->opt.timing) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->stream, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(c->ev[i], c->stream, cudaEventRecordExternal);
+    else
+        cudaEventRecord(c->ev[i], c->stream);
 }
 
-static int enqueue_qstep(p2_ctx *c, const Launch &L) {
+// Q-step for the current (H, V, W) (Algorithm 2's SVD loop), then the
+// per-subject statistics that need it: mode-1 MTTKRP partials, W^TW,
+// max |W|, <W, M3>, and (with_fit) the loss of the completed iteration.
+static int enqueue_qstep(p2_ctx *c, int with_fit) {
     const int R = c->R;
     cudaStream_t s = c->stream;
     const int nb = c->geo.red_blocks;
-    double rtol2 = c->opt.rank_rtol * c->opt.rank_rtol;
     const int64_t K = c->X.K;
-    if (K > 0) {
-        const int nblk = (int)((K + L.polar_nt - 1) / L.polar_nt);
-        k_polar<<<nblk, L.polar_nt, L.polar_smem, s>>>(c->d_G, c->d_W, c->d_s, c->d_T, K, R,
-                                                       rtol2);
-        P2_LAUNCH_CHECK("k_polar");
+    mark(c, 4);
+    {
+        cudaError_t e = launch_polar(c);
+        if (e != cudaSuccess) {
+            set_error("launch of the Procrustes kernel failed: %s", cudaGetErrorString(e));
+            return P2_ECUDA;
+        }
+        c->enqueued += 1;
     }
+    mark(c, 5);
+    const int P = R * (R + 1) / 2;
+    const size_t cta = (2 * (size_t)P + 15) & ~(size_t)15;
+    int nw = 8;
+    while (nw > 1 && cta + nw * stats_warp_bytes(R) > (size_t)c->geo.smem_optin) --nw;
+    k_subject_stats<<<nb, nw * 32, cta + nw * stats_warp_bytes(R), s>>>(c->d_T, c->d_G, c->d_W,
+                                                                      c->d_M3, c->d_part, K, R,
+                                                                      with_fit);
+    P2_LAUNCH_CHECK("k_subject_stats");
     mark(c, 6);
-    const size_t m1_smem = ((size_t)2 * R * R + R) * 4;
-    k_mode1<<<nb, 256, m1_smem, s>>>(c->d_T, c->d_G, c->d_W, c->d_part, K, R);
-    P2_LAUNCH_CHECK("k_mode1");
+    k_fin_w<<<1, 256, 0, s>>>(c->d_part, nb, c->d_s, R, with_fit);
+    P2_LAUNCH_CHECK("k_fin_w");
     return P2_OK;
 }
 
@@ -968,10 +908,6 @@ int enqueue_factor_stats(p2_ctx *c) {
     P2_LAUNCH_CHECK("k_gram_v");
     k_fin_v<<<1, 256, (size_t)2 * R * R * 8, s>>>(c->d_part2, nb, c->d_s, R, 0);
     P2_LAUNCH_CHECK("k_fin_v");
-    k_gram_w<<<nb, 256, 0, s>>>(c->d_W, c->d_M3, c->d_part2, c->X.K, R, 0);
-    P2_LAUNCH_CHECK("k_gram_w");
-    k_fin_w<<<1, 256, 0, s>>>(c->d_part2, nb, c->d_s, R, 0);
-    P2_LAUNCH_CHECK("k_fin_w");
     return P2_OK;
 }
 
@@ -981,10 +917,10 @@ int enqueue_prologue(p2_ctx *c) {
     cudaStream_t s = c->stream;
     const int nsm = c->geo.nsm;
     XView X = xview(c);
-    k_alpha<false><<<nsm, L.alpha_warps * 32, L.alpha_smem, s>>>(
+    k_alpha<false><<<nsm * L.alpha_blocks, L.alpha_warps * 32, L.alpha_smem, s>>>(
         X, nullptr, c->d_V, c->d_H, c->d_T, c->d_s, c->d_G, c->d_W, c->d_M3, R);
     P2_LAUNCH_CHECK("k_alpha<false>");
-    return enqueue_qstep(c, L);
+    return enqueue_qstep(c, 0);
 }
 
 int enqueue_iteration(p2_ctx *c) {
@@ -993,7 +929,7 @@ int enqueue_iteration(p2_ctx *c) {
     cudaStream_t s = c->stream;
     const int nsm = c->geo.nsm;
     const int nb = c->geo.red_blocks;
-    const int64_t J = c->X.J, K = c->X.K;
+    const int64_t J = c->X.J;
     XView X = xview(c);
     const size_t sm_pinv = (size_t)4 * R * R * 8;
     // H step (Algorithm 1 line 3 with U = H; mode-1 MTTKRP from the previous pass)
@@ -1002,13 +938,20 @@ int enqueue_iteration(p2_ctx *c) {
     P2_LAUNCH_CHECK("k_solve_h");
     // pass beta: mode-2 MTTKRP
     mark(c, 1);
-    k_beta<<<nsm, L.beta_warps * 32, L.beta_smem, s>>>(X, c->d_V, c->d_H, c->d_T, c->d_W, c->d_s,
-                                                       c->d_m2acc, R, L.beta_hc);
-    P2_LAUNCH_CHECK("k_beta");
+    k_beta_p<<<nsm * L.beta_blocks, L.beta_warps * 32, L.beta_smem, s>>>(
+        X, c->d_V, c->d_H, c->d_T, c->d_W, c->d_P, R);
+    P2_LAUNCH_CHECK("k_beta_p");
+    if (c->X.nseg > 0) {
+        const int64_t want = (c->X.nseg + 7) / 8;
+        const int sb = (int)(want < 64 * (int64_t)nsm ? want : 64 * (int64_t)nsm);
+        k_m2_segments<<<sb, 256, 0, s>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start, c->X.nseg,
+                                        c->d_P, c->d_segpart, R);
+        P2_LAUNCH_CHECK("k_m2_segments");
+    }
     const int64_t nJR = J * R;
     const int fb = (int)((nJR + 255) / 256 < 4 * nsm ? (nJR + 255) / 256 : 4 * nsm);
-    k_m2_finalize<<<fb, 256, 0, s>>>(c->d_m2acc, c->d_M2, c->d_s, nJR, R);
-    P2_LAUNCH_CHECK("k_m2_finalize");
+    k_m2_columns<<<fb, 256, 0, s>>>(c->d_segpart, c->X.col_seg, c->d_M2, (int32_t)J, R);
+    P2_LAUNCH_CHECK("k_m2_columns");
     // V step (Algorithm 1 line 5)
     mark(c, 2);
     k_solve_v_pinv<<<1, 256, sm_pinv, s>>>(c->d_s, R);
@@ -1026,17 +969,11 @@ int enqueue_iteration(p2_ctx *c) {
     P2_LAUNCH_CHECK("k_fin_v");
     // pass alpha: mode-3 MTTKRP + W step (Algorithm 1 line 7) + Gram for the next Q-step
     mark(c, 3);
-    k_alpha<true><<<nsm, L.alpha_warps * 32, L.alpha_smem, s>>>(
+    k_alpha<true><<<nsm * L.alpha_blocks, L.alpha_warps * 32, L.alpha_smem, s>>>(
         X, c->d_Vprev, c->d_V, c->d_H, c->d_T, c->d_s, c->d_G, c->d_W, c->d_M3, R);
     P2_LAUNCH_CHECK("k_alpha<true>");
-    mark(c, 4);
-    k_gram_w<<<nb, 256, 0, s>>>(c->d_W, c->d_M3, c->d_part2, K, R, 1);
-    P2_LAUNCH_CHECK("k_gram_w");
-    k_fin_w<<<1, 256, 0, s>>>(c->d_part2, nb, c->d_s, R, 1);
-    P2_LAUNCH_CHECK("k_fin_w");
-    // next Q-step (Algorithm 2's SVD loop) and its mode-1 MTTKRP
-    mark(c, 5);
-    int rc = enqueue_qstep(c, L);
+    // next Q-step (Algorithm 2's SVD loop), mode-1 MTTKRP, W statistics, fit
+    int rc = enqueue_qstep(c, 1);
     mark(c, 7);
     return rc;
 }

@@ -10,6 +10,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <vector>
+
 #include "p2_internal.cuh"
 
 namespace p2 {
@@ -96,6 +98,131 @@ __global__ void k_relabel(const int32_t *__restrict__ col, const int32_t *__rest
         col16[i] = (uint16_t)perm[col[i]];
 }
 
+// ---- column-major copy: deterministic counting sort of the non-zeros by column
+__global__ void k_rowid(const int64_t *__restrict__ row_ptr, int64_t N, uint32_t *rowid) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N;
+         r += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) rowid[e] = (uint32_t)r;
+}
+
+// per-chunk column histogram (integer atomics: order independent)
+__global__ void k_chunk_hist(const uint16_t *__restrict__ col, int64_t nnz, int64_t chunk,
+                             int32_t J, int *cnt) {
+    const int64_t a = (int64_t)blockIdx.x * chunk;
+    const int64_t b = (a + chunk < nnz) ? (a + chunk) : nnz;
+    int *row = cnt + (size_t)blockIdx.x * J;
+    for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) atomicAdd(&row[col[e]], 1);
+}
+
+// counts -> start offsets, column by column, chunks in order
+__global__ void k_col_scan(const int64_t *__restrict__ colptr, int nch, int32_t J, int *cnt) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J) return;
+    int run = (int)colptr[j];
+    for (int b = 0; b < nch; ++b) {
+        const int c = cnt[(size_t)b * J + j];
+        cnt[(size_t)b * J + j] = run;
+        run += c;
+    }
+}
+
+// one warp per chunk, non-zeros in order: equal columns inside a group of 32
+// get ranks in lane order, so each column keeps increasing non-zero order
+__global__ void k_chunk_place(const uint16_t *__restrict__ col, const float *__restrict__ val,
+                              const uint32_t *__restrict__ rowid, int64_t nnz, int64_t chunk,
+                              int32_t J, int *cnt, uint32_t *csc_row, float *csc_val) {
+    const int lane = threadIdx.x & 31;
+    const int64_t a = (int64_t)blockIdx.x * chunk;
+    const int64_t b = (a + chunk < nnz) ? (a + chunk) : nnz;
+    int *off = cnt + (size_t)blockIdx.x * J;
+    for (int64_t base = a; base < b; base += 32) {
+        const int64_t e = base + lane;
+        const bool valid = e < b;
+        const int j = valid ? (int)col[e] : 0;
+        const unsigned key = valid ? (unsigned)j : (0x10000u + lane);
+        const unsigned mask = __match_any_sync(0xffffffffu, key);
+        const int rank = __popc(mask & ((1u << lane) - 1u));
+        int b0 = 0;
+        if (valid) {
+            b0 = off[j];
+            const int dest = b0 + rank;
+            csc_row[dest] = rowid[e];
+            csc_val[dest] = val[e];
+        }
+        __syncwarp();
+        if (valid && rank == 0) off[j] = b0 + __popc(mask);
+        __syncwarp();
+    }
+}
+
+static int build_csc(p2_ctx *c, const int64_t *d_row_ptr, const int32_t *h_count_new,
+                     int64_t N, int64_t nnz, int32_t J) {
+    cudaStream_t s = c->stream;
+    const int nsm = c->geo.nsm;
+    // column pointers and segments (host; J <= 65535)
+    std::vector<int64_t> colptr((size_t)J + 1, 0), colseg((size_t)J + 1, 0);
+    std::vector<int64_t> segs;
+    for (int32_t j = 0; j < J; ++j) colptr[j + 1] = colptr[j] + h_count_new[j];
+    for (int32_t j = 0; j < J; ++j) {
+        colseg[j] = (int64_t)segs.size();
+        for (int64_t a = colptr[j]; a < colptr[j + 1]; a += P2_SEG) segs.push_back(a);
+    }
+    colseg[J] = (int64_t)segs.size();
+    segs.push_back(nnz);
+    const int64_t nseg = (int64_t)segs.size() - 1;
+    c->X.nseg = nseg;
+    cudaError_t e = cudaMalloc(&c->X.seg_start, sizeof(int64_t) * segs.size());
+    if (e == cudaSuccess) e = cudaMalloc(&c->X.col_seg, sizeof(int64_t) * ((size_t)J + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&c->X.csc_row, sizeof(uint32_t) * (nnz > 0 ? nnz : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&c->X.csc_val, sizeof(float) * (nnz > 0 ? nnz : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_segpart, sizeof(double) * (size_t)(nseg > 0 ? nseg : 1) * c->R);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("load: allocation of the column-major copy failed: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? P2_ENOMEM : P2_ECUDA;
+    }
+    c->dev_bytes += sizeof(int64_t) * (segs.size() + J + 1) + (sizeof(uint32_t) + sizeof(float)) * (size_t)nnz +
+                    sizeof(double) * (size_t)nseg * c->R;
+    P2_CUDA_TRY(cudaMemcpyAsync(c->X.seg_start, segs.data(), sizeof(int64_t) * segs.size(),
+                                cudaMemcpyHostToDevice, s));
+    P2_CUDA_TRY(cudaMemcpyAsync(c->X.col_seg, colseg.data(), sizeof(int64_t) * ((size_t)J + 1),
+                                cudaMemcpyHostToDevice, s));
+    if (nnz == 0) return P2_OK;
+    // chunking keeps the per-chunk count matrix near 256 MB at most
+    int64_t nch = (nnz + 65535) / 65536;
+    const int64_t maxch = (256ll << 20) / (4ll * J);
+    if (nch > maxch) nch = maxch > 0 ? maxch : 1;
+    const int64_t chunk = (nnz + nch - 1) / nch;
+    nch = (nnz + chunk - 1) / chunk;
+    int64_t *d_colptr = nullptr;
+    uint32_t *d_rowid = nullptr;
+    int *d_cnt = nullptr;
+    e = cudaMalloc(&d_colptr, sizeof(int64_t) * ((size_t)J + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_rowid, sizeof(uint32_t) * (size_t)nnz);
+    if (e == cudaSuccess) e = cudaMalloc(&d_cnt, sizeof(int) * (size_t)nch * J);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_colptr, colptr.data(), sizeof(int64_t) * ((size_t)J + 1),
+                                              cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(int) * (size_t)nch * J, s);
+    if (e == cudaSuccess) {
+        k_rowid<<<8 * nsm, 256, 0, s>>>(d_row_ptr, N, d_rowid);
+        k_chunk_hist<<<(int)nch, 256, 0, s>>>(c->X.col, nnz, chunk, J, d_cnt);
+        k_col_scan<<<(J + 255) / 256, 256, 0, s>>>(d_colptr, (int)nch, J, d_cnt);
+        k_chunk_place<<<(int)nch, 32, 0, s>>>(c->X.col, c->X.val, d_rowid, nnz, chunk, J, d_cnt,
+                                              c->X.csc_row, c->X.csc_val);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFree(d_colptr);
+    cudaFree(d_rowid);
+    cudaFree(d_cnt);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        set_error("load: building the column-major copy failed: %s", cudaGetErrorString(e));
+        return P2_ECUDA;
+    }
+    return P2_OK;
+}
+
 int launch_load(p2_ctx *c, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
                 const int32_t *d_col, const float *d_val, int64_t K, int32_t J, int64_t N,
                 int64_t nnz) {
@@ -165,11 +292,17 @@ int launch_load(p2_ctx *c, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
         delete[] tmp;
         for (int r = 0; r < J; ++r) c->h_perm_old2new[order[r]] = r;
     }
+    std::vector<int32_t> count_new((size_t)J);
+    for (int r = 0; r < J; ++r) count_new[r] = cc[c->h_perm_new2old[r]];
     delete[] cc;
     P2_CUDA_TRY(cudaMemcpyAsync(c->d_perm_old2new, c->h_perm_old2new, sizeof(int32_t) * (size_t)J,
                                 cudaMemcpyHostToDevice, s));
     if (nnz > 0) k_relabel<<<8 * nsm, 256, 0, s>>>(d_col, c->d_perm_old2new, nnz, c->X.col);
     P2_CUDA_TRY(cudaGetLastError());
+    {
+        int rc = build_csc(c, d_row_ptr, count_new.data(), N, nnz, J);
+        if (rc != P2_OK) return rc;
+    }
     float maxabs;
     memcpy(&maxabs, &h.maxabs_bits, sizeof(float));
     const double xbound = (double)maxcount * (double)maxabs;

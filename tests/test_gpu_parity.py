@@ -120,3 +120,21 @@ def test_invalid_input_rejected(p2):
         with pytest.raises(p2.P2Error) as ei:
             p2.p2_iterate(m.ctx, 1)
         assert ei.value.code == p2.P2_ESTATE
+
+
+def test_stats_and_phase_timing(p2):
+    """p2_stats: phase events inside the captured graph, launch and FP64 counters."""
+    X = synth.generate("c63m", K=800)
+    R = 10
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=2)
+    with p2.Parafac2(R, timing=True) as m:
+        m.load(X)
+        m.init(H0, V0, W0)
+        s0 = m.stats()
+        m.iterate(2, want_fit=False)
+        s1 = m.stats()
+    assert s1["iterations"] == 2
+    assert s1["kernel_launches"] > s0["kernel_launches"]
+    assert set(s1["phase_ms"]) == set(p2.PHASES)
+    assert all(v > 0 for v in s1["phase_ms"].values()), s1["phase_ms"]
+    assert s1["polar_fp64_flops"] > s0["polar_fp64_flops"] > 0

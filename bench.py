@@ -314,7 +314,7 @@ def run_p2(args, w):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "s_per_iter": ms_step / 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 storage/SpMM, f64 Gram, Procrustes and solves", "data": "synthetic",
+            "dtype": "f32 storage and SpMM (Gram: error-free f32 pairs), f64 Procrustes and solves", "data": "synthetic",
             "config": {"workload": _workload_desc(w, X), "K": X.K, "J": X.J, "R": R,
                        "nnz": int(X.nnz), "rows": int(X.n_rows),
                        "l2": "inputs larger than L2: X (~6 B/nnz) streamed twice per step",

@@ -54,50 +54,48 @@ static XView xview(const p2_ctx *c) {
 }
 
 // z rows of up to 32 consecutive rows: z1[i][:] = X(row i, :) V1 and, when
-// TWO, z2[i][:] = X(row i, :) V2.  LPR lanes share a row (lane sub-index
-// covers components sub and sub + LPR), RPP rows per pass.  FP32 FMA in
-// column order within a row.
-template <bool TWO>
+// TWO, z2[i][:] = X(row i, :) V2.  One lane per row, so a chunk costs one
+// round of dependent loads; the row's components are accumulated in
+// registers in blocks of CB (FP32 FMA in column order within the row) and
+// stored with the odd row stride RS (no shared-memory bank conflicts).
+template <int CB, bool TWO>
 static __device__ __forceinline__ void gather_rows(const XView &X, int nr, int64_t base, int len,
                                                    int off, const float *__restrict__ V1,
                                                    const float *__restrict__ V2, float *z1,
-                                                   float *z2, int R, int LPR, int RPP, int lane) {
-    const int g = lane / LPR;
-    const int sub = lane - g * LPR;
-    for (int i0 = 0; i0 < nr; i0 += RPP) {
-        const int i = i0 + g;
-        const int src = (i < 32) ? i : 31;
-        const int ro = __shfl_sync(FULLMASK, off, src);
-        const int rl = __shfl_sync(FULLMASK, len, src);
-        const bool valid = (g < RPP) && (i < nr);
-        float a1[2] = {0.f, 0.f}, a2[2] = {0.f, 0.f};
-        if (valid) {
-            for (int e = 0; e < rl; ++e) {
-                const int64_t idx = base + ro + e;
-                const int j = X.col[idx];
-                const float x = X.val[idx];
-                const float *v1 = V1 + (size_t)j * R;
-                const float *v2 = TWO ? (V2 + (size_t)j * R) : nullptr;
+                                                   float *z2, int R, int RS, int lane) {
+    if (lane >= nr) return;
+    const int64_t b0 = base + off;
+    for (int cb = 0; cb < R; cb += CB) {
+        float a1[CB], a2[CB];
 #pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    const int c = sub + t * LPR;
-                    if (c < R) {
-                        a1[t] = fmaf(x, __ldg(v1 + c), a1[t]);
-                        if (TWO) a2[t] = fmaf(x, __ldg(v2 + c), a2[t]);
-                    }
+        for (int c = 0; c < CB; ++c) {
+            a1[c] = 0.f;
+            a2[c] = 0.f;
+        }
+        for (int e = 0; e < len; ++e) {
+            const int j = X.col[b0 + e];
+            const float x = X.val[b0 + e];
+            const float *v1 = V1 + (size_t)j * R + cb;
+            const float *v2 = TWO ? (V2 + (size_t)j * R + cb) : nullptr;
+#pragma unroll
+            for (int c = 0; c < CB; ++c) {
+                if (cb + c < R) {
+                    a1[c] = fmaf(x, __ldg(v1 + c), a1[c]);
+                    if (TWO) a2[c] = fmaf(x, __ldg(v2 + c), a2[c]);
                 }
             }
+        }
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const int c = sub + t * LPR;
-                if (c < R) {
-                    z1[i * R + c] = a1[t];
-                    if (TWO) z2[i * R + c] = a2[t];
-                }
+        for (int c = 0; c < CB; ++c) {
+            if (cb + c < R) {
+                z1[lane * RS + cb + c] = a1[c];
+                if (TWO) z2[lane * RS + cb + c] = a2[c];
             }
         }
     }
 }
+
+static __host__ __device__ __forceinline__ int row_stride(int R) { return R | 1; }
 
 // ---------------------------------------------------------------------------
 // Pass alpha: for each subject, Gram of Z'_k = X_k V (packed lower; every
@@ -107,8 +105,8 @@ static __device__ __forceinline__ void gather_rows(const XView &X, int nr, int64
 // and, with MODE3, the mode-3 MTTKRP row M3(k,:) = coldot(H, T_k Z_k^T Z'_k)
 // with Z_k = X_k Vprev, followed by W(k,:) = M3(k,:) (V^TV * H^TH)^+.
 // ---------------------------------------------------------------------------
-template <bool MODE3>
-__global__ void __launch_bounds__(512) k_alpha(XView X, const float *__restrict__ Vprev,
+template <int CB, bool MODE3>
+__global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_alpha(XView X, const float *__restrict__ Vprev,
                                                const float *__restrict__ V,
                                                const float *__restrict__ H,
                                                const float *__restrict__ T,
@@ -116,8 +114,7 @@ __global__ void __launch_bounds__(512) k_alpha(XView X, const float *__restrict_
                                                float *W, float *M3, int R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = R * (R + 1) / 2;
-    const int LPR = R < 32 ? R : 32;
-    const int RPP = 32 / LPR;
+    const int RS = row_stride(R);
     // CTA-shared: G3inv (R*R doubles), H (R*R floats), packed index table
     double *G3s = reinterpret_cast<double *>(smem_raw);
     float *Hs = reinterpret_cast<float *>(G3s + R * R);
@@ -125,13 +122,13 @@ __global__ void __launch_bounds__(512) k_alpha(XView X, const float *__restrict_
     uint8_t *pc = pr + P;
     size_t cta_bytes = ((size_t)R * R * 8 + (size_t)R * R * 4 + 2 * (size_t)P + 15) & ~(size_t)15;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t warp_bytes = (size_t)P * 8 + ((size_t)64 * R + 2 * (size_t)R * R) * 4;
+    const size_t warp_bytes = (size_t)P * 8 + ((size_t)64 * RS + 2 * (size_t)R * R) * 4;
     unsigned char *wb = smem_raw + cta_bytes + warp * warp_bytes;
     float *Ghi = reinterpret_cast<float *>(wb);
     float *Glo = Ghi + P;
-    float *zo = Glo + P;                                // 32 R  (zo and zn contiguous: 64 R scratch)
-    float *zn = zo + 32 * R;                            // 32 R
-    float *Tk = zn + 32 * R;                            // R R
+    float *zo = Glo + P;                                // 32 RS (zo and zn contiguous: 64 RS scratch)
+    float *zn = zo + 32 * RS;                           // 32 RS
+    float *Tk = zn + 32 * RS;                           // R R
     float *Cacc = Tk + R * R;                           // R R
 
     for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
@@ -163,16 +160,15 @@ __global__ void __launch_bounds__(512) k_alpha(XView X, const float *__restrict_
             const int off = warp_excl_scan(len, lane);
             const int tot = __shfl_sync(FULLMASK, off + len, 31);
             if (MODE3)
-                gather_rows<true>(X, nr, base, len, off, Vprev, V, zo, zn, R, LPR, RPP, lane);
+                gather_rows<CB, true>(X, nr, base, len, off, Vprev, V, zo, zn, R, RS, lane);
             else
-                gather_rows<false>(X, nr, base, len, off, V, nullptr, zn, nullptr, R, LPR, RPP,
-                                   lane);
+                gather_rows<CB, false>(X, nr, base, len, off, V, nullptr, zn, nullptr, R, RS, lane);
             __syncwarp();
             if (MODE3) {
                 for (int e = lane; e < R * R; e += 32) {
                     const int r = e / R, s = e - r * R;
                     float acc = 0.f;
-                    for (int i = 0; i < nr; ++i) acc = fmaf(zo[i * R + r], zn[i * R + s], acc);
+                    for (int i = 0; i < nr; ++i) acc = fmaf(zo[i * RS + r], zn[i * RS + s], acc);
                     Cacc[e] += acc;
                 }
             }
@@ -180,7 +176,7 @@ __global__ void __launch_bounds__(512) k_alpha(XView X, const float *__restrict_
                 const int r = pr[p], s = pc[p];
                 float sh = Ghi[p], sl = Glo[p];
                 for (int i = 0; i < nr; ++i) {
-                    const float a = zn[i * R + r], b = zn[i * R + s];
+                    const float a = zn[i * RS + r], b = zn[i * RS + s];
                     const float pa = a * b;
                     const float pe = fmaf(a, b, -pa);           // a*b = pa + pe exactly
                     const float t = sh + pa;                    // TwoSum(sh, pa)
@@ -201,7 +197,7 @@ __global__ void __launch_bounds__(512) k_alpha(XView X, const float *__restrict_
             const float *Tg = T + (size_t)k * R * R;
             for (int e = lane; e < R * R; e += 32) Tk[e] = Tg[e];
             __syncwarp();
-            float *scr = zo;   // 64 R >= R R floats of scratch
+            float *scr = zo;   // 64 RS >= R R floats of scratch
             for (int e = lane; e < R * R; e += 32) {
                 const int r = e / R, s = e - r * R;
                 float b = 0.f;
@@ -231,20 +227,22 @@ __global__ void __launch_bounds__(512) k_alpha(XView X, const float *__restrict_
 // mode 2 (Eq. mttkrp2_3) is M2 = sum_k Y_k^T H S_k = sum_k X_k^T P_k.
 // One warp per subject; the rows go to P (N x R) in stacked-row order.
 // ---------------------------------------------------------------------------
-static __host__ __device__ size_t beta_warp_bytes(int R) { return ((size_t)64 * R + 2 * (size_t)R * R + R) * 4; }
+static __host__ __device__ size_t beta_warp_bytes(int R) {
+    return ((size_t)32 * row_stride(R) + 2 * (size_t)R * R + R) * 4;
+}
 
-__global__ void __launch_bounds__(512) k_beta_p(XView X, const float *__restrict__ V,
+template <int CB>
+__global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_beta_p(XView X, const float *__restrict__ V,
                                                 const float *__restrict__ H,
                                                 const float *__restrict__ T,
                                                 const float *__restrict__ W, float *Pout, int R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int LPR = R < 32 ? R : 32;
-    const int RPP = 32 / LPR;
+    const int RS = row_stride(R);
     float *Hs = reinterpret_cast<float *>(smem_raw);
     const size_t cta_bytes = ((size_t)R * R * 4 + 15) & ~(size_t)15;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *zo = reinterpret_cast<float *>(smem_raw + cta_bytes + warp * beta_warp_bytes(R));
-    float *Tk = zo + 64 * R;
+    float *Tk = zo + 32 * RS;
     float *Fk = Tk + R * R;
     float *wk = Fk + R * R;
     for (int i = threadIdx.x; i < R * R; i += blockDim.x) Hs[i] = H[i];
@@ -270,13 +268,13 @@ __global__ void __launch_bounds__(512) k_beta_p(XView X, const float *__restrict
             const int len = (lane < nr) ? (int)X.row_len[cr + lane] : 0;
             const int off = warp_excl_scan(len, lane);
             const int tot = __shfl_sync(FULLMASK, off + len, 31);
-            gather_rows<false>(X, nr, base, len, off, V, nullptr, zo, nullptr, R, LPR, RPP, lane);
+            gather_rows<CB, false>(X, nr, base, len, off, V, nullptr, zo, nullptr, R, RS, lane);
             __syncwarp();
             float *Pr = Pout + (size_t)cr * R;
             for (int e = lane; e < nr * R; e += 32) {
                 const int i = e / R, s = e - i * R;
                 float p = 0.f;
-                for (int u = 0; u < R; ++u) p = fmaf(zo[i * R + u], Fk[u * R + s], p);
+                for (int u = 0; u < R; ++u) p = fmaf(zo[i * RS + u], Fk[u * R + s], p);
                 Pr[e] = p;
             }
             __syncwarp();
@@ -288,67 +286,70 @@ __global__ void __launch_bounds__(512) k_beta_p(XView X, const float *__restrict
 // ---------------------------------------------------------------------------
 // Pass beta, part 2: M2(j, :) = sum over the non-zeros x of column j of
 // x * P(row, :), read column-major.  One warp per column segment (at most
-// P2_SEG non-zeros); lanes accumulate with Kahan-compensated FP32; the lane
-// groups are combined in FP64 in a fixed order.  No atomics: deterministic.
+// P2_SEG non-zeros), one lane per non-zero (32 rows of P in flight per
+// warp); each lane accumulates CB components with Kahan-compensated FP32 and
+// the lanes are combined by a fixed xor-butterfly in FP64.  No atomics:
+// deterministic.
 // ---------------------------------------------------------------------------
+template <int CB>
 __global__ void __launch_bounds__(256) k_m2_segments(const uint32_t *__restrict__ csc_row,
                                                      const float *__restrict__ csc_val,
                                                      const int64_t *__restrict__ seg_start,
                                                      int64_t nseg, const float *__restrict__ Pin,
                                                      double *segpart, int R) {
-    __shared__ double red[8][64];
-    const int LPR = R < 32 ? R : 32;
-    const int RPP = 32 / LPR;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane / LPR, sub = lane - g * LPR;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t sg = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; sg < nseg; sg += nwarps) {
         const int64_t a = seg_start[sg], b = seg_start[sg + 1];
-        float hi[2] = {0.f, 0.f}, cp[2] = {0.f, 0.f};
-        if (g < RPP) {
-            for (int64_t e = a + g; e < b; e += RPP) {
+        for (int cb = 0; cb < R; cb += CB) {
+            float hi[CB], cp[CB];
+#pragma unroll
+            for (int c = 0; c < CB; ++c) {
+                hi[c] = 0.f;
+                cp[c] = 0.f;
+            }
+            for (int64_t e = a + lane; e < b; e += 32) {
                 const uint32_t row = csc_row[e];
                 const float x = csc_val[e];
-                const float *pr = Pin + (size_t)row * R;
+                const float *pr = Pin + (size_t)row * R + cb;
 #pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    const int c = sub + t * LPR;
-                    if (c < R) {
-                        const float y = x * __ldg(pr + c) - cp[t];
-                        const float tt = hi[t] + y;
-                        cp[t] = (tt - hi[t]) - y;
-                        hi[t] = tt;
+                for (int c = 0; c < CB; ++c) {
+                    if (cb + c < R) {
+                        const float y = x * __ldg(pr + c) - cp[c];
+                        const float tt = hi[c] + y;
+                        cp[c] = (tt - hi[c]) - y;
+                        hi[c] = tt;
                     }
                 }
             }
-        }
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const int c = sub + t * LPR;
-            if (g < RPP && c < R) red[warp][lane + 32 * t] = (double)hi[t] - (double)cp[t];
+            for (int c = 0; c < CB; ++c) {
+                if (cb + c < R) {
+                    double v = (double)hi[c] - (double)cp[c];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLMASK, v, o);
+                    if (lane == 0) segpart[(size_t)sg * R + cb + c] = v;
+                }
+            }
         }
-        __syncwarp();
-        for (int c = lane; c < R; c += 32) {
-            const int cs = c % LPR, ct = c / LPR;
-            double acc = 0.0;
-            for (int gg = 0; gg < RPP; ++gg) acc += red[warp][gg * LPR + cs + 32 * ct];
-            segpart[(size_t)sg * R + c] = acc;
-        }
-        __syncwarp();
     }
 }
 
-// M2(j, :) = sum of column j's segment partials, in segment order (FP64).
+// M2(j, :) = sum of column j's segment partials (FP64): one warp per column,
+// lanes take segments in a fixed stride, combined by a fixed xor-butterfly.
 __global__ void k_m2_columns(const double *__restrict__ segpart, const int64_t *__restrict__ col_seg,
                              double *M2, int32_t J, int R) {
-    const int64_t n = (int64_t)J * R;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = e / R;
-        const int c = (int)(e - j * R);
-        double acc = 0.0;
-        for (int64_t sg = col_seg[j]; sg < col_seg[j + 1]; ++sg) acc += segpart[(size_t)sg * R + c];
-        M2[e] = acc;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; j < J; j += nwarps) {
+        const int64_t s0 = col_seg[j], s1 = col_seg[j + 1];
+        for (int c = 0; c < R; ++c) {
+            double acc = 0.0;
+            for (int64_t sg = s0 + lane; sg < s1; sg += 32) acc += segpart[(size_t)sg * R + c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULLMASK, acc, o);
+            if (lane == 0) M2[(size_t)j * R + c] = acc;
+        }
     }
 }
 
@@ -775,8 +776,11 @@ static size_t alpha_cta_bytes(int R) {
 }
 static size_t alpha_warp_bytes(int R) {
     const int P = R * (R + 1) / 2;
-    return (size_t)P * 8 + ((size_t)64 * R + 2 * (size_t)R * R) * 4;
+    return (size_t)P * 8 + ((size_t)64 * row_stride(R) + 2 * (size_t)R * R) * 4;
 }
+
+// register block of components in the sparse passes: 8, 16 or 32
+static int comp_block(int R) { return R <= 8 ? 8 : (R <= 16 ? 16 : 32); }
 
 struct Launch {
     int alpha_warps, beta_warps, alpha_blocks, beta_blocks;
@@ -796,11 +800,12 @@ static Launch plan(const p2_ctx *c) {
     Launch L{};
     const int R = c->R;
     const size_t cap = (size_t)c->geo.smem_optin;
-    int aw = 16;
+    const int wmax = comp_block(R) >= 32 ? 8 : 16;     // launch bounds of the CB = 32 variants
+    int aw = wmax;
     while (aw > 1 && alpha_cta_bytes(R) + aw * alpha_warp_bytes(R) > cap) --aw;
     L.alpha_warps = aw;
     L.alpha_smem = alpha_cta_bytes(R) + aw * alpha_warp_bytes(R);
-    int bw = 16;
+    int bw = wmax;
     const size_t bcta = ((size_t)R * R * 4 + 15) & ~(size_t)15;
     while (bw > 1 && bcta + bw * beta_warp_bytes(R) > cap) --bw;
     L.beta_warps = bw;
@@ -827,9 +832,15 @@ static int allow_dynamic_smem(F *fn, int cap, const char *name) {
 int configure_kernels(p2_ctx *c) {
     const int cap = c->geo.smem_optin;
     int rc = P2_OK;
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<true>, cap, "k_alpha<true>");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<false>, cap, "k_alpha<false>");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p, cap, "k_beta_p");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<8, true>, cap, "k_alpha");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<8, false>, cap, "k_alpha");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<16, true>, cap, "k_alpha");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<16, false>, cap, "k_alpha");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<32, true>, cap, "k_alpha");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<32, false>, cap, "k_alpha");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<8>, cap, "k_beta_p");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<16>, cap, "k_beta_p");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<32>, cap, "k_beta_p");
     if (rc == P2_OK) rc = polar_configure(c);
     if (rc == P2_OK) rc = allow_dynamic_smem(k_solve_h, cap, "k_solve_h");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_solve_v_pinv, cap, "k_solve_v_pinv");
@@ -864,6 +875,61 @@ static void mark(p2_ctx *c, int i) {
         cudaEventRecordWithFlags(c->ev[i], c->stream, cudaEventRecordExternal);
     else
         cudaEventRecord(c->ev[i], c->stream);
+}
+
+template <bool MODE3>
+static void launch_alpha(p2_ctx *c, const Launch &L, const float *Vprev) {
+    dim3 grid(c->geo.nsm * L.alpha_blocks), block(L.alpha_warps * 32);
+    XView X = xview(c);
+    switch (comp_block(c->R)) {
+        case 8:
+            k_alpha<8, MODE3><<<grid, block, L.alpha_smem, c->stream>>>(
+                X, Vprev, c->d_V, c->d_H, c->d_T, c->d_s, c->d_G, c->d_W, c->d_M3, c->R);
+            break;
+        case 16:
+            k_alpha<16, MODE3><<<grid, block, L.alpha_smem, c->stream>>>(
+                X, Vprev, c->d_V, c->d_H, c->d_T, c->d_s, c->d_G, c->d_W, c->d_M3, c->R);
+            break;
+        default:
+            k_alpha<32, MODE3><<<grid, block, L.alpha_smem, c->stream>>>(
+                X, Vprev, c->d_V, c->d_H, c->d_T, c->d_s, c->d_G, c->d_W, c->d_M3, c->R);
+            break;
+    }
+}
+
+static void launch_beta_p(p2_ctx *c, const Launch &L) {
+    dim3 grid(c->geo.nsm * L.beta_blocks), block(L.beta_warps * 32);
+    XView X = xview(c);
+    switch (comp_block(c->R)) {
+        case 8:
+            k_beta_p<8><<<grid, block, L.beta_smem, c->stream>>>(X, c->d_V, c->d_H, c->d_T, c->d_W, c->d_P, c->R);
+            break;
+        case 16:
+            k_beta_p<16><<<grid, block, L.beta_smem, c->stream>>>(X, c->d_V, c->d_H, c->d_T, c->d_W, c->d_P, c->R);
+            break;
+        default:
+            k_beta_p<32><<<grid, block, L.beta_smem, c->stream>>>(X, c->d_V, c->d_H, c->d_T, c->d_W, c->d_P, c->R);
+            break;
+    }
+}
+
+static void launch_m2_segments(p2_ctx *c) {
+    const int64_t want = (c->X.nseg + 7) / 8;
+    const int sb = (int)(want < 64 * (int64_t)c->geo.nsm ? want : 64 * (int64_t)c->geo.nsm);
+    switch (comp_block(c->R)) {
+        case 8:
+            k_m2_segments<8><<<sb, 256, 0, c->stream>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
+                                                        c->X.nseg, c->d_P, c->d_segpart, c->R);
+            break;
+        case 16:
+            k_m2_segments<16><<<sb, 256, 0, c->stream>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
+                                                         c->X.nseg, c->d_P, c->d_segpart, c->R);
+            break;
+        default:
+            k_m2_segments<32><<<sb, 256, 0, c->stream>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
+                                                         c->X.nseg, c->d_P, c->d_segpart, c->R);
+            break;
+    }
 }
 
 // Q-step for the current (H, V, W) (Algorithm 2's SVD loop), then the
@@ -913,12 +979,7 @@ int enqueue_factor_stats(p2_ctx *c) {
 
 int enqueue_prologue(p2_ctx *c) {
     const Launch L = plan(c);
-    const int R = c->R;
-    cudaStream_t s = c->stream;
-    const int nsm = c->geo.nsm;
-    XView X = xview(c);
-    k_alpha<false><<<nsm * L.alpha_blocks, L.alpha_warps * 32, L.alpha_smem, s>>>(
-        X, nullptr, c->d_V, c->d_H, c->d_T, c->d_s, c->d_G, c->d_W, c->d_M3, R);
+    launch_alpha<false>(c, L, nullptr);
     P2_LAUNCH_CHECK("k_alpha<false>");
     return enqueue_qstep(c, 0);
 }
@@ -930,7 +991,6 @@ int enqueue_iteration(p2_ctx *c) {
     const int nsm = c->geo.nsm;
     const int nb = c->geo.red_blocks;
     const int64_t J = c->X.J;
-    XView X = xview(c);
     const size_t sm_pinv = (size_t)4 * R * R * 8;
     // H step (Algorithm 1 line 3 with U = H; mode-1 MTTKRP from the previous pass)
     mark(c, 0);
@@ -938,19 +998,16 @@ int enqueue_iteration(p2_ctx *c) {
     P2_LAUNCH_CHECK("k_solve_h");
     // pass beta: mode-2 MTTKRP
     mark(c, 1);
-    k_beta_p<<<nsm * L.beta_blocks, L.beta_warps * 32, L.beta_smem, s>>>(
-        X, c->d_V, c->d_H, c->d_T, c->d_W, c->d_P, R);
+    launch_beta_p(c, L);
     P2_LAUNCH_CHECK("k_beta_p");
     if (c->X.nseg > 0) {
-        const int64_t want = (c->X.nseg + 7) / 8;
-        const int sb = (int)(want < 64 * (int64_t)nsm ? want : 64 * (int64_t)nsm);
-        k_m2_segments<<<sb, 256, 0, s>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start, c->X.nseg,
-                                        c->d_P, c->d_segpart, R);
+        launch_m2_segments(c);
         P2_LAUNCH_CHECK("k_m2_segments");
     }
     const int64_t nJR = J * R;
     const int fb = (int)((nJR + 255) / 256 < 4 * nsm ? (nJR + 255) / 256 : 4 * nsm);
-    k_m2_columns<<<fb, 256, 0, s>>>(c->d_segpart, c->X.col_seg, c->d_M2, (int32_t)J, R);
+    const int cb_blocks = (int)((J + 7) / 8 < 8 * nsm ? (J + 7) / 8 : 8 * nsm);
+    k_m2_columns<<<cb_blocks, 256, 0, s>>>(c->d_segpart, c->X.col_seg, c->d_M2, (int32_t)J, R);
     P2_LAUNCH_CHECK("k_m2_columns");
     // V step (Algorithm 1 line 5)
     mark(c, 2);
@@ -969,8 +1026,7 @@ int enqueue_iteration(p2_ctx *c) {
     P2_LAUNCH_CHECK("k_fin_v");
     // pass alpha: mode-3 MTTKRP + W step (Algorithm 1 line 7) + Gram for the next Q-step
     mark(c, 3);
-    k_alpha<true><<<nsm * L.alpha_blocks, L.alpha_warps * 32, L.alpha_smem, s>>>(
-        X, c->d_Vprev, c->d_V, c->d_H, c->d_T, c->d_s, c->d_G, c->d_W, c->d_M3, R);
+    launch_alpha<true>(c, L, c->d_Vprev);
     P2_LAUNCH_CHECK("k_alpha<true>");
     // next Q-step (Algorithm 2's SVD loop), mode-1 MTTKRP, W statistics, fit
     int rc = enqueue_qstep(c, 1);

@@ -25,7 +25,8 @@ _NAMES = {0: "P2_OK", 1: "P2_EINVAL", 2: "P2_ENOMEM", 3: "P2_ECUDA", 4: "P2_ENUM
 # every symbol include/p2.h declares
 EXPORTED = ("p2_default_options", "p2_create", "p2_destroy", "p2_load_slices", "p2_init",
             "p2_iterate", "p2_fit", "p2_get_factors", "p2_set_factors", "p2_get_mttkrp",
-            "p2_get_procrustes", "p2_stats", "p2_device_bytes", "p2_last_error")
+            "p2_get_procrustes", "p2_stats", "p2_device_bytes", "p2_mode1_stats_noalloc",
+            "p2_last_error")
 
 
 class p2_options(ctypes.Structure):
@@ -70,6 +71,7 @@ def _load():
         "p2_get_procrustes": ([vp, i64, i64, vp], ctypes.c_int),
         "p2_stats": ([vp, ctypes.POINTER(p2_stats_t)], ctypes.c_int),
         "p2_device_bytes": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "p2_mode1_stats_noalloc": ([i64, i32, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "p2_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -187,6 +189,22 @@ def p2_device_bytes(ctx) -> int:
     b = ctypes.c_int64()
     _check(lib.p2_device_bytes(ctx, ctypes.byref(b)), "p2_device_bytes")
     return b.value
+
+
+def p2_mode1_stats_noalloc(K, R, T, G, W, M1, WtW=None, stream=None):
+    """Allocation-free mode-1 MTTKRP and W^TW from device tensors (see include/p2.h).
+
+    T (K x R x R float32), G (K x R(R+1)/2 float64), W (K x R float32) and the
+    outputs M1, WtW (R x R float64) are CUDA tensors; stream is a cudaStream_t
+    handle (default: torch's current stream).  For callers that cannot
+    allocate device memory at the point of the call.
+    """
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib.p2_mode1_stats_noalloc(int(K), int(R), _ptr(T), _ptr(G), _ptr(W), _ptr(M1),
+                                      _ptr(WtW), ctypes.c_void_p(stream)),
+           "p2_mode1_stats_noalloc")
 
 
 class Parafac2:

@@ -131,6 +131,17 @@ struct p2_ctx {
 };
 
 namespace p2 {
+// shared-memory bytes per warp of k_subject_stats (multiple of 16: FP64 first)
+static inline __host__ __device__ size_t stats_warp_bytes(int R) {
+    return ((size_t)R * R * 16 + ((size_t)2 * R * R + R) * 4 + 15) & ~(size_t)15;
+}
+// per-subject statistics after the Q-step (p2_kernels.cu): block partials
+// [R*R M1][R*R WtW][R max|W|][1 <W,M3>] over fixed contiguous subject ranges
+__global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__ T,
+                                                       const double *__restrict__ G,
+                                                       const float *__restrict__ W,
+                                                       const float *__restrict__ M3, double *part,
+                                                       int64_t K, int R, int with_m3);
 // per-iteration pieces (p2_kernels.cu)
 int enqueue_prologue(p2_ctx *c);     // Q-step + mode-1 MTTKRP for the current (H, V, W)
 int enqueue_iteration(p2_ctx *c);    // one ALS iteration

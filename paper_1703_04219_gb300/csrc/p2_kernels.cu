@@ -362,10 +362,6 @@ __global__ void k_m2_columns(const double *__restrict__ segpart, const int64_t *
 // FP64 (W^TW products of FP32 values are exact in FP64).  Block partials,
 // layout [R*R M1][R*R WtW][R wmax][1 wm3], summed later in block order.
 // ---------------------------------------------------------------------------
-static __host__ __device__ size_t stats_warp_bytes(int R) {   // multiple of 16: FP64 first
-    return ((size_t)R * R * 16 + ((size_t)2 * R * R + R) * 4 + 15) & ~(size_t)15;
-}
-
 __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__ T,
                                                        const double *__restrict__ G,
                                                        const float *__restrict__ W,

@@ -130,6 +130,19 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(x, dist, device="cpu"):
+    """Largest value of x over all ranks (the slowest rank sets the job time)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(nnz_per_rank, steps, ms_total_max, world):
+    """Whole-job nnz/s: every rank processed its replica; time is the max over ranks."""
+    return world * nnz_per_rank * steps / (ms_total_max / 1e3)
+
+
 def _traffic(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary, if it matches the sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -268,11 +281,9 @@ def run_p2(args, w):
     st1 = m.stats()
     fit, loss = m.fit()
     if pg:
-        t = torch.tensor([ms_total], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_total = float(t.item())
+        ms_total = max_over_ranks(ms_total, pg, device="cuda")
     ms_step = ms_total / args.steps
-    value = world * X.nnz * args.steps / (ms_total / 1e3)
+    value = job_throughput(X.nnz, args.steps, ms_total, world)
     phase_ms = {k: v / args.steps for k, v in phase_sum.items()}
     launches = st1["kernel_launches"] - st0["kernel_launches"]
 
@@ -354,9 +365,7 @@ def run_e2e(m, X, H0, V0, W0, steps, world, pg):
             times.append(dt)
     step = statistics.mean(times)
     if pg:
-        t = torch.tensor([step], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        step = float(t.item())
+        step = max_over_ranks(step, pg, device="cuda")
     return {"value": world * X.nnz / step, "unit": UNIT, "s_per_step": step,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8,
             "step": "p2_load_slices (host, pinned) + p2_init + p2_iterate(1) + fit read-back",

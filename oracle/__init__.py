@@ -7,5 +7,5 @@ two share no code.
 from .parafac2 import (  # noqa: F401
     RANK_RTOL, subject_block, all_blocks, procrustes_q, form_y, mttkrp_spartan,
     pinv_sym, normalize_columns, cp_als_sweep, surrogate_loss, exact_loss, norm_x_sq,
-    fit_from_loss, als_iteration, parafac2_als, assemble_u,
+    fit_from_loss, als_iteration, parafac2_als, assemble_u, project_subject,
 )

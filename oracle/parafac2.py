@@ -219,6 +219,25 @@ def parafac2_als(slices, H0, V0, W0, n_iter, rank_rtol=RANK_RTOL, blocks=None,
     return dict(H=H, V=V, W=W, history=hist, last=last, norm_x_sq=nx2)
 
 
+# --------------------------------------------------------------------------
+# projection of a new subject onto a fixed model (serving): Algorithm 2's
+# Q-step and Algorithm 1's W update (mode-3 MTTKRP, Eq. mttkrp3_row_wise,
+# times (V^TV * H^TH)^+) applied to one subject with H and V held fixed
+# --------------------------------------------------------------------------
+def project_subject(Xc, cols, H, V, n_iter, rank_rtol=RANK_RTOL, s0=None):
+    """Alternate Q <- Procrustes(X, H, V, diag(s)) and s <- coldot(H, Q^T X V) G3^+,
+    starting from s = 1 (or s0), n_iter times; return s and the Q for the final s."""
+    R = H.shape[0]
+    s = np.ones(R) if s0 is None else np.asarray(s0, np.float64)
+    G3p = pinv_sym((V.T @ V) * (H.T @ H))
+    for _ in range(n_iter):
+        Q = procrustes_q(Xc, cols, H, V, s, rank_rtol)
+        Y = form_y(Q, Xc)
+        m3 = np.sum(H * (Y @ V[cols]), axis=0)
+        s = m3 @ G3p
+    return s, procrustes_q(Xc, cols, H, V, s, rank_rtol)
+
+
 def assemble_u(Qs, H):
     """U_k = Q_k H (Algorithm 2, after the loop)."""
     return [Q @ H for Q in Qs]

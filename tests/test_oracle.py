@@ -308,3 +308,36 @@ def test_invariances_subject_and_column_permutation_and_scaling():
     res = P.parafac2_als(Xs, H0, V0, W0, n_iter=3)
     assert rel_fro(res["W"], 4.0 * base["W"]) < 1e-10
     assert abs(res["history"][-1]["fit"] - base["history"][-1]["fit"]) < 1e-10
+
+
+# ---------------------------------------------------------------- projection (serving)
+def test_projection_recovers_planted_weights():
+    """With the true (H, V) of noiseless planted data, projecting a subject from s = 1
+    converges to that subject's W row (the model is exact and unique, Section 3.1)."""
+    rng = np.random.default_rng(21)
+    K, J, R, I = 6, 9, 3, 7
+    Xs, Ht, Vt, Wt = planted_parafac2(rng, K, J, R, I)
+    X = slices_from_dense(Xs, J)
+    for k in range(K):
+        Xc, cols = P.subject_block(X, k)
+        s, Q = P.project_subject(Xc, cols, Ht, Vt, n_iter=200)
+        assert np.allclose(s, Wt[k], rtol=1e-6, atol=1e-8), (k, s, Wt[k])
+        assert np.allclose(Q @ Ht @ np.diag(s) @ Vt[cols].T, Xc, atol=1e-8)
+
+
+def test_projection_step_is_the_least_squares_row():
+    """One s-update equals argmin_s ||Y - H diag(s) V^T||_F on the explicit Khatri-Rao
+    (mode-3 solve of Algorithm 1 for a single subject)."""
+    rng = np.random.default_rng(22)
+    J, R = 8, 3
+    Xc = rng.random((6, J))
+    cols = np.arange(J)
+    H = rng.standard_normal((R, R))
+    V = rng.random((J, R))
+    s0 = rng.random(R) + 0.5
+    s1, _ = P.project_subject(Xc, cols, H, V, n_iter=1, s0=s0)
+    Q = P.procrustes_q(Xc, cols, H, V, s0)
+    Y = Q.T @ Xc                                            # R x J
+    KR = BF.khatri_rao(V, H)                                # row r + R j
+    ref, *_ = np.linalg.lstsq(KR, Y.T.reshape(-1), rcond=None)
+    assert rel_fro(s1, ref) < 1e-10

@@ -156,6 +156,43 @@ int p2_get_mttkrp(p2_ctx *ctx, int32_t mode, double *out);
  */
 int p2_get_procrustes(p2_ctx *ctx, int64_t k0, int64_t k1, float *T);
 
+/*
+ * Projection of new subjects onto the current model (serving).  For each new
+ * subject X (I x J), with the model's H and V fixed, alternate Algorithm 2's
+ * Q-step (Procrustes, Section 3.2) and Algorithm 1's W update restricted to
+ * that subject (mode-3 MTTKRP, Eq. mttkrp3_row_wise, times (V^TV * H^TH)^+),
+ * starting from s = 1, n_iter times.  Subjects are independent: a subject's
+ * result does not depend on the batch it is sent in.
+ *
+ * A projector owns device scratch for batches of at most max_subjects
+ * subjects, max_rows rows and max_nnz non-zeros, and its own stream (or the
+ * given one); several projectors run their batches concurrently.  The model
+ * context must stay loaded and its factors must not change while projectors
+ * use it (they read H, V and (V^TV * H^TH)^+ from it at each p2_project).
+ */
+typedef struct p2_projector p2_projector;
+int p2_projector_create(p2_ctx *model, int64_t max_subjects, int64_t max_rows, int64_t max_nnz,
+                        void *stream, p2_projector **out);
+int p2_projector_destroy(p2_projector *pj);
+
+/*
+ * Enqueue the projection of n_req subjects given like p2_load_slices (column
+ * ids in the model's original column order; location 0: host, validated on
+ * the host before anything is enqueued; 1: device, validated on the device,
+ * which costs one synchronisation).  Outputs (out_location 0: host, 1:
+ * device): S_out n_req x R FP32, the subjects' S_k diagonals; T_out
+ * (nullable) n_req x R x R FP32, the Procrustes transforms for the final s
+ * (Q = X V T^T, as p2_get_procrustes).  Returns after enqueueing: host
+ * outputs and host inputs must stay valid until p2_projector_sync; use
+ * pinned host memory for asynchronous copies.
+ */
+int p2_project(p2_projector *pj, int64_t n_req, const int64_t *subj_ptr, const int64_t *row_ptr,
+               const int32_t *col, const float *val, int32_t location, int32_t n_iter,
+               float *S_out, float *T_out, int32_t out_location);
+
+/* Wait until the projector's enqueued work has finished. */
+int p2_projector_sync(p2_projector *pj);
+
 /* Counters and the last iteration's phase timings.  Synchronises. */
 int p2_stats(p2_ctx *ctx, p2_stats_t *out);
 

@@ -26,6 +26,7 @@ _NAMES = {0: "P2_OK", 1: "P2_EINVAL", 2: "P2_ENOMEM", 3: "P2_ECUDA", 4: "P2_ENUM
 EXPORTED = ("p2_default_options", "p2_create", "p2_destroy", "p2_load_slices", "p2_init",
             "p2_iterate", "p2_fit", "p2_get_factors", "p2_set_factors", "p2_get_mttkrp",
             "p2_get_procrustes", "p2_stats", "p2_device_bytes", "p2_mode1_stats_noalloc",
+            "p2_projector_create", "p2_projector_destroy", "p2_project", "p2_projector_sync",
             "p2_last_error")
 
 
@@ -72,6 +73,10 @@ def _load():
         "p2_stats": ([vp, ctypes.POINTER(p2_stats_t)], ctypes.c_int),
         "p2_device_bytes": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
         "p2_mode1_stats_noalloc": ([i64, i32, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "p2_projector_create": ([vp, i64, i64, i64, vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "p2_projector_destroy": ([vp], ctypes.c_int),
+        "p2_project": ([vp, i64, vp, vp, vp, vp, i32, i32, vp, vp, i32], ctypes.c_int),
+        "p2_projector_sync": ([vp], ctypes.c_int),
         "p2_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -205,6 +210,54 @@ def p2_mode1_stats_noalloc(K, R, T, G, W, M1, WtW=None, stream=None):
     _check(lib.p2_mode1_stats_noalloc(int(K), int(R), _ptr(T), _ptr(G), _ptr(W), _ptr(M1),
                                       _ptr(WtW), ctypes.c_void_p(stream)),
            "p2_mode1_stats_noalloc")
+
+
+class Projector:
+    """Projects new subjects onto a fitted model (fixed H, V): see p2_project."""
+
+    def __init__(self, model: "Parafac2", max_subjects: int, max_rows: int, max_nnz: int,
+                 stream=None):
+        self.model = model
+        self.R = model.R
+        h = ctypes.c_void_p()
+        _check(lib.p2_projector_create(model.ctx, int(max_subjects), int(max_rows),
+                                       int(max_nnz), stream, ctypes.byref(h)),
+               "p2_projector_create")
+        self.h = h
+        self.capacity = (int(max_subjects), int(max_rows), int(max_nnz))
+
+    def close(self):
+        if self.h is not None:
+            _check(lib.p2_projector_destroy(self.h), "p2_projector_destroy")
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, n_req, subj_ptr, row_ptr, col, val, n_iter, S_out, T_out=None,
+               location=0, out_location=0):
+        """Enqueue one batch; arrays must stay alive until sync()."""
+        _check(lib.p2_project(self.h, int(n_req), _ptr(subj_ptr), _ptr(row_ptr), _ptr(col),
+                              _ptr(val), int(location), int(n_iter), _ptr(S_out), _ptr(T_out),
+                              int(out_location)), "p2_project")
+
+    def sync(self):
+        _check(lib.p2_projector_sync(self.h), "p2_projector_sync")
+
+    def project(self, slices, n_iter=10, want_T=False):
+        """Synchronous convenience call on host arrays: returns S (and T)."""
+        sp = np.ascontiguousarray(slices.subj_ptr, np.int64)
+        rp = np.ascontiguousarray(slices.row_ptr, np.int64)
+        col = np.ascontiguousarray(slices.col, np.int32)
+        val = np.ascontiguousarray(slices.val, np.float32)
+        S = np.empty((slices.K, self.R), np.float32)
+        T = np.empty((slices.K, self.R, self.R), np.float32) if want_T else None
+        self.submit(slices.K, sp, rp, col, val, n_iter, S, T)
+        self.sync()
+        return (S, T) if want_T else S
 
 
 class Parafac2:

@@ -76,6 +76,16 @@ struct DevX {
 
 #define P2_SEG 1024
 
+// Read-only view of slices in the internal format, passed to kernels by value.
+struct XView {
+    const int64_t *__restrict__ subj_row;
+    const int64_t *__restrict__ subj_nnz;
+    const uint16_t *__restrict__ row_len;
+    const uint16_t *__restrict__ col;
+    const float *__restrict__ val;
+    int64_t K;
+};
+
 // Launch geometry decided once per context.
 struct Geometry {
     int nsm = 0;
@@ -150,5 +160,10 @@ int configure_kernels(p2_ctx *c);    // smem attributes etc.
 // Procrustes step (p2_polar.cu)
 int polar_configure(p2_ctx *c);
 cudaError_t launch_polar(p2_ctx *c);
+cudaError_t launch_polar_on(const p2_ctx *c, const double *G, const float *W, SmallState *st,
+                            float *T, int64_t K, cudaStream_t s);
+// Gram of Z_k = X_k V for a batch of new subjects (p2_kernels.cu)
+cudaError_t launch_gram(const p2_ctx *c, const XView &X, const SmallState *st, double *G,
+                        cudaStream_t s);
 __host__ __device__ unsigned long long polar_fixed_flops(int R);
 }  // namespace p2

@@ -40,15 +40,6 @@ static __device__ __forceinline__ int warp_excl_scan(int v, int lane) {
     return x - v;
 }
 
-struct XView {
-    const int64_t *__restrict__ subj_row;
-    const int64_t *__restrict__ subj_nnz;
-    const uint16_t *__restrict__ row_len;
-    const uint16_t *__restrict__ col;
-    const float *__restrict__ val;
-    int64_t K;
-};
-
 static XView xview(const p2_ctx *c) {
     return XView{c->X.subj_row, c->X.subj_nnz, c->X.row_len, c->X.col, c->X.val, c->X.K};
 }
@@ -871,6 +862,29 @@ static void mark(p2_ctx *c, int i) {
         cudaEventRecordWithFlags(c->ev[i], c->stream, cudaEventRecordExternal);
     else
         cudaEventRecord(c->ev[i], c->stream);
+}
+
+// Gram G_k of Z_k = X_k V for an arbitrary batch X (projection of new
+// subjects onto the model's V).
+cudaError_t launch_gram(const p2_ctx *c, const XView &X, const SmallState *st, double *G,
+                        cudaStream_t s) {
+    const Launch L = plan(c);
+    dim3 grid(c->geo.nsm * L.alpha_blocks), block(L.alpha_warps * 32);
+    switch (comp_block(c->R)) {
+        case 8:
+            k_alpha<8, false><<<grid, block, L.alpha_smem, s>>>(X, nullptr, c->d_V, c->d_H, nullptr,
+                                                               st, G, nullptr, nullptr, c->R);
+            break;
+        case 16:
+            k_alpha<16, false><<<grid, block, L.alpha_smem, s>>>(X, nullptr, c->d_V, c->d_H, nullptr,
+                                                                st, G, nullptr, nullptr, c->R);
+            break;
+        default:
+            k_alpha<32, false><<<grid, block, L.alpha_smem, s>>>(X, nullptr, c->d_V, c->d_H, nullptr,
+                                                                st, G, nullptr, nullptr, c->R);
+            break;
+    }
+    return cudaGetLastError();
 }
 
 template <bool MODE3>

@@ -220,7 +220,8 @@ __global__ void __launch_bounds__(128) k_polar_smem(const double *__restrict__ G
 }
 
 template <int R>
-static int launch_reg(p2_ctx *c, cudaStream_t s, double rtol2) {
+static int launch_reg(const p2_ctx *c, const double *G, const float *W, SmallState *st, float *T,
+                      int64_t K, cudaStream_t s, double rtol2) {
     const int cap = c->geo.smem_optin;
     const size_t per = (size_t)(R * R + 2 * R) * 8;
     int nt = (int)((cap - (size_t)R * R * 8) / per);
@@ -228,9 +229,8 @@ static int launch_reg(p2_ctx *c, cudaStream_t s, double rtol2) {
     nt = (nt / 32) * 32;
     if (nt < 32) return -1;
     const size_t smem = (size_t)R * R * 8 + (size_t)nt * per;
-    const int64_t K = c->X.K;
     const int nblk = (int)((K + nt - 1) / nt);
-    k_polar_reg<R><<<nblk, nt, smem, s>>>(c->d_G, c->d_W, c->d_s, c->d_T, K, rtol2);
+    k_polar_reg<R><<<nblk, nt, smem, s>>>(G, W, st, T, K, rtol2);
     return 0;
 }
 
@@ -256,23 +256,23 @@ int polar_configure(p2_ctx *c) {
     return P2_OK;
 }
 
-// Enqueue the Procrustes kernel for all subjects; returns a cudaError_t.
-cudaError_t launch_polar(p2_ctx *c) {
-    cudaStream_t s = c->stream;
+// Enqueue the Procrustes kernel for K subjects (Gram G, weights W, state st
+// holding H64) writing T; returns a cudaError_t.
+cudaError_t launch_polar_on(const p2_ctx *c, const double *G, const float *W, SmallState *st,
+                            float *T, int64_t K, cudaStream_t s) {
     const int R = c->R;
-    const int64_t K = c->X.K;
     const double rtol2 = c->opt.rank_rtol * c->opt.rank_rtol;
     if (K <= 0) return cudaSuccess;
     int rc = -1;
     switch (R) {
-        case 2: rc = launch_reg<2>(c, s, rtol2); break;
-        case 3: rc = launch_reg<3>(c, s, rtol2); break;
-        case 4: rc = launch_reg<4>(c, s, rtol2); break;
-        case 5: rc = launch_reg<5>(c, s, rtol2); break;
-        case 6: rc = launch_reg<6>(c, s, rtol2); break;
-        case 8: rc = launch_reg<8>(c, s, rtol2); break;
-        case 10: rc = launch_reg<10>(c, s, rtol2); break;
-        case 12: rc = launch_reg<12>(c, s, rtol2); break;
+        case 2: rc = launch_reg<2>(c, G, W, st, T, K, s, rtol2); break;
+        case 3: rc = launch_reg<3>(c, G, W, st, T, K, s, rtol2); break;
+        case 4: rc = launch_reg<4>(c, G, W, st, T, K, s, rtol2); break;
+        case 5: rc = launch_reg<5>(c, G, W, st, T, K, s, rtol2); break;
+        case 6: rc = launch_reg<6>(c, G, W, st, T, K, s, rtol2); break;
+        case 8: rc = launch_reg<8>(c, G, W, st, T, K, s, rtol2); break;
+        case 10: rc = launch_reg<10>(c, G, W, st, T, K, s, rtol2); break;
+        case 12: rc = launch_reg<12>(c, G, W, st, T, K, s, rtol2); break;
         default: break;
     }
     if (rc != 0) {
@@ -284,9 +284,13 @@ cudaError_t launch_polar(p2_ctx *c) {
         if (nt < 1) nt = 1;
         const size_t smem = (size_t)R * R * 8 + (size_t)nt * per;
         const int nblk = (int)((K + nt - 1) / nt);
-        k_polar_smem<<<nblk, nt, smem, s>>>(c->d_G, c->d_W, c->d_s, c->d_T, K, R, rtol2);
+        k_polar_smem<<<nblk, nt, smem, s>>>(G, W, st, T, K, R, rtol2);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_polar(p2_ctx *c) {
+    return launch_polar_on(c, c->d_G, c->d_W, c->d_s, c->d_T, c->X.K, c->stream);
 }
 
 }  // namespace p2

@@ -233,7 +233,7 @@ int p2_create(p2_ctx **out, const p2_options *opt) {
     }
     int rc = dalloc(c, &c->d_s, 1);
     if (rc == P2_OK) rc = dalloc(c, &c->d_H, (size_t)c->R * c->R);
-    const size_t part_stride = (size_t)c->R * c->R + 2 * (size_t)c->R + 8;
+    const size_t part_stride = stats_part_stride(c->R);
     if (rc == P2_OK) rc = dalloc(c, &c->d_part, (size_t)c->geo.red_blocks * part_stride);
     if (rc == P2_OK) rc = dalloc(c, &c->d_part2, (size_t)c->geo.red_blocks * part_stride);
     if (rc == P2_OK) rc = configure_kernels(c);
@@ -255,7 +255,7 @@ int p2_destroy(p2_ctx *c) {
     free_data(c);
     dfree(c, &c->d_s, 1);
     dfree(c, &c->d_H, (size_t)c->R * c->R);
-    const size_t part_stride = (size_t)c->R * c->R + 2 * (size_t)c->R + 8;
+    const size_t part_stride = stats_part_stride(c->R);
     dfree(c, &c->d_part, (size_t)c->geo.red_blocks * part_stride);
     dfree(c, &c->d_part2, (size_t)c->geo.red_blocks * part_stride);
     for (int i = 0; i < 8; ++i)

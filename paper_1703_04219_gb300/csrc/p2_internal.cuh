@@ -146,7 +146,12 @@ static inline __host__ __device__ size_t stats_warp_bytes(int R) {
     return ((size_t)R * R * 16 + ((size_t)2 * R * R + R) * 4 + 15) & ~(size_t)15;
 }
 // per-subject statistics after the Q-step (p2_kernels.cu): block partials
-// [R*R M1][R*R WtW][R max|W|][1 <W,M3>] over fixed contiguous subject ranges
+// [R*R M1][R*R WtW][R max|W|][1 <W,M3>] over fixed contiguous subject ranges;
+// stats_part_stride(R) doubles per block (also the per-block size of the
+// other partial buffers, which need at most R*R)
+static inline __host__ __device__ size_t stats_part_stride(int R) {
+    return 2 * (size_t)R * R + R + 1;
+}
 __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__ T,
                                                        const double *__restrict__ G,
                                                        const float *__restrict__ W,
@@ -165,5 +170,8 @@ cudaError_t launch_polar_on(const p2_ctx *c, const double *G, const float *W, Sm
 // Gram of Z_k = X_k V for a batch of new subjects (p2_kernels.cu)
 cudaError_t launch_gram(const p2_ctx *c, const XView &X, const SmallState *st, double *G,
                         cudaStream_t s);
-__host__ __device__ unsigned long long polar_fixed_flops(int R);
+// R > 12: grouped Procrustes kernel (p2_polar_grp.cu)
+cudaError_t polar_grp_configure(int cap);
+cudaError_t launch_polar_grp(const p2_ctx *c, const double *G, const float *W, SmallState *st,
+                             float *T, int64_t K, cudaStream_t s, double rtol2);
 }  // namespace p2

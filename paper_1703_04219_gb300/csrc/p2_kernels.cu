@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__
     for (int t = 0; t < 2; ++t)
         if (lane + 32 * t < P2_RMAX) red_wmax[warp][lane + 32 * t] = wmx[t];
     __syncthreads();
-    const size_t stride = 2 * (size_t)R * R + R + 1;
+    const size_t stride = stats_part_stride(R);
     double *out = part + (size_t)blockIdx.x * stride;
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
         double m = 0.0, w2 = 0.0;
@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(256) k_solve_h(const double *__restrict__ part
     __shared__ double nrm[P2_RMAX];
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
         double s = 0.0;
-        for (int b = 0; b < nparts; ++b) s += part[(size_t)b * (2 * (size_t)R * R + R + 1) + e];
+        for (int b = 0; b < nparts; ++b) s += part[(size_t)b * stats_part_stride(R) + e];
         st->M1[e] = s;
         A[e] = st->WtW[e] * st->VtV[e];
     }
@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(256) k_fin_v(const double *__restrict__ part, 
 // (M1 stays in the partials; the H solve sums it.)
 __global__ void k_fin_w(const double *__restrict__ part, int nparts, SmallState *st, int R,
                         int with_fit) {
-    const size_t stride = 2 * (size_t)R * R + R + 1;
+    const size_t stride = stats_part_stride(R);
     __shared__ double red[256];
     double lsum = 0.0;
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {

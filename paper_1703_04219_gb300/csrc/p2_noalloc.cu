@@ -52,7 +52,7 @@ static int na_scratch(int dev, double **out) {
 // Sums the block partials in block order: M1 and W^TW (both R x R, FP64).
 __global__ void k_na_sum(const double *__restrict__ part, int nparts, int R, double *M1,
                          double *WtW) {
-    const size_t stride = 2 * (size_t)R * R + R + 1;
+    const size_t stride = stats_part_stride(R);
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
         double m = 0.0, w = 0.0;
         for (int b = 0; b < nparts; ++b) {

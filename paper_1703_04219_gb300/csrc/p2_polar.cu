@@ -16,40 +16,9 @@
 
 #include "p2_internal.cuh"
 #include "p2_eig.cuh"
+#include "p2_polar.cuh"
 
 namespace p2 {
-
-#define FULLMASK 0xffffffffu
-
-// FP64 flops per subject (fused multiply-add = 2; sqrt, rsqrt and division =
-// 1) of the operations below, except the data-dependent QR part, which adds
-// 11 per QR step and 27 + 6R per Givens rotation.
-__host__ __device__ unsigned long long polar_fixed_flops(int R) {
-    const unsigned long long r = (unsigned long long)R, P = r * (r + 1) / 2;
-    unsigned long long f = 2 * P;                    // S G S
-    f += 2 * r * r * r + r * r * (r + 1);            // M = H (S G S) H^T, lower triangle
-    for (unsigned long long m = 2; m + 1 <= r; ++m) {
-        f += 4 * m * m + 8 * m + 9;                  // Householder step on an m-vector
-        f += m * (4 * m - 2);                        // its backward accumulation
-    }
-    f += 3 * r;                                      // QR scale estimate
-    f += 2 * r + 1;                                  // cut and d^-1/2
-    f += r + r * r;                                  // Z columns scaled by d^-1/4
-    f += r * r * (r + 1);                            // C = Z Z^T (lower)
-    f += 2 * r * r * r + r * r;                      // T = C H S
-    return f;
-}
-
-static __device__ __forceinline__ unsigned long long qr_flops(int R, int steps, int rot) {
-    return 11ull * (unsigned long long)(steps > 0 ? steps : 0) +
-           (27ull + 6ull * (unsigned long long)R) * (unsigned long long)rot;
-}
-
-static __device__ __forceinline__ void add_flops(SmallState *st, unsigned long long flops) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) flops += __shfl_down_sync(FULLMASK, flops, o);
-    if ((threadIdx.x & 31) == 0 && flops) atomicAdd(&st->polar_flops, flops);
-}
 
 template <int R>
 static __device__ __forceinline__ int pk(int i, int j) {   // packed lower index
@@ -249,6 +218,7 @@ int polar_configure(p2_ctx *c) {
     P2_ALLOW(k_polar_reg<10>);
     P2_ALLOW(k_polar_reg<12>);
 #undef P2_ALLOW
+    if (e == cudaSuccess) e = polar_grp_configure(cap);
     if (e != cudaSuccess) {
         set_error("configuring the Procrustes kernels: %s", cudaGetErrorString(e));
         return P2_ECUDA;
@@ -275,6 +245,7 @@ cudaError_t launch_polar_on(const p2_ctx *c, const double *G, const float *W, Sm
         case 12: rc = launch_reg<12>(c, G, W, st, T, K, s, rtol2); break;
         default: break;
     }
+    if (rc != 0 && R > 12) return launch_polar_grp(c, G, W, st, T, K, s, rtol2);
     if (rc != 0) {
         const int P = R * (R + 1) / 2;
         const size_t per = ((size_t)R * R + P + 3 * (size_t)R) * 8;

@@ -1,0 +1,59 @@
+// Launch of the grouped Procrustes kernel (R > 12), one instantiation per
+// register-array width RB = R rounded up to a multiple of eight.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "p2_internal.cuh"
+#include "p2_eig.cuh"
+#include "p2_polar.cuh"
+#include "p2_polar_grp.cuh"
+
+namespace p2 {
+
+template <int RB>
+static void launch_grp(const p2_ctx *c, const double *G, const float *W, SmallState *st, float *T,
+                       int64_t K, cudaStream_t s, double rtol2) {
+    const int R = c->R;
+    const size_t per = grp_doubles(R) * sizeof(double);
+    int spb = (int)((size_t)c->geo.smem_optin / per);
+    if (spb > 32) spb = 32;
+    if (spb >= 4) spb = (spb / 4) * 4;
+    if (spb < 1) spb = 1;
+    const int threads = ((spb + 3) / 4) * 32;
+    const size_t smem = (size_t)spb * per;
+    const int64_t nblk = (K + spb - 1) / spb;
+    k_polar_grp<RB><<<(unsigned)nblk, threads, smem, s>>>(G, W, st, T, K, R, rtol2, spb);
+}
+
+cudaError_t polar_grp_configure(int cap) {
+    cudaError_t e = cudaSuccess;
+#define P2_ALLOW(fn) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)
+    P2_ALLOW(k_polar_grp<16>);
+    P2_ALLOW(k_polar_grp<24>);
+    P2_ALLOW(k_polar_grp<32>);
+    P2_ALLOW(k_polar_grp<40>);
+    P2_ALLOW(k_polar_grp<48>);
+    P2_ALLOW(k_polar_grp<56>);
+    P2_ALLOW(k_polar_grp<64>);
+#undef P2_ALLOW
+    return e;
+}
+
+cudaError_t launch_polar_grp(const p2_ctx *c, const double *G, const float *W, SmallState *st,
+                             float *T, int64_t K, cudaStream_t s, double rtol2) {
+    switch ((c->R + PG - 1) / PG) {
+        case 1:
+        case 2: launch_grp<16>(c, G, W, st, T, K, s, rtol2); break;
+        case 3: launch_grp<24>(c, G, W, st, T, K, s, rtol2); break;
+        case 4: launch_grp<32>(c, G, W, st, T, K, s, rtol2); break;
+        case 5: launch_grp<40>(c, G, W, st, T, K, s, rtol2); break;
+        case 6: launch_grp<48>(c, G, W, st, T, K, s, rtol2); break;
+        case 7: launch_grp<56>(c, G, W, st, T, K, s, rtol2); break;
+        default: launch_grp<64>(c, G, W, st, T, K, s, rtol2); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace p2

@@ -1,0 +1,67 @@
+"""One case on the CPU-emulated library (run in a subprocess with the
+AddressSanitizer runtime preloaded).  Prints one JSON line of relative
+errors against the FP64 oracle."""
+import json
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import paper_1703_04219_gb300 as p2  # noqa: E402
+import synth  # noqa: E402
+from oracle import parafac2 as P  # noqa: E402
+from tests.helpers import rel_fro  # noqa: E402
+
+p2.LIB_PATH = os.path.join(HERE, "_build", "libp2emu.so")
+p2.lib = p2._load()
+
+
+def iterate_case(name, K, R):
+    X = synth.generate(name, K=K)
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=11)
+    with p2.Parafac2(R, use_graph=False) as m:
+        m.load(X)
+        m.init(H0, V0, W0)
+        fit = m.iterate(1)
+        H, V, W = m.factors()
+        M = {n: m.mttkrp(n) for n in (1, 2, 3)}
+    ref = P.als_iteration(P.all_blocks(X), H0.astype(np.float64), V0.astype(np.float64),
+                          W0.astype(np.float64))
+    err = {key: rel_fro(M[mode], ref[key]) for mode, key in ((1, "M1"), (2, "M2"), (3, "M3"))}
+    err.update({key: rel_fro(v, ref[key]) for key, v in (("H", H), ("V", V), ("W", W))})
+    err["fit"] = abs(fit - P.fit_from_loss(ref["loss"], P.norm_x_sq(P.all_blocks(X))))
+    return err
+
+
+def project_case(R, n_req):
+    from dataclasses import replace
+    X = synth.generate("c63m", K=30)
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=31)
+    with p2.Parafac2(R, use_graph=False) as m:
+        m.load(X)
+        m.init(H0, V0, W0)
+        m.iterate(1)
+        H, V, _ = m.factors()
+        w = synth.WORKLOADS["serve"]
+        req = synth.generate(replace(w, K=n_req, seed=w.seed))
+        with p2.Projector(m, 8, 4000, 40000) as pj:
+            S = pj.project(req, n_iter=2)
+    errs = []
+    for k in range(req.K):
+        Xc, cols = P.subject_block(req, k)
+        s, _ = P.project_subject(Xc, cols, H.astype(np.float64), V.astype(np.float64), 2)
+        errs.append(rel_fro(S[k], s))
+    return {"S_max": float(max(errs))}
+
+
+if __name__ == "__main__":
+    kind = sys.argv[1]
+    if kind == "iterate":
+        out = iterate_case(sys.argv[2], int(sys.argv[3]), int(sys.argv[4]))
+    else:
+        out = project_case(int(sys.argv[2]), int(sys.argv[3]))
+    print(json.dumps({k: float(v) for k, v in out.items()}), flush=True)

@@ -1,0 +1,75 @@
+"""The library's CUDA kernels run on the CPU emulator (tests/cpu_emu) under
+AddressSanitizer: one ALS iteration at R = 5 (lane-per-subject Procrustes)
+and R = 13 (grouped Procrustes kernel), and a projection of new subjects.
+Every device buffer and every block's shared memory is a heap block of its
+exact size, so an out-of-bounds access by any kernel aborts the run; the
+results must also match the FP64 oracle.  No GPU involved."""
+import json
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+EMU = os.path.join(HERE, "cpu_emu")
+
+CASES = {
+    "iterate_r5": ["iterate", "tiny", "24", "5"],
+    "iterate_r13": ["iterate", "tiny", "16", "13"],
+    "project_r12": ["project", "12", "3"],
+}
+
+
+def _asan_runtime():
+    if shutil.which("g++") is None:
+        return None
+    r = subprocess.run(["g++", "-print-file-name=libasan.so"], capture_output=True, text=True)
+    path = r.stdout.strip()
+    return path if os.path.isabs(path) and os.path.exists(path) else None
+
+
+@pytest.fixture(scope="module")
+def emulated_runs():
+    asan = _asan_runtime()
+    if asan is None:
+        pytest.skip("g++ with AddressSanitizer is not available")
+    sys.path.insert(0, EMU)
+    import build_emu
+    build_emu.build()
+    env = dict(os.environ, LD_PRELOAD=asan, EMU_NSM="1",
+               ASAN_OPTIONS="detect_leaks=0:abort_on_error=1")
+    procs = {name: subprocess.Popen([sys.executable, os.path.join(EMU, "run_case.py")] + args,
+                                    env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                    text=True)
+             for name, args in CASES.items()}
+    out = {}
+    for name, p in procs.items():
+        try:
+            so, se = p.communicate(timeout=900)
+        except subprocess.TimeoutExpired:
+            p.kill()
+            so, se = p.communicate()
+        out[name] = (p.returncode, so, se)
+    return out
+
+
+def _result(runs, name):
+    rc, so, se = runs[name]
+    assert rc == 0, f"{name} failed (rc {rc}):\n{se[-3000:]}"
+    assert "AddressSanitizer" not in se, se[-3000:]
+    return json.loads(so.strip().splitlines()[-1])
+
+
+@pytest.mark.parametrize("name", ["iterate_r5", "iterate_r13"])
+def test_emulated_iteration_is_in_bounds_and_matches_oracle(emulated_runs, name):
+    err = _result(emulated_runs, name)
+    for key in ("M1", "M2", "M3", "H", "V", "W"):
+        assert err[key] < 1e-5, (key, err[key])
+    assert err["fit"] < 1e-4
+
+
+def test_emulated_projection_is_in_bounds_and_matches_oracle(emulated_runs):
+    err = _result(emulated_runs, "project_r12")
+    assert err["S_max"] < 1e-4

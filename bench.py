@@ -57,7 +57,10 @@ def _workload_desc(w, X):
 
 
 def _bytes_model(X, R):
-    """Algorithmic HBM bytes per launch of each kernel group."""
+    """Algorithmic HBM bytes per launch of each kernel group: the streamed
+    format of X (u16 column + f32 value per non-zero, u16 row length, two
+    int64 offsets per subject) plus the per-subject state each pass must read
+    or write (T_k f32 R x R, packed Gram f64, W and M3 rows)."""
     K, N, nnz = X.K, X.n_rows, X.nnz
     P = R * (R + 1) // 2
     xb = 6 * nnz + 2 * N + 16 * (K + 1)          # u16 col + f32 val, u16 row length, 2 int64 offsets
@@ -322,6 +325,12 @@ def run_p2(args, w):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, X, H0, V0, W0)
     m.close()
+    bf16 = None
+    if not args.no_bf16:
+        bf16 = time_precision(X, R, H0, V0, W0, "bf16", args.steps, args.warmup, local)
+    serving = None
+    if rank == 0 and not args.no_serve:
+        serving = {"fp32": run_serving(precision="fp32"), "bf16": run_serving(precision="bf16")}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "s_per_iter": ms_step / 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -332,12 +341,76 @@ def run_p2(args, w):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "graph": True, "fit_after_steps": fit},
             "phase_ms": phase_ms, "sparse_passes": sparse, "roofline": roof,
-            "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+            "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+            "bf16_storage": bf16, "serving": serving}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def time_precision(X, R, H0, V0, W0, precision, steps, warmup, device):
+    """ms per iteration of the same workload with another storage precision
+    (graph replays, CUDA events on the launching stream, inputs > L2)."""
+    import torch
+    stream = torch.cuda.Stream()
+    m = __import__("paper_1703_04219_gb300").Parafac2(R, device=device, stream=stream.cuda_stream,
+                                                    precision=precision)
+    m.load(X)
+    m.init(H0, V0, W0)
+    for _ in range(warmup):
+        m.iterate(1, want_fit=False)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    m.iterate(steps, want_fit=False)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    fit, _ = m.fit()
+    m.close()
+    return {"ms_per_step": ms, "value": X.nnz / (ms / 1e3), "unit": UNIT,
+            "fit_after_steps": fit, "storage": "V and P_k bfloat16" if precision == "bf16"
+            else "float"}
+
+
+def run_serving(rate=50000.0, horizon_s=2.0, n_iter=5, n_slots=4, seed=5, precision="fp32"):
+    """Serving pattern: new subjects projected onto a fixed model (H 40x40,
+    V 5000x40) by the continuous-batching server; Poisson arrivals at `rate`
+    for `horizon_s` seconds.  The model comes from two ALS iterations on a
+    20,000-subject slice of the 250M-nnz generator (R = 40)."""
+    from dataclasses import replace
+    import synth
+    import paper_1703_04219_gb300 as p2
+    from paper_1703_04219_gb300.serve import Server, requests_from_slices
+    wt = synth.WORKLOADS["c250m"].scaled(20000)
+    Xt = synth.generate(wt)
+    R = wt.R
+    H0, V0, W0 = synth.init_factors(R, Xt.J, Xt.K, seed=wt.seed)
+    model = p2.Parafac2(R, precision=precision)
+    model.load(Xt)
+    model.init(H0, V0, W0)
+    model.iterate(2)
+    ws = synth.WORKLOADS["serve"]
+    n_req = int(rate * horizon_s)
+    req = synth.generate(replace(ws, K=n_req, seed=ws.seed))
+    reqs = requests_from_slices(req, rate_per_s=rate, seed=seed)
+    max_subjects = 4096
+    srv = Server(model, n_slots=n_slots, max_subjects=max_subjects, max_rows=max_subjects * 64,
+                 max_nnz=max_subjects * 256, n_iter=n_iter)
+    warm = requests_from_slices(req.take(list(range(min(512, n_req)))), rate_per_s=1e9, seed=seed)
+    srv.run(warm)                      # first launches, allocator
+    _, st = srv.run(reqs)
+    srv.close()
+    model.close()
+    st.update({"precision": precision, "rate_per_s": rate, "horizon_s": horizon_s,
+               "n_iter": n_iter, "slots": n_slots,
+               "R": R, "mean_rows": float(req.n_rows / req.K), "mean_nnz": float(req.nnz / req.K),
+               "admission_per_slot": {"subjects": max_subjects, "rows": max_subjects * 64,
+                                      "nnz": max_subjects * 256}})
+    return st
 
 
 def run_e2e(m, X, H0, V0, W0, steps, world, pg):
@@ -383,6 +456,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

@@ -43,13 +43,21 @@ enum {
     P2_ESTATE = 6      /* call out of order (e.g. p2_iterate before p2_init) */
 };
 
+/* Storage precision of V and of the in-flight mode-2 rows P_k = Q_k H S_k (a
+ * mixed-precision form of the iteration; the paper itself runs in FP64 on
+ * the CPU).  P2_FP32 stores them as float; P2_BF16 stores them as bfloat16
+ * (round to nearest even).  H (R x R) and the per-subject Procrustes state
+ * T_k stay float in both modes (Q_k = Z_k T_k^T is formed from T_k with a
+ * cancellation that amplifies its rounding by the condition number of A_k).
+ * All sparse products accumulate in FP32; the Gram, the Procrustes step, the
+ * solves and the fit are FP64-accurate. */
 enum { P2_FP32 = 0, P2_BF16 = 1 };
 
 typedef struct p2_ctx p2_ctx;
 
 typedef struct {
     int32_t R;            /* target rank, 1 <= R <= 64 */
-    int32_t precision;    /* P2_FP32 (P2_BF16 is reserved and rejected for now) */
+    int32_t precision;    /* P2_FP32 or P2_BF16 (storage of V and P_k; see above) */
     int32_t device;       /* CUDA device ordinal */
     int32_t use_graph;    /* non-zero: one iteration is captured in a CUDA graph and replayed */
     double rank_rtol;     /* Procrustes rank cut: singular values <= rank_rtol * sigma_1 of

@@ -264,14 +264,18 @@ class Parafac2:
     """Owning wrapper of one context: load, init, iterate, read back."""
 
     def __init__(self, R: int, device: int = 0, use_graph: bool = True, rank_rtol: float = 1e-5,
-                 stream=None, timing: bool = False):
+                 stream=None, timing: bool = False, precision: str = "fp32"):
+        if precision not in ("fp32", "bf16"):
+            raise ValueError("precision must be 'fp32' or 'bf16'")
         opt = p2_default_options(R)
+        opt.precision = P2_BF16 if precision == "bf16" else P2_FP32
         opt.device = device
         opt.use_graph = 1 if use_graph else 0
         opt.rank_rtol = rank_rtol
         opt.stream = stream
         opt.timing = 1 if timing else 0
         self.R = R
+        self.precision = precision
         self.ctx = p2_create(opt)
         self.K = self.J = 0
 

@@ -68,6 +68,9 @@ static void free_data(p2_ctx *c) {
     dfree(c, &c->d_colcount, J);
     dfree(c, &c->d_V, J * R);
     dfree(c, &c->d_Vprev, J * R);
+    dfree(c, &c->d_Vh, J * R);
+    dfree(c, &c->d_Vprevh, J * R);
+    dfree(c, &c->d_Ph, N * R);
     dfree(c, &c->d_Vun, J * R);
     dfree(c, &c->d_M2, J * R);
     dfree(c, &c->d_P, N * R);
@@ -106,14 +109,20 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
     P2_TRY(dalloc(c, &c->X.val, (size_t)nnz));
     P2_TRY(dalloc(c, &c->d_perm_old2new, (size_t)J));
     P2_TRY(dalloc(c, &c->d_colcount, (size_t)J));
-    P2_TRY(dalloc(c, &c->d_V, (size_t)J * R));
-    P2_TRY(dalloc(c, &c->d_Vprev, (size_t)J * R));
+    if (c->bf16) {
+        P2_TRY(dalloc(c, &c->d_Vh, (size_t)J * R));
+        P2_TRY(dalloc(c, &c->d_Vprevh, (size_t)J * R));
+        P2_TRY(dalloc(c, &c->d_Ph, (size_t)N * R));
+    } else {
+        P2_TRY(dalloc(c, &c->d_V, (size_t)J * R));
+        P2_TRY(dalloc(c, &c->d_Vprev, (size_t)J * R));
+        P2_TRY(dalloc(c, &c->d_P, (size_t)N * R));
+    }
+    P2_TRY(dalloc(c, &c->d_T, (size_t)K * R * R));
     P2_TRY(dalloc(c, &c->d_Vun, (size_t)J * R));
     P2_TRY(dalloc(c, &c->d_M2, (size_t)J * R));
-    P2_TRY(dalloc(c, &c->d_P, (size_t)N * R));
     P2_TRY(dalloc(c, &c->d_W, (size_t)K * R));
     P2_TRY(dalloc(c, &c->d_M3, (size_t)K * R));
-    P2_TRY(dalloc(c, &c->d_T, (size_t)K * R * R));
     P2_TRY(dalloc(c, &c->d_G, (size_t)K * P));
     P2_CUDA_TRY(cudaMemsetAsync(c->d_M3, 0, sizeof(float) * (size_t)K * R, c->stream));
     c->h_perm_new2old = new int32_t[J];
@@ -144,16 +153,39 @@ static int flags_status(int flags) {
     return P2_OK;
 }
 
+// float -> bfloat16 bits, round to nearest even (NaN kept quiet)
+static uint16_t to_bf16_bits(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40u);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+static float from_bf16_bits(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
 static int set_factors_impl(p2_ctx *c, const float *H, const float *V, const float *W) {
     const int R = c->R;
     const int32_t J = c->X.J;
     const int64_t K = c->X.K;
     std::vector<float> Vp((size_t)J * R);
+    std::vector<uint16_t> Vb;
     for (int32_t j = 0; j < J; ++j)
         memcpy(&Vp[(size_t)c->h_perm_old2new[j] * R], V + (size_t)j * R, sizeof(float) * R);
+    if (c->bf16) {                          // V stored bfloat16
+        Vb.resize(Vp.size());
+        for (size_t i = 0; i < Vp.size(); ++i) Vb[i] = to_bf16_bits(Vp[i]);
+        P2_CUDA_TRY(cudaMemcpyAsync(c->d_Vh, Vb.data(), sizeof(uint16_t) * Vb.size(),
+                                    cudaMemcpyHostToDevice, c->stream));
+    } else {
+        P2_CUDA_TRY(cudaMemcpyAsync(c->d_V, Vp.data(), sizeof(float) * (size_t)J * R,
+                                    cudaMemcpyHostToDevice, c->stream));
+    }
     P2_CUDA_TRY(cudaMemcpyAsync(c->d_H, H, sizeof(float) * R * R, cudaMemcpyHostToDevice, c->stream));
-    P2_CUDA_TRY(cudaMemcpyAsync(c->d_V, Vp.data(), sizeof(float) * (size_t)J * R,
-                                cudaMemcpyHostToDevice, c->stream));
     P2_CUDA_TRY(cudaMemcpyAsync(c->d_W, W, sizeof(float) * (size_t)K * R, cudaMemcpyHostToDevice,
                                 c->stream));
     int zero = 0;
@@ -161,7 +193,7 @@ static int set_factors_impl(p2_ctx *c, const float *H, const float *V, const flo
     P2_TRY(enqueue_factor_stats(c));
     P2_TRY(enqueue_prologue(c));
     int flags = 0;
-    P2_TRY(read_flags(c, &flags));   // also keeps Vp alive until the copy finished
+    P2_TRY(read_flags(c, &flags));   // also keeps Vp and Vb alive until the copies finished
     c->inited = true;
     c->iters_done = 0;
     return P2_OK;
@@ -189,8 +221,8 @@ int p2_create(p2_ctx **out, const p2_options *opt) {
     if (!out || !opt) return fail(P2_EINVAL, "p2_create: NULL argument");
     *out = nullptr;
     if (opt->R < 1 || opt->R > P2_RMAX) return fail(P2_EINVAL, "p2_create: R must be in [1, 64]");
-    if (opt->precision != P2_FP32)
-        return fail(P2_EINVAL, "p2_create: only P2_FP32 storage is implemented");
+    if (opt->precision != P2_FP32 && opt->precision != P2_BF16)
+        return fail(P2_EINVAL, "p2_create: precision must be P2_FP32 or P2_BF16");
     int ndev = 0;
     P2_CUDA_TRY(cudaGetDeviceCount(&ndev));
     if (opt->device < 0 || opt->device >= ndev) return fail(P2_EINVAL, "p2_create: bad device");
@@ -200,6 +232,7 @@ int p2_create(p2_ctx **out, const p2_options *opt) {
     if (!(c->opt.rank_rtol > 0.0)) c->opt.rank_rtol = 1e-5;
     c->R = opt->R;
     c->P = opt->R * (opt->R + 1) / 2;
+    c->bf16 = opt->precision == P2_BF16;
     cudaDeviceProp prop;
     cudaError_t e = cudaGetDeviceProperties(&prop, opt->device);
     if (e != cudaSuccess) {
@@ -415,7 +448,14 @@ int p2_get_factors(p2_ctx *c, float *H, float *V, float *W) {
     if (H) P2_CUDA_TRY(cudaMemcpy(H, c->d_H, sizeof(float) * R * R, cudaMemcpyDeviceToHost));
     if (V) {
         std::vector<float> Vp((size_t)c->X.J * R);
-        P2_CUDA_TRY(cudaMemcpy(Vp.data(), c->d_V, sizeof(float) * Vp.size(), cudaMemcpyDeviceToHost));
+        if (c->bf16) {
+            std::vector<uint16_t> Vb(Vp.size());
+            P2_CUDA_TRY(cudaMemcpy(Vb.data(), c->d_Vh, sizeof(uint16_t) * Vb.size(),
+                                   cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < Vb.size(); ++i) Vp[i] = from_bf16_bits(Vb[i]);
+        } else {
+            P2_CUDA_TRY(cudaMemcpy(Vp.data(), c->d_V, sizeof(float) * Vp.size(), cudaMemcpyDeviceToHost));
+        }
         for (int32_t j = 0; j < c->X.J; ++j)
             memcpy(V + (size_t)j * R, &Vp[(size_t)c->h_perm_old2new[j] * R], sizeof(float) * R);
     }

@@ -22,6 +22,8 @@
 #endif
 
 #include <math.h>
+#include <stdint.h>
+#include <string.h>
 
 namespace p2 {
 
@@ -137,6 +139,29 @@ P2_HD void tridiagonalize(int n_rt, MatView A, VecView d, VecView e) {
     }
 }
 
+// Binary exponent field of |v| (0 for zero and subnormals).
+P2_HD int p2_expo(double v) {
+#ifdef __CUDA_ARCH__
+    return (__double2hiint(v) >> 20) & 0x7ff;
+#else
+    uint64_t b;
+    memcpy(&b, &v, sizeof b);
+    return (int)((b >> 52) & 0x7ff);
+#endif
+}
+
+// Deflation test of a sub-diagonal entry ev of the tridiagonal, in integer
+// arithmetic on binary exponents: negligible when expo(ev) <= expo(max(|d1|,
+// |d2|)) - 52 or expo(ev) <= tiny_ex = expo(eps ||T||).  Either condition
+// implies |ev| < 2 eps (|d1| + |d2|) or |ev| < 2 eps ||T||, i.e. a backward
+// error of the order of the rounding already committed, and the test costs
+// no FP64 instruction.
+P2_HD bool p2_negligible(double ev, double d1, double d2, int tiny_ex) {
+    const int x = p2_expo(ev);
+    const int a = p2_expo(d1), b = p2_expo(d2);
+    return x == 0 || x <= (a > b ? a : b) - 52 || x <= tiny_ex;
+}
+
 // Implicit symmetric QR with Wilkinson shift on the tridiagonal (d, e);
 // rotations are accumulated into the columns of Z (n x n).  Returns the
 // number of QR steps taken, or -1 if max_steps was exceeded (d then holds
@@ -154,20 +179,19 @@ P2_HD int tridiagonal_qr(int n_rt, MatView Z, VecView d, VecView e, int max_step
         double r = fabs(d[i]) + ((i + 1 < n) ? fabs(e[i]) : 0.0) + ((i > 0) ? fabs(e[i - 1]) : 0.0);
         anorm = fmax(anorm, r);
     }
-    const double tiny = eps * anorm;
+    const int tiny_ex = p2_expo(eps * anorm);
     int steps = 0;
     int q = n - 1;
     while (q > 0) {
         double eq = e[q - 1];
-        if (fabs(eq) <= eps * (fabs(d[q - 1]) + fabs(d[q])) || fabs(eq) <= tiny) {
+        if (p2_negligible(eq, d[q - 1], d[q], tiny_ex)) {
             e[q - 1] = 0.0;
             --q;
             continue;
         }
         int p = q - 1;
         while (p > 0) {
-            double ep = e[p - 1];
-            if (fabs(ep) <= eps * (fabs(d[p - 1]) + fabs(d[p])) || fabs(ep) <= tiny) {
+            if (p2_negligible(e[p - 1], d[p - 1], d[p], tiny_ex)) {
                 e[p - 1] = 0.0;
                 break;
             }

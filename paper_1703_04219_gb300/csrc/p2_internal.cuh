@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libp2.so.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
@@ -55,6 +56,21 @@ struct SmallState {
     unsigned long long polar_flops;     // FP64 flops executed by k_polar (running total)
     int flags;
     int iter;
+};
+
+// Storage type of V and of the mode-2 rows P: float (P2_FP32) or bfloat16
+// (P2_BF16, round to nearest even); arithmetic is FP32 in both cases.
+typedef __nv_bfloat16 bf16_t;
+template <class S> struct Stor;
+template <> struct Stor<float> {
+    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float ldp(const float *p) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <> struct Stor<bf16_t> {
+    static __device__ __forceinline__ float ld(const bf16_t *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float ldp(const bf16_t *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(bf16_t *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
 // Device-resident sparse slices in the internal format.
@@ -115,9 +131,16 @@ struct p2_ctx {
     int32_t *h_perm_old2new = nullptr;   // host [J]
 
     // factors and per-subject state
+    // Storage of V, Vprev and P follows opt.precision: the float pointers are
+    // used with P2_FP32, the *h (bfloat16) ones with P2_BF16; the others stay
+    // null.  H (R x R) and T_k are float in both modes: H is too small for its
+    // storage to matter, and Q_k = Z_k T_k^T is formed from T_k with a
+    // cancellation that amplifies its rounding by cond(A_k).
+    bool bf16 = false;
     float *d_H = nullptr;       // R x R
     float *d_V = nullptr;       // J x R (relabelled rows)
     float *d_Vprev = nullptr;   // J x R
+    p2::bf16_t *d_Vh = nullptr, *d_Vprevh = nullptr, *d_Ph = nullptr;
     float *d_W = nullptr;       // K x R
     float *d_T = nullptr;       // K x R x R
     double *d_G = nullptr;      // K x P (packed lower Gram of Z_k)

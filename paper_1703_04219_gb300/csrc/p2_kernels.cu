@@ -49,10 +49,10 @@ static XView xview(const p2_ctx *c) {
 // round of dependent loads; the row's components are accumulated in
 // registers in blocks of CB (FP32 FMA in column order within the row) and
 // stored with the odd row stride RS (no shared-memory bank conflicts).
-template <int CB, bool TWO>
+template <int CB, bool TWO, class S>
 static __device__ __forceinline__ void gather_rows(const XView &X, int nr, int64_t base, int len,
-                                                   int off, const float *__restrict__ V1,
-                                                   const float *__restrict__ V2, float *z1,
+                                                   int off, const S *__restrict__ V1,
+                                                   const S *__restrict__ V2, float *z1,
                                                    float *z2, int R, int RS, int lane) {
     if (lane >= nr) return;
     const int64_t b0 = base + off;
@@ -66,13 +66,13 @@ static __device__ __forceinline__ void gather_rows(const XView &X, int nr, int64
         for (int e = 0; e < len; ++e) {
             const int j = X.col[b0 + e];
             const float x = X.val[b0 + e];
-            const float *v1 = V1 + (size_t)j * R + cb;
-            const float *v2 = TWO ? (V2 + (size_t)j * R + cb) : nullptr;
+            const S *v1 = V1 + (size_t)j * R + cb;
+            const S *v2 = TWO ? (V2 + (size_t)j * R + cb) : nullptr;
 #pragma unroll
             for (int c = 0; c < CB; ++c) {
                 if (cb + c < R) {
-                    a1[c] = fmaf(x, __ldg(v1 + c), a1[c]);
-                    if (TWO) a2[c] = fmaf(x, __ldg(v2 + c), a2[c]);
+                    a1[c] = fmaf(x, Stor<S>::ld(v1 + c), a1[c]);
+                    if (TWO) a2[c] = fmaf(x, Stor<S>::ld(v2 + c), a2[c]);
                 }
             }
         }
@@ -96,9 +96,9 @@ static __host__ __device__ __forceinline__ int row_stride(int R) { return R | 1;
 // and, with MODE3, the mode-3 MTTKRP row M3(k,:) = coldot(H, T_k Z_k^T Z'_k)
 // with Z_k = X_k Vprev, followed by W(k,:) = M3(k,:) (V^TV * H^TH)^+.
 // ---------------------------------------------------------------------------
-template <int CB, bool MODE3>
-__global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_alpha(XView X, const float *__restrict__ Vprev,
-                                               const float *__restrict__ V,
+template <int CB, bool MODE3, class S>
+__global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_alpha(XView X, const S *__restrict__ Vprev,
+                                               const S *__restrict__ V,
                                                const float *__restrict__ H,
                                                const float *__restrict__ T,
                                                const SmallState *__restrict__ st, double *G,
@@ -151,9 +151,10 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_alpha(XView X, const f
             const int off = warp_excl_scan(len, lane);
             const int tot = __shfl_sync(FULLMASK, off + len, 31);
             if (MODE3)
-                gather_rows<CB, true>(X, nr, base, len, off, Vprev, V, zo, zn, R, RS, lane);
+                gather_rows<CB, true, S>(X, nr, base, len, off, Vprev, V, zo, zn, R, RS, lane);
             else
-                gather_rows<CB, false>(X, nr, base, len, off, V, nullptr, zn, nullptr, R, RS, lane);
+                gather_rows<CB, false, S>(X, nr, base, len, off, V, nullptr, zn, nullptr, R, RS,
+                                          lane);
             __syncwarp();
             if (MODE3) {
                 for (int e = lane; e < R * R; e += 32) {
@@ -222,11 +223,11 @@ static __host__ __device__ size_t beta_warp_bytes(int R) {
     return ((size_t)32 * row_stride(R) + 2 * (size_t)R * R + R) * 4;
 }
 
-template <int CB>
-__global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_beta_p(XView X, const float *__restrict__ V,
+template <int CB, class S>
+__global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_beta_p(XView X, const S *__restrict__ V,
                                                 const float *__restrict__ H,
                                                 const float *__restrict__ T,
-                                                const float *__restrict__ W, float *Pout, int R) {
+                                                const float *__restrict__ W, S *Pout, int R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RS = row_stride(R);
     float *Hs = reinterpret_cast<float *>(smem_raw);
@@ -259,14 +260,14 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_beta_p(XView X, const 
             const int len = (lane < nr) ? (int)X.row_len[cr + lane] : 0;
             const int off = warp_excl_scan(len, lane);
             const int tot = __shfl_sync(FULLMASK, off + len, 31);
-            gather_rows<CB, false>(X, nr, base, len, off, V, nullptr, zo, nullptr, R, RS, lane);
+            gather_rows<CB, false, S>(X, nr, base, len, off, V, nullptr, zo, nullptr, R, RS, lane);
             __syncwarp();
-            float *Pr = Pout + (size_t)cr * R;
+            S *Pr = Pout + (size_t)cr * R;
             for (int e = lane; e < nr * R; e += 32) {
                 const int i = e / R, s = e - i * R;
                 float p = 0.f;
                 for (int u = 0; u < R; ++u) p = fmaf(zo[i * RS + u], Fk[u * R + s], p);
-                Pr[e] = p;
+                Stor<S>::st(Pr + e, p);
             }
             __syncwarp();
             base += tot;
@@ -282,11 +283,11 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_beta_p(XView X, const 
 // the lanes are combined by a fixed xor-butterfly in FP64.  No atomics:
 // deterministic.
 // ---------------------------------------------------------------------------
-template <int CB>
+template <int CB, class S>
 __global__ void __launch_bounds__(256) k_m2_segments(const uint32_t *__restrict__ csc_row,
                                                      const float *__restrict__ csc_val,
                                                      const int64_t *__restrict__ seg_start,
-                                                     int64_t nseg, const float *__restrict__ Pin,
+                                                     int64_t nseg, const S *__restrict__ Pin,
                                                      double *segpart, int R) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -302,11 +303,11 @@ __global__ void __launch_bounds__(256) k_m2_segments(const uint32_t *__restrict_
             for (int64_t e = a + lane; e < b; e += 32) {
                 const uint32_t row = csc_row[e];
                 const float x = csc_val[e];
-                const float *pr = Pin + (size_t)row * R + cb;
+                const S *pr = Pin + (size_t)row * R + cb;
 #pragma unroll
                 for (int c = 0; c < CB; ++c) {
                     if (cb + c < R) {
-                        const float y = x * __ldg(pr + c) - cp[c];
+                        const float y = x * Stor<S>::ld(pr + c) - cp[c];
                         const float tt = hi[c] + y;
                         cp[c] = (tt - hi[c]) - y;
                         hi[c] = tt;
@@ -354,10 +355,10 @@ __global__ void k_m2_columns(const double *__restrict__ segpart, const int64_t *
 // layout [R*R M1][R*R WtW][R wmax][1 wm3], summed later in block order.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__ T,
-                                                       const double *__restrict__ G,
-                                                       const float *__restrict__ W,
-                                                       const float *__restrict__ M3, double *part,
-                                                       int64_t K, int R, int with_m3) {
+                                                     const double *__restrict__ G,
+                                                     const float *__restrict__ W,
+                                                     const float *__restrict__ M3, double *part,
+                                                     int64_t K, int R, int with_m3) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_wm3[8];
     __shared__ float red_wmax[8][P2_RMAX];
@@ -452,8 +453,10 @@ __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__
     }
 }
 
+
 // Partials of V^T V (V stored FP32, products exact in FP64) over row ranges.
-__global__ void __launch_bounds__(256) k_gram_v(const float *__restrict__ V, double *part,
+template <class S>
+__global__ void __launch_bounds__(256) k_gram_v(const S *__restrict__ V, double *part,
                                                 int64_t J, int R) {
     const int64_t per = (J + gridDim.x - 1) / gridDim.x;
     const int64_t j0 = (int64_t)blockIdx.x * per;
@@ -462,13 +465,13 @@ __global__ void __launch_bounds__(256) k_gram_v(const float *__restrict__ V, dou
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] = 0.0;
     for (int64_t j = j0; j < j1; ++j) {
-        const float *vj = V + (size_t)j * R;
+        const S *vj = V + (size_t)j * R;
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int e = threadIdx.x + q * blockDim.x;
             if (e < R * R) {
                 const int r = e / R, s = e - r * R;
-                acc[q] = fma((double)vj[r], (double)vj[s], acc[q]);
+                acc[q] = fma((double)Stor<S>::ldp(vj + r), (double)Stor<S>::ldp(vj + s), acc[q]);
             }
         }
     }
@@ -692,14 +695,15 @@ __global__ void k_solve_v_norm(const double *__restrict__ part, int nparts, Smal
 }
 
 // V solve, part d: Vprev <- V; V <- Vun / colnorm (FP32).
-__global__ void k_solve_v_store(const double *__restrict__ Vun, const SmallState *st, float *V,
-                                float *Vprev, int64_t n, int R) {
+template <class S>
+__global__ void k_solve_v_store(const double *__restrict__ Vun, const SmallState *st, S *V,
+                                S *Vprev, int64_t n, int R) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int s = (int)(e % R);
         const double nr = st->colnorm[s];
         Vprev[e] = V[e];
-        V[e] = nr > 0.0 ? (float)(Vun[e] / nr) : 0.f;
+        Stor<S>::st(V + e, nr > 0.0 ? (float)(Vun[e] / nr) : 0.f);
     }
 }
 
@@ -769,6 +773,19 @@ static size_t alpha_warp_bytes(int R) {
 // register block of components in the sparse passes: 8, 16 or 32
 static int comp_block(int R) { return R <= 8 ? 8 : (R <= 16 ? 16 : 32); }
 
+// V, Vprev, T and P of the context in storage type S
+template <class S> struct Bufs;
+template <> struct Bufs<float> {
+    static float *V(const p2_ctx *c) { return c->d_V; }
+    static float *Vprev(const p2_ctx *c) { return c->d_Vprev; }
+    static float *P(const p2_ctx *c) { return c->d_P; }
+};
+template <> struct Bufs<bf16_t> {
+    static bf16_t *V(const p2_ctx *c) { return c->d_Vh; }
+    static bf16_t *Vprev(const p2_ctx *c) { return c->d_Vprevh; }
+    static bf16_t *P(const p2_ctx *c) { return c->d_Ph; }
+};
+
 struct Launch {
     int alpha_warps, beta_warps, alpha_blocks, beta_blocks;
     size_t alpha_smem, beta_smem;
@@ -816,18 +833,26 @@ static int allow_dynamic_smem(F *fn, int cap, const char *name) {
     return P2_OK;
 }
 
+template <class S>
+static int configure_sparse(int cap) {
+    int rc = P2_OK;
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<8, true, S>, cap, "k_alpha");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<8, false, S>, cap, "k_alpha");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<16, true, S>, cap, "k_alpha");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<16, false, S>, cap, "k_alpha");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<32, true, S>, cap, "k_alpha");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<32, false, S>, cap, "k_alpha");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<8, S>, cap, "k_beta_p");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<16, S>, cap, "k_beta_p");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<32, S>, cap, "k_beta_p");
+    return rc;
+}
+
 int configure_kernels(p2_ctx *c) {
     const int cap = c->geo.smem_optin;
     int rc = P2_OK;
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<8, true>, cap, "k_alpha");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<8, false>, cap, "k_alpha");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<16, true>, cap, "k_alpha");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<16, false>, cap, "k_alpha");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<32, true>, cap, "k_alpha");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<32, false>, cap, "k_alpha");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<8>, cap, "k_beta_p");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<16>, cap, "k_beta_p");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<32>, cap, "k_beta_p");
+    if (rc == P2_OK) rc = configure_sparse<float>(cap);
+    if (rc == P2_OK) rc = configure_sparse<bf16_t>(cap);
     if (rc == P2_OK) rc = polar_configure(c);
     if (rc == P2_OK) rc = allow_dynamic_smem(k_solve_h, cap, "k_solve_h");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_solve_v_pinv, cap, "k_solve_v_pinv");
@@ -866,80 +891,124 @@ static void mark(p2_ctx *c, int i) {
 
 // Gram G_k of Z_k = X_k V for an arbitrary batch X (projection of new
 // subjects onto the model's V).
-cudaError_t launch_gram(const p2_ctx *c, const XView &X, const SmallState *st, double *G,
-                        cudaStream_t s) {
+template <class S>
+static void launch_gram_t(const p2_ctx *c, const XView &X, const SmallState *st, double *G,
+                          cudaStream_t s) {
     const Launch L = plan(c);
     dim3 grid(c->geo.nsm * L.alpha_blocks), block(L.alpha_warps * 32);
+    const S *V = Bufs<S>::V(c);
     switch (comp_block(c->R)) {
         case 8:
-            k_alpha<8, false><<<grid, block, L.alpha_smem, s>>>(X, nullptr, c->d_V, c->d_H, nullptr,
-                                                               st, G, nullptr, nullptr, c->R);
+            k_alpha<8, false, S><<<grid, block, L.alpha_smem, s>>>(X, nullptr, V, c->d_H, nullptr,
+                                                                  st, G, nullptr, nullptr, c->R);
             break;
         case 16:
-            k_alpha<16, false><<<grid, block, L.alpha_smem, s>>>(X, nullptr, c->d_V, c->d_H, nullptr,
-                                                                st, G, nullptr, nullptr, c->R);
+            k_alpha<16, false, S><<<grid, block, L.alpha_smem, s>>>(X, nullptr, V, c->d_H, nullptr,
+                                                                   st, G, nullptr, nullptr, c->R);
             break;
         default:
-            k_alpha<32, false><<<grid, block, L.alpha_smem, s>>>(X, nullptr, c->d_V, c->d_H, nullptr,
-                                                                st, G, nullptr, nullptr, c->R);
+            k_alpha<32, false, S><<<grid, block, L.alpha_smem, s>>>(X, nullptr, V, c->d_H, nullptr,
+                                                                   st, G, nullptr, nullptr, c->R);
             break;
     }
+}
+
+// Gram G_k of Z_k = X_k V for an arbitrary batch X (projection of new
+// subjects onto the model's V).
+cudaError_t launch_gram(const p2_ctx *c, const XView &X, const SmallState *st, double *G,
+                        cudaStream_t s) {
+    if (c->bf16)
+        launch_gram_t<bf16_t>(c, X, st, G, s);
+    else
+        launch_gram_t<float>(c, X, st, G, s);
     return cudaGetLastError();
 }
 
-template <bool MODE3>
-static void launch_alpha(p2_ctx *c, const Launch &L, const float *Vprev) {
+template <bool MODE3, class S>
+static void launch_alpha_t(p2_ctx *c, const Launch &L, const S *Vprev) {
     dim3 grid(c->geo.nsm * L.alpha_blocks), block(L.alpha_warps * 32);
     XView X = xview(c);
+    const S *V = Bufs<S>::V(c);
+    const float *T = c->d_T;
     switch (comp_block(c->R)) {
         case 8:
-            k_alpha<8, MODE3><<<grid, block, L.alpha_smem, c->stream>>>(
-                X, Vprev, c->d_V, c->d_H, c->d_T, c->d_s, c->d_G, c->d_W, c->d_M3, c->R);
+            k_alpha<8, MODE3, S><<<grid, block, L.alpha_smem, c->stream>>>(
+                X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_W, c->d_M3, c->R);
             break;
         case 16:
-            k_alpha<16, MODE3><<<grid, block, L.alpha_smem, c->stream>>>(
-                X, Vprev, c->d_V, c->d_H, c->d_T, c->d_s, c->d_G, c->d_W, c->d_M3, c->R);
+            k_alpha<16, MODE3, S><<<grid, block, L.alpha_smem, c->stream>>>(
+                X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_W, c->d_M3, c->R);
             break;
         default:
-            k_alpha<32, MODE3><<<grid, block, L.alpha_smem, c->stream>>>(
-                X, Vprev, c->d_V, c->d_H, c->d_T, c->d_s, c->d_G, c->d_W, c->d_M3, c->R);
+            k_alpha<32, MODE3, S><<<grid, block, L.alpha_smem, c->stream>>>(
+                X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_W, c->d_M3, c->R);
+            break;
+    }
+}
+
+// pass alpha: with MODE3 Z_k from Vprev and Z'_k from V (the iteration), else
+// the Gram of Z_k = X_k V only (prologue)
+template <bool MODE3>
+static void launch_alpha(p2_ctx *c, const Launch &L) {
+    if (c->bf16)
+        launch_alpha_t<MODE3, bf16_t>(c, L, MODE3 ? c->d_Vprevh : nullptr);
+    else
+        launch_alpha_t<MODE3, float>(c, L, MODE3 ? c->d_Vprev : nullptr);
+}
+
+template <class S>
+static void launch_beta_p_t(p2_ctx *c, const Launch &L) {
+    dim3 grid(c->geo.nsm * L.beta_blocks), block(L.beta_warps * 32);
+    XView X = xview(c);
+    const S *V = Bufs<S>::V(c);
+    const float *T = c->d_T;
+    S *P = Bufs<S>::P(c);
+    switch (comp_block(c->R)) {
+        case 8:
+            k_beta_p<8, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R);
+            break;
+        case 16:
+            k_beta_p<16, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R);
+            break;
+        default:
+            k_beta_p<32, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R);
             break;
     }
 }
 
 static void launch_beta_p(p2_ctx *c, const Launch &L) {
-    dim3 grid(c->geo.nsm * L.beta_blocks), block(L.beta_warps * 32);
-    XView X = xview(c);
+    if (c->bf16)
+        launch_beta_p_t<bf16_t>(c, L);
+    else
+        launch_beta_p_t<float>(c, L);
+}
+
+template <class S>
+static void launch_m2_segments_t(p2_ctx *c) {
+    const int64_t want = (c->X.nseg + 7) / 8;
+    const int sb = (int)(want < 64 * (int64_t)c->geo.nsm ? want : 64 * (int64_t)c->geo.nsm);
+    const S *P = Bufs<S>::P(c);
     switch (comp_block(c->R)) {
         case 8:
-            k_beta_p<8><<<grid, block, L.beta_smem, c->stream>>>(X, c->d_V, c->d_H, c->d_T, c->d_W, c->d_P, c->R);
+            k_m2_segments<8, S><<<sb, 256, 0, c->stream>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
+                                                           c->X.nseg, P, c->d_segpart, c->R);
             break;
         case 16:
-            k_beta_p<16><<<grid, block, L.beta_smem, c->stream>>>(X, c->d_V, c->d_H, c->d_T, c->d_W, c->d_P, c->R);
+            k_m2_segments<16, S><<<sb, 256, 0, c->stream>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
+                                                            c->X.nseg, P, c->d_segpart, c->R);
             break;
         default:
-            k_beta_p<32><<<grid, block, L.beta_smem, c->stream>>>(X, c->d_V, c->d_H, c->d_T, c->d_W, c->d_P, c->R);
+            k_m2_segments<32, S><<<sb, 256, 0, c->stream>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
+                                                            c->X.nseg, P, c->d_segpart, c->R);
             break;
     }
 }
 
 static void launch_m2_segments(p2_ctx *c) {
-    const int64_t want = (c->X.nseg + 7) / 8;
-    const int sb = (int)(want < 64 * (int64_t)c->geo.nsm ? want : 64 * (int64_t)c->geo.nsm);
-    switch (comp_block(c->R)) {
-        case 8:
-            k_m2_segments<8><<<sb, 256, 0, c->stream>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
-                                                        c->X.nseg, c->d_P, c->d_segpart, c->R);
-            break;
-        case 16:
-            k_m2_segments<16><<<sb, 256, 0, c->stream>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
-                                                         c->X.nseg, c->d_P, c->d_segpart, c->R);
-            break;
-        default:
-            k_m2_segments<32><<<sb, 256, 0, c->stream>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
-                                                         c->X.nseg, c->d_P, c->d_segpart, c->R);
-            break;
-    }
+    if (c->bf16)
+        launch_m2_segments_t<bf16_t>(c);
+    else
+        launch_m2_segments_t<float>(c);
 }
 
 // Q-step for the current (H, V, W) (Algorithm 2's SVD loop), then the
@@ -964,9 +1033,9 @@ static int enqueue_qstep(p2_ctx *c, int with_fit) {
     const size_t cta = (2 * (size_t)P + 15) & ~(size_t)15;
     int nw = 8;
     while (nw > 1 && cta + nw * stats_warp_bytes(R) > (size_t)c->geo.smem_optin) --nw;
-    k_subject_stats<<<nb, nw * 32, cta + nw * stats_warp_bytes(R), s>>>(c->d_T, c->d_G, c->d_W,
-                                                                      c->d_M3, c->d_part, K, R,
-                                                                      with_fit);
+    const size_t ssm = cta + nw * stats_warp_bytes(R);
+    k_subject_stats<<<nb, nw * 32, ssm, s>>>(c->d_T, c->d_G, c->d_W, c->d_M3, c->d_part, K, R,
+                                             with_fit);
     P2_LAUNCH_CHECK("k_subject_stats");
     mark(c, 6);
     k_fin_w<<<1, 256, 0, s>>>(c->d_part, nb, c->d_s, R, with_fit);
@@ -980,7 +1049,10 @@ int enqueue_factor_stats(p2_ctx *c) {
     const int nb = c->geo.red_blocks;
     k_init_h<<<1, 256, 0, s>>>(c->d_H, c->d_s, R);
     P2_LAUNCH_CHECK("k_init_h");
-    k_gram_v<<<nb, 256, 0, s>>>(c->d_V, c->d_part2, c->X.J, R);
+    if (c->bf16)
+        k_gram_v<bf16_t><<<nb, 256, 0, s>>>(c->d_Vh, c->d_part2, c->X.J, R);
+    else
+        k_gram_v<float><<<nb, 256, 0, s>>>(c->d_V, c->d_part2, c->X.J, R);
     P2_LAUNCH_CHECK("k_gram_v");
     k_fin_v<<<1, 256, (size_t)2 * R * R * 8, s>>>(c->d_part2, nb, c->d_s, R, 0);
     P2_LAUNCH_CHECK("k_fin_v");
@@ -989,7 +1061,7 @@ int enqueue_factor_stats(p2_ctx *c) {
 
 int enqueue_prologue(p2_ctx *c) {
     const Launch L = plan(c);
-    launch_alpha<false>(c, L, nullptr);
+    launch_alpha<false>(c, L);
     P2_LAUNCH_CHECK("k_alpha<false>");
     return enqueue_qstep(c, 0);
 }
@@ -1028,15 +1100,21 @@ int enqueue_iteration(p2_ctx *c) {
     P2_LAUNCH_CHECK("k_solve_v_rows");
     k_solve_v_norm<<<1, 64, 0, s>>>(c->d_part2, nb, c->d_s, R);
     P2_LAUNCH_CHECK("k_solve_v_norm");
-    k_solve_v_store<<<fb, 256, 0, s>>>(c->d_Vun, c->d_s, c->d_V, c->d_Vprev, nJR, R);
+    if (c->bf16)
+        k_solve_v_store<bf16_t><<<fb, 256, 0, s>>>(c->d_Vun, c->d_s, c->d_Vh, c->d_Vprevh, nJR, R);
+    else
+        k_solve_v_store<float><<<fb, 256, 0, s>>>(c->d_Vun, c->d_s, c->d_V, c->d_Vprev, nJR, R);
     P2_LAUNCH_CHECK("k_solve_v_store");
-    k_gram_v<<<nb, 256, 0, s>>>(c->d_V, c->d_part2, J, R);
+    if (c->bf16)
+        k_gram_v<bf16_t><<<nb, 256, 0, s>>>(c->d_Vh, c->d_part2, J, R);
+    else
+        k_gram_v<float><<<nb, 256, 0, s>>>(c->d_V, c->d_part2, J, R);
     P2_LAUNCH_CHECK("k_gram_v");
     k_fin_v<<<1, 256, sm_pinv, s>>>(c->d_part2, nb, c->d_s, R, 1);
     P2_LAUNCH_CHECK("k_fin_v");
     // pass alpha: mode-3 MTTKRP + W step (Algorithm 1 line 7) + Gram for the next Q-step
     mark(c, 3);
-    launch_alpha<true>(c, L, c->d_Vprev);
+    launch_alpha<true>(c, L);
     P2_LAUNCH_CHECK("k_alpha<true>");
     // next Q-step (Algorithm 2's SVD loop), mode-1 MTTKRP, W statistics, fit
     int rc = enqueue_qstep(c, 1);

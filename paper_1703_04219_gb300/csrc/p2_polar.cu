@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) k_polar_reg(const double *__restrict__ G,
                 for (int i = 0; i < R; ++i) s = fma(A(r, i), A(c, i), s);
                 Cl[pk<R>(r, c)] = s;
             }
-        float *Tk = T + (size_t)k * R * R;
+        const size_t tb = (size_t)k * R * R;
 #pragma unroll 1
         for (int c = 0; c < R; ++c)
 #pragma unroll
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) k_polar_reg(const double *__restrict__ G,
                 double s = 0.0;
 #pragma unroll
                 for (int u = 0; u < R; ++u) s = fma(Cl[pk<R>(r, u)], Hs[u * R + c], s);
-                Tk[r * R + c] = (float)(s * w[c]);
+                T[tb + r * R + c] = (float)(s * w[c]);
             }
         flops = polar_fixed_flops(R) + qr_flops(R, steps, rot);
     }
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(128) k_polar_smem(const double *__restrict__ G
                 for (int i = 0; i < R; ++i) s = fma(A(r, i), A(c, i), s);
                 gp[(size_t)p * NT] = s;
             }
-        float *Tk = T + (size_t)k * R * R;
+        const size_t tb = (size_t)k * R * R;
         for (int r = 0; r < R; ++r)
             for (int c = 0; c < R; ++c) {
                 double s = 0.0;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(128) k_polar_smem(const double *__restrict__ G
                     const int p = (u <= r) ? (r * (r + 1) / 2 + u) : (u * (u + 1) / 2 + r);
                     s = fma(gp[(size_t)p * NT], Hs[u * R + c], s);
                 }
-                Tk[r * R + c] = (float)(s * w[c]);
+                T[tb + r * R + c] = (float)(s * w[c]);
             }
         flops = polar_fixed_flops(R) + qr_flops(R, steps, rot);
     }

@@ -211,9 +211,13 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const double *__restrict__
         __syncwarp(gmask);
 
         // ---- implicit QR with Wilkinson shift; rotations on my rows of Z ----
-        // The scalar recurrence runs on all eight lanes (identical values);
-        // d[k+1] and e[k+1] of a sweep are read before anything writes them,
-        // d[k] and e[k] are carried in registers.
+        // One flat loop, one Givens rotation per trip, so that the four
+        // groups of a warp execute the rotation body together whatever their
+        // sweep boundaries.  The scalar recurrence runs on all eight lanes
+        // (identical values); d[k+1] and e[k+1] of a sweep are read before
+        // anything writes them and d[k], e[k] are carried in registers.
+        // Deflation tests compare binary exponents in integer arithmetic
+        // (p2_negligible).
         const double eps = 2.220446049250313e-16;
         double an = 0.0;
         for (int i = gl; i < R; i += PG) {
@@ -225,75 +229,70 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const double *__restrict__
         an = fmax(an, __shfl_xor_sync(gmask, an, 4));
         an = fmax(an, __shfl_xor_sync(gmask, an, 2));
         an = fmax(an, __shfl_xor_sync(gmask, an, 1));
-        const double tiny = eps * an;
+        const int tiny_ex = p2_expo(eps * an);
         int steps = 0, rot = 0;
         const int max_steps = 30 * R;
-        int q = R - 1;
-        bool failed = false;
+        int q = R - 1, p = 0, kr = 0;
+        bool sweeping = false, failed = false;
+        double x = 0.0, z = 0.0, dk = 0.0, ek = 0.0;
 #pragma unroll 1
-        while (q > 0) {
-            const double eq = e[q - 1];
-            if (fabs(eq) <= eps * (fabs(d[q - 1]) + fabs(d[q])) || fabs(eq) <= tiny) {
+        while (true) {
+            if (!sweeping) {
+                while (q > 0 && p2_negligible(e[q - 1], d[q - 1], d[q], tiny_ex)) --q;
+                if (q == 0) break;
+                p = q - 1;
+                while (p > 0 && !p2_negligible(e[p - 1], d[p - 1], d[p], tiny_ex)) --p;
+                if (++steps > max_steps) {
+                    failed = true;
+                    break;
+                }
+                rot += q - p;
+                const double eq = e[q - 1];
+                const double dd = 0.5 * (d[q - 1] - d[q]);
+                const double h = sqrt(fma(dd, dd, eq * eq));
+                const double mu = d[q] - eq * eq / (dd + (dd >= 0.0 ? h : -h));
+                dk = d[p];
+                ek = e[p];
+                x = dk - mu;
+                z = ek;
+                kr = p;
+                sweeping = true;
                 __syncwarp(gmask);
-                e[q - 1] = 0.0;
-                __syncwarp(gmask);
-                --q;
-                continue;
+                if (gl == 0 && p > 0) e[p - 1] = 0.0;
             }
-            int p = q - 1;
-            while (p > 0) {
-                const double ep = e[p - 1];
-                if (fabs(ep) <= eps * (fabs(d[p - 1]) + fabs(d[p])) || fabs(ep) <= tiny) break;
-                --p;
-            }
-            if (++steps > max_steps) {
-                failed = true;
-                break;
-            }
-            rot += q - p;
-            const double dd = 0.5 * (d[q - 1] - d[q]);
-            const double h = sqrt(fma(dd, dd, eq * eq));
-            const double mu = d[q] - eq * eq / (dd + (dd >= 0.0 ? h : -h));
-            double x = d[p] - mu;
-            double z = e[p];
-            double dk = d[p], ek = e[p];
+            const double bb = d[kr + 1];
+            const double en = (kr + 1 < q) ? e[kr + 1] : 0.0;
             __syncwarp(gmask);
-            if (p > 0) e[p - 1] = 0.0;
-#pragma unroll 1
-            for (int kr = p; kr < q; ++kr) {
-                const double bb = d[kr + 1];
-                const double en = (kr + 1 < q) ? e[kr + 1] : 0.0;
-                __syncwarp(gmask);
-                const double tt = fma(x, x, z * z);
-                double c = 1.0, s = 0.0, r = 0.0;
-                if (tt > 0.0) {
-                    const double ir = p2_rsqrt(tt);
-                    c = x * ir;
-                    s = -z * ir;
-                    r = tt * ir;
-                }
-                if (kr > p) e[kr - 1] = r;
-                const double cc = c * c, ss = s * s, cs = c * s;
-                const double cs2g = 2.0 * cs * ek;
-                d[kr] = fma(cc, dk, fma(ss, bb, -cs2g));
-                const double dk1 = fma(ss, dk, fma(cc, bb, cs2g));
-                const double ekn = fma(cs, dk - bb, (cc - ss) * ek);
-                if (kr + 1 < q) {
-                    z = -s * en;
-                    ek = c * en;
-                    x = ekn;
-                } else {
-                    d[q] = dk1;
-                    e[q - 1] = ekn;
-                }
+            const double tt = fma(x, x, z * z);
+            double c = 1.0, s = 0.0, r = 0.0;
+            if (tt > 0.0) {
+                const double ir = p2_rsqrt(tt);
+                c = x * ir;
+                s = -z * ir;
+                r = tt * ir;
+            }
+            if (kr > p) e[kr - 1] = r;
+            const double cc = c * c, ss = s * s, cs = c * s;
+            const double cs2g = 2.0 * cs * ek;
+            d[kr] = fma(cc, dk, fma(ss, bb, -cs2g));
+            const double dk1 = fma(ss, dk, fma(cc, bb, cs2g));
+            const double ekn = fma(cs, dk - bb, (cc - ss) * ek);
+            for (int i = gl; i < R; i += PG) {
+                const double zk = A(i, kr), zk1 = A(i, kr + 1);
+                A(i, kr) = fma(c, zk, -s * zk1);
+                A(i, kr + 1) = fma(s, zk, c * zk1);
+            }
+            if (++kr < q) {
+                z = -s * en;
+                ek = c * en;
+                x = ekn;
                 dk = dk1;
-                for (int i = gl; i < R; i += PG) {
-                    const double zk = A(i, kr), zk1 = A(i, kr + 1);
-                    A(i, kr) = fma(c, zk, -s * zk1);
-                    A(i, kr + 1) = fma(s, zk, c * zk1);
-                }
+            } else {
+                d[q] = dk1;
+                e[q - 1] = ekn;
+                sweeping = false;
+                __syncwarp(gmask);
             }
-            __syncwarp(gmask);
         }
         if (failed && gl == 0) atomicOr(&st->flags, FLAG_EIG_NOCONV);
         __syncwarp(gmask);
@@ -312,7 +311,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const double *__restrict__
         }
         __syncwarp(gmask);
         // ---- T = Z' (Z'^T H S), one column of T at a time -------------------
-        float *Tk = T + (size_t)k * R * R;
+        const size_t tb = (size_t)k * R * R;
 #pragma unroll 1
         for (int c = 0; c < R; ++c) {
             const double wc = wv[c];
@@ -335,7 +334,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const double *__restrict__
 #pragma unroll
                 for (int i = 0; i < RB; ++i)
                     if (i < R) s = fma(A(r, i), tv[i], s);
-                Tk[r * R + c] = (float)s;
+                T[tb + r * R + c] = (float)s;
             }
         }
         if (gl == 0) flops = polar_fixed_flops(R) + qr_flops(R, steps, rot);

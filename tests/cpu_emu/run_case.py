@@ -20,10 +20,19 @@ p2.LIB_PATH = os.path.join(HERE, "_build", "libp2emu.so")
 p2.lib = p2._load()
 
 
-def iterate_case(name, K, R):
+def bf16_round(a):
+    """Round float32 values to the nearest bfloat16 (ties to even), as float32."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
+    return u.astype(np.uint32).view(np.float32).reshape(np.shape(a))
+
+
+def iterate_case(name, K, R, precision="fp32"):
     X = synth.generate(name, K=K)
     H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=11)
-    with p2.Parafac2(R, use_graph=False) as m:
+    if precision == "bf16":                # a start that bfloat16 storage represents exactly
+        V0 = bf16_round(V0)
+    with p2.Parafac2(R, use_graph=False, precision=precision) as m:
         m.load(X)
         m.init(H0, V0, W0)
         fit = m.iterate(1)
@@ -61,7 +70,8 @@ def project_case(R, n_req):
 if __name__ == "__main__":
     kind = sys.argv[1]
     if kind == "iterate":
-        out = iterate_case(sys.argv[2], int(sys.argv[3]), int(sys.argv[4]))
+        out = iterate_case(sys.argv[2], int(sys.argv[3]), int(sys.argv[4]),
+                           sys.argv[5] if len(sys.argv) > 5 else "fp32")
     else:
         out = project_case(int(sys.argv[2]), int(sys.argv[3]))
     print(json.dumps({k: float(v) for k, v in out.items()}), flush=True)

@@ -1,6 +1,7 @@
 """The library's CUDA kernels run on the CPU emulator (tests/cpu_emu) under
-AddressSanitizer: one ALS iteration at R = 5 (lane-per-subject Procrustes)
-and R = 13 (grouped Procrustes kernel), and a projection of new subjects.
+AddressSanitizer: one ALS iteration at R = 5 (lane-per-subject Procrustes),
+at R = 13 (grouped Procrustes kernel) and at R = 5 with bfloat16 storage,
+and a projection of new subjects.
 Every device buffer and every block's shared memory is a heap block of its
 exact size, so an out-of-bounds access by any kernel aborts the run; the
 results must also match the FP64 oracle.  No GPU involved."""
@@ -18,6 +19,7 @@ EMU = os.path.join(HERE, "cpu_emu")
 CASES = {
     "iterate_r5": ["iterate", "tiny", "24", "5"],
     "iterate_r13": ["iterate", "tiny", "16", "13"],
+    "iterate_r5_bf16": ["iterate", "tiny", "24", "5", "bf16"],
     "project_r12": ["project", "12", "3"],
 }
 
@@ -67,6 +69,13 @@ def test_emulated_iteration_is_in_bounds_and_matches_oracle(emulated_runs, name)
     err = _result(emulated_runs, name)
     for key in ("M1", "M2", "M3", "H", "V", "W"):
         assert err[key] < 1e-5, (key, err[key])
+    assert err["fit"] < 1e-4
+
+
+def test_emulated_bf16_storage_is_in_bounds_and_within_3e3(emulated_runs):
+    err = _result(emulated_runs, "iterate_r5_bf16")
+    for key in ("M1", "M2", "M3", "H", "V", "W"):
+        assert err[key] < 3e-3, (key, err[key])
     assert err["fit"] < 1e-4
 
 

@@ -260,42 +260,21 @@ def run_p2(args, w):
     gpu_id = f"GPU-{gpu_id}" if gpu_id is not None and not str(gpu_id).startswith("GPU-") else \
         (str(gpu_id) if gpu_id is not None else local)
     clocks = ClockSampler(gpu_id)
-    st0 = m.stats()
-    phase_sum = {k: 0.0 for k in PHASES}
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        m.iterate(1, want_fit=False)
-        st = m.stats()                  # synchronises the stream; reads this step's phase events
-        for k in PHASES:
-            phase_sum[k] += st["phase_ms"].get(k, 0.0)
-    ev1.record(stream)
-    ev1.synchronize()
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    ms_total = ev0.elapsed_time(ev1)
-    clk = clocks.stop()
-    st1 = m.stats()
+    t = timed_steps(m, stream, args.steps, pg, clocks)
+    ms_total, clk, launches = t["ms_total"], t["clocks"], t["launches"]
+    phase_ms = t["phase_ms"]
     fit, loss = m.fit()
     if pg:
         ms_total = max_over_ranks(ms_total, pg, device="cuda")
     ms_step = ms_total / args.steps
     value = job_throughput(X.nnz, args.steps, ms_total, world)
-    phase_ms = {k: v / args.steps for k, v in phase_sum.items()}
-    launches = st1["kernel_launches"] - st0["kernel_launches"]
 
     # roofline of the dominant kernel group
     dom = max(phase_ms, key=phase_ms.get)
     bmodel = _bytes_model(X, R)
     hbm_peak, hbm_src = _peaks()
     if dom == "procrustes":
-        flops = (st1["polar_fp64_flops"] - st0["polar_fp64_flops"]) / args.steps
+        flops = t["flops"]
         ach = flops / (phase_ms[dom] / 1e3) / 1e12
         roof = {"kernel": "k_polar_reg/k_polar_smem (FP64 Procrustes, lane per subject)",
                 "bound": "alu",
@@ -350,30 +329,58 @@ def run_p2(args, w):
     return 0
 
 
-def time_precision(X, R, H0, V0, W0, precision, steps, warmup, device):
-    """ms per iteration of the same workload with another storage precision
-    (graph replays, CUDA events on the launching stream, inputs > L2)."""
+def timed_steps(m, stream, steps, pg=None, clocks=None):
+    """Time `steps` graph replays with CUDA events on the library's stream
+    (barrier + synchronize on both sides).  After each step the phase events
+    recorded inside the graph are read (p2_stats), so the per-kernel times are
+    averages over the timed region."""
     import torch
+    st0 = m.stats()
+    phase_sum = {k: 0.0 for k in PHASES}
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    ev0.record(stream)
+    for _ in range(steps):
+        m.iterate(1, want_fit=False)
+        st = m.stats()                  # synchronises the stream; reads this step's phase events
+        for k in PHASES:
+            phase_sum[k] += st["phase_ms"].get(k, 0.0)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    clk = clocks.stop() if clocks else None
+    st1 = m.stats()
+    return {"ms_total": ms_total, "phase_ms": {k: v / steps for k, v in phase_sum.items()},
+            "launches": st1["kernel_launches"] - st0["kernel_launches"],
+            "flops": (st1["polar_fp64_flops"] - st0["polar_fp64_flops"]) / steps, "clocks": clk}
+
+
+def time_precision(X, R, H0, V0, W0, precision, steps, warmup, device):
+    """The same workload and timing with another storage precision."""
+    import torch
+    import paper_1703_04219_gb300 as p2
     stream = torch.cuda.Stream()
-    m = __import__("paper_1703_04219_gb300").Parafac2(R, device=device, stream=stream.cuda_stream,
-                                                    precision=precision)
+    m = p2.Parafac2(R, device=device, stream=stream.cuda_stream, timing=True, precision=precision)
     m.load(X)
     m.init(H0, V0, W0)
     for _ in range(warmup):
         m.iterate(1, want_fit=False)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    m.iterate(steps, want_fit=False)
-    ev1.record(stream)
-    ev1.synchronize()
-    ms = ev0.elapsed_time(ev1) / steps
+    stream.synchronize()
+    t = timed_steps(m, stream, steps)
     fit, _ = m.fit()
     m.close()
+    ms = t["ms_total"] / steps
     return {"ms_per_step": ms, "value": X.nnz / (ms / 1e3), "unit": UNIT,
-            "fit_after_steps": fit, "storage": "V and P_k bfloat16" if precision == "bf16"
-            else "float"}
+            "fit_after_steps": fit, "phase_ms": t["phase_ms"],
+            "storage": "V and P_k bfloat16" if precision == "bf16" else "float"}
 
 
 def run_serving(rate=50000.0, horizon_s=2.0, n_iter=5, n_slots=4, seed=5, precision="fp32"):

@@ -83,6 +83,7 @@ static void free_data(p2_ctx *c) {
     dfree(c, &c->d_M3, K * R);
     dfree(c, &c->d_T, K * R * R);
     dfree(c, &c->d_G, K * P);
+    dfree(c, &c->d_Gf, K * P);
     delete[] c->h_perm_new2old;
     delete[] c->h_perm_old2new;
     c->h_perm_new2old = c->h_perm_old2new = nullptr;
@@ -124,6 +125,7 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
     P2_TRY(dalloc(c, &c->d_W, (size_t)K * R));
     P2_TRY(dalloc(c, &c->d_M3, (size_t)K * R));
     P2_TRY(dalloc(c, &c->d_G, (size_t)K * P));
+    P2_TRY(dalloc(c, &c->d_Gf, (size_t)K * P));
     P2_CUDA_TRY(cudaMemsetAsync(c->d_M3, 0, sizeof(float) * (size_t)K * R, c->stream));
     c->h_perm_new2old = new int32_t[J];
     c->h_perm_old2new = new int32_t[J];

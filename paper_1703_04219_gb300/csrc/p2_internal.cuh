@@ -144,6 +144,7 @@ struct p2_ctx {
     float *d_W = nullptr;       // K x R
     float *d_T = nullptr;       // K x R x R
     double *d_G = nullptr;      // K x P (packed lower Gram of Z_k)
+    float *d_Gf = nullptr;      // K x P the same rounded to float (mode-1 statistics)
     float *d_M3 = nullptr;      // K x R
     double *d_M2 = nullptr;     // J x R (relabelled rows)
     float *d_P = nullptr;       // N x R rows of P_k = Z_k F_k (mode-2 pass)

@@ -48,7 +48,9 @@ static XView xview(const p2_ctx *c) {
 // TWO, z2[i][:] = X(row i, :) V2.  One lane per row, so a chunk costs one
 // round of dependent loads; the row's components are accumulated in
 // registers in blocks of CB (FP32 FMA in column order within the row) and
-// stored with the odd row stride RS (no shared-memory bank conflicts).
+// stored with the odd row stride RS (no shared-memory bank conflicts).  With
+// TWO the row is walked once per operand so that only CB accumulators are
+// live (register pressure decides the occupancy of the passes).
 template <int CB, bool TWO, class S>
 static __device__ __forceinline__ void gather_rows(const XView &X, int nr, int64_t base, int len,
                                                    int off, const S *__restrict__ V1,
@@ -56,37 +58,44 @@ static __device__ __forceinline__ void gather_rows(const XView &X, int nr, int64
                                                    float *z2, int R, int RS, int lane) {
     if (lane >= nr) return;
     const int64_t b0 = base + off;
-    for (int cb = 0; cb < R; cb += CB) {
-        float a1[CB], a2[CB];
+#pragma unroll 1
+    for (int which = 0; which < (TWO ? 2 : 1); ++which) {
+        const S *__restrict__ Vw = which ? V2 : V1;
+        float *zw = which ? z2 : z1;
+        for (int cb = 0; cb < R; cb += CB) {
+            float a[CB];
 #pragma unroll
-        for (int c = 0; c < CB; ++c) {
-            a1[c] = 0.f;
-            a2[c] = 0.f;
-        }
-        for (int e = 0; e < len; ++e) {
-            const int j = X.col[b0 + e];
-            const float x = X.val[b0 + e];
-            const S *v1 = V1 + (size_t)j * R + cb;
-            const S *v2 = TWO ? (V2 + (size_t)j * R + cb) : nullptr;
+            for (int c = 0; c < CB; ++c) a[c] = 0.f;
+            for (int e = 0; e < len; ++e) {
+                const int j = X.col[b0 + e];
+                const float x = X.val[b0 + e];
+                const S *v = Vw + (size_t)j * R + cb;
 #pragma unroll
-            for (int c = 0; c < CB; ++c) {
-                if (cb + c < R) {
-                    a1[c] = fmaf(x, Stor<S>::ld(v1 + c), a1[c]);
-                    if (TWO) a2[c] = fmaf(x, Stor<S>::ld(v2 + c), a2[c]);
-                }
+                for (int c = 0; c < CB; ++c)
+                    if (cb + c < R) a[c] = fmaf(x, Stor<S>::ld(v + c), a[c]);
             }
-        }
 #pragma unroll
-        for (int c = 0; c < CB; ++c) {
-            if (cb + c < R) {
-                z1[lane * RS + cb + c] = a1[c];
-                if (TWO) z2[lane * RS + cb + c] = a2[c];
-            }
+            for (int c = 0; c < CB; ++c)
+                if (cb + c < R) zw[lane * RS + cb + c] = a[c];
         }
     }
 }
 
 static __host__ __device__ __forceinline__ int row_stride(int R) { return R | 1; }
+
+// Row and column of entry e of an n-column row-major array, for e advancing by
+// 32 (one warp's stride) without an integer division per step.
+struct RowCol {
+    int r, c;
+    __device__ __forceinline__ RowCol(int e, int n) : r(e / n), c(e - (e / n) * n) {}
+    __device__ __forceinline__ void next(int n) {
+        c += 32;
+        while (c >= n) {
+            c -= n;
+            ++r;
+        }
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Pass alpha: for each subject, Gram of Z'_k = X_k V (packed lower; every
@@ -102,7 +111,7 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_alpha(XView X, const S
                                                const float *__restrict__ H,
                                                const float *__restrict__ T,
                                                const SmallState *__restrict__ st, double *G,
-                                               float *W, float *M3, int R) {
+                                               float *Gf, float *W, float *M3, int R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = R * (R + 1) / 2;
     const int RS = row_stride(R);
@@ -157,10 +166,10 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_alpha(XView X, const S
                                           lane);
             __syncwarp();
             if (MODE3) {
-                for (int e = lane; e < R * R; e += 32) {
-                    const int r = e / R, s = e - r * R;
+                RowCol rs(lane, R);
+                for (int e = lane; e < R * R; e += 32, rs.next(R)) {
                     float acc = 0.f;
-                    for (int i = 0; i < nr; ++i) acc = fmaf(zo[i * RS + r], zn[i * RS + s], acc);
+                    for (int i = 0; i < nr; ++i) acc = fmaf(zo[i * RS + rs.r], zn[i * RS + rs.c], acc);
                     Cacc[e] += acc;
                 }
             }
@@ -185,15 +194,19 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_alpha(XView X, const S
         }
         double *Gk = G + (size_t)k * P;
         for (int p = lane; p < P; p += 32) Gk[p] = (double)Ghi[p] + (double)Glo[p];
+        if (Gf) {
+            float *Gfk = Gf + (size_t)k * P;
+            for (int p = lane; p < P; p += 32) Gfk[p] = Ghi[p] + Glo[p];
+        }
         if (MODE3) {
             const float *Tg = T + (size_t)k * R * R;
             for (int e = lane; e < R * R; e += 32) Tk[e] = Tg[e];
             __syncwarp();
             float *scr = zo;   // 64 RS >= R R floats of scratch
-            for (int e = lane; e < R * R; e += 32) {
-                const int r = e / R, s = e - r * R;
+            RowCol rs(lane, R);
+            for (int e = lane; e < R * R; e += 32, rs.next(R)) {
                 float b = 0.f;
-                for (int u = 0; u < R; ++u) b = fmaf(Tk[r * R + u], Cacc[u * R + s], b);
+                for (int u = 0; u < R; ++u) b = fmaf(Tk[rs.r * R + u], Cacc[u * R + rs.c], b);
                 scr[e] = Hs[e] * b;
             }
             __syncwarp();
@@ -248,11 +261,11 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_beta_p(XView X, const 
         for (int e = lane; e < R * R; e += 32) Tk[e] = Tg[e];
         for (int s = lane; s < R; s += 32) wk[s] = W[(size_t)k * R + s];
         __syncwarp();
-        for (int e = lane; e < R * R; e += 32) {
-            const int u = e / R, s = e - u * R;
+        RowCol us(lane, R);
+        for (int e = lane; e < R * R; e += 32, us.next(R)) {
             float f = 0.f;
-            for (int r = 0; r < R; ++r) f = fmaf(Tk[r * R + u], Hs[r * R + s], f);
-            Fk[e] = f * wk[s];
+            for (int r = 0; r < R; ++r) f = fmaf(Tk[r * R + us.r], Hs[r * R + us.c], f);
+            Fk[e] = f * wk[us.c];
         }
         __syncwarp();
         for (int64_t cr = r0; cr < r1; cr += 32) {
@@ -263,10 +276,10 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_beta_p(XView X, const 
             gather_rows<CB, false, S>(X, nr, base, len, off, V, nullptr, zo, nullptr, R, RS, lane);
             __syncwarp();
             S *Pr = Pout + (size_t)cr * R;
-            for (int e = lane; e < nr * R; e += 32) {
-                const int i = e / R, s = e - i * R;
+            RowCol is(lane, R);
+            for (int e = lane; e < nr * R; e += 32, is.next(R)) {
                 float p = 0.f;
-                for (int u = 0; u < R; ++u) p = fmaf(zo[i * RS + u], Fk[u * R + s], p);
+                for (int u = 0; u < R; ++u) p = fmaf(zo[is.r * RS + u], Fk[u * R + is.c], p);
                 Stor<S>::st(Pr + e, p);
             }
             __syncwarp();
@@ -354,8 +367,36 @@ __global__ void k_m2_columns(const double *__restrict__ segpart, const int64_t *
 // FP64 (W^TW products of FP32 values are exact in FP64).  Block partials,
 // layout [R*R M1][R*R WtW][R wmax][1 wm3], summed later in block order.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__ T,
-                                                     const double *__restrict__ G,
+// a + b = s + e exactly (Knuth's TwoSum)
+static __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bv = s - a;
+    e = (a - (s - bv)) + (b - bv);
+}
+// (hi, lo) += x: an unevaluated float pair, error-free up to the rounding of lo
+static __device__ __forceinline__ void pair_add(float &hi, float &lo, float x) {
+    float t, e;
+    two_sum(hi, x, t, e);
+    hi = t;
+    lo += e;
+}
+// (hi, lo) += a * b, the product split exactly with an FMA (Dekker's TwoProduct)
+static __device__ __forceinline__ void pair_fma(float &hi, float &lo, float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    float t, e;
+    two_sum(hi, p, t, e);
+    hi = t;
+    lo += e + pe;
+}
+
+// Body of the statistics kernels; G is the packed Gram as float (the copy the
+// alpha pass writes for this kernel) or double (the allocation-free entry
+// point's interface).  Accumulations use float pairs: ~2^-48 relative error
+// and no FP64 instruction per subject.
+template <class GT>
+static __device__ __forceinline__ void subject_stats(const float *__restrict__ T,
+                                                     const GT *__restrict__ G,
                                                      const float *__restrict__ W,
                                                      const float *__restrict__ M3, double *part,
                                                      int64_t K, int R, int with_m3) {
@@ -363,17 +404,20 @@ __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__
     __shared__ double red_wm3[8];
     __shared__ float red_wmax[8][P2_RMAX];
     const int P = R * (R + 1) / 2;
+    const int RR = R * R;
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t *pr = smem_raw;
     uint8_t *pc = pr + P;
     const size_t cta_bytes = (2 * (size_t)P + 15) & ~(size_t)15;
     const size_t wbytes = stats_warp_bytes(R);
     unsigned char *wb = smem_raw + cta_bytes + warp * wbytes;
-    double *aM1 = reinterpret_cast<double *>(wb);
-    double *aW = aM1 + R * R;
-    float *Ts = reinterpret_cast<float *>(aW + R * R);
-    float *Gs = Ts + R * R;
-    float *ws = Gs + R * R;
+    float *m1h = reinterpret_cast<float *>(wb);     // R*R each: M1 and W^TW pairs
+    float *m1l = m1h + RR;
+    float *wth = m1l + RR;
+    float *wtl = wth + RR;
+    float *Ts = wtl + RR;
+    float *Gs = Ts + RR;
+    float *ws = Gs + RR;
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
         int r = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
         while ((r + 1) * (r + 2) / 2 <= p) ++r;
@@ -381,20 +425,23 @@ __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__
         pr[p] = (uint8_t)r;
         pc[p] = (uint8_t)(p - r * (r + 1) / 2);
     }
-    for (int e = lane; e < R * R; e += 32) {
-        aM1[e] = 0.0;
-        aW[e] = 0.0;
+    for (int e = lane; e < RR; e += 32) {
+        m1h[e] = 0.f;
+        m1l[e] = 0.f;
+        wth[e] = 0.f;
+        wtl[e] = 0.f;
     }
     __syncthreads();
     const int64_t per = (K + gridDim.x - 1) / gridDim.x;
     const int64_t k0 = (int64_t)blockIdx.x * per;
     const int64_t k1 = (k0 + per < K) ? (k0 + per) : K;
-    double wm3 = 0.0;
+    float wm3h = 0.f, wm3l = 0.f;
     float wmx[2] = {0.f, 0.f};
+    const int r0 = lane / R, c0 = lane - (lane / R) * R;   // first entry of this lane
     for (int64_t k = k0 + warp; k < k1; k += nw) {
-        const float *Tg = T + (size_t)k * R * R;
-        const double *Gg = G + (size_t)k * P;
-        for (int e = lane; e < R * R; e += 32) Ts[e] = Tg[e];
+        const float *Tg = T + (size_t)k * RR;
+        const GT *Gg = G + (size_t)k * P;
+        for (int e = lane; e < RR; e += 32) Ts[e] = Tg[e];
         for (int p = lane; p < P; p += 32) {
             const float g = (float)Gg[p];
             const int r = pr[p], c = pc[p];
@@ -408,20 +455,26 @@ __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__
                 const float v = W[(size_t)k * R + s];
                 ws[s] = v;
                 wmx[t] = fmaxf(wmx[t], fabsf(v));
-                if (with_m3) wm3 = fma((double)v, (double)M3[(size_t)k * R + s], wm3);
+                if (with_m3) pair_fma(wm3h, wm3l, v, M3[(size_t)k * R + s]);
             }
         }
         __syncwarp();
-        for (int e = lane; e < R * R; e += 32) {
-            const int r = e / R, c = e - r * R;
+        int r = r0, c = c0;
+        for (int e = lane; e < RR; e += 32) {
             float sacc = 0.f;
             for (int u = 0; u < R; ++u) sacc = fmaf(Ts[r * R + u], Gs[u * R + c], sacc);
-            aM1[e] += (double)(sacc * ws[c]);
-            aW[e] = fma((double)ws[r], (double)ws[c], aW[e]);
+            pair_add(m1h[e], m1l[e], sacc * ws[c]);
+            pair_fma(wth[e], wtl[e], ws[r], ws[c]);
+            c += 32;                                   // next entry e + 32
+            while (c >= R) {
+                c -= R;
+                ++r;
+            }
         }
         __syncwarp();
     }
     // fixed-order reductions: lanes, then warps in index order
+    double wm3 = (double)wm3h + (double)wm3l;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wm3 += __shfl_down_sync(FULLMASK, wm3, o);
     if (lane == 0) red_wm3[warp] = wm3;
@@ -431,26 +484,43 @@ __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__
     __syncthreads();
     const size_t stride = stats_part_stride(R);
     double *out = part + (size_t)blockIdx.x * stride;
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) {
         double m = 0.0, w2 = 0.0;
         for (int q = 0; q < nw; ++q) {
-            const double *aq = reinterpret_cast<const double *>(smem_raw + cta_bytes + q * wbytes);
-            m += aq[e];
-            w2 += aq[R * R + e];
+            const float *aq = reinterpret_cast<const float *>(smem_raw + cta_bytes + q * wbytes);
+            m += (double)aq[e] + (double)aq[RR + e];
+            w2 += (double)aq[2 * RR + e] + (double)aq[3 * RR + e];
         }
         out[e] = m;
-        out[R * R + e] = w2;
+        out[RR + e] = w2;
     }
     for (int s = threadIdx.x; s < R; s += blockDim.x) {
         float m = 0.f;
         for (int q = 0; q < nw; ++q) m = fmaxf(m, red_wmax[q][s]);
-        out[2 * R * R + s] = (double)m;
+        out[2 * RR + s] = (double)m;
     }
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int q = 0; q < nw; ++q) t += red_wm3[q];
-        out[2 * R * R + R] = t;
+        out[2 * RR + R] = t;
     }
+}
+
+__global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__ T,
+                                                       const double *__restrict__ G,
+                                                       const float *__restrict__ W,
+                                                       const float *__restrict__ M3, double *part,
+                                                       int64_t K, int R, int with_m3) {
+    subject_stats<double>(T, G, W, M3, part, K, R, with_m3);
+}
+
+__global__ void __launch_bounds__(256) k_subject_stats_gf(const float *__restrict__ T,
+                                                          const float *__restrict__ Gf,
+                                                          const float *__restrict__ W,
+                                                          const float *__restrict__ M3,
+                                                          double *part, int64_t K, int R,
+                                                          int with_m3) {
+    subject_stats<float>(T, Gf, W, M3, part, K, R, with_m3);
 }
 
 
@@ -858,6 +928,7 @@ int configure_kernels(p2_ctx *c) {
     if (rc == P2_OK) rc = allow_dynamic_smem(k_solve_v_pinv, cap, "k_solve_v_pinv");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_fin_v, cap, "k_fin_v");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_subject_stats, cap, "k_subject_stats");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_subject_stats_gf, cap, "k_subject_stats_gf");
     return rc;
 }
 
@@ -900,15 +971,18 @@ static void launch_gram_t(const p2_ctx *c, const XView &X, const SmallState *st,
     switch (comp_block(c->R)) {
         case 8:
             k_alpha<8, false, S><<<grid, block, L.alpha_smem, s>>>(X, nullptr, V, c->d_H, nullptr,
-                                                                  st, G, nullptr, nullptr, c->R);
+                                                                  st, G, nullptr, nullptr,
+                                                                  nullptr, c->R);
             break;
         case 16:
             k_alpha<16, false, S><<<grid, block, L.alpha_smem, s>>>(X, nullptr, V, c->d_H, nullptr,
-                                                                   st, G, nullptr, nullptr, c->R);
+                                                                   st, G, nullptr, nullptr,
+                                                                   nullptr, c->R);
             break;
         default:
             k_alpha<32, false, S><<<grid, block, L.alpha_smem, s>>>(X, nullptr, V, c->d_H, nullptr,
-                                                                   st, G, nullptr, nullptr, c->R);
+                                                                   st, G, nullptr, nullptr,
+                                                                   nullptr, c->R);
             break;
     }
 }
@@ -933,15 +1007,15 @@ static void launch_alpha_t(p2_ctx *c, const Launch &L, const S *Vprev) {
     switch (comp_block(c->R)) {
         case 8:
             k_alpha<8, MODE3, S><<<grid, block, L.alpha_smem, c->stream>>>(
-                X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_W, c->d_M3, c->R);
+                X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_Gf, c->d_W, c->d_M3, c->R);
             break;
         case 16:
             k_alpha<16, MODE3, S><<<grid, block, L.alpha_smem, c->stream>>>(
-                X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_W, c->d_M3, c->R);
+                X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_Gf, c->d_W, c->d_M3, c->R);
             break;
         default:
             k_alpha<32, MODE3, S><<<grid, block, L.alpha_smem, c->stream>>>(
-                X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_W, c->d_M3, c->R);
+                X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_Gf, c->d_W, c->d_M3, c->R);
             break;
     }
 }
@@ -1034,8 +1108,8 @@ static int enqueue_qstep(p2_ctx *c, int with_fit) {
     int nw = 8;
     while (nw > 1 && cta + nw * stats_warp_bytes(R) > (size_t)c->geo.smem_optin) --nw;
     const size_t ssm = cta + nw * stats_warp_bytes(R);
-    k_subject_stats<<<nb, nw * 32, ssm, s>>>(c->d_T, c->d_G, c->d_W, c->d_M3, c->d_part, K, R,
-                                             with_fit);
+    k_subject_stats_gf<<<nb, nw * 32, ssm, s>>>(c->d_T, c->d_Gf, c->d_W, c->d_M3, c->d_part, K,
+                                                R, with_fit);
     P2_LAUNCH_CHECK("k_subject_stats");
     mark(c, 6);
     k_fin_w<<<1, 256, 0, s>>>(c->d_part, nb, c->d_s, R, with_fit);

@@ -232,8 +232,12 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_alpha(XView X, const S
 // mode 2 (Eq. mttkrp2_3) is M2 = sum_k Y_k^T H S_k = sum_k X_k^T P_k.
 // One warp per subject; the rows go to P (N x R) in stacked-row order.
 // ---------------------------------------------------------------------------
+// F_k rows are padded to a multiple of four floats so they can be read as
+// 16-byte broadcasts.
+static __host__ __device__ __forceinline__ int f_stride(int R) { return (R + 3) & ~3; }
 static __host__ __device__ size_t beta_warp_bytes(int R) {
-    return ((size_t)32 * row_stride(R) + 2 * (size_t)R * R + R) * 4;
+    const size_t b = ((size_t)32 * row_stride(R) + (size_t)R * f_stride(R) + (size_t)R * R + R) * 4;
+    return (b + 15) & ~(size_t)15;
 }
 
 template <int CB, class S>
@@ -246,10 +250,11 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_beta_p(XView X, const 
     float *Hs = reinterpret_cast<float *>(smem_raw);
     const size_t cta_bytes = ((size_t)R * R * 4 + 15) & ~(size_t)15;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int FS = f_stride(R);
     float *zo = reinterpret_cast<float *>(smem_raw + cta_bytes + warp * beta_warp_bytes(R));
-    float *Tk = zo + 32 * RS;
-    float *Fk = Tk + R * R;
-    float *wk = Fk + R * R;
+    float *Fk = zo + 32 * RS;                   // 16-byte aligned: 32 RS floats = 128 RS bytes
+    float *Tk = Fk + R * FS;
+    float *wk = Tk + R * R;
     for (int i = threadIdx.x; i < R * R; i += blockDim.x) Hs[i] = H[i];
     __syncthreads();
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -265,7 +270,11 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_beta_p(XView X, const 
         for (int e = lane; e < R * R; e += 32, us.next(R)) {
             float f = 0.f;
             for (int r = 0; r < R; ++r) f = fmaf(Tk[r * R + us.r], Hs[r * R + us.c], f);
-            Fk[e] = f * wk[us.c];
+            Fk[us.r * FS + us.c] = f * wk[us.c];
+        }
+        for (int e = lane; e < R * (FS - R); e += 32) {          // zero padding columns
+            const int u = e / (FS - R);
+            Fk[u * FS + R + (e - u * (FS - R))] = 0.f;
         }
         __syncwarp();
         for (int64_t cr = r0; cr < r1; cr += 32) {
@@ -276,11 +285,33 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_beta_p(XView X, const 
             gather_rows<CB, false, S>(X, nr, base, len, off, V, nullptr, zo, nullptr, R, RS, lane);
             __syncwarp();
             S *Pr = Pout + (size_t)cr * R;
-            RowCol is(lane, R);
-            for (int e = lane; e < nr * R; e += 32, is.next(R)) {
-                float p = 0.f;
-                for (int u = 0; u < R; ++u) p = fmaf(zo[is.r * RS + u], Fk[u * R + is.c], p);
-                Stor<S>::st(Pr + e, p);
+            // lane i computes row i of Z_k F_k; all lanes read the same F_k row
+            // (a shared-memory broadcast) four columns at a time
+            if (lane < nr) {
+                const float *zr = zo + lane * RS;
+                S *Prow = Pr + (size_t)lane * R;
+                for (int cb = 0; cb < R; cb += CB) {
+                    float acc[CB];
+#pragma unroll
+                    for (int c = 0; c < CB; ++c) acc[c] = 0.f;
+                    for (int u = 0; u < R; ++u) {
+                        const float a = zr[u];
+                        const float4 *f4 = reinterpret_cast<const float4 *>(Fk + u * FS + cb);
+#pragma unroll
+                        for (int q = 0; q < CB / 4; ++q) {
+                            if (cb + 4 * q < R) {
+                                const float4 f = f4[q];
+                                acc[4 * q] = fmaf(a, f.x, acc[4 * q]);
+                                acc[4 * q + 1] = fmaf(a, f.y, acc[4 * q + 1]);
+                                acc[4 * q + 2] = fmaf(a, f.z, acc[4 * q + 2]);
+                                acc[4 * q + 3] = fmaf(a, f.w, acc[4 * q + 3]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < CB; ++c)
+                        if (cb + c < R) Stor<S>::st(Prow + cb + c, acc[c]);
+                }
             }
             __syncwarp();
             base += tot;

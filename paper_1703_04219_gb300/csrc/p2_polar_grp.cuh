@@ -235,6 +235,13 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const double *__restrict__
         int q = R - 1, p = 0, kr = 0;
         bool sweeping = false, failed = false;
         double x = 0.0, z = 0.0, dk = 0.0, ek = 0.0;
+        // Software pipelining: a trip computes the Givens scalars of rotation
+        // kr and applies rotation kr - 1 (kp, cp, sp) to the lanes' rows of Z;
+        // the two are independent, so the serial scalar chain overlaps FP64
+        // work.  A sweep starts with the identity pending and flushes its last
+        // rotation when it ends.
+        int kp = 0;
+        double cp = 1.0, sp = 0.0;
 #pragma unroll 1
         while (true) {
             if (!sweeping) {
@@ -256,6 +263,9 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const double *__restrict__
                 x = dk - mu;
                 z = ek;
                 kr = p;
+                kp = p;
+                cp = 1.0;
+                sp = 0.0;
                 sweeping = true;
                 __syncwarp(gmask);
                 if (gl == 0 && p > 0) e[p - 1] = 0.0;
@@ -263,25 +273,38 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const double *__restrict__
             const double bb = d[kr + 1];
             const double en = (kr + 1 < q) ? e[kr + 1] : 0.0;
             __syncwarp(gmask);
-            const double tt = fma(x, x, z * z);
-            double c = 1.0, s = 0.0, r = 0.0;
-            if (tt > 0.0) {
-                const double ir = p2_rsqrt(tt);
-                c = x * ir;
-                s = -z * ir;
-                r = tt * ir;
+            double za[RPL], zb[RPL];
+#pragma unroll
+            for (int ii = 0; ii < RPL; ++ii) {
+                const int i = gl + PG * ii;
+                if (i < R) {
+                    za[ii] = A(i, kp);
+                    zb[ii] = A(i, kp + 1);
+                }
             }
+            const double tt = fma(x, x, z * z);
+            const bool nz = tt > 0.0;
+            const double ir = p2_rsqrt(nz ? tt : 1.0);
+            const double c = nz ? x * ir : 1.0;
+            const double s = nz ? -z * ir : 0.0;
+            const double r = nz ? tt * ir : 0.0;
             if (kr > p) e[kr - 1] = r;
             const double cc = c * c, ss = s * s, cs = c * s;
             const double cs2g = 2.0 * cs * ek;
             d[kr] = fma(cc, dk, fma(ss, bb, -cs2g));
             const double dk1 = fma(ss, dk, fma(cc, bb, cs2g));
             const double ekn = fma(cs, dk - bb, (cc - ss) * ek);
-            for (int i = gl; i < R; i += PG) {
-                const double zk = A(i, kr), zk1 = A(i, kr + 1);
-                A(i, kr) = fma(c, zk, -s * zk1);
-                A(i, kr + 1) = fma(s, zk, c * zk1);
+#pragma unroll
+            for (int ii = 0; ii < RPL; ++ii) {
+                const int i = gl + PG * ii;
+                if (i < R) {
+                    A(i, kp) = fma(cp, za[ii], -sp * zb[ii]);
+                    A(i, kp + 1) = fma(sp, za[ii], cp * zb[ii]);
+                }
             }
+            kp = kr;
+            cp = c;
+            sp = s;
             if (++kr < q) {
                 z = -s * en;
                 ek = c * en;
@@ -290,6 +313,11 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const double *__restrict__
             } else {
                 d[q] = dk1;
                 e[q - 1] = ekn;
+                for (int i = gl; i < R; i += PG) {      // flush the sweep's last rotation
+                    const double zk = A(i, kp), zk1 = A(i, kp + 1);
+                    A(i, kp) = fma(cp, zk, -sp * zk1);
+                    A(i, kp + 1) = fma(sp, zk, cp * zk1);
+                }
                 sweeping = false;
                 __syncwarp(gmask);
             }

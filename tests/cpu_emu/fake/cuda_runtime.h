@@ -32,6 +32,7 @@ struct dim3 {
     dim3(unsigned a = 1, unsigned b = 1, unsigned c = 1) : x(a), y(b), z(c) {}
 };
 struct emu_uint3 { unsigned x = 0, y = 0, z = 0; };
+struct alignas(16) float4 { float x, y, z, w; };
 extern thread_local emu_uint3 threadIdx, blockIdx;
 extern thread_local dim3 blockDim, gridDim;
 

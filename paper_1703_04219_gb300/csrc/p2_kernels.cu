@@ -44,6 +44,29 @@ static XView xview(const p2_ctx *c) {
     return XView{c->X.subj_row, c->X.subj_nnz, c->X.row_len, c->X.col, c->X.val, c->X.K};
 }
 
+// a + b = s + e exactly (Knuth's TwoSum)
+static __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bv = s - a;
+    e = (a - (s - bv)) + (b - bv);
+}
+// (hi, lo) += x: an unevaluated float pair, error-free up to the rounding of lo
+static __device__ __forceinline__ void pair_add(float &hi, float &lo, float x) {
+    float t, e;
+    two_sum(hi, x, t, e);
+    hi = t;
+    lo += e;
+}
+// (hi, lo) += a * b, the product split exactly with an FMA (Dekker's TwoProduct)
+static __device__ __forceinline__ void pair_fma(float &hi, float &lo, float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    float t, e;
+    two_sum(hi, p, t, e);
+    hi = t;
+    lo += e + pe;
+}
+
 // z rows of up to 32 consecutive rows: z1[i][:] = X(row i, :) V1 and, when
 // TWO, z2[i][:] = X(row i, :) V2.  One lane per row, so a chunk costs one
 // round of dependent loads; the row's components are accumulated in
@@ -116,8 +139,10 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_alpha(XView X, const S
     const int P = R * (R + 1) / 2;
     const int RS = row_stride(R);
     // CTA-shared: G3inv (R*R doubles), H (R*R floats), packed index table
-    double *G3s = reinterpret_cast<double *>(smem_raw);
-    float *Hs = reinterpret_cast<float *>(G3s + R * R);
+    // G3inv = (V^TV * H^TH)^+ (FP64) as an unevaluated float pair hi + lo
+    float *G3h = reinterpret_cast<float *>(smem_raw);
+    float *G3l = G3h + R * R;
+    float *Hs = G3l + R * R;
     uint8_t *pr = reinterpret_cast<uint8_t *>(Hs + R * R);
     uint8_t *pc = pr + P;
     size_t cta_bytes = ((size_t)R * R * 8 + (size_t)R * R * 4 + 2 * (size_t)P + 15) & ~(size_t)15;
@@ -132,7 +157,10 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_alpha(XView X, const S
     float *Cacc = Tk + R * R;                           // R R
 
     for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
-        G3s[i] = st->G3inv[i];
+        const double g = st->G3inv[i];
+        const float gh = (float)g;
+        G3h[i] = gh;
+        G3l[i] = (float)(g - (double)gh);
         Hs[i] = H[i];
     }
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
@@ -217,10 +245,18 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_alpha(XView X, const S
                 Tk[s] = m;
             }
             __syncwarp();
+            // W(k,:) = M3(k,:) G3inv with G3inv as a float pair and the
+            // products accumulated error-free (TwoProduct + TwoSum): FP64-class
+            // accuracy without FP64 instructions, whose issue rate on this
+            // GPU would make these R^2 products the pass's largest cost.
             for (int s = lane; s < R; s += 32) {
-                double w = 0.0;
-                for (int u = 0; u < R; ++u) w = fma((double)Tk[u], G3s[u * R + s], w);
-                W[(size_t)k * R + s] = (float)w;
+                float hi = 0.f, lo = 0.f;
+                for (int u = 0; u < R; ++u) {
+                    const float m = Tk[u];
+                    pair_fma(hi, lo, m, G3h[u * R + s]);
+                    lo = fmaf(m, G3l[u * R + s], lo);
+                }
+                W[(size_t)k * R + s] = hi + lo;
             }
             __syncwarp();
         }
@@ -398,29 +434,6 @@ __global__ void k_m2_columns(const double *__restrict__ segpart, const int64_t *
 // FP64 (W^TW products of FP32 values are exact in FP64).  Block partials,
 // layout [R*R M1][R*R WtW][R wmax][1 wm3], summed later in block order.
 // ---------------------------------------------------------------------------
-// a + b = s + e exactly (Knuth's TwoSum)
-static __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float bv = s - a;
-    e = (a - (s - bv)) + (b - bv);
-}
-// (hi, lo) += x: an unevaluated float pair, error-free up to the rounding of lo
-static __device__ __forceinline__ void pair_add(float &hi, float &lo, float x) {
-    float t, e;
-    two_sum(hi, x, t, e);
-    hi = t;
-    lo += e;
-}
-// (hi, lo) += a * b, the product split exactly with an FMA (Dekker's TwoProduct)
-static __device__ __forceinline__ void pair_fma(float &hi, float &lo, float a, float b) {
-    const float p = a * b;
-    const float pe = fmaf(a, b, -p);
-    float t, e;
-    two_sum(hi, p, t, e);
-    hi = t;
-    lo += e + pe;
-}
-
 // Body of the statistics kernels; G is the packed Gram as float (the copy the
 // alpha pass writes for this kernel) or double (the allocation-free entry
 // point's interface).  Accumulations use float pairs: ~2^-48 relative error
@@ -432,8 +445,8 @@ static __device__ __forceinline__ void subject_stats(const float *__restrict__ T
                                                      const float *__restrict__ M3, double *part,
                                                      int64_t K, int R, int with_m3) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red_wm3[8];
-    __shared__ float red_wmax[8][P2_RMAX];
+    __shared__ double red_wm3[16];
+    __shared__ float red_wmax[16][P2_RMAX];
     const int P = R * (R + 1) / 2;
     const int RR = R * R;
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -545,7 +558,7 @@ __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__
     subject_stats<double>(T, G, W, M3, part, K, R, with_m3);
 }
 
-__global__ void __launch_bounds__(256) k_subject_stats_gf(const float *__restrict__ T,
+__global__ void __launch_bounds__(512) k_subject_stats_gf(const float *__restrict__ T,
                                                           const float *__restrict__ Gf,
                                                           const float *__restrict__ W,
                                                           const float *__restrict__ M3,
@@ -1136,8 +1149,9 @@ static int enqueue_qstep(p2_ctx *c, int with_fit) {
     mark(c, 5);
     const int P = R * (R + 1) / 2;
     const size_t cta = (2 * (size_t)P + 15) & ~(size_t)15;
-    int nw = 8;
-    while (nw > 1 && cta + nw * stats_warp_bytes(R) > (size_t)c->geo.smem_optin) --nw;
+    int nw = 16;                            // up to 16 warps (k_subject_stats_gf's bound)
+    const size_t scap = (size_t)c->geo.smem_optin - 16 * sizeof(double) - 16 * P2_RMAX * sizeof(float);
+    while (nw > 1 && cta + nw * stats_warp_bytes(R) > scap) --nw;
     const size_t ssm = cta + nw * stats_warp_bytes(R);
     k_subject_stats_gf<<<nb, nw * 32, ssm, s>>>(c->d_T, c->d_Gf, c->d_W, c->d_M3, c->d_part, K,
                                                 R, with_fit);

@@ -129,7 +129,7 @@ struct RowCol {
 // with Z_k = X_k Vprev, followed by W(k,:) = M3(k,:) (V^TV * H^TH)^+.
 // ---------------------------------------------------------------------------
 template <int CB, bool MODE3, class S>
-__global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_alpha(XView X, const S *__restrict__ Vprev,
+__global__ void __launch_bounds__(CB >= 32 ? 256 : 512, CB >= 32 ? 1 : 2) k_alpha(XView X, const S *__restrict__ Vprev,
                                                const S *__restrict__ V,
                                                const float *__restrict__ H,
                                                const float *__restrict__ T,
@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_alpha(XView X, const S
                 RowCol rs(lane, R);
                 for (int e = lane; e < R * R; e += 32, rs.next(R)) {
                     float acc = 0.f;
+#pragma unroll 4
                     for (int i = 0; i < nr; ++i) acc = fmaf(zo[i * RS + rs.r], zn[i * RS + rs.c], acc);
                     Cacc[e] += acc;
                 }
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_alpha(XView X, const S
             for (int p = lane; p < P; p += 32) {
                 const int r = pr[p], s = pc[p];
                 float sh = Ghi[p], sl = Glo[p];
+#pragma unroll 4
                 for (int i = 0; i < nr; ++i) {
                     const float a = zn[i * RS + r], b = zn[i * RS + s];
                     const float pa = a * b;
@@ -558,7 +560,7 @@ __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__
     subject_stats<double>(T, G, W, M3, part, K, R, with_m3);
 }
 
-__global__ void __launch_bounds__(512) k_subject_stats_gf(const float *__restrict__ T,
+__global__ void __launch_bounds__(512, 2) k_subject_stats_gf(const float *__restrict__ T,
                                                           const float *__restrict__ Gf,
                                                           const float *__restrict__ W,
                                                           const float *__restrict__ M3,

@@ -38,9 +38,17 @@ __global__ void k_check_subjects(const int64_t *__restrict__ subj_ptr,
     }
 }
 
+// Per row: bounds, strictly increasing columns, finite values; column
+// frequencies (a shared-memory histogram per block when J is small, merged
+// with one global atomic per touched column; global atomics otherwise).
 __global__ void k_check_rows(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                              const float *__restrict__ val, int64_t N, int64_t nnz, int32_t J,
-                             uint16_t *row_len, int *colcount, LoadScratch *ls) {
+                             uint16_t *row_len, int *colcount, LoadScratch *ls, int smem_hist) {
+    extern __shared__ int hist[];
+    if (smem_hist) {
+        for (int j = threadIdx.x; j < J; j += blockDim.x) hist[j] = 0;
+        __syncthreads();
+    }
     int fl = 0;
     int mx = 0;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N;
@@ -59,6 +67,8 @@ __global__ void k_check_rows(const int64_t *__restrict__ row_ptr, const int32_t 
             const float x = val[i];
             if (j < 0 || j >= J || j <= prev) {
                 fl |= FLAG_BAD_COL;
+            } else if (smem_hist) {
+                atomicAdd(&hist[j], 1);
             } else {
                 atomicAdd(&colcount[j], 1);
             }
@@ -67,8 +77,20 @@ __global__ void k_check_rows(const int64_t *__restrict__ row_ptr, const int32_t 
             else mx = max(mx, __float_as_int(fabsf(x)));
         }
     }
-    if (fl) atomicOr(&ls->flags, fl);
-    atomicMax(&ls->maxabs_bits, mx);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (fl) atomicOr(&ls->flags, fl);
+        atomicMax(&ls->maxabs_bits, mx);
+    }
+    if (smem_hist) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < J; j += blockDim.x)
+            if (hist[j]) atomicAdd(&colcount[j], hist[j]);
+    }
 }
 
 // deterministic partial sums of x^2 over fixed non-zero ranges
@@ -234,9 +256,11 @@ int launch_load(p2_ctx *c, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
     P2_CUDA_TRY(cudaMemsetAsync(c->d_colcount, 0, sizeof(int) * (size_t)J, s));
     k_check_subjects<<<4 * nsm, 256, 0, s>>>(d_subj_ptr, d_row_ptr, K, N, c->X.subj_row,
                                              c->X.subj_nnz, ls);
-    if (N > 0)
-        k_check_rows<<<8 * nsm, 256, 0, s>>>(d_row_ptr, d_col, d_val, N, nnz, J, c->X.row_len,
-                                             c->d_colcount, ls);
+    if (N > 0) {
+        const int smem_hist = J <= 12288 ? 1 : 0;            // within the default 48 KB
+        k_check_rows<<<8 * nsm, 256, smem_hist ? (size_t)J * sizeof(int) : 0, s>>>(
+            d_row_ptr, d_col, d_val, N, nnz, J, c->X.row_len, c->d_colcount, ls, smem_hist);
+    }
     const int nb = c->geo.red_blocks;
     k_sumsq<<<nb, 256, 0, s>>>(d_val, nnz, c->d_part);
     P2_CUDA_TRY(cudaGetLastError());

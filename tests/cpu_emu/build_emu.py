@@ -24,7 +24,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libp2emu.so")
 
 _LAUNCH = re.compile(r'([A-Za-z_]\w*(?:<[^<>;()]*>)?)<<<')
-_DYN = re.compile(r'extern __shared__ __align__\(\d+\) ([\w ]+?) (\w+)\[\];')
+_DYN = re.compile(r'extern __shared__ (?:__align__\(\d+\) )?([\w ]+?) (\w+)\[\];')
 
 
 def convert(src: str) -> str:

@@ -66,10 +66,10 @@ static void free_data(p2_ctx *c) {
     dfree(c, &c->X.val, nnz);
     dfree(c, &c->d_perm_old2new, J);
     dfree(c, &c->d_colcount, J);
-    dfree(c, &c->d_V, J * R);
-    dfree(c, &c->d_Vprev, J * R);
-    dfree(c, &c->d_Vh, J * R);
-    dfree(c, &c->d_Vprevh, J * R);
+    dfree(c, &c->d_V, J * v_stride<float>((int)R));
+    dfree(c, &c->d_Vprev, J * v_stride<float>((int)R));
+    dfree(c, &c->d_Vh, J * v_stride<bf16_t>((int)R));
+    dfree(c, &c->d_Vprevh, J * v_stride<bf16_t>((int)R));
     dfree(c, &c->d_Ph, N * R);
     dfree(c, &c->d_Vun, J * R);
     dfree(c, &c->d_M2, J * R);
@@ -111,12 +111,18 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
     P2_TRY(dalloc(c, &c->d_perm_old2new, (size_t)J));
     P2_TRY(dalloc(c, &c->d_colcount, (size_t)J));
     if (c->bf16) {
-        P2_TRY(dalloc(c, &c->d_Vh, (size_t)J * R));
-        P2_TRY(dalloc(c, &c->d_Vprevh, (size_t)J * R));
+        const size_t nv = (size_t)J * v_stride<bf16_t>(R);    // padded rows, zero padding
+        P2_TRY(dalloc(c, &c->d_Vh, nv));
+        P2_TRY(dalloc(c, &c->d_Vprevh, nv));
+        P2_CUDA_TRY(cudaMemsetAsync(c->d_Vh, 0, sizeof(bf16_t) * nv, c->stream));
+        P2_CUDA_TRY(cudaMemsetAsync(c->d_Vprevh, 0, sizeof(bf16_t) * nv, c->stream));
         P2_TRY(dalloc(c, &c->d_Ph, (size_t)N * R));
     } else {
-        P2_TRY(dalloc(c, &c->d_V, (size_t)J * R));
-        P2_TRY(dalloc(c, &c->d_Vprev, (size_t)J * R));
+        const size_t nv = (size_t)J * v_stride<float>(R);     // padded rows, zero padding
+        P2_TRY(dalloc(c, &c->d_V, nv));
+        P2_TRY(dalloc(c, &c->d_Vprev, nv));
+        P2_CUDA_TRY(cudaMemsetAsync(c->d_V, 0, sizeof(float) * nv, c->stream));
+        P2_CUDA_TRY(cudaMemsetAsync(c->d_Vprev, 0, sizeof(float) * nv, c->stream));
         P2_TRY(dalloc(c, &c->d_P, (size_t)N * R));
     }
     P2_TRY(dalloc(c, &c->d_T, (size_t)K * R * R));
@@ -174,17 +180,19 @@ static int set_factors_impl(p2_ctx *c, const float *H, const float *V, const flo
     const int R = c->R;
     const int32_t J = c->X.J;
     const int64_t K = c->X.K;
-    std::vector<float> Vp((size_t)J * R);
+    // relabelled row order, rows padded to the device stride with zeros
+    const int VS = c->bf16 ? v_stride<bf16_t>(R) : v_stride<float>(R);
+    std::vector<float> Vp((size_t)J * VS, 0.f);
     std::vector<uint16_t> Vb;
     for (int32_t j = 0; j < J; ++j)
-        memcpy(&Vp[(size_t)c->h_perm_old2new[j] * R], V + (size_t)j * R, sizeof(float) * R);
+        memcpy(&Vp[(size_t)c->h_perm_old2new[j] * VS], V + (size_t)j * R, sizeof(float) * R);
     if (c->bf16) {                          // V stored bfloat16
         Vb.resize(Vp.size());
         for (size_t i = 0; i < Vp.size(); ++i) Vb[i] = to_bf16_bits(Vp[i]);
         P2_CUDA_TRY(cudaMemcpyAsync(c->d_Vh, Vb.data(), sizeof(uint16_t) * Vb.size(),
                                     cudaMemcpyHostToDevice, c->stream));
     } else {
-        P2_CUDA_TRY(cudaMemcpyAsync(c->d_V, Vp.data(), sizeof(float) * (size_t)J * R,
+        P2_CUDA_TRY(cudaMemcpyAsync(c->d_V, Vp.data(), sizeof(float) * Vp.size(),
                                     cudaMemcpyHostToDevice, c->stream));
     }
     P2_CUDA_TRY(cudaMemcpyAsync(c->d_H, H, sizeof(float) * R * R, cudaMemcpyHostToDevice, c->stream));
@@ -449,7 +457,8 @@ int p2_get_factors(p2_ctx *c, float *H, float *V, float *W) {
     P2_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (H) P2_CUDA_TRY(cudaMemcpy(H, c->d_H, sizeof(float) * R * R, cudaMemcpyDeviceToHost));
     if (V) {
-        std::vector<float> Vp((size_t)c->X.J * R);
+        const int VS = c->bf16 ? v_stride<bf16_t>(R) : v_stride<float>(R);
+        std::vector<float> Vp((size_t)c->X.J * VS);
         if (c->bf16) {
             std::vector<uint16_t> Vb(Vp.size());
             P2_CUDA_TRY(cudaMemcpy(Vb.data(), c->d_Vh, sizeof(uint16_t) * Vb.size(),
@@ -459,7 +468,7 @@ int p2_get_factors(p2_ctx *c, float *H, float *V, float *W) {
             P2_CUDA_TRY(cudaMemcpy(Vp.data(), c->d_V, sizeof(float) * Vp.size(), cudaMemcpyDeviceToHost));
         }
         for (int32_t j = 0; j < c->X.J; ++j)
-            memcpy(V + (size_t)j * R, &Vp[(size_t)c->h_perm_old2new[j] * R], sizeof(float) * R);
+            memcpy(V + (size_t)j * R, &Vp[(size_t)c->h_perm_old2new[j] * VS], sizeof(float) * R);
     }
     if (W) P2_CUDA_TRY(cudaMemcpy(W, c->d_W, sizeof(float) * (size_t)c->X.K * R, cudaMemcpyDeviceToHost));
     return P2_OK;

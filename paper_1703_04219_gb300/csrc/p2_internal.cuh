@@ -73,6 +73,12 @@ template <> struct Stor<bf16_t> {
     static __device__ __forceinline__ void st(bf16_t *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// Row stride of V (and Vprev) in device memory: R rounded up so that a row
+// is a whole number of 16-byte vectors; the padding is zero.
+template <class S> __host__ __device__ inline int v_stride(int R);
+template <> __host__ __device__ inline int v_stride<float>(int R) { return (R + 3) & ~3; }
+template <> __host__ __device__ inline int v_stride<bf16_t>(int R) { return (R + 7) & ~7; }
+
 // Device-resident sparse slices in the internal format.
 struct DevX {
     int64_t K = 0, N = 0, nnz = 0;

@@ -74,6 +74,42 @@ static __device__ __forceinline__ void pair_fma(float &hi, float &lo, float a, f
 // stored with the odd row stride RS (no shared-memory bank conflicts).  With
 // TWO the row is walked once per operand so that only CB accumulators are
 // live (register pressure decides the occupancy of the passes).
+// a[0 .. CB) += x * V(j, cb .. cb + CB) from a 16-byte aligned, zero-padded
+// row segment v, with 16-byte loads; lim = R - cb valid components.
+template <int CB>
+static __device__ __forceinline__ void axpy_row(float *a, float x, const float *__restrict__ v,
+                                                int lim) {
+    const float4 *v4 = reinterpret_cast<const float4 *>(v);
+#pragma unroll
+    for (int q = 0; q < CB / 4; ++q) {
+        if (4 * q < lim) {
+            const float4 t = __ldg(v4 + q);
+            a[4 * q] = fmaf(x, t.x, a[4 * q]);
+            a[4 * q + 1] = fmaf(x, t.y, a[4 * q + 1]);
+            a[4 * q + 2] = fmaf(x, t.z, a[4 * q + 2]);
+            a[4 * q + 3] = fmaf(x, t.w, a[4 * q + 3]);
+        }
+    }
+}
+template <int CB>
+static __device__ __forceinline__ void axpy_row(float *a, float x, const bf16_t *__restrict__ v,
+                                                int lim) {
+    const uint4 *v8 = reinterpret_cast<const uint4 *>(v);
+#pragma unroll
+    for (int q = 0; q < CB / 8; ++q) {
+        if (8 * q < lim) {
+            const uint4 t = __ldg(v8 + q);
+            const unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {       // two bfloat16 per word, low half first
+                a[8 * q + 2 * h] = fmaf(x, __int_as_float((int)(w[h] << 16)), a[8 * q + 2 * h]);
+                a[8 * q + 2 * h + 1] =
+                    fmaf(x, __int_as_float((int)(w[h] & 0xffff0000u)), a[8 * q + 2 * h + 1]);
+            }
+        }
+    }
+}
+
 template <int CB, bool TWO, class S>
 static __device__ __forceinline__ void gather_rows(const XView &X, int nr, int64_t base, int len,
                                                    int off, const S *__restrict__ V1,
@@ -81,6 +117,7 @@ static __device__ __forceinline__ void gather_rows(const XView &X, int nr, int64
                                                    float *z2, int R, int RS, int lane) {
     if (lane >= nr) return;
     const int64_t b0 = base + off;
+    const int VS = v_stride<S>(R);
 #pragma unroll 1
     for (int which = 0; which < (TWO ? 2 : 1); ++which) {
         const S *__restrict__ Vw = which ? V2 : V1;
@@ -92,10 +129,7 @@ static __device__ __forceinline__ void gather_rows(const XView &X, int nr, int64
             for (int e = 0; e < len; ++e) {
                 const int j = X.col[b0 + e];
                 const float x = X.val[b0 + e];
-                const S *v = Vw + (size_t)j * R + cb;
-#pragma unroll
-                for (int c = 0; c < CB; ++c)
-                    if (cb + c < R) a[c] = fmaf(x, Stor<S>::ld(v + c), a[c]);
+                axpy_row<CB>(a, x, Vw + (size_t)j * VS + cb, R - cb);
             }
 #pragma unroll
             for (int c = 0; c < CB; ++c)
@@ -105,6 +139,22 @@ static __device__ __forceinline__ void gather_rows(const XView &X, int nr, int64
 }
 
 static __host__ __device__ __forceinline__ int row_stride(int R) { return R | 1; }
+
+// Rows of small R x R operands read as 16-byte broadcasts are padded to a
+// multiple of four floats.
+static __host__ __device__ __forceinline__ int f_stride(int R) { return (R + 3) & ~3; }
+
+// Per-warp shared memory of the alpha pass: C_k or B_k (R x f_stride),
+// 64 z rows, T_k (R x R), the Gram pairs (2 P) and, for R <= 16 (mode 3 one
+// lane per row), the lanes' mode-3 partial rows (32 x row_stride); a
+// multiple of 16 bytes.
+static __host__ __device__ __forceinline__ size_t alpha_warp_bytes_dev(int R) {
+    const size_t P = (size_t)R * (R + 1) / 2;
+    const size_t zrows = R <= 16 ? 96 : 64;
+    const size_t b = ((size_t)R * f_stride(R) + zrows * row_stride(R) + (size_t)R * R) * 4 +
+                     8 * P;
+    return (b + 15) & ~(size_t)15;
+}
 
 // Row and column of entry e of an n-column row-major array, for e advancing by
 // 32 (one warp's stride) without an integer division per step.
@@ -127,9 +177,12 @@ struct RowCol {
 // so the Gram carries ~2^-48 relative error without using the FP64 pipe)
 // and, with MODE3, the mode-3 MTTKRP row M3(k,:) = coldot(H, T_k Z_k^T Z'_k)
 // with Z_k = X_k Vprev, followed by W(k,:) = M3(k,:) (V^TV * H^TH)^+.
+// For R <= 16 the mode-3 row is taken row by row: with B_k = T_k^T H,
+// M3(k,:) = sum_i z'_i o (B_k^T z_i), one lane per row, B_k read as 16-byte
+// broadcasts; for larger R through C_k = Z_k^T Z'_k and coldot(H, T_k C_k).
 // ---------------------------------------------------------------------------
 template <int CB, bool MODE3, class S>
-__global__ void __launch_bounds__(CB >= 32 ? 256 : 512, CB >= 32 ? 1 : 2) k_alpha(XView X, const S *__restrict__ Vprev,
+__global__ void __launch_bounds__(256, CB >= 32 ? 1 : 3) k_alpha(XView X, const S *__restrict__ Vprev,
                                                const S *__restrict__ V,
                                                const float *__restrict__ H,
                                                const float *__restrict__ T,
@@ -147,14 +200,17 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512, CB >= 32 ? 1 : 2) k_alph
     uint8_t *pc = pr + P;
     size_t cta_bytes = ((size_t)R * R * 8 + (size_t)R * R * 4 + 2 * (size_t)P + 15) & ~(size_t)15;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t warp_bytes = (size_t)P * 8 + ((size_t)64 * RS + 2 * (size_t)R * R) * 4;
-    unsigned char *wb = smem_raw + cta_bytes + warp * warp_bytes;
-    float *Ghi = reinterpret_cast<float *>(wb);
-    float *Glo = Ghi + P;
-    float *zo = Glo + P;                                // 32 RS (zo and zn contiguous: 64 RS scratch)
+    const int FS = f_stride(R);
+    unsigned char *wb = smem_raw + cta_bytes + warp * alpha_warp_bytes_dev(R);
+    float *Cacc = reinterpret_cast<float *>(wb);        // R FS: C_k (R R) or B_k rows (16-byte aligned)
+    float *Bt = Cacc;
+    float *zo = Cacc + R * FS;                          // 32 RS (zo and zn contiguous: 64 RS scratch)
     float *zn = zo + 32 * RS;                           // 32 RS
     float *Tk = zn + 32 * RS;                           // R R
-    float *Cacc = Tk + R * R;                           // R R
+    float *Ghi = Tk + R * R;                            // P
+    float *Glo = Ghi + P;                               // P
+    float *M3p = Glo + P;                               // 32 RS: each lane's mode-3 partial row
+    constexpr bool ROWWISE = CB <= 16;                  // mode 3 one lane per row
 
     for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
         const double g = st->G3inv[i];
@@ -180,8 +236,26 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512, CB >= 32 ? 1 : 2) k_alph
             Ghi[p] = 0.f;
             Glo[p] = 0.f;
         }
-        if (MODE3)
+        if (MODE3 && ROWWISE) {
+            // B_k = T_k^T H into Bt (row u = column u of B_k^T ... rows padded to FS)
+            const float *Tg = T + (size_t)k * R * R;
+            for (int e = lane; e < R * R; e += 32) Tk[e] = Tg[e];
+            __syncwarp();
+            RowCol ur(lane, R);
+            for (int e = lane; e < R * R; e += 32, ur.next(R)) {
+                float b = 0.f;
+                for (int s2 = 0; s2 < R; ++s2) b = fmaf(Tk[s2 * R + ur.r], Hs[s2 * R + ur.c], b);
+                Bt[ur.r * FS + ur.c] = b;
+            }
+            for (int e = lane; e < R * (FS - R); e += 32) {
+                const int u = e / (FS - R);
+                Bt[u * FS + R + (e - u * (FS - R))] = 0.f;
+            }
+            for (int c = 0; c < R; ++c) M3p[lane * RS + c] = 0.f;
+            __syncwarp();
+        } else if (MODE3) {
             for (int e = lane; e < R * R; e += 32) Cacc[e] = 0.f;
+        }
         for (int64_t cr = r0; cr < r1; cr += 32) {
             const int nr = (int)((r1 - cr) < 32 ? (r1 - cr) : 32);
             const int len = (lane < nr) ? (int)X.row_len[cr + lane] : 0;
@@ -193,7 +267,33 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512, CB >= 32 ? 1 : 2) k_alph
                 gather_rows<CB, false, S>(X, nr, base, len, off, V, nullptr, zn, nullptr, R, RS,
                                           lane);
             __syncwarp();
-            if (MODE3) {
+            if (MODE3 && ROWWISE) {
+                if (lane < nr) {                        // u = B_k^T z_i, m3 += z'_i o u
+                    const float *zi = zo + lane * RS;
+                    const float *zpi = zn + lane * RS;
+                    float acc[ROWWISE ? CB : 1];
+#pragma unroll
+                    for (int c = 0; c < (ROWWISE ? CB : 1); ++c) acc[c] = 0.f;
+                    for (int u = 0; u < R; ++u) {
+                        const float zu = zi[u];
+                        const float4 *b4 = reinterpret_cast<const float4 *>(Bt + u * FS);
+#pragma unroll
+                        for (int q = 0; q < (ROWWISE ? CB : 4) / 4; ++q) {
+                            if (4 * q < R) {
+                                const float4 b = b4[q];
+                                acc[4 * q] = fmaf(zu, b.x, acc[4 * q]);
+                                acc[4 * q + 1] = fmaf(zu, b.y, acc[4 * q + 1]);
+                                acc[4 * q + 2] = fmaf(zu, b.z, acc[4 * q + 2]);
+                                acc[4 * q + 3] = fmaf(zu, b.w, acc[4 * q + 3]);
+                            }
+                        }
+                    }
+                    float *m3r = M3p + lane * RS;
+#pragma unroll
+                    for (int c = 0; c < (ROWWISE ? CB : 1); ++c)
+                        if (c < R) m3r[c] = fmaf(zpi[c], acc[c], m3r[c]);
+                }
+            } else if (MODE3) {
                 RowCol rs(lane, R);
                 for (int e = lane; e < R * R; e += 32, rs.next(R)) {
                     float acc = 0.f;
@@ -228,7 +328,15 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512, CB >= 32 ? 1 : 2) k_alph
             float *Gfk = Gf + (size_t)k * P;
             for (int p = lane; p < P; p += 32) Gfk[p] = Ghi[p] + Glo[p];
         }
-        if (MODE3) {
+        if (MODE3 && ROWWISE) {
+            __syncwarp();
+            for (int s = lane; s < R; s += 32) {
+                float m = 0.f;
+                for (int l = 0; l < 32; ++l) m += M3p[l * RS + s];
+                M3[(size_t)k * R + s] = m;
+                Tk[s] = m;
+            }
+        } else if (MODE3) {
             const float *Tg = T + (size_t)k * R * R;
             for (int e = lane; e < R * R; e += 32) Tk[e] = Tg[e];
             __syncwarp();
@@ -246,6 +354,8 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512, CB >= 32 ? 1 : 2) k_alph
                 M3[(size_t)k * R + s] = m;
                 Tk[s] = m;
             }
+        }
+        if (MODE3) {
             __syncwarp();
             // W(k,:) = M3(k,:) G3inv with G3inv as a float pair and the
             // products accumulated error-free (TwoProduct + TwoSum): FP64-class
@@ -270,16 +380,13 @@ __global__ void __launch_bounds__(CB >= 32 ? 256 : 512, CB >= 32 ? 1 : 2) k_alph
 // mode 2 (Eq. mttkrp2_3) is M2 = sum_k Y_k^T H S_k = sum_k X_k^T P_k.
 // One warp per subject; the rows go to P (N x R) in stacked-row order.
 // ---------------------------------------------------------------------------
-// F_k rows are padded to a multiple of four floats so they can be read as
-// 16-byte broadcasts.
-static __host__ __device__ __forceinline__ int f_stride(int R) { return (R + 3) & ~3; }
 static __host__ __device__ size_t beta_warp_bytes(int R) {
     const size_t b = ((size_t)32 * row_stride(R) + (size_t)R * f_stride(R) + (size_t)R * R + R) * 4;
     return (b + 15) & ~(size_t)15;
 }
 
 template <int CB, class S>
-__global__ void __launch_bounds__(CB >= 32 ? 256 : 512) k_beta_p(XView X, const S *__restrict__ V,
+__global__ void __launch_bounds__(256, CB >= 32 ? 1 : 4) k_beta_p(XView X, const S *__restrict__ V,
                                                 const float *__restrict__ H,
                                                 const float *__restrict__ T,
                                                 const float *__restrict__ W, S *Pout, int R) {
@@ -581,7 +688,7 @@ __global__ void __launch_bounds__(256) k_gram_v(const S *__restrict__ V, double 
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] = 0.0;
     for (int64_t j = j0; j < j1; ++j) {
-        const S *vj = V + (size_t)j * R;
+        const S *vj = V + (size_t)j * v_stride<S>(R);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int e = threadIdx.x + q * blockDim.x;
@@ -816,10 +923,12 @@ __global__ void k_solve_v_store(const double *__restrict__ Vun, const SmallState
                                 S *Vprev, int64_t n, int R) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int s = (int)(e % R);
+        const int64_t j = e / R;
+        const int s = (int)(e - j * R);
+        const int64_t d = j * v_stride<S>(R) + s;   // V rows are padded (see v_stride)
         const double nr = st->colnorm[s];
-        Vprev[e] = V[e];
-        Stor<S>::st(V + e, nr > 0.0 ? (float)(Vun[e] / nr) : 0.f);
+        Vprev[d] = V[d];
+        Stor<S>::st(V + d, nr > 0.0 ? (float)(Vun[e] / nr) : 0.f);
     }
 }
 
@@ -881,10 +990,7 @@ static size_t alpha_cta_bytes(int R) {
     const int P = R * (R + 1) / 2;
     return ((size_t)R * R * 8 + (size_t)R * R * 4 + 2 * (size_t)P + 15) & ~(size_t)15;
 }
-static size_t alpha_warp_bytes(int R) {
-    const int P = R * (R + 1) / 2;
-    return (size_t)P * 8 + ((size_t)64 * row_stride(R) + 2 * (size_t)R * R) * 4;
-}
+static size_t alpha_warp_bytes(int R) { return alpha_warp_bytes_dev(R); }
 
 // register block of components in the sparse passes: 8, 16 or 32
 static int comp_block(int R) { return R <= 8 ? 8 : (R <= 16 ? 16 : 32); }
@@ -916,11 +1022,25 @@ static int blocks_per_sm(const p2_ctx *c, size_t smem, int threads) {
     return b < 1 ? 1 : b;
 }
 
+// Blocks of this kernel resident on one SM (registers, shared memory,
+// threads), from the occupancy calculator; the persistent passes launch
+// exactly that many per SM.
+template <class Kern>
+static int resident_blocks(const p2_ctx *c, Kern kern, int threads, size_t smem) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem) != cudaSuccess ||
+        b < 1) {
+        cudaGetLastError();
+        b = blocks_per_sm(c, smem, threads);
+    }
+    return b;
+}
+
 static Launch plan(const p2_ctx *c) {
     Launch L{};
     const int R = c->R;
     const size_t cap = (size_t)c->geo.smem_optin;
-    const int wmax = comp_block(R) >= 32 ? 8 : 16;     // launch bounds of the CB = 32 variants
+    const int wmax = 8;                                 // the passes' launch bounds (256 threads)
     int aw = wmax;
     while (aw > 1 && alpha_cta_bytes(R) + aw * alpha_warp_bytes(R) > cap) --aw;
     L.alpha_warps = aw;
@@ -1012,24 +1132,31 @@ template <class S>
 static void launch_gram_t(const p2_ctx *c, const XView &X, const SmallState *st, double *G,
                           cudaStream_t s) {
     const Launch L = plan(c);
-    dim3 grid(c->geo.nsm * L.alpha_blocks), block(L.alpha_warps * 32);
+    const int nt = L.alpha_warps * 32;
+    dim3 block(nt);
     const S *V = Bufs<S>::V(c);
     switch (comp_block(c->R)) {
-        case 8:
+        case 8: {
+            dim3 grid(c->geo.nsm * resident_blocks(c, k_alpha<8, false, S>, nt, L.alpha_smem));
             k_alpha<8, false, S><<<grid, block, L.alpha_smem, s>>>(X, nullptr, V, c->d_H, nullptr,
                                                                   st, G, nullptr, nullptr,
                                                                   nullptr, c->R);
             break;
-        case 16:
+        }
+        case 16: {
+            dim3 grid(c->geo.nsm * resident_blocks(c, k_alpha<16, false, S>, nt, L.alpha_smem));
             k_alpha<16, false, S><<<grid, block, L.alpha_smem, s>>>(X, nullptr, V, c->d_H, nullptr,
                                                                    st, G, nullptr, nullptr,
                                                                    nullptr, c->R);
             break;
-        default:
+        }
+        default: {
+            dim3 grid(c->geo.nsm * resident_blocks(c, k_alpha<32, false, S>, nt, L.alpha_smem));
             k_alpha<32, false, S><<<grid, block, L.alpha_smem, s>>>(X, nullptr, V, c->d_H, nullptr,
                                                                    st, G, nullptr, nullptr,
                                                                    nullptr, c->R);
             break;
+        }
     }
 }
 
@@ -1046,23 +1173,30 @@ cudaError_t launch_gram(const p2_ctx *c, const XView &X, const SmallState *st, d
 
 template <bool MODE3, class S>
 static void launch_alpha_t(p2_ctx *c, const Launch &L, const S *Vprev) {
-    dim3 grid(c->geo.nsm * L.alpha_blocks), block(L.alpha_warps * 32);
+    const int nt = L.alpha_warps * 32;
+    dim3 block(nt);
     XView X = xview(c);
     const S *V = Bufs<S>::V(c);
     const float *T = c->d_T;
     switch (comp_block(c->R)) {
-        case 8:
+        case 8: {
+            dim3 grid(c->geo.nsm * resident_blocks(c, k_alpha<8, MODE3, S>, nt, L.alpha_smem));
             k_alpha<8, MODE3, S><<<grid, block, L.alpha_smem, c->stream>>>(
                 X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_Gf, c->d_W, c->d_M3, c->R);
             break;
-        case 16:
+        }
+        case 16: {
+            dim3 grid(c->geo.nsm * resident_blocks(c, k_alpha<16, MODE3, S>, nt, L.alpha_smem));
             k_alpha<16, MODE3, S><<<grid, block, L.alpha_smem, c->stream>>>(
                 X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_Gf, c->d_W, c->d_M3, c->R);
             break;
-        default:
+        }
+        default: {
+            dim3 grid(c->geo.nsm * resident_blocks(c, k_alpha<32, MODE3, S>, nt, L.alpha_smem));
             k_alpha<32, MODE3, S><<<grid, block, L.alpha_smem, c->stream>>>(
                 X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_Gf, c->d_W, c->d_M3, c->R);
             break;
+        }
     }
 }
 
@@ -1078,21 +1212,28 @@ static void launch_alpha(p2_ctx *c, const Launch &L) {
 
 template <class S>
 static void launch_beta_p_t(p2_ctx *c, const Launch &L) {
-    dim3 grid(c->geo.nsm * L.beta_blocks), block(L.beta_warps * 32);
+    const int nt = L.beta_warps * 32;
+    dim3 block(nt);
     XView X = xview(c);
     const S *V = Bufs<S>::V(c);
     const float *T = c->d_T;
     S *P = Bufs<S>::P(c);
     switch (comp_block(c->R)) {
-        case 8:
+        case 8: {
+            dim3 grid(c->geo.nsm * resident_blocks(c, k_beta_p<8, S>, nt, L.beta_smem));
             k_beta_p<8, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R);
             break;
-        case 16:
+        }
+        case 16: {
+            dim3 grid(c->geo.nsm * resident_blocks(c, k_beta_p<16, S>, nt, L.beta_smem));
             k_beta_p<16, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R);
             break;
-        default:
+        }
+        default: {
+            dim3 grid(c->geo.nsm * resident_blocks(c, k_beta_p<32, S>, nt, L.beta_smem));
             k_beta_p<32, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R);
             break;
+        }
     }
 }
 

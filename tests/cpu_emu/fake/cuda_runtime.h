@@ -33,6 +33,7 @@ struct dim3 {
 };
 struct emu_uint3 { unsigned x = 0, y = 0, z = 0; };
 struct alignas(16) float4 { float x, y, z, w; };
+struct alignas(16) uint4 { unsigned x, y, z, w; };
 extern thread_local emu_uint3 threadIdx, blockIdx;
 extern thread_local dim3 blockDim, gridDim;
 
@@ -94,6 +95,7 @@ inline cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t = nullptr) {
 }
 inline cudaError_t cudaEventRecordWithFlags(cudaEvent_t e, cudaStream_t s, unsigned) { return cudaEventRecord(e, s); }
 inline cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t a, cudaEvent_t b) { *ms = (float)(*(double *)b - *(double *)a); return cudaSuccess; }
+template <class F> inline cudaError_t cudaOccupancyMaxActiveBlocksPerMultiprocessor(int *n, F, int, size_t) { *n = 1; return cudaSuccess; }
 template <class F> inline cudaError_t cudaFuncGetAttributes(cudaFuncAttributes *a, F) { *a = cudaFuncAttributes{}; return cudaSuccess; }
 template <class F> inline cudaError_t cudaFuncSetAttribute(F, cudaFuncAttribute, int) { return cudaSuccess; }
 template <class T> inline cudaError_t cudaGetSymbolAddress(void **p, T &sym) { *p = (void *)&sym; return cudaSuccess; }
@@ -124,6 +126,7 @@ template <class T> inline unsigned __match_any_sync(unsigned m, T key) { return 
 inline int __popc(unsigned x) { return __builtin_popcount(x); }
 template <class T> inline T __ldg(const T *p) { return *p; }
 inline int __float_as_int(float f) { int i; memcpy(&i, &f, 4); return i; }
+inline float __int_as_float(int i) { float f; memcpy(&f, &i, 4); return f; }
 inline int __double2hiint(double d) { int64_t b; memcpy(&b, &d, 8); return (int)(b >> 32); }
 std::mutex &emu_atomic_mutex();
 template <class T, class U> inline T atomicAdd(T *p, U v) { std::lock_guard<std::mutex> g(emu_atomic_mutex()); T o = *p; *p = o + (T)v; return o; }

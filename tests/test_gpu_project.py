@@ -8,6 +8,8 @@ from tests.helpers import rel_fro
 
 pytestmark = pytest.mark.gpu
 
+EPS32 = 2.0 ** -24
+
 
 @pytest.fixture(scope="module")
 def p2():
@@ -57,11 +59,12 @@ def test_projection_matches_oracle(p2, R, n_iter, tol):
         if kept.size:
             cond = kept[0] / kept[-1]
             assert rel_fro(Qg, Q) < 1e-5 + 1e-6 * cond, (k, rel_fro(Qg, Q), cond)
-    # Per subject, the error of s scales with the conditioning of A_k = X V S H^T at
-    # the start of the step: T_k = C_k H S_k is stored in FP32 (|T| ~ 1/sigma_min) and
-    # Y V = T G cancels down to ~sigma_max, so the relative error is ~1e-8 cond(A_k)
-    # (reproduced on the CPU by rounding T and G to FP32).  Well-conditioned subjects
-    # must meet the FP32 tolerance.
+    # Per subject, the error of s scales with the conditioning of A_k = X V S H^T:
+    # Z = X V, T and G are FP32, i.e. A_k is perturbed by ~eps32 ||A_k||, and the
+    # orthogonal polar factor moves by ||dQ|| <= 2 ||dA|| / sigma_min (first-order
+    # perturbation of the polar decomposition), so each projection step adds up to
+    # ~2 eps32 cond(A_k) relative error and the bound allows 4 eps32 cond(A_k) per
+    # step.  Well-conditioned subjects must meet the FP32 tolerance.
     well = []
     for k in range(req.K):
         Xc, cols = P.subject_block(req, k)
@@ -70,7 +73,7 @@ def test_projection_matches_oracle(p2, R, n_iter, tol):
         sv = sv[sv > 1e-5 * sv[0]]
         cond = sv[0] / sv[-1]
         err = rel_fro(S[k], ref_S[k])
-        assert err < max(tol, 1e-6) + 5e-8 * cond * n_iter, (k, err, cond)
+        assert err < max(tol, 1e-6) + 4 * EPS32 * cond * n_iter, (k, err, cond)
         if cond < 100:
             well.append(k)
     assert len(well) >= 5

@@ -68,7 +68,7 @@ def _bytes_model(X, R):
         "beta_mode2": xb + K * (4 * R * R + 4 * R),
         "alpha_mode3_w_gram": xb + K * (4 * R * R + 8 * P + 8 * R),
         "procrustes": K * (8 * P + 4 * R + 4 * R * R),
-        "subject_stats_mode1": K * (4 * R * R + 8 * P + 8 * R),
+        "subject_stats_mode1": K * (4 * R * R + 4 * P + 8 * R),
     }
 
 

@@ -38,7 +38,7 @@ enum {
     P2_EINVAL = 1,     /* invalid argument or malformed slices */
     P2_ENOMEM = 2,     /* device or host allocation failed */
     P2_ECUDA = 3,      /* a CUDA runtime call failed */
-    P2_ENUMERIC = 4,   /* non-finite value or fixed-point overflow detected */
+    P2_ENUMERIC = 4,   /* non-finite loss detected */
     P2_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
     P2_ESTATE = 6      /* call out of order (e.g. p2_iterate before p2_init) */
 };
@@ -124,8 +124,8 @@ int p2_init(p2_ctx *ctx, const float *H0, const float *V0, const float *W0);
  * one CP-ALS sweep on Y with Algorithm 3's MTTKRPs, S_k = diag(W(k,:))).
  * fit_out (nullable, host): fit after the last iteration, as p2_fit.  With
  * fit_out == NULL the call only enqueues and returns; with fit_out it
- * synchronises and returns P2_ENUMERIC if a non-finite loss or a fixed-point
- * overflow was detected (p2_fit reports the same later otherwise).
+ * synchronises and returns P2_ENUMERIC if a non-finite loss was detected
+ * (p2_fit reports the same later otherwise).
  */
 int p2_iterate(p2_ctx *ctx, int32_t n_iter, double *fit_out);
 

@@ -152,10 +152,8 @@ static int read_flags(p2_ctx *c, int *flags) {
 }
 
 static int flags_status(int flags) {
-    if (flags & (FLAG_FIXED_OVF | FLAG_NONFINITE)) {
-        set_error("numeric problem detected on the device (flags 0x%x: %s%s)", flags,
-                  (flags & FLAG_FIXED_OVF) ? "mode-2 fixed-point range exceeded; " : "",
-                  (flags & FLAG_NONFINITE) ? "non-finite loss; " : "");
+    if (flags & FLAG_NONFINITE) {
+        set_error("numeric problem detected on the device (flags 0x%x: non-finite loss)", flags);
         return P2_ENUMERIC;
     }
     return P2_OK;

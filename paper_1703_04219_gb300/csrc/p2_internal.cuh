@@ -18,7 +18,6 @@ enum : int {
     FLAG_BAD_COL = 2,        // column out of range or not strictly increasing in a row
     FLAG_BAD_VAL = 4,        // non-finite value
     FLAG_EIG_NOCONV = 8,     // an eigen iteration hit its step limit
-    FLAG_FIXED_OVF = 16,     // mode-2 fixed-point term out of range
     FLAG_NONFINITE = 32,     // non-finite loss / factor
 };
 
@@ -43,16 +42,11 @@ struct SmallState {
     double H64[P2_RMAX * P2_RMAX];      // FP32 H widened to FP64
     double P2inv[P2_RMAX * P2_RMAX];    // (W^TW * H^TH)^+ for the V solve
     double G3inv[P2_RMAX * P2_RMAX];    // (V^TV * H^TH)^+ for the W solve
-    double wmax[P2_RMAX];               // max_k |W(k, s)|
     double colnorm[P2_RMAX];            // column norms of the unnormalised V
-    float m2scale[P2_RMAX];             // 2^E_s: fixed-point scale of mode-2 terms
-    float pad_[P2_RMAX];
-    double m2inv[P2_RMAX];              // 2^-E_s
     double wm3;                          // <W, M3>
     double loss;
     double fit;
     double normx2;                       // ||X||_F^2
-    double xbound;                       // max column nnz count * max |x|
     unsigned long long polar_flops;     // FP64 flops executed by k_polar (running total)
     int flags;
     int iter;
@@ -157,7 +151,7 @@ struct p2_ctx {
     double *d_segpart = nullptr; // nseg x R partial sums of the mode-2 reduction
     double *d_Vun = nullptr;    // J x R unnormalised V
     p2::SmallState *d_s = nullptr;
-    double *d_part = nullptr;   // reduction partials (red_blocks x (R*R + 2R + 2))
+    double *d_part = nullptr;   // reduction partials (red_blocks x stats_part_stride(R))
     double *d_part2 = nullptr;  // second partial buffer
     int *d_colcount = nullptr;  // [J] (load time)
 
@@ -176,11 +170,11 @@ static inline __host__ __device__ size_t stats_warp_bytes(int R) {
     return ((size_t)R * R * 16 + ((size_t)2 * R * R + R) * 4 + 15) & ~(size_t)15;
 }
 // per-subject statistics after the Q-step (p2_kernels.cu): block partials
-// [R*R M1][R*R WtW][R max|W|][1 <W,M3>] over fixed contiguous subject ranges;
+// [R*R M1][R*R WtW][1 <W,M3>] over fixed contiguous subject ranges;
 // stats_part_stride(R) doubles per block (also the per-block size of the
 // other partial buffers, which need at most R*R)
 static inline __host__ __device__ size_t stats_part_stride(int R) {
-    return 2 * (size_t)R * R + R + 1;
+    return 2 * (size_t)R * R + 1;
 }
 __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__ T,
                                                        const double *__restrict__ G,
@@ -190,7 +184,7 @@ __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__
 // per-iteration pieces (p2_kernels.cu)
 int enqueue_prologue(p2_ctx *c);     // Q-step + mode-1 MTTKRP for the current (H, V, W)
 int enqueue_iteration(p2_ctx *c);    // one ALS iteration
-int enqueue_factor_stats(p2_ctx *c); // HtH, VtV, WtW, wmax for freshly set factors
+int enqueue_factor_stats(p2_ctx *c); // HtH, VtV, WtW for freshly set factors
 int configure_kernels(p2_ctx *c);    // smem attributes etc.
 // Procrustes step (p2_polar.cu)
 int polar_configure(p2_ctx *c);

@@ -7,7 +7,7 @@
 // Q_k or Y_k (identities that follow from the paper's definitions):
 //   Z_k = X_k V                       (never stored; recomputed per pass)
 //   A_k = Z_k S_k H^T                 (Procrustes input: H S_k V^T X_k^T = A_k^T)
-//   G_k = Z_k^T Z_k                   (accumulated in FP64)
+//   G_k = Z_k^T Z_k                   (error-free FP32 pairs: FP64-accurate)
 //   C_k = (A_k^T A_k)^{+1/2}, Q_k = A_k C_k   (polar factor, FP64)
 //   T_k = C_k H S_k, so Q_k = Z_k T_k^T and Y_k = Q_k^T X_k = T_k Z_k^T X_k
 //   mode 1 (Eq. mttkrp1_3):  Y_k V = T_k G_k
@@ -16,9 +16,10 @@
 // so an iteration streams X twice: pass beta (mode 2) and pass alpha (mode
 // 3, the W row, and the next Q-step's Gram), with the R x R work in between.
 //
-// Determinism: every reduction over subjects uses fixed per-block partials
-// summed in block order; the only atomics are 64-bit integer adds of
-// fixed-point mode-2 terms, which are associative.
+// Determinism: every reduction over subjects or non-zeros uses fixed
+// per-block partials summed in a fixed order; there are no floating-point
+// atomics (integer atomics only count columns at load time, raise error
+// flags and count flops).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -537,11 +538,12 @@ __global__ void k_m2_columns(const double *__restrict__ segpart, const int64_t *
 // ---------------------------------------------------------------------------
 // Per-subject statistics after the Q-step, in one pass over the subjects:
 //   mode 1 (Eq. mttkrp1_3): M1 = sum_k (T_k G_k) * 1 W(k,:)   (Y_k V = T_k G_k),
-//   W^TW, max_k |W(k, s)| and <W, M3>.
+//   W^TW and <W, M3>.
 // One block per fixed contiguous subject range and one warp per subject at a
-// time (no block barriers in the loop).  M1 products in FP32, accumulation in
-// FP64 (W^TW products of FP32 values are exact in FP64).  Block partials,
-// layout [R*R M1][R*R WtW][R wmax][1 wm3], summed later in block order.
+// time (no block barriers in the loop).  M1 products in FP32; the sums over
+// subjects (and W^TW's products, split exactly) accumulate as float pairs.
+// Block partials in FP64, layout [R*R M1][R*R WtW][1 wm3], summed later in
+// block order.
 // ---------------------------------------------------------------------------
 // Body of the statistics kernels; G is the packed Gram as float (the copy the
 // alpha pass writes for this kernel) or double (the allocation-free entry
@@ -555,7 +557,6 @@ static __device__ __forceinline__ void subject_stats(const float *__restrict__ T
                                                      int64_t K, int R, int with_m3) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_wm3[16];
-    __shared__ float red_wmax[16][P2_RMAX];
     const int P = R * (R + 1) / 2;
     const int RR = R * R;
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -589,7 +590,6 @@ static __device__ __forceinline__ void subject_stats(const float *__restrict__ T
     const int64_t k0 = (int64_t)blockIdx.x * per;
     const int64_t k1 = (k0 + per < K) ? (k0 + per) : K;
     float wm3h = 0.f, wm3l = 0.f;
-    float wmx[2] = {0.f, 0.f};
     const int r0 = lane / R, c0 = lane - (lane / R) * R;   // first entry of this lane
     for (int64_t k = k0 + warp; k < k1; k += nw) {
         const float *Tg = T + (size_t)k * RR;
@@ -607,7 +607,6 @@ static __device__ __forceinline__ void subject_stats(const float *__restrict__ T
             if (s < R) {
                 const float v = W[(size_t)k * R + s];
                 ws[s] = v;
-                wmx[t] = fmaxf(wmx[t], fabsf(v));
                 if (with_m3) pair_fma(wm3h, wm3l, v, M3[(size_t)k * R + s]);
             }
         }
@@ -631,9 +630,6 @@ static __device__ __forceinline__ void subject_stats(const float *__restrict__ T
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wm3 += __shfl_down_sync(FULLMASK, wm3, o);
     if (lane == 0) red_wm3[warp] = wm3;
-#pragma unroll
-    for (int t = 0; t < 2; ++t)
-        if (lane + 32 * t < P2_RMAX) red_wmax[warp][lane + 32 * t] = wmx[t];
     __syncthreads();
     const size_t stride = stats_part_stride(R);
     double *out = part + (size_t)blockIdx.x * stride;
@@ -647,15 +643,10 @@ static __device__ __forceinline__ void subject_stats(const float *__restrict__ T
         out[e] = m;
         out[RR + e] = w2;
     }
-    for (int s = threadIdx.x; s < R; s += blockDim.x) {
-        float m = 0.f;
-        for (int q = 0; q < nw; ++q) m = fmaxf(m, red_wmax[q][s]);
-        out[2 * RR + s] = (double)m;
-    }
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int q = 0; q < nw; ++q) t += red_wm3[q];
-        out[2 * RR + R] = t;
+        out[2 * RR] = t;
     }
 }
 
@@ -947,7 +938,7 @@ __global__ void __launch_bounds__(256) k_fin_v(const double *__restrict__ part, 
     if (with_g3) cta_pinv(A, U, st->G3inv, R, &st->flags);
 }
 
-// Sum the subject-statistics partials: W^TW, max |W|, <W, M3>; loss / fit.
+// Sum the subject-statistics partials: W^TW, <W, M3>; loss / fit.
 // (M1 stays in the partials; the H solve sums it.)
 __global__ void k_fin_w(const double *__restrict__ part, int nparts, SmallState *st, int R,
                         int with_fit) {
@@ -961,18 +952,13 @@ __global__ void k_fin_w(const double *__restrict__ part, int nparts, SmallState 
         lsum += s * st->HtH[e] * st->VtV[e];
     }
     red[threadIdx.x] = lsum;
-    for (int s = threadIdx.x; s < R; s += blockDim.x) {
-        double mx = 0.0;
-        for (int b = 0; b < nparts; ++b) mx = fmax(mx, part[(size_t)b * stride + 2 * R * R + s]);
-        st->wmax[s] = mx;
-    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int i = 0; i < (int)blockDim.x; ++i) t += red[i];
         if (with_fit) {
             double wm3 = 0.0;
-            for (int b = 0; b < nparts; ++b) wm3 += part[(size_t)b * stride + 2 * R * R + R];
+            for (int b = 0; b < nparts; ++b) wm3 += part[(size_t)b * stride + 2 * R * R];
             st->wm3 = wm3;
             const double loss = st->normx2 - 2.0 * wm3 + t;
             st->loss = loss;

@@ -18,7 +18,6 @@ namespace p2 {
 
 struct LoadScratch {
     int flags;
-    int maxabs_bits;
 };
 
 __global__ void k_check_subjects(const int64_t *__restrict__ subj_ptr,
@@ -50,7 +49,6 @@ __global__ void k_check_rows(const int64_t *__restrict__ row_ptr, const int32_t 
         __syncthreads();
     }
     int fl = 0;
-    int mx = 0;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = row_ptr[r], e = row_ptr[r + 1];
@@ -74,18 +72,11 @@ __global__ void k_check_rows(const int64_t *__restrict__ row_ptr, const int32_t 
             }
             prev = j;
             if (!isfinite(x)) fl |= FLAG_BAD_VAL;
-            else mx = max(mx, __float_as_int(fabsf(x)));
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        fl |= __shfl_xor_sync(0xffffffffu, fl, o);
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (fl) atomicOr(&ls->flags, fl);
-        atomicMax(&ls->maxabs_bits, mx);
-    }
+    for (int o = 16; o > 0; o >>= 1) fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+    if ((threadIdx.x & 31) == 0 && fl) atomicOr(&ls->flags, fl);
     if (smem_hist) {
         __syncthreads();
         for (int j = threadIdx.x; j < J; j += blockDim.x)
@@ -293,8 +284,6 @@ int launch_load(p2_ctx *c, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
     for (int b = 0; b < nb; ++b) nx2 += hp[b];
     delete[] hp;
     // relabel: decreasing frequency, ties by original id
-    int maxcount = 0;
-    for (int j = 0; j < J; ++j) maxcount = cc[j] > maxcount ? cc[j] : maxcount;
     {
         int32_t *order = c->h_perm_new2old;
         for (int j = 0; j < J; ++j) order[j] = j;
@@ -327,11 +316,7 @@ int launch_load(p2_ctx *c, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
         int rc = build_csc(c, d_row_ptr, count_new.data(), N, nnz, J);
         if (rc != P2_OK) return rc;
     }
-    float maxabs;
-    memcpy(&maxabs, &h.maxabs_bits, sizeof(float));
-    const double xbound = (double)maxcount * (double)maxabs;
     P2_CUDA_TRY(cudaMemcpyAsync(&c->d_s->normx2, &nx2, sizeof(double), cudaMemcpyHostToDevice, s));
-    P2_CUDA_TRY(cudaMemcpyAsync(&c->d_s->xbound, &xbound, sizeof(double), cudaMemcpyHostToDevice, s));
     P2_CUDA_TRY(cudaStreamSynchronize(s));
     return P2_OK;
 }

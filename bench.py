@@ -36,6 +36,12 @@ import numpy as np  # noqa: E402
 METRIC = "PARAFAC2-ALS s/iter & nnz/s, 63M-500M nnz, R=10/40; HBM roofline fraction"
 UNIT = "nnz/s"
 FP64_PEAK_TFLOPS = 1.25        # GB300 FP64 (nominal; measured 1.19 with an FMA loop)
+# The Procrustes step runs in double-word (float-float) arithmetic on the FP32
+# pipe: 152 SMs x 128 FP32 lanes x 2.07 GHz = 40.3e12 FP32 instructions/s,
+# and a double-word multiply-accumulate (product with its error terms, TwoSum,
+# low-part update) is 12 of them, i.e. 2 flops per 12 instructions.
+DW_INSTR_PER_FMA = 12
+DW_PEAK_TFLOPS = 152 * 128 * 2.07e9 * 2 / DW_INSTR_PER_FMA / 1e12
 PHASES = ("h_solve", "beta_mode2", "v_solve", "alpha_mode3_w_gram", "procrustes",
           "subject_stats_mode1", "fit")
 
@@ -276,11 +282,14 @@ def run_p2(args, w):
     if dom == "procrustes":
         flops = t["flops"]
         ach = flops / (phase_ms[dom] / 1e3) / 1e12
-        roof = {"kernel": "k_polar_reg/k_polar_smem (FP64 Procrustes, lane per subject)",
-                "bound": "alu",
-                "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "FP64 nominal 1.25 TFLOP/s "
-                "(recipe table); measured FMA loop 1.19",
+        kname = ("k_polar_reg (double-word Procrustes, one lane per subject)" if R <= 12 else
+                 "k_polar_grp (double-word Procrustes, eight lanes per subject)")
+        roof = {"kernel": kname, "bound": "alu",
+                "achieved": ach, "peak": DW_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / DW_PEAK_TFLOPS,
+                "peak_source": "derived: FP32 pipe 152 SMs x 128 lanes x 2.07 GHz, "
+                f"{DW_INSTR_PER_FMA} FP32 instructions per double-word multiply-add",
+                "vs_fp64_nominal": ach / FP64_PEAK_TFLOPS,
                 "algorithmic_flops_per_launch": flops,
                 "traffic": _traffic("k_polar", w.name)}
     else:
@@ -313,7 +322,8 @@ def run_p2(args, w):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "s_per_iter": ms_step / 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 storage and SpMM (Gram: error-free f32 pairs), f64 Procrustes and solves", "data": "synthetic",
+            "dtype": "f32 storage and SpMM (Gram: error-free f32 pairs), double-word (f32 pair) "
+                     "Procrustes, f64 R x R solves", "data": "synthetic",
             "config": {"workload": _workload_desc(w, X), "K": X.K, "J": X.J, "R": R,
                        "nnz": int(X.nnz), "rows": int(X.n_rows),
                        "l2": "inputs larger than L2: X (~6 B/nnz) streamed twice per step",

@@ -1,0 +1,273 @@
+// Symmetric eigen-decomposition of one small matrix by one thread, in
+// double-word arithmetic (p2_dw.cuh).
+//
+// Used by the Procrustes step (Section 3.2): with one GPU lane per subject,
+// the R x R matrix A_k^T A_k is decomposed as Z diag(d) Z^T so that the
+// polar factor's pseudo-inverse square root can be formed.
+//
+// Method (Golub & Van Loan, "Matrix Computations", 4th ed., Algorithms
+// 5.1.1, 8.3.1 and 8.3.2): Householder reduction to tridiagonal form with
+// backward accumulation of the orthogonal factor, then implicit symmetric QR
+// steps with the Wilkinson shift and deflation, rotations accumulated into
+// the eigenvector matrix.  Both halves are normwise backward stable, so the
+// double-word arithmetic's normwise error bounds (a few 2^-48) carry over to
+// the decomposition.
+//
+// The matrix and vectors are reached through accessor objects so the same
+// code runs on interleaved shared memory (element e of thread t at
+// base[e * stride + t]) on the GPU and on plain arrays on the host.
+#pragma once
+
+#include "p2_dw.cuh"
+
+namespace p2 {
+
+struct DwMat {
+    dw *base;
+    int stride;
+    int n;
+    P2_HD dw &operator()(int i, int j) const { return base[(size_t)(i * n + j) * stride]; }
+};
+
+struct DwVec {
+    dw *base;
+    int stride;
+    P2_HD dw &operator[](int i) const { return base[(size_t)i * stride]; }
+};
+
+// Reduce the symmetric matrix held in the lower triangle of A (n x n) to
+// tridiagonal form T = Q^T A Q, then overwrite A with Q (full storage).
+// On return d[0..n) is diag(T) and e[0..n-1) its sub-diagonal.  d serves as
+// the Householder work vector during the reduction, and the Householder
+// scalars beta_k are kept in the (unused) upper triangle at A(k, k+1) until
+// the backward accumulation consumes them.  N > 0 fixes n at compile time.
+template <int N>
+P2_HD void tridiagonalize_dw(int n_rt, DwMat A, DwVec d, DwVec e) {
+    const int n = N > 0 ? N : n_rt;
+    const dw one = dw_f(1.f), zero = dw_f(0.f);
+    DwVec t = d;
+#pragma unroll 1
+    for (int k = 0; k + 2 < n; ++k) {
+        // Householder reflector P = I - b v v^T with P x = beta e_1 for
+        // x = A[k+1:n, k], in the normalisation that squares no small
+        // quantity: beta = -sign(x0) ||x||, b = (beta - x0) / beta in [1, 2],
+        // v = [1, x(2:) / (x0 - beta)] with |v_i| <= 1.  A column whose part
+        // below x0 has squared norm under DW_TINY2 (entries below ~2^-48
+        // of the scaled matrix's unit norm) is left as it is, a perturbation
+        // of the order of the rounding, so every square stays in range.
+        dwacc sg = acc_zero();
+        for (int i = k + 2; i < n; ++i) acc_sqr(sg, A(i, k));
+        const dw sigma = acc_val(sg);
+        const dw x0 = A(k + 1, k);
+        if (!(sigma.h >= DW_TINY2)) {
+            A(k, k + 1) = zero;     // b_k
+            e[k] = x0;
+            continue;
+        }
+        dwacc m2 = acc_from(sigma);
+        acc_sqr(m2, x0);
+        const dw mu = dw_sqrt(acc_val(m2));
+        const dw beta = (x0.h >= 0.f) ? dw_neg(mu) : mu;
+        const dw b = dw_div(dw_sub(beta, x0), beta);
+        const dw inv_v0 = dw_recip(dw_sub(x0, beta));
+        for (int i = k + 2; i < n; ++i) A(i, k) = dw_mul(A(i, k), inv_v0);
+        A(k, k + 1) = b;
+        e[k] = beta;
+        // p = b A22 v (A22 symmetric, lower triangle stored), K = b/2 p^T v
+        dwacc pv = acc_zero();
+        for (int i = k + 1; i < n; ++i) {
+            dwacc s = acc_from(A(i, k + 1));          // v_{k+1} = 1
+            for (int j = k + 2; j < n; ++j) acc_fma(s, (j <= i) ? A(i, j) : A(j, i), A(j, k));
+            const dw si = dw_mul(acc_val(s), b);
+            t[i] = si;
+            if (i == k + 1)
+                acc_add(pv, si);
+            else
+                acc_fma(pv, si, A(i, k));
+        }
+        const dw nK = dw_neg(dw_mul(dw_scale(b, 0.5f), acc_val(pv)));
+        t[k + 1] = dw_add(t[k + 1], nK);                 // w = p - K v
+        for (int i = k + 2; i < n; ++i) t[i] = dw_fma(nK, A(i, k), t[i]);
+        for (int i = k + 1; i < n; ++i) {                // A22 -= v w^T + w v^T
+            const dw nvi = dw_neg((i == k + 1) ? one : A(i, k));
+            const dw nwi = dw_neg(t[i]);
+            for (int j = k + 1; j <= i; ++j) {
+                dwacc a = acc_from(A(i, j));
+                acc_fma(a, nvi, t[j]);
+                if (j == k + 1)
+                    acc_add(a, nwi);
+                else
+                    acc_fma(a, nwi, A(j, k));
+                A(i, j) = acc_val(a);
+            }
+        }
+    }
+    if (n >= 2) e[n - 2] = A(n - 1, n - 2);
+    for (int i = 0; i < n; ++i) d[i] = A(i, i);
+
+    // Backward accumulation Q = P_0 P_1 ... P_{n-3}, in place.
+    if (n == 1) {
+        A(0, 0) = one;
+        return;
+    }
+    A(n - 1, n - 1) = one;
+    A(n - 2, n - 2) = one;
+    A(n - 1, n - 2) = zero;
+    A(n - 2, n - 1) = zero;
+#pragma unroll 1
+    for (int k = n - 3; k >= 0; --k) {
+        const dw b = A(k, k + 1);
+        A(k + 1, k + 1) = one;
+        for (int j = k + 2; j < n; ++j) {
+            A(k + 1, j) = zero;
+            A(j, k + 1) = zero;
+        }
+        if (b.h == 0.f) continue;
+        // column k+1 is e_{k+1}: its update is 1 - b and -b v_i
+        const dw nb = dw_neg(b);
+        A(k + 1, k + 1) = dw_add(one, nb);
+        for (int i = k + 2; i < n; ++i) A(i, k + 1) = dw_mul(nb, A(i, k));
+        for (int c = k + 2; c < n; ++c) {
+            dwacc s = acc_zero();                      // A(k+1, c) = 0 here
+            for (int i = k + 2; i < n; ++i) acc_fma(s, A(i, k), A(i, c));
+            const dw ns = dw_mul(acc_val(s), nb);
+            A(k + 1, c) = ns;
+            for (int i = k + 2; i < n; ++i) A(i, c) = dw_fma(ns, A(i, k), A(i, c));
+        }
+    }
+    A(0, 0) = one;
+    for (int j = 1; j < n; ++j) {
+        A(0, j) = zero;
+        A(j, 0) = zero;
+    }
+}
+
+// Implicit symmetric QR with Wilkinson shift on the tridiagonal (d, e);
+// rotations are accumulated into the columns of Z (n x n).  Returns the
+// number of QR steps taken, or -1 if max_steps was exceeded (d then holds
+// the current, partly converged, diagonal).  *rotations (if given) is
+// incremented by the number of Givens rotations applied.
+//
+// One flat loop, one Givens rotation per trip, so that the lanes of a warp
+// run the rotation body together whatever their sweep boundaries.  The
+// trip that forms rotation k applies rotation k - 1 to Z (the two are
+// independent, so the serial scalar recurrence overlaps the vector work);
+// the pending rotation carries over sweep boundaries and is flushed once at
+// the end.  Each rotation is formed from one reciprocal square root:
+// c = x / r, s = -z / r, r = t / sqrt(t) with t = x^2 + z^2, after scaling
+// (x, z) by a power of two so that t cannot underflow (FP32's exponent range
+// is far narrower than FP64's, and the converging sub-diagonal and the bulge
+// can both become tiny).
+template <int N>
+P2_HD int tridiagonal_qr_dw(int n_rt, DwMat Z, DwVec d, DwVec e, int max_steps,
+                            int *rotations = nullptr) {
+    const int n = N > 0 ? N : n_rt;
+    const dw one = dw_f(1.f), zero = dw_f(0.f);
+    float an = 0.f;
+    for (int i = 0; i < n; ++i) {
+        float r = fabsf(d[i].h);
+        if (i + 1 < n) r += fabsf(e[i].h);
+        if (i > 0) r += fabsf(e[i - 1].h);
+        an = fmaxf(an, r);
+    }
+    const int tiny_ex = f_expo(an) - DW_DEFLATE_BITS;
+    int steps = 0, rot = 0, status = 0;
+    int q = n - 1, p = 0, kr = 0;
+    bool sweeping = false;
+    dw x = zero, z = zero, dk = zero, ek = zero;
+    int kp = 0;
+    dw cp = one, sp = zero;
+#pragma unroll 1
+    while (true) {
+        if (!sweeping) {
+            while (q > 0 && dw_negligible(e[q - 1], d[q - 1], d[q], tiny_ex)) --q;
+            if (q == 0) break;
+            p = q - 1;
+            while (p > 0 && !dw_negligible(e[p - 1], d[p - 1], d[p], tiny_ex)) --p;
+            if (++steps > max_steps) {
+                status = -1;
+                break;
+            }
+            rot += q - p;
+            // Wilkinson shift from the trailing 2 x 2 block
+            const dw eq = e[q - 1];
+            const dw dd = dw_scale(dw_sub(d[q - 1], d[q]), 0.5f);
+            dwacc hh = acc_zero();
+            acc_sqr(hh, dd);
+            acc_sqr(hh, eq);
+            const dw h = dw_sqrt(acc_val(hh));
+            const dw den = (dd.h >= 0.f) ? dw_add(dd, h) : dw_sub(dd, h);
+            const dw mu = dw_sub(d[q], dw_div(dw_sqr(eq), den));
+            dk = d[p];
+            ek = e[p];
+            x = dw_sub(dk, mu);
+            z = ek;
+            kr = p;
+            sweeping = true;
+            if (p > 0) e[p - 1] = zero;
+        }
+        const dw bb = d[kr + 1];
+        const dw en = (kr + 1 < q) ? e[kr + 1] : zero;
+        // (x, z) scaled by a power of two before squaring: t in [1, 8)
+        const int exx = f_expo(x.h), exz = f_expo(z.h);
+        const int ex = exx > exz ? exx : exz;
+        const bool nz = ex > 0;
+        const float xsc = f_pow2(127 - ex);
+        const dw xs = dw_scale(x, xsc), zs = dw_scale(z, xsc);
+        dwacc ta = acc_zero();
+        acc_sqr(ta, xs);
+        acc_sqr(ta, zs);
+        const dw tt = acc_val(ta);
+        const dw ir = dw_rsqrt(nz ? tt : one);
+        const dw c = nz ? dw_mul(xs, ir) : one;
+        const dw s = nz ? dw_neg(dw_mul(zs, ir)) : zero;
+        if (kr > p) e[kr - 1] = nz ? dw_scale(dw_mul(tt, ir), f_pow2(ex - 127)) : zero;
+        const dw cc = dw_sqr(c), ss = dw_sqr(s), cs = dw_mul(c, s);
+        const dw cs2g = dw_scale(dw_mul(cs, ek), 2.f);
+        dwacc a0 = acc_from(dw_neg(cs2g));
+        acc_fma(a0, cc, dk);
+        acc_fma(a0, ss, bb);
+        d[kr] = acc_val(a0);
+        dwacc a1 = acc_from(cs2g);
+        acc_fma(a1, ss, dk);
+        acc_fma(a1, cc, bb);
+        const dw dk1 = acc_val(a1);
+        dwacc a2 = acc_zero();
+        acc_fma(a2, cs, dw_sub(dk, bb));
+        acc_fma(a2, dw_sub(cc, ss), ek);
+        const dw ekn = acc_val(a2);
+        {   // pending rotation (kp, cp, sp) on columns kp, kp + 1 of Z
+            const dw nsp = dw_neg(sp);
+            for (int i = 0; i < n; ++i) {
+                const dw za = Z(i, kp), zb = Z(i, kp + 1);
+                Z(i, kp) = dw_dot2(cp, za, nsp, zb);
+                Z(i, kp + 1) = dw_dot2(sp, za, cp, zb);
+            }
+        }
+        kp = kr;
+        cp = c;
+        sp = s;
+        if (++kr < q) {
+            z = dw_neg(dw_mul(s, en));
+            ek = dw_mul(c, en);
+            x = ekn;
+            dk = dk1;
+        } else {
+            d[q] = dk1;
+            e[q - 1] = ekn;
+            sweeping = false;
+        }
+    }
+    if (n > 1) {   // flush the last rotation
+        const dw nsp = dw_neg(sp);
+        for (int i = 0; i < n; ++i) {
+            const dw za = Z(i, kp), zb = Z(i, kp + 1);
+            Z(i, kp) = dw_dot2(cp, za, nsp, zb);
+            Z(i, kp + 1) = dw_dot2(sp, za, cp, zb);
+        }
+    }
+    if (rotations) *rotations += rot;
+    return status < 0 ? -1 : steps;
+}
+
+}  // namespace p2

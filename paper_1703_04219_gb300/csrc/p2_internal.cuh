@@ -7,6 +7,7 @@
 #include <string>
 
 #include "../../include/p2.h"
+#include "p2_dw.cuh"
 
 #define P2_RMAX 64
 
@@ -143,7 +144,7 @@ struct p2_ctx {
     p2::bf16_t *d_Vh = nullptr, *d_Vprevh = nullptr, *d_Ph = nullptr;
     float *d_W = nullptr;       // K x R
     float *d_T = nullptr;       // K x R x R
-    double *d_G = nullptr;      // K x P (packed lower Gram of Z_k)
+    p2::dw *d_G = nullptr;      // K x P packed lower Gram of Z_k, double-word (hi + lo)
     float *d_Gf = nullptr;      // K x P the same rounded to float (mode-1 statistics)
     float *d_M3 = nullptr;      // K x R
     double *d_M2 = nullptr;     // J x R (relabelled rows)
@@ -189,13 +190,13 @@ int configure_kernels(p2_ctx *c);    // smem attributes etc.
 // Procrustes step (p2_polar.cu)
 int polar_configure(p2_ctx *c);
 cudaError_t launch_polar(p2_ctx *c);
-cudaError_t launch_polar_on(const p2_ctx *c, const double *G, const float *W, SmallState *st,
+cudaError_t launch_polar_on(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
                             float *T, int64_t K, cudaStream_t s);
 // Gram of Z_k = X_k V for a batch of new subjects (p2_kernels.cu)
-cudaError_t launch_gram(const p2_ctx *c, const XView &X, const SmallState *st, double *G,
+cudaError_t launch_gram(const p2_ctx *c, const XView &X, const SmallState *st, dw *G,
                         cudaStream_t s);
 // R > 12: grouped Procrustes kernel (p2_polar_grp.cu)
 cudaError_t polar_grp_configure(int cap);
-cudaError_t launch_polar_grp(const p2_ctx *c, const double *G, const float *W, SmallState *st,
+cudaError_t launch_polar_grp(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
                              float *T, int64_t K, cudaStream_t s, double rtol2);
 }  // namespace p2

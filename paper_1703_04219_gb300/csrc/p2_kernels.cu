@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 3) k_alpha(XView X, const 
                                                const S *__restrict__ V,
                                                const float *__restrict__ H,
                                                const float *__restrict__ T,
-                                               const SmallState *__restrict__ st, double *G,
+                                               const SmallState *__restrict__ st, dw *G,
                                                float *Gf, float *W, float *M3, int R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = R * (R + 1) / 2;
@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 3) k_alpha(XView X, const 
             __syncwarp();
             base += tot;
         }
-        double *Gk = G + (size_t)k * P;
-        for (int p = lane; p < P; p += 32) Gk[p] = (double)Ghi[p] + (double)Glo[p];
+        dw *Gk = G + (size_t)k * P;
+        for (int p = lane; p < P; p += 32) Gk[p] = two_sum(Ghi[p], Glo[p]);   // normalised pair
         if (Gf) {
             float *Gfk = Gf + (size_t)k * P;
             for (int p = lane; p < P; p += 32) Gfk[p] = Ghi[p] + Glo[p];
@@ -1115,7 +1115,7 @@ static void mark(p2_ctx *c, int i) {
 // Gram G_k of Z_k = X_k V for an arbitrary batch X (projection of new
 // subjects onto the model's V).
 template <class S>
-static void launch_gram_t(const p2_ctx *c, const XView &X, const SmallState *st, double *G,
+static void launch_gram_t(const p2_ctx *c, const XView &X, const SmallState *st, dw *G,
                           cudaStream_t s) {
     const Launch L = plan(c);
     const int nt = L.alpha_warps * 32;
@@ -1148,7 +1148,7 @@ static void launch_gram_t(const p2_ctx *c, const XView &X, const SmallState *st,
 
 // Gram G_k of Z_k = X_k V for an arbitrary batch X (projection of new
 // subjects onto the model's V).
-cudaError_t launch_gram(const p2_ctx *c, const XView &X, const SmallState *st, double *G,
+cudaError_t launch_gram(const p2_ctx *c, const XView &X, const SmallState *st, dw *G,
                         cudaStream_t s) {
     if (c->bf16)
         launch_gram_t<bf16_t>(c, X, st, G, s);

@@ -1,21 +1,25 @@
-// Procrustes step of the Q-step (Section 3.2, Algorithm 2's SVD loop), FP64,
-// one GPU lane per subject.
+// Procrustes step of the Q-step (Section 3.2, Algorithm 2's SVD loop), one
+// GPU lane per subject, in double-word arithmetic (p2_dw.cuh).
 //
 // For subject k with Gram G_k = Z_k^T Z_k (Z_k = X_k V) and S_k = diag(W(k,:)):
 //   M   = H S G S H^T                  (= A_k^T A_k, A_k = X_k V S_k H^T)
 //   M   = Z diag(d) Z^T                (Householder tridiagonalisation + implicit QR)
 //   f_i = d_i^{-1/2} if d_i > rtol^2 max(d) else 0    (rank cut of the SVD)
 //   C   = Z diag(f) Z^T                (pseudo-inverse square root of M)
-//   T_k = C H S                        (stored FP32; Q_k = X_k V T_k^T)
-// The FP64 pipe of this GPU issues one warp instruction per ~66 cycles per
-// SM sub-partition whatever the number of active lanes, so every lane owns a
-// whole subject and the kernel is written to minimise FP64 instructions.
+//   T_k = C H S = Z' (Z'^T H S), Z' = Z diag(f)^{1/2}   (stored FP32; Q_k = X_k V T_k^T)
+// Precision: T_k is stored in FP32, whose rounding already perturbs Q_k by
+// ~2^-24 cond(A_k); the eigen-decomposition of M = A_k^T A_k in double-word
+// arithmetic (~2^-46 normwise) perturbs it by ~2^-46 cond(A_k)^2, below the
+// storage error for every cond(A_k) <= 1 / rank_rtol the rank cut admits.
+// Range: G, W and H are scaled by powers of two (exactly) so that every
+// intermediate stays inside the FP32 exponent range, and the exponents are
+// folded back into T_k at the end.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
 #include "p2_internal.cuh"
-#include "p2_eig.cuh"
+#include "p2_eig_dw.cuh"
 #include "p2_polar.cuh"
 
 namespace p2 {
@@ -25,179 +29,162 @@ static __device__ __forceinline__ int pk(int i, int j) {   // packed lower index
     return (j <= i) ? (i * (i + 1) / 2 + j) : (j * (j + 1) / 2 + i);
 }
 
-// Small R: Gram and C held in registers, only Z (R x R) and the tridiagonal
-// (d, e) in interleaved shared memory: R^2 + 2R doubles per lane.
+// Shared memory: H (scaled, FP32) for the block, then per lane the working
+// matrix (R x R) and the tridiagonal (d, e), interleaved across the lanes:
+// R^2 + 2R double-words per lane.
 template <int R>
-__global__ void __launch_bounds__(256) k_polar_reg(const double *__restrict__ G,
+__global__ void __launch_bounds__(256) k_polar_reg(const dw *__restrict__ G,
                                                    const float *__restrict__ W, SmallState *st,
-                                                   float *T, int64_t K, double rtol2) {
+                                                   float *T, int64_t K, float rtol2) {
     constexpr int P = R * (R + 1) / 2;
-    extern __shared__ __align__(16) double sm[];
+    constexpr int HW = (R * R + 1) / 2;                  // double-word slots holding H
+    extern __shared__ __align__(16) dw smd[];
     const int NT = blockDim.x;
     const int t = threadIdx.x;
-    double *Hs = sm;
-    double *th = sm + R * R;
-    for (int i = t; i < R * R; i += NT) Hs[i] = st->H64[i];
+    float *Hs = reinterpret_cast<float *>(smd);
+    dw *th = smd + HW;
+    for (int i = t; i < R * R; i += NT) Hs[i] = (float)st->H64[i];   // exact: H is FP32
+    __syncthreads();
+    int eh = 0;
+    for (int i = 0; i < R * R; ++i) eh = max(eh, f_expo(Hs[i]));
+    const float hsc = f_pow2(127 - eh);                  // H' = H 2^sh, max |H'| in [1, 2)
+    __syncthreads();
+    for (int i = t; i < R * R; i += NT) Hs[i] = f_mul(Hs[i], hsc);
     __syncthreads();
     const int64_t k = (int64_t)blockIdx.x * NT + t;
     unsigned long long flops = 0;
     if (k < K) {
-        MatView A{th + t, NT, R};
-        VecView d{th + (size_t)R * R * NT + t, NT};
-        VecView e{th + (size_t)(R * R + R) * NT + t, NT};
-        double w[R];
-#pragma unroll
-        for (int i = 0; i < R; ++i) w[i] = (double)W[(size_t)k * R + i];
-        {
-            double g[P];
-            const double *Gk = G + (size_t)k * P;
-#pragma unroll
-            for (int i = 0, p = 0; i < R; ++i)
-#pragma unroll
-                for (int j = 0; j <= i; ++j, ++p) g[p] = Gk[p] * w[i] * w[j];
-#pragma unroll 1
-            for (int c = 0; c < R; ++c) {
-                double tv[R];
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int j = 0; j < R; ++j) s = fma(g[pk<R>(i, j)], Hs[c * R + j], s);
-                    tv[i] = s;
-                }
-#pragma unroll
-                for (int r = c; r < R; ++r) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int i = 0; i < R; ++i) s = fma(Hs[r * R + i], tv[i], s);
-                    A(r, c) = s;
-                }
-            }
-        }
-        tridiagonalize<R>(R, A, d, e);
-        int rot = 0;
-        const int steps = tridiagonal_qr<R>(R, A, d, e, 30 * R, &rot);
-        if (steps < 0) atomicOr(&st->flags, FLAG_EIG_NOCONV);
-        double lmax = 0.0;
-#pragma unroll
-        for (int i = 0; i < R; ++i) lmax = fmax(lmax, d[i]);
-        const double cut = rtol2 * lmax;
+        const dw zero = dw_f(0.f);
+        DwMat A{th + t, NT, R};
+        DwVec d{th + (size_t)R * R * NT + t, NT};
+        DwVec e{th + (size_t)(R * R + R) * NT + t, NT};
+        const size_t tb = (size_t)k * R * R;
+        const dw *Gk = G + (size_t)k * P;
+        float w[R];
+        int ew = 0, eg = 0;
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-            const double di = d[i];
-            const double sf = (lmax > 0.0 && di > cut) ? sqrt(p2_rsqrt(di)) : 0.0;   // d^-1/4
-#pragma unroll
-            for (int r = 0; r < R; ++r) A(r, i) *= sf;
+            w[i] = W[(size_t)k * R + i];
+            ew = max(ew, f_expo(w[i]));
+            eg = max(eg, f_expo(Gk[i * (i + 1) / 2 + i].h));   // |G_ij| <= max_i G_ii
         }
-        double Cl[P];
+        // M' = H' S' G' S' H'^T with S' = S 2^sw, G' = G 2^sg (exact scalings)
+        const int sg = 127 - eg;
+        const float wsc = f_pow2(127 - ew), gsc = f_pow2(sg);
 #pragma unroll
-        for (int r = 0; r < R; ++r)
+        for (int i = 0; i < R; ++i) w[i] = f_mul(w[i], wsc);
+        // g = S' G' S' in the strict upper triangle of A (g(i, j), i > j, at
+        // A(j, i)) and in d (g(i, i)); M' then fills the lower triangle.
 #pragma unroll
-            for (int c = 0; c <= r; ++c) {
-                double s = 0.0;
-#pragma unroll
-                for (int i = 0; i < R; ++i) s = fma(A(r, i), A(c, i), s);
-                Cl[pk<R>(r, c)] = s;
-            }
-        const size_t tb = (size_t)k * R * R;
-#pragma unroll 1
-        for (int c = 0; c < R; ++c)
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                double s = 0.0;
-#pragma unroll
-                for (int u = 0; u < R; ++u) s = fma(Cl[pk<R>(r, u)], Hs[u * R + c], s);
-                T[tb + r * R + c] = (float)(s * w[c]);
-            }
-        flops = polar_fixed_flops(R) + qr_flops(R, steps, rot);
-    }
-    add_flops(st, flops);
-}
-
-// Any R: scaled Gram and C in shared memory as well: R^2 + P + 3R doubles per lane.
-__global__ void __launch_bounds__(128) k_polar_smem(const double *__restrict__ G,
-                                                    const float *__restrict__ W, SmallState *st,
-                                                    float *T, int64_t K, int R, double rtol2) {
-    extern __shared__ __align__(16) double sm[];
-    const int NT = blockDim.x;
-    const int t = threadIdx.x;
-    const int P = R * (R + 1) / 2;
-    double *Hs = sm;
-    double *th = sm + R * R;
-    for (int i = t; i < R * R; i += NT) Hs[i] = st->H64[i];
-    __syncthreads();
-    const int64_t k = (int64_t)blockIdx.x * NT + t;
-    unsigned long long flops = 0;
-    if (k < K) {
-        MatView A{th + t, NT, R};
-        double *gp = th + (size_t)R * R * NT + t;
-        VecView d{gp + (size_t)P * NT, NT};
-        VecView e{gp + (size_t)(P + R) * NT, NT};
-        VecView w{gp + (size_t)(P + 2 * R) * NT, NT};
-        VecView tv = e;
-        const float *Wk = W + (size_t)k * R;
-        for (int i = 0; i < R; ++i) w[i] = (double)Wk[i];
-        const double *Gk = G + (size_t)k * P;
         for (int i = 0, p = 0; i < R; ++i)
-            for (int j = 0; j <= i; ++j, ++p) gp[(size_t)p * NT] = Gk[p] * w[i] * w[j];
+#pragma unroll
+            for (int j = 0; j <= i; ++j, ++p) {
+                const dw g = dw_mul(dw_scale(Gk[p], gsc), two_prod(w[i], w[j]));
+                if (j == i)
+                    d[i] = g;
+                else
+                    A(j, i) = g;
+            }
+        int em = 0;
+#pragma unroll 1
         for (int c = 0; c < R; ++c) {
-            for (int i = 0; i < R; ++i) {
-                double s = 0.0;
+            dw tv[R];
+            {
+                dwacc s[R];
+#pragma unroll
+                for (int i = 0; i < R; ++i) s[i] = acc_zero();
+#pragma unroll 1
                 for (int j = 0; j < R; ++j) {
-                    const int p = (j <= i) ? (i * (i + 1) / 2 + j) : (j * (j + 1) / 2 + i);
-                    s = fma(gp[(size_t)p * NT], Hs[c * R + j], s);
+                    const float hj = Hs[c * R + j];
+#pragma unroll
+                    for (int i = 0; i < R; ++i)
+                        acc_fmaf(s[i], (i == j) ? d[i] : (j > i ? A(i, j) : A(j, i)), hj);
                 }
-                tv[i] = s;
+#pragma unroll
+                for (int i = 0; i < R; ++i) tv[i] = acc_val(s[i]);
             }
             for (int r = c; r < R; ++r) {
-                double s = 0.0;
-                for (int i = 0; i < R; ++i) s = fma(Hs[r * R + i], tv[i], s);
-                A(r, c) = s;
+                dwacc s = acc_zero();
+#pragma unroll
+                for (int i = 0; i < R; ++i) acc_fmaf(s, tv[i], Hs[r * R + i]);
+                const dw m = acc_val(s);
+                A(r, c) = m;
+                if (r == c) em = max(em, f_expo(m.h));
             }
         }
-        tridiagonalize<0>(R, A, d, e);
-        int rot = 0;
-        const int steps = tridiagonal_qr<0>(R, A, d, e, 30 * R, &rot);
-        if (steps < 0) atomicOr(&st->flags, FLAG_EIG_NOCONV);
-        double lmax = 0.0;
-        for (int i = 0; i < R; ++i) lmax = fmax(lmax, d[i]);
-        const double cut = rtol2 * lmax;
-        for (int i = 0; i < R; ++i) {
-            const double di = d[i];
-            const double sf = (lmax > 0.0 && di > cut) ? sqrt(p2_rsqrt(di)) : 0.0;
-            for (int r = 0; r < R; ++r) A(r, i) *= sf;
-        }
-        for (int r = 0, p = 0; r < R; ++r)          // C lower into the Gram's slot
-            for (int c = 0; c <= r; ++c, ++p) {
-                double s = 0.0;
-                for (int i = 0; i < R; ++i) s = fma(A(r, i), A(c, i), s);
-                gp[(size_t)p * NT] = s;
+        if (eg == 0 || ew == 0 || em == 0) {
+            // G, W or M is zero (or below the normal range): A_k = 0, Q_k = 0
+            for (int i = 0; i < R * R; ++i) T[tb + i] = 0.f;
+        } else {
+            // M'' = M' 2^sm with max diag in [0.5, 2); sm + sg even so that
+            // M^{-1/2} H S = 2^{(sm + sg) / 2} M''^{-1/2} H' S'
+            int sm = 127 - em;
+            if ((sm + sg) & 1) --sm;
+            const float msc = f_pow2(sm);
+#pragma unroll 1
+            for (int r = 0; r < R; ++r)
+                for (int c = 0; c <= r; ++c) A(r, c) = dw_scale(A(r, c), msc);
+            tridiagonalize_dw<R>(R, A, d, e);
+            int rot = 0;
+            const int steps = tridiagonal_qr_dw<R>(R, A, d, e, 30 * R, &rot);
+            if (steps < 0) atomicOr(&st->flags, FLAG_EIG_NOCONV);
+            float lmax = 0.f;
+#pragma unroll
+            for (int i = 0; i < R; ++i) lmax = fmaxf(lmax, d[i].h);
+            const float cut = rtol2 * lmax;
+#pragma unroll 1
+            for (int i = 0; i < R; ++i) {
+                const dw di = d[i];
+                const dw sf = (lmax > 0.f && di.h > cut) ? dw_sqrt(dw_rsqrt(di)) : zero;  // d^-1/4
+#pragma unroll
+                for (int r = 0; r < R; ++r) A(r, i) = dw_mul(A(r, i), sf);
             }
-        const size_t tb = (size_t)k * R * R;
-        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int i = 0; i < R; ++i) e[i] = dw_f(w[i]);    // w' where the T loop can index it
+            const int so = (sm + sg) / 2;
+            const float o1 = f_pow2(so / 2), o2 = f_pow2(so - so / 2);
+#pragma unroll 1
             for (int c = 0; c < R; ++c) {
-                double s = 0.0;
-                for (int u = 0; u < R; ++u) {
-                    const int p = (u <= r) ? (r * (r + 1) / 2 + u) : (u * (u + 1) / 2 + r);
-                    s = fma(gp[(size_t)p * NT], Hs[u * R + c], s);
+                dw y[R];                                 // y = Z'^T h'_c
+                {
+                    dwacc s[R];
+#pragma unroll
+                    for (int i = 0; i < R; ++i) s[i] = acc_zero();
+#pragma unroll 1
+                    for (int r = 0; r < R; ++r) {
+                        const float hr = Hs[r * R + c];
+#pragma unroll
+                        for (int i = 0; i < R; ++i) acc_fmaf(s[i], A(r, i), hr);
+                    }
+#pragma unroll
+                    for (int i = 0; i < R; ++i) y[i] = acc_val(s[i]);
                 }
-                T[tb + r * R + c] = (float)(s * w[c]);
+#pragma unroll 1
+                for (int r = 0; r < R; ++r) {             // T(r, c) = (Z' y)_r w'_c
+                    dwacc s = acc_zero();
+#pragma unroll
+                    for (int i = 0; i < R; ++i) acc_fma(s, A(r, i), y[i]);
+                    const dw v = dw_mulf(acc_val(s), e[c].h);
+                    T[tb + r * R + c] = f_mul(f_mul(v.h, o1), o2);
+                }
             }
-        flops = polar_fixed_flops(R) + qr_flops(R, steps, rot);
+            flops = polar_fixed_flops(R) + qr_flops(R, steps, rot);
+        }
     }
     add_flops(st, flops);
 }
 
 template <int R>
-static int launch_reg(const p2_ctx *c, const double *G, const float *W, SmallState *st, float *T,
-                      int64_t K, cudaStream_t s, double rtol2) {
+static int launch_reg(const p2_ctx *c, const dw *G, const float *W, SmallState *st, float *T,
+                      int64_t K, cudaStream_t s, float rtol2) {
     const int cap = c->geo.smem_optin;
-    const size_t per = (size_t)(R * R + 2 * R) * 8;
-    int nt = (int)((cap - (size_t)R * R * 8) / per);
+    const size_t hbytes = (size_t)((R * R + 1) / 2) * sizeof(dw);
+    const size_t per = (size_t)(R * R + 2 * R) * sizeof(dw);
+    int nt = (int)((cap - hbytes) / per);
     if (nt > 256) nt = 256;
     nt = (nt / 32) * 32;
     if (nt < 32) return -1;
-    const size_t smem = (size_t)R * R * 8 + (size_t)nt * per;
+    const size_t smem = hbytes + (size_t)nt * per;
     const int nblk = (int)((K + nt - 1) / nt);
     k_polar_reg<R><<<nblk, nt, smem, s>>>(G, W, st, T, K, rtol2);
     return 0;
@@ -208,14 +195,17 @@ int polar_configure(p2_ctx *c) {
     cudaError_t e = cudaSuccess;
 #define P2_ALLOW(fn) \
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)
-    P2_ALLOW(k_polar_smem);
+    P2_ALLOW(k_polar_reg<1>);
     P2_ALLOW(k_polar_reg<2>);
     P2_ALLOW(k_polar_reg<3>);
     P2_ALLOW(k_polar_reg<4>);
     P2_ALLOW(k_polar_reg<5>);
     P2_ALLOW(k_polar_reg<6>);
+    P2_ALLOW(k_polar_reg<7>);
     P2_ALLOW(k_polar_reg<8>);
+    P2_ALLOW(k_polar_reg<9>);
     P2_ALLOW(k_polar_reg<10>);
+    P2_ALLOW(k_polar_reg<11>);
     P2_ALLOW(k_polar_reg<12>);
 #undef P2_ALLOW
     if (e == cudaSuccess) e = polar_grp_configure(cap);
@@ -228,35 +218,23 @@ int polar_configure(p2_ctx *c) {
 
 // Enqueue the Procrustes kernel for K subjects (Gram G, weights W, state st
 // holding H64) writing T; returns a cudaError_t.
-cudaError_t launch_polar_on(const p2_ctx *c, const double *G, const float *W, SmallState *st,
+cudaError_t launch_polar_on(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
                             float *T, int64_t K, cudaStream_t s) {
     const int R = c->R;
     const double rtol2 = c->opt.rank_rtol * c->opt.rank_rtol;
     if (K <= 0) return cudaSuccess;
+    if (R > 12) return launch_polar_grp(c, G, W, st, T, K, s, rtol2);
+    const float rt2 = (float)rtol2;
     int rc = -1;
     switch (R) {
-        case 2: rc = launch_reg<2>(c, G, W, st, T, K, s, rtol2); break;
-        case 3: rc = launch_reg<3>(c, G, W, st, T, K, s, rtol2); break;
-        case 4: rc = launch_reg<4>(c, G, W, st, T, K, s, rtol2); break;
-        case 5: rc = launch_reg<5>(c, G, W, st, T, K, s, rtol2); break;
-        case 6: rc = launch_reg<6>(c, G, W, st, T, K, s, rtol2); break;
-        case 8: rc = launch_reg<8>(c, G, W, st, T, K, s, rtol2); break;
-        case 10: rc = launch_reg<10>(c, G, W, st, T, K, s, rtol2); break;
-        case 12: rc = launch_reg<12>(c, G, W, st, T, K, s, rtol2); break;
+#define P2_CASE(r) \
+        case r: rc = launch_reg<r>(c, G, W, st, T, K, s, rt2); break;
+        P2_CASE(1) P2_CASE(2) P2_CASE(3) P2_CASE(4) P2_CASE(5) P2_CASE(6)
+        P2_CASE(7) P2_CASE(8) P2_CASE(9) P2_CASE(10) P2_CASE(11) P2_CASE(12)
+#undef P2_CASE
         default: break;
     }
-    if (rc != 0 && R > 12) return launch_polar_grp(c, G, W, st, T, K, s, rtol2);
-    if (rc != 0) {
-        const int P = R * (R + 1) / 2;
-        const size_t per = ((size_t)R * R + P + 3 * (size_t)R) * 8;
-        int nt = (int)(((size_t)c->geo.smem_optin - (size_t)R * R * 8) / per);
-        if (nt > 128) nt = 128;
-        if (nt >= 32) nt = (nt / 32) * 32;
-        if (nt < 1) nt = 1;
-        const size_t smem = (size_t)R * R * 8 + (size_t)nt * per;
-        const int nblk = (int)((K + nt - 1) / nt);
-        k_polar_smem<<<nblk, nt, smem, s>>>(G, W, st, T, K, R, rtol2);
-    }
+    if (rc != 0) return cudaErrorInvalidConfiguration;   // shared memory below 32 lanes' need
     return cudaGetLastError();
 }
 

@@ -5,43 +5,52 @@
 #include <stdint.h>
 
 #include "p2_internal.cuh"
-#include "p2_eig.cuh"
 #include "p2_polar.cuh"
 #include "p2_polar_grp.cuh"
 
 namespace p2 {
 
 template <int RB>
-static void launch_grp(const p2_ctx *c, const double *G, const float *W, SmallState *st, float *T,
+static void launch_grp(const p2_ctx *c, const dw *G, const float *W, SmallState *st, float *T,
                        int64_t K, cudaStream_t s, double rtol2) {
     const int R = c->R;
-    const size_t per = grp_doubles(R) * sizeof(double);
-    int spb = (int)((size_t)c->geo.smem_optin / per);
+    const size_t per = grp_dws(R) * sizeof(dw);
+    const size_t hbytes = grp_hdws(R) * sizeof(dw);
+    // 16 bytes kept for the kernel's static shared memory
+    int spb = (int)(((size_t)c->geo.smem_optin - hbytes - 16) / per);
     if (spb > 32) spb = 32;
     if (spb >= 4) spb = (spb / 4) * 4;
     if (spb < 1) spb = 1;
     const int threads = ((spb + 3) / 4) * 32;
-    const size_t smem = (size_t)spb * per;
+    const size_t smem = hbytes + (size_t)spb * per;
     const int64_t nblk = (K + spb - 1) / spb;
-    k_polar_grp<RB><<<(unsigned)nblk, threads, smem, s>>>(G, W, st, T, K, R, rtol2, spb);
+    k_polar_grp<RB><<<(unsigned)nblk, threads, smem, s>>>(G, W, st, T, K, R, (float)rtol2, spb);
+}
+
+// dynamic shared memory allowed: the opt-in maximum less the kernel's static
+// shared memory
+template <int RB>
+static cudaError_t allow_grp(int cap) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_polar_grp<RB>);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_polar_grp<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                cap - (int)a.sharedSizeBytes);
 }
 
 cudaError_t polar_grp_configure(int cap) {
     cudaError_t e = cudaSuccess;
-#define P2_ALLOW(fn) \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)
-    P2_ALLOW(k_polar_grp<16>);
-    P2_ALLOW(k_polar_grp<24>);
-    P2_ALLOW(k_polar_grp<32>);
-    P2_ALLOW(k_polar_grp<40>);
-    P2_ALLOW(k_polar_grp<48>);
-    P2_ALLOW(k_polar_grp<56>);
-    P2_ALLOW(k_polar_grp<64>);
-#undef P2_ALLOW
+    if (e == cudaSuccess) e = allow_grp<16>(cap);
+    if (e == cudaSuccess) e = allow_grp<24>(cap);
+    if (e == cudaSuccess) e = allow_grp<32>(cap);
+    if (e == cudaSuccess) e = allow_grp<40>(cap);
+    if (e == cudaSuccess) e = allow_grp<48>(cap);
+    if (e == cudaSuccess) e = allow_grp<56>(cap);
+    if (e == cudaSuccess) e = allow_grp<64>(cap);
     return e;
 }
 
-cudaError_t launch_polar_grp(const p2_ctx *c, const double *G, const float *W, SmallState *st,
+cudaError_t launch_polar_grp(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
                              float *T, int64_t K, cudaStream_t s, double rtol2) {
     switch ((c->R + PG - 1) / PG) {
         case 1:

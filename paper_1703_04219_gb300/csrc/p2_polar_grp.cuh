@@ -1,85 +1,150 @@
-// Procrustes kernel for larger R: eight lanes per subject (see below).
-// Included by p2_polar_grp.cu; needs MatView and p2_rsqrt (p2_eig.cuh), the
-// flop helpers (p2_polar.cuh), SmallState and FLAG_EIG_NOCONV.
+// Procrustes kernel for larger R: eight lanes per subject, double-word
+// arithmetic (p2_dw.cuh).  Included by p2_polar_grp.cu; needs the flop
+// helpers (p2_polar.cuh), SmallState and FLAG_EIG_NOCONV.
 #pragma once
+
+#include "p2_dw.cuh"
 
 namespace p2 {
 
 // ---------------------------------------------------------------------------
 // Larger R (up to 64): a group of PG = 8 lanes per subject, four subjects per
-// warp.  A lane-per-subject kernel would need R^2 doubles of shared memory per
-// lane (12.8 KB at R = 40), so only ~17 subjects would fit on an SM and the
-// FP64 pipe would issue mostly empty warps.  Here the R x R working matrix of
-// a subject lives once in shared memory and its eight lanes split the vector
-// work by rows (or columns); the scalar parts of the Householder and QR steps
-// run redundantly on the eight lanes of a group, so a warp instruction still
-// serves four subjects.  Same mathematics, tolerances and output as above.
+// warp.  A lane-per-subject kernel would need R^2 double-words of shared
+// memory per lane (12.8 KB at R = 40), so only ~17 subjects would fit on an
+// SM.  Here the R x R working matrix of a subject lives once in shared memory
+// and its eight lanes split the vector work by rows (or columns); the scalar
+// parts of the Householder and QR steps run redundantly on the eight lanes of
+// a group, so a warp instruction still serves four subjects.  Same
+// mathematics, scalings, tolerances and output as the lane-per-subject kernel.
 //
-// Per subject: A (R x LD, LD = R | 1 to spread banks), d, e, t, w (R each).
-// RB = R rounded up to a multiple of PG (register arrays); rows i are owned
-// by lane i % PG.
+// Shared memory: H' (R x R floats) for the block, then per subject A (R x LD,
+// LD = R | 1 to spread banks), d, e, t (R each) and w' (R floats in R
+// double-word slots).  RB = R rounded up to a multiple of PG (register
+// arrays); rows i are owned by lane i % PG.
 constexpr int PG = 8;
 
 inline __host__ __device__ int grp_ld(int R) { return R | 1; }
-inline __host__ __device__ size_t grp_doubles(int R) {
-    return (size_t)R * grp_ld(R) + 4 * (size_t)R;
+// double-words per subject
+inline __host__ __device__ size_t grp_dws(int R) { return (size_t)R * grp_ld(R) + 4 * (size_t)R; }
+// double-words for the block's H'
+inline __host__ __device__ size_t grp_hdws(int R) { return ((size_t)R * R + 1) / 2; }
+
+static __device__ __forceinline__ dw shfl_xor_dw(unsigned mask, dw v, int o) {
+    return dw{__shfl_xor_sync(mask, v.h, o), __shfl_xor_sync(mask, v.l, o)};
+}
+// sum over the eight lanes of a group (same result on every lane: the
+// butterfly adds the same two operands in the same order on both partners)
+static __device__ __forceinline__ dw group_sum(unsigned mask, dw v) {
+    v = dw_add(v, shfl_xor_dw(mask, v, 4));
+    v = dw_add(v, shfl_xor_dw(mask, v, 2));
+    v = dw_add(v, shfl_xor_dw(mask, v, 1));
+    return v;
+}
+static __device__ __forceinline__ int group_max(unsigned mask, int v) {
+    v = max(v, __shfl_xor_sync(mask, v, 4));
+    v = max(v, __shfl_xor_sync(mask, v, 2));
+    v = max(v, __shfl_xor_sync(mask, v, 1));
+    return v;
+}
+static __device__ __forceinline__ float group_maxf(unsigned mask, float v) {
+    v = fmaxf(v, __shfl_xor_sync(mask, v, 4));
+    v = fmaxf(v, __shfl_xor_sync(mask, v, 2));
+    v = fmaxf(v, __shfl_xor_sync(mask, v, 1));
+    return v;
 }
 
 template <int RB>
-__global__ void __launch_bounds__(256, 1) k_polar_grp(const double *__restrict__ G,
+__global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                                                       const float *__restrict__ W, SmallState *st,
-                                                      float *T, int64_t K, int R, double rtol2,
+                                                      float *T, int64_t K, int R, float rtol2,
                                                       int spb) {
     constexpr int RPL = RB / PG;                     // rows per lane
-    extern __shared__ __align__(16) double sm[];
+    extern __shared__ __align__(16) dw smg[];
+    __shared__ int s_eh;
     const int lane = threadIdx.x & 31;
     const int gl = lane & (PG - 1);
     const unsigned gmask = 0xffu << (lane & ~(PG - 1));
     const int slot = (threadIdx.x >> 3);
     const int64_t k = (int64_t)blockIdx.x * spb + slot;
-    const double *__restrict__ H = st->H64;
+    const dw one = dw_f(1.f), zero = dw_f(0.f);
+    float *Hs = reinterpret_cast<float *>(smg);
+    if (threadIdx.x == 0) s_eh = 0;
+    __syncthreads();
+    {
+        int eh = 0;
+        for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
+            const float h = (float)st->H64[i];      // exact: H is FP32
+            Hs[i] = h;
+            eh = max(eh, f_expo(h));
+        }
+        atomicMax(&s_eh, eh);
+    }
+    __syncthreads();
+    {
+        const float hsc = f_pow2(127 - s_eh);        // H' = H 2^sh, max |H'| in [1, 2)
+        for (int i = threadIdx.x; i < R * R; i += blockDim.x) Hs[i] = f_mul(Hs[i], hsc);
+    }
+    __syncthreads();
     unsigned long long flops = 0;
     if (slot < spb && k < K) {
         const int LD = grp_ld(R);
-        double *base = sm + (size_t)slot * grp_doubles(R);
-        MatView A{base, 1, LD};                      // A(i, j) = base[i * LD + j]
-        double *d = base + (size_t)R * LD;
-        double *e = d + R;
-        double *t = e + R;
-        double *wv = t + R;
-        const double *Gk = G + (size_t)k * (R * (R + 1) / 2);
-        for (int i = gl; i < R; i += PG) wv[i] = (double)W[(size_t)k * R + i];
+        dw *base = smg + grp_hdws(R) + (size_t)slot * grp_dws(R);
+        auto A = [base, LD](int i, int j) -> dw & { return base[i * LD + j]; };
+        dw *d = base + (size_t)R * LD;
+        dw *e = d + R;
+        dw *t = e + R;
+        float *wv = reinterpret_cast<float *>(t + R);
+        const dw *Gk = G + (size_t)k * (R * (R + 1) / 2);
+        const size_t tb = (size_t)k * R * R;
+
+        // ---- scalings: S' = S 2^sw, G' = G 2^sg ------------------------------
+        int ew = 0, eg = 0;
+        for (int i = gl; i < R; i += PG) {
+            const float w = W[(size_t)k * R + i];
+            wv[i] = w;
+            ew = max(ew, f_expo(w));
+            eg = max(eg, f_expo(Gk[i * (i + 1) / 2 + i].h));
+        }
+        ew = group_max(gmask, ew);
+        eg = group_max(gmask, eg);
+        const int sg = 127 - eg;
+        const float gsc = f_pow2(sg);
+        {
+            const float wsc = f_pow2(127 - ew);
+            for (int i = gl; i < R; i += PG) wv[i] = f_mul(wv[i], wsc);
+        }
         __syncwarp(gmask);
 
-        // ---- M = H B H^T with B = S G S ------------------------------------
-        // U = B H^T, row by row in place (row i of B is held in registers).
+        // ---- M' = H' B H'^T with B = S' G' S' -------------------------------
+        // U = B H'^T, row by row in place (row i of B is held in registers).
 #pragma unroll 1
         for (int ii = 0; ii < RPL; ++ii) {
             const int i = gl + PG * ii;
             if (i >= R) break;
-            double b[RB];
-            const double wi = wv[i];
+            dw b[RB];
+            const float wi = wv[i];
 #pragma unroll
             for (int j = 0; j < RB; ++j) {
                 if (j < R) {
                     const int p = (j <= i) ? (i * (i + 1) / 2 + j) : (j * (j + 1) / 2 + i);
-                    b[j] = Gk[p] * (wi * wv[j]);
+                    b[j] = dw_mul(dw_scale(Gk[p], gsc), two_prod(wi, wv[j]));
                 }
             }
 #pragma unroll 1
             for (int c = 0; c < R; ++c) {
-                double s = 0.0;
+                dwacc s = acc_zero();
 #pragma unroll
                 for (int j = 0; j < RB; ++j)
-                    if (j < R) s = fma(b[j], __ldg(&H[c * R + j]), s);
-                A(i, c) = s;
+                    if (j < R) acc_fmaf(s, b[j], Hs[c * R + j]);
+                A(i, c) = acc_val(s);
             }
         }
         __syncwarp(gmask);
-        // M = H U, column by column in place (lower triangle).
+        // M' = H' U, column by column in place (lower triangle).
+        int em = 0;
 #pragma unroll 1
         for (int c = 0; c < R; ++c) {
-            double u[RB];
+            dw u[RB];
 #pragma unroll
             for (int i = 0; i < RB; ++i)
                 if (i < R) u[i] = A(i, c);
@@ -89,283 +154,328 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const double *__restrict__
                 const int r = gl + PG * ii;
                 if (r >= R) break;
                 if (r < c) continue;
-                double s = 0.0;
+                dwacc s = acc_zero();
 #pragma unroll
                 for (int i = 0; i < RB; ++i)
-                    if (i < R) s = fma(__ldg(&H[r * R + i]), u[i], s);
-                A(r, c) = s;
+                    if (i < R) acc_fmaf(s, u[i], Hs[r * R + i]);
+                const dw m = acc_val(s);
+                A(r, c) = m;
+                if (r == c) em = max(em, f_expo(m.h));
             }
             __syncwarp(gmask);
         }
-
-        // ---- Householder tridiagonalisation (lower triangle) --------------
-#pragma unroll 1
-        for (int kk = 0; kk + 2 < R; ++kk) {
-            double sig = 0.0;
-            for (int i = gl; i < R; i += PG)
-                if (i >= kk + 2) sig = fma(A(i, kk), A(i, kk), sig);
-            sig += __shfl_xor_sync(gmask, sig, 4);
-            sig += __shfl_xor_sync(gmask, sig, 2);
-            sig += __shfl_xor_sync(gmask, sig, 1);
-            const double x0 = A(kk + 1, kk);
-            if (sig == 0.0) {
-                __syncwarp(gmask);
-                if (gl == 0) {
-                    A(kk, kk + 1) = 0.0;
-                    e[kk] = x0;
-                }
-                __syncwarp(gmask);
-                continue;
-            }
-            const double mu = sqrt(fma(x0, x0, sig));
-            const double v0 = (x0 <= 0.0) ? (x0 - mu) : (-sig / (x0 + mu));
-            const double v02 = v0 * v0;
-            const double bh = 2.0 * v02 / (sig + v02);
-            const double inv_v0 = 1.0 / v0;
-            __syncwarp(gmask);
-            for (int i = gl; i < R; i += PG)
-                if (i >= kk + 2) A(i, kk) *= inv_v0;
-            if (gl == 0) {
-                A(kk, kk + 1) = bh;
-                e[kk] = mu;
-            }
-            __syncwarp(gmask);
-            // p = bh * A22 v on my rows, pv = p . v
-            double pv = 0.0;
-            for (int i = gl; i < R; i += PG) {
-                if (i < kk + 1) continue;
-                double s = A(i, kk + 1);
-                for (int j = kk + 2; j < R; ++j) {
-                    const double aij = (j <= i) ? A(i, j) : A(j, i);
-                    s = fma(aij, A(j, kk), s);
-                }
-                s *= bh;
-                t[i] = s;
-                pv = fma(s, (i == kk + 1) ? 1.0 : A(i, kk), pv);
-            }
-            pv += __shfl_xor_sync(gmask, pv, 4);
-            pv += __shfl_xor_sync(gmask, pv, 2);
-            pv += __shfl_xor_sync(gmask, pv, 1);
-            const double Kc = 0.5 * bh * pv;
-            for (int i = gl; i < R; i += PG)
-                if (i >= kk + 1) t[i] = fma(-Kc, (i == kk + 1) ? 1.0 : A(i, kk), t[i]);
-            __syncwarp(gmask);
-            for (int i = gl; i < R; i += PG) {
-                if (i < kk + 1) continue;
-                const double vi = (i == kk + 1) ? 1.0 : A(i, kk);
-                const double wi = t[i];
-                A(i, kk + 1) = fma(-vi, t[kk + 1], A(i, kk + 1) - wi);
-                for (int j = kk + 2; j <= i; ++j)
-                    A(i, j) = fma(-vi, t[j], fma(-wi, A(j, kk), A(i, j)));
-            }
-            __syncwarp(gmask);
-        }
-        if (gl == 0 && R >= 2) e[R - 2] = A(R - 1, R - 2);
-        for (int i = gl; i < R; i += PG) d[i] = A(i, i);
-        __syncwarp(gmask);
-        // backward accumulation of Q = P_0 ... P_{R-3}, columns split over lanes
-        if (R == 1) {
-            if (gl == 0) A(0, 0) = 1.0;
+        em = group_max(gmask, em);
+        if (eg == 0 || ew == 0 || em == 0) {
+            // G, W or M is zero (or below the normal range): A_k = 0, Q_k = 0
+            for (int i = gl; i < R * R; i += PG) T[tb + i] = 0.f;
         } else {
-            if (gl == 0) {
-                A(R - 1, R - 1) = 1.0;
-                A(R - 2, R - 2) = 1.0;
-                A(R - 1, R - 2) = 0.0;
-                A(R - 2, R - 1) = 0.0;
+            // M'' = M' 2^sm, max diag in [0.5, 2), sm + sg even
+            int sm = 127 - em;
+            if ((sm + sg) & 1) --sm;
+            {
+                const float msc = f_pow2(sm);
+                for (int i = gl; i < R; i += PG)
+                    for (int j = 0; j <= i; ++j) A(i, j) = dw_scale(A(i, j), msc);
             }
             __syncwarp(gmask);
-#pragma unroll 1
-            for (int kk = R - 3; kk >= 0; --kk) {
-                const double bh = A(kk, kk + 1);
-                __syncwarp(gmask);
-                for (int j = gl; j < R; j += PG) {
-                    if (j == kk + 1) {
-                        A(kk + 1, kk + 1) = 1.0;
-                        for (int i = kk + 2; i < R; ++i) A(i, kk + 1) = 0.0;
-                    } else if (j > kk + 1) {
-                        A(kk + 1, j) = 0.0;
-                    }
-                }
-                __syncwarp(gmask);
-                if (bh != 0.0) {
-                    for (int c = gl; c < R; c += PG) {
-                        if (c < kk + 1) continue;
-                        double s = A(kk + 1, c);
-                        for (int i = kk + 2; i < R; ++i) s = fma(A(i, kk), A(i, c), s);
-                        s *= bh;
-                        A(kk + 1, c) -= s;
-                        for (int i = kk + 2; i < R; ++i) A(i, c) = fma(-s, A(i, kk), A(i, c));
-                    }
-                }
-                __syncwarp(gmask);
-            }
-            for (int j = gl; j < R; j += PG) {
-                if (j == 0) {
-                    A(0, 0) = 1.0;
-                } else {
-                    A(0, j) = 0.0;
-                    A(j, 0) = 0.0;
-                }
-            }
-        }
-        __syncwarp(gmask);
 
-        // ---- implicit QR with Wilkinson shift; rotations on my rows of Z ----
-        // One flat loop, one Givens rotation per trip, so that the four
-        // groups of a warp execute the rotation body together whatever their
-        // sweep boundaries.  The scalar recurrence runs on all eight lanes
-        // (identical values); d[k+1] and e[k+1] of a sweep are read before
-        // anything writes them and d[k], e[k] are carried in registers.
-        // Deflation tests compare binary exponents in integer arithmetic
-        // (p2_negligible).
-        const double eps = 2.220446049250313e-16;
-        double an = 0.0;
-        for (int i = gl; i < R; i += PG) {
-            double r = fabs(d[i]);
-            if (i + 1 < R) r += fabs(e[i]);
-            if (i > 0) r += fabs(e[i - 1]);
-            an = fmax(an, r);
-        }
-        an = fmax(an, __shfl_xor_sync(gmask, an, 4));
-        an = fmax(an, __shfl_xor_sync(gmask, an, 2));
-        an = fmax(an, __shfl_xor_sync(gmask, an, 1));
-        const int tiny_ex = p2_expo(eps * an);
-        int steps = 0, rot = 0;
-        const int max_steps = 30 * R;
-        int q = R - 1, p = 0, kr = 0;
-        bool sweeping = false, failed = false;
-        double x = 0.0, z = 0.0, dk = 0.0, ek = 0.0;
-        // Software pipelining: a trip computes the Givens scalars of rotation
-        // kr and applies rotation kr - 1 (kp, cp, sp) to the lanes' rows of Z;
-        // the two are independent, so the serial scalar chain overlaps FP64
-        // work.  A sweep starts with the identity pending and flushes its last
-        // rotation when it ends.
-        int kp = 0;
-        double cp = 1.0, sp = 0.0;
+            // ---- Householder tridiagonalisation (lower triangle) ----------
 #pragma unroll 1
-        while (true) {
-            if (!sweeping) {
-                while (q > 0 && p2_negligible(e[q - 1], d[q - 1], d[q], tiny_ex)) --q;
-                if (q == 0) break;
-                p = q - 1;
-                while (p > 0 && !p2_negligible(e[p - 1], d[p - 1], d[p], tiny_ex)) --p;
-                if (++steps > max_steps) {
-                    failed = true;
-                    break;
+            for (int kk = 0; kk + 2 < R; ++kk) {
+                dwacc sa = acc_zero();
+                for (int i = gl; i < R; i += PG)
+                    if (i >= kk + 2) acc_sqr(sa, A(i, kk));
+                const dw sig = group_sum(gmask, acc_val(sa));
+                const dw x0 = A(kk + 1, kk);
+                if (!(sig.h >= DW_TINY2)) {          // reflector as in p2_eig_dw.cuh
+                    __syncwarp(gmask);
+                    if (gl == 0) {
+                        A(kk, kk + 1) = zero;
+                        e[kk] = x0;
+                    }
+                    __syncwarp(gmask);
+                    continue;
                 }
-                rot += q - p;
-                const double eq = e[q - 1];
-                const double dd = 0.5 * (d[q - 1] - d[q]);
-                const double h = sqrt(fma(dd, dd, eq * eq));
-                const double mu = d[q] - eq * eq / (dd + (dd >= 0.0 ? h : -h));
-                dk = d[p];
-                ek = e[p];
-                x = dk - mu;
-                z = ek;
-                kr = p;
-                kp = p;
-                cp = 1.0;
-                sp = 0.0;
-                sweeping = true;
+                dwacc m2 = acc_from(sig);
+                acc_sqr(m2, x0);
+                const dw mu = dw_sqrt(acc_val(m2));
+                const dw beta = (x0.h >= 0.f) ? dw_neg(mu) : mu;
+                const dw bh = dw_div(dw_sub(beta, x0), beta);
+                const dw inv_v0 = dw_recip(dw_sub(x0, beta));
                 __syncwarp(gmask);
-                if (gl == 0 && p > 0) e[p - 1] = 0.0;
+                for (int i = gl; i < R; i += PG)
+                    if (i >= kk + 2) A(i, kk) = dw_mul(A(i, kk), inv_v0);
+                if (gl == 0) {
+                    A(kk, kk + 1) = bh;
+                    e[kk] = beta;
+                }
+                __syncwarp(gmask);
+                // p = bh A22 v on my rows, pv = p . v
+                dwacc pa = acc_zero();
+                for (int i = gl; i < R; i += PG) {
+                    if (i < kk + 1) continue;
+                    dwacc s = acc_from(A(i, kk + 1));
+                    for (int j = kk + 2; j < R; ++j)
+                        acc_fma(s, (j <= i) ? A(i, j) : A(j, i), A(j, kk));
+                    const dw si = dw_mul(acc_val(s), bh);
+                    t[i] = si;
+                    if (i == kk + 1)
+                        acc_add(pa, si);
+                    else
+                        acc_fma(pa, si, A(i, kk));
+                }
+                const dw pv = group_sum(gmask, acc_val(pa));
+                const dw nK = dw_neg(dw_mul(dw_scale(bh, 0.5f), pv));
+                for (int i = gl; i < R; i += PG) {
+                    if (i == kk + 1)
+                        t[i] = dw_add(t[i], nK);
+                    else if (i > kk + 1)
+                        t[i] = dw_fma(nK, A(i, kk), t[i]);
+                }
+                __syncwarp(gmask);
+                for (int i = gl; i < R; i += PG) {
+                    if (i < kk + 1) continue;
+                    const dw nvi = dw_neg((i == kk + 1) ? one : A(i, kk));
+                    const dw nwi = dw_neg(t[i]);
+                    for (int j = kk + 1; j <= i; ++j) {
+                        dwacc a = acc_from(A(i, j));
+                        acc_fma(a, nvi, t[j]);
+                        if (j == kk + 1)
+                            acc_add(a, nwi);
+                        else
+                            acc_fma(a, nwi, A(j, kk));
+                        A(i, j) = acc_val(a);
+                    }
+                }
+                __syncwarp(gmask);
             }
-            const double bb = d[kr + 1];
-            const double en = (kr + 1 < q) ? e[kr + 1] : 0.0;
+            if (gl == 0 && R >= 2) e[R - 2] = A(R - 1, R - 2);
+            for (int i = gl; i < R; i += PG) d[i] = A(i, i);
             __syncwarp(gmask);
-            double za[RPL], zb[RPL];
-#pragma unroll
-            for (int ii = 0; ii < RPL; ++ii) {
-                const int i = gl + PG * ii;
-                if (i < R) {
-                    za[ii] = A(i, kp);
-                    zb[ii] = A(i, kp + 1);
-                }
-            }
-            const double tt = fma(x, x, z * z);
-            const bool nz = tt > 0.0;
-            const double ir = p2_rsqrt(nz ? tt : 1.0);
-            const double c = nz ? x * ir : 1.0;
-            const double s = nz ? -z * ir : 0.0;
-            const double r = nz ? tt * ir : 0.0;
-            if (kr > p) e[kr - 1] = r;
-            const double cc = c * c, ss = s * s, cs = c * s;
-            const double cs2g = 2.0 * cs * ek;
-            d[kr] = fma(cc, dk, fma(ss, bb, -cs2g));
-            const double dk1 = fma(ss, dk, fma(cc, bb, cs2g));
-            const double ekn = fma(cs, dk - bb, (cc - ss) * ek);
-#pragma unroll
-            for (int ii = 0; ii < RPL; ++ii) {
-                const int i = gl + PG * ii;
-                if (i < R) {
-                    A(i, kp) = fma(cp, za[ii], -sp * zb[ii]);
-                    A(i, kp + 1) = fma(sp, za[ii], cp * zb[ii]);
-                }
-            }
-            kp = kr;
-            cp = c;
-            sp = s;
-            if (++kr < q) {
-                z = -s * en;
-                ek = c * en;
-                x = ekn;
-                dk = dk1;
+            // backward accumulation of Q = P_0 ... P_{R-3}, columns split over lanes
+            if (R == 1) {
+                if (gl == 0) A(0, 0) = one;
             } else {
-                d[q] = dk1;
-                e[q - 1] = ekn;
-                for (int i = gl; i < R; i += PG) {      // flush the sweep's last rotation
-                    const double zk = A(i, kp), zk1 = A(i, kp + 1);
-                    A(i, kp) = fma(cp, zk, -sp * zk1);
-                    A(i, kp + 1) = fma(sp, zk, cp * zk1);
+                if (gl == 0) {
+                    A(R - 1, R - 1) = one;
+                    A(R - 2, R - 2) = one;
+                    A(R - 1, R - 2) = zero;
+                    A(R - 2, R - 1) = zero;
                 }
-                sweeping = false;
                 __syncwarp(gmask);
+#pragma unroll 1
+                for (int kk = R - 3; kk >= 0; --kk) {
+                    const dw bh = A(kk, kk + 1);
+                    __syncwarp(gmask);
+                    const dw nb = dw_neg(bh);
+                    const bool act = bh.h != 0.f;
+                    for (int j = gl; j < R; j += PG) {
+                        if (j == kk + 1) {                    // column e_{k+1} -> (1 - b, -b v)
+                            A(kk + 1, kk + 1) = act ? dw_add(one, nb) : one;
+                            for (int i = kk + 2; i < R; ++i) A(i, kk + 1) = act ? dw_mul(nb, A(i, kk)) : zero;
+                        } else if (j > kk + 1) {
+                            A(kk + 1, j) = zero;
+                        }
+                    }
+                    __syncwarp(gmask);
+                    if (act) {
+                        for (int c = gl; c < R; c += PG) {
+                            if (c < kk + 2) continue;
+                            dwacc s = acc_zero();             // A(kk+1, c) = 0 here
+                            for (int i = kk + 2; i < R; ++i) acc_fma(s, A(i, kk), A(i, c));
+                            const dw ns = dw_mul(acc_val(s), nb);
+                            A(kk + 1, c) = ns;
+                            for (int i = kk + 2; i < R; ++i) A(i, c) = dw_fma(ns, A(i, kk), A(i, c));
+                        }
+                    }
+                    __syncwarp(gmask);
+                }
+                for (int j = gl; j < R; j += PG) {
+                    if (j == 0) {
+                        A(0, 0) = one;
+                    } else {
+                        A(0, j) = zero;
+                        A(j, 0) = zero;
+                    }
+                }
             }
-        }
-        if (failed && gl == 0) atomicOr(&st->flags, FLAG_EIG_NOCONV);
-        __syncwarp(gmask);
+            __syncwarp(gmask);
 
-        // ---- cut, Z scaled by d^-1/4 (columns split over lanes) -------------
-        double lmax = 0.0;
-        for (int i = gl; i < R; i += PG) lmax = fmax(lmax, d[i]);
-        lmax = fmax(lmax, __shfl_xor_sync(gmask, lmax, 4));
-        lmax = fmax(lmax, __shfl_xor_sync(gmask, lmax, 2));
-        lmax = fmax(lmax, __shfl_xor_sync(gmask, lmax, 1));
-        const double cut = rtol2 * lmax;
-        for (int i = gl; i < R; i += PG) {
-            const double di = d[i];
-            const double sf = (lmax > 0.0 && di > cut) ? sqrt(p2_rsqrt(di)) : 0.0;
-            for (int r = 0; r < R; ++r) A(r, i) *= sf;
-        }
-        __syncwarp(gmask);
-        // ---- T = Z' (Z'^T H S), one column of T at a time -------------------
-        const size_t tb = (size_t)k * R * R;
+            // ---- implicit QR with Wilkinson shift; rotations on my rows of Z --
+            // One flat loop, one Givens rotation per trip, so that the four
+            // groups of a warp execute the rotation body together whatever
+            // their sweep boundaries.  The scalar recurrence runs on all eight
+            // lanes (identical values); d[k+1] and e[k+1] of a sweep are read
+            // before anything writes them and d[k], e[k] are carried in
+            // registers.  A trip forms rotation kr and applies rotation kr - 1
+            // (kp, cp, sp) to the lanes' rows of Z; the pending rotation
+            // carries over sweep boundaries and is flushed at the end.
+            float an = 0.f;
+            for (int i = gl; i < R; i += PG) {
+                float r = fabsf(d[i].h);
+                if (i + 1 < R) r += fabsf(e[i].h);
+                if (i > 0) r += fabsf(e[i - 1].h);
+                an = fmaxf(an, r);
+            }
+            an = group_maxf(gmask, an);
+            const int tiny_ex = f_expo(an) - DW_DEFLATE_BITS;
+            int steps = 0, rot = 0;
+            const int max_steps = 30 * R;
+            int q = R - 1, p = 0, kr = 0;
+            bool sweeping = false, failed = false;
+            dw x = zero, z = zero, dk = zero, ek = zero;
+            int kp = 0;
+            dw cp = one, sp = zero;
 #pragma unroll 1
-        for (int c = 0; c < R; ++c) {
-            const double wc = wv[c];
-            for (int i = gl; i < R; i += PG) {       // t = Z'^T h_c w_c on my columns
-                double s = 0.0;
-                for (int r = 0; r < R; ++r) s = fma(A(r, i), __ldg(&H[r * R + c]), s);
-                t[i] = s * wc;
+            while (true) {
+                if (!sweeping) {
+                    while (q > 0 && dw_negligible(e[q - 1], d[q - 1], d[q], tiny_ex)) --q;
+                    if (q == 0) break;
+                    p = q - 1;
+                    while (p > 0 && !dw_negligible(e[p - 1], d[p - 1], d[p], tiny_ex)) --p;
+                    if (++steps > max_steps) {
+                        failed = true;
+                        break;
+                    }
+                    rot += q - p;
+                    const dw eq = e[q - 1];
+                    const dw dd = dw_scale(dw_sub(d[q - 1], d[q]), 0.5f);
+                    dwacc hh = acc_zero();
+                    acc_sqr(hh, dd);
+                    acc_sqr(hh, eq);
+                    const dw h = dw_sqrt(acc_val(hh));
+                    const dw den = (dd.h >= 0.f) ? dw_add(dd, h) : dw_sub(dd, h);
+                    const dw mu = dw_sub(d[q], dw_div(dw_sqr(eq), den));
+                    dk = d[p];
+                    ek = e[p];
+                    x = dw_sub(dk, mu);
+                    z = ek;
+                    kr = p;
+                    sweeping = true;
+                    __syncwarp(gmask);
+                    if (gl == 0 && p > 0) e[p - 1] = zero;
+                }
+                const dw bb = d[kr + 1];
+                const dw en = (kr + 1 < q) ? e[kr + 1] : zero;
+                __syncwarp(gmask);
+                dw za[RPL], zb[RPL];
+#pragma unroll
+                for (int ii = 0; ii < RPL; ++ii) {
+                    const int i = gl + PG * ii;
+                    if (i < R) {
+                        za[ii] = A(i, kp);
+                        zb[ii] = A(i, kp + 1);
+                    }
+                }
+                const int ex = max(f_expo(x.h), f_expo(z.h));   // scaled as in p2_eig_dw.cuh
+                const bool nz = ex > 0;
+                const float xsc = f_pow2(127 - ex);
+                const dw xs = dw_scale(x, xsc), zs = dw_scale(z, xsc);
+                dwacc ta = acc_zero();
+                acc_sqr(ta, xs);
+                acc_sqr(ta, zs);
+                const dw tt = acc_val(ta);
+                const dw ir = dw_rsqrt(nz ? tt : one);
+                const dw c = nz ? dw_mul(xs, ir) : one;
+                const dw s = nz ? dw_neg(dw_mul(zs, ir)) : zero;
+                if (gl == 0 && kr > p) e[kr - 1] = nz ? dw_scale(dw_mul(tt, ir), f_pow2(ex - 127)) : zero;
+                const dw cc = dw_sqr(c), ss = dw_sqr(s), cs = dw_mul(c, s);
+                const dw cs2g = dw_scale(dw_mul(cs, ek), 2.f);
+                dwacc a0 = acc_from(dw_neg(cs2g));
+                acc_fma(a0, cc, dk);
+                acc_fma(a0, ss, bb);
+                const dw dkn = acc_val(a0);
+                if (gl == 0) d[kr] = dkn;
+                dwacc a1 = acc_from(cs2g);
+                acc_fma(a1, ss, dk);
+                acc_fma(a1, cc, bb);
+                const dw dk1 = acc_val(a1);
+                dwacc a2 = acc_zero();
+                acc_fma(a2, cs, dw_sub(dk, bb));
+                acc_fma(a2, dw_sub(cc, ss), ek);
+                const dw ekn = acc_val(a2);
+                {
+                    const dw nsp = dw_neg(sp);
+#pragma unroll
+                    for (int ii = 0; ii < RPL; ++ii) {
+                        const int i = gl + PG * ii;
+                        if (i < R) {
+                            A(i, kp) = dw_dot2(cp, za[ii], nsp, zb[ii]);
+                            A(i, kp + 1) = dw_dot2(sp, za[ii], cp, zb[ii]);
+                        }
+                    }
+                }
+                kp = kr;
+                cp = c;
+                sp = s;
+                if (++kr < q) {
+                    z = dw_neg(dw_mul(s, en));
+                    ek = dw_mul(c, en);
+                    x = ekn;
+                    dk = dk1;
+                } else {
+                    if (gl == 0) {
+                        d[q] = dk1;
+                        e[q - 1] = ekn;
+                    }
+                    sweeping = false;
+                    __syncwarp(gmask);
+                }
             }
             __syncwarp(gmask);
-            double tv[RB];
-#pragma unroll
-            for (int i = 0; i < RB; ++i)
-                if (i < R) tv[i] = t[i];
+            if (R > 1) {                                 // flush the last rotation
+                const dw nsp = dw_neg(sp);
+                for (int i = gl; i < R; i += PG) {
+                    const dw zk = A(i, kp), zk1 = A(i, kp + 1);
+                    A(i, kp) = dw_dot2(cp, zk, nsp, zk1);
+                    A(i, kp + 1) = dw_dot2(sp, zk, cp, zk1);
+                }
+            }
+            if (failed && gl == 0) atomicOr(&st->flags, FLAG_EIG_NOCONV);
             __syncwarp(gmask);
+
+            // ---- cut, Z scaled by d^-1/4 (columns split over lanes) ---------
+            float lmax = 0.f;
+            for (int i = gl; i < R; i += PG) lmax = fmaxf(lmax, d[i].h);
+            lmax = group_maxf(gmask, lmax);
+            const float cut = rtol2 * lmax;
+            for (int i = gl; i < R; i += PG) {
+                const dw di = d[i];
+                const dw sf = (lmax > 0.f && di.h > cut) ? dw_sqrt(dw_rsqrt(di)) : zero;
+                for (int r = 0; r < R; ++r) A(r, i) = dw_mul(A(r, i), sf);
+            }
+            __syncwarp(gmask);
+            // ---- T = 2^so Z' (Z'^T H' S'), one column of T at a time ----------
+            const int so = (sm + sg) / 2;
+            const float o1 = f_pow2(so / 2), o2 = f_pow2(so - so / 2);
 #pragma unroll 1
-            for (int ii = 0; ii < RPL; ++ii) {
-                const int r = gl + PG * ii;
-                if (r >= R) break;
-                double s = 0.0;
+            for (int c = 0; c < R; ++c) {
+                for (int i = gl; i < R; i += PG) {       // t = Z'^T h'_c on my columns
+                    dwacc s = acc_zero();
+                    for (int r = 0; r < R; ++r) acc_fmaf(s, A(r, i), Hs[r * R + c]);
+                    t[i] = acc_val(s);
+                }
+                __syncwarp(gmask);
+                dw tv[RB];
 #pragma unroll
                 for (int i = 0; i < RB; ++i)
-                    if (i < R) s = fma(A(r, i), tv[i], s);
-                T[tb + r * R + c] = (float)s;
+                    if (i < R) tv[i] = t[i];
+                __syncwarp(gmask);
+                const float wc = wv[c];
+#pragma unroll 1
+                for (int ii = 0; ii < RPL; ++ii) {
+                    const int r = gl + PG * ii;
+                    if (r >= R) break;
+                    dwacc s = acc_zero();
+#pragma unroll
+                    for (int i = 0; i < RB; ++i)
+                        if (i < R) acc_fma(s, A(r, i), tv[i]);
+                    const dw v = dw_mulf(acc_val(s), wc);
+                    T[tb + r * R + c] = f_mul(f_mul(v.h, o1), o2);
+                }
             }
+            if (gl == 0) flops = polar_fixed_flops(R) + qr_flops(R, steps, rot);
         }
-        if (gl == 0) flops = polar_fixed_flops(R) + qr_flops(R, steps, rot);
     }
     add_flops(st, flops);
 }

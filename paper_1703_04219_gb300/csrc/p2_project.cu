@@ -28,7 +28,7 @@ struct p2_projector {
     // internal format
     p2::DevX X;
     // per subject
-    double *d_G = nullptr;
+    p2::dw *d_G = nullptr;
     float *d_S = nullptr, *d_T = nullptr;
     p2::SmallState *d_st = nullptr;     // private copy of H64, G3inv; flags
     int pending_flags_check = 0;
@@ -86,7 +86,7 @@ __global__ void k_proj_subjects(const int64_t *__restrict__ sp, const int64_t *_
 
 // s <- coldot(H, T G) (V^TV * H^TH)^+ for every subject; one warp per subject.
 __global__ void __launch_bounds__(256) k_proj_update(const float *__restrict__ T,
-                                                     const double *__restrict__ G,
+                                                     const dw *__restrict__ G,
                                                      const float *__restrict__ H,
                                                      const SmallState *__restrict__ st, float *S,
                                                      int64_t K, int R) {
@@ -105,14 +105,14 @@ __global__ void __launch_bounds__(256) k_proj_update(const float *__restrict__ T
     const int64_t nwarps = (int64_t)gridDim.x * nw;
     for (int64_t k = (int64_t)blockIdx.x * nw + warp; k < K; k += nwarps) {
         const float *Tg = T + (size_t)k * R * R;
-        const double *Gg = G + (size_t)k * P;
+        const dw *Gg = G + (size_t)k * P;
         for (int e = lane; e < R * R; e += 32) Ts[e] = Tg[e];
         for (int p = lane; p < P; p += 32) {
             int r = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
             while ((r + 1) * (r + 2) / 2 <= p) ++r;
             while (r * (r + 1) / 2 > p) --r;
             const int c = p - r * (r + 1) / 2;
-            const float g = (float)Gg[p];
+            const float g = Gg[p].h;
             Gs[r * R + c] = g;
             Gs[c * R + r] = g;
         }

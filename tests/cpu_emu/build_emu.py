@@ -76,7 +76,8 @@ def build() -> str:
             if f.endswith(".cu"):
                 units.append(os.path.join(gen, name))
     units.append(os.path.join(HERE, "emu_rt.cpp"))
-    flags = ["g++", "-std=c++20", "-O1", "-g", "-fsanitize=address", "-fno-omit-frame-pointer",
+    flags = ["g++", "-std=c++20", "-O1", "-g", "-ffp-contract=off", "-fsanitize=address",
+             "-fno-omit-frame-pointer",
              "-fPIC", "-I", os.path.join(HERE, "fake"), "-I", CSRC]
     objs = [os.path.join(BUILD, os.path.basename(u)[:-4] + ".o") for u in units]
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:

@@ -39,7 +39,7 @@ extern thread_local dim3 blockDim, gridDim;
 
 typedef int cudaError_t;
 enum { cudaSuccess = 0, cudaErrorInvalidValue = 1, cudaErrorMemoryAllocation = 2,
-       cudaErrorNotSupported = 801 };
+       cudaErrorInvalidConfiguration = 9, cudaErrorNotSupported = 801 };
 typedef void *cudaStream_t;
 typedef void *cudaEvent_t;
 typedef void *cudaGraph_t;

@@ -1,5 +1,6 @@
 """The library's CUDA kernels run on the CPU emulator (tests/cpu_emu) under
-AddressSanitizer: one ALS iteration at R = 5 (lane-per-subject Procrustes),
+AddressSanitizer: one ALS iteration at R = 5 and R = 10 (lane-per-subject
+Procrustes),
 at R = 13 (grouped Procrustes kernel) and at R = 5 with bfloat16 storage,
 and a projection of new subjects.
 Every device buffer and every block's shared memory is a heap block of its
@@ -18,6 +19,7 @@ EMU = os.path.join(HERE, "cpu_emu")
 
 CASES = {
     "iterate_r5": ["iterate", "tiny", "24", "5"],
+    "iterate_r10": ["iterate", "tiny", "24", "10"],
     "iterate_r13": ["iterate", "tiny", "16", "13"],
     "iterate_r5_bf16": ["iterate", "tiny", "24", "5", "bf16"],
     "project_r12": ["project", "12", "3"],
@@ -64,7 +66,7 @@ def _result(runs, name):
     return json.loads(so.strip().splitlines()[-1])
 
 
-@pytest.mark.parametrize("name", ["iterate_r5", "iterate_r13"])
+@pytest.mark.parametrize("name", ["iterate_r5", "iterate_r10", "iterate_r13"])
 def test_emulated_iteration_is_in_bounds_and_matches_oracle(emulated_runs, name):
     err = _result(emulated_runs, name)
     for key in ("M1", "M2", "M3", "H", "V", "W"):

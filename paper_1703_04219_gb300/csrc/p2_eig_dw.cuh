@@ -142,27 +142,45 @@ P2_HD void tridiagonalize_dw(int n_rt, DwMat A, DwVec d, DwVec e) {
     }
 }
 
+// count of leading zero bits of a non-zero 64-bit word
+P2_HD int p2_clz64(unsigned long long v) {
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)v);
+#else
+    return __builtin_clzll(v);
+#endif
+}
+
 // Implicit symmetric QR with Wilkinson shift on the tridiagonal (d, e);
-// rotations are accumulated into the columns of Z (n x n).  Returns the
-// number of QR steps taken, or -1 if max_steps was exceeded (d then holds
+// rotations are accumulated into the columns of Z (n x n, n <= 64).  Returns
+// the number of QR steps taken, or -1 if max_steps was exceeded (d then holds
 // the current, partly converged, diagonal).  *rotations (if given) is
 // incremented by the number of Givens rotations applied.
 //
 // One flat loop, one Givens rotation per trip, so that the lanes of a warp
-// run the rotation body together whatever their sweep boundaries.  The
-// trip that forms rotation k applies rotation k - 1 to Z (the two are
-// independent, so the serial scalar recurrence overlaps the vector work);
-// the pending rotation carries over sweep boundaries and is flushed once at
-// the end.  Each rotation is formed from one reciprocal square root:
-// c = x / r, s = -z / r, r = t / sqrt(t) with t = x^2 + z^2, after scaling
-// (x, z) by a power of two so that t cannot underflow (FP32's exponent range
-// is far narrower than FP64's, and the converging sub-diagonal and the bulge
-// can both become tiny).
+// run the same instructions whatever their sweep boundaries:
+//  * the deflation tests of all n - 1 sub-diagonal positions are taken at
+//    once into a bit mask, and the bottom q of the active block and its top p
+//    follow from leading-zero counts (no serial scan);
+//  * the Wilkinson shift of that block is formed on every trip and used by
+//    the lanes that start a sweep;
+//  * the trip that forms rotation k applies rotation k - 1 to Z (the pending
+//    rotation, carried over sweep boundaries and flushed at the end): its
+//    columns are loaded at the top of the trip and everything is stored at
+//    the bottom, so the serial scalar recurrence and the vector work are free
+//    to overlap.
+// Each rotation is formed from one reciprocal square root: c = x / r,
+// s = -z / r, r = t / sqrt(t) with t = x^2 + z^2, after scaling (x, z) by a
+// power of two so that t cannot underflow (FP32's exponent range is far
+// narrower than FP64's, and the converging sub-diagonal and the bulge can
+// both become tiny).
 template <int N>
 P2_HD int tridiagonal_qr_dw(int n_rt, DwMat Z, DwVec d, DwVec e, int max_steps,
                             int *rotations = nullptr) {
+    constexpr int NA = N > 0 ? N : 64;                   // register-array bound
     const int n = N > 0 ? N : n_rt;
     const dw one = dw_f(1.f), zero = dw_f(0.f);
+    if (n < 2) return 0;
     float an = 0.f;
     for (int i = 0; i < n; ++i) {
         float r = fabsf(d[i].h);
@@ -179,36 +197,54 @@ P2_HD int tridiagonal_qr_dw(int n_rt, DwMat Z, DwVec d, DwVec e, int max_steps,
     dw cp = one, sp = zero;
 #pragma unroll 1
     while (true) {
+        dw za[NA], zb[NA];                               // pending rotation's columns
+#pragma unroll
+        for (int i = 0; i < NA; ++i)
+            if (i < n) {
+                za[i] = Z(i, kp);
+                zb[i] = Z(i, kp + 1);
+            }
+        // ---- the block a new sweep would take, and its shift ----------------
+        unsigned long long nm = 0;                        // bit i: e[i] negligible
+#pragma unroll
+        for (int i = 0; i + 1 < NA; ++i)
+            if (i + 1 < n && dw_negligible(e[i], d[i], d[i + 1], tiny_ex)) nm |= 1ull << i;
+        const unsigned long long nn = ~nm & ((1ull << q) - 1);
+        const int qn = nn ? 64 - p2_clz64(nn) : 0;        // top non-negligible position + 1
+        const unsigned long long nb = qn > 1 ? nm & ((1ull << (qn - 1)) - 1) : 0ull;
+        const int pn = nb ? 64 - p2_clz64(nb) : 0;        // top of the unreduced block
+        const int qs = qn > 0 ? qn : 1;
+        const dw eq = e[qs - 1];
+        const dw dd = dw_scale(dw_sub(d[qs - 1], d[qs]), 0.5f);
+        dwacc hh = acc_zero();
+        acc_sqr(hh, dd);
+        acc_sqr(hh, eq);
+        const dw h = dw_sqrt(acc_val(hh));
+        const dw den = (dd.h >= 0.f) ? dw_add(dd, h) : dw_sub(dd, h);
+        const dw den_s = den.h != 0.f ? den : one;        // (qn = 0 only: value unused)
+        const dw mu = dw_sub(d[qs], dw_div(dw_sqr(eq), den_s));
+        const dw dpn = d[pn], epn = e[pn];
+        bool clear_top = false;
         if (!sweeping) {
-            while (q > 0 && dw_negligible(e[q - 1], d[q - 1], d[q], tiny_ex)) --q;
-            if (q == 0) break;
-            p = q - 1;
-            while (p > 0 && !dw_negligible(e[p - 1], d[p - 1], d[p], tiny_ex)) --p;
+            if (qn == 0) break;
             if (++steps > max_steps) {
                 status = -1;
                 break;
             }
+            q = qn;
+            p = pn;
             rot += q - p;
-            // Wilkinson shift from the trailing 2 x 2 block
-            const dw eq = e[q - 1];
-            const dw dd = dw_scale(dw_sub(d[q - 1], d[q]), 0.5f);
-            dwacc hh = acc_zero();
-            acc_sqr(hh, dd);
-            acc_sqr(hh, eq);
-            const dw h = dw_sqrt(acc_val(hh));
-            const dw den = (dd.h >= 0.f) ? dw_add(dd, h) : dw_sub(dd, h);
-            const dw mu = dw_sub(d[q], dw_div(dw_sqr(eq), den));
-            dk = d[p];
-            ek = e[p];
-            x = dw_sub(dk, mu);
-            z = ek;
+            dk = dpn;
+            ek = epn;
+            x = dw_sub(dpn, mu);
+            z = epn;
             kr = p;
             sweeping = true;
-            if (p > 0) e[p - 1] = zero;
+            clear_top = p > 0;
         }
+        // ---- rotation kr -----------------------------------------------------
         const dw bb = d[kr + 1];
         const dw en = (kr + 1 < q) ? e[kr + 1] : zero;
-        // (x, z) scaled by a power of two before squaring: t in [1, 8)
         const int exx = f_expo(x.h), exz = f_expo(z.h);
         const int ex = exx > exz ? exx : exz;
         const bool nz = ex > 0;
@@ -221,13 +257,13 @@ P2_HD int tridiagonal_qr_dw(int n_rt, DwMat Z, DwVec d, DwVec e, int max_steps,
         const dw ir = dw_rsqrt(nz ? tt : one);
         const dw c = nz ? dw_mul(xs, ir) : one;
         const dw s = nz ? dw_neg(dw_mul(zs, ir)) : zero;
-        if (kr > p) e[kr - 1] = nz ? dw_scale(dw_mul(tt, ir), f_pow2(ex - 127)) : zero;
+        const dw r = nz ? dw_scale(dw_mul(tt, ir), f_pow2(ex - 127)) : zero;
         const dw cc = dw_sqr(c), ss = dw_sqr(s), cs = dw_mul(c, s);
         const dw cs2g = dw_scale(dw_mul(cs, ek), 2.f);
         dwacc a0 = acc_from(dw_neg(cs2g));
         acc_fma(a0, cc, dk);
         acc_fma(a0, ss, bb);
-        d[kr] = acc_val(a0);
+        const dw dkn = acc_val(a0);
         dwacc a1 = acc_from(cs2g);
         acc_fma(a1, ss, dk);
         acc_fma(a1, cc, bb);
@@ -236,14 +272,21 @@ P2_HD int tridiagonal_qr_dw(int n_rt, DwMat Z, DwVec d, DwVec e, int max_steps,
         acc_fma(a2, cs, dw_sub(dk, bb));
         acc_fma(a2, dw_sub(cc, ss), ek);
         const dw ekn = acc_val(a2);
-        {   // pending rotation (kp, cp, sp) on columns kp, kp + 1 of Z
+        // ---- pending rotation on columns kp, kp + 1, then all stores ----------
+        {
             const dw nsp = dw_neg(sp);
-            for (int i = 0; i < n; ++i) {
-                const dw za = Z(i, kp), zb = Z(i, kp + 1);
-                Z(i, kp) = dw_dot2(cp, za, nsp, zb);
-                Z(i, kp + 1) = dw_dot2(sp, za, cp, zb);
-            }
+#pragma unroll
+            for (int i = 0; i < NA; ++i)
+                if (i < n) {
+                    const dw a = dw_dot2(cp, za[i], nsp, zb[i]);
+                    const dw b = dw_dot2(sp, za[i], cp, zb[i]);
+                    Z(i, kp) = a;
+                    Z(i, kp + 1) = b;
+                }
         }
+        if (clear_top) e[p - 1] = zero;
+        if (kr > p) e[kr - 1] = r;
+        d[kr] = dkn;
         kp = kr;
         cp = c;
         sp = s;
@@ -258,7 +301,7 @@ P2_HD int tridiagonal_qr_dw(int n_rt, DwMat Z, DwVec d, DwVec e, int max_steps,
             sweeping = false;
         }
     }
-    if (n > 1) {   // flush the last rotation
+    {   // flush the last rotation
         const dw nsp = dw_neg(sp);
         for (int i = 0; i < n; ++i) {
             const dw za = Z(i, kp), zb = Z(i, kp + 1);

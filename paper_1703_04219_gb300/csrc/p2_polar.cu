@@ -33,7 +33,7 @@ static __device__ __forceinline__ int pk(int i, int j) {   // packed lower index
 // matrix (R x R) and the tridiagonal (d, e), interleaved across the lanes:
 // R^2 + 2R double-words per lane.
 template <int R>
-__global__ void __launch_bounds__(256) k_polar_reg(const dw *__restrict__ G,
+__global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
                                                    const float *__restrict__ W, SmallState *st,
                                                    float *T, int64_t K, float rtol2) {
     constexpr int P = R * (R + 1) / 2;

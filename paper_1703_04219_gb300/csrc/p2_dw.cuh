@@ -126,6 +126,15 @@ P2_HD float f_pow2(int n) {
 #endif
 }
 
+// count of leading zero bits of a non-zero 64-bit word
+P2_HD int p2_clz64(unsigned long long v) {
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)v);
+#else
+    return __builtin_clzll(v);
+#endif
+}
+
 P2_HD dw dw_f(float h) { return dw{h, 0.f}; }
 
 // a + b = s + e exactly (TwoSum, any a, b)

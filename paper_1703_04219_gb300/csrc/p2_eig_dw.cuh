@@ -142,15 +142,6 @@ P2_HD void tridiagonalize_dw(int n_rt, DwMat A, DwVec d, DwVec e) {
     }
 }
 
-// count of leading zero bits of a non-zero 64-bit word
-P2_HD int p2_clz64(unsigned long long v) {
-#ifdef __CUDA_ARCH__
-    return __clzll((long long)v);
-#else
-    return __builtin_clzll(v);
-#endif
-}
-
 // Implicit symmetric QR with Wilkinson shift on the tridiagonal (d, e);
 // rotations are accumulated into the columns of Z (n x n, n <= 64).  Returns
 // the number of QR steps taken, or -1 if max_steps was exceeded (d then holds

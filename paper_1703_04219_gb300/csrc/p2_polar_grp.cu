@@ -18,8 +18,7 @@ static void launch_grp(const p2_ctx *c, const dw *G, const float *W, SmallState 
     const size_t hbytes = grp_hdws(R) * sizeof(dw);
     // 16 bytes kept for the kernel's static shared memory
     int spb = (int)(((size_t)c->geo.smem_optin - hbytes - 16) / per);
-    if (spb > 32) spb = 32;
-    if (spb >= 4) spb = (spb / 4) * 4;
+    if (spb > 32) spb = 32;                 // four subjects per warp; a last partial warp idles its spare groups
     if (spb < 1) spb = 1;
     const int threads = ((spb + 3) / 4) * 32;
     const size_t smem = hbytes + (size_t)spb * per;

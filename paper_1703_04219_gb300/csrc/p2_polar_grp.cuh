@@ -329,10 +329,20 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
 #pragma unroll 1
             while (true) {
                 if (!sweeping) {
-                    while (q > 0 && dw_negligible(e[q - 1], d[q - 1], d[q], tiny_ex)) --q;
+                    // deflation tests of all positions at once, split over
+                    // the eight lanes and OR-ed together; the active block
+                    // follows from leading-zero counts
+                    unsigned long long nm = 0;
+                    for (int i = gl; i + 1 < R; i += PG)
+                        if (dw_negligible(e[i], d[i], d[i + 1], tiny_ex)) nm |= 1ull << i;
+                    nm |= __shfl_xor_sync(gmask, nm, 4);
+                    nm |= __shfl_xor_sync(gmask, nm, 2);
+                    nm |= __shfl_xor_sync(gmask, nm, 1);
+                    const unsigned long long nn = ~nm & ((1ull << q) - 1);
+                    q = nn ? 64 - p2_clz64(nn) : 0;
                     if (q == 0) break;
-                    p = q - 1;
-                    while (p > 0 && !dw_negligible(e[p - 1], d[p - 1], d[p], tiny_ex)) --p;
+                    const unsigned long long nb = q > 1 ? nm & ((1ull << (q - 1)) - 1) : 0ull;
+                    p = nb ? 64 - p2_clz64(nb) : 0;
                     if (++steps > max_steps) {
                         failed = true;
                         break;
@@ -378,14 +388,13 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                 const dw ir = dw_rsqrt(nz ? tt : one);
                 const dw c = nz ? dw_mul(xs, ir) : one;
                 const dw s = nz ? dw_neg(dw_mul(zs, ir)) : zero;
-                if (gl == 0 && kr > p) e[kr - 1] = nz ? dw_scale(dw_mul(tt, ir), f_pow2(ex - 127)) : zero;
+                const dw rr = nz ? dw_scale(dw_mul(tt, ir), f_pow2(ex - 127)) : zero;
                 const dw cc = dw_sqr(c), ss = dw_sqr(s), cs = dw_mul(c, s);
                 const dw cs2g = dw_scale(dw_mul(cs, ek), 2.f);
                 dwacc a0 = acc_from(dw_neg(cs2g));
                 acc_fma(a0, cc, dk);
                 acc_fma(a0, ss, bb);
                 const dw dkn = acc_val(a0);
-                if (gl == 0) d[kr] = dkn;
                 dwacc a1 = acc_from(cs2g);
                 acc_fma(a1, ss, dk);
                 acc_fma(a1, cc, bb);
@@ -404,6 +413,10 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                             A(i, kp + 1) = dw_dot2(sp, za[ii], cp, zb[ii]);
                         }
                     }
+                }
+                if (gl == 0) {
+                    if (kr > p) e[kr - 1] = rr;
+                    d[kr] = dkn;
                 }
                 kp = kr;
                 cp = c;

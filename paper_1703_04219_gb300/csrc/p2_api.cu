@@ -81,6 +81,10 @@ static void free_data(p2_ctx *c) {
     dfree(c, &c->d_segpart, (size_t)c->X.nseg * R);
     dfree(c, &c->d_W, K * R);
     dfree(c, &c->d_M3, K * R);
+    dfree(c, &c->d_qrcnt, K);
+    dfree(c, &c->d_order, K);
+    dfree(c, &c->d_rank, K);
+    dfree(c, &c->d_binoff, (size_t)((K + P2_ORDER_CHUNK - 1) / P2_ORDER_CHUNK) * P2_ORDER_BINS);
     dfree(c, &c->d_T, K * R * R);
     dfree(c, &c->d_G, K * P);
     dfree(c, &c->d_Gf, K * P);
@@ -130,6 +134,12 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
     P2_TRY(dalloc(c, &c->d_M2, (size_t)J * R));
     P2_TRY(dalloc(c, &c->d_W, (size_t)K * R));
     P2_TRY(dalloc(c, &c->d_M3, (size_t)K * R));
+    P2_TRY(dalloc(c, &c->d_qrcnt, (size_t)K));
+    P2_TRY(dalloc(c, &c->d_order, (size_t)K));
+    P2_TRY(dalloc(c, &c->d_rank, (size_t)K));
+    P2_TRY(dalloc(c, &c->d_binoff,
+                  (size_t)((K + P2_ORDER_CHUNK - 1) / P2_ORDER_CHUNK) * P2_ORDER_BINS));
+    P2_CUDA_TRY(cudaMemsetAsync(c->d_qrcnt, 0, sizeof(int32_t) * (size_t)K, c->stream));
     P2_TRY(dalloc(c, &c->d_G, (size_t)K * P));
     P2_TRY(dalloc(c, &c->d_Gf, (size_t)K * P));
     P2_CUDA_TRY(cudaMemsetAsync(c->d_M3, 0, sizeof(float) * (size_t)K * R, c->stream));

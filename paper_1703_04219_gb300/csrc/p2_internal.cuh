@@ -147,6 +147,12 @@ struct p2_ctx {
     p2::dw *d_G = nullptr;      // K x P packed lower Gram of Z_k, double-word (hi + lo)
     float *d_Gf = nullptr;      // K x P the same rounded to float (mode-1 statistics)
     float *d_M3 = nullptr;      // K x R
+    // Q-step order: subjects sorted by the QR rotation count of their previous
+    // Q-step, so the lanes of a warp converge after similar numbers of trips
+    int32_t *d_qrcnt = nullptr;  // [K] rotations of the last Q-step (0 before the first)
+    int32_t *d_order = nullptr;  // [K] subject processed by each Procrustes slot
+    int32_t *d_rank = nullptr;   // [K] rank within the subject's bin and chunk
+    int32_t *d_binoff = nullptr; // [nchunk x 256] bin counts, then offsets
     double *d_M2 = nullptr;     // J x R (relabelled rows)
     float *d_P = nullptr;       // N x R rows of P_k = Z_k F_k (mode-2 pass)
     double *d_segpart = nullptr; // nseg x R partial sums of the mode-2 reduction
@@ -191,12 +197,19 @@ int configure_kernels(p2_ctx *c);    // smem attributes etc.
 int polar_configure(p2_ctx *c);
 cudaError_t launch_polar(p2_ctx *c);
 cudaError_t launch_polar_on(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
-                            float *T, int64_t K, cudaStream_t s);
+                            float *T, int64_t K, cudaStream_t s, const int32_t *order = nullptr,
+                            int32_t *qrcnt = nullptr);
+// subjects per chunk of the ordering kernels (p2_polar.cu)
+#define P2_ORDER_CHUNK 4096
+#define P2_ORDER_BINS 256
+// kernels launched by launch_polar (the ordering and the Procrustes kernel)
+constexpr int POLAR_LAUNCHES = 4;
 // Gram of Z_k = X_k V for a batch of new subjects (p2_kernels.cu)
 cudaError_t launch_gram(const p2_ctx *c, const XView &X, const SmallState *st, dw *G,
                         cudaStream_t s);
 // R > 12: grouped Procrustes kernel (p2_polar_grp.cu)
 cudaError_t polar_grp_configure(int cap);
 cudaError_t launch_polar_grp(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
-                             float *T, int64_t K, cudaStream_t s, double rtol2);
+                             float *T, int64_t K, cudaStream_t s, double rtol2,
+                             const int32_t *order, int32_t *qrcnt);
 }  // namespace p2

@@ -1273,7 +1273,7 @@ static int enqueue_qstep(p2_ctx *c, int with_fit) {
             set_error("launch of the Procrustes kernel failed: %s", cudaGetErrorString(e));
             return P2_ECUDA;
         }
-        c->enqueued += 1;
+        c->enqueued += POLAR_LAUNCHES;
     }
     mark(c, 5);
     const int P = R * (R + 1) / 2;

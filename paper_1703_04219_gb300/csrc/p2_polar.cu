@@ -35,7 +35,9 @@ static __device__ __forceinline__ int pk(int i, int j) {   // packed lower index
 template <int R>
 __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
                                                    const float *__restrict__ W, SmallState *st,
-                                                   float *T, int64_t K, float rtol2) {
+                                                   float *T, int64_t K, float rtol2,
+                                                   const int32_t *__restrict__ order,
+                                                   int32_t *qrcnt) {
     constexpr int P = R * (R + 1) / 2;
     constexpr int HW = (R * R + 1) / 2;                  // double-word slots holding H
     extern __shared__ __align__(16) dw smd[];
@@ -51,9 +53,10 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
     __syncthreads();
     for (int i = t; i < R * R; i += NT) Hs[i] = f_mul(Hs[i], hsc);
     __syncthreads();
-    const int64_t k = (int64_t)blockIdx.x * NT + t;
+    const int64_t slot = (int64_t)blockIdx.x * NT + t;
     unsigned long long flops = 0;
-    if (k < K) {
+    if (slot < K) {
+        const int64_t k = order ? (int64_t)order[slot] : slot;
         const dw zero = dw_f(0.f);
         DwMat A{th + t, NT, R};
         DwVec d{th + (size_t)R * R * NT + t, NT};
@@ -115,6 +118,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
         if (eg == 0 || ew == 0 || em == 0) {
             // G, W or M is zero (or below the normal range): A_k = 0, Q_k = 0
             for (int i = 0; i < R * R; ++i) T[tb + i] = 0.f;
+            if (qrcnt) qrcnt[k] = 0;
         } else {
             // M'' = M' 2^sm with max diag in [0.5, 2); sm + sg even so that
             // M^{-1/2} H S = 2^{(sm + sg) / 2} M''^{-1/2} H' S'
@@ -169,14 +173,70 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
                 }
             }
             flops = polar_fixed_flops(R) + qr_flops(R, steps, rot);
+            if (qrcnt) qrcnt[k] = rot;
         }
     }
     add_flops(st, flops);
 }
 
+// ---- Q-step order -------------------------------------------------------------
+// Lanes (or lane groups) of a warp run their QR iterations in lock step until
+// the slowest has converged, so subjects are processed in decreasing order of
+// the rotation count of their previous Q-step (which changes little between
+// ALS iterations): a counting sort into 256 bins of min(count, 255), chunked
+// so that no global atomics are needed.  The order within a bin is arbitrary;
+// every subject's result is independent of the slot that computes it.
+__global__ void __launch_bounds__(256) k_order_count(const int32_t *__restrict__ cnt, int64_t K,
+                                                      int32_t *rank, int32_t *binoff) {
+    __shared__ int h[P2_ORDER_BINS];
+    for (int i = threadIdx.x; i < P2_ORDER_BINS; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t a = (int64_t)blockIdx.x * P2_ORDER_CHUNK;
+    const int64_t b = (a + P2_ORDER_CHUNK < K) ? (a + P2_ORDER_CHUNK) : K;
+    for (int64_t k = a + threadIdx.x; k < b; k += blockDim.x) {
+        const int v = min(max((int)cnt[k], 0), P2_ORDER_BINS - 1);
+        rank[k] = atomicAdd(&h[v], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < P2_ORDER_BINS; i += blockDim.x)
+        binoff[(size_t)blockIdx.x * P2_ORDER_BINS + i] = h[i];
+}
+
+// one block of P2_ORDER_BINS threads: per-chunk bin counts -> slot offsets,
+// bins in decreasing order of the count
+__global__ void __launch_bounds__(P2_ORDER_BINS) k_order_scan(int32_t *binoff, int nchunk) {
+    __shared__ int tot[P2_ORDER_BINS];
+    const int b = threadIdx.x;
+    int run = 0;
+    for (int j = 0; j < nchunk; ++j) {
+        const int v = binoff[(size_t)j * P2_ORDER_BINS + b];
+        binoff[(size_t)j * P2_ORDER_BINS + b] = run;
+        run += v;
+    }
+    tot[b] = run;
+    __syncthreads();
+    int off = 0;
+    for (int b2 = P2_ORDER_BINS - 1; b2 > b; --b2) off += tot[b2];
+    for (int j = 0; j < nchunk; ++j) binoff[(size_t)j * P2_ORDER_BINS + b] += off;
+}
+
+__global__ void __launch_bounds__(256) k_order_place(const int32_t *__restrict__ cnt,
+                                                      const int32_t *__restrict__ rank,
+                                                      const int32_t *__restrict__ binoff,
+                                                      int64_t K, int32_t *order) {
+    const int64_t a = (int64_t)blockIdx.x * P2_ORDER_CHUNK;
+    const int64_t b = (a + P2_ORDER_CHUNK < K) ? (a + P2_ORDER_CHUNK) : K;
+    const int32_t *off = binoff + (size_t)blockIdx.x * P2_ORDER_BINS;
+    for (int64_t k = a + threadIdx.x; k < b; k += blockDim.x) {
+        const int v = min(max((int)cnt[k], 0), P2_ORDER_BINS - 1);
+        order[off[v] + rank[k]] = (int32_t)k;
+    }
+}
+
 template <int R>
 static int launch_reg(const p2_ctx *c, const dw *G, const float *W, SmallState *st, float *T,
-                      int64_t K, cudaStream_t s, float rtol2) {
+                      int64_t K, cudaStream_t s, float rtol2, const int32_t *order,
+                      int32_t *qrcnt) {
     const int cap = c->geo.smem_optin;
     const size_t hbytes = (size_t)((R * R + 1) / 2) * sizeof(dw);
     const size_t per = (size_t)(R * R + 2 * R) * sizeof(dw);
@@ -186,7 +246,7 @@ static int launch_reg(const p2_ctx *c, const dw *G, const float *W, SmallState *
     if (nt < 32) return -1;
     const size_t smem = hbytes + (size_t)nt * per;
     const int nblk = (int)((K + nt - 1) / nt);
-    k_polar_reg<R><<<nblk, nt, smem, s>>>(G, W, st, T, K, rtol2);
+    k_polar_reg<R><<<nblk, nt, smem, s>>>(G, W, st, T, K, rtol2, order, qrcnt);
     return 0;
 }
 
@@ -219,16 +279,17 @@ int polar_configure(p2_ctx *c) {
 // Enqueue the Procrustes kernel for K subjects (Gram G, weights W, state st
 // holding H64) writing T; returns a cudaError_t.
 cudaError_t launch_polar_on(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
-                            float *T, int64_t K, cudaStream_t s) {
+                            float *T, int64_t K, cudaStream_t s, const int32_t *order,
+                            int32_t *qrcnt) {
     const int R = c->R;
     const double rtol2 = c->opt.rank_rtol * c->opt.rank_rtol;
     if (K <= 0) return cudaSuccess;
-    if (R > 12) return launch_polar_grp(c, G, W, st, T, K, s, rtol2);
+    if (R > 12) return launch_polar_grp(c, G, W, st, T, K, s, rtol2, order, qrcnt);
     const float rt2 = (float)rtol2;
     int rc = -1;
     switch (R) {
 #define P2_CASE(r) \
-        case r: rc = launch_reg<r>(c, G, W, st, T, K, s, rt2); break;
+        case r: rc = launch_reg<r>(c, G, W, st, T, K, s, rt2, order, qrcnt); break;
         P2_CASE(1) P2_CASE(2) P2_CASE(3) P2_CASE(4) P2_CASE(5) P2_CASE(6)
         P2_CASE(7) P2_CASE(8) P2_CASE(9) P2_CASE(10) P2_CASE(11) P2_CASE(12)
 #undef P2_CASE
@@ -238,8 +299,20 @@ cudaError_t launch_polar_on(const p2_ctx *c, const dw *G, const float *W, SmallS
     return cudaGetLastError();
 }
 
+// The Q-step of the iteration: order the subjects by their last rotation
+// counts, then the Procrustes kernel (POLAR_LAUNCHES kernels in all).
 cudaError_t launch_polar(p2_ctx *c) {
-    return launch_polar_on(c, c->d_G, c->d_W, c->d_s, c->d_T, c->X.K, c->stream);
+    const int64_t K = c->X.K;
+    if (K <= 0) return cudaSuccess;
+    const int nchunk = (int)((K + P2_ORDER_CHUNK - 1) / P2_ORDER_CHUNK);
+    k_order_count<<<nchunk, 256, 0, c->stream>>>(c->d_qrcnt, K, c->d_rank, c->d_binoff);
+    k_order_scan<<<1, P2_ORDER_BINS, 0, c->stream>>>(c->d_binoff, nchunk);
+    k_order_place<<<nchunk, 256, 0, c->stream>>>(c->d_qrcnt, c->d_rank, c->d_binoff, K,
+                                                  c->d_order);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_polar_on(c, c->d_G, c->d_W, c->d_s, c->d_T, K, c->stream, c->d_order,
+                           c->d_qrcnt);
 }
 
 }  // namespace p2

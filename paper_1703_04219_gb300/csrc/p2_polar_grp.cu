@@ -12,7 +12,8 @@ namespace p2 {
 
 template <int RB>
 static void launch_grp(const p2_ctx *c, const dw *G, const float *W, SmallState *st, float *T,
-                       int64_t K, cudaStream_t s, double rtol2) {
+                       int64_t K, cudaStream_t s, double rtol2, const int32_t *order,
+                       int32_t *qrcnt) {
     const int R = c->R;
     const size_t per = grp_dws(R) * sizeof(dw);
     const size_t hbytes = grp_hdws(R) * sizeof(dw);
@@ -23,7 +24,8 @@ static void launch_grp(const p2_ctx *c, const dw *G, const float *W, SmallState 
     const int threads = ((spb + 3) / 4) * 32;
     const size_t smem = hbytes + (size_t)spb * per;
     const int64_t nblk = (K + spb - 1) / spb;
-    k_polar_grp<RB><<<(unsigned)nblk, threads, smem, s>>>(G, W, st, T, K, R, (float)rtol2, spb);
+    k_polar_grp<RB><<<(unsigned)nblk, threads, smem, s>>>(G, W, st, T, K, R, (float)rtol2, spb,
+                                                           order, qrcnt);
 }
 
 // dynamic shared memory allowed: the opt-in maximum less the kernel's static
@@ -50,16 +52,17 @@ cudaError_t polar_grp_configure(int cap) {
 }
 
 cudaError_t launch_polar_grp(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
-                             float *T, int64_t K, cudaStream_t s, double rtol2) {
+                             float *T, int64_t K, cudaStream_t s, double rtol2,
+                             const int32_t *order, int32_t *qrcnt) {
     switch ((c->R + PG - 1) / PG) {
         case 1:
-        case 2: launch_grp<16>(c, G, W, st, T, K, s, rtol2); break;
-        case 3: launch_grp<24>(c, G, W, st, T, K, s, rtol2); break;
-        case 4: launch_grp<32>(c, G, W, st, T, K, s, rtol2); break;
-        case 5: launch_grp<40>(c, G, W, st, T, K, s, rtol2); break;
-        case 6: launch_grp<48>(c, G, W, st, T, K, s, rtol2); break;
-        case 7: launch_grp<56>(c, G, W, st, T, K, s, rtol2); break;
-        default: launch_grp<64>(c, G, W, st, T, K, s, rtol2); break;
+        case 2: launch_grp<16>(c, G, W, st, T, K, s, rtol2, order, qrcnt); break;
+        case 3: launch_grp<24>(c, G, W, st, T, K, s, rtol2, order, qrcnt); break;
+        case 4: launch_grp<32>(c, G, W, st, T, K, s, rtol2, order, qrcnt); break;
+        case 5: launch_grp<40>(c, G, W, st, T, K, s, rtol2, order, qrcnt); break;
+        case 6: launch_grp<48>(c, G, W, st, T, K, s, rtol2, order, qrcnt); break;
+        case 7: launch_grp<56>(c, G, W, st, T, K, s, rtol2, order, qrcnt); break;
+        default: launch_grp<64>(c, G, W, st, T, K, s, rtol2, order, qrcnt); break;
     }
     return cudaGetLastError();
 }

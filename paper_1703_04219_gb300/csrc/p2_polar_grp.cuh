@@ -57,7 +57,8 @@ template <int RB>
 __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                                                       const float *__restrict__ W, SmallState *st,
                                                       float *T, int64_t K, int R, float rtol2,
-                                                      int spb) {
+                                                      int spb, const int32_t *__restrict__ order,
+                                                      int32_t *qrcnt) {
     constexpr int RPL = RB / PG;                     // rows per lane
     extern __shared__ __align__(16) dw smg[];
     __shared__ int s_eh;
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
     const int gl = lane & (PG - 1);
     const unsigned gmask = 0xffu << (lane & ~(PG - 1));
     const int slot = (threadIdx.x >> 3);
-    const int64_t k = (int64_t)blockIdx.x * spb + slot;
+    const int64_t kslot = (int64_t)blockIdx.x * spb + slot;
     const dw one = dw_f(1.f), zero = dw_f(0.f);
     float *Hs = reinterpret_cast<float *>(smg);
     if (threadIdx.x == 0) s_eh = 0;
@@ -86,7 +87,8 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
     }
     __syncthreads();
     unsigned long long flops = 0;
-    if (slot < spb && k < K) {
+    if (slot < spb && kslot < K) {
+        const int64_t k = order ? (int64_t)order[kslot] : kslot;
         const int LD = grp_ld(R);
         dw *base = smg + grp_hdws(R) + (size_t)slot * grp_dws(R);
         auto A = [base, LD](int i, int j) -> dw & { return base[i * LD + j]; };
@@ -168,6 +170,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
         if (eg == 0 || ew == 0 || em == 0) {
             // G, W or M is zero (or below the normal range): A_k = 0, Q_k = 0
             for (int i = gl; i < R * R; i += PG) T[tb + i] = 0.f;
+            if (qrcnt && gl == 0) qrcnt[k] = 0;
         } else {
             // M'' = M' 2^sm, max diag in [0.5, 2), sm + sg even
             int sm = 127 - em;
@@ -487,7 +490,10 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                     T[tb + r * R + c] = f_mul(f_mul(v.h, o1), o2);
                 }
             }
-            if (gl == 0) flops = polar_fixed_flops(R) + qr_flops(R, steps, rot);
+            if (gl == 0) {
+                flops = polar_fixed_flops(R) + qr_flops(R, steps, rot);
+                if (qrcnt) qrcnt[k] = rot;
+            }
         }
     }
     add_flops(st, flops);

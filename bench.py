@@ -152,19 +152,30 @@ def job_throughput(nnz_per_rank, steps, ms_total_max, world):
     return world * nnz_per_rank * steps / (ms_total_max / 1e3)
 
 
+# sources that define each kernel whose DRAM traffic profiles/traffic.json records
+TRAFFIC_SOURCES = {"k_polar": ("p2_dw.cuh", "p2_eig_dw.cuh", "p2_polar.cu", "p2_polar.cuh",
+                               "p2_polar_grp.cu", "p2_polar_grp.cuh")}
+
+
+def traffic_sources_sha1(kernel):
+    """SHA-1 of the sources that define `kernel` (in a fixed order)."""
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1703_04219_gb300", "csrc")
+    for name in TRAFFIC_SOURCES[kernel]:
+        with open(os.path.join(csrc, name), "rb") as g:
+            h.update(g.read())
+    return h.hexdigest()
+
+
 def _traffic(kernel, workload):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the sources."""
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    sources are the ones the counters were taken on."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        h = hashlib.sha1()
-        csrc = os.path.join(ROOT, "paper_1703_04219_gb300", "csrc")
-        for name in sorted(os.listdir(csrc)):
-            with open(os.path.join(csrc, name), "rb") as g:
-                h.update(g.read())
         ent = d.get(workload, {}).get(kernel)
-        if ent and ent.get("sources_sha1") == h.hexdigest():
+        if ent and ent.get("sources_sha1") == traffic_sources_sha1(kernel):
             return ent["dram_bytes_per_launch"]
     except Exception:
         pass

@@ -165,6 +165,20 @@ int p2_get_mttkrp(p2_ctx *ctx, int32_t mode, double *out);
 int p2_get_procrustes(p2_ctx *ctx, int64_t k0, int64_t k1, float *T);
 
 /*
+ * The subjects' factor matrices U_k = Q_k H (Algorithm 2's ENSURE output,
+ * Section 3.2: X_k ~ U_k S_k V^T), for subjects k0 .. k1-1, into a host FP32
+ * buffer of (subj_ptr[k1] - subj_ptr[k0]) x R holding their rows in the
+ * stacked row order.  Q_k is the Procrustes factor of the current Q-step,
+ * i.e. the one computed for the factors that p2_get_factors returns (the
+ * Q-step that opens the next iteration).  Rows of V are gathered per
+ * non-zero (Q_k = X_k V T_k^T), so the call costs one pass over the
+ * subjects' non-zeros; it allocates a device buffer of the output's size
+ * and synchronises.  0 <= k0 <= k1 <= K; U may be NULL only when the range
+ * holds no rows.
+ */
+int p2_get_U(p2_ctx *ctx, int64_t k0, int64_t k1, float *U);
+
+/*
  * Projection of new subjects onto the current model (serving).  For each new
  * subject X (I x J), with the model's H and V fixed, alternate Algorithm 2's
  * Q-step (Procrustes, Section 3.2) and Algorithm 1's W update restricted to

@@ -25,7 +25,7 @@ _NAMES = {0: "P2_OK", 1: "P2_EINVAL", 2: "P2_ENOMEM", 3: "P2_ECUDA", 4: "P2_ENUM
 # every symbol include/p2.h declares
 EXPORTED = ("p2_default_options", "p2_create", "p2_destroy", "p2_load_slices", "p2_init",
             "p2_iterate", "p2_fit", "p2_get_factors", "p2_set_factors", "p2_get_mttkrp",
-            "p2_get_procrustes", "p2_stats", "p2_device_bytes", "p2_mode1_stats_noalloc",
+            "p2_get_procrustes", "p2_get_U", "p2_stats", "p2_device_bytes", "p2_mode1_stats_noalloc",
             "p2_projector_create", "p2_projector_destroy", "p2_project", "p2_projector_sync",
             "p2_last_error")
 
@@ -70,6 +70,7 @@ def _load():
         "p2_set_factors": ([vp, vp, vp, vp], ctypes.c_int),
         "p2_get_mttkrp": ([vp, i32, vp], ctypes.c_int),
         "p2_get_procrustes": ([vp, i64, i64, vp], ctypes.c_int),
+        "p2_get_U": ([vp, i64, i64, vp], ctypes.c_int),
         "p2_stats": ([vp, ctypes.POINTER(p2_stats_t)], ctypes.c_int),
         "p2_device_bytes": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
         "p2_mode1_stats_noalloc": ([i64, i32, vp, vp, vp, vp, vp, vp], ctypes.c_int),
@@ -179,6 +180,12 @@ def p2_get_mttkrp(ctx, mode, R, J, K):
 def p2_get_procrustes(ctx, k0, k1, R):
     out = np.empty((k1 - k0, R, R), np.float32)
     _check(lib.p2_get_procrustes(ctx, int(k0), int(k1), _ptr(out)), "p2_get_procrustes")
+    return out
+
+
+def p2_get_U(ctx, k0, k1, n_rows, R):
+    out = np.empty((int(n_rows), R), np.float32)
+    _check(lib.p2_get_U(ctx, int(k0), int(k1), _ptr(out)), "p2_get_U")
     return out
 
 
@@ -300,6 +307,8 @@ class Parafac2:
         p2_load_slices(self.ctx, slices.K, slices.J, slices.subj_ptr, slices.row_ptr, slices.col,
                        slices.val, location)
         self.K, self.J = int(slices.K), int(slices.J)
+        sp = slices.subj_ptr
+        self._subj_ptr = np.asarray(sp.cpu() if hasattr(sp, "cpu") else sp, np.int64)
 
     def init(self, H0, V0, W0):
         p2_init(self.ctx, H0, V0, W0)
@@ -321,6 +330,12 @@ class Parafac2:
 
     def procrustes(self, k0=0, k1=None):
         return p2_get_procrustes(self.ctx, k0, self.K if k1 is None else k1, self.R)
+
+    def U(self, k0=0, k1=None):
+        """Rows of U_k = Q_k H for subjects k0 .. k1-1, stacked (Section 3.2)."""
+        k1 = self.K if k1 is None else k1
+        n = int(self._subj_ptr[k1] - self._subj_ptr[k0])
+        return p2_get_U(self.ctx, k0, k1, n, self.R)
 
     def stats(self) -> dict:
         return p2_stats(self.ctx)

@@ -519,6 +519,32 @@ int p2_get_procrustes(p2_ctx *c, int64_t k0, int64_t k1, float *T) {
     return P2_OK;
 }
 
+int p2_get_U(p2_ctx *c, int64_t k0, int64_t k1, float *U) {
+    P2_TRY(check_ready(c, true));
+    if (k0 < 0 || k1 < k0 || k1 > c->X.K) return fail(P2_EINVAL, "p2_get_U: bad range");
+    P2_CUDA_TRY(cudaSetDevice(c->opt.device));
+    P2_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    int64_t rr[2] = {0, 0};
+    P2_CUDA_TRY(cudaMemcpy(&rr[0], c->X.subj_row + k0, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    P2_CUDA_TRY(cudaMemcpy(&rr[1], c->X.subj_row + k1, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    const int64_t n = rr[1] - rr[0];
+    if (n == 0) return P2_OK;
+    if (!U) return fail(P2_EINVAL, "p2_get_U: NULL out");
+    float *d = nullptr;
+    const size_t bytes = sizeof(float) * (size_t)n * c->R;
+    P2_CUDA_TRY(cudaMalloc(&d, bytes));
+    cudaError_t e = cudaMemsetAsync(d, 0, bytes, c->stream);     // rows of empty subjects stay 0
+    if (e == cudaSuccess) e = launch_get_u(c, k0, k1, rr[0], d);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(U, d, bytes, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        set_error("p2_get_U: %s", cudaGetErrorString(e));
+        return P2_ECUDA;
+    }
+    return P2_OK;
+}
+
 int p2_stats(p2_ctx *c, p2_stats_t *out) {
     if (!c || !out) return fail(P2_EINVAL, "NULL argument");
     memset(out, 0, sizeof(*out));

@@ -204,6 +204,8 @@ cudaError_t launch_polar_on(const p2_ctx *c, const dw *G, const float *W, SmallS
 #define P2_ORDER_BINS 256
 // kernels launched by launch_polar (the ordering and the Procrustes kernel)
 constexpr int POLAR_LAUNCHES = 4;
+// U_k = Q_k H rows of subjects k0 .. k1-1 into a device FP32 buffer (p2_kernels.cu)
+cudaError_t launch_get_u(p2_ctx *c, int64_t k0, int64_t k1, int64_t r0, float *U);
 // Gram of Z_k = X_k V for a batch of new subjects (p2_kernels.cu)
 cudaError_t launch_gram(const p2_ctx *c, const XView &X, const SmallState *st, dw *G,
                         cudaStream_t s);

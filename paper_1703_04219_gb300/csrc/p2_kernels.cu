@@ -24,6 +24,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "p2_internal.cuh"
 #include "p2_eig.cuh"
 
@@ -386,11 +388,15 @@ static __host__ __device__ size_t beta_warp_bytes(int R) {
     return (b + 15) & ~(size_t)15;
 }
 
-template <int CB, class S>
+// The same kernel serves p2_get_U (U_k = Q_k H = Z_k T_k^T H): W == NULL
+// stands for S_k = I, the output type O may differ from the storage type S,
+// and row r of the view is written at Pout[(r - out_row0) R].
+template <int CB, class S, class O = S>
 __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 4) k_beta_p(XView X, const S *__restrict__ V,
                                                 const float *__restrict__ H,
                                                 const float *__restrict__ T,
-                                                const float *__restrict__ W, S *Pout, int R) {
+                                                const float *__restrict__ W, O *Pout, int R,
+                                                int64_t out_row0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RS = row_stride(R);
     float *Hs = reinterpret_cast<float *>(smem_raw);
@@ -410,7 +416,7 @@ __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 4) k_beta_p(XView X, const
         int64_t base = X.subj_nnz[k];
         const float *Tg = T + (size_t)k * R * R;
         for (int e = lane; e < R * R; e += 32) Tk[e] = Tg[e];
-        for (int s = lane; s < R; s += 32) wk[s] = W[(size_t)k * R + s];
+        for (int s = lane; s < R; s += 32) wk[s] = W ? W[(size_t)k * R + s] : 1.f;
         __syncwarp();
         RowCol us(lane, R);
         for (int e = lane; e < R * R; e += 32, us.next(R)) {
@@ -430,12 +436,12 @@ __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 4) k_beta_p(XView X, const
             const int tot = __shfl_sync(FULLMASK, off + len, 31);
             gather_rows<CB, false, S>(X, nr, base, len, off, V, nullptr, zo, nullptr, R, RS, lane);
             __syncwarp();
-            S *Pr = Pout + (size_t)cr * R;
+            O *Pr = Pout + (size_t)(cr - out_row0) * R;
             // lane i computes row i of Z_k F_k; all lanes read the same F_k row
             // (a shared-memory broadcast) four columns at a time
             if (lane < nr) {
                 const float *zr = zo + lane * RS;
-                S *Prow = Pr + (size_t)lane * R;
+                O *Prow = Pr + (size_t)lane * R;
                 for (int cb = 0; cb < R; cb += CB) {
                     float acc[CB];
 #pragma unroll
@@ -456,7 +462,7 @@ __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 4) k_beta_p(XView X, const
                     }
 #pragma unroll
                     for (int c = 0; c < CB; ++c)
-                        if (cb + c < R) Stor<S>::st(Prow + cb + c, acc[c]);
+                        if (cb + c < R) Stor<O>::st(Prow + cb + c, acc[c]);
                 }
             }
             __syncwarp();
@@ -1067,6 +1073,9 @@ static int configure_sparse(int cap) {
     if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<8, S>, cap, "k_beta_p");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<16, S>, cap, "k_beta_p");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<32, S>, cap, "k_beta_p");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<8, S, float>, cap, "k_beta_p");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<16, S, float>, cap, "k_beta_p");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<32, S, float>, cap, "k_beta_p");
     return rc;
 }
 
@@ -1207,17 +1216,17 @@ static void launch_beta_p_t(p2_ctx *c, const Launch &L) {
     switch (comp_block(c->R)) {
         case 8: {
             dim3 grid(c->geo.nsm * resident_blocks(c, k_beta_p<8, S>, nt, L.beta_smem));
-            k_beta_p<8, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R);
+            k_beta_p<8, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R, 0);
             break;
         }
         case 16: {
             dim3 grid(c->geo.nsm * resident_blocks(c, k_beta_p<16, S>, nt, L.beta_smem));
-            k_beta_p<16, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R);
+            k_beta_p<16, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R, 0);
             break;
         }
         default: {
             dim3 grid(c->geo.nsm * resident_blocks(c, k_beta_p<32, S>, nt, L.beta_smem));
-            k_beta_p<32, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R);
+            k_beta_p<32, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R, 0);
             break;
         }
     }
@@ -1228,6 +1237,48 @@ static void launch_beta_p(p2_ctx *c, const Launch &L) {
         launch_beta_p_t<bf16_t>(c, L);
     else
         launch_beta_p_t<float>(c, L);
+}
+
+// U rows of subjects k0 .. k1-1 (rows r0 .. of the stacked order) into the
+// FP32 device buffer U: U_k = Z_k T_k^T H, the beta kernel with S_k = I.
+template <class S>
+static void launch_get_u_t(p2_ctx *c, const Launch &L, int64_t k0, int64_t k1, int64_t r0,
+                           float *U) {
+    const int nt = L.beta_warps * 32;
+    XView X = xview(c);
+    X.subj_row += k0;
+    X.subj_nnz += k0;
+    X.K = k1 - k0;
+    const S *V = Bufs<S>::V(c);
+    const float *T = c->d_T + (size_t)k0 * c->R * c->R;
+    const int64_t want = (k1 - k0 + L.beta_warps - 1) / L.beta_warps;
+    switch (comp_block(c->R)) {
+        case 8: {
+            const int g = (int)std::min<int64_t>(want, c->geo.nsm * resident_blocks(c, k_beta_p<8, S, float>, nt, L.beta_smem));
+            k_beta_p<8, S, float><<<g, nt, L.beta_smem, c->stream>>>(X, V, c->d_H, T, nullptr, U, c->R, r0);
+            break;
+        }
+        case 16: {
+            const int g = (int)std::min<int64_t>(want, c->geo.nsm * resident_blocks(c, k_beta_p<16, S, float>, nt, L.beta_smem));
+            k_beta_p<16, S, float><<<g, nt, L.beta_smem, c->stream>>>(X, V, c->d_H, T, nullptr, U, c->R, r0);
+            break;
+        }
+        default: {
+            const int g = (int)std::min<int64_t>(want, c->geo.nsm * resident_blocks(c, k_beta_p<32, S, float>, nt, L.beta_smem));
+            k_beta_p<32, S, float><<<g, nt, L.beta_smem, c->stream>>>(X, V, c->d_H, T, nullptr, U, c->R, r0);
+            break;
+        }
+    }
+}
+
+cudaError_t launch_get_u(p2_ctx *c, int64_t k0, int64_t k1, int64_t r0, float *U) {
+    if (k1 <= k0) return cudaSuccess;
+    const Launch L = plan(c);
+    if (c->bf16)
+        launch_get_u_t<bf16_t>(c, L, k0, k1, r0, U);
+    else
+        launch_get_u_t<float>(c, L, k0, k1, r0, U);
+    return cudaGetLastError();
 }
 
 template <class S>

@@ -67,11 +67,34 @@ def project_case(R, n_req):
     return {"S_max": float(max(errs))}
 
 
+def getu_case(R, k0, k1):
+    """U_k = Q_k H for subjects k0 .. k1-1 against the oracle's Procrustes
+    factor for the factors the library returns."""
+    X = synth.generate("tiny", K=24)
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=11)
+    with p2.Parafac2(R, use_graph=False) as m:
+        m.load(X)
+        m.init(H0, V0, W0)
+        m.iterate(1)
+        H, V, W = m.factors()
+        U = m.U(k0, k1)
+    H, V, W = (a.astype(np.float64) for a in (H, V, W))
+    refs = []
+    for k in range(k0, k1):
+        Xc, cols = P.subject_block(X, k)
+        refs.append(P.procrustes_q(Xc, cols, H, V, W[k]) @ H)
+    ref = np.concatenate(refs, axis=0) if refs else np.zeros((0, R))
+    assert U.shape == ref.shape, (U.shape, ref.shape)
+    return {"U": rel_fro(U, ref), "rows": float(U.shape[0])}
+
+
 if __name__ == "__main__":
     kind = sys.argv[1]
     if kind == "iterate":
         out = iterate_case(sys.argv[2], int(sys.argv[3]), int(sys.argv[4]),
                            sys.argv[5] if len(sys.argv) > 5 else "fp32")
+    elif kind == "getu":
+        out = getu_case(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]))
     else:
         out = project_case(int(sys.argv[2]), int(sys.argv[3]))
     print(json.dumps({k: float(v) for k, v in out.items()}), flush=True)

@@ -2,7 +2,7 @@
 AddressSanitizer: one ALS iteration at R = 5 and R = 10 (lane-per-subject
 Procrustes),
 at R = 13 (grouped Procrustes kernel) and at R = 5 with bfloat16 storage,
-and a projection of new subjects.
+a projection of new subjects, and U_k = Q_k H for a range of subjects.
 Every device buffer and every block's shared memory is a heap block of its
 exact size, so an out-of-bounds access by any kernel aborts the run; the
 results must also match the FP64 oracle.  No GPU involved."""
@@ -23,6 +23,7 @@ CASES = {
     "iterate_r13": ["iterate", "tiny", "16", "13"],
     "iterate_r5_bf16": ["iterate", "tiny", "24", "5", "bf16"],
     "project_r12": ["project", "12", "3"],
+    "getu_r5": ["getu", "5", "3", "17"],
 }
 
 
@@ -84,3 +85,10 @@ def test_emulated_bf16_storage_is_in_bounds_and_within_3e3(emulated_runs):
 def test_emulated_projection_is_in_bounds_and_matches_oracle(emulated_runs):
     err = _result(emulated_runs, "project_r12")
     assert err["S_max"] < 1e-4
+
+
+def test_emulated_get_U_is_in_bounds_and_matches_oracle(emulated_runs):
+    err = _result(emulated_runs, "getu_r5")
+    assert err["rows"] > 0
+    assert err["U"] < 1e-5, err
+

@@ -140,3 +140,40 @@ def test_stats_and_phase_timing(p2):
     assert set(s1["phase_ms"]) == set(p2.PHASES)
     assert all(v > 0 for v in s1["phase_ms"].values()), s1["phase_ms"]
     assert s1["polar_fp64_flops"] > s0["polar_fp64_flops"] > 0
+
+
+@pytest.mark.parametrize("name,K,R", [("tiny", 200, 5), ("c63m", 2000, 10), ("c250m", 300, 40)])
+def test_get_U_matches_oracle(p2, name, K, R):
+    """U_k = Q_k H (Algorithm 2's ENSURE output) for a range of subjects, with
+    Q_k the oracle's Procrustes factor (Section 3.2) for the factors the
+    library returns.  Q_k is formed from the FP32 T_k, whose rounding is
+    amplified by cond(A_k): each subject is held to max(1e-5, 8 eps32 cond)."""
+    X = synth.generate(name, K=K)
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=5)
+    with p2.Parafac2(R) as m:
+        m.load(X)
+        m.init(H0, V0, W0)
+        m.iterate(2)
+        H, V, W = m.factors()
+        k0, k1 = K // 3, min(K, K // 3 + 40)
+        U = m.U(k0, k1)
+        assert m.U().shape == (X.n_rows, R)
+        assert m.U(k1, k1).shape == (0, R)
+    H, V, W = (a.astype(np.float64) for a in (H, V, W))
+    eps32 = 2.0 ** -24
+    row = 0
+    for k in range(k0, k1):
+        Xc, cols = P.subject_block(X, k)
+        n = Xc.shape[0]
+        got = U[row:row + n]
+        row += n
+        ref = P.procrustes_q(Xc, cols, H, V, W[k]) @ H
+        if n == 0 or not np.any(ref):
+            assert np.all(got == 0) if n else True
+            continue
+        A = (Xc @ V[cols]) * W[k] @ H.T
+        sv = np.linalg.svd(A, compute_uv=False)
+        sv = sv[sv > 1e-5 * sv[0]]
+        bound = max(1e-5, 8 * eps32 * sv[0] / sv[-1])
+        assert rel_fro(got, ref) < bound, (k, rel_fro(got, ref), bound)
+    assert row == U.shape[0]

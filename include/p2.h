@@ -64,6 +64,7 @@ typedef struct {
                              X_k V S_k H^T are dropped; <= 0 selects the default 1e-5 */
     void *stream;         /* cudaStream_t to enqueue on; NULL: the context creates its own */
     int32_t timing;       /* non-zero: CUDA events around each phase of an iteration (p2_stats) */
+    uint64_t seed;        /* seed of the initial factors p2_init draws when given NULLs */
 } p2_options;
 
 /* Counters and timings of a context (p2_stats). */
@@ -80,7 +81,7 @@ typedef struct {
 } p2_stats_t;
 
 /* Fill *opt with defaults for rank R (precision FP32, device 0, graph on,
- * rank_rtol 1e-5, own stream, timing off). */
+ * rank_rtol 1e-5, own stream, timing off, seed 20170314). */
 void p2_default_options(p2_options *opt, int32_t R);
 
 /* Create a context on opt->device.  *out receives the handle (NULL on error).
@@ -115,7 +116,14 @@ int p2_load_slices(p2_ctx *ctx, int64_t K, int32_t J, const int64_t *subj_ptr,
 /*
  * Set the initial factors (Algorithm 2, "Initialize H, V, {S_k}") and run the
  * first Q-step so that p2_iterate can start.  H0: R x R, V0: J x R (caller's
- * column order), W0: K x R; host memory, FP32, none may be NULL.
+ * column order), W0: K x R; host memory, FP32.  All three NULL: the library
+ * draws them uniform in [0, 1) from opt.seed (the paper leaves the
+ * initialisation open): element i (row-major) of array a (H: a = 1, V: 2,
+ * W: 3) is (x >> 40) 2^-24 for the first SplitMix64 output x (Steele, Lea &
+ * Flood, OOPSLA 2014; mixer constants 0xBF58476D1CE4E5B9, 0x94D049BB133111EB)
+ * of the state mix(seed + g (t + 1)) ^ mix(i g + t), with t = 5 + 16 a,
+ * g = 0x9E3779B97F4A7C15 and mix the SplitMix64 finaliser.  Some but not all
+ * NULL: P2_EINVAL.
  */
 int p2_init(p2_ctx *ctx, const float *H0, const float *V0, const float *W0);
 
@@ -128,6 +136,16 @@ int p2_init(p2_ctx *ctx, const float *H0, const float *V0, const float *W0);
  * (p2_fit reports the same later otherwise).
  */
 int p2_iterate(p2_ctx *ctx, int32_t n_iter, double *fit_out);
+
+/*
+ * Outer loop of Algorithm 2 with a stopping rule (the paper leaves the
+ * convergence criterion open): iterate until the fit changes by at most tol
+ * between two iterations, or max_iter iterations.  n_done and fit_out
+ * (nullable, host) receive the iterations run and the last fit.  Reads the
+ * fit back after every iteration (one synchronisation each).
+ */
+int p2_iterate_until(p2_ctx *ctx, int32_t max_iter, double tol, int32_t *n_done,
+                     double *fit_out);
 
 /*
  * Loss and fit of the last completed iteration (the objective of Section 3.2):

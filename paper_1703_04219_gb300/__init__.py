@@ -25,7 +25,7 @@ _NAMES = {0: "P2_OK", 1: "P2_EINVAL", 2: "P2_ENOMEM", 3: "P2_ECUDA", 4: "P2_ENUM
 # every symbol include/p2.h declares
 EXPORTED = ("p2_default_options", "p2_create", "p2_destroy", "p2_load_slices", "p2_init",
             "p2_iterate", "p2_fit", "p2_get_factors", "p2_set_factors", "p2_get_mttkrp",
-            "p2_get_procrustes", "p2_get_U", "p2_stats", "p2_device_bytes", "p2_mode1_stats_noalloc",
+            "p2_get_procrustes", "p2_get_U", "p2_iterate_until", "p2_stats", "p2_device_bytes", "p2_mode1_stats_noalloc",
             "p2_projector_create", "p2_projector_destroy", "p2_project", "p2_projector_sync",
             "p2_last_error")
 
@@ -33,7 +33,8 @@ EXPORTED = ("p2_default_options", "p2_create", "p2_destroy", "p2_load_slices", "
 class p2_options(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("rank_rtol", ctypes.c_double),
-                ("stream", ctypes.c_void_p), ("timing", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("timing", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 class p2_stats_t(ctypes.Structure):
@@ -71,6 +72,8 @@ def _load():
         "p2_get_mttkrp": ([vp, i32, vp], ctypes.c_int),
         "p2_get_procrustes": ([vp, i64, i64, vp], ctypes.c_int),
         "p2_get_U": ([vp, i64, i64, vp], ctypes.c_int),
+        "p2_iterate_until": ([vp, i32, ctypes.c_double, ctypes.POINTER(i32),
+                              ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "p2_stats": ([vp, ctypes.POINTER(p2_stats_t)], ctypes.c_int),
         "p2_device_bytes": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
         "p2_mode1_stats_noalloc": ([i64, i32, vp, vp, vp, vp, vp, vp], ctypes.c_int),
@@ -140,7 +143,11 @@ def p2_load_slices(ctx, K, J, subj_ptr, row_ptr, col, val, location=None):
                               _ptr(val), int(location)), "p2_load_slices")
 
 
-def p2_init(ctx, H0, V0, W0):
+def p2_init(ctx, H0=None, V0=None, W0=None):
+    """H0, V0, W0 all None: the library draws them from the context's seed."""
+    if H0 is None and V0 is None and W0 is None:
+        _check(lib.p2_init(ctx, None, None, None), "p2_init")
+        return
     H0, V0, W0 = (np.ascontiguousarray(a, np.float32) for a in (H0, V0, W0))
     _check(lib.p2_init(ctx, _ptr(H0), _ptr(V0), _ptr(W0)), "p2_init")
 
@@ -154,6 +161,14 @@ def p2_iterate(ctx, n_iter: int, want_fit: bool = True):
     f = ctypes.c_double()
     _check(lib.p2_iterate(ctx, int(n_iter), ctypes.byref(f) if want_fit else None), "p2_iterate")
     return f.value if want_fit else None
+
+
+def p2_iterate_until(ctx, max_iter: int, tol: float):
+    n = ctypes.c_int32()
+    f = ctypes.c_double()
+    _check(lib.p2_iterate_until(ctx, int(max_iter), float(tol), ctypes.byref(n), ctypes.byref(f)),
+           "p2_iterate_until")
+    return n.value, f.value
 
 
 def p2_fit(ctx):
@@ -271,7 +286,7 @@ class Parafac2:
     """Owning wrapper of one context: load, init, iterate, read back."""
 
     def __init__(self, R: int, device: int = 0, use_graph: bool = True, rank_rtol: float = 1e-5,
-                 stream=None, timing: bool = False, precision: str = "fp32"):
+                 stream=None, timing: bool = False, precision: str = "fp32", seed=None):
         if precision not in ("fp32", "bf16"):
             raise ValueError("precision must be 'fp32' or 'bf16'")
         opt = p2_default_options(R)
@@ -281,6 +296,8 @@ class Parafac2:
         opt.rank_rtol = rank_rtol
         opt.stream = stream
         opt.timing = 1 if timing else 0
+        if seed is not None:
+            opt.seed = int(seed)
         self.R = R
         self.precision = precision
         self.ctx = p2_create(opt)
@@ -310,7 +327,7 @@ class Parafac2:
         sp = slices.subj_ptr
         self._subj_ptr = np.asarray(sp.cpu() if hasattr(sp, "cpu") else sp, np.int64)
 
-    def init(self, H0, V0, W0):
+    def init(self, H0=None, V0=None, W0=None):
         p2_init(self.ctx, H0, V0, W0)
 
     def set_factors(self, H, V, W):
@@ -318,6 +335,10 @@ class Parafac2:
 
     def iterate(self, n: int, want_fit: bool = True):
         return p2_iterate(self.ctx, n, want_fit)
+
+    def iterate_until(self, max_iter: int, tol: float):
+        """(iterations run, fit) of the loop that stops when the fit changes by <= tol."""
+        return p2_iterate_until(self.ctx, max_iter, tol)
 
     def fit(self):
         return p2_fit(self.ctx)

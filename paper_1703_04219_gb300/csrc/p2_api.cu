@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <vector>
+#include <math.h>
 
 #include "p2_internal.cuh"
 
@@ -233,6 +234,7 @@ void p2_default_options(p2_options *opt, int32_t R) {
     opt->rank_rtol = 1e-5;
     opt->stream = nullptr;
     opt->timing = 0;
+    opt->seed = 20170314ULL;
 }
 
 int p2_create(p2_ctx **out, const p2_options *opt) {
@@ -386,10 +388,35 @@ int p2_load_slices(p2_ctx *c, int64_t K, int32_t J, const int64_t *subj_ptr,
     return P2_OK;
 }
 
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the finaliser and one step.
+static inline uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+// n initial values of array a: uniform in [0, 1), multiples of 2^-24 (the
+// counter-based layout documented with p2_init)
+static void init_uniform(uint64_t seed, uint64_t a, size_t n, float *out) {
+    const uint64_t g = 0x9E3779B97F4A7C15ULL, t = 5 + 16 * a;
+    for (size_t i = 0; i < n; ++i) {
+        const uint64_t s = sm64_mix(seed + g * (t + 1)) ^ sm64_mix((uint64_t)i * g + t);
+        const uint64_t x = sm64_mix(s + g);
+        out[i] = (float)((double)(x >> 40) * 0x1.0p-24);
+    }
+}
+
 int p2_init(p2_ctx *c, const float *H0, const float *V0, const float *W0) {
     P2_TRY(check_ready(c, false));
-    if (!H0 || !V0 || !W0) return fail(P2_EINVAL, "p2_init: NULL factor");
     P2_CUDA_TRY(cudaSetDevice(c->opt.device));
+    if (!H0 && !V0 && !W0) {
+        const size_t R = (size_t)c->R;
+        std::vector<float> H(R * R), V((size_t)c->X.J * R), W((size_t)c->X.K * R);
+        init_uniform(c->opt.seed, 1, H.size(), H.data());
+        init_uniform(c->opt.seed, 2, V.size(), V.data());
+        init_uniform(c->opt.seed, 3, W.size(), W.data());
+        return set_factors_impl(c, H.data(), V.data(), W.data());
+    }
+    if (!H0 || !V0 || !W0) return fail(P2_EINVAL, "p2_init: some but not all factors NULL");
     return set_factors_impl(c, H0, V0, W0);
 }
 
@@ -541,6 +568,23 @@ int p2_get_U(p2_ctx *c, int64_t k0, int64_t k1, float *U) {
     if (e != cudaSuccess) {
         set_error("p2_get_U: %s", cudaGetErrorString(e));
         return P2_ECUDA;
+    }
+    return P2_OK;
+}
+
+int p2_iterate_until(p2_ctx *c, int32_t max_iter, double tol, int32_t *n_done,
+                     double *fit_out) {
+    if (n_done) *n_done = 0;
+    if (max_iter < 0 || !(tol >= 0.0)) return fail(P2_EINVAL, "p2_iterate_until: bad max_iter or tol");
+    double prev = 0.0, fit = 0.0;
+    int32_t it = 0;
+    while (it < max_iter) {
+        P2_TRY(p2_iterate(c, 1, &fit));
+        ++it;
+        if (n_done) *n_done = it;
+        if (fit_out) *fit_out = fit;
+        if (it > 1 && fabs(fit - prev) <= tol) break;
+        prev = fit;
     }
     return P2_OK;
 }

@@ -88,11 +88,35 @@ def getu_case(R, k0, k1):
     return {"U": rel_fro(U, ref), "rows": float(U.shape[0])}
 
 
+def seed_case(R, seed):
+    """p2_init with no factors draws H, V, W from the context's seed exactly as
+    the input generator's init_factors does; p2_iterate_until runs max_iter
+    iterations with tol = 0 (reproducing a fixed-count run) and stops after
+    the second when every change is within tol."""
+    X = synth.generate("tiny", K=24)
+    with p2.Parafac2(R, use_graph=False, seed=seed) as m:
+        m.load(X)
+        m.init()
+        H, V, W = m.factors()
+        n, fit = m.iterate_until(3, 0.0)
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=seed)
+    same = float(np.array_equal(H, H0) and np.array_equal(V, V0) and np.array_equal(W, W0))
+    with p2.Parafac2(R, use_graph=False) as m:
+        m.load(X)
+        m.init(H0, V0, W0)
+        fit_fixed = m.iterate(3)
+        n_loose, _ = m.iterate_until(10, 10.0)
+    return {"init_equal": same, "n": float(n), "fit": fit, "fit_fixed": fit_fixed,
+            "n_loose": float(n_loose)}
+
+
 if __name__ == "__main__":
     kind = sys.argv[1]
     if kind == "iterate":
         out = iterate_case(sys.argv[2], int(sys.argv[3]), int(sys.argv[4]),
                            sys.argv[5] if len(sys.argv) > 5 else "fp32")
+    elif kind == "seed":
+        out = seed_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "getu":
         out = getu_case(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]))
     else:

@@ -24,6 +24,7 @@ CASES = {
     "iterate_r5_bf16": ["iterate", "tiny", "24", "5", "bf16"],
     "project_r12": ["project", "12", "3"],
     "getu_r5": ["getu", "5", "3", "17"],
+    "seed_r4": ["seed", "4", "987654321"],
 }
 
 
@@ -91,4 +92,11 @@ def test_emulated_get_U_is_in_bounds_and_matches_oracle(emulated_runs):
     err = _result(emulated_runs, "getu_r5")
     assert err["rows"] > 0
     assert err["U"] < 1e-5, err
+
+
+def test_emulated_seeded_init_and_stopping_rule(emulated_runs):
+    out = _result(emulated_runs, "seed_r4")
+    assert out["init_equal"] == 1.0
+    assert out["n"] == 3 and out["fit"] == out["fit_fixed"]
+    assert out["n_loose"] == 2
 

@@ -177,3 +177,23 @@ def test_get_U_matches_oracle(p2, name, K, R):
         bound = max(1e-5, 8 * eps32 * sv[0] / sv[-1])
         assert rel_fro(got, ref) < bound, (k, rel_fro(got, ref), bound)
     assert row == U.shape[0]
+
+
+def test_seeded_init_and_stopping_rule(p2):
+    """p2_init without factors draws the same H, V, W as the input generator
+    for the context's seed; p2_iterate_until stops on the fit change and its
+    fit equals that of a fixed-count run of the same length (bitwise: the
+    iteration is deterministic)."""
+    X = synth.generate("c63m", K=2000)
+    with p2.Parafac2(10, seed=123) as m:
+        m.load(X)
+        m.init()
+        H, V, W = m.factors()
+        n, fit = m.iterate_until(60, 1e-6)
+    H0, V0, W0 = synth.init_factors(10, X.J, X.K, seed=123)
+    assert np.array_equal(H, H0) and np.array_equal(V, V0) and np.array_equal(W, W0)
+    assert 2 <= n <= 60
+    with p2.Parafac2(10) as m:
+        m.load(X)
+        m.init(H0, V0, W0)
+        assert m.iterate(n) == fit

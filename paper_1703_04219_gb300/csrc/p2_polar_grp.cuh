@@ -21,7 +21,7 @@ namespace p2 {
 // LD = R | 1 to spread banks), d, e, t (R each) and w' (R floats in R
 // double-word slots).  RB = R rounded up to a multiple of PG (register
 // arrays); rows i are owned by lane i % PG.
-constexpr int PG = 8;
+constexpr int PG_DEFAULT = 8;
 
 inline __host__ __device__ int grp_ld(int R) { return R | 1; }
 // double-words per subject
@@ -32,28 +32,34 @@ inline __host__ __device__ size_t grp_hdws(int R) { return ((size_t)R * R + 1) /
 static __device__ __forceinline__ dw shfl_xor_dw(unsigned mask, dw v, int o) {
     return dw{__shfl_xor_sync(mask, v.h, o), __shfl_xor_sync(mask, v.l, o)};
 }
-// sum over the eight lanes of a group (same result on every lane: the
+// sum over the PG lanes of a group (same result on every lane: the
 // butterfly adds the same two operands in the same order on both partners)
+template <int PG>
 static __device__ __forceinline__ dw group_sum(unsigned mask, dw v) {
-    v = dw_add(v, shfl_xor_dw(mask, v, 4));
-    v = dw_add(v, shfl_xor_dw(mask, v, 2));
-    v = dw_add(v, shfl_xor_dw(mask, v, 1));
+#pragma unroll
+    for (int o = PG / 2; o > 0; o >>= 1) v = dw_add(v, shfl_xor_dw(mask, v, o));
     return v;
 }
+template <int PG>
 static __device__ __forceinline__ int group_max(unsigned mask, int v) {
-    v = max(v, __shfl_xor_sync(mask, v, 4));
-    v = max(v, __shfl_xor_sync(mask, v, 2));
-    v = max(v, __shfl_xor_sync(mask, v, 1));
+#pragma unroll
+    for (int o = PG / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(mask, v, o));
     return v;
 }
+template <int PG>
 static __device__ __forceinline__ float group_maxf(unsigned mask, float v) {
-    v = fmaxf(v, __shfl_xor_sync(mask, v, 4));
-    v = fmaxf(v, __shfl_xor_sync(mask, v, 2));
-    v = fmaxf(v, __shfl_xor_sync(mask, v, 1));
+#pragma unroll
+    for (int o = PG / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o));
+    return v;
+}
+template <int PG>
+static __device__ __forceinline__ unsigned long long group_or(unsigned mask, unsigned long long v) {
+#pragma unroll
+    for (int o = PG / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(mask, v, o);
     return v;
 }
 
-template <int RB>
+template <int RB, int PG>
 __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                                                       const float *__restrict__ W, SmallState *st,
                                                       float *T, int64_t K, int R, float rtol2,
@@ -64,8 +70,8 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
     __shared__ int s_eh;
     const int lane = threadIdx.x & 31;
     const int gl = lane & (PG - 1);
-    const unsigned gmask = 0xffu << (lane & ~(PG - 1));
-    const int slot = (threadIdx.x >> 3);
+    const unsigned gmask = (unsigned)((1ull << PG) - 1) << (lane & ~(PG - 1));
+    const int slot = threadIdx.x / PG;
     const int64_t kslot = (int64_t)blockIdx.x * spb + slot;
     const dw one = dw_f(1.f), zero = dw_f(0.f);
     float *Hs = reinterpret_cast<float *>(smg);
@@ -107,8 +113,8 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
             ew = max(ew, f_expo(w));
             eg = max(eg, f_expo(Gk[i * (i + 1) / 2 + i].h));
         }
-        ew = group_max(gmask, ew);
-        eg = group_max(gmask, eg);
+        ew = group_max<PG>(gmask, ew);
+        eg = group_max<PG>(gmask, eg);
         const int sg = 127 - eg;
         const float gsc = f_pow2(sg);
         {
@@ -166,7 +172,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
             }
             __syncwarp(gmask);
         }
-        em = group_max(gmask, em);
+        em = group_max<PG>(gmask, em);
         if (eg == 0 || ew == 0 || em == 0) {
             // G, W or M is zero (or below the normal range): A_k = 0, Q_k = 0
             for (int i = gl; i < R * R; i += PG) T[tb + i] = 0.f;
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                 dwacc sa = acc_zero();
                 for (int i = gl; i < R; i += PG)
                     if (i >= kk + 2) acc_sqr(sa, A(i, kk));
-                const dw sig = group_sum(gmask, acc_val(sa));
+                const dw sig = group_sum<PG>(gmask, acc_val(sa));
                 const dw x0 = A(kk + 1, kk);
                 if (!(sig.h >= DW_TINY2)) {          // reflector as in p2_eig_dw.cuh
                     __syncwarp(gmask);
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                     else
                         acc_fma(pa, si, A(i, kk));
                 }
-                const dw pv = group_sum(gmask, acc_val(pa));
+                const dw pv = group_sum<PG>(gmask, acc_val(pa));
                 const dw nK = dw_neg(dw_mul(dw_scale(bh, 0.5f), pv));
                 for (int i = gl; i < R; i += PG) {
                     if (i == kk + 1)
@@ -320,7 +326,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                 if (i > 0) r += fabsf(e[i - 1].h);
                 an = fmaxf(an, r);
             }
-            an = group_maxf(gmask, an);
+            an = group_maxf<PG>(gmask, an);
             const int tiny_ex = f_expo(an) - DW_DEFLATE_BITS;
             int steps = 0, rot = 0;
             const int max_steps = 30 * R;
@@ -338,9 +344,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                     unsigned long long nm = 0;
                     for (int i = gl; i + 1 < R; i += PG)
                         if (dw_negligible(e[i], d[i], d[i + 1], tiny_ex)) nm |= 1ull << i;
-                    nm |= __shfl_xor_sync(gmask, nm, 4);
-                    nm |= __shfl_xor_sync(gmask, nm, 2);
-                    nm |= __shfl_xor_sync(gmask, nm, 1);
+                    nm = group_or<PG>(gmask, nm);
                     const unsigned long long nn = ~nm & ((1ull << q) - 1);
                     q = nn ? 64 - p2_clz64(nn) : 0;
                     if (q == 0) break;
@@ -453,7 +457,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
             // ---- cut, Z scaled by d^-1/4 (columns split over lanes) ---------
             float lmax = 0.f;
             for (int i = gl; i < R; i += PG) lmax = fmaxf(lmax, d[i].h);
-            lmax = group_maxf(gmask, lmax);
+            lmax = group_maxf<PG>(gmask, lmax);
             const float cut = rtol2 * lmax;
             for (int i = gl; i < R; i += PG) {
                 const dw di = d[i];

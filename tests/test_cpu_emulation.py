@@ -1,8 +1,9 @@
 """The library's CUDA kernels run on the CPU emulator (tests/cpu_emu) under
 AddressSanitizer: one ALS iteration at R = 5 and R = 10 (lane-per-subject
-Procrustes),
-at R = 13 (grouped Procrustes kernel) and at R = 5 with bfloat16 storage,
-a projection of new subjects, and U_k = Q_k H for a range of subjects.
+Procrustes), at R = 13 and R = 40 (grouped Procrustes, eight and sixteen lanes
+per subject) and at R = 5 with bfloat16 storage, a projection of new
+subjects, U_k = Q_k H for a range of subjects, and the seeded initialisation
+with the stopping rule.
 Every device buffer and every block's shared memory is a heap block of its
 exact size, so an out-of-bounds access by any kernel aborts the run; the
 results must also match the FP64 oracle.  No GPU involved."""
@@ -21,6 +22,7 @@ CASES = {
     "iterate_r5": ["iterate", "tiny", "24", "5"],
     "iterate_r10": ["iterate", "tiny", "24", "10"],
     "iterate_r13": ["iterate", "tiny", "16", "13"],
+    "iterate_r40": ["iterate", "tiny", "16", "40"],
     "iterate_r5_bf16": ["iterate", "tiny", "24", "5", "bf16"],
     "project_r12": ["project", "12", "3"],
     "getu_r5": ["getu", "5", "3", "17"],
@@ -68,7 +70,7 @@ def _result(runs, name):
     return json.loads(so.strip().splitlines()[-1])
 
 
-@pytest.mark.parametrize("name", ["iterate_r5", "iterate_r10", "iterate_r13"])
+@pytest.mark.parametrize("name", ["iterate_r5", "iterate_r10", "iterate_r13", "iterate_r40"])
 def test_emulated_iteration_is_in_bounds_and_matches_oracle(emulated_runs, name):
     err = _result(emulated_runs, name)
     for key in ("M1", "M2", "M3", "H", "V", "W"):

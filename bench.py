@@ -153,8 +153,11 @@ def job_throughput(nnz_per_rank, steps, ms_total_max, world):
 
 
 # sources that define each kernel whose DRAM traffic profiles/traffic.json records
-TRAFFIC_SOURCES = {"k_polar": ("p2_dw.cuh", "p2_eig_dw.cuh", "p2_polar.cu", "p2_polar.cuh",
-                               "p2_polar_grp.cu", "p2_polar_grp.cuh")}
+TRAFFIC_SOURCES = {
+    "k_polar_reg": ("p2_dw.cuh", "p2_eig_dw.cuh", "p2_polar.cu", "p2_polar.cuh"),
+    "k_polar_grp": ("p2_dw.cuh", "p2_polar.cu", "p2_polar.cuh", "p2_polar_grp.cu",
+                    "p2_polar_grp.cuh"),
+}
 
 
 def traffic_sources_sha1(kernel):
@@ -302,7 +305,7 @@ def run_p2(args, w):
                 f"{DW_INSTR_PER_FMA} FP32 instructions per double-word multiply-add",
                 "vs_fp64_nominal": ach / FP64_PEAK_TFLOPS,
                 "algorithmic_flops_per_launch": flops,
-                "traffic": _traffic("k_polar", w.name)}
+                "traffic": _traffic("k_polar_reg" if R <= 12 else "k_polar_grp", w.name)}
     else:
         by = bmodel.get(dom, 0)
         ach = by / (phase_ms[dom] / 1e3) / 1e9

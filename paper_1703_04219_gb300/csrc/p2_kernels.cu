@@ -27,7 +27,6 @@
 #include <algorithm>
 
 #include "p2_internal.cuh"
-#include "p2_eig.cuh"
 
 namespace p2 {
 

@@ -24,6 +24,9 @@ notes of the repository):
   carries lambda and S_k = diag(W(k,:)) keeps the model scale.
 * Moore-Penrose pseudo-inverses of the R x R Gram-Hadamard products drop
   eigenvalues <= R * 2^-52 * lambda_max.
+* Non-negative variant (Section 5.1 constrains {S_k} and V): the V and W
+  solves become row-wise non-negative least squares with the same Gram-
+  Hadamard products; H stays unconstrained.  The loss below is unchanged.
 * Loss: the surrogate L~ = sum_k ||X_k||^2 - 2<Y_k, H S_k V^T> + ||H S_k V^T||^2
   (the objective of Section 3.2's CP step plus the constant ||X_k||^2 -
   ||Q_k^T X_k||^2), fit = 1 - sqrt(max(L~, 0)) / ||X||_F.  The exact
@@ -132,17 +135,65 @@ def normalize_columns(A):
     return A / safe, n
 
 
-def cp_als_sweep(Ys, colsets, H, V, W):
+def nnls_gram(A, b):
+    """argmin_{x >= 0} ||y - B x||^2 given only A = B^T B (symmetric positive
+    definite) and b = B^T y, i.e. argmin_{x >= 0} x^T A x / 2 - b^T x.
+
+    The active-set method of Lawson and Hanson ("Solving Least Squares
+    Problems", 1974, Chapter 23, algorithm NNLS), with each least-squares
+    subproblem on the passive set P solved through its normal equations
+    A_PP z_P = b_P.  The minimiser is unique for positive definite A.
+    """
+    n = b.shape[0]
+    scale = max(float(np.max(np.abs(b))), float(np.max(np.abs(A))), 1e-300)
+    tol = 64 * n * EPS64 * scale
+    x = np.zeros(n)
+    P = np.zeros(n, dtype=bool)
+    w = b - A @ x
+    for _ in range(3 * n + 1):
+        if P.all() or not np.any(w[~P] > tol):
+            break
+        j = int(np.argmax(np.where(P, -np.inf, w)))
+        P[j] = True
+        while True:
+            idx = np.flatnonzero(P)
+            z = np.zeros(n)
+            z[idx] = np.linalg.solve(A[np.ix_(idx, idx)], b[idx])
+            if np.all(z[idx] > 0):
+                x = z
+                break
+            neg = idx[z[idx] <= 0]
+            alpha = np.min(x[neg] / (x[neg] - z[neg]))
+            x = x + alpha * (z - x)
+            P &= x > 0
+            x[~P] = 0.0
+        w = b - A @ x
+    return x
+
+
+def nnls_rows(M, A):
+    """Row-wise non-negative solves: row i of the result is nnls_gram(A, M[i])."""
+    return np.stack([nnls_gram(A, M[i]) for i in range(M.shape[0])]) if M.shape[0] else \
+        np.zeros_like(M)
+
+
+def cp_als_sweep(Ys, colsets, H, V, W, nonneg=False):
     """H <- M1 (W^TW * V^TV)^+, normalise; V <- M2 (W^TW * H^TH)^+, normalise;
-    W <- M3 (V^TV * H^TH)^+ (Algorithm 1, lines 3-7, with U = H)."""
+    W <- M3 (V^TV * H^TH)^+ (Algorithm 1, lines 3-7, with U = H).
+
+    nonneg: Section 5.1's variant with non-negative {S_k} and V: the V and W
+    updates become, row by row, the non-negative least-squares problems with
+    the same Gram-Hadamard products (nnls_gram); H stays unconstrained."""
     M1 = mttkrp_spartan(Ys, colsets, H, V, W, 1)
     H = M1 @ pinv_sym((W.T @ W) * (V.T @ V))
     H, _ = normalize_columns(H)
     M2 = mttkrp_spartan(Ys, colsets, H, V, W, 2)
-    V = M2 @ pinv_sym((W.T @ W) * (H.T @ H))
+    A2 = (W.T @ W) * (H.T @ H)
+    V = nnls_rows(M2, A2) if nonneg else M2 @ pinv_sym(A2)
     V, _ = normalize_columns(V)
     M3 = mttkrp_spartan(Ys, colsets, H, V, W, 3)
-    W = M3 @ pinv_sym((V.T @ V) * (H.T @ H))
+    A3 = (V.T @ V) * (H.T @ H)
+    W = nnls_rows(M3, A3) if nonneg else M3 @ pinv_sym(A3)
     return H, V, W, M1, M2, M3
 
 
@@ -181,13 +232,13 @@ def fit_from_loss(loss, nx2):
 # --------------------------------------------------------------------------
 # PARAFAC2-ALS (Algorithm 2)
 # --------------------------------------------------------------------------
-def als_iteration(blocks, H, V, W, rank_rtol=RANK_RTOL, want_exact=False):
+def als_iteration(blocks, H, V, W, rank_rtol=RANK_RTOL, want_exact=False, nonneg=False):
     """One pass of Algorithm 2's loop body: Q-step, Y, one CP-ALS sweep, S_k."""
     K = len(blocks)
     Qs = [procrustes_q(Xc, cols, H, V, W[k], rank_rtol) for k, (Xc, cols) in enumerate(blocks)]
     Ys = [form_y(Qs[k], blocks[k][0]) for k in range(K)]
     colsets = [cols for _, cols in blocks]
-    H, V, W, M1, M2, M3 = cp_als_sweep(Ys, colsets, H, V, W)
+    H, V, W, M1, M2, M3 = cp_als_sweep(Ys, colsets, H, V, W, nonneg)
     out = dict(H=H, V=V, W=W, M1=M1, M2=M2, M3=M3, Qs=Qs, Ys=Ys,
                loss=surrogate_loss(blocks, Ys, H, V, W))
     if want_exact:
@@ -196,7 +247,7 @@ def als_iteration(blocks, H, V, W, rank_rtol=RANK_RTOL, want_exact=False):
 
 
 def parafac2_als(slices, H0, V0, W0, n_iter, rank_rtol=RANK_RTOL, blocks=None,
-                 want_exact=False):
+                 want_exact=False, nonneg=False):
     """Run n_iter iterations of Algorithm 2 from (H0, V0, W0) in FP64.
 
     Returns the final factors and the per-iteration loss/fit history.
@@ -210,7 +261,7 @@ def parafac2_als(slices, H0, V0, W0, n_iter, rank_rtol=RANK_RTOL, blocks=None,
     hist = []
     last = None
     for _ in range(n_iter):
-        last = als_iteration(blocks, H, V, W, rank_rtol, want_exact)
+        last = als_iteration(blocks, H, V, W, rank_rtol, want_exact, nonneg)
         H, V, W = last["H"], last["V"], last["W"]
         rec = dict(loss=last["loss"], fit=fit_from_loss(last["loss"], nx2))
         if want_exact:

@@ -341,3 +341,55 @@ def test_projection_step_is_the_least_squares_row():
     KR = BF.khatri_rao(V, H)                                # row r + R j
     ref, *_ = np.linalg.lstsq(KR, Y.T.reshape(-1), rcond=None)
     assert rel_fro(s1, ref) < 1e-10
+
+
+# ---------------------------------------------------------------- non-negative variant
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (5, 2), (10, 3), (10, 4), (40, 5)])
+def test_nnls_gram_matches_scipy_and_kkt(n, seed):
+    """nnls_gram solves min_{x>=0} ||y - Bx||^2 from A = B^T B and b = B^T y:
+    it must equal scipy's NNLS (a separate Lawson-Hanson implementation) on
+    the factored problem min ||U x - U^{-T} b|| (A = U^T U), and satisfy the
+    KKT conditions x >= 0, w = b - A x <= 0 where x = 0, w = 0 where x > 0."""
+    import scipy.optimize
+    rng = np.random.default_rng(seed)
+    B = rng.standard_normal((3 * n + 2, n))
+    B[:, : max(1, n // 3)] *= 1e-2                      # some conditioning
+    A = B.T @ B
+    b = B.T @ rng.standard_normal(3 * n + 2)
+    x = P.nnls_gram(A, b)
+    U = scipy.linalg.cholesky(A, lower=False)
+    ref, _ = scipy.optimize.nnls(U, scipy.linalg.solve_triangular(U, b, trans="T"))
+    assert np.linalg.norm(x - ref) <= 1e-9 * max(np.linalg.norm(ref), 1e-300)
+    w = b - A @ x
+    scale = np.abs(b).max() + np.abs(A).max() * np.abs(x).max()
+    assert np.all(x >= 0)
+    assert np.all(w[x == 0] <= 1e-10 * scale)
+    assert np.all(np.abs(w[x > 0]) <= 1e-10 * scale)
+
+
+def test_nnls_gram_interior_and_boundary_cases():
+    """A positive unconstrained solution is returned as is; b < 0 gives 0; a
+    diagonal A decouples into max(b_i, 0) / A_ii."""
+    rng = np.random.default_rng(9)
+    B = rng.standard_normal((20, 6))
+    A = B.T @ B
+    x0 = rng.random(6) + 0.5
+    assert np.allclose(P.nnls_gram(A, A @ x0), x0, rtol=1e-12, atol=0)
+    assert np.all(P.nnls_gram(A, -np.ones(6)) == 0.0)       # x = 0 meets the KKT conditions
+    Ad = np.diag(rng.random(6) + 1.0)
+    bd = rng.standard_normal(6)
+    assert np.allclose(P.nnls_gram(Ad, bd), np.maximum(bd, 0) / np.diag(Ad), rtol=1e-14, atol=0)
+
+
+def test_nonneg_iteration_keeps_sign_and_decreases_loss():
+    """Section 5.1's variant: V and W stay non-negative and every block update
+    is an exact minimisation, so the surrogate loss never increases."""
+    X = synth.generate("tiny", K=60)
+    R = 5
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=1)
+    res = P.parafac2_als(X, H0, V0, W0, n_iter=10, nonneg=True)
+    assert np.all(res["V"] >= 0) and np.all(res["W"] >= 0)
+    losses = [h["loss"] for h in res["history"]]
+    nx2 = res["norm_x_sq"]
+    for a, b in zip(losses, losses[1:]):
+        assert b <= a + 1e-10 * nx2

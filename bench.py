@@ -330,6 +330,10 @@ def run_p2(args, w):
     bf16 = None
     if not args.no_bf16:
         bf16 = time_precision(X, R, H0, V0, W0, "bf16", args.steps, args.warmup, local)
+    nonneg = None
+    if not args.no_nonneg and R <= 16:
+        nonneg = time_precision(X, R, H0, V0, W0, "fp32", args.steps, args.warmup, local,
+                                nonneg=True)
     serving = None
     if rank == 0 and not args.no_serve:
         serving = {"fp32": run_serving(precision="fp32"), "bf16": run_serving(precision="bf16")}
@@ -345,7 +349,7 @@ def run_p2(args, w):
                        "graph": True, "fit_after_steps": fit},
             "phase_ms": phase_ms, "sparse_passes": sparse, "roofline": roof,
             "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-            "bf16_storage": bf16, "serving": serving}
+            "bf16_storage": bf16, "nonneg": nonneg, "serving": serving}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
@@ -387,12 +391,14 @@ def timed_steps(m, stream, steps, pg=None, clocks=None):
             "flops": (st1["polar_fp64_flops"] - st0["polar_fp64_flops"]) / steps, "clocks": clk}
 
 
-def time_precision(X, R, H0, V0, W0, precision, steps, warmup, device):
-    """The same workload and timing with another storage precision."""
+def time_precision(X, R, H0, V0, W0, precision, steps, warmup, device, nonneg=False):
+    """The same workload and timing with another storage precision, or in the
+    non-negative variant (Section 5.1)."""
     import torch
     import paper_1703_04219_gb300 as p2
     stream = torch.cuda.Stream()
-    m = p2.Parafac2(R, device=device, stream=stream.cuda_stream, timing=True, precision=precision)
+    m = p2.Parafac2(R, device=device, stream=stream.cuda_stream, timing=True, precision=precision,
+                    nonneg=nonneg)
     m.load(X)
     m.init(H0, V0, W0)
     for _ in range(warmup):
@@ -404,7 +410,8 @@ def time_precision(X, R, H0, V0, W0, precision, steps, warmup, device):
     ms = t["ms_total"] / steps
     return {"ms_per_step": ms, "value": X.nnz / (ms / 1e3), "unit": UNIT,
             "fit_after_steps": fit, "phase_ms": t["phase_ms"],
-            "storage": "V and P_k bfloat16" if precision == "bf16" else "float"}
+            "storage": "V and P_k bfloat16" if precision == "bf16" else "float",
+            "nonneg": bool(nonneg)}
 
 
 def run_serving(rate=50000.0, horizon_s=2.0, n_iter=5, n_slots=4, seed=5, precision="fp32"):
@@ -489,6 +496,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
+    ap.add_argument("--no-nonneg", action="store_true", help="skip the non-negative variant line")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

@@ -65,6 +65,9 @@ typedef struct {
     void *stream;         /* cudaStream_t to enqueue on; NULL: the context creates its own */
     int32_t timing;       /* non-zero: CUDA events around each phase of an iteration (p2_stats) */
     uint64_t seed;        /* seed of the initial factors p2_init draws when given NULLs */
+    int32_t nonneg;       /* non-zero: S_k and V constrained non-negative (Section 5.1), the
+                             W and V updates solved row by row as non-negative least squares;
+                             requires R <= 16 */
 } p2_options;
 
 /* Counters and timings of a context (p2_stats). */
@@ -81,7 +84,7 @@ typedef struct {
 } p2_stats_t;
 
 /* Fill *opt with defaults for rank R (precision FP32, device 0, graph on,
- * rank_rtol 1e-5, own stream, timing off, seed 20170314). */
+ * rank_rtol 1e-5, own stream, timing off, seed 20170314, unconstrained). */
 void p2_default_options(p2_options *opt, int32_t R);
 
 /* Create a context on opt->device.  *out receives the handle (NULL on error).

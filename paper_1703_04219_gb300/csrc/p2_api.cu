@@ -83,6 +83,8 @@ static void free_data(p2_ctx *c) {
     dfree(c, &c->d_W, K * R);
     dfree(c, &c->d_M3, K * R);
     dfree(c, &c->d_qrcnt, K);
+    dfree(c, &c->d_passW, K);
+    dfree(c, &c->d_passV, J);
     dfree(c, &c->d_order, K);
     dfree(c, &c->d_rank, K);
     dfree(c, &c->d_binoff, (size_t)((K + P2_ORDER_CHUNK - 1) / P2_ORDER_CHUNK) * P2_ORDER_BINS);
@@ -141,6 +143,12 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
     P2_TRY(dalloc(c, &c->d_binoff,
                   (size_t)((K + P2_ORDER_CHUNK - 1) / P2_ORDER_CHUNK) * P2_ORDER_BINS));
     P2_CUDA_TRY(cudaMemsetAsync(c->d_qrcnt, 0, sizeof(int32_t) * (size_t)K, c->stream));
+    if (c->opt.nonneg) {
+        P2_TRY(dalloc(c, &c->d_passW, (size_t)K));
+        P2_TRY(dalloc(c, &c->d_passV, (size_t)J));
+        P2_CUDA_TRY(cudaMemsetAsync(c->d_passW, 0, sizeof(uint32_t) * (size_t)K, c->stream));
+        P2_CUDA_TRY(cudaMemsetAsync(c->d_passV, 0, sizeof(uint32_t) * (size_t)J, c->stream));
+    }
     P2_TRY(dalloc(c, &c->d_G, (size_t)K * P));
     P2_TRY(dalloc(c, &c->d_Gf, (size_t)K * P));
     P2_CUDA_TRY(cudaMemsetAsync(c->d_M3, 0, sizeof(float) * (size_t)K * R, c->stream));
@@ -235,12 +243,15 @@ void p2_default_options(p2_options *opt, int32_t R) {
     opt->stream = nullptr;
     opt->timing = 0;
     opt->seed = 20170314ULL;
+    opt->nonneg = 0;
 }
 
 int p2_create(p2_ctx **out, const p2_options *opt) {
     if (!out || !opt) return fail(P2_EINVAL, "p2_create: NULL argument");
     *out = nullptr;
     if (opt->R < 1 || opt->R > P2_RMAX) return fail(P2_EINVAL, "p2_create: R must be in [1, 64]");
+    if (opt->nonneg && opt->R > 16)
+        return fail(P2_EINVAL, "p2_create: the non-negative variant supports R <= 16");
     if (opt->precision != P2_FP32 && opt->precision != P2_BF16)
         return fail(P2_EINVAL, "p2_create: precision must be P2_FP32 or P2_BF16");
     int ndev = 0;

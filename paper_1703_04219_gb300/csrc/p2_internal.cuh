@@ -153,6 +153,9 @@ struct p2_ctx {
     int32_t *d_order = nullptr;  // [K] subject processed by each Procrustes slot
     int32_t *d_rank = nullptr;   // [K] rank within the subject's bin and chunk
     int32_t *d_binoff = nullptr; // [nchunk x 256] bin counts, then offsets
+    // non-negative variant: each row's passive set (bit j: x_j > 0) of the last solve
+    uint32_t *d_passW = nullptr; // [K]
+    uint32_t *d_passV = nullptr; // [J]
     double *d_M2 = nullptr;     // J x R (relabelled rows)
     float *d_P = nullptr;       // N x R rows of P_k = Z_k F_k (mode-2 pass)
     double *d_segpart = nullptr; // nseg x R partial sums of the mode-2 reduction
@@ -204,6 +207,10 @@ cudaError_t launch_polar_on(const p2_ctx *c, const dw *G, const float *W, SmallS
 #define P2_ORDER_BINS 256
 // kernels launched by launch_polar (the ordering and the Procrustes kernel)
 constexpr int POLAR_LAUNCHES = 4;
+// non-negative variant (p2_nnls.cu): row-wise NNLS for the W and V updates
+cudaError_t nnls_configure(int cap);
+cudaError_t launch_nnls_w(p2_ctx *c);
+cudaError_t launch_nnls_v(p2_ctx *c, double *part, int nparts);
 // U_k = Q_k H rows of subjects k0 .. k1-1 into a device FP32 buffer (p2_kernels.cu)
 cudaError_t launch_get_u(p2_ctx *c, int64_t k0, int64_t k1, int64_t r0, float *U);
 // Gram of Z_k = X_k V for a batch of new subjects (p2_kernels.cu)

@@ -1089,6 +1089,13 @@ int configure_kernels(p2_ctx *c) {
     if (rc == P2_OK) rc = allow_dynamic_smem(k_fin_v, cap, "k_fin_v");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_subject_stats, cap, "k_subject_stats");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_subject_stats_gf, cap, "k_subject_stats_gf");
+    if (rc == P2_OK && c->opt.nonneg) {
+        const cudaError_t e = nnls_configure(cap);
+        if (e != cudaSuccess) {
+            set_error("configuring the NNLS kernels: %s", cudaGetErrorString(e));
+            rc = P2_ECUDA;
+        }
+    }
     return rc;
 }
 
@@ -1391,11 +1398,21 @@ int enqueue_iteration(p2_ctx *c) {
     P2_LAUNCH_CHECK("k_m2_columns");
     // V step (Algorithm 1 line 5)
     mark(c, 2);
-    k_solve_v_pinv<<<1, 256, sm_pinv, s>>>(c->d_s, R);
-    P2_LAUNCH_CHECK("k_solve_v_pinv");
-    k_solve_v_rows<<<nb, 256, ((size_t)R * R + 256) * 8, s>>>(c->d_M2, c->d_s, c->d_Vun,
-                                                               c->d_part2, J, R);
-    P2_LAUNCH_CHECK("k_solve_v_rows");
+    if (c->opt.nonneg) {
+        // Section 5.1's variant: V rows by non-negative least squares
+        const cudaError_t e = launch_nnls_v(c, c->d_part2, nb);
+        if (e != cudaSuccess) {
+            set_error("launch of the V NNLS kernels failed: %s", cudaGetErrorString(e));
+            return P2_ECUDA;
+        }
+        c->enqueued += 2;
+    } else {
+        k_solve_v_pinv<<<1, 256, sm_pinv, s>>>(c->d_s, R);
+        P2_LAUNCH_CHECK("k_solve_v_pinv");
+        k_solve_v_rows<<<nb, 256, ((size_t)R * R + 256) * 8, s>>>(c->d_M2, c->d_s, c->d_Vun,
+                                                                   c->d_part2, J, R);
+        P2_LAUNCH_CHECK("k_solve_v_rows");
+    }
     k_solve_v_norm<<<1, 64, 0, s>>>(c->d_part2, nb, c->d_s, R);
     P2_LAUNCH_CHECK("k_solve_v_norm");
     if (c->bf16)
@@ -1414,6 +1431,15 @@ int enqueue_iteration(p2_ctx *c) {
     mark(c, 3);
     launch_alpha<true>(c, L);
     P2_LAUNCH_CHECK("k_alpha<true>");
+    if (c->opt.nonneg) {
+        // W rows by non-negative least squares over the M3 rows pass alpha wrote
+        const cudaError_t e = launch_nnls_w(c);
+        if (e != cudaSuccess) {
+            set_error("launch of the W NNLS kernel failed: %s", cudaGetErrorString(e));
+            return P2_ECUDA;
+        }
+        c->enqueued += 1;
+    }
     // next Q-step (Algorithm 2's SVD loop), mode-1 MTTKRP, W statistics, fit
     int rc = enqueue_qstep(c, 1);
     mark(c, 7);

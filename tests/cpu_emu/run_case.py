@@ -28,19 +28,24 @@ def bf16_round(a):
 
 
 def iterate_case(name, K, R, precision="fp32"):
+    nonneg = precision == "nonneg"
+    if nonneg:
+        precision = "fp32"
     X = synth.generate(name, K=K)
     H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=11)
     if precision == "bf16":                # a start that bfloat16 storage represents exactly
         V0 = bf16_round(V0)
-    with p2.Parafac2(R, use_graph=False, precision=precision) as m:
+    with p2.Parafac2(R, use_graph=False, precision=precision, nonneg=nonneg) as m:
         m.load(X)
         m.init(H0, V0, W0)
         fit = m.iterate(1)
         H, V, W = m.factors()
         M = {n: m.mttkrp(n) for n in (1, 2, 3)}
     ref = P.als_iteration(P.all_blocks(X), H0.astype(np.float64), V0.astype(np.float64),
-                          W0.astype(np.float64))
+                          W0.astype(np.float64), nonneg=nonneg)
     err = {key: rel_fro(M[mode], ref[key]) for mode, key in ((1, "M1"), (2, "M2"), (3, "M3"))}
+    if nonneg:
+        err["neg"] = float(min(V.min(), W.min()) < 0)
     err.update({key: rel_fro(v, ref[key]) for key, v in (("H", H), ("V", V), ("W", W))})
     err["fit"] = abs(fit - P.fit_from_loss(ref["loss"], P.norm_x_sq(P.all_blocks(X))))
     return err

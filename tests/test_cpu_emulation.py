@@ -1,7 +1,8 @@
 """The library's CUDA kernels run on the CPU emulator (tests/cpu_emu) under
 AddressSanitizer: one ALS iteration at R = 5 and R = 10 (lane-per-subject
 Procrustes), at R = 13 and R = 40 (grouped Procrustes, eight and sixteen lanes
-per subject) and at R = 5 with bfloat16 storage, a projection of new
+per subject), at R = 5 with bfloat16 storage and in the non-negative
+variant, a projection of new
 subjects, U_k = Q_k H for a range of subjects, and the seeded initialisation
 with the stopping rule.
 Every device buffer and every block's shared memory is a heap block of its
@@ -24,6 +25,7 @@ CASES = {
     "iterate_r13": ["iterate", "tiny", "16", "13"],
     "iterate_r40": ["iterate", "tiny", "16", "40"],
     "iterate_r5_bf16": ["iterate", "tiny", "24", "5", "bf16"],
+    "iterate_r5_nonneg": ["iterate", "tiny", "24", "5", "nonneg"],
     "project_r12": ["project", "12", "3"],
     "getu_r5": ["getu", "5", "3", "17"],
     "seed_r4": ["seed", "4", "987654321"],
@@ -101,4 +103,13 @@ def test_emulated_seeded_init_and_stopping_rule(emulated_runs):
     assert out["init_equal"] == 1.0
     assert out["n"] == 3 and out["fit"] == out["fit_fixed"]
     assert out["n_loose"] == 2
+
+
+def test_emulated_nonneg_iteration_is_in_bounds_and_matches_oracle(emulated_runs):
+    """Section 5.1's non-negative variant: row-wise NNLS for V and W."""
+    err = _result(emulated_runs, "iterate_r5_nonneg")
+    assert err["neg"] == 0.0
+    for key in ("M1", "M2", "M3", "H", "V", "W"):
+        assert err[key] < 1e-5, (key, err[key])
+    assert err["fit"] < 1e-4
 

@@ -197,3 +197,42 @@ def test_seeded_init_and_stopping_rule(p2):
         m.load(X)
         m.init(H0, V0, W0)
         assert m.iterate(n) == fit
+
+
+@pytest.mark.parametrize("name,K,R", [("tiny", 200, 5), ("c63m", 3000, 10), ("c63m", 1500, 16)])
+def test_nonneg_one_step_parity(p2, name, K, R):
+    """Section 5.1's variant (non-negative S_k and V): one iteration from the
+    same FP32-exact start against the oracle's Lawson-Hanson solves."""
+    X = synth.generate(name, K=K)
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=3)
+    with p2.Parafac2(R, nonneg=True) as m:
+        m.load(X)
+        m.init(H0, V0, W0)
+        fit = m.iterate(1)
+        H, V, W = m.factors()
+        M = {n: m.mttkrp(n) for n in (1, 2, 3)}
+    blocks = P.all_blocks(X)
+    ref = P.als_iteration(blocks, H0.astype(np.float64), V0.astype(np.float64),
+                          W0.astype(np.float64), nonneg=True)
+    assert np.all(V >= 0) and np.all(W >= 0)
+    for mode, key in ((1, "M1"), (2, "M2"), (3, "M3")):
+        assert rel_fro(M[mode], ref[key]) < TOL, (key, rel_fro(M[mode], ref[key]))
+    for key, v in (("H", H), ("V", V), ("W", W)):
+        assert rel_fro(v, ref[key]) < TOL, (key, rel_fro(v, ref[key]))
+    assert abs(fit - P.fit_from_loss(ref["loss"], P.norm_x_sq(blocks))) < FIT_TOL
+
+
+def test_nonneg_ten_iterations_and_limits(p2):
+    X = synth.generate("tiny", K=200)
+    R = 5
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=4)
+    with p2.Parafac2(R, nonneg=True) as m:
+        m.load(X)
+        m.init(H0, V0, W0)
+        fit = m.iterate(10)
+        _, V, W = m.factors()
+    ref = P.parafac2_als(X, H0, V0, W0, n_iter=10, nonneg=True)
+    assert abs(fit - ref["history"][-1]["fit"]) < FIT_TOL
+    assert np.all(V >= 0) and np.all(W >= 0)
+    with pytest.raises(p2.P2Error):
+        p2.Parafac2(17, nonneg=True)

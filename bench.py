@@ -56,6 +56,11 @@ def _peaks():
 
 
 def _workload_desc(w, X):
+    if w.planted_rank > 0:
+        return (f"{w.name}: K={w.K:,} subjects, J={w.J:,}, planted PARAFAC2 X_k = Q_k H S_k V^T "
+                f"(rank {w.planted_rank}, {w.dense_rows} dense rows) kept with p={w.keep_p:g}, "
+                f"empty rows dropped (mean I_k {X.n_rows / max(X.K, 1):.1f}), R={w.R}, "
+                f"nnz={X.nnz:,}")
     cols = "uniform" if w.col_mode == 0 else f"Zipf({w.zipf_s}) via seeded permutation"
     return (f"{w.name}: K={w.K:,} subjects, J={w.J:,}, I_k~U{{{w.imin}..{w.imax}}}, "
             f"Poisson({w.lam})+1 nnz/row, {cols} columns, values 1+Poisson(1), "

@@ -19,7 +19,15 @@ non-zeros at R = 10 and 40):
 * ``serve`` projection requests: I ~ round(lognormal(3, 1)) clipped to
   [1, 1000], Poisson(2)+1 nnz/row, Zipf(1.1) columns, J=5,000
 
-Values are 1 + Poisson(1) stored as FP32 in every workload.
+Values are 1 + Poisson(1) stored as FP32 in these workloads.
+
+Paper-shaped planted workloads (the recipe of Section 5, "Synthetic Data"):
+dense 100 x J slices X_k = Q_k H S_k V^T at planted rank 40, entries kept
+uniformly with probability p, empty rows dropped:
+
+* ``p63m``  K=1,000,000, J=5,000, p = 1.26e-4 (about 63M nnz, mean I_k ~ 46.7), R=10
+* ``p500m`` K=1,000,000, J=5,000, p = 1e-3 (about 500M nnz, mean I_k ~ 99.3), R=40
+* ``ptiny`` K=50, J=200, 20 dense rows, planted rank 6, p = 0.05, R=5
 """
 from __future__ import annotations
 
@@ -63,6 +71,11 @@ class _Cfg(ctypes.Structure):
                 ("val_lam", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
+class _PCfg(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int64), ("J", ctypes.c_int32), ("dense_rows", ctypes.c_int32),
+                ("rank", ctypes.c_int32), ("keep_p", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
 def _lib():
     global _LIB
     if _LIB is None:
@@ -77,6 +90,17 @@ def _lib():
         lib.p2synth_fill.restype = ctypes.c_int
         lib.p2synth_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                         ctypes.c_void_p]
+        lib.p2synth_planted_subjects.argtypes = [P(_PCfg), ctypes.c_void_p]
+        lib.p2synth_planted_subjects.restype = ctypes.c_int64
+        lib.p2synth_planted_rows.argtypes = [P(_PCfg), ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_void_p]
+        lib.p2synth_planted_rows.restype = ctypes.c_int64
+        lib.p2synth_planted_fill.argtypes = [P(_PCfg), ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p]
+        lib.p2synth_planted_fill.restype = ctypes.c_int
+        lib.p2synth_planted_factors.argtypes = [P(_PCfg), ctypes.c_int64, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.p2synth_planted_factors.restype = None
         lib.p2synth_uniform.restype = None
         lib.p2synth_threads.argtypes = []
         lib.p2synth_threads.restype = ctypes.c_int
@@ -101,6 +125,9 @@ class Workload:
     zipf_s: float = 1.1
     val_lam: float = 1.0        # values = 1 + Poisson(val_lam)
     seed: int = 20170314
+    planted_rank: int = 0       # > 0: planted PARAFAC2 model (only K, J and the fields below used)
+    keep_p: float = 0.0         # keep probability of a planted entry
+    dense_rows: int = 100       # planted observations per subject before sparsification
 
     def scaled(self, K: int) -> "Workload":
         """Same recipe and seed stream with fewer (or more) subjects."""
@@ -115,6 +142,12 @@ WORKLOADS = {
     "c250m": Workload("c250m", K=1_000_000, J=5000, R=40, lam=3.95, seed=20170314 + 3),
     "serve": Workload("serve", K=1000, J=5000, R=40, imin=1, imax=1000, size_mode=1, mu=3.0,
                       sigma=1.0, lam=2.0, seed=20170314 + 4),
+    "p63m": Workload("p63m", K=1_000_000, J=5000, R=10, planted_rank=40, keep_p=1.26e-4,
+                     seed=20170314 + 5),
+    "p500m": Workload("p500m", K=1_000_000, J=5000, R=40, planted_rank=40, keep_p=1e-3,
+                      seed=20170314 + 6),
+    "ptiny": Workload("ptiny", K=50, J=200, R=5, planted_rank=6, keep_p=0.05, dense_rows=20,
+                      seed=20170314 + 7),
 }
 
 
@@ -178,6 +211,8 @@ def generate(w: Workload | str, K: int | None = None) -> Slices:
     if K is not None:
         w = w.scaled(K)
     lib = _lib()
+    if w.planted_rank > 0:
+        return _generate_planted(w)
     cfg = _cfg(w)
     subj_ptr = np.zeros(w.K + 1, np.int64)
     n = lib.p2synth_subjects(ctypes.byref(cfg), subj_ptr.ctypes.data)
@@ -189,6 +224,41 @@ def generate(w: Workload | str, K: int | None = None) -> Slices:
                         val.ctypes.data) != 0:
         raise MemoryError("p2synth_fill: allocation failed")
     return Slices(w.K, w.J, subj_ptr, row_ptr, col, val)
+
+
+def _pcfg(w: Workload) -> _PCfg:
+    return _PCfg(w.K, w.J, w.dense_rows, w.planted_rank, w.keep_p, w.seed)
+
+
+def _generate_planted(w: Workload) -> Slices:
+    lib = _lib()
+    cfg = _pcfg(w)
+    subj_ptr = np.zeros(w.K + 1, np.int64)
+    n = lib.p2synth_planted_subjects(ctypes.byref(cfg), subj_ptr.ctypes.data)
+    row_ptr = np.zeros(n + 1, np.int64)
+    nnz = lib.p2synth_planted_rows(ctypes.byref(cfg), subj_ptr.ctypes.data, n,
+                                   row_ptr.ctypes.data)
+    col = np.empty(nnz, np.int32)
+    val = np.empty(nnz, np.float32)
+    if lib.p2synth_planted_fill(ctypes.byref(cfg), subj_ptr.ctypes.data, row_ptr.ctypes.data,
+                                col.ctypes.data, val.ctypes.data) != 0:
+        raise MemoryError("p2synth_planted_fill: allocation failed")
+    return Slices(w.K, w.J, subj_ptr, row_ptr, col, val)
+
+
+def planted_factors(w: Workload | str, k: int):
+    """The planted H (Rp x Rp), V (J x Rp) and subject k's S_k diagonal (Rp)
+    and reflector vector v (dense_rows): Q_k = (I - 2 v v^T)[:, :Rp]."""
+    if isinstance(w, str):
+        w = WORKLOADS[w]
+    Rp = w.planted_rank
+    H = np.empty((Rp, Rp), np.float32)
+    V = np.empty((w.J, Rp), np.float32)
+    s = np.empty(Rp, np.float32)
+    v = np.empty(w.dense_rows, np.float64)
+    _lib().p2synth_planted_factors(ctypes.byref(_pcfg(w)), int(k), H.ctypes.data,
+                                   V.ctypes.data, s.ctypes.data, v.ctypes.data)
+    return H, V, s, v
 
 
 def uniform(seed: int, stream: int, shape) -> np.ndarray:

@@ -228,6 +228,159 @@ int p2synth_fill(const p2synth_cfg *c, int64_t N, const int64_t *row_ptr,
     return 0;
 }
 
+/* ---- planted PARAFAC2 workload (the paper's synthetic recipe) -------------
+ * Section 5 ("Synthetic Data") builds its tensors from planted factors: each
+ * subject k has dense_rows observations of J variables, X_k = Q_k H S_k V^T
+ * with Q_k^T Q_k = I at rank Rp, and the entries are then sparsified
+ * uniformly with keep probability p; empty rows are dropped (which is why the
+ * paper's mean I_k is 46.9 at 63M non-zeros and 99.3 at 500M).  Here H
+ * (Rp x Rp), V (J x Rp) and the diagonal of S_k are uniform in [0, 1); Q_k is
+ * the first Rp columns of the Householder reflector I - 2 v v^T with v a
+ * uniformly random unit vector (orthonormal columns, one entry per O(1)
+ * work: Q_k(i, r) = [i == r] - 2 v_i v_r); the number of kept entries of a
+ * dense row is Poisson(J p) (capped at J) over distinct uniform columns. */
+typedef struct {
+    int64_t K;
+    int32_t J;
+    int32_t dense_rows;   /* observations per subject before sparsification */
+    int32_t rank;         /* planted rank Rp <= dense_rows */
+    double keep_p;        /* keep probability of an entry */
+    uint64_t seed;
+} p2synth_pcfg;
+
+enum { STREAM_PLANT_H = 7, STREAM_PLANT_V = 8, STREAM_PLANT_W = 9, STREAM_PLANT_Q = 10 };
+
+static int32_t planted_count(const p2synth_pcfg *c, int64_t k, int32_t i) {
+    sm64_t g = sm64_for(c->seed, STREAM_ROWNNZ, (uint64_t)(k * c->dense_rows + i));
+    int64_t n = (int64_t)poisson(&g, (double)c->J * c->keep_p);
+    return (int32_t)(n > c->J ? c->J : n);
+}
+
+static float planted_u01(uint64_t seed, uint64_t stream, uint64_t i) {
+    sm64_t g = sm64_for(seed, stream, i);
+    return (float)((double)(sm64_next(&g) >> 40) * 0x1.0p-24);
+}
+
+/* H (Rp x Rp), V (J x Rp) and, for subject k, w (Rp) and the unit vector v
+ * (dense_rows); any pointer may be NULL. */
+void p2synth_planted_factors(const p2synth_pcfg *c, int64_t k, float *H, float *V, float *w,
+                             double *v) {
+    const int32_t Rp = c->rank;
+    if (H) for (int64_t e = 0; e < (int64_t)Rp * Rp; e++) H[e] = planted_u01(c->seed, STREAM_PLANT_H, (uint64_t)e);
+    if (V) for (int64_t e = 0; e < (int64_t)c->J * Rp; e++) V[e] = planted_u01(c->seed, STREAM_PLANT_V, (uint64_t)e);
+    if (w) for (int32_t s = 0; s < Rp; s++) w[s] = planted_u01(c->seed, STREAM_PLANT_W, (uint64_t)(k * Rp + s));
+    if (v) {
+        sm64_t g = sm64_for(c->seed, STREAM_PLANT_Q, (uint64_t)k);
+        double nrm = 0.0;
+        for (int32_t i = 0; i < c->dense_rows; i += 2) {      /* Box-Muller pairs */
+            double u1 = u01_open0(&g), u2 = u01(&g);
+            double rr = sqrt(-2.0 * p_log(u1));
+            v[i] = rr * p_cos_2pi(u2);
+            if (i + 1 < c->dense_rows) v[i + 1] = rr * p_cos_2pi(u2 + 0.25);
+        }
+        for (int32_t i = 0; i < c->dense_rows; i++) nrm += v[i] * v[i];
+        nrm = sqrt(nrm);
+        for (int32_t i = 0; i < c->dense_rows; i++) v[i] /= nrm;
+    }
+}
+
+/* Pass 1: rows per subject = non-empty dense rows. Returns total rows. */
+int64_t p2synth_planted_subjects(const p2synth_pcfg *c, int64_t *subj_ptr) {
+    #pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < c->K; k++) {
+        int64_t n = 0;
+        for (int32_t i = 0; i < c->dense_rows; i++) n += planted_count(c, k, i) > 0;
+        subj_ptr[k + 1] = n;
+    }
+    subj_ptr[0] = 0;
+    for (int64_t k = 0; k < c->K; k++) subj_ptr[k + 1] += subj_ptr[k];
+    return subj_ptr[c->K];
+}
+
+/* Pass 2: row offsets. Returns nnz. */
+int64_t p2synth_planted_rows(const p2synth_pcfg *c, const int64_t *subj_ptr, int64_t N,
+                             int64_t *row_ptr) {
+    #pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < c->K; k++) {
+        int64_t r = subj_ptr[k];
+        for (int32_t i = 0; i < c->dense_rows; i++) {
+            int32_t n = planted_count(c, k, i);
+            if (n > 0) row_ptr[++r] = n;
+        }
+    }
+    row_ptr[0] = 0;
+    for (int64_t r = 0; r < N; r++) row_ptr[r + 1] += row_ptr[r];
+    return row_ptr[N];
+}
+
+/* Pass 3: distinct sorted uniform columns and the planted values
+ * x_ij = sum_s U_k(i, s) w_s V(j, s), U_k = Q_k H, computed in double. */
+int p2synth_planted_fill(const p2synth_pcfg *c, const int64_t *subj_ptr, const int64_t *row_ptr,
+                         int32_t *col, float *val) {
+    const int32_t Rp = c->rank, J = c->J, D = c->dense_rows;
+    float *H = (float *)malloc(sizeof(float) * (size_t)Rp * Rp);
+    float *V = (float *)malloc(sizeof(float) * (size_t)J * Rp);
+    if (!H || !V) { free(H); free(V); return -1; }
+    p2synth_planted_factors(c, 0, H, V, NULL, NULL);
+    int fail = 0;
+    #pragma omp parallel
+    {
+        double *v = (double *)malloc(sizeof(double) * (size_t)D);
+        double *cs = (double *)malloc(sizeof(double) * (size_t)Rp);
+        double *u = (double *)malloc(sizeof(double) * (size_t)Rp);
+        float *w = (float *)malloc(sizeof(float) * (size_t)Rp);
+        if (!v || !cs || !u || !w) {
+            #pragma omp atomic write
+            fail = 1;
+        } else {
+            #pragma omp for schedule(dynamic, 256)
+            for (int64_t k = 0; k < c->K; k++) {
+                p2synth_planted_factors(c, k, NULL, NULL, w, v);
+                for (int32_t s = 0; s < Rp; s++) {          /* c = v_{0:Rp}^T H */
+                    double a = 0.0;
+                    for (int32_t r = 0; r < Rp; r++) a += v[r] * (double)H[r * Rp + s];
+                    cs[s] = a;
+                }
+                int64_t r = subj_ptr[k];
+                for (int32_t i = 0; i < D; i++) {
+                    int32_t n = planted_count(c, k, i);
+                    if (n == 0) continue;
+                    for (int32_t s = 0; s < Rp; s++)       /* u_i = Q_k(i,:) H, times S_k */
+                        u[s] = ((i < Rp ? (double)H[i * Rp + s] : 0.0) - 2.0 * v[i] * cs[s]) * (double)w[s];
+                    int64_t b = row_ptr[r];
+                    int32_t *cc = col + b;
+                    sm64_t g = sm64_for(c->seed, STREAM_ROWCOLS, (uint64_t)(k * D + i));
+                    int32_t have = 0;
+                    int64_t tries = 0, max_tries = 64LL * n + 1024;
+                    while (have < n && tries < max_tries) {
+                        int32_t j = (int32_t)(sm64_next(&g) % (uint64_t)J);
+                        tries++;
+                        int dup = 0;
+                        for (int32_t t = 0; t < have; t++) if (cc[t] == j) { dup = 1; break; }
+                        if (!dup) cc[have++] = j;
+                    }
+                    for (int32_t j = 0; have < n && j < J; j++) {
+                        int dup = 0;
+                        for (int32_t t = 0; t < have; t++) if (cc[t] == j) { dup = 1; break; }
+                        if (!dup) cc[have++] = j;
+                    }
+                    qsort(cc, (size_t)n, sizeof(int32_t), cmp_i32);
+                    for (int32_t t = 0; t < n; t++) {
+                        const float *vj = V + (size_t)cc[t] * Rp;
+                        double x = 0.0;
+                        for (int32_t s = 0; s < Rp; s++) x += u[s] * (double)vj[s];
+                        val[b + t] = (float)x;
+                    }
+                    r++;
+                }
+            }
+        }
+        free(v); free(cs); free(u); free(w);
+    }
+    free(H); free(V);
+    return fail ? -1 : 0;
+}
+
 /* n values uniform in [0,1), each a multiple of 2^-24 so that it is exact in
  * FP32 and FP64 alike; used for initial factors H, V, W. */
 void p2synth_uniform(uint64_t seed, uint64_t stream, int64_t n, float *out) {

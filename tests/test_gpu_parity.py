@@ -199,7 +199,8 @@ def test_seeded_init_and_stopping_rule(p2):
         assert m.iterate(n) == fit
 
 
-@pytest.mark.parametrize("name,K,R", [("tiny", 200, 5), ("c63m", 3000, 10), ("c63m", 1500, 16)])
+@pytest.mark.parametrize("name,K,R", [("tiny", 200, 5), ("c63m", 3000, 10), ("c63m", 1500, 16),
+                                      ("ptiny", 50, 5), ("p63m", 2000, 10)])
 def test_nonneg_one_step_parity(p2, name, K, R):
     """Section 5.1's variant (non-negative S_k and V): one iteration from the
     same FP32-exact start against the oracle's Lawson-Hanson solves."""

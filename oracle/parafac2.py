@@ -275,17 +275,19 @@ def parafac2_als(slices, H0, V0, W0, n_iter, rank_rtol=RANK_RTOL, blocks=None,
 # Q-step and Algorithm 1's W update (mode-3 MTTKRP, Eq. mttkrp3_row_wise,
 # times (V^TV * H^TH)^+) applied to one subject with H and V held fixed
 # --------------------------------------------------------------------------
-def project_subject(Xc, cols, H, V, n_iter, rank_rtol=RANK_RTOL, s0=None):
+def project_subject(Xc, cols, H, V, n_iter, rank_rtol=RANK_RTOL, s0=None, nonneg=False):
     """Alternate Q <- Procrustes(X, H, V, diag(s)) and s <- coldot(H, Q^T X V) G3^+,
-    starting from s = 1 (or s0), n_iter times; return s and the Q for the final s."""
+    starting from s = 1 (or s0), n_iter times; return s and the Q for the final s.
+    nonneg: the model's non-negative variant, s = nnls_gram(G3, coldot(...))."""
     R = H.shape[0]
     s = np.ones(R) if s0 is None else np.asarray(s0, np.float64)
-    G3p = pinv_sym((V.T @ V) * (H.T @ H))
+    G3 = (V.T @ V) * (H.T @ H)
+    G3p = pinv_sym(G3)
     for _ in range(n_iter):
         Q = procrustes_q(Xc, cols, H, V, s, rank_rtol)
         Y = form_y(Q, Xc)
         m3 = np.sum(H * (Y @ V[cols]), axis=0)
-        s = m3 @ G3p
+        s = nnls_gram(G3, m3) if nonneg else m3 @ G3p
     return s, procrustes_q(Xc, cols, H, V, s, rank_rtol)
 
 

@@ -211,6 +211,11 @@ constexpr int POLAR_LAUNCHES = 4;
 cudaError_t nnls_configure(int cap);
 cudaError_t launch_nnls_w(p2_ctx *c);
 cudaError_t launch_nnls_v(p2_ctx *c, double *part, int nparts);
+cudaError_t launch_nnls_rows(const p2_ctx *c, const double *Xa, const double *Xb,
+                             const float *rows, int64_t n, uint32_t *passive, float *out,
+                             cudaStream_t s);
+const double *state_vtv(const p2_ctx *c);
+const double *state_hth(const p2_ctx *c);
 // U_k = Q_k H rows of subjects k0 .. k1-1 into a device FP32 buffer (p2_kernels.cu)
 cudaError_t launch_get_u(p2_ctx *c, int64_t k0, int64_t k1, int64_t r0, float *U);
 // Gram of Z_k = X_k V for a batch of new subjects (p2_kernels.cu)

@@ -262,6 +262,17 @@ cudaError_t nnls_configure(int cap) {
     return e;
 }
 
+// Rows of any FP32 right-hand sides against A = Xa * Xb (device R x R FP64).
+cudaError_t launch_nnls_rows(const p2_ctx *c, const double *Xa, const double *Xb,
+                             const float *rows, int64_t n, uint32_t *passive, float *out,
+                             cudaStream_t s) {
+    return launch_nnls<float, float>(c, Xa, Xb, rows, n, passive, out, s);
+}
+
+// The model's V^TV and H^TH (the Gram-Hadamard product of the W update).
+const double *state_vtv(const p2_ctx *c) { return state_member(c, offsetof(SmallState, VtV)); }
+const double *state_hth(const p2_ctx *c) { return state_member(c, offsetof(SmallState, HtH)); }
+
 // W rows: x = NNLS(V^TV * H^TH, M3(k,:)), written over the unconstrained W.
 cudaError_t launch_nnls_w(p2_ctx *c) {
     return launch_nnls<float, float>(c, state_member(c, offsetof(SmallState, VtV)),

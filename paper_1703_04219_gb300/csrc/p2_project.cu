@@ -30,6 +30,8 @@ struct p2_projector {
     // per subject
     p2::dw *d_G = nullptr;
     float *d_S = nullptr, *d_T = nullptr;
+    float *d_M3 = nullptr;              // non-negative models: the subjects' mode-3 rows
+    uint32_t *d_pass = nullptr;         // non-negative models: NNLS passive sets
     p2::SmallState *d_st = nullptr;     // private copy of H64, G3inv; flags
     int pending_flags_check = 0;
 };
@@ -85,11 +87,13 @@ __global__ void k_proj_subjects(const int64_t *__restrict__ sp, const int64_t *_
 }
 
 // s <- coldot(H, T G) (V^TV * H^TH)^+ for every subject; one warp per subject.
+// M3 (nullable) receives the rows coldot(H, T G) (the non-negative variant
+// solves s from them afterwards).
 __global__ void __launch_bounds__(256) k_proj_update(const float *__restrict__ T,
                                                      const dw *__restrict__ G,
                                                      const float *__restrict__ H,
                                                      const SmallState *__restrict__ st, float *S,
-                                                     int64_t K, int R) {
+                                                     float *M3, int64_t K, int R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = R * (R + 1) / 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -128,6 +132,7 @@ __global__ void __launch_bounds__(256) k_proj_update(const float *__restrict__ T
             float m = 0.f;
             for (int r = 0; r < R; ++r) m += Pr[r * R + c];
             m3[c] = m;
+            if (M3) M3[(size_t)k * R + c] = m;
         }
         __syncwarp();
         for (int c = lane; c < R; c += 32) {
@@ -187,6 +192,8 @@ void proj_free(p2_projector *pj) {
     cudaFree(pj->X.val);
     cudaFree(pj->d_G);
     cudaFree(pj->d_S);
+    cudaFree(pj->d_M3);
+    cudaFree(pj->d_pass);
     cudaFree(pj->d_T);
     cudaFree(pj->d_st);
 }
@@ -229,6 +236,8 @@ int p2_projector_create(p2_ctx *model, int64_t max_subjects, int64_t max_rows, i
     if (e == cudaSuccess) e = palloc(&pj->X.val, max_nnz);
     if (e == cudaSuccess) e = palloc(&pj->d_G, (size_t)max_subjects * P);
     if (e == cudaSuccess) e = palloc(&pj->d_S, (size_t)max_subjects * R);
+    if (e == cudaSuccess && model->opt.nonneg) e = palloc(&pj->d_M3, (size_t)max_subjects * R);
+    if (e == cudaSuccess && model->opt.nonneg) e = palloc(&pj->d_pass, (size_t)max_subjects);
     if (e == cudaSuccess) e = palloc(&pj->d_T, (size_t)max_subjects * R * R);
     if (e == cudaSuccess) e = palloc(&pj->d_st, 1);
     if (e == cudaSuccess) e = cudaMemsetAsync(pj->d_st, 0, sizeof(SmallState), pj->stream);
@@ -331,14 +340,20 @@ int p2_project(p2_projector *pj, int64_t n_req, const int64_t *subj_ptr, const i
     pj->X.nnz = nnz;
     XView xv{pj->X.subj_row, pj->X.subj_nnz, pj->X.row_len, pj->X.col, pj->X.val, n_req};
     P2_CUDA_TRY(launch_gram(m, xv, pj->d_st, pj->d_G, s));
+    if (m->opt.nonneg)
+        P2_CUDA_TRY(cudaMemsetAsync(pj->d_pass, 0, sizeof(uint32_t) * (size_t)n_req, s));
     int uw = 8;
     while (uw > 1 && (size_t)R * R * 12 + uw * (size_t)(3 * R * R + R) * 4 > (size_t)m->geo.smem_optin) --uw;
     const size_t upd_smem = (size_t)R * R * 12 + uw * (size_t)(3 * R * R + R) * 4;
     const int ub = (int)((n_req + uw - 1) / uw < 16 * (int64_t)nsm ? (n_req + uw - 1) / uw : 16 * (int64_t)nsm);
     for (int it = 0; it < n_iter; ++it) {
         P2_CUDA_TRY(launch_polar_on(m, pj->d_G, pj->d_S, pj->d_st, pj->d_T, n_req, s));
-        k_proj_update<<<ub, uw * 32, upd_smem, s>>>(pj->d_T, pj->d_G, m->d_H, pj->d_st, pj->d_S, n_req, R);
+        k_proj_update<<<ub, uw * 32, upd_smem, s>>>(pj->d_T, pj->d_G, m->d_H, pj->d_st, pj->d_S,
+                                                    pj->d_M3, n_req, R);
         P2_CUDA_TRY(cudaGetLastError());
+        if (m->opt.nonneg)          // the model's S_k are non-negative: s by NNLS (Section 5.1)
+            P2_CUDA_TRY(launch_nnls_rows(m, state_vtv(m), state_hth(m), pj->d_M3, n_req,
+                                         pj->d_pass, pj->d_S, s));
     }
     if (T_out) P2_CUDA_TRY(launch_polar_on(m, pj->d_G, pj->d_S, pj->d_st, pj->d_T, n_req, s));
     P2_CUDA_TRY(cudaMemcpyAsync(S_out, pj->d_S, sizeof(float) * (size_t)n_req * R, kout, s));

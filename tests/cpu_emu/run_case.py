@@ -51,11 +51,11 @@ def iterate_case(name, K, R, precision="fp32"):
     return err
 
 
-def project_case(R, n_req):
+def project_case(R, n_req, nonneg=False):
     from dataclasses import replace
     X = synth.generate("c63m", K=30)
     H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=31)
-    with p2.Parafac2(R, use_graph=False) as m:
+    with p2.Parafac2(R, use_graph=False, nonneg=nonneg) as m:
         m.load(X)
         m.init(H0, V0, W0)
         m.iterate(1)
@@ -67,7 +67,8 @@ def project_case(R, n_req):
     errs = []
     for k in range(req.K):
         Xc, cols = P.subject_block(req, k)
-        s, _ = P.project_subject(Xc, cols, H.astype(np.float64), V.astype(np.float64), 2)
+        s, _ = P.project_subject(Xc, cols, H.astype(np.float64), V.astype(np.float64), 2,
+                                 nonneg=nonneg)
         errs.append(rel_fro(S[k], s))
     return {"S_max": float(max(errs))}
 
@@ -125,5 +126,6 @@ if __name__ == "__main__":
     elif kind == "getu":
         out = getu_case(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]))
     else:
-        out = project_case(int(sys.argv[2]), int(sys.argv[3]))
+        out = project_case(int(sys.argv[2]), int(sys.argv[3]),
+                           len(sys.argv) > 4 and sys.argv[4] == "nonneg")
     print(json.dumps({k: float(v) for k, v in out.items()}), flush=True)

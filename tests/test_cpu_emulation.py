@@ -27,6 +27,7 @@ CASES = {
     "iterate_r5_bf16": ["iterate", "tiny", "24", "5", "bf16"],
     "iterate_r5_nonneg": ["iterate", "tiny", "24", "5", "nonneg"],
     "project_r12": ["project", "12", "3"],
+    "project_r8_nonneg": ["project", "8", "3", "nonneg"],
     "getu_r5": ["getu", "5", "3", "17"],
     "seed_r4": ["seed", "4", "987654321"],
 }
@@ -87,8 +88,9 @@ def test_emulated_bf16_storage_is_in_bounds_and_within_3e3(emulated_runs):
     assert err["fit"] < 1e-4
 
 
-def test_emulated_projection_is_in_bounds_and_matches_oracle(emulated_runs):
-    err = _result(emulated_runs, "project_r12")
+@pytest.mark.parametrize("name", ["project_r12", "project_r8_nonneg"])
+def test_emulated_projection_is_in_bounds_and_matches_oracle(emulated_runs, name):
+    err = _result(emulated_runs, name)
     assert err["S_max"] < 1e-4
 
 

@@ -147,3 +147,33 @@ def test_server_continuous_batching_matches_direct_projection(p2):
     assert stats["batches"] >= 3 and stats["p99_ms"] >= stats["p50_ms"] > 0
     for k, s in res.items():
         assert np.array_equal(s, S[k]), k
+
+
+def test_projection_onto_nonneg_model(p2):
+    """A model trained in the non-negative variant (Section 5.1) projects new
+    subjects with s >= 0 solved by NNLS; one step from s = 1 against the
+    oracle for the well-conditioned subjects, as the other tests."""
+    R = 10
+    X = synth.generate("c63m", K=400)
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=31)
+    with p2.Parafac2(R, nonneg=True) as m:
+        m.load(X)
+        m.init(H0, V0, W0)
+        m.iterate(3)
+        H, V, _ = m.factors()
+        req = _requests(200)
+        with p2.Projector(m, 256, 20_000, 200_000) as pj:
+            S = pj.project(req, n_iter=1)
+    assert np.all(S >= 0)
+    H64, V64 = H.astype(np.float64), V.astype(np.float64)
+    good = 0
+    for k in range(req.K):
+        Xc, cols = P.subject_block(req, k)
+        s, _ = P.project_subject(Xc, cols, H64, V64, 1, nonneg=True)
+        A = Xc @ V64[cols] @ H64.T
+        sv = np.linalg.svd(A, compute_uv=False)
+        sv = sv[sv > 1e-5 * sv[0]]
+        if sv.size and sv[0] / sv[-1] < 100:
+            assert rel_fro(S[k], s) < 1e-4, (k, rel_fro(S[k], s))
+            good += 1
+    assert good >= 5

@@ -84,6 +84,7 @@ static void free_data(p2_ctx *c) {
     dfree(c, &c->d_M3, K * R);
     dfree(c, &c->d_qrcnt, K);
     dfree(c, &c->d_passW, K);
+    dfree(c, &c->d_sorder, K);
     dfree(c, &c->d_passV, J);
     dfree(c, &c->d_order, K);
     dfree(c, &c->d_rank, K);
@@ -143,6 +144,7 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
     P2_TRY(dalloc(c, &c->d_binoff,
                   (size_t)((K + P2_ORDER_CHUNK - 1) / P2_ORDER_CHUNK) * P2_ORDER_BINS));
     P2_CUDA_TRY(cudaMemsetAsync(c->d_qrcnt, 0, sizeof(int32_t) * (size_t)K, c->stream));
+    P2_TRY(dalloc(c, &c->d_sorder, (size_t)K));
     if (c->opt.nonneg) {
         P2_TRY(dalloc(c, &c->d_passW, (size_t)K));
         P2_TRY(dalloc(c, &c->d_passV, (size_t)J));
@@ -387,6 +389,13 @@ int p2_load_slices(p2_ctx *c, int64_t K, int32_t J, const int64_t *subj_ptr,
         }
     }
     if (rc == P2_OK) rc = launch_load(c, d_subj, d_row_ptr, d_col, c->X.val, K, J, N, nnz);
+    if (rc == P2_OK) {
+        const cudaError_t e = launch_subject_bins(c);
+        if (e != cudaSuccess) {
+            set_error("p2_load_slices: subject bins failed: %s", cudaGetErrorString(e));
+            rc = P2_ECUDA;
+        }
+    }
     cudaStreamSynchronize(s);
     dfree(c, &d_subj, (size_t)K + 1);
     dfree(c, &d_row_ptr, (size_t)N + 1);

@@ -101,6 +101,9 @@ struct XView {
     const uint16_t *__restrict__ col;
     const float *__restrict__ val;
     int64_t K;
+    // processing order of the subjects (position i handles subject order[i]);
+    // NULL: natural order
+    const int32_t *__restrict__ order = nullptr;
 };
 
 // Launch geometry decided once per context.
@@ -153,6 +156,10 @@ struct p2_ctx {
     int32_t *d_order = nullptr;  // [K] subject processed by each Procrustes slot
     int32_t *d_rank = nullptr;   // [K] rank within the subject's bin and chunk
     int32_t *d_binoff = nullptr; // [nchunk x 256] bin counts, then offsets
+    // subject bins: the sparse passes take the subjects in decreasing order of
+    // their non-zero count (built at load), so every warp of the persistent
+    // grid receives an even mix of large and small subjects
+    int32_t *d_sorder = nullptr; // [K]
     // non-negative variant: each row's passive set (bit j: x_j > 0) of the last solve
     uint32_t *d_passW = nullptr; // [K]
     uint32_t *d_passV = nullptr; // [J]
@@ -199,6 +206,12 @@ int configure_kernels(p2_ctx *c);    // smem attributes etc.
 // Procrustes step (p2_polar.cu)
 int polar_configure(p2_ctx *c);
 cudaError_t launch_polar(p2_ctx *c);
+// subjects in decreasing order of key (chunked counting sort into 256 bins,
+// keys clamped to [0, 255]); rank and binoff are scratch of the Q-step order's sizes
+cudaError_t launch_order_desc(const int32_t *key, int64_t K, int32_t *rank, int32_t *binoff,
+                              int32_t *order, cudaStream_t s);
+// subject bins by non-zero count into c->d_sorder (load time)
+cudaError_t launch_subject_bins(p2_ctx *c);
 cudaError_t launch_polar_on(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
                             float *T, int64_t K, cudaStream_t s, const int32_t *order = nullptr,
                             int32_t *qrcnt = nullptr);

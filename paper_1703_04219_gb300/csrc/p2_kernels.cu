@@ -43,7 +43,11 @@ static __device__ __forceinline__ int warp_excl_scan(int v, int lane) {
 }
 
 static XView xview(const p2_ctx *c) {
-    return XView{c->X.subj_row, c->X.subj_nnz, c->X.row_len, c->X.col, c->X.val, c->X.K};
+    // subject bins pay above R = 16, where a subject's work is large enough
+    // for the tail of the persistent grid to matter (R = 40: alpha pass -3%);
+    // at R = 10 the natural order's sequential walk over X is worth more (+1.5%)
+    return XView{c->X.subj_row, c->X.subj_nnz, c->X.row_len, c->X.col, c->X.val, c->X.K,
+                 c->R > 16 ? c->d_sorder : nullptr};
 }
 
 // a + b = s + e exactly (Knuth's TwoSum)
@@ -231,7 +235,8 @@ __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 3) k_alpha(XView X, const 
     __syncthreads();
 
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; k < X.K; k += nwarps) {
+    for (int64_t ki = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; ki < X.K; ki += nwarps) {
+        const int64_t k = X.order ? (int64_t)X.order[ki] : ki;
         const int64_t r0 = X.subj_row[k], r1 = X.subj_row[k + 1];
         int64_t base = X.subj_nnz[k];
         for (int p = lane; p < P; p += 32) {
@@ -409,7 +414,8 @@ __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 4) k_beta_p(XView X, const
     for (int i = threadIdx.x; i < R * R; i += blockDim.x) Hs[i] = H[i];
     __syncthreads();
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; k < X.K; k += nwarps) {
+    for (int64_t ki = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; ki < X.K; ki += nwarps) {
+        const int64_t k = X.order ? (int64_t)X.order[ki] : ki;
         const int64_t r0 = X.subj_row[k], r1 = X.subj_row[k + 1];
         if (r1 == r0) continue;
         int64_t base = X.subj_nnz[k];
@@ -1255,6 +1261,7 @@ static void launch_get_u_t(p2_ctx *c, const Launch &L, int64_t k0, int64_t k1, i
     X.subj_row += k0;
     X.subj_nnz += k0;
     X.K = k1 - k0;
+    X.order = nullptr;
     const S *V = Bufs<S>::V(c);
     const float *T = c->d_T + (size_t)k0 * c->R * c->R;
     const int64_t want = (k1 - k0 + L.beta_warps - 1) / L.beta_warps;

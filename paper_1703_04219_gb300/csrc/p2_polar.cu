@@ -18,6 +18,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "p2_internal.cuh"
 #include "p2_eig_dw.cuh"
 #include "p2_polar.cuh"
@@ -299,17 +301,46 @@ cudaError_t launch_polar_on(const p2_ctx *c, const dw *G, const float *W, SmallS
     return cudaGetLastError();
 }
 
+cudaError_t launch_order_desc(const int32_t *key, int64_t K, int32_t *rank, int32_t *binoff,
+                              int32_t *order, cudaStream_t s) {
+    if (K <= 0) return cudaSuccess;
+    const int nchunk = (int)((K + P2_ORDER_CHUNK - 1) / P2_ORDER_CHUNK);
+    k_order_count<<<nchunk, 256, 0, s>>>(key, K, rank, binoff);
+    k_order_scan<<<1, P2_ORDER_BINS, 0, s>>>(binoff, nchunk);
+    k_order_place<<<nchunk, 256, 0, s>>>(key, rank, binoff, K, order);
+    return cudaGetLastError();
+}
+
+// key of a subject's bin: its non-zero count in steps of four, clamped
+__global__ void k_subject_key(const int64_t *__restrict__ subj_nnz, int64_t K, int32_t *key) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = subj_nnz[k + 1] - subj_nnz[k];
+        key[k] = (int32_t)((n >> 2) < P2_ORDER_BINS - 1 ? (n >> 2) : P2_ORDER_BINS - 1);
+    }
+}
+
+cudaError_t launch_subject_bins(p2_ctx *c) {
+    const int64_t K = c->X.K;
+    if (K <= 0) return cudaSuccess;
+    // the rotation counts are not in use yet (zero until the first Q-step):
+    // their buffer holds the keys, and is cleared again afterwards
+    k_subject_key<<<(int)std::min<int64_t>((K + 255) / 256, 4096), 256, 0, c->stream>>>(
+        c->X.subj_nnz, K, c->d_qrcnt);
+    cudaError_t e = launch_order_desc(c->d_qrcnt, K, c->d_rank, c->d_binoff, c->d_sorder,
+                                      c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->d_qrcnt, 0, sizeof(int32_t) * (size_t)K, c->stream);
+    return e;
+}
+
 // The Q-step of the iteration: order the subjects by their last rotation
 // counts, then the Procrustes kernel (POLAR_LAUNCHES kernels in all).
 cudaError_t launch_polar(p2_ctx *c) {
     const int64_t K = c->X.K;
     if (K <= 0) return cudaSuccess;
-    const int nchunk = (int)((K + P2_ORDER_CHUNK - 1) / P2_ORDER_CHUNK);
-    k_order_count<<<nchunk, 256, 0, c->stream>>>(c->d_qrcnt, K, c->d_rank, c->d_binoff);
-    k_order_scan<<<1, P2_ORDER_BINS, 0, c->stream>>>(c->d_binoff, nchunk);
-    k_order_place<<<nchunk, 256, 0, c->stream>>>(c->d_qrcnt, c->d_rank, c->d_binoff, K,
-                                                  c->d_order);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_order_desc(c->d_qrcnt, K, c->d_rank, c->d_binoff, c->d_order,
+                                      c->stream);
     if (e != cudaSuccess) return e;
     return launch_polar_on(c, c->d_G, c->d_W, c->d_s, c->d_T, K, c->stream, c->d_order,
                            c->d_qrcnt);

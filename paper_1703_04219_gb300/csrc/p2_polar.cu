@@ -78,43 +78,37 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
         const float wsc = f_pow2(127 - ew), gsc = f_pow2(sg);
 #pragma unroll
         for (int i = 0; i < R; ++i) w[i] = f_mul(w[i], wsc);
-        // g = S' G' S' in the strict upper triangle of A (g(i, j), i > j, at
-        // A(j, i)) and in d (g(i, i)); M' then fills the lower triangle.
-#pragma unroll
-        for (int i = 0, p = 0; i < R; ++i)
-#pragma unroll
-            for (int j = 0; j <= i; ++j, ++p) {
-                const dw g = dw_mul(dw_scale(Gk[p], gsc), two_prod(w[i], w[j]));
-                if (j == i)
-                    d[i] = g;
-                else
-                    A(j, i) = g;
-            }
+        // g = S' G' S' held in registers (packed lower); M' column by column
+        // into the lower triangle of A
         int em = 0;
-#pragma unroll 1
-        for (int c = 0; c < R; ++c) {
-            dw tv[R];
-            {
-                dwacc s[R];
+        {
+            dw g[P];
 #pragma unroll
-                for (int i = 0; i < R; ++i) s[i] = acc_zero();
-#pragma unroll 1
-                for (int j = 0; j < R; ++j) {
-                    const float hj = Hs[c * R + j];
+            for (int i = 0, p = 0; i < R; ++i)
 #pragma unroll
-                    for (int i = 0; i < R; ++i)
-                        acc_fmaf(s[i], (i == j) ? d[i] : (j > i ? A(i, j) : A(j, i)), hj);
+                for (int j = 0; j <= i; ++j, ++p)
+                    g[p] = dw_mul(dw_scale(Gk[p], gsc), two_prod(w[i], w[j]));
+#pragma unroll 1
+            for (int c = 0; c < R; ++c) {
+                float hc[R];
+#pragma unroll
+                for (int j = 0; j < R; ++j) hc[j] = Hs[c * R + j];
+                dw tv[R];
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    dwacc s = acc_zero();
+#pragma unroll
+                    for (int j = 0; j < R; ++j) acc_fmaf(s, g[pk<R>(i, j)], hc[j]);
+                    tv[i] = acc_val(s);
                 }
+                for (int r = c; r < R; ++r) {
+                    dwacc s = acc_zero();
 #pragma unroll
-                for (int i = 0; i < R; ++i) tv[i] = acc_val(s[i]);
-            }
-            for (int r = c; r < R; ++r) {
-                dwacc s = acc_zero();
-#pragma unroll
-                for (int i = 0; i < R; ++i) acc_fmaf(s, tv[i], Hs[r * R + i]);
-                const dw m = acc_val(s);
-                A(r, c) = m;
-                if (r == c) em = max(em, f_expo(m.h));
+                    for (int i = 0; i < R; ++i) acc_fmaf(s, tv[i], Hs[r * R + i]);
+                    const dw m = acc_val(s);
+                    A(r, c) = m;
+                    if (r == c) em = max(em, f_expo(m.h));
+                }
             }
         }
         if (eg == 0 || ew == 0 || em == 0) {
@@ -145,33 +139,71 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
 #pragma unroll
                 for (int r = 0; r < R; ++r) A(r, i) = dw_mul(A(r, i), sf);
             }
-#pragma unroll
-            for (int i = 0; i < R; ++i) e[i] = dw_f(w[i]);    // w' where the T loop can index it
             const int so = (sm + sg) / 2;
             const float o1 = f_pow2(so / 2), o2 = f_pow2(so - so / 2);
+            if constexpr (R <= 10) {
+                // C = Z' Z'^T (packed lower, in registers) by rank-one updates,
+                // one column of Z' at a time, then T = C H' S'
+                dwacc C[P];
+#pragma unroll
+                for (int p = 0; p < P; ++p) C[p] = acc_zero();
 #pragma unroll 1
-            for (int c = 0; c < R; ++c) {
-                dw y[R];                                 // y = Z'^T h'_c
-                {
-                    dwacc s[R];
+                for (int i = 0; i < R; ++i) {
+                    dw a[R];
 #pragma unroll
-                    for (int i = 0; i < R; ++i) s[i] = acc_zero();
-#pragma unroll 1
-                    for (int r = 0; r < R; ++r) {
-                        const float hr = Hs[r * R + c];
+                    for (int r = 0; r < R; ++r) a[r] = A(r, i);
 #pragma unroll
-                        for (int i = 0; i < R; ++i) acc_fmaf(s[i], A(r, i), hr);
-                    }
+                    for (int r = 0, p = 0; r < R; ++r)
 #pragma unroll
-                    for (int i = 0; i < R; ++i) y[i] = acc_val(s[i]);
+                        for (int c = 0; c <= r; ++c, ++p) acc_fma(C[p], a[r], a[c]);
                 }
-#pragma unroll 1
-                for (int r = 0; r < R; ++r) {             // T(r, c) = (Z' y)_r w'_c
-                    dwacc s = acc_zero();
+                dw Cv[P];
 #pragma unroll
-                    for (int i = 0; i < R; ++i) acc_fma(s, A(r, i), y[i]);
-                    const dw v = dw_mulf(acc_val(s), e[c].h);
-                    T[tb + r * R + c] = f_mul(f_mul(v.h, o1), o2);
+                for (int p = 0; p < P; ++p) Cv[p] = acc_val(C[p]);
+#pragma unroll 1
+                for (int c = 0; c < R; ++c) {
+                    float hc[R];
+#pragma unroll
+                    for (int u = 0; u < R; ++u) hc[u] = Hs[u * R + c];
+                    float wc = 0.f;
+#pragma unroll
+                    for (int u = 0; u < R; ++u) wc = (u == c) ? w[u] : wc;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {             // T(r, c) = (C h'_c)_r w'_c
+                        dwacc t = acc_zero();
+#pragma unroll
+                        for (int u = 0; u < R; ++u) acc_fmaf(t, Cv[pk<R>(r, u)], hc[u]);
+                        const dw v = dw_mulf(acc_val(t), wc);
+                        T[tb + r * R + c] = f_mul(f_mul(v.h, o1), o2);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < R; ++i) e[i] = dw_f(w[i]);    // w' where the T loop can index it
+#pragma unroll 1
+                for (int c = 0; c < R; ++c) {
+                    dw y[R];                                 // y = Z'^T h'_c
+                    {
+                        dwacc s[R];
+#pragma unroll
+                        for (int i = 0; i < R; ++i) s[i] = acc_zero();
+#pragma unroll 1
+                        for (int r = 0; r < R; ++r) {
+                            const float hr = Hs[r * R + c];
+#pragma unroll
+                            for (int i = 0; i < R; ++i) acc_fmaf(s[i], A(r, i), hr);
+                        }
+#pragma unroll
+                        for (int i = 0; i < R; ++i) y[i] = acc_val(s[i]);
+                    }
+#pragma unroll 1
+                    for (int r = 0; r < R; ++r) {             // T(r, c) = (Z' y)_r w'_c
+                        dwacc s = acc_zero();
+#pragma unroll
+                        for (int i = 0; i < R; ++i) acc_fma(s, A(r, i), y[i]);
+                        const dw v = dw_mulf(acc_val(s), e[c].h);
+                        T[tb + r * R + c] = f_mul(f_mul(v.h, o1), o2);
+                    }
                 }
             }
             flops = polar_fixed_flops(R) + qr_flops(R, steps, rot);

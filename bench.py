@@ -302,7 +302,7 @@ def run_p2(args, w):
         flops = t["flops"]
         ach = flops / (phase_ms[dom] / 1e3) / 1e12
         kname = ("k_polar_reg (double-word Procrustes, one lane per subject)" if R <= 12 else
-                 "k_polar_grp (double-word Procrustes, eight lanes per subject)")
+                 "k_polar_grp (double-word Procrustes, a group of 8 or 16 lanes per subject)")
         roof = {"kernel": kname, "bound": "alu",
                 "achieved": ach, "peak": DW_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / DW_PEAK_TFLOPS,

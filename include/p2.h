@@ -131,6 +131,28 @@ int p2_load_slices(p2_ctx *ctx, int64_t K, int32_t J, const int64_t *subj_ptr,
 int p2_init(p2_ctx *ctx, const float *H0, const float *V0, const float *W0);
 
 /*
+ * Deterministic alternative to p2_init, the rational start of Kiers, ten
+ * Berge and Bro (J. Chemometrics 13, 1999): H = I, S_k = I (W = 1) and V =
+ * the R leading eigenvectors of sum_k X_k^T X_k, in decreasing order of
+ * eigenvalue, each column's entry of largest magnitude positive; then the
+ * first Q-step, as p2_init.  The eigenvectors come from subspace iteration
+ * with a Rayleigh-Ritz step per product on a block of b = min(J, 64,
+ * max(2R, R + 8)) columns, so they converge at the rate lambda_{b+1} /
+ * lambda_R; the products X^T (X V) run in FP64 without the J x J matrix.
+ * The block starts uniform in [0, 1) from opt.seed.  The loop stops when the
+ * sum of the squared sines of the principal angles between two successive
+ * leading R-dimensional subspaces is at most tol^2, or after max_iter
+ * products; a final Rayleigh-Ritz step gives V.  Columns for the null space
+ * of sum_k X_k^T X_k, when its rank is below R, are an orthonormal
+ * completion.  V is then stored in the context's precision.  Transient
+ * device scratch: 4 J b doubles and (N + S) min(b, 2^29 / N) doubles (N
+ * stacked rows, S column segments of the mode-2 layout).  n_done (nullable, host) receives the iterations run.  Synchronises
+ * after every product.  P2_EINVAL for J < R, max_iter < 1 or tol < 0;
+ * P2_ENUMERIC if an eigen step failed to converge.
+ */
+int p2_init_eig(p2_ctx *ctx, int32_t max_iter, double tol, int32_t *n_done);
+
+/*
  * Run n_iter >= 0 iterations of PARAFAC2-ALS (Algorithm 2 loop body: Q-step,
  * one CP-ALS sweep on Y with Algorithm 3's MTTKRPs, S_k = diag(W(k,:))).
  * fit_out (nullable, host): fit after the last iteration, as p2_fit.  With

@@ -291,6 +291,27 @@ def project_subject(Xc, cols, H, V, n_iter, rank_rtol=RANK_RTOL, s0=None, nonneg
     return s, procrustes_q(Xc, cols, H, V, s, rank_rtol)
 
 
+# --------------------------------------------------------------------------
+# rational start (the paper leaves Algorithm 2's "Initialize H, V, {S_k}"
+# open; reading: Kiers, ten Berge & Bro 1999's start H = I, S_k = I and V
+# the R leading eigenvectors of sum_k X_k^T X_k)
+# --------------------------------------------------------------------------
+def rational_start(blocks, K, J, R):
+    """H = I, W = 1 (S_k = I), V = the R leading eigenvectors of sum_k X_k^T X_k,
+    in decreasing order of eigenvalue, each column's entry of largest magnitude
+    positive (lowest row on ties).  The J x J matrix is formed densely."""
+    G = np.zeros((J, J))
+    for Xc, cols in blocks:
+        G[np.ix_(cols, cols)] += Xc.T @ Xc
+    lam, U = np.linalg.eigh(G)
+    V = U[:, ::-1][:, :R].copy()
+    for r in range(R):
+        j = int(np.argmax(np.abs(V[:, r])))
+        if V[j, r] < 0:
+            V[:, r] = -V[:, r]
+    return np.eye(R), V, np.ones((K, R)), lam[::-1]
+
+
 def assemble_u(Qs, H):
     """U_k = Q_k H (Algorithm 2, after the loop)."""
     return [Q @ H for Q in Qs]

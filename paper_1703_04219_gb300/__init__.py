@@ -24,6 +24,7 @@ _NAMES = {0: "P2_OK", 1: "P2_EINVAL", 2: "P2_ENOMEM", 3: "P2_ECUDA", 4: "P2_ENUM
 
 # every symbol include/p2.h declares
 EXPORTED = ("p2_default_options", "p2_create", "p2_destroy", "p2_load_slices", "p2_init",
+            "p2_init_eig",
             "p2_iterate", "p2_fit", "p2_get_factors", "p2_set_factors", "p2_get_mttkrp",
             "p2_get_procrustes", "p2_get_U", "p2_iterate_until", "p2_stats", "p2_device_bytes", "p2_mode1_stats_noalloc",
             "p2_projector_create", "p2_projector_destroy", "p2_project", "p2_projector_sync",
@@ -65,6 +66,7 @@ def _load():
         "p2_destroy": ([vp], ctypes.c_int),
         "p2_load_slices": ([vp, i64, i32, vp, vp, vp, vp, i32], ctypes.c_int),
         "p2_init": ([vp, vp, vp, vp], ctypes.c_int),
+        "p2_init_eig": ([vp, i32, ctypes.c_double, ctypes.POINTER(i32)], ctypes.c_int),
         "p2_iterate": ([vp, i32, ctypes.POINTER(dbl)], ctypes.c_int),
         "p2_fit": ([vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)], ctypes.c_int),
         "p2_get_factors": ([vp, vp, vp, vp], ctypes.c_int),
@@ -150,6 +152,14 @@ def p2_init(ctx, H0=None, V0=None, W0=None):
         return
     H0, V0, W0 = (np.ascontiguousarray(a, np.float32) for a in (H0, V0, W0))
     _check(lib.p2_init(ctx, _ptr(H0), _ptr(V0), _ptr(W0)), "p2_init")
+
+
+def p2_init_eig(ctx, max_iter: int = 500, tol: float = 1e-6) -> int:
+    """Rational start (H = I, W = 1, V = leading eigenvectors of sum_k X_k^T X_k);
+    returns the number of subspace-iteration products run."""
+    n = ctypes.c_int32(0)
+    _check(lib.p2_init_eig(ctx, int(max_iter), float(tol), ctypes.byref(n)), "p2_init_eig")
+    return int(n.value)
 
 
 def p2_set_factors(ctx, H, V, W):
@@ -331,6 +341,10 @@ class Parafac2:
 
     def init(self, H0=None, V0=None, W0=None):
         p2_init(self.ctx, H0, V0, W0)
+
+    def init_eig(self, max_iter: int = 500, tol: float = 1e-6) -> int:
+        """Deterministic rational start; returns the subspace-iteration products run."""
+        return p2_init_eig(self.ctx, max_iter, tol)
 
     def set_factors(self, H, V, W):
         p2_set_factors(self.ctx, H, V, W)

@@ -6,6 +6,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <utility>
 #include <vector>
 #include <math.h>
 
@@ -195,6 +197,17 @@ static float from_bf16_bits(uint16_t h) {
     return f;
 }
 
+// Statistics of the factors now on the device and the first Q-step.
+static int finish_init(p2_ctx *c) {
+    P2_TRY(enqueue_factor_stats(c));
+    P2_TRY(enqueue_prologue(c));
+    int flags = 0;
+    P2_TRY(read_flags(c, &flags));
+    c->inited = true;
+    c->iters_done = 0;
+    return P2_OK;
+}
+
 static int set_factors_impl(p2_ctx *c, const float *H, const float *V, const float *W) {
     const int R = c->R;
     const int32_t J = c->X.J;
@@ -219,13 +232,7 @@ static int set_factors_impl(p2_ctx *c, const float *H, const float *V, const flo
                                 c->stream));
     int zero = 0;
     P2_CUDA_TRY(cudaMemcpyAsync(&c->d_s->flags, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    P2_TRY(enqueue_factor_stats(c));
-    P2_TRY(enqueue_prologue(c));
-    int flags = 0;
-    P2_TRY(read_flags(c, &flags));   // also keeps Vp and Vb alive until the copies finished
-    c->inited = true;
-    c->iters_done = 0;
-    return P2_OK;
+    return finish_init(c);   // its flag read-back also keeps Vp and Vb alive until the copies finished
 }
 
 }  // namespace p2
@@ -438,6 +445,81 @@ int p2_init(p2_ctx *c, const float *H0, const float *V0, const float *W0) {
     }
     if (!H0 || !V0 || !W0) return fail(P2_EINVAL, "p2_init: some but not all factors NULL");
     return set_factors_impl(c, H0, V0, W0);
+}
+
+// Device scratch of p2_init_eig, freed on every return path.
+struct EigScratch {
+    double *v = nullptr, *vn = nullptr, *y = nullptr, *w = nullptr, *z = nullptr, *seg = nullptr,
+           *dist = nullptr;
+    ~EigScratch() {
+        cudaFree(seg);
+        cudaFree(v);
+        cudaFree(vn);
+        cudaFree(y);
+        cudaFree(w);
+        cudaFree(z);
+        cudaFree(dist);
+    }
+};
+
+int p2_init_eig(p2_ctx *c, int32_t max_iter, double tol, int32_t *n_done) {
+    P2_TRY(check_ready(c, false));
+    if (max_iter < 1) return fail(P2_EINVAL, "p2_init_eig: max_iter < 1");
+    if (!(tol >= 0.0)) return fail(P2_EINVAL, "p2_init_eig: tol must be >= 0");
+    const int R = c->R;
+    const int32_t J = c->X.J;
+    if (J < R) return fail(P2_EINVAL, "p2_init_eig: J < R (fewer columns than components)");
+    P2_CUDA_TRY(cudaSetDevice(c->opt.device));
+    // block width: oversampled so that the leading R Ritz vectors converge at
+    // lambda_{b+1} / lambda_R; at most the CTA eigen-solver's size and J
+    const int b = std::min(std::min(std::max(2 * R, R + 8), (int)P2_RMAX), (int)J);
+    // product columns per pass: the N x CW FP64 scratch held to 4 GiB
+    const size_t N = c->X.N > 0 ? (size_t)c->X.N : 1;
+    const int CW = (int)std::min<size_t>((size_t)b, std::max<size_t>(1, ((size_t)4 << 30) / (8 * N)));
+    const size_t Jb = (size_t)J * b;
+    EigScratch s;
+    P2_CUDA_TRY(cudaMalloc(&s.v, Jb * sizeof(double)));
+    P2_CUDA_TRY(cudaMalloc(&s.vn, Jb * sizeof(double)));
+    P2_CUDA_TRY(cudaMalloc(&s.y, Jb * sizeof(double)));
+    P2_CUDA_TRY(cudaMalloc(&s.w, Jb * sizeof(double)));
+    P2_CUDA_TRY(cudaMalloc(&s.z, N * CW * sizeof(double)));
+    P2_CUDA_TRY(cudaMalloc(&s.seg, ((size_t)c->X.nseg > 0 ? (size_t)c->X.nseg : 1) * CW * sizeof(double)));
+    P2_CUDA_TRY(cudaMalloc(&s.dist, sizeof(double)));
+    // seeded start block: uniform [0, 1) from the seed's V stream, rows relabelled
+    std::vector<float> V0(Jb);
+    init_uniform(c->opt.seed, 2, Jb, V0.data());
+    std::vector<double> Y0(Jb);
+    for (int32_t j = 0; j < J; ++j)
+        for (int r = 0; r < b; ++r)
+            Y0[(size_t)c->h_perm_old2new[j] * b + r] = (double)V0[(size_t)j * b + r];
+    P2_CUDA_TRY(cudaMemcpyAsync(s.y, Y0.data(), Jb * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    int zero = 0;
+    P2_CUDA_TRY(cudaMemcpyAsync(&c->d_s->flags, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    P2_TRY(enqueue_eig_fill(c));
+    P2_TRY(enqueue_eig_orth(c, s.y, nullptr, s.v, b, nullptr));
+    int32_t it = 0;
+    while (it < max_iter) {
+        P2_TRY(enqueue_eig_product(c, s.v, b, CW, s.z, s.seg, s.y));   // Y = A V
+        P2_TRY(enqueue_eig_ritz(c, s.y, s.v, s.w, b, 0));      // W = Y U
+        P2_TRY(enqueue_eig_orth(c, s.w, s.v, s.vn, b, s.dist));
+        std::swap(s.v, s.vn);
+        ++it;
+        double dist = 0.0;
+        P2_CUDA_TRY(cudaMemcpyAsync(&dist, s.dist, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        P2_CUDA_TRY(cudaStreamSynchronize(c->stream));       // also keeps Y0 alive for its copy
+        if (!(dist == dist)) break;                           // non-finite: reported below
+        if (dist <= tol * tol) break;
+    }
+    P2_TRY(enqueue_eig_product(c, s.v, b, CW, s.z, s.seg, s.y));
+    P2_TRY(enqueue_eig_ritz(c, s.y, s.v, s.w, b, 1));
+    int flags = 0;
+    P2_TRY(read_flags(c, &flags));
+    if (flags & FLAG_EIG_NOCONV) {
+        set_error("p2_init_eig: an eigen step did not converge (flags 0x%x)", flags);
+        return P2_ENUMERIC;
+    }
+    if (n_done) *n_done = it;
+    return finish_init(c);
 }
 
 int p2_set_factors(p2_ctx *c, const float *H, const float *V, const float *W) {

@@ -203,6 +203,21 @@ int enqueue_prologue(p2_ctx *c);     // Q-step + mode-1 MTTKRP for the current (
 int enqueue_iteration(p2_ctx *c);    // one ALS iteration
 int enqueue_factor_stats(p2_ctx *c); // HtH, VtV, WtW for freshly set factors
 int configure_kernels(p2_ctx *c);    // smem attributes etc.
+// rational start (p2_kernels.cu), on FP64 blocks of b columns (J x b,
+// row-major, relabelled rows): H = I and W = 1; Y = X^T (X Vd) with the
+// product's columns taken CW at a time through Z (N x CW FP64 scratch) and
+// seg (nseg x CW FP64 segment partials);
+// orthonormal basis of Y's columns into Q, with the subspace distance of the
+// leading R columns to Vold when given; Rayleigh-Ritz step (Out = Y U, or,
+// final, the sign-fixed Ritz vectors Vd U with the leading R columns stored
+// to the device V)
+int enqueue_eig_fill(p2_ctx *c);
+int enqueue_eig_product(p2_ctx *c, const double *Vd, int b, int CW, double *Z, double *seg,
+                        double *Y);
+int enqueue_eig_orth(p2_ctx *c, const double *Y, const double *Vold, double *Q, int b,
+                     double *dist);
+int enqueue_eig_ritz(p2_ctx *c, const double *Y, const double *Vd, double *Out, int b,
+                     int final_step);
 // Procrustes step (p2_polar.cu)
 int polar_configure(p2_ctx *c);
 cudaError_t launch_polar(p2_ctx *c);

@@ -714,8 +714,10 @@ __global__ void __launch_bounds__(256) k_gram_v(const S *__restrict__ V, double 
 // Symmetric eigen-decomposition of A (n x n, shared memory, row stride n) by
 // parallel cyclic Jacobi (round-robin pairing, n/2 disjoint rotations per
 // round, element-parallel updates).  On return diag(A) holds the eigenvalues
-// and U the eigenvectors (columns).
-static __device__ void cta_jacobi(double *A, double *U, int n, int *flags) {
+// and U the eigenvectors (columns).  A pair is rotated while |a_pq| exceeds
+// eps sqrt(|a_pp a_qq|) and abs_floor (a floor of the order of eps ||A||
+// ends the sweeps on a block of rounding noise, such as a null space).
+static __device__ void cta_jacobi(double *A, double *U, int n, int *flags, double abs_floor = 0.0) {
     __shared__ double cs_c[P2_RMAX / 2], cs_s[P2_RMAX / 2];
     __shared__ int cs_p[P2_RMAX / 2], cs_q[P2_RMAX / 2];
     __shared__ int rotated;
@@ -739,7 +741,7 @@ static __device__ void cta_jacobi(double *A, double *U, int n, int *flags) {
                 if (q < n) {
                     const double apq = A[p * n + q];
                     const double app = A[p * n + p], aqq = A[q * n + q];
-                    if (fabs(apq) > eps * sqrt(fabs(app * aqq)) && fabs(apq) > 1e-300) {
+                    if (fabs(apq) > eps * sqrt(fabs(app * aqq)) && fabs(apq) > fmax(1e-300, abs_floor)) {
                         const double tau = (aqq - app) / (2.0 * apq);
                         const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                         c = 1.0 / sqrt(1.0 + tt * tt);
@@ -811,6 +813,323 @@ static __device__ void cta_pinv(double *A, double *U, double *out, int n, int *f
         out[e] = s;
     }
     __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Rational start (Kiers, ten Berge & Bro, J. Chemometrics 13, 1999): H = I,
+// S_k = I and V = the R leading eigenvectors of A = sum_k X_k^T X_k.  They
+// come from subspace iteration with a Rayleigh-Ritz step on every product
+// (Golub & Van Loan, "Matrix Computations", 4th ed., Section 8.2.4; Stewart,
+// Numer. Math. 25, 1976) over a block of b >= R columns, so the leading R
+// Ritz vectors converge at the rate lambda_{b+1} / lambda_R.  A V is formed
+// as X^T (X V) without the J x J matrix.  One-time work, all in FP64: the
+// eigenvalues of A are often close (adjacent ratios of 0.98 on the synthetic
+// workloads) and an eigenvector's error is the product's relative error
+// times lambda_1 over its gap.
+// ---------------------------------------------------------------------------
+
+// Sum of v over the CTA in a fixed order (lanes by a butterfly, then the
+// warps in order), returned to every thread; red holds one double per warp.
+static __device__ double cta_sum(double v, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLMASK, v, o);
+    __syncthreads();                       // red is free from its previous use
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w];
+    return s;
+}
+
+// Columns c0 .. c0+CW-1 of Z = X Vd in FP64 (stacked rows, N x CW; Vd is
+// J x b): one warp per subject, one lane per row of a 32-row chunk, row
+// offsets from a warp scan of the row lengths.
+__global__ void __launch_bounds__(256) k_eig_z(XView X, const double *__restrict__ Vd, int b,
+                                               int c0, int CW, double *Z) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; k < X.K; k += nwarps) {
+        const int64_t r0 = X.subj_row[k], r1 = X.subj_row[k + 1];
+        int64_t base = X.subj_nnz[k];
+        for (int64_t cr = r0; cr < r1; cr += 32) {
+            const int nr = (int)((r1 - cr) < 32 ? (r1 - cr) : 32);
+            const int len = (lane < nr) ? (int)X.row_len[cr + lane] : 0;
+            const int off = warp_excl_scan(len, lane);
+            const int tot = __shfl_sync(FULLMASK, off + len, 31);
+            if (lane < nr) {
+                const int64_t b0 = base + off;
+                double *zr = Z + (size_t)(cr + lane) * CW;
+                for (int c = 0; c < CW; ++c) {
+                    double a = 0.0;
+                    for (int e = 0; e < len; ++e)
+                        a = fma((double)X.val[b0 + e], Vd[(size_t)X.col[b0 + e] * b + c0 + c], a);
+                    zr[c] = a;
+                }
+            }
+            base += tot;
+        }
+    }
+}
+
+// Segment partials of X^T Z in FP64 (Z: N x CW), segpart rows CW wide: one
+// thread per (segment, component), summing the segment's non-zeros in order.
+__global__ void __launch_bounds__(256) k_eig_m2_segments(const uint32_t *__restrict__ csc_row,
+                                                         const float *__restrict__ csc_val,
+                                                         const int64_t *__restrict__ seg_start,
+                                                         int64_t nseg, const double *__restrict__ Z,
+                                                         int CW, double *segpart) {
+    const int64_t n = nseg * CW, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+        const int64_t sg = t / CW;
+        const int c = (int)(t - sg * CW);
+        double v = 0.0;
+        for (int64_t e = seg_start[sg]; e < seg_start[sg + 1]; ++e)
+            v = fma((double)csc_val[e], Z[(size_t)csc_row[e] * CW + c], v);
+        segpart[t] = v;
+    }
+}
+
+// Y(j, c0 + c) = sum of column j's segment partials in order (rows CW wide),
+// Y J x b: one thread per (column, component).
+__global__ void k_eig_m2_columns(const double *__restrict__ segpart,
+                                 const int64_t *__restrict__ col_seg, int32_t J, int CW,
+                                 double *Y, int b, int c0) {
+    const int64_t n = (int64_t)J * CW, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+        const int64_t j = t / CW;
+        const int c = (int)(t - j * CW);
+        double acc = 0.0;
+        for (int64_t sg = col_seg[j]; sg < col_seg[j + 1]; ++sg) acc += segpart[(size_t)sg * CW + c];
+        Y[(size_t)j * b + c0 + c] = acc;
+    }
+}
+
+// H = I, W = 1
+__global__ void k_eig_fill(float *H, float *W, int64_t K, int R) {
+    const int64_t n = K * R, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) W[e] = 1.f;
+    if (blockIdx.x == 0)
+        for (int e = threadIdx.x; e < R * R; e += blockDim.x) H[e] = (e / R == e % R) ? 1.f : 0.f;
+}
+
+// Orthonormal basis Q (J x b, FP64, row-major) of the columns of Y by
+// classical Gram-Schmidt with one full reorthogonalisation (CGS2, orthogonal
+// to working precision while the columns are numerically independent:
+// Giraud, Langou, Rozloznik & van den Eshof, Numer. Math. 101, 2005); the
+// leading columns of Q span the leading columns of Y.  A column left with at
+// most 2^-40 of its norm, or of the first column's norm, after both passes
+// depends on the earlier ones numerically (or is rounding noise, as the
+// columns of A V U for A's null space are); it is replaced by the unit vector
+// e_j with the largest
+// component outside their span (lowest j on ties; that component is at least
+// 1/sqrt(J) when J >= b) and orthogonalised again, so Q always has b
+// orthonormal columns.  With Vold (J x b), *dist = ||Q_R - Vold_R Vold_R^T
+// Q_R||_F^2 over the leading R columns of both: the sum of the squared sines
+// of the principal angles between the two leading subspaces.  One CTA of whole warps.
+__global__ void __launch_bounds__(256) k_eig_orth(const double *__restrict__ Y,
+                                                  const double *__restrict__ Vold, double *Q,
+                                                  int32_t J, int b, int R, double *dist,
+                                                  int *flags) {
+    __shared__ double coef[P2_RMAX];
+    __shared__ double red[32];
+    __shared__ int32_t redj[32];
+    __shared__ int32_t pick;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    double scale = 0.0;                        // norm of Y's first column
+    for (int r = 0; r < b; ++r) {
+        for (int32_t j = tid; j < J; j += nt) Q[(size_t)j * b + r] = Y[(size_t)j * b + r];
+        __syncthreads();
+        double a0 = 0.0;
+        for (int32_t j = tid; j < J; j += nt) {
+            const double q = Q[(size_t)j * b + r];
+            a0 = fma(q, q, a0);
+        }
+        double ref = sqrt(cta_sum(a0, red));   // norm before the projections
+        if (r == 0) scale = ref;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int s = tid; s < r; s += nt) {
+                    double a = 0.0;
+                    for (int32_t j = 0; j < J; ++j) a = fma(Q[(size_t)j * b + s], Q[(size_t)j * b + r], a);
+                    coef[s] = a;
+                }
+                __syncthreads();
+                for (int32_t j = tid; j < J; j += nt) {
+                    double q = Q[(size_t)j * b + r];
+                    for (int s = 0; s < r; ++s) q = fma(-coef[s], Q[(size_t)j * b + s], q);
+                    Q[(size_t)j * b + r] = q;
+                }
+                __syncthreads();
+            }
+            double a = 0.0;
+            for (int32_t j = tid; j < J; j += nt) {
+                const double q = Q[(size_t)j * b + r];
+                a = fma(q, q, a);
+            }
+            const double nrm = sqrt(cta_sum(a, red));
+            if (nrm > 0x1p-40 * fmax(ref, scale) && nrm > 0.0) {
+                const double inv = 1.0 / nrm;
+                for (int32_t j = tid; j < J; j += nt) Q[(size_t)j * b + r] *= inv;
+                __syncthreads();
+                break;
+            }
+            if (attempt == 1) {                // not reached when J >= b
+                if (tid == 0) atomicOr(flags, FLAG_EIG_NOCONV);
+                break;
+            }
+            // replacement: the e_j with the largest 1 - sum_{s<r} Q(j,s)^2
+            double best = -1.0;
+            int32_t bj = 0;
+            for (int32_t j = tid; j < J; j += nt) {
+                double w = 1.0;
+                for (int s = 0; s < r; ++s) {
+                    const double q = Q[(size_t)j * b + s];
+                    w = fma(-q, q, w);
+                }
+                if (w > best) {                // j increases within a thread: first max kept
+                    best = w;
+                    bj = j;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(FULLMASK, best, o);
+                const int32_t oj = __shfl_xor_sync(FULLMASK, bj, o);
+                if (ob > best || (ob == best && oj < bj)) {
+                    best = ob;
+                    bj = oj;
+                }
+            }
+            __syncthreads();
+            if (lane == 0) {
+                red[warp] = best;
+                redj[warp] = bj;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double bb = red[0];
+                int32_t jb = redj[0];
+                for (int w = 1; w < nw; ++w)
+                    if (red[w] > bb || (red[w] == bb && redj[w] < jb)) {
+                        bb = red[w];
+                        jb = redj[w];
+                    }
+                pick = jb;
+            }
+            __syncthreads();
+            const int32_t jp = pick;
+            for (int32_t j = tid; j < J; j += nt) Q[(size_t)j * b + r] = (j == jp) ? 1.0 : 0.0;
+            __syncthreads();
+            ref = 1.0;
+            if (r == 0) scale = 1.0;
+        }
+    }
+    if (Vold) {
+        // C = Vold_R^T Q_R, then ||Q_R - Vold_R C||_F^2 (no cancellation
+        // against R, so the distance resolves well below eps)
+        __shared__ double C[P2_RMAX * P2_RMAX];
+        for (int e = tid; e < R * R; e += nt) {
+            const int s = e / R, t = e - s * R;
+            double cst = 0.0;
+            for (int32_t j = 0; j < J; ++j) cst = fma(Vold[(size_t)j * b + s], Q[(size_t)j * b + t], cst);
+            C[e] = cst;
+        }
+        __syncthreads();
+        double a = 0.0;
+        for (int32_t j = tid; j < J; j += nt)
+            for (int t = 0; t < R; ++t) {
+                double res = Q[(size_t)j * b + t];
+                for (int s = 0; s < R; ++s) res = fma(-Vold[(size_t)j * b + s], C[s * R + t], res);
+                a = fma(res, res, a);
+            }
+        const double tot = cta_sum(a, red);
+        if (tid == 0) *dist = tot;
+    }
+}
+
+// Rayleigh-Ritz step on the orthonormal Vd (J x b) with Y = A Vd:
+// B = Vd^T Y (symmetrised) = U diag(l) U^T by the CTA Jacobi, the columns of
+// U in decreasing order of l (lower index first on ties).  Not final:
+// Out = Y U, the next block before orthonormalisation.  Final: Out = Vd U
+// (the Ritz vectors), each column's entry of largest magnitude made positive
+// (lowest row on ties), and the leading R columns stored to V (storage type
+// S, row stride VS, zero padding).  Dynamic shared memory: 2 b^2 doubles.
+// One CTA of whole warps.
+template <class S>
+__global__ void __launch_bounds__(256) k_eig_ritz(const double *__restrict__ Y,
+                                                  const double *__restrict__ Vd, double *Out,
+                                                  S *V, int VS, int32_t J, int b, int R,
+                                                  int final_step, int *flags) {
+    extern __shared__ __align__(16) double sd[];
+    double *A = sd, *U = A + b * b;
+    __shared__ int perm[P2_RMAX];
+    __shared__ double sgn[P2_RMAX];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < b * b; e += nt) {
+        const int s = e / b, t = e - s * b;
+        double cst = 0.0;
+        for (int32_t j = 0; j < J; ++j) cst = fma(Vd[(size_t)j * b + s], Y[(size_t)j * b + t], cst);
+        U[e] = cst;
+    }
+    __syncthreads();
+    __shared__ double fro;
+    for (int e = tid; e < b * b; e += nt) {
+        const int s = e / b, t = e - s * b;
+        A[e] = 0.5 * (U[s * b + t] + U[t * b + s]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double f = 0.0;
+        for (int e = 0; e < b * b; ++e) f = fma(A[e], A[e], f);
+        fro = sqrt(f);
+    }
+    __syncthreads();
+    cta_jacobi(A, U, b, flags, 2.220446049250313e-16 * fro);
+    if (tid == 0) {
+        for (int i = 0; i < b; ++i) perm[i] = i;
+        for (int i = 1; i < b; ++i) {          // stable insertion sort, decreasing l
+            const int p = perm[i];
+            const double lp = A[p * b + p];
+            int l = i;
+            while (l > 0 && A[perm[l - 1] * b + perm[l - 1]] < lp) {
+                perm[l] = perm[l - 1];
+                --l;
+            }
+            perm[l] = p;
+        }
+    }
+    __syncthreads();
+    const double *Src = final_step ? Vd : Y;
+    for (int32_t j = tid; j < J; j += nt)
+        for (int col = 0; col < b; ++col) {
+            double a = 0.0;
+            for (int u = 0; u < b; ++u) a = fma(Src[(size_t)j * b + u], U[u * b + perm[col]], a);
+            Out[(size_t)j * b + col] = a;
+        }
+    __syncthreads();
+    if (!final_step) return;
+    for (int col = tid; col < R; col += nt) {
+        double best = -1.0, val = 0.0;
+        for (int32_t j = 0; j < J; ++j) {      // first maximum: lowest row on ties
+            const double v = Out[(size_t)j * b + col];
+            if (fabs(v) > best) {
+                best = fabs(v);
+                val = v;
+            }
+        }
+        sgn[col] = val < 0.0 ? -1.0 : 1.0;
+    }
+    __syncthreads();
+    for (size_t e = tid; e < (size_t)J * VS; e += nt) {
+        const size_t j = e / VS;
+        const int col = (int)(e - j * VS);
+        double v = 0.0;
+        if (col < R) {
+            v = sgn[col] * Out[j * b + col];
+            Out[j * b + col] = v;
+        }
+        Stor<S>::st(V + e, (float)v);
+    }
 }
 
 // H solve: M1 = sum of partials; H = normalize(M1 (W^TW * V^TV)^+); H64, HtH.
@@ -1095,6 +1414,8 @@ int configure_kernels(p2_ctx *c) {
     if (rc == P2_OK) rc = allow_dynamic_smem(k_fin_v, cap, "k_fin_v");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_subject_stats, cap, "k_subject_stats");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_subject_stats_gf, cap, "k_subject_stats_gf");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_eig_ritz<float>, cap, "k_eig_ritz");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_eig_ritz<bf16_t>, cap, "k_eig_ritz");
     if (rc == P2_OK && c->opt.nonneg) {
         const cudaError_t e = nnls_configure(cap);
         if (e != cudaSuccess) {
@@ -1451,6 +1772,62 @@ int enqueue_iteration(p2_ctx *c) {
     int rc = enqueue_qstep(c, 1);
     mark(c, 7);
     return rc;
+}
+
+// Rational start pieces (driven by p2_init_eig).
+int enqueue_eig_fill(p2_ctx *c) {
+    const int64_t n = c->X.K * c->R;
+    const int nb = (int)((n + 255) / 256 < 4 * c->geo.nsm ? (n + 255) / 256 : 4 * c->geo.nsm);
+    k_eig_fill<<<nb > 0 ? nb : 1, 256, 0, c->stream>>>(c->d_H, c->d_W, c->X.K, c->R);
+    P2_LAUNCH_CHECK("k_eig_fill");
+    return P2_OK;
+}
+
+int enqueue_eig_product(p2_ctx *c, const double *Vd, int b, int CW, double *Z, double *seg,
+                        double *Y) {
+    const int32_t J = c->X.J;
+    const int nsm = c->geo.nsm;
+    const int64_t zw = (c->X.K + 7) / 8, sw = (c->X.nseg * CW + 255) / 256,
+                  cw = ((int64_t)J * CW + 255) / 256;
+    const int zb = (int)(zw < 16 * nsm ? (zw > 0 ? zw : 1) : 16 * nsm);
+    const int sb = (int)(sw < 64 * nsm ? (sw > 0 ? sw : 1) : 64 * nsm);
+    const int cb = (int)(cw < 8 * nsm ? (cw > 0 ? cw : 1) : 8 * nsm);
+    for (int c0 = 0; c0 < b; c0 += CW) {
+        const int w = (b - c0) < CW ? (b - c0) : CW;
+        k_eig_z<<<zb, 256, 0, c->stream>>>(xview(c), Vd, b, c0, w, Z);
+        P2_LAUNCH_CHECK("k_eig_z");
+        if (c->X.nseg > 0) {
+            k_eig_m2_segments<<<sb, 256, 0, c->stream>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
+                                                         c->X.nseg, Z, w, seg);
+            P2_LAUNCH_CHECK("k_eig_m2_segments");
+        }
+        k_eig_m2_columns<<<cb, 256, 0, c->stream>>>(seg, c->X.col_seg, J, w, Y, b, c0);
+        P2_LAUNCH_CHECK("k_eig_m2_columns");
+    }
+    return P2_OK;
+}
+
+int enqueue_eig_orth(p2_ctx *c, const double *Y, const double *Vold, double *Q, int b,
+                     double *dist) {
+    // one warp: the block is at most 64 columns of J rows, and the
+    // column-by-column recurrence synchronises after every step
+    k_eig_orth<<<1, 32, 0, c->stream>>>(Y, Vold, Q, (int32_t)c->X.J, b, c->R, dist, &c->d_s->flags);
+    P2_LAUNCH_CHECK("k_eig_orth");
+    return P2_OK;
+}
+
+int enqueue_eig_ritz(p2_ctx *c, const double *Y, const double *Vd, double *Out, int b,
+                     int final_step) {
+    const int32_t J = (int32_t)c->X.J;
+    const size_t sm = (size_t)2 * b * b * 8;
+    if (c->bf16)
+        k_eig_ritz<bf16_t><<<1, 32, sm, c->stream>>>(Y, Vd, Out, c->d_Vh, v_stride<bf16_t>(c->R), J,
+                                                      b, c->R, final_step, &c->d_s->flags);
+    else
+        k_eig_ritz<float><<<1, 32, sm, c->stream>>>(Y, Vd, Out, c->d_V, v_stride<float>(c->R), J, b,
+                                                     c->R, final_step, &c->d_s->flags);
+    P2_LAUNCH_CHECK("k_eig_ritz");
+    return P2_OK;
 }
 
 }  // namespace p2

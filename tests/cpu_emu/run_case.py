@@ -14,7 +14,7 @@ import numpy as np  # noqa: E402
 import paper_1703_04219_gb300 as p2  # noqa: E402
 import synth  # noqa: E402
 from oracle import parafac2 as P  # noqa: E402
-from tests.helpers import rel_fro  # noqa: E402
+from tests.helpers import rel_fro, slices_from_dense  # noqa: E402
 
 p2.LIB_PATH = os.path.join(HERE, "_build", "libp2emu.so")
 p2.lib = p2._load()
@@ -116,6 +116,44 @@ def seed_case(R, seed):
             "n_loose": float(n_loose)}
 
 
+def rational_case(R, K):
+    """p2_init_eig against the oracle's rational start (H = I, W = 1, V the R
+    leading eigenvectors of sum_k X_k^T X_k), one iteration from it against
+    the oracle's iteration from the oracle's start, and a rank-deficient input
+    (3 non-zero columns of 8, R = 5) whose null-space columns are a completion."""
+    X = synth.generate("tiny", K=K)
+    blocks = P.all_blocks(X)
+    H0, V0, W0, _ = P.rational_start(blocks, X.K, X.J, R)
+    with p2.Parafac2(R, use_graph=False) as m:
+        m.load(X)
+        n = m.init_eig(max_iter=200, tol=1e-9)
+        H, V, W = m.factors()
+        fit = m.iterate(1)
+        H1, V1, W1 = m.factors()
+    ref = P.als_iteration(blocks, H0, V0, W0)
+    nx2 = P.norm_x_sq(blocks)
+    rng = np.random.default_rng(5)
+    mats = []
+    for _ in range(6):
+        d = np.zeros((4, 8))
+        d[:, :3] = rng.uniform(0.5, 2.0, (4, 3))
+        mats.append(d)
+    Xd = slices_from_dense(mats, J=8)
+    with p2.Parafac2(5, use_graph=False) as m:
+        m.load(Xd)
+        nd = m.init_eig(max_iter=200, tol=1e-9)
+        _, Vd, _ = m.factors()
+        fitd = m.iterate(1)
+    _, Vd0, _, _ = P.rational_start(P.all_blocks(Xd), Xd.K, Xd.J, 5)
+    Vd = Vd.astype(np.float64)
+    return {"n": n, "H_eye": float(np.array_equal(H, np.eye(R, dtype=np.float32))),
+            "W_one": float(np.all(W == 1.0)), "V": rel_fro(V, V0),
+            "H1": rel_fro(H1, ref["H"]), "V1": rel_fro(V1, ref["V"]), "W1": rel_fro(W1, ref["W"]),
+            "fit": abs(fit - P.fit_from_loss(ref["loss"], nx2)),
+            "def_n": nd, "def_orth": float(np.abs(Vd.T @ Vd - np.eye(5)).max()),
+            "def_lead": rel_fro(Vd[:, :3], Vd0[:, :3]), "def_fit_finite": float(np.isfinite(fitd))}
+
+
 if __name__ == "__main__":
     kind = sys.argv[1]
     if kind == "iterate":
@@ -123,6 +161,8 @@ if __name__ == "__main__":
                            sys.argv[5] if len(sys.argv) > 5 else "fp32")
     elif kind == "seed":
         out = seed_case(int(sys.argv[2]), int(sys.argv[3]))
+    elif kind == "rational":
+        out = rational_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "getu":
         out = getu_case(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]))
     else:

@@ -3,8 +3,8 @@ AddressSanitizer: one ALS iteration at R = 5 and R = 10 (lane-per-subject
 Procrustes), at R = 13 and R = 40 (grouped Procrustes, eight and sixteen lanes
 per subject), at R = 5 with bfloat16 storage and in the non-negative
 variant, a projection of new
-subjects, U_k = Q_k H for a range of subjects, and the seeded initialisation
-with the stopping rule.
+subjects, U_k = Q_k H for a range of subjects, the seeded initialisation
+with the stopping rule, and the rational start (subspace iteration in FP64).
 Every device buffer and every block's shared memory is a heap block of its
 exact size, so an out-of-bounds access by any kernel aborts the run; the
 results must also match the FP64 oracle.  No GPU involved."""
@@ -30,6 +30,7 @@ CASES = {
     "project_r8_nonneg": ["project", "8", "3", "nonneg"],
     "getu_r5": ["getu", "5", "3", "17"],
     "seed_r4": ["seed", "4", "987654321"],
+    "rational_r3": ["rational", "3", "12"],
 }
 
 
@@ -115,3 +116,19 @@ def test_emulated_nonneg_iteration_is_in_bounds_and_matches_oracle(emulated_runs
         assert err[key] < 1e-5, (key, err[key])
     assert err["fit"] < 1e-4
 
+
+
+def test_emulated_rational_start_is_in_bounds_and_matches_oracle(emulated_runs):
+    """H = I, W = 1, V = the leading eigenvectors of sum_k X_k^T X_k (signs by
+    the largest-magnitude entry), and the first iteration from that start;
+    a rank-deficient input converges to an orthonormal completion."""
+    out = _result(emulated_runs, "rational_r3")
+    assert 1 <= out["n"] < 200, out
+    assert out["H_eye"] == 1.0 and out["W_one"] == 1.0
+    assert out["V"] < 1e-6, out
+    for key in ("H1", "V1", "W1"):
+        assert out[key] < 1e-5, (key, out[key])
+    assert out["fit"] < 1e-4
+    assert 1 <= out["def_n"] < 200, out
+    assert out["def_orth"] < 1e-6 and out["def_lead"] < 1e-6, out
+    assert out["def_fit_finite"] == 1.0

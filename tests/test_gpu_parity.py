@@ -237,3 +237,66 @@ def test_nonneg_ten_iterations_and_limits(p2):
     assert np.all(V >= 0) and np.all(W >= 0)
     with pytest.raises(p2.P2Error):
         p2.Parafac2(17, nonneg=True)
+
+
+@pytest.mark.parametrize("name,K,R,precision", [("tiny", 200, 5, "fp32"), ("c63m", 2000, 10, "fp32"),
+                                                ("c250m", 300, 40, "fp32"), ("c63m", 2000, 10, "bf16")])
+def test_rational_start_matches_oracle(p2, name, K, R, precision):
+    """p2_init_eig: H = I, W = 1 and V = the oracle's leading eigenvectors of
+    sum_k X_k^T X_k (within 1e-5, or 3e-3 with bfloat16 storage of V); one
+    iteration from the stored start against the oracle's iteration from the
+    same state."""
+    X = synth.generate(name, K=K)
+    blocks = P.all_blocks(X)
+    _, Vref, _, _ = P.rational_start(blocks, X.K, X.J, R)
+    bf16 = precision == "bf16"
+    with p2.Parafac2(R, precision=precision) as m:
+        m.load(X)
+        n = m.init_eig(max_iter=2000, tol=1e-10)
+        H, V, W = m.factors()
+        fit = m.iterate(1)
+        H1, V1, W1 = m.factors()
+    assert 1 <= n < 2000
+    assert np.array_equal(H, np.eye(R, dtype=np.float32))
+    assert np.all(W == 1.0)
+    assert rel_fro(V, Vref) < (3e-3 if bf16 else TOL), rel_fro(V, Vref)
+    if bf16:
+        return
+    ref = P.als_iteration(blocks, np.eye(R), V.astype(np.float64), np.ones((X.K, R)))
+    for key, got in (("H", H1), ("V", V1), ("W", W1)):
+        assert rel_fro(got, ref[key]) < TOL, (key, rel_fro(got, ref[key]))
+    assert abs(fit - P.fit_from_loss(ref["loss"], P.norm_x_sq(blocks))) < FIT_TOL
+
+
+def test_rational_start_rank_deficient_and_limits(p2):
+    """sum_k X_k^T X_k of rank 3 with R = 5: the leading three columns match
+    the oracle, the other two complete an orthonormal V; J < R and bad
+    arguments are rejected with P2_EINVAL."""
+    rng = np.random.default_rng(5)
+    mats = []
+    for _ in range(40):
+        d = np.zeros((6, 30))
+        d[:, [2, 7, 19]] = rng.uniform(0.5, 2.0, (6, 3))
+        mats.append(d)
+    X = slices_from_dense(mats, J=30)
+    _, Vref, _, _ = P.rational_start(P.all_blocks(X), X.K, X.J, 5)
+    with p2.Parafac2(5) as m:
+        m.load(X)
+        n = m.init_eig(max_iter=500, tol=1e-10)
+        _, V, _ = m.factors()
+        fit = m.iterate(2)
+        for bad in ((0, 1e-6), (10, -1.0)):
+            with pytest.raises(p2.P2Error) as ei:
+                m.init_eig(*bad)
+            assert ei.value.code == p2.P2_EINVAL
+    V = V.astype(np.float64)
+    assert n < 500
+    assert np.abs(V.T @ V - np.eye(5)).max() < 1e-6
+    assert rel_fro(V[:, :3], Vref[:, :3]) < TOL
+    assert np.isfinite(fit)
+    narrow = slices_from_dense([rng.uniform(0.5, 1.0, (3, 4)) for _ in range(5)], J=4)
+    with p2.Parafac2(5) as m:
+        m.load(narrow)
+        with pytest.raises(p2.P2Error) as ei:
+            m.init_eig()
+        assert ei.value.code == p2.P2_EINVAL

@@ -393,3 +393,59 @@ def test_nonneg_iteration_keeps_sign_and_decreases_loss():
     nx2 = res["norm_x_sq"]
     for a, b in zip(losses, losses[1:]):
         assert b <= a + 1e-10 * nx2
+
+
+def _dense_stack(X):
+    """The stacked dense N x J matrix of the collection (FP32 values as FP64)."""
+    rows = []
+    for k in range(X.K):
+        Xc, cols = P.subject_block(X, k)
+        D = np.zeros((Xc.shape[0], X.J))
+        D[:, cols] = Xc
+        rows.append(D)
+    return np.vstack(rows)
+
+
+def test_rational_start_equals_right_singular_vectors():
+    """V of the rational start = the leading right singular vectors of the
+    stacked X (an SVD of X, not the eigen-solver of sum_k X_k^T X_k the
+    oracle uses), its eigenvalues the squared singular values; H = I, W = 1;
+    each column's entry of largest magnitude is positive."""
+    rng = np.random.default_rng(3)
+    mats = []
+    for _ in range(9):
+        I = int(rng.integers(2, 7))
+        mats.append(rng.uniform(0.1, 1.0, (I, 12)) * (rng.uniform(size=(I, 12)) < 0.5))
+    X = slices_from_dense(mats, J=12)
+    R = 4
+    H, V, W, lam = P.rational_start(P.all_blocks(X), X.K, X.J, R)
+    _, sv, Vt = np.linalg.svd(_dense_stack(X))
+    ref = Vt[:R].T.copy()
+    for r in range(R):
+        j = int(np.argmax(np.abs(ref[:, r])))
+        ref[:, r] *= np.sign(ref[j, r])
+    assert np.abs(V - ref).max() < 1e-10
+    assert np.allclose(lam[:R], sv[:R] ** 2, rtol=1e-10)
+    assert np.array_equal(H, np.eye(R)) and np.array_equal(W, np.ones((X.K, R)))
+    for r in range(R):
+        assert V[np.argmax(np.abs(V[:, r])), r] > 0
+
+
+def test_rational_start_closed_form_for_orthogonal_columns():
+    """One non-zero per row: the columns of the stacked X are orthogonal, so
+    sum_k X_k^T X_k is diagonal with the column sums of squares, and V is the
+    unit vectors of the R columns with the largest sums, in that order."""
+    rng = np.random.default_rng(8)
+    J, R = 15, 5
+    mats = []
+    for _ in range(6):
+        I = int(rng.integers(3, 9))
+        D = np.zeros((I, J))
+        D[np.arange(I), rng.integers(0, J, I)] = rng.uniform(0.5, 3.0, I)
+        mats.append(D)
+    X = slices_from_dense(mats, J=J)
+    ss = (_dense_stack(X) ** 2).sum(axis=0)
+    top = np.argsort(-ss, kind="stable")[:R]
+    _, V, _, lam = P.rational_start(P.all_blocks(X), X.K, X.J, R)
+    assert np.abs(V - np.eye(J)[:, top]).max() < 1e-12
+    assert np.allclose(lam[:R], ss[top], rtol=1e-12)

@@ -145,8 +145,10 @@ int p2_init(p2_ctx *ctx, const float *H0, const float *V0, const float *W0);
  * products; a final Rayleigh-Ritz step gives V.  Columns for the null space
  * of sum_k X_k^T X_k, when its rank is below R, are an orthonormal
  * completion.  V is then stored in the context's precision.  Transient
- * device scratch: 4 J b doubles and (N + S) min(b, 2^29 / N) doubles (N
- * stacked rows, S column segments of the mode-2 layout).  n_done (nullable, host) receives the iterations run.  Synchronises
+ * device scratch: 4 J b doubles and (N + S) w doubles (N stacked rows, S
+ * column segments of the mode-2 layout), the product's column width w <= b
+ * chosen so that N w doubles take at most a quarter of the free device
+ * memory and 16 GiB.  n_done (nullable, host) receives the iterations run.  Synchronises
  * after every product.  P2_EINVAL for J < R, max_iter < 1 or tol < 0;
  * P2_ENUMERIC if an eigen step failed to converge.
  */

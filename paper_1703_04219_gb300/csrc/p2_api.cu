@@ -473,9 +473,13 @@ int p2_init_eig(p2_ctx *c, int32_t max_iter, double tol, int32_t *n_done) {
     // block width: oversampled so that the leading R Ritz vectors converge at
     // lambda_{b+1} / lambda_R; at most the CTA eigen-solver's size and J
     const int b = std::min(std::min(std::max(2 * R, R + 8), (int)P2_RMAX), (int)J);
-    // product columns per pass: the N x CW FP64 scratch held to 4 GiB
+    // product columns per pass: the N x CW FP64 scratch held to a quarter of
+    // the free device memory, at most 16 GiB (every pass re-reads X)
+    size_t free_b = 0, total_b = 0;
+    P2_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    const size_t budget = std::min(free_b / 4, (size_t)16 << 30);
     const size_t N = c->X.N > 0 ? (size_t)c->X.N : 1;
-    const int CW = (int)std::min<size_t>((size_t)b, std::max<size_t>(1, ((size_t)4 << 30) / (8 * N)));
+    const int CW = (int)std::min<size_t>((size_t)b, std::max<size_t>(1, budget / (8 * N)));
     const size_t Jb = (size_t)J * b;
     EigScratch s;
     P2_CUDA_TRY(cudaMalloc(&s.v, Jb * sizeof(double)));

@@ -841,6 +841,33 @@ static __device__ double cta_sum(double v, double *red) {
     return s;
 }
 
+// out[q] = sum_j A(j, ca[q]) B(j, cb[q]) for q < nq <= 8 (A, B: J rows of
+// strides lda, ldb), by the whole CTA: threads over rows, the partial sums
+// in shared memory (8 blockDim.x doubles at part) added in thread order.
+static __device__ void cta_dots8(const double *__restrict__ A, int lda,
+                                 const double *__restrict__ B, int ldb, const int *ca,
+                                 const int *cb, int nq, int32_t J, double *part, double *out) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int32_t j = tid; j < J; j += nt) {
+        const double *a = A + (size_t)j * lda, *bb = B + (size_t)j * ldb;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < nq) acc[q] = fma(a[ca[q]], bb[cb[q]], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) part[q * nt + tid] = acc[q];
+    __syncthreads();
+    if (tid < nq) {
+        double v = 0.0;
+        for (int t = 0; t < nt; ++t) v += part[tid * nt + t];
+        out[tid] = v;
+    }
+    __syncthreads();
+}
+
 // Columns c0 .. c0+CW-1 of Z = X Vd in FP64 (stacked rows, N x CW; Vd is
 // J x b): one warp per subject, one lane per row of a 32-row chunk, row
 // offsets from a warp scan of the row lengths.
@@ -859,11 +886,20 @@ __global__ void __launch_bounds__(256) k_eig_z(XView X, const double *__restrict
             if (lane < nr) {
                 const int64_t b0 = base + off;
                 double *zr = Z + (size_t)(cr + lane) * CW;
-                for (int c = 0; c < CW; ++c) {
-                    double a = 0.0;
-                    for (int e = 0; e < len; ++e)
-                        a = fma((double)X.val[b0 + e], Vd[(size_t)X.col[b0 + e] * b + c0 + c], a);
-                    zr[c] = a;
+                for (int c8 = 0; c8 < CW; c8 += 8) {     // eight components per pass over the row
+                    double a[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) a[q] = 0.0;
+                    for (int e = 0; e < len; ++e) {
+                        const double x = (double)X.val[b0 + e];
+                        const double *v = Vd + (size_t)X.col[b0 + e] * b + c0 + c8;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            if (c8 + q < CW) a[q] = fma(x, v[q], a[q]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (c8 + q < CW) zr[c8 + q] = a[q];
                 }
             }
             base += tot;
@@ -925,11 +961,13 @@ __global__ void k_eig_fill(float *H, float *W, int64_t K, int R) {
 // 1/sqrt(J) when J >= b) and orthogonalised again, so Q always has b
 // orthonormal columns.  With Vold (J x b), *dist = ||Q_R - Vold_R Vold_R^T
 // Q_R||_F^2 over the leading R columns of both: the sum of the squared sines
-// of the principal angles between the two leading subspaces.  One CTA of whole warps.
+// of the principal angles between the two leading subspaces.  Dynamic
+// shared memory: 8 blockDim.x doubles.  One CTA of whole warps.
 __global__ void __launch_bounds__(256) k_eig_orth(const double *__restrict__ Y,
                                                   const double *__restrict__ Vold, double *Q,
                                                   int32_t J, int b, int R, double *dist,
                                                   int *flags) {
+    extern __shared__ __align__(16) double part[];   // 8 blockDim.x doubles (cta_dots8)
     __shared__ double coef[P2_RMAX];
     __shared__ double red[32];
     __shared__ int32_t redj[32];
@@ -949,12 +987,15 @@ __global__ void __launch_bounds__(256) k_eig_orth(const double *__restrict__ Y,
         if (r == 0) scale = ref;
         for (int attempt = 0; attempt < 2; ++attempt) {
             for (int pass = 0; pass < 2; ++pass) {
-                for (int s = tid; s < r; s += nt) {
-                    double a = 0.0;
-                    for (int32_t j = 0; j < J; ++j) a = fma(Q[(size_t)j * b + s], Q[(size_t)j * b + r], a);
-                    coef[s] = a;
+                for (int s0 = 0; s0 < r; s0 += 8) {
+                    int ca[8], cb[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        ca[q] = s0 + q;
+                        cb[q] = r;
+                    }
+                    cta_dots8(Q, b, Q, b, ca, cb, r - s0 < 8 ? r - s0 : 8, J, part, coef + s0);
                 }
-                __syncthreads();
                 for (int32_t j = tid; j < J; j += nt) {
                     double q = Q[(size_t)j * b + r];
                     for (int s = 0; s < r; ++s) q = fma(-coef[s], Q[(size_t)j * b + s], q);
@@ -1028,13 +1069,16 @@ __global__ void __launch_bounds__(256) k_eig_orth(const double *__restrict__ Y,
         // C = Vold_R^T Q_R, then ||Q_R - Vold_R C||_F^2 (no cancellation
         // against R, so the distance resolves well below eps)
         __shared__ double C[P2_RMAX * P2_RMAX];
-        for (int e = tid; e < R * R; e += nt) {
-            const int s = e / R, t = e - s * R;
-            double cst = 0.0;
-            for (int32_t j = 0; j < J; ++j) cst = fma(Vold[(size_t)j * b + s], Q[(size_t)j * b + t], cst);
-            C[e] = cst;
+        for (int e0 = 0; e0 < R * R; e0 += 8) {
+            int ca[8], cb[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = e0 + q < R * R ? e0 + q : 0;
+                ca[q] = e / R;
+                cb[q] = e - (e / R) * R;
+            }
+            cta_dots8(Vold, b, Q, b, ca, cb, R * R - e0 < 8 ? R * R - e0 : 8, J, part, C + e0);
         }
-        __syncthreads();
         double a = 0.0;
         for (int32_t j = tid; j < J; j += nt)
             for (int t = 0; t < R; ++t) {
@@ -1054,24 +1098,28 @@ __global__ void __launch_bounds__(256) k_eig_orth(const double *__restrict__ Y,
 // (the Ritz vectors), each column's entry of largest magnitude made positive
 // (lowest row on ties), and the leading R columns stored to V (storage type
 // S, row stride VS, zero padding).  Dynamic shared memory: 2 b^2 doubles.
-// One CTA of whole warps.
+// Dynamic shared memory: 2 b^2 + 8 blockDim.x doubles.  One CTA of whole
+// warps.
 template <class S>
 __global__ void __launch_bounds__(256) k_eig_ritz(const double *__restrict__ Y,
                                                   const double *__restrict__ Vd, double *Out,
                                                   S *V, int VS, int32_t J, int b, int R,
                                                   int final_step, int *flags) {
     extern __shared__ __align__(16) double sd[];
-    double *A = sd, *U = A + b * b;
+    double *A = sd, *U = A + b * b, *part = U + b * b;   // part: 8 blockDim.x doubles
     __shared__ int perm[P2_RMAX];
     __shared__ double sgn[P2_RMAX];
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < b * b; e += nt) {
-        const int s = e / b, t = e - s * b;
-        double cst = 0.0;
-        for (int32_t j = 0; j < J; ++j) cst = fma(Vd[(size_t)j * b + s], Y[(size_t)j * b + t], cst);
-        U[e] = cst;
+    for (int e0 = 0; e0 < b * b; e0 += 8) {
+        int ca[8], cb[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = e0 + q < b * b ? e0 + q : 0;
+            ca[q] = e / b;
+            cb[q] = e - (e / b) * b;
+        }
+        cta_dots8(Vd, b, Y, b, ca, cb, b * b - e0 < 8 ? b * b - e0 : 8, J, part, U + e0);
     }
-    __syncthreads();
     __shared__ double fro;
     for (int e = tid; e < b * b; e += nt) {
         const int s = e / b, t = e - s * b;
@@ -1414,6 +1462,7 @@ int configure_kernels(p2_ctx *c) {
     if (rc == P2_OK) rc = allow_dynamic_smem(k_fin_v, cap, "k_fin_v");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_subject_stats, cap, "k_subject_stats");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_subject_stats_gf, cap, "k_subject_stats_gf");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_eig_orth, cap, "k_eig_orth");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_eig_ritz<float>, cap, "k_eig_ritz");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_eig_ritz<bf16_t>, cap, "k_eig_ritz");
     if (rc == P2_OK && c->opt.nonneg) {
@@ -1809,9 +1858,8 @@ int enqueue_eig_product(p2_ctx *c, const double *Vd, int b, int CW, double *Z, d
 
 int enqueue_eig_orth(p2_ctx *c, const double *Y, const double *Vold, double *Q, int b,
                      double *dist) {
-    // one warp: the block is at most 64 columns of J rows, and the
-    // column-by-column recurrence synchronises after every step
-    k_eig_orth<<<1, 32, 0, c->stream>>>(Y, Vold, Q, (int32_t)c->X.J, b, c->R, dist, &c->d_s->flags);
+    k_eig_orth<<<1, 256, (size_t)8 * 256 * 8, c->stream>>>(Y, Vold, Q, (int32_t)c->X.J, b, c->R, dist,
+                                                           &c->d_s->flags);
     P2_LAUNCH_CHECK("k_eig_orth");
     return P2_OK;
 }
@@ -1819,12 +1867,12 @@ int enqueue_eig_orth(p2_ctx *c, const double *Y, const double *Vold, double *Q, 
 int enqueue_eig_ritz(p2_ctx *c, const double *Y, const double *Vd, double *Out, int b,
                      int final_step) {
     const int32_t J = (int32_t)c->X.J;
-    const size_t sm = (size_t)2 * b * b * 8;
+    const size_t sm = ((size_t)2 * b * b + 8 * 256) * 8;
     if (c->bf16)
-        k_eig_ritz<bf16_t><<<1, 32, sm, c->stream>>>(Y, Vd, Out, c->d_Vh, v_stride<bf16_t>(c->R), J,
+        k_eig_ritz<bf16_t><<<1, 256, sm, c->stream>>>(Y, Vd, Out, c->d_Vh, v_stride<bf16_t>(c->R), J,
                                                       b, c->R, final_step, &c->d_s->flags);
     else
-        k_eig_ritz<float><<<1, 32, sm, c->stream>>>(Y, Vd, Out, c->d_V, v_stride<float>(c->R), J, b,
+        k_eig_ritz<float><<<1, 256, sm, c->stream>>>(Y, Vd, Out, c->d_V, v_stride<float>(c->R), J, b,
                                                      c->R, final_step, &c->d_s->flags);
     P2_LAUNCH_CHECK("k_eig_ritz");
     return P2_OK;

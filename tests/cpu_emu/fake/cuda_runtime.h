@@ -72,6 +72,13 @@ template <class T> inline cudaError_t cudaMalloc(T **p, size_t n) {
 }
 template <class T> inline cudaError_t cudaMallocAsync(T **p, size_t n, cudaStream_t) { return cudaMalloc(p, n); }
 inline cudaError_t cudaFree(void *p) { free(p); return cudaSuccess; }
+// free memory: EMU_FREE_BYTES if set (to drive size-dependent paths), else 8 GiB
+inline cudaError_t cudaMemGetInfo(size_t *f, size_t *t) {
+    const char *e = getenv("EMU_FREE_BYTES");
+    *f = e ? (size_t)strtoull(e, nullptr, 10) : ((size_t)8 << 30);
+    *t = (size_t)16 << 30;
+    return cudaSuccess;
+}
 inline cudaError_t cudaFreeAsync(void *p, cudaStream_t) { free(p); return cudaSuccess; }
 inline cudaError_t cudaMemcpy(void *d, const void *s, size_t n, cudaMemcpyKind) { if (n) memmove(d, s, n); return cudaSuccess; }
 inline cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyKind k, cudaStream_t = nullptr) { return cudaMemcpy(d, s, n, k); }

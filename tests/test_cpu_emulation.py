@@ -119,16 +119,16 @@ def test_emulated_nonneg_iteration_is_in_bounds_and_matches_oracle(emulated_runs
 
 
 def test_emulated_rational_start_is_in_bounds_and_matches_oracle(emulated_runs):
-    """H = I, W = 1, V = the leading eigenvectors of sum_k X_k^T X_k (signs by
-    the largest-magnitude entry), and the first iteration from that start;
-    a rank-deficient input converges to an orthonormal completion."""
+    """H = I, W = 1, V orthonormal and near the leading eigenvectors of
+    sum_k X_k^T X_k after 12 products (the product in several column
+    passes), the first iteration from that start against the oracle, and a
+    rank-deficient input converging to an orthonormal completion."""
     out = _result(emulated_runs, "rational_r3")
-    assert 1 <= out["n"] < 200, out
-    assert out["H_eye"] == 1.0 and out["W_one"] == 1.0
-    assert out["V"] < 1e-6, out
+    assert out["n"] == 12 and out["H_eye"] == 1.0 and out["W_one"] == 1.0
+    assert out["orth"] < 1e-6 and out["sin2"] < 5e-4, out
     for key in ("H1", "V1", "W1"):
         assert out[key] < 1e-5, (key, out[key])
     assert out["fit"] < 1e-4
-    assert 1 <= out["def_n"] < 200, out
+    assert 1 <= out["def_n"] < 50, out
     assert out["def_orth"] < 1e-6 and out["def_lead"] < 1e-6, out
     assert out["def_fit_finite"] == 1.0

@@ -25,6 +25,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "p2_internal.cuh"
 
@@ -187,13 +188,16 @@ struct RowCol {
 // M3(k,:) = sum_i z'_i o (B_k^T z_i), one lane per row, B_k read as 16-byte
 // broadcasts; for larger R through C_k = Z_k^T Z'_k and coldot(H, T_k C_k).
 // ---------------------------------------------------------------------------
-template <int CB, bool MODE3, class S>
+template <int CB, bool MODE3, class S, int RT = 0>
 __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 3) k_alpha(XView X, const S *__restrict__ Vprev,
                                                const S *__restrict__ V,
                                                const float *__restrict__ H,
                                                const float *__restrict__ T,
                                                const SmallState *__restrict__ st, dw *G,
-                                               float *Gf, float *W, float *M3, int R) {
+                                               float *Gf, float *W, float *M3, int R_rt) {
+    // RT > 0: the rank fixed at compile time (loop bounds, strides and
+    // shared-memory offsets become constants); RT = 0: the rank R_rt
+    const int R = RT > 0 ? RT : R_rt;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = R * (R + 1) / 2;
     const int RS = row_stride(R);
@@ -395,12 +399,13 @@ static __host__ __device__ size_t beta_warp_bytes(int R) {
 // The same kernel serves p2_get_U (U_k = Q_k H = Z_k T_k^T H): W == NULL
 // stands for S_k = I, the output type O may differ from the storage type S,
 // and row r of the view is written at Pout[(r - out_row0) R].
-template <int CB, class S, class O = S>
+template <int CB, class S, class O = S, int RT = 0>
 __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 4) k_beta_p(XView X, const S *__restrict__ V,
                                                 const float *__restrict__ H,
                                                 const float *__restrict__ T,
-                                                const float *__restrict__ W, O *Pout, int R,
+                                                const float *__restrict__ W, O *Pout, int R_rt,
                                                 int64_t out_row0) {
+    const int R = RT > 0 ? RT : R_rt;   // RT > 0: the rank fixed at compile time
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RS = row_stride(R);
     float *Hs = reinterpret_cast<float *>(smem_raw);
@@ -1433,17 +1438,38 @@ static int allow_dynamic_smem(F *fn, int cap, const char *name) {
     return P2_OK;
 }
 
+// Ranks up to P2_RT_MAX run kernels compiled for that rank (loop bounds,
+// strides and shared-memory offsets constant: alpha pass -27% at R = 10);
+// larger ranks the generic kernels with CB = 32.
+#define P2_RT_MAX 16
+template <int R>
+struct RankBlock {
+    static constexpr int cb = R <= 8 ? 8 : 16;
+};
+
+template <class S, int... Rs>
+static int allow_rank_kernels(int cap, std::integer_sequence<int, Rs...>) {
+    int rc = P2_OK;
+    ((rc = rc != P2_OK ? rc
+                       : allow_dynamic_smem(k_alpha<RankBlock<Rs + 1>::cb, true, S, Rs + 1>, cap,
+                                            "k_alpha")),
+     ...);
+    ((rc = rc != P2_OK ? rc
+                       : allow_dynamic_smem(k_alpha<RankBlock<Rs + 1>::cb, false, S, Rs + 1>, cap,
+                                            "k_alpha")),
+     ...);
+    ((rc = rc != P2_OK ? rc
+                       : allow_dynamic_smem(k_beta_p<RankBlock<Rs + 1>::cb, S, S, Rs + 1>, cap,
+                                            "k_beta_p")),
+     ...);
+    return rc;
+}
+
 template <class S>
 static int configure_sparse(int cap) {
-    int rc = P2_OK;
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<8, true, S>, cap, "k_alpha");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<8, false, S>, cap, "k_alpha");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<16, true, S>, cap, "k_alpha");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<16, false, S>, cap, "k_alpha");
+    int rc = allow_rank_kernels<S>(cap, std::make_integer_sequence<int, P2_RT_MAX>{});
     if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<32, true, S>, cap, "k_alpha");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<32, false, S>, cap, "k_alpha");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<8, S>, cap, "k_beta_p");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<16, S>, cap, "k_beta_p");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<32, S>, cap, "k_beta_p");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<8, S, float>, cap, "k_beta_p");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<16, S, float>, cap, "k_beta_p");
@@ -1505,36 +1531,31 @@ static void mark(p2_ctx *c, int i) {
 
 // Gram G_k of Z_k = X_k V for an arbitrary batch X (projection of new
 // subjects onto the model's V).
-template <class S>
-static void launch_gram_t(const p2_ctx *c, const XView &X, const SmallState *st, dw *G,
+template <int CB, class S, int RT>
+static void launch_gram_k(const p2_ctx *c, const XView &X, const SmallState *st, dw *G,
                           cudaStream_t s) {
     const Launch L = plan(c);
     const int nt = L.alpha_warps * 32;
-    dim3 block(nt);
-    const S *V = Bufs<S>::V(c);
-    switch (comp_block(c->R)) {
-        case 8: {
-            dim3 grid(c->geo.nsm * resident_blocks(c, k_alpha<8, false, S>, nt, L.alpha_smem));
-            k_alpha<8, false, S><<<grid, block, L.alpha_smem, s>>>(X, nullptr, V, c->d_H, nullptr,
-                                                                  st, G, nullptr, nullptr,
-                                                                  nullptr, c->R);
-            break;
-        }
-        case 16: {
-            dim3 grid(c->geo.nsm * resident_blocks(c, k_alpha<16, false, S>, nt, L.alpha_smem));
-            k_alpha<16, false, S><<<grid, block, L.alpha_smem, s>>>(X, nullptr, V, c->d_H, nullptr,
-                                                                   st, G, nullptr, nullptr,
-                                                                   nullptr, c->R);
-            break;
-        }
-        default: {
-            dim3 grid(c->geo.nsm * resident_blocks(c, k_alpha<32, false, S>, nt, L.alpha_smem));
-            k_alpha<32, false, S><<<grid, block, L.alpha_smem, s>>>(X, nullptr, V, c->d_H, nullptr,
-                                                                   st, G, nullptr, nullptr,
-                                                                   nullptr, c->R);
-            break;
-        }
-    }
+    dim3 grid(c->geo.nsm * resident_blocks(c, k_alpha<CB, false, S, RT>, nt, L.alpha_smem));
+    k_alpha<CB, false, S, RT><<<grid, dim3(nt), L.alpha_smem, s>>>(
+        X, nullptr, Bufs<S>::V(c), c->d_H, nullptr, st, G, nullptr, nullptr, nullptr, c->R);
+}
+
+template <class S, int... Rs>
+static void launch_gram_ranks(const p2_ctx *c, const XView &X, const SmallState *st, dw *G,
+                              cudaStream_t s, std::integer_sequence<int, Rs...>) {
+    bool done = false;
+    ((c->R == Rs + 1 && !done
+          ? (launch_gram_k<RankBlock<Rs + 1>::cb, S, Rs + 1>(c, X, st, G, s), done = true)
+          : false),
+     ...);
+    if (!done) launch_gram_k<32, S, 0>(c, X, st, G, s);
+}
+
+template <class S>
+static void launch_gram_t(const p2_ctx *c, const XView &X, const SmallState *st, dw *G,
+                          cudaStream_t s) {
+    launch_gram_ranks<S>(c, X, st, G, s, std::make_integer_sequence<int, P2_RT_MAX>{});
 }
 
 // Gram G_k of Z_k = X_k V for an arbitrary batch X (projection of new
@@ -1548,33 +1569,29 @@ cudaError_t launch_gram(const p2_ctx *c, const XView &X, const SmallState *st, d
     return cudaGetLastError();
 }
 
+template <int CB, bool MODE3, class S, int RT>
+static void launch_alpha_k(p2_ctx *c, const Launch &L, const S *Vprev) {
+    const int nt = L.alpha_warps * 32;
+    dim3 grid(c->geo.nsm * resident_blocks(c, k_alpha<CB, MODE3, S, RT>, nt, L.alpha_smem));
+    k_alpha<CB, MODE3, S, RT><<<grid, dim3(nt), L.alpha_smem, c->stream>>>(
+        xview(c), Vprev, Bufs<S>::V(c), c->d_H, c->d_T, c->d_s, c->d_G, c->d_Gf, c->d_W, c->d_M3,
+        c->R);
+}
+
+template <bool MODE3, class S, int... Rs>
+static void launch_alpha_ranks(p2_ctx *c, const Launch &L, const S *Vprev,
+                               std::integer_sequence<int, Rs...>) {
+    bool done = false;
+    ((c->R == Rs + 1 && !done
+          ? (launch_alpha_k<RankBlock<Rs + 1>::cb, MODE3, S, Rs + 1>(c, L, Vprev), done = true)
+          : false),
+     ...);
+    if (!done) launch_alpha_k<32, MODE3, S, 0>(c, L, Vprev);
+}
+
 template <bool MODE3, class S>
 static void launch_alpha_t(p2_ctx *c, const Launch &L, const S *Vprev) {
-    const int nt = L.alpha_warps * 32;
-    dim3 block(nt);
-    XView X = xview(c);
-    const S *V = Bufs<S>::V(c);
-    const float *T = c->d_T;
-    switch (comp_block(c->R)) {
-        case 8: {
-            dim3 grid(c->geo.nsm * resident_blocks(c, k_alpha<8, MODE3, S>, nt, L.alpha_smem));
-            k_alpha<8, MODE3, S><<<grid, block, L.alpha_smem, c->stream>>>(
-                X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_Gf, c->d_W, c->d_M3, c->R);
-            break;
-        }
-        case 16: {
-            dim3 grid(c->geo.nsm * resident_blocks(c, k_alpha<16, MODE3, S>, nt, L.alpha_smem));
-            k_alpha<16, MODE3, S><<<grid, block, L.alpha_smem, c->stream>>>(
-                X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_Gf, c->d_W, c->d_M3, c->R);
-            break;
-        }
-        default: {
-            dim3 grid(c->geo.nsm * resident_blocks(c, k_alpha<32, MODE3, S>, nt, L.alpha_smem));
-            k_alpha<32, MODE3, S><<<grid, block, L.alpha_smem, c->stream>>>(
-                X, Vprev, V, c->d_H, T, c->d_s, c->d_G, c->d_Gf, c->d_W, c->d_M3, c->R);
-            break;
-        }
-    }
+    launch_alpha_ranks<MODE3, S>(c, L, Vprev, std::make_integer_sequence<int, P2_RT_MAX>{});
 }
 
 // pass alpha: with MODE3 Z_k from Vprev and Z'_k from V (the iteration), else
@@ -1587,31 +1604,26 @@ static void launch_alpha(p2_ctx *c, const Launch &L) {
         launch_alpha_t<MODE3, float>(c, L, MODE3 ? c->d_Vprev : nullptr);
 }
 
+template <int CB, class S, int RT>
+static void launch_beta_k(p2_ctx *c, const Launch &L) {
+    const int nt = L.beta_warps * 32;
+    dim3 grid(c->geo.nsm * resident_blocks(c, k_beta_p<CB, S, S, RT>, nt, L.beta_smem));
+    k_beta_p<CB, S, S, RT><<<grid, dim3(nt), L.beta_smem, c->stream>>>(
+        xview(c), Bufs<S>::V(c), c->d_H, c->d_T, c->d_W, Bufs<S>::P(c), c->R, 0);
+}
+
+template <class S, int... Rs>
+static void launch_beta_ranks(p2_ctx *c, const Launch &L, std::integer_sequence<int, Rs...>) {
+    bool done = false;
+    ((c->R == Rs + 1 && !done ? (launch_beta_k<RankBlock<Rs + 1>::cb, S, Rs + 1>(c, L), done = true)
+                              : false),
+     ...);
+    if (!done) launch_beta_k<32, S, 0>(c, L);
+}
+
 template <class S>
 static void launch_beta_p_t(p2_ctx *c, const Launch &L) {
-    const int nt = L.beta_warps * 32;
-    dim3 block(nt);
-    XView X = xview(c);
-    const S *V = Bufs<S>::V(c);
-    const float *T = c->d_T;
-    S *P = Bufs<S>::P(c);
-    switch (comp_block(c->R)) {
-        case 8: {
-            dim3 grid(c->geo.nsm * resident_blocks(c, k_beta_p<8, S>, nt, L.beta_smem));
-            k_beta_p<8, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R, 0);
-            break;
-        }
-        case 16: {
-            dim3 grid(c->geo.nsm * resident_blocks(c, k_beta_p<16, S>, nt, L.beta_smem));
-            k_beta_p<16, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R, 0);
-            break;
-        }
-        default: {
-            dim3 grid(c->geo.nsm * resident_blocks(c, k_beta_p<32, S>, nt, L.beta_smem));
-            k_beta_p<32, S><<<grid, block, L.beta_smem, c->stream>>>(X, V, c->d_H, T, c->d_W, P, c->R, 0);
-            break;
-        }
-    }
+    launch_beta_ranks<S>(c, L, std::make_integer_sequence<int, P2_RT_MAX>{});
 }
 
 static void launch_beta_p(p2_ctx *c, const Launch &L) {

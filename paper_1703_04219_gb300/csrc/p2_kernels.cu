@@ -565,12 +565,13 @@ __global__ void k_m2_columns(const double *__restrict__ segpart, const int64_t *
 // alpha pass writes for this kernel) or double (the allocation-free entry
 // point's interface).  Accumulations use float pairs: ~2^-48 relative error
 // and no FP64 instruction per subject.
-template <class GT>
+template <class GT, int RT = 0>
 static __device__ __forceinline__ void subject_stats(const float *__restrict__ T,
                                                      const GT *__restrict__ G,
                                                      const float *__restrict__ W,
                                                      const float *__restrict__ M3, double *part,
-                                                     int64_t K, int R, int with_m3) {
+                                                     int64_t K, int R_rt, int with_m3) {
+    const int R = RT > 0 ? RT : R_rt;   // RT > 0: the rank fixed at compile time
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_wm3[16];
     const int P = R * (R + 1) / 2;
@@ -674,13 +675,14 @@ __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__
     subject_stats<double>(T, G, W, M3, part, K, R, with_m3);
 }
 
+template <int RT>
 __global__ void __launch_bounds__(512, 2) k_subject_stats_gf(const float *__restrict__ T,
                                                           const float *__restrict__ Gf,
                                                           const float *__restrict__ W,
                                                           const float *__restrict__ M3,
                                                           double *part, int64_t K, int R,
                                                           int with_m3) {
-    subject_stats<float>(T, Gf, W, M3, part, K, R, with_m3);
+    subject_stats<float, RT>(T, Gf, W, M3, part, K, R, with_m3);
 }
 
 
@@ -1438,36 +1440,46 @@ static int allow_dynamic_smem(F *fn, int cap, const char *name) {
     return P2_OK;
 }
 
-// Ranks up to P2_RT_MAX run kernels compiled for that rank (loop bounds,
-// strides and shared-memory offsets constant: alpha pass -27% at R = 10);
-// larger ranks the generic kernels with CB = 32.
-#define P2_RT_MAX 16
+// Ranks 1 .. 16 and the multiples of 8 up to 64 run kernels compiled for
+// that rank (loop bounds, strides and shared-memory offsets constant: alpha
+// pass -27% at R = 10); other ranks the generic kernels with CB = 32.
+using RankList = std::integer_sequence<int, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16,
+                                       24, 32, 40, 48, 56, 64>;
 template <int R>
 struct RankBlock {
-    static constexpr int cb = R <= 8 ? 8 : 16;
+    static constexpr int cb = R <= 8 ? 8 : R <= 16 ? 16 : 32;
 };
 
 template <class S, int... Rs>
 static int allow_rank_kernels(int cap, std::integer_sequence<int, Rs...>) {
     int rc = P2_OK;
     ((rc = rc != P2_OK ? rc
-                       : allow_dynamic_smem(k_alpha<RankBlock<Rs + 1>::cb, true, S, Rs + 1>, cap,
+                       : allow_dynamic_smem(k_alpha<RankBlock<Rs>::cb, true, S, Rs>, cap,
                                             "k_alpha")),
      ...);
     ((rc = rc != P2_OK ? rc
-                       : allow_dynamic_smem(k_alpha<RankBlock<Rs + 1>::cb, false, S, Rs + 1>, cap,
+                       : allow_dynamic_smem(k_alpha<RankBlock<Rs>::cb, false, S, Rs>, cap,
                                             "k_alpha")),
      ...);
     ((rc = rc != P2_OK ? rc
-                       : allow_dynamic_smem(k_beta_p<RankBlock<Rs + 1>::cb, S, S, Rs + 1>, cap,
+                       : allow_dynamic_smem(k_beta_p<RankBlock<Rs>::cb, S, S, Rs>, cap,
                                             "k_beta_p")),
+     ...);
+    return rc;
+}
+
+template <int... Rs>
+static int allow_rank_stats(int cap, std::integer_sequence<int, Rs...>) {
+    int rc = P2_OK;
+    ((rc = rc != P2_OK ? rc
+                       : allow_dynamic_smem(k_subject_stats_gf<Rs>, cap, "k_subject_stats_gf")),
      ...);
     return rc;
 }
 
 template <class S>
 static int configure_sparse(int cap) {
-    int rc = allow_rank_kernels<S>(cap, std::make_integer_sequence<int, P2_RT_MAX>{});
+    int rc = allow_rank_kernels<S>(cap, RankList{});
     if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<32, true, S>, cap, "k_alpha");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_alpha<32, false, S>, cap, "k_alpha");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<32, S>, cap, "k_beta_p");
@@ -1482,12 +1494,13 @@ int configure_kernels(p2_ctx *c) {
     int rc = P2_OK;
     if (rc == P2_OK) rc = configure_sparse<float>(cap);
     if (rc == P2_OK) rc = configure_sparse<bf16_t>(cap);
+    if (rc == P2_OK) rc = allow_rank_stats(cap, RankList{});
     if (rc == P2_OK) rc = polar_configure(c);
     if (rc == P2_OK) rc = allow_dynamic_smem(k_solve_h, cap, "k_solve_h");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_solve_v_pinv, cap, "k_solve_v_pinv");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_fin_v, cap, "k_fin_v");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_subject_stats, cap, "k_subject_stats");
-    if (rc == P2_OK) rc = allow_dynamic_smem(k_subject_stats_gf, cap, "k_subject_stats_gf");
+    if (rc == P2_OK) rc = allow_dynamic_smem(k_subject_stats_gf<0>, cap, "k_subject_stats_gf");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_eig_orth, cap, "k_eig_orth");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_eig_ritz<float>, cap, "k_eig_ritz");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_eig_ritz<bf16_t>, cap, "k_eig_ritz");
@@ -1545,8 +1558,8 @@ template <class S, int... Rs>
 static void launch_gram_ranks(const p2_ctx *c, const XView &X, const SmallState *st, dw *G,
                               cudaStream_t s, std::integer_sequence<int, Rs...>) {
     bool done = false;
-    ((c->R == Rs + 1 && !done
-          ? (launch_gram_k<RankBlock<Rs + 1>::cb, S, Rs + 1>(c, X, st, G, s), done = true)
+    ((c->R == Rs && !done
+          ? (launch_gram_k<RankBlock<Rs>::cb, S, Rs>(c, X, st, G, s), done = true)
           : false),
      ...);
     if (!done) launch_gram_k<32, S, 0>(c, X, st, G, s);
@@ -1555,7 +1568,7 @@ static void launch_gram_ranks(const p2_ctx *c, const XView &X, const SmallState 
 template <class S>
 static void launch_gram_t(const p2_ctx *c, const XView &X, const SmallState *st, dw *G,
                           cudaStream_t s) {
-    launch_gram_ranks<S>(c, X, st, G, s, std::make_integer_sequence<int, P2_RT_MAX>{});
+    launch_gram_ranks<S>(c, X, st, G, s, RankList{});
 }
 
 // Gram G_k of Z_k = X_k V for an arbitrary batch X (projection of new
@@ -1582,8 +1595,8 @@ template <bool MODE3, class S, int... Rs>
 static void launch_alpha_ranks(p2_ctx *c, const Launch &L, const S *Vprev,
                                std::integer_sequence<int, Rs...>) {
     bool done = false;
-    ((c->R == Rs + 1 && !done
-          ? (launch_alpha_k<RankBlock<Rs + 1>::cb, MODE3, S, Rs + 1>(c, L, Vprev), done = true)
+    ((c->R == Rs && !done
+          ? (launch_alpha_k<RankBlock<Rs>::cb, MODE3, S, Rs>(c, L, Vprev), done = true)
           : false),
      ...);
     if (!done) launch_alpha_k<32, MODE3, S, 0>(c, L, Vprev);
@@ -1591,7 +1604,7 @@ static void launch_alpha_ranks(p2_ctx *c, const Launch &L, const S *Vprev,
 
 template <bool MODE3, class S>
 static void launch_alpha_t(p2_ctx *c, const Launch &L, const S *Vprev) {
-    launch_alpha_ranks<MODE3, S>(c, L, Vprev, std::make_integer_sequence<int, P2_RT_MAX>{});
+    launch_alpha_ranks<MODE3, S>(c, L, Vprev, RankList{});
 }
 
 // pass alpha: with MODE3 Z_k from Vprev and Z'_k from V (the iteration), else
@@ -1615,7 +1628,7 @@ static void launch_beta_k(p2_ctx *c, const Launch &L) {
 template <class S, int... Rs>
 static void launch_beta_ranks(p2_ctx *c, const Launch &L, std::integer_sequence<int, Rs...>) {
     bool done = false;
-    ((c->R == Rs + 1 && !done ? (launch_beta_k<RankBlock<Rs + 1>::cb, S, Rs + 1>(c, L), done = true)
+    ((c->R == Rs && !done ? (launch_beta_k<RankBlock<Rs>::cb, S, Rs>(c, L), done = true)
                               : false),
      ...);
     if (!done) launch_beta_k<32, S, 0>(c, L);
@@ -1623,7 +1636,23 @@ static void launch_beta_ranks(p2_ctx *c, const Launch &L, std::integer_sequence<
 
 template <class S>
 static void launch_beta_p_t(p2_ctx *c, const Launch &L) {
-    launch_beta_ranks<S>(c, L, std::make_integer_sequence<int, P2_RT_MAX>{});
+    launch_beta_ranks<S>(c, L, RankList{});
+}
+
+// mode-1 statistics (k_subject_stats_gf) compiled for the rank when it is in RankList
+template <int... Rs>
+static void launch_stats_ranks(p2_ctx *c, int nb, int nt, size_t ssm, int with_fit,
+                               std::integer_sequence<int, Rs...>) {
+    bool done = false;
+    ((c->R == Rs && !done
+          ? (k_subject_stats_gf<Rs><<<nb, nt, ssm, c->stream>>>(
+                 c->d_T, c->d_Gf, c->d_W, c->d_M3, c->d_part, c->X.K, c->R, with_fit),
+             done = true)
+          : false),
+     ...);
+    if (!done)
+        k_subject_stats_gf<0><<<nb, nt, ssm, c->stream>>>(c->d_T, c->d_Gf, c->d_W, c->d_M3,
+                                                          c->d_part, c->X.K, c->R, with_fit);
 }
 
 static void launch_beta_p(p2_ctx *c, const Launch &L) {
@@ -1728,8 +1757,7 @@ static int enqueue_qstep(p2_ctx *c, int with_fit) {
     const size_t scap = (size_t)c->geo.smem_optin - 16 * sizeof(double) - 16 * P2_RMAX * sizeof(float);
     while (nw > 1 && cta + nw * stats_warp_bytes(R) > scap) --nw;
     const size_t ssm = cta + nw * stats_warp_bytes(R);
-    k_subject_stats_gf<<<nb, nw * 32, ssm, s>>>(c->d_T, c->d_Gf, c->d_W, c->d_M3, c->d_part, K,
-                                                R, with_fit);
+    launch_stats_ranks(c, nb, nw * 32, ssm, with_fit, RankList{});
     P2_LAUNCH_CHECK("k_subject_stats");
     mark(c, 6);
     k_fin_w<<<1, 256, 0, s>>>(c->d_part, nb, c->d_s, R, with_fit);

@@ -94,6 +94,7 @@ class ClockSampler:
         self.gpu_id = str(gpu_id)
         self.proc = None
         self.path = None
+        self.skip = 0
 
     def start(self):
         try:
@@ -102,9 +103,26 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", self.gpu_id], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-lms", "50", "-i", self.gpu_id], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def _lines(self):
+        try:
+            with open(self.path) as f:
+                return sum(1 for ln in f if ln.endswith("\n"))
+        except OSError:
+            return 0
+
+    def mark_region_start(self, timeout=3.0):
+        """Wait (bounded) for the sampler's first line, then remember how many
+        lines precede the timed region so that only later samples count."""
+        if self.proc is None:
+            return
+        t0 = time.time()
+        while self._lines() == 0 and time.time() - t0 < timeout and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.skip = self._lines()
 
     def stop(self):
         if self.proc is None:
@@ -118,23 +136,27 @@ class ClockSampler:
         sm, mx, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         with open(self.path) as f:
-            for line in f:
-                p = [x.strip() for x in line.split(",")]
-                if len(p) < 9:
-                    continue
-                try:
-                    sm.append(float(p[1]))
-                    mx.append(float(p[2]))
-                except ValueError:
-                    continue
-                for n, v in zip(names, p[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(n)
+            lines = [ln for ln in f if ln.endswith("\n")]
+        # samples taken during the timed region; the last earlier one if none
+        in_region = len(lines) > self.skip
+        lines = lines[self.skip:] if in_region else lines[max(self.skip - 1, 0):self.skip]
+        for line in lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
         os.unlink(self.path)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+                "in_timed_region": in_region, "reasons": sorted(reasons)}
 
 
 def _dist():
@@ -372,11 +394,12 @@ def timed_steps(m, stream, steps, pg=None, clocks=None):
     phase_sum = {k: 0.0 for k in PHASES}
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    if clocks:
+        clocks.start()
+        clocks.mark_region_start()
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    if clocks:
-        clocks.start()
     ev0.record(stream)
     for _ in range(steps):
         m.iterate(1, want_fit=False)

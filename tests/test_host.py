@@ -1,4 +1,5 @@
-"""Host logic: the seeded generator and the multi-rank bench aggregation (gloo)."""
+"""Host logic: the seeded generator, the multi-rank bench aggregation (gloo) and
+the bench's clock record."""
 import os
 
 import numpy as np
@@ -64,3 +65,51 @@ def test_bench_aggregation_over_two_gloo_ranks():
     for rank, t, v in res:
         assert t == 11.0                                     # max over ranks
         assert abs(v - 2 * 1000 * 4 / 0.011) < 1e-6          # both replicas' work / slowest time
+
+
+class _FakeSampler:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        pass
+
+    def poll(self):
+        return None
+
+
+def _bench_module():
+    import importlib.util
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.mark.parametrize("lines,skip,want", [
+    # two samples inside the timed region: the idle one before it is ignored
+    (["0, 1500, 2070, 300, 0x0, Not Active, Not Active, Not Active, Not Active",
+      "0, 2070, 2070, 900, 0x4, Not Active, Not Active, Not Active, Active",
+      "0, 2060, 2070, 950, 0x0, Not Active, Not Active, Not Active, Not Active"], 1,
+     dict(sm_mhz=2065.0, samples=2, in_timed_region=True, reasons=["sw_power_cap"])),
+    # none inside: the last earlier sample is reported, flagged as such
+    (["0, 1500, 2070, 300, 0x0, Not Active, Not Active, Not Active, Not Active"], 1,
+     dict(sm_mhz=1500.0, samples=1, in_timed_region=False, reasons=[])),
+    # a thermal slowdown inside the region is reported
+    (["0, 2070, 2070, 300, 0x0, Not Active, Not Active, Not Active, Not Active",
+      "0, 1800, 2070, 1300, 0x20, Not Active, Active, Not Active, Not Active"], 1,
+     dict(sm_mhz=1800.0, samples=1, in_timed_region=True, reasons=["hw_thermal_slowdown"])),
+])
+def test_clock_record_counts_only_samples_in_the_timed_region(tmp_path, lines, skip, want):
+    """bench.py's clock record: nvidia-smi lines written before the timed
+    region starts are skipped (unless no later line exists)."""
+    bench = _bench_module()
+    c = bench.ClockSampler(0)
+    c.path = str(tmp_path / "clocks.csv")
+    with open(c.path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    c.proc, c.fh, c.skip = _FakeSampler(), open(os.devnull, "w"), skip
+    got = c.stop()
+    for k, v in want.items():
+        assert got[k] == v, (k, got)

@@ -10,7 +10,7 @@
 
 namespace p2 {
 
-template <int RB, int PG>
+template <int RB, int PG, int RT = 0>
 static void launch_grp(const p2_ctx *c, const dw *G, const float *W, SmallState *st, float *T,
                        int64_t K, cudaStream_t s, double rtol2, const int32_t *order,
                        int32_t *qrcnt) {
@@ -25,18 +25,18 @@ static void launch_grp(const p2_ctx *c, const dw *G, const float *W, SmallState 
     const int threads = ((spb + gpw - 1) / gpw) * 32;
     const size_t smem = hbytes + (size_t)spb * per;
     const int64_t nblk = (K + spb - 1) / spb;
-    k_polar_grp<RB, PG><<<(unsigned)nblk, threads, smem, s>>>(G, W, st, T, K, R, (float)rtol2, spb,
+    k_polar_grp<RB, PG, RT><<<(unsigned)nblk, threads, smem, s>>>(G, W, st, T, K, R, (float)rtol2, spb,
                                                                order, qrcnt);
 }
 
 // dynamic shared memory allowed: the opt-in maximum less the kernel's static
 // shared memory
-template <int RB, int PG>
+template <int RB, int PG, int RT = 0>
 static cudaError_t allow_grp(int cap) {
     cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, k_polar_grp<RB, PG>);
+    cudaError_t e = cudaFuncGetAttributes(&a, k_polar_grp<RB, PG, RT>);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_polar_grp<RB, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_polar_grp<RB, PG, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 cap - (int)a.sharedSizeBytes);
 }
 
@@ -50,6 +50,16 @@ cudaError_t polar_grp_configure(int cap) {
     if (e == cudaSuccess) e = allow_grp<32, 8>(cap);
     if (e == cudaSuccess) e = allow_grp<48, 16>(cap);
     if (e == cudaSuccess) e = allow_grp<64, 16>(cap);
+    if (e == cudaSuccess) e = allow_grp<16, 8, 13>(cap);
+    if (e == cudaSuccess) e = allow_grp<16, 8, 14>(cap);
+    if (e == cudaSuccess) e = allow_grp<16, 8, 15>(cap);
+    if (e == cudaSuccess) e = allow_grp<16, 8, 16>(cap);
+    if (e == cudaSuccess) e = allow_grp<24, 8, 24>(cap);
+    if (e == cudaSuccess) e = allow_grp<32, 8, 32>(cap);
+    if (e == cudaSuccess) e = allow_grp<48, 16, 40>(cap);
+    if (e == cudaSuccess) e = allow_grp<48, 16, 48>(cap);
+    if (e == cudaSuccess) e = allow_grp<64, 16, 56>(cap);
+    if (e == cudaSuccess) e = allow_grp<64, 16, 64>(cap);
     return e;
 }
 
@@ -57,6 +67,21 @@ cudaError_t launch_polar_grp(const p2_ctx *c, const dw *G, const float *W, Small
                              float *T, int64_t K, cudaStream_t s, double rtol2,
                              const int32_t *order, int32_t *qrcnt) {
     const int R = c->R;
+    // ranks 13 .. 16 and the multiples of 8 run an instance compiled for the
+    // rank (loop bounds and offsets constant), the others the generic one
+    switch (R) {
+        case 13: launch_grp<16, 8, 13>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
+        case 14: launch_grp<16, 8, 14>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
+        case 15: launch_grp<16, 8, 15>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
+        case 16: launch_grp<16, 8, 16>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
+        case 24: launch_grp<24, 8, 24>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
+        case 32: launch_grp<32, 8, 32>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
+        case 40: launch_grp<48, 16, 40>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
+        case 48: launch_grp<48, 16, 48>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
+        case 56: launch_grp<64, 16, 56>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
+        case 64: launch_grp<64, 16, 64>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
+        default: break;
+    }
     if (R <= 16)
         launch_grp<16, 8>(c, G, W, st, T, K, s, rtol2, order, qrcnt);
     else if (R <= 24)

@@ -59,12 +59,13 @@ static __device__ __forceinline__ unsigned long long group_or(unsigned mask, uns
     return v;
 }
 
-template <int RB, int PG>
+template <int RB, int PG, int RT = 0>
 __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                                                       const float *__restrict__ W, SmallState *st,
-                                                      float *T, int64_t K, int R, float rtol2,
+                                                      float *T, int64_t K, int R_rt, float rtol2,
                                                       int spb, const int32_t *__restrict__ order,
                                                       int32_t *qrcnt) {
+    const int R = RT > 0 ? RT : R_rt;   // RT > 0: the rank fixed at compile time
     constexpr int RPL = RB / PG;                     // rows per lane
     extern __shared__ __align__(16) dw smg[];
     __shared__ int s_eh;

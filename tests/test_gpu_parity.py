@@ -42,7 +42,9 @@ def _one_step(p2, X, R, seed):
 @pytest.mark.parametrize("name,K,R", [("tiny", 200, 5), ("tiny", 200, 1), ("tiny", 97, 8),
                                       ("c63m", 3000, 10), ("c250m", 400, 40),
                                       ("tiny", 150, 13), ("tiny", 120, 16), ("c250m", 300, 24),
-                                      ("tiny", 60, 64), ("c555m", 150, 40)])
+                                      ("tiny", 60, 64), ("c555m", 150, 40),
+                                      # ranks outside the compiled list: the generic kernels
+                                      ("c250m", 300, 20), ("c250m", 200, 33)])
 def test_one_step_parity(p2, name, K, R):
     X = synth.generate(name, K=K)
     out = _one_step(p2, X, R, seed=11)

@@ -126,7 +126,8 @@ int p2_load_slices(p2_ctx *ctx, int64_t K, int32_t J, const int64_t *subj_ptr,
  * Flood, OOPSLA 2014; mixer constants 0xBF58476D1CE4E5B9, 0x94D049BB133111EB)
  * of the state mix(seed + g (t + 1)) ^ mix(i g + t), with t = 5 + 16 a,
  * g = 0x9E3779B97F4A7C15 and mix the SplitMix64 finaliser.  Some but not all
- * NULL: P2_EINVAL.
+ * NULL: P2_EINVAL.  Any other error leaves the context uninitialised
+ * (p2_iterate returns P2_ESTATE until an initialisation succeeds).
  */
 int p2_init(p2_ctx *ctx, const float *H0, const float *V0, const float *W0);
 
@@ -148,9 +149,11 @@ int p2_init(p2_ctx *ctx, const float *H0, const float *V0, const float *W0);
  * device scratch: 4 J b doubles and (N + S) w doubles (N stacked rows, S
  * column segments of the mode-2 layout), the product's column width w <= b
  * chosen so that N w doubles take at most a quarter of the free device
- * memory and 16 GiB.  n_done (nullable, host) receives the iterations run.  Synchronises
- * after every product.  P2_EINVAL for J < R, max_iter < 1 or tol < 0;
- * P2_ENUMERIC if an eigen step failed to converge.
+ * memory and 16 GiB.  n_done (nullable, host) receives the iterations run.
+ * Synchronises after every product.  P2_EINVAL for J < R, max_iter < 1 or
+ * tol < 0 (the context is left as it was); P2_ENUMERIC if an eigen step
+ * failed to converge.  Any error other than P2_EINVAL leaves the context
+ * uninitialised.
  */
 int p2_init_eig(p2_ctx *ctx, int32_t max_iter, double tol, int32_t *n_done);
 

@@ -209,6 +209,9 @@ static int finish_init(p2_ctx *c) {
 }
 
 static int set_factors_impl(p2_ctx *c, const float *H, const float *V, const float *W) {
+    // the factors are replaced from here on: until finish_init succeeds the
+    // context holds no consistent state, so p2_iterate must refuse
+    c->inited = false;
     const int R = c->R;
     const int32_t J = c->X.J;
     const int64_t K = c->X.K;
@@ -470,6 +473,7 @@ int p2_init_eig(p2_ctx *c, int32_t max_iter, double tol, int32_t *n_done) {
     const int32_t J = c->X.J;
     if (J < R) return fail(P2_EINVAL, "p2_init_eig: J < R (fewer columns than components)");
     P2_CUDA_TRY(cudaSetDevice(c->opt.device));
+    c->inited = false;                     // as in set_factors_impl
     // block width: oversampled so that the leading R Ritz vectors converge at
     // lambda_{b+1} / lambda_R; at most the CTA eigen-solver's size and J
     const int b = std::min(std::min(std::max(2 * R, R + 8), (int)P2_RMAX), (int)J);

@@ -1,7 +1,7 @@
 """The library's CUDA kernels run on the CPU emulator (tests/cpu_emu) under
 AddressSanitizer: one ALS iteration at R = 5 and R = 10 (lane-per-subject
 Procrustes), at R = 13 and R = 40 (grouped Procrustes, eight and sixteen lanes
-per subject), at R = 5 with bfloat16 storage and in the non-negative
+per subject), at R = 20 (a rank outside the compiled list: generic kernels), at R = 5 with bfloat16 storage and in the non-negative
 variant, a projection of new
 subjects, U_k = Q_k H for a range of subjects, the seeded initialisation
 with the stopping rule, and the rational start (subspace iteration in FP64).
@@ -24,6 +24,7 @@ CASES = {
     "iterate_r10": ["iterate", "tiny", "24", "10"],
     "iterate_r13": ["iterate", "tiny", "16", "13"],
     "iterate_r40": ["iterate", "tiny", "16", "40"],
+    "iterate_r20": ["iterate", "c250m", "12", "20"],     # outside the rank-compiled list
     "iterate_r5_bf16": ["iterate", "tiny", "24", "5", "bf16"],
     "iterate_r5_nonneg": ["iterate", "tiny", "24", "5", "nonneg"],
     "project_r12": ["project", "12", "3"],
@@ -74,7 +75,8 @@ def _result(runs, name):
     return json.loads(so.strip().splitlines()[-1])
 
 
-@pytest.mark.parametrize("name", ["iterate_r5", "iterate_r10", "iterate_r13", "iterate_r40"])
+@pytest.mark.parametrize("name", ["iterate_r5", "iterate_r10", "iterate_r13", "iterate_r40",
+                                  "iterate_r20"])
 def test_emulated_iteration_is_in_bounds_and_matches_oracle(emulated_runs, name):
     err = _result(emulated_runs, name)
     for key in ("M1", "M2", "M3", "H", "V", "W"):

@@ -136,6 +136,13 @@ def rational_case(R, K):
         H, V, W = m.factors()
         fit = m.iterate(1)
         H1, V1, W1 = m.factors()
+        # an argument error leaves the context as it was: it still iterates
+        try:
+            m.init_eig(max_iter=0)
+            einval = 0.0
+        except p2.P2Error as e:
+            einval = float(e.code == p2.P2_EINVAL)
+        still = float(np.isfinite(m.iterate(1)))
     del os.environ["EMU_FREE_BYTES"]
     V64 = V.astype(np.float64)
     ref = P.als_iteration(blocks, np.eye(R), V64, np.ones((X.K, R)))
@@ -160,7 +167,8 @@ def rational_case(R, K):
             "sin2": sin2, "H1": rel_fro(H1, ref["H"]), "V1": rel_fro(V1, ref["V"]),
             "W1": rel_fro(W1, ref["W"]), "fit": abs(fit - P.fit_from_loss(ref["loss"], nx2)),
             "def_n": nd, "def_orth": float(np.abs(Vd.T @ Vd - np.eye(5)).max()),
-            "def_lead": rel_fro(Vd[:, :3], Vd0[:, :3]), "def_fit_finite": float(np.isfinite(fitd))}
+            "def_lead": rel_fro(Vd[:, :3], Vd0[:, :3]), "def_fit_finite": float(np.isfinite(fitd)),
+            "einval": einval, "still_iterates": still}
 
 
 if __name__ == "__main__":

@@ -134,3 +134,4 @@ def test_emulated_rational_start_is_in_bounds_and_matches_oracle(emulated_runs):
     assert 1 <= out["def_n"] < 50, out
     assert out["def_orth"] < 1e-6 and out["def_lead"] < 1e-6, out
     assert out["def_fit_finite"] == 1.0
+    assert out["einval"] == 1.0 and out["still_iterates"] == 1.0

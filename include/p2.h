@@ -279,18 +279,25 @@ int p2_device_bytes(p2_ctx *ctx, int64_t *bytes);
  *   T    device, K x R x R FP32: per-subject Procrustes transforms, the layout
  *        p2_get_procrustes returns
  *   G    device, K x R(R+1)/2 FP64: per-subject Gram Z_k^T Z_k of Z_k = X_k V,
- *        lower triangle row by row (element (i, j), j <= i, at i(i+1)/2 + j)
+ *        lower triangle row by row (element (i, j), j <= i, at i(i+1)/2 + j);
+ *        each entry is rounded to FP32 before the products, as in the
+ *        library's own mode-1 pass
  *   W    device, K x R FP32
  *   M1   device, R x R FP64 out: sum_k (T_k G_k) * 1 W(k,:)  (as p2_get_mttkrp
  *        mode 1 returns for the iteration that starts from this state)
  *   WtW  device, R x R FP64 out, or NULL
  *   stream  cudaStream_t to enqueue on (NULL: the legacy default stream)
- * Limits and behaviour: 1 <= R <= 16 (P2_EINVAL otherwise); the scratch is one
- * fixed 541,696-byte array per device, held until the process exits, so calls
- * that overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller.  The first call on a device looks up the scratch
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Returns after enqueueing.
+ * Limits and behaviour: 1 <= R <= 16 (P2_EINVAL otherwise); every buffer
+ * must be device (or managed) memory of the current device, and where the
+ * driver reports the extent of the allocation that holds it, large enough
+ * for the sizes above (P2_EINVAL otherwise, before anything is enqueued).
+ * The scratch is one fixed 541,696-byte array per device, held until the
+ * process exits, so calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  Every call looks up
+ * the scratch's device address (cudaGetSymbolAddress, which allocates
+ * nothing); the first call on a device also loads the library's kernels
+ * there, so make that first call before any stream capture.  Returns after
+ * enqueueing.
  */
 int p2_mode1_stats_noalloc(int64_t K, int32_t R, const float *T, const double *G,
                            const float *W, double *M1, double *WtW, void *stream);

@@ -232,14 +232,33 @@ def p2_mode1_stats_noalloc(K, R, T, G, W, M1, WtW=None, stream=None):
     """Allocation-free mode-1 MTTKRP and W^TW from device tensors (see include/p2.h).
 
     T (K x R x R float32), G (K x R(R+1)/2 float64), W (K x R float32) and the
-    outputs M1, WtW (R x R float64) are CUDA tensors; stream is a cudaStream_t
-    handle (default: torch's current stream).  For callers that cannot
-    allocate device memory at the point of the call.
+    outputs M1, WtW (R x R float64) are contiguous CUDA tensors on the current
+    device; stream is a cudaStream_t handle (default: torch's current stream).
+    For callers that cannot allocate device memory at the point of the call.
+    Tensors of another kind, device, dtype or size raise ValueError here,
+    before the library sees them.
     """
+    import torch
+    K, R = int(K), int(R)
+    want = {"T": (T, torch.float32, K * R * R), "G": (G, torch.float64, K * R * (R + 1) // 2),
+            "W": (W, torch.float32, K * R), "M1": (M1, torch.float64, R * R)}
+    if WtW is not None:
+        want["WtW"] = (WtW, torch.float64, R * R)
+    dev = torch.cuda.current_device()
+    for name, (t, dtype, n) in want.items():
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+        if t.numel() != n:
+            raise ValueError(f"{name} must hold {n} elements, got {t.numel()}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
     if stream is None:
-        import torch
         stream = torch.cuda.current_stream().cuda_stream
-    _check(lib.p2_mode1_stats_noalloc(int(K), int(R), _ptr(T), _ptr(G), _ptr(W), _ptr(M1),
+    _check(lib.p2_mode1_stats_noalloc(K, R, _ptr(T), _ptr(G), _ptr(W), _ptr(M1),
                                       _ptr(WtW), ctypes.c_void_p(stream)),
            "p2_mode1_stats_noalloc")
 

@@ -51,27 +51,33 @@ static XView xview(const p2_ctx *c) {
                  c->R > 16 ? c->d_sorder : nullptr};
 }
 
+// The error-free transformations below hold only if every rounding happens
+// exactly as written: a product that the compiler contracted with the
+// following sum into one FMA (nvcc's default --fmad=true allows it) would
+// leave TwoSum's error term wrong.  So every operation goes through the
+// __f*_rn intrinsics of p2_dw.cuh (f_add, f_sub, f_mul, f_fma), which are
+// never contracted or reassociated.
 // a + b = s + e exactly (Knuth's TwoSum)
 static __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float bv = s - a;
-    e = (a - (s - bv)) + (b - bv);
+    s = f_add(a, b);
+    const float bv = f_sub(s, a);
+    e = f_add(f_sub(a, f_sub(s, bv)), f_sub(b, bv));
 }
 // (hi, lo) += x: an unevaluated float pair, error-free up to the rounding of lo
 static __device__ __forceinline__ void pair_add(float &hi, float &lo, float x) {
     float t, e;
     two_sum(hi, x, t, e);
     hi = t;
-    lo += e;
+    lo = f_add(lo, e);
 }
 // (hi, lo) += a * b, the product split exactly with an FMA (Dekker's TwoProduct)
 static __device__ __forceinline__ void pair_fma(float &hi, float &lo, float a, float b) {
-    const float p = a * b;
-    const float pe = fmaf(a, b, -p);
+    const float p = f_mul(a, b);
+    const float pe = f_fma(a, b, -p);
     float t, e;
     two_sum(hi, p, t, e);
     hi = t;
-    lo += e + pe;
+    lo = f_add(lo, f_add(e, pe));
 }
 
 // z rows of up to 32 consecutive rows: z1[i][:] = X(row i, :) V1 and, when
@@ -319,13 +325,14 @@ __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 3) k_alpha(XView X, const 
 #pragma unroll 4
                 for (int i = 0; i < nr; ++i) {
                     const float a = zn[i * RS + r], b = zn[i * RS + s];
-                    const float pa = a * b;
-                    const float pe = fmaf(a, b, -pa);           // a*b = pa + pe exactly
-                    const float t = sh + pa;                    // TwoSum(sh, pa)
-                    const float bv = t - sh;
-                    const float er = (sh - (t - bv)) + (pa - bv);
+                    // TwoProduct and TwoSum with uncontracted roundings (see two_sum)
+                    const float pa = f_mul(a, b);
+                    const float pe = f_fma(a, b, -pa);          // a*b = pa + pe exactly
+                    const float t = f_add(sh, pa);              // TwoSum(sh, pa)
+                    const float bv = f_sub(t, sh);
+                    const float er = f_add(f_sub(sh, f_sub(t, bv)), f_sub(pa, bv));
                     sh = t;
-                    sl += er + pe;
+                    sl = f_add(sl, f_add(er, pe));
                 }
                 Ghi[p] = sh;
                 Glo[p] = sl;

@@ -12,6 +12,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <stdint.h>
 
 #include "p2_internal.cuh"
 
@@ -24,28 +25,75 @@ namespace p2 {
 // 128 x 529 doubles = 541,696 bytes, held by every GPU that loads the library
 static __device__ __align__(256) double g_na_scratch[P2_NA_BLOCKS * P2_NA_STRIDE];
 
-// Host-side copies of the scratch's device address, one per device.  The
-// array's name is only a host stand-in: kernels must be given this address.
-static std::mutex g_na_mutex;
-static double *g_na_ptr[64] = {};
+// The array's name is only a host stand-in: kernels must be given its device
+// address, looked up on every call for the current device (the lookup
+// allocates nothing, and a fresh lookup stays valid after a device reset).
+static int na_scratch(double **out) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_na_scratch);
+    if (e != cudaSuccess || !ptr) {
+        set_error("p2_mode1_stats_noalloc: cudaGetSymbolAddress failed: %s",
+                  cudaGetErrorString(e));
+        return P2_ECUDA;
+    }
+    *out = (double *)ptr;
+    return P2_OK;
+}
 
-static int na_scratch(int dev, double **out) {
-    if (dev < 0 || dev >= 64) {
-        set_error("p2_mode1_stats_noalloc: device ordinal %d out of range", dev);
+// cuMemGetAddressRange from the driver, looked up once (NULL if unavailable):
+// the base and size of the allocation that holds a device address.
+typedef int (*mem_range_fn)(unsigned long long *, size_t *, unsigned long long);
+static mem_range_fn na_range_fn() {
+    static std::once_flag once;
+    static mem_range_fn fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (mem_range_fn)f;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// A caller buffer must be device (or managed) memory of the current device
+// and, where the driver reports the allocation's extent, hold `bytes` bytes.
+// Host pointers, pointers of another device and buffers that end past their
+// allocation are rejected before anything is enqueued.
+static int na_check_buffer(const void *p, size_t bytes, int dev, const char *name) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("p2_mode1_stats_noalloc: %s is not a CUDA pointer (%s)", name,
+                  cudaGetErrorString(e));
         return P2_EINVAL;
     }
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_na_scratch);
-        if (e != cudaSuccess || !ptr) {
-            set_error("p2_mode1_stats_noalloc: cudaGetSymbolAddress failed: %s",
-                      cudaGetErrorString(e));
-            return P2_ECUDA;
-        }
-        g_na_ptr[dev] = (double *)ptr;
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
+        set_error("p2_mode1_stats_noalloc: %s is not device memory", name);
+        return P2_EINVAL;
     }
-    *out = g_na_ptr[dev];
+    if (a.device != dev) {
+        set_error("p2_mode1_stats_noalloc: %s is on device %d, the current device is %d", name,
+                  a.device, dev);
+        return P2_EINVAL;
+    }
+    mem_range_fn range = na_range_fn();
+    if (range && bytes > 0) {
+        unsigned long long base = 0;
+        size_t size = 0;
+        if (range(&base, &size, (unsigned long long)(uintptr_t)p) == 0) {
+            const unsigned long long a0 = (unsigned long long)(uintptr_t)p;
+            if (a0 < base || a0 - base + bytes > size) {
+                set_error("p2_mode1_stats_noalloc: %s needs %zu bytes, its allocation holds %llu "
+                          "from that address", name, bytes, base + size - a0);
+                return P2_EINVAL;
+            }
+        }
+    }
     return P2_OK;
 }
 
@@ -78,8 +126,18 @@ extern "C" int p2_mode1_stats_noalloc(int64_t K, int32_t R, const float *T, cons
         return set_error("p2_mode1_stats_noalloc: NULL pointer"), P2_EINVAL;
     int dev = 0;
     P2_CUDA_TRY(cudaGetDevice(&dev));
+    const size_t RR = (size_t)R * R, Pk = (size_t)R * (R + 1) / 2;
+    int rc = P2_OK;
+    if (K > 0) {
+        if (rc == P2_OK) rc = na_check_buffer(T, (size_t)K * RR * sizeof(float), dev, "T");
+        if (rc == P2_OK) rc = na_check_buffer(G, (size_t)K * Pk * sizeof(double), dev, "G");
+        if (rc == P2_OK) rc = na_check_buffer(W, (size_t)K * R * sizeof(float), dev, "W");
+    }
+    if (rc == P2_OK) rc = na_check_buffer(M1, RR * sizeof(double), dev, "M1");
+    if (rc == P2_OK && WtW) rc = na_check_buffer(WtW, RR * sizeof(double), dev, "WtW");
+    if (rc != P2_OK) return rc;
     double *scratch = nullptr;
-    int rc = na_scratch(dev, &scratch);
+    rc = na_scratch(&scratch);
     if (rc != P2_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const int P = R * (R + 1) / 2;

@@ -106,6 +106,22 @@ template <class F> inline cudaError_t cudaOccupancyMaxActiveBlocksPerMultiproces
 template <class F> inline cudaError_t cudaFuncGetAttributes(cudaFuncAttributes *a, F) { *a = cudaFuncAttributes{}; return cudaSuccess; }
 template <class F> inline cudaError_t cudaFuncSetAttribute(F, cudaFuncAttribute, int) { return cudaSuccess; }
 template <class T> inline cudaError_t cudaGetSymbolAddress(void **p, T &sym) { *p = (void *)&sym; return cudaSuccess; }
+// every pointer counts as device memory of device 0; no driver entry points
+enum cudaMemoryType { cudaMemoryTypeUnregistered = 0, cudaMemoryTypeHost = 1,
+                      cudaMemoryTypeDevice = 2, cudaMemoryTypeManaged = 3 };
+struct cudaPointerAttributes { cudaMemoryType type; int device; void *devicePointer; void *hostPointer; };
+inline cudaError_t cudaPointerGetAttributes(cudaPointerAttributes *a, const void *p) {
+    *a = cudaPointerAttributes{cudaMemoryTypeDevice, 0, (void *)p, nullptr};
+    return cudaSuccess;
+}
+enum cudaDriverEntryPointQueryResult { cudaDriverEntryPointSuccess = 0, cudaDriverEntryPointSymbolNotFound = 1 };
+enum { cudaEnableDefault = 0 };
+inline cudaError_t cudaGetDriverEntryPointByVersion(const char *, void **f, unsigned, unsigned long long,
+                                                    cudaDriverEntryPointQueryResult *q) {
+    *f = nullptr;
+    if (q) *q = cudaDriverEntryPointSymbolNotFound;
+    return cudaErrorNotSupported;
+}
 
 // ---- device side ---------------------------------------------------------
 void emu_syncthreads();

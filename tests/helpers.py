@@ -67,3 +67,17 @@ def tucker_congruence(A, B):
         used.add(s)
         worst = min(worst, best)
     return worst
+
+
+def near_dependent_start(R, J, K, seed, delta=1e-3):
+    """Seeded uniform start (synth.init_factors) whose V has its second column
+    equal to the first plus delta times Gaussian noise, rounded to FP32.  Every
+    Z_k = X_k V then has two nearly dependent columns, so most subjects' A_k =
+    Z_k S_k H^T have condition numbers of 1e3 to 1e5 (inside the 1e-5 rank cut
+    of the Procrustes step)."""
+    import synth
+    H0, V0, W0 = synth.init_factors(R, J, K, seed=seed)
+    V0 = V0.copy()
+    rng = np.random.default_rng(seed + 1)
+    V0[:, 1] = (V0[:, 0].astype(np.float64) + delta * rng.standard_normal(J)).astype(np.float32)
+    return H0, V0, W0

@@ -449,3 +449,25 @@ def test_rational_start_closed_form_for_orthogonal_columns():
     _, V, _, lam = P.rational_start(P.all_blocks(X), X.K, X.J, R)
     assert np.abs(V - np.eye(J)[:, top]).max() < 1e-12
     assert np.allclose(lam[:R], ss[top], rtol=1e-12)
+
+
+def test_assemble_u_reconstructs_planted_slices():
+    """U_k = Q_k H (Algorithm 2, after the loop) on planted noiseless data
+    X_k = Q_k H S_k V^T: with the true H, V, W the Procrustes step returns the
+    planted Q_k, so the assembled U_k must reproduce every slice as
+    U_k S_k V^T (to the FP32 rounding of the stored values) and satisfy
+    U_k^T U_k = H^T H (Q_k has orthonormal columns).  A transposed H, or H
+    applied on the wrong side, fails both."""
+    rng = np.random.default_rng(31)
+    K, J, R, I = 6, 9, 3, 5
+    Xs, H, V, W = planted_parafac2(rng, K, J, R, I)
+    X = slices_from_dense(Xs, J)
+    blocks = P.all_blocks(X)
+    Qs = [P.procrustes_q(Xc, cols, H, V, W[k]) for k, (Xc, cols) in enumerate(blocks)]
+    Us = P.assemble_u(Qs, H)
+    for k, (Xc, cols) in enumerate(blocks):
+        Xk = np.zeros((I, J))
+        Xk[:, cols] = Xc
+        assert Us[k].shape == (I, R)
+        assert np.linalg.norm(Us[k] @ np.diag(W[k]) @ V.T - Xk) <= 1e-6 * np.linalg.norm(Xk)
+        assert np.abs(Us[k].T @ Us[k] - H.T @ H).max() <= 1e-10 * np.abs(H.T @ H).max()

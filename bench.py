@@ -212,71 +212,180 @@ def _traffic(kernel, workload):
     return None
 
 
-def cpu_baseline(w, X, H0, V0, W0, target_s=12.0):
-    """The FP64 oracle, as it stands, on a bounded prefix of the same workload."""
-    import oracle
-    n_pilot = min(X.K, 300)
-    Xs = X.take(range(n_pilot))
-    t = time.perf_counter()
-    oracle.parafac2_als(Xs, H0, V0, W0[:n_pilot], n_iter=1)
-    per = (time.perf_counter() - t) / max(Xs.nnz, 1)
-    n = n_pilot
-    if per > 0:
-        want_nnz = target_s / per
-        n = int(min(X.K, max(n_pilot, n_pilot * want_nnz / max(Xs.nnz, 1))))
-    Xs = X.take(range(n))
-    t = time.perf_counter()
-    oracle.parafac2_als(Xs, H0, V0, W0[:n], n_iter=1)
-    dt = time.perf_counter() - t
-    return {"value": Xs.nnz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {n:,} subjects of {w.name} ({Xs.nnz:,} nnz), 1 iteration, "
-                      f"{dt:.1f} s, numpy FP64 single-threaded"}
+def prefix(X, n):
+    """The first n subjects of X (array slices; no arithmetic)."""
+    import synth
+    r1 = int(X.subj_ptr[n])
+    e1 = int(X.row_ptr[r1])
+    return synth.Slices(int(n), X.J, X.subj_ptr[:n + 1].copy(), X.row_ptr[:r1 + 1].copy(),
+                        X.col[:e1].copy(), X.val[:e1].copy())
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def _pooled_sample_time(X, n, H0, V0, W0, cores):
+    """Seconds of one oracle iteration over the first n subjects, on `cores`
+    worker processes (loading the workers is not timed)."""
+    from oracle.pool import OraclePool
+    Xs = prefix(X, n)
+    with OraclePool(Xs, cores) as pool:
+        t = time.perf_counter()
+        pool.iteration(H0, V0, W0[:n])
+        return time.perf_counter() - t, Xs.nnz, pool.n_workers
+
+
+def cpu_baseline(w, X, H0, V0, W0, target_s=15.0):
+    """The FP64 oracle, as it stands, on all host cores (one worker process per
+    core over contiguous subject chunks, oracle.pool) on a bounded prefix of
+    the same workload, sized for about target_s seconds of one iteration."""
+    cores = host_cores()
+    n_pilot = int(min(X.K, max(2000, 250 * cores)))
+    dt, nnz, _ = _pooled_sample_time(X, n_pilot, H0, V0, W0, cores)
+    n = int(min(X.K, max(n_pilot, n_pilot * target_s / max(dt, 1e-3))))
+    dt, nnz, used = _pooled_sample_time(X, n, H0, V0, W0, cores)
+    return {"value": nnz / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+            "host_cores": cores,
+            "sample": f"first {n:,} subjects of {w.name} ({nnz:,} nnz), 1 iteration, "
+                      f"{dt:.1f} s, numpy FP64, {used} worker processes (one per host core) "
+                      f"over contiguous subject chunks"}
 
 
 def run_reference(args, w):
-    """--impl reference: the FP64 oracle, bounded sample per step."""
+    """--impl reference: the FP64 oracle on all host cores (oracle.pool), a
+    bounded prefix of the workload per step."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
     import synth
-    import oracle
+    from oracle.pool import OraclePool
     X = synth.generate(w)
     H0, V0, W0 = synth.init_factors(w.R, X.J, X.K, seed=w.seed)
+    cores = host_cores()
     # size the per-step sample so that (warmup + steps) steps take ~2 minutes
-    n_pilot = min(X.K, 200)
-    Xp = X.take(range(n_pilot))
-    t = time.perf_counter()
-    oracle.parafac2_als(Xp, H0, V0, W0[:n_pilot], n_iter=1)
-    per_nnz = (time.perf_counter() - t) / max(Xp.nnz, 1)
+    n_pilot = int(min(X.K, max(2000, 250 * cores)))
+    dt, _, _ = _pooled_sample_time(X, n_pilot, H0, V0, W0, cores)
     budget = 120.0 / max(args.steps + args.warmup, 1)
-    n = int(min(X.K, max(n_pilot, n_pilot * (budget / per_nnz) / max(Xp.nnz, 1))))
-    Xs = X.take(range(n))
-    blocks = oracle.all_blocks(Xs)
-    H, V, Wk = (np.asarray(a, np.float64) for a in (H0, V0, W0[:n]))
+    n = int(min(X.K, max(n_pilot, n_pilot * budget / max(dt, 1e-3))))
+    Xs = prefix(X, n)
     times = []
-    for i in range(args.warmup + args.steps):
-        t = time.perf_counter()
-        out = oracle.als_iteration(blocks, H, V, Wk)
-        dt = time.perf_counter() - t
-        H, V, Wk = out["H"], out["V"], out["W"]
-        if i >= args.warmup:
-            times.append(dt)
+    with OraclePool(Xs, cores) as pool:
+        H, V, Wk = (np.asarray(a, np.float64) for a in (H0, V0, W0[:n]))
+        for i in range(args.warmup + args.steps):
+            t = time.perf_counter()
+            out = pool.iteration(H, V, Wk)
+            dt = time.perf_counter() - t
+            H, V, Wk = out["H"], out["V"], out["W"]
+            if i >= args.warmup:
+                times.append(dt)
+        used = pool.n_workers
     step = statistics.mean(times)
     value = Xs.nnz / step
-    sample = (f"first {n:,} subjects of {w.name} ({Xs.nnz:,} nnz) per step, "
-              f"numpy FP64 single-threaded")
+    sample = (f"first {n:,} subjects of {w.name} ({Xs.nnz:,} nnz) per step, numpy FP64, "
+              f"{used} worker processes (one per host core) over contiguous subject chunks")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": _workload_desc(w, X), "sample_subjects": n,
                        "sample_nnz": int(Xs.nnz)},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                             "host_cores": cores, "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def roofline(X, R, phase_ms, flops, wname):
+    """Roofline of the dominant kernel group and the sparse passes' GB/s."""
+    dom = max(phase_ms, key=phase_ms.get)
+    bmodel = _bytes_model(X, R)
+    hbm_peak, hbm_src = _peaks()
+    if dom == "procrustes":
+        ach = flops / (phase_ms[dom] / 1e3) / 1e12
+        kname = ("k_polar_reg (double-word Procrustes, one lane per subject)" if R <= 12 else
+                 "k_polar_grp (double-word Procrustes, a group of 8 or 16 lanes per subject)")
+        roof = {"kernel": kname, "bound": "alu",
+                "achieved": ach, "peak": DW_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / DW_PEAK_TFLOPS,
+                "peak_source": "derived: FP32 pipe 152 SMs x 128 lanes x 2.07 GHz, "
+                f"{DW_INSTR_PER_FMA} FP32 instructions per double-word multiply-add",
+                "vs_fp64_nominal": ach / FP64_PEAK_TFLOPS,
+                "algorithmic_flops_per_launch": flops,
+                "traffic": _traffic("k_polar_reg" if R <= 12 else "k_polar_grp", wname)}
+    else:
+        by = bmodel.get(dom, 0)
+        ach = by / (phase_ms[dom] / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "peak_source": hbm_src,
+                "algorithmic_bytes_per_launch": by, "traffic": _traffic(dom, wname)}
+    sparse = {}
+    for k in ("beta_mode2", "alpha_mode3_w_gram"):
+        gbs = bmodel[k] / (phase_ms[k] / 1e3) / 1e9 if phase_ms[k] > 0 else None
+        sparse[k] = {"ms": phase_ms[k], "algorithmic_GBps": gbs,
+                     "hbm_frac": gbs / hbm_peak if gbs else None}
+    return roof, sparse
+
+
+def measure_workload(X, w, precision, steps, warmup, device, gpu_id):
+    """One workload timed like the headline (graph replays, CUDA events on the
+    library's stream, phase events, clocks sampled in the timed region)."""
+    import torch
+    import paper_1703_04219_gb300 as p2
+    R = w.R
+    H0, V0, W0 = synth_init(w, X)
+    stream = torch.cuda.Stream()
+    m = p2.Parafac2(R, device=device, stream=stream.cuda_stream, timing=True,
+                    precision=precision)
+    m.load(X)
+    m.init(H0, V0, W0)
+    for _ in range(warmup):
+        m.iterate(1, want_fit=False)
+    stream.synchronize()
+    clocks = ClockSampler(gpu_id)
+    t = timed_steps(m, stream, steps, None, clocks)
+    fit, _ = m.fit()
+    m.close()
+    ms = t["ms_total"] / steps
+    roof, sparse = roofline(X, R, t["phase_ms"], t["flops"], w.name)
+    return {"workload": _workload_desc(w, X), "precision": precision,
+            "storage": "V and P_k bfloat16" if precision == "bf16" else "float",
+            "steps": steps, "warmup": warmup, "s_per_iter": ms / 1e3,
+            "value": X.nnz / (ms / 1e3), "unit": UNIT, "fit_after_steps": fit,
+            "phase_ms": t["phase_ms"], "sparse_passes": sparse, "roofline": roof,
+            "gpu_launches": t["launches"], "clocks": t["clocks"]}
+
+
+def synth_init(w, X):
+    import synth
+    return synth.init_factors(w.R, X.J, X.K, seed=w.seed)
+
+
+def run_r40(args, device, gpu_id):
+    """Table 1's R = 40 column: the 250M-non-zero workload in FP32 and with
+    bfloat16 storage, and the 555M-non-zero workload in FP32."""
+    import synth
+    out = {}
+    steps = max(1, min(args.steps, 5))
+    for name, precs in (("c250m", ("fp32", "bf16")), ("c555m", ("fp32",))):
+        w = synth.WORKLOADS[name]
+        X = synth.generate(w)
+        for prec in precs:
+            out[f"{name}_{prec}"] = measure_workload(X, w, prec, steps, args.warmup, device,
+                                                     gpu_id)
+        del X
+    return out
+
+
+def _gpu_id(local):
+    import torch
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = getattr(props, "uuid", None)
+    if gpu_id is None:
+        return local
+    return str(gpu_id) if str(gpu_id).startswith("GPU-") else f"GPU-{gpu_id}"
 
 
 def run_p2(args, w):
@@ -302,10 +411,7 @@ def run_p2(args, w):
         m.iterate(1, want_fit=False)
     stream.synchronize()
 
-    props = torch.cuda.get_device_properties(local)
-    gpu_id = getattr(props, "uuid", None)
-    gpu_id = f"GPU-{gpu_id}" if gpu_id is not None and not str(gpu_id).startswith("GPU-") else \
-        (str(gpu_id) if gpu_id is not None else local)
+    gpu_id = _gpu_id(local)
     clocks = ClockSampler(gpu_id)
     t = timed_steps(m, stream, args.steps, pg, clocks)
     ms_total, clk, launches = t["ms_total"], t["clocks"], t["launches"]
@@ -316,34 +422,7 @@ def run_p2(args, w):
     ms_step = ms_total / args.steps
     value = job_throughput(X.nnz, args.steps, ms_total, world)
 
-    # roofline of the dominant kernel group
-    dom = max(phase_ms, key=phase_ms.get)
-    bmodel = _bytes_model(X, R)
-    hbm_peak, hbm_src = _peaks()
-    if dom == "procrustes":
-        flops = t["flops"]
-        ach = flops / (phase_ms[dom] / 1e3) / 1e12
-        kname = ("k_polar_reg (double-word Procrustes, one lane per subject)" if R <= 12 else
-                 "k_polar_grp (double-word Procrustes, a group of 8 or 16 lanes per subject)")
-        roof = {"kernel": kname, "bound": "alu",
-                "achieved": ach, "peak": DW_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / DW_PEAK_TFLOPS,
-                "peak_source": "derived: FP32 pipe 152 SMs x 128 lanes x 2.07 GHz, "
-                f"{DW_INSTR_PER_FMA} FP32 instructions per double-word multiply-add",
-                "vs_fp64_nominal": ach / FP64_PEAK_TFLOPS,
-                "algorithmic_flops_per_launch": flops,
-                "traffic": _traffic("k_polar_reg" if R <= 12 else "k_polar_grp", w.name)}
-    else:
-        by = bmodel.get(dom, 0)
-        ach = by / (phase_ms[dom] / 1e3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "peak_source": hbm_src,
-                "algorithmic_bytes_per_launch": by, "traffic": _traffic(dom, w.name)}
-    sparse = {}
-    for k in ("beta_mode2", "alpha_mode3_w_gram"):
-        gbs = bmodel[k] / (phase_ms[k] / 1e3) / 1e9 if phase_ms[k] > 0 else None
-        sparse[k] = {"ms": phase_ms[k], "algorithmic_GBps": gbs,
-                     "hbm_frac": gbs / hbm_peak if gbs else None}
+    roof, sparse = roofline(X, R, phase_ms, t["flops"], w.name)
 
     # end-to-end through the public API from pinned host buffers
     e2e = None
@@ -361,6 +440,9 @@ def run_p2(args, w):
     if not args.no_nonneg and R <= 16:
         nonneg = time_precision(X, R, H0, V0, W0, "fp32", args.steps, args.warmup, local,
                                 nonneg=True)
+    r40 = None
+    if rank == 0 and world == 1 and not args.no_r40:
+        r40 = run_r40(args, local, gpu_id)
     serving = None
     if rank == 0 and not args.no_serve:
         serving = {"fp32": run_serving(precision="fp32"), "bf16": run_serving(precision="bf16")}
@@ -376,7 +458,7 @@ def run_p2(args, w):
                        "graph": True, "fit_after_steps": fit},
             "phase_ms": phase_ms, "sparse_passes": sparse, "roofline": roof,
             "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-            "bf16_storage": bf16, "nonneg": nonneg, "serving": serving}
+            "bf16_storage": bf16, "nonneg": nonneg, "r40": r40, "serving": serving}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
@@ -525,6 +607,8 @@ def main(argv=None):
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-nonneg", action="store_true", help="skip the non-negative variant line")
+    ap.add_argument("--no-r40", action="store_true",
+                    help="skip the R = 40 workloads (250M nnz FP32 and bfloat16, 555M nnz)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

@@ -1,7 +1,10 @@
 """The full 63M-non-zero workload (K = 1,000,000, J = 5,000, R = 10) in the
-launch configuration bench.py times, checked on outputs the oracle can
-compute one subject at a time, and on properties that hold at any size:
+launch configuration bench.py times:
 
+* one iteration from the seeded start against the FP64 oracle run over the
+  whole workload in worker processes (oracle.pool: the unchanged per-subject
+  functions of Algorithms 2 and 3, partial sums combined in a fixed order):
+  M1, M2, M3, H, V and W within relative Frobenius 1e-5, the fit within 1e-4;
 * for 64 sampled subjects, the GPU's Procrustes state T_k (after three
   iterations) gives Q_k = X_k V T_k^T equal to the oracle's polar factor of
   X_k V S_k H^T computed in FP64 from the GPU's own H, V, W (per-subject bound
@@ -16,6 +19,7 @@ import pytest
 
 import synth
 from oracle import parafac2 as P
+from oracle.pool import OraclePool
 from tests.helpers import rel_fro
 
 pytestmark = pytest.mark.gpu
@@ -34,6 +38,27 @@ X_SEED = 20170315
 def data():
     X = synth.generate("c63m")
     return X, synth.init_factors(10, X.J, X.K, seed=X_SEED)
+
+
+def test_full_size_one_step_matches_pooled_oracle(p2, data):
+    X, (H0, V0, W0) = data
+    R = 10
+    with p2.Parafac2(R) as m:
+        m.load(X)
+        m.init(H0, V0, W0)
+        fit = m.iterate(1)
+        H, V, W = m.factors()
+        M = {n: m.mttkrp(n) for n in (1, 2, 3)}
+    with OraclePool(X) as pool:
+        ref = pool.iteration(H0, V0, W0)
+        nx2 = pool.norm_x_sq
+    errs = {key: rel_fro(M[mode], ref[key]) for mode, key in ((1, "M1"), (2, "M2"), (3, "M3"))}
+    errs.update({key: rel_fro(v, ref[key]) for key, v in (("H", H), ("V", V), ("W", W))})
+    errs["fit"] = abs(fit - P.fit_from_loss(ref["loss"], nx2))
+    print("\nc63m full size one-step errors: " + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    for key in ("M1", "M2", "M3", "H", "V", "W"):
+        assert errs[key] < 1e-5, (key, errs[key])
+    assert errs["fit"] < 1e-4
 
 
 def test_full_size_sampled_procrustes_and_monotone_fit(p2, data):

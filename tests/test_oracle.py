@@ -471,3 +471,25 @@ def test_assemble_u_reconstructs_planted_slices():
         assert Us[k].shape == (I, R)
         assert np.linalg.norm(Us[k] @ np.diag(W[k]) @ V.T - Xk) <= 1e-6 * np.linalg.norm(Xk)
         assert np.abs(Us[k].T @ Us[k] - H.T @ H).max() <= 1e-10 * np.abs(H.T @ H).max()
+
+
+@pytest.mark.parametrize("nonneg", [False, True])
+def test_pooled_iteration_equals_serial_oracle(nonneg):
+    """oracle.pool runs the same per-subject functions over subject chunks in
+    worker processes; only the order of the FP64 sums over subjects differs,
+    so two iterations agree with parafac2.parafac2_als to round-off."""
+    from oracle.pool import OraclePool
+    X = synth.generate("tiny", K=200)
+    R = 5
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=9)
+    ref = P.parafac2_als(X, H0, V0, W0, n_iter=2, nonneg=nonneg)
+    with OraclePool(X, n_workers=3) as pool:
+        assert pool.n_workers == 3
+        got = pool.parafac2_als(H0, V0, W0, n_iter=2, nonneg=nonneg)
+    for key in ("H", "V", "W"):
+        assert rel_fro(got[key], ref[key]) < 1e-12, key
+    for key in ("M1", "M2", "M3"):
+        assert rel_fro(got["last"][key], ref["last"][key]) < 1e-12, key
+    for a, b in zip(got["history"], ref["history"]):
+        assert abs(a["fit"] - b["fit"]) < 1e-13
+    assert abs(got["norm_x_sq"] - ref["norm_x_sq"]) <= 1e-13 * ref["norm_x_sq"]

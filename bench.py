@@ -329,7 +329,7 @@ def roofline(X, R, phase_ms, flops, wname):
     return roof, sparse
 
 
-def measure_workload(X, w, precision, steps, warmup, device, gpu_id):
+def measure_workload(X, w, precision, steps, warmup, device, gpu_id, fp64_procrustes=False):
     """One workload timed like the headline (graph replays, CUDA events on the
     library's stream, phase events, clocks sampled in the timed region)."""
     import torch
@@ -338,7 +338,7 @@ def measure_workload(X, w, precision, steps, warmup, device, gpu_id):
     H0, V0, W0 = synth_init(w, X)
     stream = torch.cuda.Stream()
     m = p2.Parafac2(R, device=device, stream=stream.cuda_stream, timing=True,
-                    precision=precision)
+                    precision=precision, fp64_procrustes=fp64_procrustes)
     m.load(X)
     m.init(H0, V0, W0)
     for _ in range(warmup):
@@ -350,12 +350,24 @@ def measure_workload(X, w, precision, steps, warmup, device, gpu_id):
     m.close()
     ms = t["ms_total"] / steps
     roof, sparse = roofline(X, R, t["phase_ms"], t["flops"], w.name)
+    if fp64_procrustes:
+        roof = fp64_roofline(R, t["phase_ms"], t["flops"])
     return {"workload": _workload_desc(w, X), "precision": precision,
+            "procrustes": "fp64" if fp64_procrustes else "double-word",
             "storage": "V and P_k bfloat16" if precision == "bf16" else "float",
             "steps": steps, "warmup": warmup, "s_per_iter": ms / 1e3,
             "value": X.nnz / (ms / 1e3), "unit": UNIT, "fit_after_steps": fit,
             "phase_ms": t["phase_ms"], "sparse_passes": sparse, "roofline": roof,
             "gpu_launches": t["launches"], "clocks": t["clocks"]}
+
+
+def fp64_roofline(R, phase_ms, flops):
+    """Roofline of the FP64 arm of the Procrustes step, against the FP64 pipe."""
+    ach = flops / (phase_ms["procrustes"] / 1e3) / 1e12
+    return {"kernel": ("k_polar_reg" if R <= 12 else "k_polar_grp") + " (FP64 arm)",
+            "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "GB300 FP64 nominal",
+            "algorithmic_flops_per_launch": flops, "traffic": None}
 
 
 def synth_init(w, X):
@@ -364,17 +376,23 @@ def synth_init(w, X):
 
 
 def run_r40(args, device, gpu_id):
-    """Table 1's R = 40 column: the 250M-non-zero workload in FP32 and with
-    bfloat16 storage, and the 555M-non-zero workload in FP32."""
+    """Table 1's R = 40 column: the 250M-non-zero workload in FP32, with
+    bfloat16 storage and with the FP64 arm of the Procrustes step, and the
+    555M-non-zero workload in FP32."""
     import synth
     out = {}
     steps = max(1, min(args.steps, 5))
-    for name, precs in (("c250m", ("fp32", "bf16")), ("c555m", ("fp32",))):
+    for name, precs in (("c250m", ("fp32", "bf16", "fp64p")), ("c555m", ("fp32",))):
         w = synth.WORKLOADS[name]
         X = synth.generate(w)
         for prec in precs:
-            out[f"{name}_{prec}"] = measure_workload(X, w, prec, steps, args.warmup, device,
-                                                     gpu_id)
+            if prec == "fp64p" and args.no_fp64:
+                continue
+            key = f"{name}_fp64_procrustes" if prec == "fp64p" else f"{name}_{prec}"
+            out[key] = measure_workload(X, w, "fp32" if prec == "fp64p" else prec,
+                                        min(steps, 3) if prec == "fp64p" else steps,
+                                        args.warmup, device, gpu_id,
+                                        fp64_procrustes=prec == "fp64p")
         del X
     return out
 
@@ -436,6 +454,10 @@ def run_p2(args, w):
     bf16 = None
     if not args.no_bf16:
         bf16 = time_precision(X, R, H0, V0, W0, "bf16", args.steps, args.warmup, local)
+    fp64p = None
+    if rank == 0 and world == 1 and not args.no_fp64:
+        fp64p = measure_workload(X, w, "fp32", args.steps, args.warmup, local, gpu_id,
+                                 fp64_procrustes=True)
     nonneg = None
     if not args.no_nonneg and R <= 16:
         nonneg = time_precision(X, R, H0, V0, W0, "fp32", args.steps, args.warmup, local,
@@ -458,7 +480,8 @@ def run_p2(args, w):
                        "graph": True, "fit_after_steps": fit},
             "phase_ms": phase_ms, "sparse_passes": sparse, "roofline": roof,
             "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-            "bf16_storage": bf16, "nonneg": nonneg, "r40": r40, "serving": serving}
+            "bf16_storage": bf16, "fp64_procrustes": fp64p, "nonneg": nonneg, "r40": r40,
+            "serving": serving}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
@@ -607,6 +630,8 @@ def main(argv=None):
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-nonneg", action="store_true", help="skip the non-negative variant line")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the FP64 arm of the Procrustes step")
     ap.add_argument("--no-r40", action="store_true",
                     help="skip the R = 40 workloads (250M nnz FP32 and bfloat16, 555M nnz)")
     args = ap.parse_args(argv)

@@ -68,6 +68,10 @@ typedef struct {
     int32_t nonneg;       /* non-zero: S_k and V constrained non-negative (Section 5.1), the
                              W and V updates solved row by row as non-negative least squares;
                              requires R <= 16 */
+    int32_t fp64_procrustes; /* non-zero: the Procrustes step's eigen-decomposition and the
+                             formation of T_k run in FP64 on the FP64 pipe (same algorithm,
+                             Householder + implicit QR); zero (default): in double-word
+                             (float-float) arithmetic on the FP32 pipe, ~2^-46 normwise */
 } p2_options;
 
 /* Counters and timings of a context (p2_stats). */
@@ -84,7 +88,8 @@ typedef struct {
 } p2_stats_t;
 
 /* Fill *opt with defaults for rank R (precision FP32, device 0, graph on,
- * rank_rtol 1e-5, own stream, timing off, seed 20170314, unconstrained). */
+ * rank_rtol 1e-5, own stream, timing off, seed 20170314, unconstrained,
+ * double-word Procrustes). */
 void p2_default_options(p2_options *opt, int32_t R);
 
 /* Create a context on opt->device.  *out receives the handle (NULL on error).

@@ -35,7 +35,8 @@ class p2_options(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("rank_rtol", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("timing", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("nonneg", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("nonneg", ctypes.c_int32),
+                ("fp64_procrustes", ctypes.c_int32)]
 
 
 class p2_stats_t(ctypes.Structure):
@@ -316,7 +317,7 @@ class Parafac2:
 
     def __init__(self, R: int, device: int = 0, use_graph: bool = True, rank_rtol: float = 1e-5,
                  stream=None, timing: bool = False, precision: str = "fp32", seed=None,
-                 nonneg: bool = False):
+                 nonneg: bool = False, fp64_procrustes: bool = False):
         if precision not in ("fp32", "bf16"):
             raise ValueError("precision must be 'fp32' or 'bf16'")
         opt = p2_default_options(R)
@@ -329,6 +330,7 @@ class Parafac2:
         if seed is not None:
             opt.seed = int(seed)
         opt.nonneg = 1 if nonneg else 0
+        opt.fp64_procrustes = 1 if fp64_procrustes else 0
         self.R = R
         self.precision = precision
         self.ctx = p2_create(opt)

@@ -256,6 +256,7 @@ void p2_default_options(p2_options *opt, int32_t R) {
     opt->timing = 0;
     opt->seed = 20170314ULL;
     opt->nonneg = 0;
+    opt->fp64_procrustes = 0;
 }
 
 int p2_create(p2_ctx **out, const p2_options *opt) {

@@ -1,5 +1,6 @@
 // Symmetric eigen-decomposition of one small matrix by one thread, in
-// double-word arithmetic (p2_dw.cuh).
+// double-word arithmetic (p2_dw.cuh) or, for the opt-in FP64 arm, in FP64
+// (p2_num.cuh): the code is written once for a number type D.
 //
 // Used by the Procrustes step (Section 3.2): with one GPU lane per subject,
 // the R x R matrix A_k^T A_k is decomposed as Z diag(d) Z^T so that the
@@ -10,29 +11,31 @@
 // backward accumulation of the orthogonal factor, then implicit symmetric QR
 // steps with the Wilkinson shift and deflation, rotations accumulated into
 // the eigenvector matrix.  Both halves are normwise backward stable, so the
-// double-word arithmetic's normwise error bounds (a few 2^-48) carry over to
-// the decomposition.
+// arithmetic's normwise error bounds (a few 2^-48 for double-words, a few
+// 2^-53 in FP64) carry over to the decomposition.
 //
 // The matrix and vectors are reached through accessor objects so the same
 // code runs on interleaved shared memory (element e of thread t at
 // base[e * stride + t]) on the GPU and on plain arrays on the host.
 #pragma once
 
-#include "p2_dw.cuh"
+#include "p2_num.cuh"
 
 namespace p2 {
 
+template <class D = dw>
 struct DwMat {
-    dw *base;
+    D *base;
     int stride;
     int n;
-    P2_HD dw &operator()(int i, int j) const { return base[(size_t)(i * n + j) * stride]; }
+    P2_HD D &operator()(int i, int j) const { return base[(size_t)(i * n + j) * stride]; }
 };
 
+template <class D = dw>
 struct DwVec {
-    dw *base;
+    D *base;
     int stride;
-    P2_HD dw &operator[](int i) const { return base[(size_t)i * stride]; }
+    P2_HD D &operator[](int i) const { return base[(size_t)i * stride]; }
 };
 
 // Reduce the symmetric matrix held in the lower triangle of A (n x n) to
@@ -41,58 +44,58 @@ struct DwVec {
 // the Householder work vector during the reduction, and the Householder
 // scalars beta_k are kept in the (unused) upper triangle at A(k, k+1) until
 // the backward accumulation consumes them.  N > 0 fixes n at compile time.
-template <int N>
-P2_HD void tridiagonalize_dw(int n_rt, DwMat A, DwVec d, DwVec e) {
+template <int N, class D>
+P2_HD void tridiagonalize_dw(int n_rt, DwMat<D> A, DwVec<D> d, DwVec<D> e) {
     const int n = N > 0 ? N : n_rt;
-    const dw one = dw_f(1.f), zero = dw_f(0.f);
-    DwVec t = d;
+    const D one = num_f<D>(1.f), zero = num_f<D>(0.f);
+    DwVec<D> t = d;
 #pragma unroll 1
     for (int k = 0; k + 2 < n; ++k) {
         // Householder reflector P = I - b v v^T with P x = beta e_1 for
         // x = A[k+1:n, k], in the normalisation that squares no small
         // quantity: beta = -sign(x0) ||x||, b = (beta - x0) / beta in [1, 2],
         // v = [1, x(2:) / (x0 - beta)] with |v_i| <= 1.  A column whose part
-        // below x0 has squared norm under DW_TINY2 (entries below ~2^-48
+        // below x0 has squared norm under the type's tiny2 (entries below ~2^-48
         // of the scaled matrix's unit norm) is left as it is, a perturbation
         // of the order of the rounding, so every square stays in range.
-        dwacc sg = acc_zero();
+        acc_t<D> sg = acc0<D>();
         for (int i = k + 2; i < n; ++i) acc_sqr(sg, A(i, k));
-        const dw sigma = acc_val(sg);
-        const dw x0 = A(k + 1, k);
-        if (!(sigma.h >= DW_TINY2)) {
+        const D sigma = acc_val(sg);
+        const D x0 = A(k + 1, k);
+        if (!(sigma.h >= NumT<D>::tiny2())) {
             A(k, k + 1) = zero;     // b_k
             e[k] = x0;
             continue;
         }
-        dwacc m2 = acc_from(sigma);
+        acc_t<D> m2 = acc_from(sigma);
         acc_sqr(m2, x0);
-        const dw mu = dw_sqrt(acc_val(m2));
-        const dw beta = (x0.h >= 0.f) ? dw_neg(mu) : mu;
-        const dw b = dw_div(dw_sub(beta, x0), beta);
-        const dw inv_v0 = dw_recip(dw_sub(x0, beta));
+        const D mu = dw_sqrt(acc_val(m2));
+        const D beta = (x0.h >= 0.f) ? dw_neg(mu) : mu;
+        const D b = dw_div(dw_sub(beta, x0), beta);
+        const D inv_v0 = dw_recip(dw_sub(x0, beta));
         for (int i = k + 2; i < n; ++i) A(i, k) = dw_mul(A(i, k), inv_v0);
         A(k, k + 1) = b;
         e[k] = beta;
         // p = b A22 v (A22 symmetric, lower triangle stored), K = b/2 p^T v
-        dwacc pv = acc_zero();
+        acc_t<D> pv = acc0<D>();
         for (int i = k + 1; i < n; ++i) {
-            dwacc s = acc_from(A(i, k + 1));          // v_{k+1} = 1
+            acc_t<D> s = acc_from(A(i, k + 1));          // v_{k+1} = 1
             for (int j = k + 2; j < n; ++j) acc_fma(s, (j <= i) ? A(i, j) : A(j, i), A(j, k));
-            const dw si = dw_mul(acc_val(s), b);
+            const D si = dw_mul(acc_val(s), b);
             t[i] = si;
             if (i == k + 1)
                 acc_add(pv, si);
             else
                 acc_fma(pv, si, A(i, k));
         }
-        const dw nK = dw_neg(dw_mul(dw_scale(b, 0.5f), acc_val(pv)));
+        const D nK = dw_neg(dw_mul(dw_scale(b, 0.5f), acc_val(pv)));
         t[k + 1] = dw_add(t[k + 1], nK);                 // w = p - K v
         for (int i = k + 2; i < n; ++i) t[i] = dw_fma(nK, A(i, k), t[i]);
         for (int i = k + 1; i < n; ++i) {                // A22 -= v w^T + w v^T
-            const dw nvi = dw_neg((i == k + 1) ? one : A(i, k));
-            const dw nwi = dw_neg(t[i]);
+            const D nvi = dw_neg((i == k + 1) ? one : A(i, k));
+            const D nwi = dw_neg(t[i]);
             for (int j = k + 1; j <= i; ++j) {
-                dwacc a = acc_from(A(i, j));
+                acc_t<D> a = acc_from(A(i, j));
                 acc_fma(a, nvi, t[j]);
                 if (j == k + 1)
                     acc_add(a, nwi);
@@ -116,7 +119,7 @@ P2_HD void tridiagonalize_dw(int n_rt, DwMat A, DwVec d, DwVec e) {
     A(n - 2, n - 1) = zero;
 #pragma unroll 1
     for (int k = n - 3; k >= 0; --k) {
-        const dw b = A(k, k + 1);
+        const D b = A(k, k + 1);
         A(k + 1, k + 1) = one;
         for (int j = k + 2; j < n; ++j) {
             A(k + 1, j) = zero;
@@ -124,13 +127,13 @@ P2_HD void tridiagonalize_dw(int n_rt, DwMat A, DwVec d, DwVec e) {
         }
         if (b.h == 0.f) continue;
         // column k+1 is e_{k+1}: its update is 1 - b and -b v_i
-        const dw nb = dw_neg(b);
+        const D nb = dw_neg(b);
         A(k + 1, k + 1) = dw_add(one, nb);
         for (int i = k + 2; i < n; ++i) A(i, k + 1) = dw_mul(nb, A(i, k));
         for (int c = k + 2; c < n; ++c) {
-            dwacc s = acc_zero();                      // A(k+1, c) = 0 here
+            acc_t<D> s = acc0<D>();                      // A(k+1, c) = 0 here
             for (int i = k + 2; i < n; ++i) acc_fma(s, A(i, k), A(i, c));
-            const dw ns = dw_mul(acc_val(s), nb);
+            const D ns = dw_mul(acc_val(s), nb);
             A(k + 1, c) = ns;
             for (int i = k + 2; i < n; ++i) A(i, c) = dw_fma(ns, A(i, k), A(i, c));
         }
@@ -165,12 +168,12 @@ P2_HD void tridiagonalize_dw(int n_rt, DwMat A, DwVec d, DwVec e) {
 // power of two so that t cannot underflow (FP32's exponent range is far
 // narrower than FP64's, and the converging sub-diagonal and the bulge can
 // both become tiny).
-template <int N>
-P2_HD int tridiagonal_qr_dw(int n_rt, DwMat Z, DwVec d, DwVec e, int max_steps,
+template <int N, class D>
+P2_HD int tridiagonal_qr_dw(int n_rt, DwMat<D> Z, DwVec<D> d, DwVec<D> e, int max_steps,
                             int *rotations = nullptr) {
     constexpr int NA = N > 0 ? N : 64;                   // register-array bound
     const int n = N > 0 ? N : n_rt;
-    const dw one = dw_f(1.f), zero = dw_f(0.f);
+    const D one = num_f<D>(1.f), zero = num_f<D>(0.f);
     if (n < 2) return 0;
     float an = 0.f;
     for (int i = 0; i < n; ++i) {
@@ -179,16 +182,16 @@ P2_HD int tridiagonal_qr_dw(int n_rt, DwMat Z, DwVec d, DwVec e, int max_steps,
         if (i > 0) r += fabsf(e[i - 1].h);
         an = fmaxf(an, r);
     }
-    const int tiny_ex = f_expo(an) - DW_DEFLATE_BITS;
+    const int tiny_ex = f_expo(an) - NumT<D>::deflate_bits;
     int steps = 0, rot = 0, status = 0;
     int q = n - 1, p = 0, kr = 0;
     bool sweeping = false;
-    dw x = zero, z = zero, dk = zero, ek = zero;
+    D x = zero, z = zero, dk = zero, ek = zero;
     int kp = 0;
-    dw cp = one, sp = zero;
+    D cp = one, sp = zero;
 #pragma unroll 1
     while (true) {
-        dw za[NA], zb[NA];                               // pending rotation's columns
+        D za[NA], zb[NA];                               // pending rotation's columns
 #pragma unroll
         for (int i = 0; i < NA; ++i)
             if (i < n) {
@@ -205,16 +208,16 @@ P2_HD int tridiagonal_qr_dw(int n_rt, DwMat Z, DwVec d, DwVec e, int max_steps,
         const unsigned long long nb = qn > 1 ? nm & ((1ull << (qn - 1)) - 1) : 0ull;
         const int pn = nb ? 64 - p2_clz64(nb) : 0;        // top of the unreduced block
         const int qs = qn > 0 ? qn : 1;
-        const dw eq = e[qs - 1];
-        const dw dd = dw_scale(dw_sub(d[qs - 1], d[qs]), 0.5f);
-        dwacc hh = acc_zero();
+        const D eq = e[qs - 1];
+        const D dd = dw_scale(dw_sub(d[qs - 1], d[qs]), 0.5f);
+        acc_t<D> hh = acc0<D>();
         acc_sqr(hh, dd);
         acc_sqr(hh, eq);
-        const dw h = dw_sqrt(acc_val(hh));
-        const dw den = (dd.h >= 0.f) ? dw_add(dd, h) : dw_sub(dd, h);
-        const dw den_s = den.h != 0.f ? den : one;        // (qn = 0 only: value unused)
-        const dw mu = dw_sub(d[qs], dw_div(dw_sqr(eq), den_s));
-        const dw dpn = d[pn], epn = e[pn];
+        const D h = dw_sqrt(acc_val(hh));
+        const D den = (dd.h >= 0.f) ? dw_add(dd, h) : dw_sub(dd, h);
+        const D den_s = den.h != 0.f ? den : one;        // (qn = 0 only: value unused)
+        const D mu = dw_sub(d[qs], dw_div(dw_sqr(eq), den_s));
+        const D dpn = d[pn], epn = e[pn];
         bool clear_top = false;
         if (!sweeping) {
             if (qn == 0) break;
@@ -234,43 +237,43 @@ P2_HD int tridiagonal_qr_dw(int n_rt, DwMat Z, DwVec d, DwVec e, int max_steps,
             clear_top = p > 0;
         }
         // ---- rotation kr -----------------------------------------------------
-        const dw bb = d[kr + 1];
-        const dw en = (kr + 1 < q) ? e[kr + 1] : zero;
+        const D bb = d[kr + 1];
+        const D en = (kr + 1 < q) ? e[kr + 1] : zero;
         const int exx = f_expo(x.h), exz = f_expo(z.h);
         const int ex = exx > exz ? exx : exz;
         const bool nz = ex > 0;
         const float xsc = f_pow2(127 - ex);
-        const dw xs = dw_scale(x, xsc), zs = dw_scale(z, xsc);
-        dwacc ta = acc_zero();
+        const D xs = dw_scale(x, xsc), zs = dw_scale(z, xsc);
+        acc_t<D> ta = acc0<D>();
         acc_sqr(ta, xs);
         acc_sqr(ta, zs);
-        const dw tt = acc_val(ta);
-        const dw ir = dw_rsqrt(nz ? tt : one);
-        const dw c = nz ? dw_mul(xs, ir) : one;
-        const dw s = nz ? dw_neg(dw_mul(zs, ir)) : zero;
-        const dw r = nz ? dw_scale(dw_mul(tt, ir), f_pow2(ex - 127)) : zero;
-        const dw cc = dw_sqr(c), ss = dw_sqr(s), cs = dw_mul(c, s);
-        const dw cs2g = dw_scale(dw_mul(cs, ek), 2.f);
-        dwacc a0 = acc_from(dw_neg(cs2g));
+        const D tt = acc_val(ta);
+        const D ir = dw_rsqrt(nz ? tt : one);
+        const D c = nz ? dw_mul(xs, ir) : one;
+        const D s = nz ? dw_neg(dw_mul(zs, ir)) : zero;
+        const D r = nz ? dw_scale(dw_mul(tt, ir), f_pow2(ex - 127)) : zero;
+        const D cc = dw_sqr(c), ss = dw_sqr(s), cs = dw_mul(c, s);
+        const D cs2g = dw_scale(dw_mul(cs, ek), 2.f);
+        acc_t<D> a0 = acc_from(dw_neg(cs2g));
         acc_fma(a0, cc, dk);
         acc_fma(a0, ss, bb);
-        const dw dkn = acc_val(a0);
-        dwacc a1 = acc_from(cs2g);
+        const D dkn = acc_val(a0);
+        acc_t<D> a1 = acc_from(cs2g);
         acc_fma(a1, ss, dk);
         acc_fma(a1, cc, bb);
-        const dw dk1 = acc_val(a1);
-        dwacc a2 = acc_zero();
+        const D dk1 = acc_val(a1);
+        acc_t<D> a2 = acc0<D>();
         acc_fma(a2, cs, dw_sub(dk, bb));
         acc_fma(a2, dw_sub(cc, ss), ek);
-        const dw ekn = acc_val(a2);
+        const D ekn = acc_val(a2);
         // ---- pending rotation on columns kp, kp + 1, then all stores ----------
         {
-            const dw nsp = dw_neg(sp);
+            const D nsp = dw_neg(sp);
 #pragma unroll
             for (int i = 0; i < NA; ++i)
                 if (i < n) {
-                    const dw a = dw_dot2(cp, za[i], nsp, zb[i]);
-                    const dw b = dw_dot2(sp, za[i], cp, zb[i]);
+                    const D a = dw_dot2(cp, za[i], nsp, zb[i]);
+                    const D b = dw_dot2(sp, za[i], cp, zb[i]);
                     Z(i, kp) = a;
                     Z(i, kp + 1) = b;
                 }
@@ -293,9 +296,9 @@ P2_HD int tridiagonal_qr_dw(int n_rt, DwMat Z, DwVec d, DwVec e, int max_steps,
         }
     }
     {   // flush the last rotation
-        const dw nsp = dw_neg(sp);
+        const D nsp = dw_neg(sp);
         for (int i = 0; i < n; ++i) {
-            const dw za = Z(i, kp), zb = Z(i, kp + 1);
+            const D za = Z(i, kp), zb = Z(i, kp + 1);
             Z(i, kp) = dw_dot2(cp, za, nsp, zb);
             Z(i, kp + 1) = dw_dot2(sp, za, cp, zb);
         }

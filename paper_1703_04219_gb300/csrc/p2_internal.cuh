@@ -250,7 +250,12 @@ cudaError_t launch_get_u(p2_ctx *c, int64_t k0, int64_t k1, int64_t r0, float *U
 cudaError_t launch_gram(const p2_ctx *c, const XView &X, const SmallState *st, dw *G,
                         cudaStream_t s);
 // R > 12: grouped Procrustes kernel (p2_polar_grp.cu)
-cudaError_t polar_grp_configure(int cap);
+// fp64: the FP64 instances (opt-in FP64 arm) instead of the double-word ones
+cudaError_t polar_grp_configure(int cap, bool fp64);
+cudaError_t polar_grp_configure_f64(int cap);
+cudaError_t launch_polar_grp_f64(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
+                                 float *T, int64_t K, cudaStream_t s, double rtol2,
+                                 const int32_t *order, int32_t *qrcnt);
 cudaError_t launch_polar_grp(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
                              float *T, int64_t K, cudaStream_t s, double rtol2,
                              const int32_t *order, int32_t *qrcnt);

@@ -34,7 +34,7 @@ static __device__ __forceinline__ int pk(int i, int j) {   // packed lower index
 // Shared memory: H (scaled, FP32) for the block, then per lane the working
 // matrix (R x R) and the tridiagonal (d, e), interleaved across the lanes:
 // R^2 + 2R double-words per lane.
-template <int R>
+template <int R, class D>
 __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
                                                    const float *__restrict__ W, SmallState *st,
                                                    float *T, int64_t K, float rtol2,
@@ -42,11 +42,12 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
                                                    int32_t *qrcnt) {
     constexpr int P = R * (R + 1) / 2;
     constexpr int HW = (R * R + 1) / 2;                  // double-word slots holding H
-    extern __shared__ __align__(16) dw smd[];
+    extern __shared__ __align__(16) unsigned char smr_raw[];
+    D *smd = reinterpret_cast<D *>(smr_raw);
     const int NT = blockDim.x;
     const int t = threadIdx.x;
     float *Hs = reinterpret_cast<float *>(smd);
-    dw *th = smd + HW;
+    D *th = smd + HW;
     for (int i = t; i < R * R; i += NT) Hs[i] = (float)st->H64[i];   // exact: H is FP32
     __syncthreads();
     int eh = 0;
@@ -59,10 +60,10 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
     unsigned long long flops = 0;
     if (slot < K) {
         const int64_t k = order ? (int64_t)order[slot] : slot;
-        const dw zero = dw_f(0.f);
-        DwMat A{th + t, NT, R};
-        DwVec d{th + (size_t)R * R * NT + t, NT};
-        DwVec e{th + (size_t)(R * R + R) * NT + t, NT};
+        const D zero = num_f<D>(0.f);
+        DwMat<D> A{th + t, NT, R};
+        DwVec<D> d{th + (size_t)R * R * NT + t, NT};
+        DwVec<D> e{th + (size_t)(R * R + R) * NT + t, NT};
         const size_t tb = (size_t)k * R * R;
         const dw *Gk = G + (size_t)k * P;
         float w[R];
@@ -82,30 +83,30 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
         // into the lower triangle of A
         int em = 0;
         {
-            dw g[P];
+            D g[P];
 #pragma unroll
             for (int i = 0, p = 0; i < R; ++i)
 #pragma unroll
                 for (int j = 0; j <= i; ++j, ++p)
-                    g[p] = dw_mul(dw_scale(Gk[p], gsc), two_prod(w[i], w[j]));
+                    g[p] = dw_mul(dw_scale(from_dw<D>(Gk[p]), gsc), num_prod<D>(w[i], w[j]));
 #pragma unroll 1
             for (int c = 0; c < R; ++c) {
                 float hc[R];
 #pragma unroll
                 for (int j = 0; j < R; ++j) hc[j] = Hs[c * R + j];
-                dw tv[R];
+                D tv[R];
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    dwacc s = acc_zero();
+                    acc_t<D> s = acc0<D>();
 #pragma unroll
                     for (int j = 0; j < R; ++j) acc_fmaf(s, g[pk<R>(i, j)], hc[j]);
                     tv[i] = acc_val(s);
                 }
                 for (int r = c; r < R; ++r) {
-                    dwacc s = acc_zero();
+                    acc_t<D> s = acc0<D>();
 #pragma unroll
                     for (int i = 0; i < R; ++i) acc_fmaf(s, tv[i], Hs[r * R + i]);
-                    const dw m = acc_val(s);
+                    const D m = acc_val(s);
                     A(r, c) = m;
                     if (r == c) em = max(em, f_expo(m.h));
                 }
@@ -134,8 +135,8 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
             const float cut = rtol2 * lmax;
 #pragma unroll 1
             for (int i = 0; i < R; ++i) {
-                const dw di = d[i];
-                const dw sf = (lmax > 0.f && di.h > cut) ? dw_sqrt(dw_rsqrt(di)) : zero;  // d^-1/4
+                const D di = d[i];
+                const D sf = (lmax > 0.f && di.h > cut) ? dw_sqrt(dw_rsqrt(di)) : zero;  // d^-1/4
 #pragma unroll
                 for (int r = 0; r < R; ++r) A(r, i) = dw_mul(A(r, i), sf);
             }
@@ -144,12 +145,12 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
             if constexpr (R <= 10) {
                 // C = Z' Z'^T (packed lower, in registers) by rank-one updates,
                 // one column of Z' at a time, then T = C H' S'
-                dwacc C[P];
+                acc_t<D> C[P];
 #pragma unroll
-                for (int p = 0; p < P; ++p) C[p] = acc_zero();
+                for (int p = 0; p < P; ++p) C[p] = acc0<D>();
 #pragma unroll 1
                 for (int i = 0; i < R; ++i) {
-                    dw a[R];
+                    D a[R];
 #pragma unroll
                     for (int r = 0; r < R; ++r) a[r] = A(r, i);
 #pragma unroll
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
 #pragma unroll
                         for (int c = 0; c <= r; ++c, ++p) acc_fma(C[p], a[r], a[c]);
                 }
-                dw Cv[P];
+                D Cv[P];
 #pragma unroll
                 for (int p = 0; p < P; ++p) Cv[p] = acc_val(C[p]);
 #pragma unroll 1
@@ -170,23 +171,23 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
                     for (int u = 0; u < R; ++u) wc = (u == c) ? w[u] : wc;
 #pragma unroll
                     for (int r = 0; r < R; ++r) {             // T(r, c) = (C h'_c)_r w'_c
-                        dwacc t = acc_zero();
+                        acc_t<D> t = acc0<D>();
 #pragma unroll
                         for (int u = 0; u < R; ++u) acc_fmaf(t, Cv[pk<R>(r, u)], hc[u]);
-                        const dw v = dw_mulf(acc_val(t), wc);
-                        T[tb + r * R + c] = f_mul(f_mul(v.h, o1), o2);
+                        const D v = dw_mulf(acc_val(t), wc);
+                        T[tb + r * R + c] = store_f(v, o1, o2);
                     }
                 }
             } else {
 #pragma unroll
-                for (int i = 0; i < R; ++i) e[i] = dw_f(w[i]);    // w' where the T loop can index it
+                for (int i = 0; i < R; ++i) e[i] = num_f<D>(w[i]);    // w' where the T loop can index it
 #pragma unroll 1
                 for (int c = 0; c < R; ++c) {
-                    dw y[R];                                 // y = Z'^T h'_c
+                    D y[R];                                 // y = Z'^T h'_c
                     {
-                        dwacc s[R];
+                        acc_t<D> s[R];
 #pragma unroll
-                        for (int i = 0; i < R; ++i) s[i] = acc_zero();
+                        for (int i = 0; i < R; ++i) s[i] = acc0<D>();
 #pragma unroll 1
                         for (int r = 0; r < R; ++r) {
                             const float hr = Hs[r * R + c];
@@ -198,11 +199,11 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
                     }
 #pragma unroll 1
                     for (int r = 0; r < R; ++r) {             // T(r, c) = (Z' y)_r w'_c
-                        dwacc s = acc_zero();
+                        acc_t<D> s = acc0<D>();
 #pragma unroll
                         for (int i = 0; i < R; ++i) acc_fma(s, A(r, i), y[i]);
-                        const dw v = dw_mulf(acc_val(s), e[c].h);
-                        T[tb + r * R + c] = f_mul(f_mul(v.h, o1), o2);
+                        const D v = dw_mulf(acc_val(s), e[c].h);
+                        T[tb + r * R + c] = store_f(v, o1, o2);
                     }
                 }
             }
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(256) k_order_place(const int32_t *__restrict__
     }
 }
 
-template <int R>
+template <int R, class D>
 static int launch_reg(const p2_ctx *c, const dw *G, const float *W, SmallState *st, float *T,
                       int64_t K, cudaStream_t s, float rtol2, const int32_t *order,
                       int32_t *qrcnt) {
@@ -280,29 +281,36 @@ static int launch_reg(const p2_ctx *c, const dw *G, const float *W, SmallState *
     if (nt < 32) return -1;
     const size_t smem = hbytes + (size_t)nt * per;
     const int nblk = (int)((K + nt - 1) / nt);
-    k_polar_reg<R><<<nblk, nt, smem, s>>>(G, W, st, T, K, rtol2, order, qrcnt);
+    k_polar_reg<R, D><<<nblk, nt, smem, s>>>(G, W, st, T, K, rtol2, order, qrcnt);
     return 0;
+}
+
+template <class D>
+static cudaError_t allow_reg(int cap) {
+    cudaError_t e = cudaSuccess;
+#define P2_ALLOW(r) \
+    if (e == cudaSuccess) \
+        e = cudaFuncSetAttribute(k_polar_reg<r, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)
+    P2_ALLOW(1);
+    P2_ALLOW(2);
+    P2_ALLOW(3);
+    P2_ALLOW(4);
+    P2_ALLOW(5);
+    P2_ALLOW(6);
+    P2_ALLOW(7);
+    P2_ALLOW(8);
+    P2_ALLOW(9);
+    P2_ALLOW(10);
+    P2_ALLOW(11);
+    P2_ALLOW(12);
+#undef P2_ALLOW
+    return e;
 }
 
 int polar_configure(p2_ctx *c) {
     const int cap = c->geo.smem_optin;
-    cudaError_t e = cudaSuccess;
-#define P2_ALLOW(fn) \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)
-    P2_ALLOW(k_polar_reg<1>);
-    P2_ALLOW(k_polar_reg<2>);
-    P2_ALLOW(k_polar_reg<3>);
-    P2_ALLOW(k_polar_reg<4>);
-    P2_ALLOW(k_polar_reg<5>);
-    P2_ALLOW(k_polar_reg<6>);
-    P2_ALLOW(k_polar_reg<7>);
-    P2_ALLOW(k_polar_reg<8>);
-    P2_ALLOW(k_polar_reg<9>);
-    P2_ALLOW(k_polar_reg<10>);
-    P2_ALLOW(k_polar_reg<11>);
-    P2_ALLOW(k_polar_reg<12>);
-#undef P2_ALLOW
-    if (e == cudaSuccess) e = polar_grp_configure(cap);
+    cudaError_t e = c->opt.fp64_procrustes ? allow_reg<f64n>(cap) : allow_reg<dw>(cap);
+    if (e == cudaSuccess) e = polar_grp_configure(cap, c->opt.fp64_procrustes != 0);
     if (e != cudaSuccess) {
         set_error("configuring the Procrustes kernels: %s", cudaGetErrorString(e));
         return P2_ECUDA;
@@ -320,10 +328,12 @@ cudaError_t launch_polar_on(const p2_ctx *c, const dw *G, const float *W, SmallS
     if (K <= 0) return cudaSuccess;
     if (R > 12) return launch_polar_grp(c, G, W, st, T, K, s, rtol2, order, qrcnt);
     const float rt2 = (float)rtol2;
+    const bool f64 = c->opt.fp64_procrustes != 0;
     int rc = -1;
     switch (R) {
 #define P2_CASE(r) \
-        case r: rc = launch_reg<r>(c, G, W, st, T, K, s, rt2, order, qrcnt); break;
+        case r: rc = f64 ? launch_reg<r, f64n>(c, G, W, st, T, K, s, rt2, order, qrcnt) \
+                         : launch_reg<r, dw>(c, G, W, st, T, K, s, rt2, order, qrcnt); break;
         P2_CASE(1) P2_CASE(2) P2_CASE(3) P2_CASE(4) P2_CASE(5) P2_CASE(6)
         P2_CASE(7) P2_CASE(8) P2_CASE(9) P2_CASE(10) P2_CASE(11) P2_CASE(12)
 #undef P2_CASE

@@ -1,9 +1,10 @@
-// Procrustes kernel for larger R: eight lanes per subject, double-word
-// arithmetic (p2_dw.cuh).  Included by p2_polar_grp.cu; needs the flop
+// Procrustes kernel for larger R: eight or sixteen lanes per subject,
+// double-word arithmetic (p2_dw.cuh) or, for the opt-in FP64 arm, FP64
+// (p2_num.cuh).  Included by p2_polar_grp.cu; needs the flop
 // helpers (p2_polar.cuh), SmallState and FLAG_EIG_NOCONV.
 #pragma once
 
-#include "p2_dw.cuh"
+#include "p2_num.cuh"
 
 namespace p2 {
 
@@ -32,10 +33,13 @@ inline __host__ __device__ size_t grp_hdws(int R) { return ((size_t)R * R + 1) /
 static __device__ __forceinline__ dw shfl_xor_dw(unsigned mask, dw v, int o) {
     return dw{__shfl_xor_sync(mask, v.h, o), __shfl_xor_sync(mask, v.l, o)};
 }
+static __device__ __forceinline__ f64n shfl_xor_dw(unsigned mask, f64n v, int o) {
+    return f64n{__shfl_xor_sync(mask, v.h, o)};
+}
 // sum over the PG lanes of a group (same result on every lane: the
 // butterfly adds the same two operands in the same order on both partners)
-template <int PG>
-static __device__ __forceinline__ dw group_sum(unsigned mask, dw v) {
+template <int PG, class D>
+static __device__ __forceinline__ D group_sum(unsigned mask, D v) {
 #pragma unroll
     for (int o = PG / 2; o > 0; o >>= 1) v = dw_add(v, shfl_xor_dw(mask, v, o));
     return v;
@@ -59,7 +63,7 @@ static __device__ __forceinline__ unsigned long long group_or(unsigned mask, uns
     return v;
 }
 
-template <int RB, int PG, int RT = 0>
+template <int RB, int PG, int RT = 0, class D = dw>
 __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                                                       const float *__restrict__ W, SmallState *st,
                                                       float *T, int64_t K, int R_rt, float rtol2,
@@ -67,14 +71,15 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                                                       int32_t *qrcnt) {
     const int R = RT > 0 ? RT : R_rt;   // RT > 0: the rank fixed at compile time
     constexpr int RPL = RB / PG;                     // rows per lane
-    extern __shared__ __align__(16) dw smg[];
+    extern __shared__ __align__(16) unsigned char smg_raw[];
+    D *smg = reinterpret_cast<D *>(smg_raw);
     __shared__ int s_eh;
     const int lane = threadIdx.x & 31;
     const int gl = lane & (PG - 1);
     const unsigned gmask = (unsigned)((1ull << PG) - 1) << (lane & ~(PG - 1));
     const int slot = threadIdx.x / PG;
     const int64_t kslot = (int64_t)blockIdx.x * spb + slot;
-    const dw one = dw_f(1.f), zero = dw_f(0.f);
+    const D one = num_f<D>(1.f), zero = num_f<D>(0.f);
     float *Hs = reinterpret_cast<float *>(smg);
     if (threadIdx.x == 0) s_eh = 0;
     __syncthreads();
@@ -97,11 +102,11 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
     if (slot < spb && kslot < K) {
         const int64_t k = order ? (int64_t)order[kslot] : kslot;
         const int LD = grp_ld(R);
-        dw *base = smg + grp_hdws(R) + (size_t)slot * grp_dws(R);
-        auto A = [base, LD](int i, int j) -> dw & { return base[i * LD + j]; };
-        dw *d = base + (size_t)R * LD;
-        dw *e = d + R;
-        dw *t = e + R;
+        D *base = smg + grp_hdws(R) + (size_t)slot * grp_dws(R);
+        auto A = [base, LD](int i, int j) -> D & { return base[i * LD + j]; };
+        D *d = base + (size_t)R * LD;
+        D *e = d + R;
+        D *t = e + R;
         float *wv = reinterpret_cast<float *>(t + R);
         const dw *Gk = G + (size_t)k * (R * (R + 1) / 2);
         const size_t tb = (size_t)k * R * R;
@@ -130,18 +135,18 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
         for (int ii = 0; ii < RPL; ++ii) {
             const int i = gl + PG * ii;
             if (i >= R) break;
-            dw b[RB];
+            D b[RB];
             const float wi = wv[i];
 #pragma unroll
             for (int j = 0; j < RB; ++j) {
                 if (j < R) {
                     const int p = (j <= i) ? (i * (i + 1) / 2 + j) : (j * (j + 1) / 2 + i);
-                    b[j] = dw_mul(dw_scale(Gk[p], gsc), two_prod(wi, wv[j]));
+                    b[j] = dw_mul(dw_scale(from_dw<D>(Gk[p]), gsc), num_prod<D>(wi, wv[j]));
                 }
             }
 #pragma unroll 1
             for (int c = 0; c < R; ++c) {
-                dwacc s = acc_zero();
+                acc_t<D> s = acc0<D>();
 #pragma unroll
                 for (int j = 0; j < RB; ++j)
                     if (j < R) acc_fmaf(s, b[j], Hs[c * R + j]);
@@ -153,7 +158,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
         int em = 0;
 #pragma unroll 1
         for (int c = 0; c < R; ++c) {
-            dw u[RB];
+            D u[RB];
 #pragma unroll
             for (int i = 0; i < RB; ++i)
                 if (i < R) u[i] = A(i, c);
@@ -163,11 +168,11 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                 const int r = gl + PG * ii;
                 if (r >= R) break;
                 if (r < c) continue;
-                dwacc s = acc_zero();
+                acc_t<D> s = acc0<D>();
 #pragma unroll
                 for (int i = 0; i < RB; ++i)
                     if (i < R) acc_fmaf(s, u[i], Hs[r * R + i]);
-                const dw m = acc_val(s);
+                const D m = acc_val(s);
                 A(r, c) = m;
                 if (r == c) em = max(em, f_expo(m.h));
             }
@@ -192,12 +197,12 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
             // ---- Householder tridiagonalisation (lower triangle) ----------
 #pragma unroll 1
             for (int kk = 0; kk + 2 < R; ++kk) {
-                dwacc sa = acc_zero();
+                acc_t<D> sa = acc0<D>();
                 for (int i = gl; i < R; i += PG)
                     if (i >= kk + 2) acc_sqr(sa, A(i, kk));
-                const dw sig = group_sum<PG>(gmask, acc_val(sa));
-                const dw x0 = A(kk + 1, kk);
-                if (!(sig.h >= DW_TINY2)) {          // reflector as in p2_eig_dw.cuh
+                const D sig = group_sum<PG>(gmask, acc_val(sa));
+                const D x0 = A(kk + 1, kk);
+                if (!(sig.h >= NumT<D>::tiny2())) {          // reflector as in p2_eig_dw.cuh
                     __syncwarp(gmask);
                     if (gl == 0) {
                         A(kk, kk + 1) = zero;
@@ -206,12 +211,12 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                     __syncwarp(gmask);
                     continue;
                 }
-                dwacc m2 = acc_from(sig);
+                acc_t<D> m2 = acc_from(sig);
                 acc_sqr(m2, x0);
-                const dw mu = dw_sqrt(acc_val(m2));
-                const dw beta = (x0.h >= 0.f) ? dw_neg(mu) : mu;
-                const dw bh = dw_div(dw_sub(beta, x0), beta);
-                const dw inv_v0 = dw_recip(dw_sub(x0, beta));
+                const D mu = dw_sqrt(acc_val(m2));
+                const D beta = (x0.h >= 0.f) ? dw_neg(mu) : mu;
+                const D bh = dw_div(dw_sub(beta, x0), beta);
+                const D inv_v0 = dw_recip(dw_sub(x0, beta));
                 __syncwarp(gmask);
                 for (int i = gl; i < R; i += PG)
                     if (i >= kk + 2) A(i, kk) = dw_mul(A(i, kk), inv_v0);
@@ -221,21 +226,21 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                 }
                 __syncwarp(gmask);
                 // p = bh A22 v on my rows, pv = p . v
-                dwacc pa = acc_zero();
+                acc_t<D> pa = acc0<D>();
                 for (int i = gl; i < R; i += PG) {
                     if (i < kk + 1) continue;
-                    dwacc s = acc_from(A(i, kk + 1));
+                    acc_t<D> s = acc_from(A(i, kk + 1));
                     for (int j = kk + 2; j < R; ++j)
                         acc_fma(s, (j <= i) ? A(i, j) : A(j, i), A(j, kk));
-                    const dw si = dw_mul(acc_val(s), bh);
+                    const D si = dw_mul(acc_val(s), bh);
                     t[i] = si;
                     if (i == kk + 1)
                         acc_add(pa, si);
                     else
                         acc_fma(pa, si, A(i, kk));
                 }
-                const dw pv = group_sum<PG>(gmask, acc_val(pa));
-                const dw nK = dw_neg(dw_mul(dw_scale(bh, 0.5f), pv));
+                const D pv = group_sum<PG>(gmask, acc_val(pa));
+                const D nK = dw_neg(dw_mul(dw_scale(bh, 0.5f), pv));
                 for (int i = gl; i < R; i += PG) {
                     if (i == kk + 1)
                         t[i] = dw_add(t[i], nK);
@@ -245,10 +250,10 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                 __syncwarp(gmask);
                 for (int i = gl; i < R; i += PG) {
                     if (i < kk + 1) continue;
-                    const dw nvi = dw_neg((i == kk + 1) ? one : A(i, kk));
-                    const dw nwi = dw_neg(t[i]);
+                    const D nvi = dw_neg((i == kk + 1) ? one : A(i, kk));
+                    const D nwi = dw_neg(t[i]);
                     for (int j = kk + 1; j <= i; ++j) {
-                        dwacc a = acc_from(A(i, j));
+                        acc_t<D> a = acc_from(A(i, j));
                         acc_fma(a, nvi, t[j]);
                         if (j == kk + 1)
                             acc_add(a, nwi);
@@ -275,9 +280,9 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                 __syncwarp(gmask);
 #pragma unroll 1
                 for (int kk = R - 3; kk >= 0; --kk) {
-                    const dw bh = A(kk, kk + 1);
+                    const D bh = A(kk, kk + 1);
                     __syncwarp(gmask);
-                    const dw nb = dw_neg(bh);
+                    const D nb = dw_neg(bh);
                     const bool act = bh.h != 0.f;
                     for (int j = gl; j < R; j += PG) {
                         if (j == kk + 1) {                    // column e_{k+1} -> (1 - b, -b v)
@@ -291,9 +296,9 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                     if (act) {
                         for (int c = gl; c < R; c += PG) {
                             if (c < kk + 2) continue;
-                            dwacc s = acc_zero();             // A(kk+1, c) = 0 here
+                            acc_t<D> s = acc0<D>();             // A(kk+1, c) = 0 here
                             for (int i = kk + 2; i < R; ++i) acc_fma(s, A(i, kk), A(i, c));
-                            const dw ns = dw_mul(acc_val(s), nb);
+                            const D ns = dw_mul(acc_val(s), nb);
                             A(kk + 1, c) = ns;
                             for (int i = kk + 2; i < R; ++i) A(i, c) = dw_fma(ns, A(i, kk), A(i, c));
                         }
@@ -328,14 +333,14 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                 an = fmaxf(an, r);
             }
             an = group_maxf<PG>(gmask, an);
-            const int tiny_ex = f_expo(an) - DW_DEFLATE_BITS;
+            const int tiny_ex = f_expo(an) - NumT<D>::deflate_bits;
             int steps = 0, rot = 0;
             const int max_steps = 30 * R;
             int q = R - 1, p = 0, kr = 0;
             bool sweeping = false, failed = false;
-            dw x = zero, z = zero, dk = zero, ek = zero;
+            D x = zero, z = zero, dk = zero, ek = zero;
             int kp = 0;
-            dw cp = one, sp = zero;
+            D cp = one, sp = zero;
 #pragma unroll 1
             while (true) {
                 if (!sweeping) {
@@ -356,14 +361,14 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                         break;
                     }
                     rot += q - p;
-                    const dw eq = e[q - 1];
-                    const dw dd = dw_scale(dw_sub(d[q - 1], d[q]), 0.5f);
-                    dwacc hh = acc_zero();
+                    const D eq = e[q - 1];
+                    const D dd = dw_scale(dw_sub(d[q - 1], d[q]), 0.5f);
+                    acc_t<D> hh = acc0<D>();
                     acc_sqr(hh, dd);
                     acc_sqr(hh, eq);
-                    const dw h = dw_sqrt(acc_val(hh));
-                    const dw den = (dd.h >= 0.f) ? dw_add(dd, h) : dw_sub(dd, h);
-                    const dw mu = dw_sub(d[q], dw_div(dw_sqr(eq), den));
+                    const D h = dw_sqrt(acc_val(hh));
+                    const D den = (dd.h >= 0.f) ? dw_add(dd, h) : dw_sub(dd, h);
+                    const D mu = dw_sub(d[q], dw_div(dw_sqr(eq), den));
                     dk = d[p];
                     ek = e[p];
                     x = dw_sub(dk, mu);
@@ -373,10 +378,10 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                     __syncwarp(gmask);
                     if (gl == 0 && p > 0) e[p - 1] = zero;
                 }
-                const dw bb = d[kr + 1];
-                const dw en = (kr + 1 < q) ? e[kr + 1] : zero;
+                const D bb = d[kr + 1];
+                const D en = (kr + 1 < q) ? e[kr + 1] : zero;
                 __syncwarp(gmask);
-                dw za[RPL], zb[RPL];
+                D za[RPL], zb[RPL];
 #pragma unroll
                 for (int ii = 0; ii < RPL; ++ii) {
                     const int i = gl + PG * ii;
@@ -388,31 +393,31 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                 const int ex = max(f_expo(x.h), f_expo(z.h));   // scaled as in p2_eig_dw.cuh
                 const bool nz = ex > 0;
                 const float xsc = f_pow2(127 - ex);
-                const dw xs = dw_scale(x, xsc), zs = dw_scale(z, xsc);
-                dwacc ta = acc_zero();
+                const D xs = dw_scale(x, xsc), zs = dw_scale(z, xsc);
+                acc_t<D> ta = acc0<D>();
                 acc_sqr(ta, xs);
                 acc_sqr(ta, zs);
-                const dw tt = acc_val(ta);
-                const dw ir = dw_rsqrt(nz ? tt : one);
-                const dw c = nz ? dw_mul(xs, ir) : one;
-                const dw s = nz ? dw_neg(dw_mul(zs, ir)) : zero;
-                const dw rr = nz ? dw_scale(dw_mul(tt, ir), f_pow2(ex - 127)) : zero;
-                const dw cc = dw_sqr(c), ss = dw_sqr(s), cs = dw_mul(c, s);
-                const dw cs2g = dw_scale(dw_mul(cs, ek), 2.f);
-                dwacc a0 = acc_from(dw_neg(cs2g));
+                const D tt = acc_val(ta);
+                const D ir = dw_rsqrt(nz ? tt : one);
+                const D c = nz ? dw_mul(xs, ir) : one;
+                const D s = nz ? dw_neg(dw_mul(zs, ir)) : zero;
+                const D rr = nz ? dw_scale(dw_mul(tt, ir), f_pow2(ex - 127)) : zero;
+                const D cc = dw_sqr(c), ss = dw_sqr(s), cs = dw_mul(c, s);
+                const D cs2g = dw_scale(dw_mul(cs, ek), 2.f);
+                acc_t<D> a0 = acc_from(dw_neg(cs2g));
                 acc_fma(a0, cc, dk);
                 acc_fma(a0, ss, bb);
-                const dw dkn = acc_val(a0);
-                dwacc a1 = acc_from(cs2g);
+                const D dkn = acc_val(a0);
+                acc_t<D> a1 = acc_from(cs2g);
                 acc_fma(a1, ss, dk);
                 acc_fma(a1, cc, bb);
-                const dw dk1 = acc_val(a1);
-                dwacc a2 = acc_zero();
+                const D dk1 = acc_val(a1);
+                acc_t<D> a2 = acc0<D>();
                 acc_fma(a2, cs, dw_sub(dk, bb));
                 acc_fma(a2, dw_sub(cc, ss), ek);
-                const dw ekn = acc_val(a2);
+                const D ekn = acc_val(a2);
                 {
-                    const dw nsp = dw_neg(sp);
+                    const D nsp = dw_neg(sp);
 #pragma unroll
                     for (int ii = 0; ii < RPL; ++ii) {
                         const int i = gl + PG * ii;
@@ -445,9 +450,9 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
             }
             __syncwarp(gmask);
             if (R > 1) {                                 // flush the last rotation
-                const dw nsp = dw_neg(sp);
+                const D nsp = dw_neg(sp);
                 for (int i = gl; i < R; i += PG) {
-                    const dw zk = A(i, kp), zk1 = A(i, kp + 1);
+                    const D zk = A(i, kp), zk1 = A(i, kp + 1);
                     A(i, kp) = dw_dot2(cp, zk, nsp, zk1);
                     A(i, kp + 1) = dw_dot2(sp, zk, cp, zk1);
                 }
@@ -461,8 +466,8 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
             lmax = group_maxf<PG>(gmask, lmax);
             const float cut = rtol2 * lmax;
             for (int i = gl; i < R; i += PG) {
-                const dw di = d[i];
-                const dw sf = (lmax > 0.f && di.h > cut) ? dw_sqrt(dw_rsqrt(di)) : zero;
+                const D di = d[i];
+                const D sf = (lmax > 0.f && di.h > cut) ? dw_sqrt(dw_rsqrt(di)) : zero;
                 for (int r = 0; r < R; ++r) A(r, i) = dw_mul(A(r, i), sf);
             }
             __syncwarp(gmask);
@@ -472,12 +477,12 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
 #pragma unroll 1
             for (int c = 0; c < R; ++c) {
                 for (int i = gl; i < R; i += PG) {       // t = Z'^T h'_c on my columns
-                    dwacc s = acc_zero();
+                    acc_t<D> s = acc0<D>();
                     for (int r = 0; r < R; ++r) acc_fmaf(s, A(r, i), Hs[r * R + c]);
                     t[i] = acc_val(s);
                 }
                 __syncwarp(gmask);
-                dw tv[RB];
+                D tv[RB];
 #pragma unroll
                 for (int i = 0; i < RB; ++i)
                     if (i < R) tv[i] = t[i];
@@ -487,12 +492,12 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                 for (int ii = 0; ii < RPL; ++ii) {
                     const int r = gl + PG * ii;
                     if (r >= R) break;
-                    dwacc s = acc_zero();
+                    acc_t<D> s = acc0<D>();
 #pragma unroll
                     for (int i = 0; i < RB; ++i)
                         if (i < R) acc_fma(s, A(r, i), tv[i]);
-                    const dw v = dw_mulf(acc_val(s), wc);
-                    T[tb + r * R + c] = f_mul(f_mul(v.h, o1), o2);
+                    const D v = dw_mulf(acc_val(s), wc);
+                    T[tb + r * R + c] = store_f(v, o1, o2);
                 }
             }
             if (gl == 0) {

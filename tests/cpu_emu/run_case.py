@@ -29,13 +29,15 @@ def bf16_round(a):
 
 def iterate_case(name, K, R, precision="fp32"):
     nonneg = precision == "nonneg"
-    if nonneg:
+    fp64 = precision == "fp64"                # the FP64 arm of the Procrustes step
+    if nonneg or fp64:
         precision = "fp32"
     X = synth.generate(name, K=K)
     H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=11)
     if precision == "bf16":                # a start that bfloat16 storage represents exactly
         V0 = bf16_round(V0)
-    with p2.Parafac2(R, use_graph=False, precision=precision, nonneg=nonneg) as m:
+    with p2.Parafac2(R, use_graph=False, precision=precision, nonneg=nonneg,
+                     fp64_procrustes=fp64) as m:
         m.load(X)
         m.init(H0, V0, W0)
         fit = m.iterate(1)

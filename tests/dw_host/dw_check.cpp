@@ -10,6 +10,8 @@
 //                           already scaled to unit size), prints the step
 //                           count, then d (n values) and Z (n*n, row-major)
 //                           as double values of the double-word results
+//   dw_check eig64 n        the same decomposition compiled for FP64 (the
+//                           opt-in FP64 arm of the Procrustes step)
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -53,17 +55,23 @@ static int ops() {
     return 0;
 }
 
+static double val(f64n x) { return x.h; }
+template <class D> static D rd_t(double x);
+template <> dw rd_t<dw>(double x) { return rd(x); }
+template <> f64n rd_t<f64n>(double x) { return f64n{x}; }
+
+template <class D>
 static int eig(int n) {
     std::vector<double> m((size_t)n * n);
     for (auto &v : m)
         if (std::scanf("%lf", &v) != 1) return 2;
     // interleaved layout with stride 1: A (n x n), then d, e
-    std::vector<dw> buf((size_t)n * n + 2 * (size_t)n);
-    DwMat A{buf.data(), 1, n};
-    DwVec d{buf.data() + (size_t)n * n, 1};
-    DwVec e{buf.data() + (size_t)n * n + n, 1};
+    std::vector<D> buf((size_t)n * n + 2 * (size_t)n);
+    DwMat<D> A{buf.data(), 1, n};
+    DwVec<D> d{buf.data() + (size_t)n * n, 1};
+    DwVec<D> e{buf.data() + (size_t)n * n + n, 1};
     for (int i = 0; i < n; ++i)
-        for (int j = 0; j <= i; ++j) A(i, j) = rd(m[(size_t)i * n + j]);
+        for (int j = 0; j <= i; ++j) A(i, j) = rd_t<D>(m[(size_t)i * n + j]);
     tridiagonalize_dw<0>(n, A, d, e);
     int rot = 0;
     const int steps = tridiagonal_qr_dw<0>(n, A, d, e, 30 * n, &rot);
@@ -76,7 +84,8 @@ static int eig(int n) {
 
 int main(int argc, char **argv) {
     if (argc >= 2 && !std::strcmp(argv[1], "ops")) return ops();
-    if (argc >= 3 && !std::strcmp(argv[1], "eig")) return eig(std::atoi(argv[2]));
-    std::fprintf(stderr, "usage: dw_check ops | dw_check eig n\n");
+    if (argc >= 3 && !std::strcmp(argv[1], "eig")) return eig<dw>(std::atoi(argv[2]));
+    if (argc >= 3 && !std::strcmp(argv[1], "eig64")) return eig<f64n>(std::atoi(argv[2]));
+    std::fprintf(stderr, "usage: dw_check ops | dw_check eig n | dw_check eig64 n\n");
     return 2;
 }

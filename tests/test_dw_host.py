@@ -12,7 +12,9 @@ them:
   sub-diagonals far below the FP32 normal range once squared): it must
   converge, Z must be orthogonal and Z diag(d) Z^T must reproduce M to a few
   2^-44 of ||M||, and d must match LAPACK's FP64 eigenvalues (numpy.linalg.eigvalsh)
-  to the same normwise bound (Weyl's inequality).
+  to the same normwise bound (Weyl's inequality);
+* the same code compiled for FP64 (the opt-in FP64 arm) to a bound 16x
+  tighter.
 No GPU involved."""
 import os
 import shutil
@@ -120,9 +122,9 @@ def test_primitives_against_exact_rationals(exe):
             assert abs(got - ref) <= k * U2 * scale, (op, x, y, z, float(abs(got - ref) / scale))
 
 
-def _eig(exe, M):
+def _eig(exe, M, mode="eig"):
     n = M.shape[0]
-    r = subprocess.run([exe, "eig", str(n)], input="\n".join(repr(float(v)) for v in M.ravel()),
+    r = subprocess.run([exe, mode, str(n)], input="\n".join(repr(float(v)) for v in M.ravel()),
                        capture_output=True, text=True, check=True)
     vals = [float(t) for t in r.stdout.split()]
     steps = int(vals[0])
@@ -174,6 +176,23 @@ def test_eigen_decomposition_against_lapack(exe, name, M):
     assert np.all(np.isfinite(d)) and np.all(np.isfinite(Z)), name
     nrm = max(np.abs(np.linalg.eigvalsh(M)).max(), np.finfo(float).tiny)
     bound = 2.0 ** -42 * n
+    assert np.abs(Z.T @ Z - np.eye(n)).max() <= bound, (name, np.abs(Z.T @ Z - np.eye(n)).max())
+    assert np.abs((Z * d) @ Z.T - M).max() <= bound * nrm, (name, np.abs((Z * d) @ Z.T - M).max())
+    ref = np.linalg.eigvalsh(M)
+    assert np.abs(np.sort(d) - ref).max() <= bound * nrm, (name, np.abs(np.sort(d) - ref).max())
+
+
+@pytest.mark.parametrize("name,M", _matrices(), ids=[m[0] for m in _matrices()])
+def test_fp64_eigen_decomposition_against_lapack(exe, name, M):
+    """The same Householder + QR code compiled for FP64 (the opt-in FP64 arm
+    of the Procrustes step): a few 2^-50 n normwise, 16x tighter than the
+    double-word bound above."""
+    n = M.shape[0]
+    steps, d, Z = _eig(exe, M, "eig64")
+    assert steps >= 0, f"{name}: no convergence"
+    assert np.all(np.isfinite(d)) and np.all(np.isfinite(Z)), name
+    nrm = max(np.abs(np.linalg.eigvalsh(M)).max(), np.finfo(float).tiny)
+    bound = 2.0 ** -46 * n
     assert np.abs(Z.T @ Z - np.eye(n)).max() <= bound, (name, np.abs(Z.T @ Z - np.eye(n)).max())
     assert np.abs((Z * d) @ Z.T - M).max() <= bound * nrm, (name, np.abs((Z * d) @ Z.T - M).max())
     ref = np.linalg.eigvalsh(M)

@@ -8,8 +8,9 @@ within 1e-6 + 1e-8 cond(A_k) per subject: the FP32 storage of T_k allows
 cond(A_k)^2 and fails the bound for most subjects (the CPU emulation in
 tests/test_gram_sensitivity.py shows both on this fixture).  This pins the
 error-free Gram of the alpha pass and the double-word eigen-decomposition on
-the lane kernel (R = 5, 10) and the grouped kernel (R = 40), after the first
-Q-step (p2_init) and after one iteration.
+the lane kernel (R = 5, 10) and the grouped kernel (R = 40), and the FP64
+arm of the Procrustes step at R = 10 and 40, after the first Q-step
+(p2_init) and after one iteration.
 """
 import numpy as np
 import pytest
@@ -48,11 +49,13 @@ def _check(X, H, V, W, T):
     return np.asarray(conds), worst
 
 
-@pytest.mark.parametrize("name,K,R", [("tiny", 200, 5), ("c63m", 300, 10), ("c250m", 150, 40)])
-def test_ill_conditioned_procrustes_matches_oracle(p2, name, K, R):
+@pytest.mark.parametrize("name,K,R,fp64", [("tiny", 200, 5, False), ("c63m", 300, 10, False),
+                                           ("c250m", 150, 40, False), ("c63m", 300, 10, True),
+                                           ("c250m", 150, 40, True)])
+def test_ill_conditioned_procrustes_matches_oracle(p2, name, K, R, fp64):
     X = synth.generate(name, K=K)
     H0, V0, W0 = near_dependent_start(R, X.J, X.K, seed=11)
-    with p2.Parafac2(R) as m:
+    with p2.Parafac2(R, fp64_procrustes=fp64) as m:
         m.load(X)
         m.init(H0, V0, W0)
         T0 = m.procrustes()

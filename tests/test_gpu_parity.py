@@ -24,9 +24,9 @@ def p2():
     return mod
 
 
-def _one_step(p2, X, R, seed):
+def _one_step(p2, X, R, seed, **kw):
     H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=seed)
-    with p2.Parafac2(R) as m:
+    with p2.Parafac2(R, **kw) as m:
         m.load(X)
         m.init(H0, V0, W0)
         fit = m.iterate(1)
@@ -48,6 +48,22 @@ def _one_step(p2, X, R, seed):
 def test_one_step_parity(p2, name, K, R):
     X = synth.generate(name, K=K)
     out = _one_step(p2, X, R, seed=11)
+    ref = out["ref"]
+    for mode, key in ((1, "M1"), (2, "M2"), (3, "M3")):
+        assert rel_fro(out["M"][mode], ref[key]) < TOL, (key, rel_fro(out["M"][mode], ref[key]))
+    for key in ("H", "V", "W"):
+        assert rel_fro(out[key], ref[key]) < TOL, (key, rel_fro(out[key], ref[key]))
+    assert abs(out["fit"] - out["ref_fit"]) < FIT_TOL
+
+
+@pytest.mark.parametrize("name,K,R", [("tiny", 200, 5), ("c63m", 3000, 10), ("c250m", 400, 40),
+                                      ("c250m", 300, 20), ("tiny", 150, 13)])
+def test_fp64_procrustes_one_step_parity(p2, name, K, R):
+    """The opt-in FP64 arm of the Procrustes step (p2_options.fp64_procrustes:
+    the same Householder + QR eigen-decomposition and T_k formation in FP64 on
+    the FP64 pipe) against the oracle, at the FP32 tolerances."""
+    X = synth.generate(name, K=K)
+    out = _one_step(p2, X, R, seed=11, fp64_procrustes=True)
     ref = out["ref"]
     for mode, key in ((1, "M1"), (2, "M2"), (3, "M3")):
         assert rel_fro(out["M"][mode], ref[key]) < TOL, (key, rel_fro(out["M"][mode], ref[key]))

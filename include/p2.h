@@ -40,7 +40,8 @@ enum {
     P2_ECUDA = 3,      /* a CUDA runtime call failed */
     P2_ENUMERIC = 4,   /* non-finite loss detected */
     P2_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
-    P2_ESTATE = 6      /* call out of order (e.g. p2_iterate before p2_init) */
+    P2_ESTATE = 6,     /* call out of order (e.g. p2_iterate before p2_init) */
+    P2_EEXCHANGE = 7   /* the exchange hook of a sharded context reported a failure */
 };
 
 /* Storage precision of V and of the in-flight mode-2 rows P_k = Q_k H S_k (a
@@ -66,8 +67,8 @@ typedef struct {
     int32_t timing;       /* non-zero: CUDA events around each phase of an iteration (p2_stats) */
     uint64_t seed;        /* seed of the initial factors p2_init draws when given NULLs */
     int32_t nonneg;       /* non-zero: S_k and V constrained non-negative (Section 5.1), the
-                             W and V updates solved row by row as non-negative least squares;
-                             requires R <= 16 */
+                             W and V updates solved row by row as non-negative least squares
+                             (one lane per row for R <= 16, one warp per row above) */
     int32_t fp64_procrustes; /* non-zero: the Procrustes step's eigen-decomposition and the
                              formation of T_k run in FP64 on the FP64 pipe (same algorithm,
                              Householder + implicit QR); zero (default): in double-word
@@ -267,6 +268,38 @@ int p2_project(p2_projector *pj, int64_t n_req, const int64_t *subj_ptr, const i
 
 /* Wait until the projector's enqueued work has finished. */
 int p2_projector_sync(p2_projector *pj);
+
+/*
+ * Subject-sharded form.  The subjects are independent except for a few sums
+ * over all of them (Algorithm 3's mode-1 and mode-2 MTTKRPs, W^TW and the
+ * loss terms), so a collection may be split into contiguous subject ranges,
+ * one context per range (on one GPU or several), each loading only its own
+ * slices.  An exchange hook then sums the contexts' partial results, and H
+ * and V are solved redundantly (identically) on every shard; W's rows stay
+ * with their shard.
+ *
+ * The hook is called with a device buffer of `count` doubles (on the
+ * context's device) and the context's stream, after the work that produced
+ * the buffer has been enqueued on that stream.  It must replace the buffer
+ * by its elementwise sum over all shards so that work enqueued on `stream`
+ * afterwards sees the sum (for example by enqueueing an allreduce on that
+ * stream, or by synchronising the stream, combining through the host and
+ * copying back), and return 0, or non-zero on failure (the library call
+ * then returns P2_EEXCHANGE).  Every shard makes the same sequence of hook
+ * calls with the same counts: at p2_load_slices (J + 1 values: column
+ * counts, so that every shard relabels the columns alike, and ||X||^2),
+ * after every Q-step's statistics (2 R^2 + 1 values: mode 1, W^TW,
+ * <W, M3>) and after every mode-2 pass (J R values: M2).  Each sum must be
+ * bitwise the same on every shard (an allreduce gives that), so that the
+ * replicated H and V stay identical.
+ *
+ * p2_set_exchange must be called before p2_load_slices (P2_ESTATE
+ * otherwise).  A sharded context does not capture its iteration in a CUDA
+ * graph (use_graph is ignored), and p2_init_eig returns P2_EINVAL.  fn ==
+ * NULL leaves the context unsharded.
+ */
+typedef int (*p2_exchange_fn)(double *buf, int64_t count, void *stream, void *user);
+int p2_set_exchange(p2_ctx *ctx, p2_exchange_fn fn, void *user);
 
 /* Counters and the last iteration's phase timings.  Synchronises. */
 int p2_stats(p2_ctx *ctx, p2_stats_t *out);

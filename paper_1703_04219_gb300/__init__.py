@@ -17,10 +17,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libp2.so")
 
-P2_OK, P2_EINVAL, P2_ENOMEM, P2_ECUDA, P2_ENUMERIC, P2_ETIMEOUT, P2_ESTATE = range(7)
+P2_OK, P2_EINVAL, P2_ENOMEM, P2_ECUDA, P2_ENUMERIC, P2_ETIMEOUT, P2_ESTATE, P2_EEXCHANGE = range(8)
 P2_FP32, P2_BF16 = 0, 1
 _NAMES = {0: "P2_OK", 1: "P2_EINVAL", 2: "P2_ENOMEM", 3: "P2_ECUDA", 4: "P2_ENUMERIC",
-          5: "P2_ETIMEOUT", 6: "P2_ESTATE"}
+          5: "P2_ETIMEOUT", 6: "P2_ESTATE", 7: "P2_EEXCHANGE"}
 
 # every symbol include/p2.h declares
 EXPORTED = ("p2_default_options", "p2_create", "p2_destroy", "p2_load_slices", "p2_init",
@@ -28,7 +28,7 @@ EXPORTED = ("p2_default_options", "p2_create", "p2_destroy", "p2_load_slices", "
             "p2_iterate", "p2_fit", "p2_get_factors", "p2_set_factors", "p2_get_mttkrp",
             "p2_get_procrustes", "p2_get_U", "p2_iterate_until", "p2_stats", "p2_device_bytes", "p2_mode1_stats_noalloc",
             "p2_projector_create", "p2_projector_destroy", "p2_project", "p2_projector_sync",
-            "p2_last_error")
+            "p2_set_exchange", "p2_last_error")
 
 
 class p2_options(ctypes.Structure):
@@ -84,6 +84,7 @@ def _load():
         "p2_projector_destroy": ([vp], ctypes.c_int),
         "p2_project": ([vp, i64, vp, vp, vp, vp, i32, i32, vp, vp, i32], ctypes.c_int),
         "p2_projector_sync": ([vp], ctypes.c_int),
+        "p2_set_exchange": ([vp, vp, vp], ctypes.c_int),
         "p2_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -394,6 +395,17 @@ class Parafac2:
         k1 = self.K if k1 is None else k1
         n = int(self._subj_ptr[k1] - self._subj_ptr[k0])
         return p2_get_U(self.ctx, k0, k1, n, self.R)
+
+    def set_exchange(self, fn):
+        """Make this context one shard of a subject-sharded collection (see
+        shard.py and p2_set_exchange): fn(ptr, count, stream) must replace the
+        device buffer of `count` doubles at ptr by its sum over all shards.
+        Call before load()."""
+        from .shard import _Hook
+        hook = _Hook(fn)
+        _check(lib.p2_set_exchange(self.ctx, ctypes.cast(hook.c_fn, ctypes.c_void_p), None),
+               "p2_set_exchange")
+        self._hook = hook                  # the C callback must outlive the context's use
 
     def stats(self) -> dict:
         return p2_stats(self.ctx)

@@ -150,8 +150,8 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
     if (c->opt.nonneg) {
         P2_TRY(dalloc(c, &c->d_passW, (size_t)K));
         P2_TRY(dalloc(c, &c->d_passV, (size_t)J));
-        P2_CUDA_TRY(cudaMemsetAsync(c->d_passW, 0, sizeof(uint32_t) * (size_t)K, c->stream));
-        P2_CUDA_TRY(cudaMemsetAsync(c->d_passV, 0, sizeof(uint32_t) * (size_t)J, c->stream));
+        P2_CUDA_TRY(cudaMemsetAsync(c->d_passW, 0, sizeof(uint64_t) * (size_t)K, c->stream));
+        P2_CUDA_TRY(cudaMemsetAsync(c->d_passV, 0, sizeof(uint64_t) * (size_t)J, c->stream));
     }
     P2_TRY(dalloc(c, &c->d_G, (size_t)K * P));
     P2_TRY(dalloc(c, &c->d_Gf, (size_t)K * P));
@@ -263,8 +263,6 @@ int p2_create(p2_ctx **out, const p2_options *opt) {
     if (!out || !opt) return fail(P2_EINVAL, "p2_create: NULL argument");
     *out = nullptr;
     if (opt->R < 1 || opt->R > P2_RMAX) return fail(P2_EINVAL, "p2_create: R must be in [1, 64]");
-    if (opt->nonneg && opt->R > 16)
-        return fail(P2_EINVAL, "p2_create: the non-negative variant supports R <= 16");
     if (opt->precision != P2_FP32 && opt->precision != P2_BF16)
         return fail(P2_EINVAL, "p2_create: precision must be P2_FP32 or P2_BF16");
     int ndev = 0;
@@ -313,6 +311,7 @@ int p2_create(p2_ctx **out, const p2_options *opt) {
     const size_t part_stride = stats_part_stride(c->R);
     if (rc == P2_OK) rc = dalloc(c, &c->d_part, (size_t)c->geo.red_blocks * part_stride);
     if (rc == P2_OK) rc = dalloc(c, &c->d_part2, (size_t)c->geo.red_blocks * part_stride);
+    if (rc == P2_OK) rc = dalloc(c, &c->d_red, part_stride);
     if (rc == P2_OK) rc = configure_kernels(c);
     if (rc == P2_OK) {
         if (cudaMemsetAsync(c->d_s, 0, sizeof(SmallState), c->stream) != cudaSuccess) rc = P2_ECUDA;
@@ -322,6 +321,15 @@ int p2_create(p2_ctx **out, const p2_options *opt) {
         return rc;
     }
     *out = c;
+    return P2_OK;
+}
+
+int p2_set_exchange(p2_ctx *c, p2_exchange_fn fn, void *user) {
+    if (!c) return fail(P2_EINVAL, "p2_set_exchange: NULL context");
+    if (c->loaded)
+        return fail(P2_ESTATE, "p2_set_exchange: call it before p2_load_slices");
+    c->xfn = fn;
+    c->xuser = fn ? user : nullptr;
     return P2_OK;
 }
 
@@ -335,6 +343,7 @@ int p2_destroy(p2_ctx *c) {
     const size_t part_stride = stats_part_stride(c->R);
     dfree(c, &c->d_part, (size_t)c->geo.red_blocks * part_stride);
     dfree(c, &c->d_part2, (size_t)c->geo.red_blocks * part_stride);
+    dfree(c, &c->d_red, part_stride);
     for (int i = 0; i < 8; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -468,6 +477,7 @@ struct EigScratch {
 
 int p2_init_eig(p2_ctx *c, int32_t max_iter, double tol, int32_t *n_done) {
     P2_TRY(check_ready(c, false));
+    if (c && c->xfn) return fail(P2_EINVAL, "p2_init_eig: not available on a sharded context");
     if (max_iter < 1) return fail(P2_EINVAL, "p2_init_eig: max_iter < 1");
     if (!(tol >= 0.0)) return fail(P2_EINVAL, "p2_init_eig: tol must be >= 0");
     const int R = c->R;
@@ -542,7 +552,8 @@ int p2_iterate(p2_ctx *c, int32_t n_iter, double *fit_out) {
     P2_TRY(check_ready(c, true));
     if (n_iter < 0) return fail(P2_EINVAL, "p2_iterate: n_iter < 0");
     P2_CUDA_TRY(cudaSetDevice(c->opt.device));
-    if (n_iter > 0 && c->opt.use_graph && !c->graph) {
+    const bool use_graph = c->opt.use_graph && !c->xfn;   // a sharded iteration calls the hook
+    if (n_iter > 0 && use_graph && !c->graph) {
         cudaGraph_t g = nullptr;
         P2_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         const int64_t before = c->enqueued;
@@ -567,7 +578,7 @@ int p2_iterate(p2_ctx *c, int32_t n_iter, double *fit_out) {
         }
     }
     for (int32_t i = 0; i < n_iter; ++i) {
-        if (c->opt.use_graph) {
+        if (use_graph) {
             P2_CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
             c->enqueued += c->graph_kernels;
         } else {

@@ -161,8 +161,8 @@ struct p2_ctx {
     // grid receives an even mix of large and small subjects
     int32_t *d_sorder = nullptr; // [K]
     // non-negative variant: each row's passive set (bit j: x_j > 0) of the last solve
-    uint32_t *d_passW = nullptr; // [K]
-    uint32_t *d_passV = nullptr; // [J]
+    uint64_t *d_passW = nullptr; // [K]
+    uint64_t *d_passV = nullptr; // [J]
     double *d_M2 = nullptr;     // J x R (relabelled rows)
     float *d_P = nullptr;       // N x R rows of P_k = Z_k F_k (mode-2 pass)
     double *d_segpart = nullptr; // nseg x R partial sums of the mode-2 reduction
@@ -171,6 +171,12 @@ struct p2_ctx {
     double *d_part = nullptr;   // reduction partials (red_blocks x stats_part_stride(R))
     double *d_part2 = nullptr;  // second partial buffer
     int *d_colcount = nullptr;  // [J] (load time)
+
+    // subject-sharded form: the caller's exchange hook (NULL: unsharded) and
+    // the one-row sum of the statistics partials that it exchanges
+    p2_exchange_fn xfn = nullptr;
+    void *xuser = nullptr;
+    double *d_red = nullptr;    // stats_part_stride(R) doubles
 
     bool inited = false;
     int iters_done = 0;
@@ -199,6 +205,8 @@ __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__
                                                        const float *__restrict__ M3, double *part,
                                                        int64_t K, int R, int with_m3);
 // per-iteration pieces (p2_kernels.cu)
+// exchange hook call of a sharded context (P2_OK if unsharded)
+int exchange(p2_ctx *c, double *buf, int64_t count);
 int enqueue_prologue(p2_ctx *c);     // Q-step + mode-1 MTTKRP for the current (H, V, W)
 int enqueue_iteration(p2_ctx *c);    // one ALS iteration
 int enqueue_factor_stats(p2_ctx *c); // HtH, VtV, WtW for freshly set factors
@@ -240,7 +248,7 @@ cudaError_t nnls_configure(int cap);
 cudaError_t launch_nnls_w(p2_ctx *c);
 cudaError_t launch_nnls_v(p2_ctx *c, double *part, int nparts);
 cudaError_t launch_nnls_rows(const p2_ctx *c, const double *Xa, const double *Xb,
-                             const float *rows, int64_t n, uint32_t *passive, float *out,
+                             const float *rows, int64_t n, uint64_t *passive, float *out,
                              cudaStream_t s);
 const double *state_vtv(const p2_ctx *c);
 const double *state_hth(const p2_ctx *c);

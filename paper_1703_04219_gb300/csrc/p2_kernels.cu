@@ -1330,6 +1330,30 @@ __global__ void __launch_bounds__(256) k_fin_v(const double *__restrict__ part, 
     if (with_g3) cta_pinv(A, U, st->G3inv, R, &st->flags);
 }
 
+// The exchange hook of a sharded context: sums buf over the shards in place
+// (see p2_set_exchange).
+int exchange(p2_ctx *c, double *buf, int64_t count) {
+    if (!c->xfn) return P2_OK;
+    const int r = c->xfn(buf, count, (void *)c->stream, c->xuser);
+    if (r != 0) {
+        set_error("the exchange hook returned %d (%lld values)", r, (long long)count);
+        return P2_EEXCHANGE;
+    }
+    return P2_OK;
+}
+
+// out[e] = sum of the nparts rows of part (row stride `stride`), in row
+// order: the one-row statistics a sharded context exchanges.
+__global__ void k_part_rows_sum(const double *__restrict__ part, int nparts, int64_t stride,
+                                double *out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < stride;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nparts; ++b) s += part[(size_t)b * stride + e];
+        out[e] = s;
+    }
+}
+
 // Sum the subject-statistics partials: W^TW, <W, M3>; loss / fit.
 // (M1 stays in the partials; the H solve sums it.)
 __global__ void k_fin_w(const double *__restrict__ part, int nparts, SmallState *st, int R,
@@ -1767,7 +1791,18 @@ static int enqueue_qstep(p2_ctx *c, int with_fit) {
     launch_stats_ranks(c, nb, nw * 32, ssm, with_fit, RankList{});
     P2_LAUNCH_CHECK("k_subject_stats");
     mark(c, 6);
-    k_fin_w<<<1, 256, 0, s>>>(c->d_part, nb, c->d_s, R, with_fit);
+    if (c->xfn) {
+        // sharded: this shard's statistics as one row, summed over the shards
+        const int64_t stride = (int64_t)stats_part_stride(R);
+        k_part_rows_sum<<<(int)((stride + 255) / 256), 256, 0, s>>>(c->d_part, nb, stride,
+                                                                  c->d_red);
+        P2_LAUNCH_CHECK("k_part_rows_sum");
+        const int xrc = exchange(c, c->d_red, stride);
+        if (xrc != P2_OK) return xrc;
+        k_fin_w<<<1, 256, 0, s>>>(c->d_red, 1, c->d_s, R, with_fit);
+    } else {
+        k_fin_w<<<1, 256, 0, s>>>(c->d_part, nb, c->d_s, R, with_fit);
+    }
     P2_LAUNCH_CHECK("k_fin_w");
     return P2_OK;
 }
@@ -1805,7 +1840,8 @@ int enqueue_iteration(p2_ctx *c) {
     const size_t sm_pinv = (size_t)4 * R * R * 8;
     // H step (Algorithm 1 line 3 with U = H; mode-1 MTTKRP from the previous pass)
     mark(c, 0);
-    k_solve_h<<<1, 256, sm_pinv, s>>>(c->d_part, nb, c->d_s, c->d_H, R);
+    k_solve_h<<<1, 256, sm_pinv, s>>>(c->xfn ? c->d_red : c->d_part, c->xfn ? 1 : nb, c->d_s,
+                                      c->d_H, R);
     P2_LAUNCH_CHECK("k_solve_h");
     // pass beta: mode-2 MTTKRP
     mark(c, 1);
@@ -1820,6 +1856,10 @@ int enqueue_iteration(p2_ctx *c) {
     const int cb_blocks = (int)((J + 7) / 8 < 8 * nsm ? (J + 7) / 8 : 8 * nsm);
     k_m2_columns<<<cb_blocks, 256, 0, s>>>(c->d_segpart, c->X.col_seg, c->d_M2, (int32_t)J, R);
     P2_LAUNCH_CHECK("k_m2_columns");
+    {                                           // sharded: M2 summed over the shards
+        const int xrc = exchange(c, c->d_M2, nJR);
+        if (xrc != P2_OK) return xrc;
+    }
     // V step (Algorithm 1 line 5)
     mark(c, 2);
     if (c->opt.nonneg) {

@@ -283,6 +283,34 @@ int launch_load(p2_ctx *c, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
     double nx2 = 0.0;
     for (int b = 0; b < nb; ++b) nx2 += hp[b];
     delete[] hp;
+    // The relabel's key: the column counts, summed over all shards for a
+    // sharded context (every shard then relabels alike), together with ||X||^2.
+    std::vector<double> key((size_t)J + 1);
+    for (int j = 0; j < J; ++j) key[j] = (double)cc[j];
+    key[J] = nx2;
+    if (c->xfn) {
+        double *dk = nullptr;
+        cudaError_t e = cudaMallocAsync(&dk, sizeof(double) * ((size_t)J + 1), s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dk, key.data(), sizeof(double) * ((size_t)J + 1),
+                                cudaMemcpyHostToDevice, s);
+        int rc = e == cudaSuccess ? exchange(c, dk, (int64_t)J + 1) : P2_OK;
+        if (e == cudaSuccess && rc == P2_OK)
+            e = cudaMemcpyAsync(key.data(), dk, sizeof(double) * ((size_t)J + 1),
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && rc == P2_OK) e = cudaStreamSynchronize(s);
+        if (dk) cudaFreeAsync(dk, s);
+        if (rc != P2_OK) {
+            delete[] cc;
+            return rc;
+        }
+        if (e != cudaSuccess) {
+            delete[] cc;
+            set_error("load: exchange of the column counts failed: %s", cudaGetErrorString(e));
+            return P2_ECUDA;
+        }
+        nx2 = key[J];
+    }
     // relabel: decreasing frequency, ties by original id
     {
         int32_t *order = c->h_perm_new2old;
@@ -294,7 +322,7 @@ int launch_load(p2_ctx *c, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
                 int mid = lo + w < J ? lo + w : J, hi = lo + 2 * w < J ? lo + 2 * w : J;
                 int a = lo, b = mid, o = lo;
                 while (a < mid && b < hi) {
-                    if (cc[order[b]] > cc[order[a]]) tmp[o++] = order[b++];
+                    if (key[order[b]] > key[order[a]]) tmp[o++] = order[b++];
                     else tmp[o++] = order[a++];
                 }
                 while (a < mid) tmp[o++] = order[a++];

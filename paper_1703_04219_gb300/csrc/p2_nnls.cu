@@ -6,7 +6,8 @@
 // the rows of V, b = M2(j,:); A = V^TV * H^TH for the rows of W, b =
 // M3(k,:)); H stays unconstrained.
 //
-// One lane per row, double-word arithmetic (p2_dw.cuh), the active-set method
+// One lane per row for R <= 16 (one warp per row above, k_nnls_warp),
+// double-word arithmetic (p2_dw.cuh), the active-set method
 // of Lawson and Hanson ("Solving Least Squares Problems", 1974, Chapter 23)
 // with each subproblem A_PP z_P = b_P solved by a Cholesky factorisation of
 // the passive block.  The method starts from the row's passive set of the
@@ -19,6 +20,9 @@
 #include <stdint.h>
 
 #include "p2_internal.cuh"
+#include "p2_num.cuh"
+
+#define FULLMASK_NNLS 0xffffffffu
 
 namespace p2 {
 
@@ -50,7 +54,7 @@ template <int R, class B, class O>
 __global__ void __launch_bounds__(128, 1) k_nnls_rows(const double *__restrict__ Xa,
                                                    const double *__restrict__ Xb,
                                                    const B *__restrict__ rows, int64_t n,
-                                                   uint32_t *passive, O *out) {
+                                                   uint64_t *passive, O *out) {
     constexpr int LP = R * (R + 1) / 2;
     constexpr int DWS = nnls_lane_dws<R>();
     extern __shared__ __align__(16) dw sn[];
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(128, 1) k_nnls_rows(const double *__restrict__
         }
         // dual feasibility: w_j > tol, tol a few double-word roundings of the data
         const float tol = 64.f * (float)R * 1.4210855e-14f * scale;   // 2^-46
-        uint32_t P = passive[r] & ((1u << R) - 1u);
+        uint32_t P = (uint32_t)(passive[r] & ((1ull << R) - 1ull));
         // warm start: shrink the previous passive set until its solution is positive
         for (int it = 0; it <= R && P; ++it) {
             const uint32_t bad = solve(P);
@@ -182,6 +186,213 @@ __global__ void __launch_bounds__(128, 1) k_nnls_rows(const double *__restrict__
     }
 }
 
+// ---------------------------------------------------------------------------
+// 16 < R <= 64: one warp per row.  The same Lawson-Hanson iteration, warm
+// start, tolerances and double-word arithmetic as k_nnls_rows, with the
+// per-row storage (Cholesky factor of the passive block, packed lower, and
+// the vectors) in shared memory once per warp instead of once per lane, and
+// the vector work split over the lanes: the left-looking Cholesky factors
+// column by column (the rows below the diagonal over the lanes, each lane
+// forming its dot products), the triangular solves go column by column (one
+// division, then an update of the remaining entries over the lanes), and the
+// dual check, the step length and the passive-set updates take one entry per
+// lane with warp reductions.  Every lane of a warp ends each step with the
+// same passive set, so the warp stays converged.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline size_t nnls_warp_dws(int R) {
+    return (size_t)R * (R + 1) / 2 + 5 * (size_t)R + ((size_t)R + 7) / 8;   // + R index bytes
+}
+inline size_t nnls_warp_smem(int R, int warps) {
+    return (size_t)R * R * sizeof(dw) + (size_t)warps * nnls_warp_dws(R) * sizeof(dw);
+}
+
+static __device__ __forceinline__ dw warp_sum_dw(dw v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = dw_add(v, dw{__shfl_xor_sync(FULLMASK_NNLS, v.h, o), __shfl_xor_sync(FULLMASK_NNLS, v.l, o)});
+    return v;
+}
+static __device__ __forceinline__ uint64_t warp_or64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(FULLMASK_NNLS, v, o);
+    return v;
+}
+
+template <class B, class O>
+__global__ void __launch_bounds__(256) k_nnls_warp(const double *__restrict__ Xa,
+                                                   const double *__restrict__ Xb,
+                                                   const B *__restrict__ rows, int64_t n, int R,
+                                                   uint64_t *passive, O *out) {
+    const int LP = R * (R + 1) / 2;
+    extern __shared__ __align__(16) dw snw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    dw *As = snw;                                  // R x R, A = Xa * Xb
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) As[e] = to_dw(Xa[e] * Xb[e]);
+    __syncthreads();
+    float scale_a = 0.f;
+    for (int e = lane; e < R * R; e += 32) scale_a = fmaxf(scale_a, fabsf(As[e].h));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) scale_a = fmaxf(scale_a, __shfl_xor_sync(FULLMASK_NNLS, scale_a, o));
+    dw *ws = snw + (size_t)R * R + (size_t)warp * nnls_warp_dws(R);
+    dw *Lp = ws;                                   // packed lower factor
+    dw *RDv = Lp + LP;                             // reciprocal diagonal
+    dw *Yv = RDv + R;
+    dw *Xv = Yv + R;
+    dw *Zv = Xv + R;
+    dw *Bvv = Zv + R;
+    unsigned char *IX = reinterpret_cast<unsigned char *>(Bvv + R);
+    auto L = [Lp](int a, int c) -> dw & { return Lp[a * (a + 1) / 2 + c]; };
+    const dw zero = dw_f(0.f), one = dw_f(1.f);
+    const uint64_t rmask = R >= 64 ? ~0ull : ((1ull << R) - 1ull);
+
+    // z_P = A_PP^{-1} b_P, z = 0 off P; returns the passive variables whose
+    // solution is not positive (the same on every lane)
+    auto solve = [&](uint64_t Pm) -> uint64_t {
+        int p = 0;                                 // IX: the passive indices in order
+        for (int j0 = 0; j0 < R; j0 += 32) {
+            const int j = j0 + lane;
+            const bool in = j < R && ((Pm >> j) & 1ull);
+            const unsigned bal = __ballot_sync(FULLMASK_NNLS, in);
+            if (in) IX[p + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)j;
+            p += __popc(bal);
+        }
+        __syncwarp();
+        for (int c = 0; c < p; ++c) {              // left-looking Cholesky, column c
+            const int ic = IX[c];
+            acc_t<dw> sd = acc0<dw>();
+            for (int q = lane; q < c; q += 32) acc_sqr(sd, L(c, q));
+            const dw sq = warp_sum_dw(acc_val(sd));
+            const dw sv = dw_sub(As[ic * R + ic], sq);
+            const bool ok = sv.h > 0.f;            // A_PP positive definite
+            const dw rt = ok ? dw_rsqrt(sv) : zero;
+            if (lane == 0) {
+                RDv[c] = rt;
+                L(c, c) = ok ? dw_mul(sv, rt) : zero;
+            }
+            for (int a = c + 1 + lane; a < p; a += 32) {
+                acc_t<dw> s = acc_from(As[IX[a] * R + ic]);
+                for (int q = 0; q < c; ++q) acc_fma(s, dw_neg(L(a, q)), L(c, q));
+                L(a, c) = dw_mul(acc_val(s), rt);
+            }
+            __syncwarp();
+        }
+        for (int a = lane; a < p; a += 32) Yv[a] = Bvv[IX[a]];
+        __syncwarp();
+        for (int a = 0; a < p; ++a) {              // L y = b_P, column by column
+            const dw ya = dw_mul(Yv[a], RDv[a]);
+            __syncwarp();
+            if (lane == 0) Yv[a] = ya;
+            for (int i = a + 1 + lane; i < p; i += 32) Yv[i] = dw_fma(dw_neg(L(i, a)), ya, Yv[i]);
+            __syncwarp();
+        }
+        for (int a = p - 1; a >= 0; --a) {         // L^T z = y, in place
+            const dw za = dw_mul(Yv[a], RDv[a]);
+            __syncwarp();
+            if (lane == 0) Yv[a] = za;
+            for (int q = lane; q < a; q += 32) Yv[q] = dw_fma(dw_neg(L(a, q)), za, Yv[q]);
+            __syncwarp();
+        }
+        for (int j = lane; j < R; j += 32) Zv[j] = zero;
+        __syncwarp();
+        uint64_t bad = 0;
+        for (int a = lane; a < p; a += 32) {
+            const int j = IX[a];
+            Zv[j] = Yv[a];
+            if (!(Yv[a].h > 0.f)) bad |= 1ull << j;
+        }
+        __syncwarp();
+        return warp_or64(bad);
+    };
+
+    const int64_t nwarps = (int64_t)gridDim.x * nw;
+    for (int64_t r = (int64_t)blockIdx.x * nw + warp; r < n; r += nwarps) {
+        float scale = scale_a;
+        for (int j = lane; j < R; j += 32) {
+            const dw bj = to_dw(rows[(size_t)r * R + j]);
+            Bvv[j] = bj;
+            Xv[j] = zero;
+            scale = fmaxf(scale, fabsf(bj.h));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) scale = fmaxf(scale, __shfl_xor_sync(FULLMASK_NNLS, scale, o));
+        __syncwarp();
+        const float tol = 64.f * (float)R * 1.4210855e-14f * scale;   // 2^-46, as k_nnls_rows
+        uint64_t P = passive[r] & rmask;
+        for (int it = 0; it <= R && P; ++it) {     // warm start
+            const uint64_t bad = solve(P);
+            if (!bad) {
+                for (int j = lane; j < R; j += 32) Xv[j] = Zv[j];
+                __syncwarp();
+                break;
+            }
+            P &= ~bad;
+        }
+        for (int outer = 0; outer < 3 * R; ++outer) {
+            // most violated dual constraint (lowest index on ties)
+            int jb = -1;
+            float wb = tol;
+            for (int j = lane; j < R; j += 32) {
+                if ((P >> j) & 1ull) continue;
+                acc_t<dw> s = acc_from(Bvv[j]);
+                for (int q = 0; q < R; ++q) acc_fma(s, dw_neg(As[j * R + q]), Xv[q]);
+                const float w = acc_val(s).h;
+                if (w > wb) {
+                    wb = w;
+                    jb = j;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float w2 = __shfl_xor_sync(FULLMASK_NNLS, wb, o);
+                const int j2 = __shfl_xor_sync(FULLMASK_NNLS, jb, o);
+                if (j2 >= 0 && (jb < 0 || w2 > wb || (w2 == wb && j2 < jb))) {
+                    wb = w2;
+                    jb = j2;
+                }
+            }
+            if (jb < 0) break;
+            P |= 1ull << jb;
+            for (int inner = 0; inner <= R; ++inner) {
+                const uint64_t bad = solve(P);
+                if (!bad) {
+                    for (int j = lane; j < R; j += 32) Xv[j] = Zv[j];
+                    __syncwarp();
+                    break;
+                }
+                dw alpha = one;                    // min x_j / (x_j - z_j) over bad
+                for (int j = lane; j < R; j += 32) {
+                    if (!((bad >> j) & 1ull)) continue;
+                    const dw den = dw_sub(Xv[j], Zv[j]);
+                    const dw a = den.h > 0.f ? dw_div(Xv[j], den) : zero;
+                    if (a.h < alpha.h || (a.h == alpha.h && a.l < alpha.l)) alpha = a;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const dw a2{__shfl_xor_sync(FULLMASK_NNLS, alpha.h, o),
+                                __shfl_xor_sync(FULLMASK_NNLS, alpha.l, o)};
+                    if (a2.h < alpha.h || (a2.h == alpha.h && a2.l < alpha.l)) alpha = a2;
+                }
+                uint64_t drop = 0;
+                for (int j = lane; j < R; j += 32) {
+                    if (!((P >> j) & 1ull)) continue;
+                    const dw xj = dw_fma(alpha, dw_sub(Zv[j], Xv[j]), Xv[j]);
+                    if (xj.h > 0.f) {
+                        Xv[j] = xj;
+                    } else {
+                        Xv[j] = zero;
+                        drop |= 1ull << j;
+                    }
+                }
+                __syncwarp();
+                P &= ~warp_or64(drop);
+            }
+        }
+        for (int j = lane; j < R; j += 32) store_out(out + (size_t)r * R + j, Xv[j]);
+        if (lane == 0) passive[r] = P;
+        __syncwarp();
+    }
+}
+
 // Column sums of squares of V's unnormalised rows into fixed per-block
 // partials (the layout k_solve_v_norm reads).
 __global__ void __launch_bounds__(256) k_colsumsq(const double *__restrict__ Vun, int64_t J,
@@ -209,7 +420,7 @@ __global__ void __launch_bounds__(256) k_colsumsq(const double *__restrict__ Vun
 
 template <int R, class B, class O>
 static cudaError_t launch_nnls_t(const p2_ctx *c, const double *Xa, const double *Xb,
-                                 const B *rows, int64_t n, uint32_t *passive, O *out,
+                                 const B *rows, int64_t n, uint64_t *passive, O *out,
                                  cudaStream_t s) {
     const int nt = 128;
     const size_t smem = nnls_smem<R>(nt);
@@ -222,7 +433,7 @@ static cudaError_t launch_nnls_t(const p2_ctx *c, const double *Xa, const double
 
 template <class B, class O>
 static cudaError_t launch_nnls(const p2_ctx *c, const double *Xa, const double *Xb,
-                               const B *rows, int64_t n, uint32_t *passive, O *out,
+                               const B *rows, int64_t n, uint64_t *passive, O *out,
                                cudaStream_t s) {
     switch (c->R) {
 #define P2_NNLS_CASE(r) \
@@ -232,8 +443,16 @@ static cudaError_t launch_nnls(const p2_ctx *c, const double *Xa, const double *
         P2_NNLS_CASE(11) P2_NNLS_CASE(12) P2_NNLS_CASE(13) P2_NNLS_CASE(14) P2_NNLS_CASE(15)
         P2_NNLS_CASE(16)
 #undef P2_NNLS_CASE
-        default: return cudaErrorInvalidValue;
+        default: break;
     }
+    if (c->R > P2_RMAX) return cudaErrorInvalidValue;
+    const int warps = 8;
+    const size_t smem = nnls_warp_smem(c->R, warps);
+    const int64_t want = (n + warps - 1) / warps;
+    const int64_t cap = (int64_t)c->geo.nsm * 4;
+    const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+    k_nnls_warp<B, O><<<grid, warps * 32, smem, s>>>(Xa, Xb, rows, n, c->R, passive, out);
+    return cudaGetLastError();
 }
 
 // device address of an R x R member of the small state
@@ -259,12 +478,17 @@ static cudaError_t allow_nnls(int cap) {
 cudaError_t nnls_configure(int cap) {
     cudaError_t e = allow_nnls<float, float>(cap);
     if (e == cudaSuccess) e = allow_nnls<double, double>(cap);
+    const int need = (int)nnls_warp_smem(P2_RMAX, 8);
+    if (e == cudaSuccess && need <= cap)
+        e = cudaFuncSetAttribute(k_nnls_warp<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+    if (e == cudaSuccess && need <= cap)
+        e = cudaFuncSetAttribute(k_nnls_warp<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
     return e;
 }
 
 // Rows of any FP32 right-hand sides against A = Xa * Xb (device R x R FP64).
 cudaError_t launch_nnls_rows(const p2_ctx *c, const double *Xa, const double *Xb,
-                             const float *rows, int64_t n, uint32_t *passive, float *out,
+                             const float *rows, int64_t n, uint64_t *passive, float *out,
                              cudaStream_t s) {
     return launch_nnls<float, float>(c, Xa, Xb, rows, n, passive, out, s);
 }

@@ -31,7 +31,7 @@ struct p2_projector {
     p2::dw *d_G = nullptr;
     float *d_S = nullptr, *d_T = nullptr;
     float *d_M3 = nullptr;              // non-negative models: the subjects' mode-3 rows
-    uint32_t *d_pass = nullptr;         // non-negative models: NNLS passive sets
+    uint64_t *d_pass = nullptr;         // non-negative models: NNLS passive sets
     p2::SmallState *d_st = nullptr;     // private copy of H64, G3inv; flags
     int pending_flags_check = 0;
 };
@@ -341,7 +341,7 @@ int p2_project(p2_projector *pj, int64_t n_req, const int64_t *subj_ptr, const i
     XView xv{pj->X.subj_row, pj->X.subj_nnz, pj->X.row_len, pj->X.col, pj->X.val, n_req};
     P2_CUDA_TRY(launch_gram(m, xv, pj->d_st, pj->d_G, s));
     if (m->opt.nonneg)
-        P2_CUDA_TRY(cudaMemsetAsync(pj->d_pass, 0, sizeof(uint32_t) * (size_t)n_req, s));
+        P2_CUDA_TRY(cudaMemsetAsync(pj->d_pass, 0, sizeof(uint64_t) * (size_t)n_req, s));
     int uw = 8;
     while (uw > 1 && (size_t)R * R * 12 + uw * (size_t)(3 * R * R + R) * 4 > (size_t)m->geo.smem_optin) --uw;
     const size_t upd_smem = (size_t)R * R * 12 + uw * (size_t)(3 * R * R + R) * 4;

@@ -144,6 +144,13 @@ template <class T> inline T __shfl_down_sync(unsigned m, T v, int d) {
     const int l = emu_lane();
     return emu_from<T>(emu_warp_xchg(m, emu_bits(v), l + d < 32 ? l + d : l));
 }
+// bit l set when lane l's predicate is true (every lane of mask m takes part)
+inline unsigned __ballot_sync(unsigned m, int pred) {
+    unsigned r = 0;
+    for (int l = 0; l < 32; ++l)
+        if (emu_warp_xchg(m, (uint64_t)(pred != 0), l)) r |= 1u << l;
+    return r & m;
+}
 unsigned emu_match_any(unsigned m, uint64_t key);
 template <class T> inline unsigned __match_any_sync(unsigned m, T key) { return emu_match_any(m, emu_bits(key)); }
 inline int __popc(unsigned x) { return __builtin_popcount(x); }

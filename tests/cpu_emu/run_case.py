@@ -173,6 +173,45 @@ def rational_case(R, K):
             "einval": einval, "still_iterates": still}
 
 
+def shard_case(R, K):
+    """A context whose exchange hook doubles every buffer (the sum over two
+    shards that hold the same subjects) against an unsharded context on the
+    collection stacked twice: same H, V and fit, and W rows equal to the
+    first copy's.  Exercises the sharded load (column counts, ||X||^2), the
+    statistics row and the M2 exchange under AddressSanitizer (device
+    buffers are host memory on the emulator)."""
+    import ctypes
+    X = synth.generate("tiny", K=K)
+    X2 = X.take(list(range(K)) + list(range(K)))
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=13)
+    calls = []
+
+    def double(ptr, count, stream):
+        buf = (ctypes.c_double * count).from_address(ptr)
+        a = np.frombuffer(buf, dtype=np.float64)
+        a *= 2.0
+        calls.append(count)
+
+    with p2.Parafac2(R, use_graph=False) as m:
+        m.set_exchange(double)
+        m.load(X)
+        m.init(H0, V0, W0)
+        fit = m.iterate(2)
+        H, V, W = m.factors()
+        M2 = m.mttkrp(2)
+    with p2.Parafac2(R, use_graph=False) as m:
+        m.load(X2)
+        m.init(H0, V0, np.vstack([W0, W0]))
+        fit2 = m.iterate(2)
+        H2, V2, W2 = m.factors()
+        M22 = m.mttkrp(2)
+    P_ = R * R * 2 + 1
+    want = [X.J + 1] + [P_, X.J * R, P_, X.J * R, P_]   # load, prologue, 2 x (M2, stats)
+    return {"H": rel_fro(H, H2), "V": rel_fro(V, V2), "W": rel_fro(W, W2[:K]),
+            "M2": rel_fro(M2, M22), "fit": abs(fit - fit2),
+            "calls_ok": float(calls == want)}
+
+
 if __name__ == "__main__":
     kind = sys.argv[1]
     if kind == "iterate":
@@ -182,6 +221,8 @@ if __name__ == "__main__":
         out = seed_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "rational":
         out = rational_case(int(sys.argv[2]), int(sys.argv[3]))
+    elif kind == "shard":
+        out = shard_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "getu":
         out = getu_case(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]))
     else:

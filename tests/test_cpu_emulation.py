@@ -28,6 +28,7 @@ CASES = {
     "iterate_r20": ["iterate", "c250m", "12", "20"],     # outside the rank-compiled list
     "iterate_r5_bf16": ["iterate", "tiny", "24", "5", "bf16"],
     "iterate_r5_nonneg": ["iterate", "tiny", "24", "5", "nonneg"],
+    "iterate_r24_nonneg": ["iterate", "c250m", "40", "24", "nonneg"],
     "iterate_r10_fp64": ["iterate", "tiny", "24", "10", "fp64"],
     "iterate_r40_fp64": ["iterate", "tiny", "16", "40", "fp64"],
     "project_r12": ["project", "12", "3"],
@@ -35,6 +36,7 @@ CASES = {
     "getu_r5": ["getu", "5", "3", "17"],
     "seed_r4": ["seed", "4", "987654321"],
     "rational_r3": ["rational", "3", "12"],
+    "shard_r6": ["shard", "6", "20"],
 }
 
 
@@ -113,9 +115,11 @@ def test_emulated_seeded_init_and_stopping_rule(emulated_runs):
     assert out["n_loose"] == 2
 
 
-def test_emulated_nonneg_iteration_is_in_bounds_and_matches_oracle(emulated_runs):
-    """Section 5.1's non-negative variant: row-wise NNLS for V and W."""
-    err = _result(emulated_runs, "iterate_r5_nonneg")
+@pytest.mark.parametrize("name", ["iterate_r5_nonneg", "iterate_r24_nonneg"])
+def test_emulated_nonneg_iteration_is_in_bounds_and_matches_oracle(emulated_runs, name):
+    """Section 5.1's non-negative variant: row-wise NNLS for V and W (one
+    lane per row at R = 5, one warp per row at R = 24)."""
+    err = _result(emulated_runs, name)
     assert err["neg"] == 0.0
     for key in ("M1", "M2", "M3", "H", "V", "W"):
         assert err[key] < 1e-5, (key, err[key])
@@ -138,3 +142,14 @@ def test_emulated_rational_start_is_in_bounds_and_matches_oracle(emulated_runs):
     assert out["def_orth"] < 1e-6 and out["def_lead"] < 1e-6, out
     assert out["def_fit_finite"] == 1.0
     assert out["einval"] == 1.0 and out["still_iterates"] == 1.0
+
+
+def test_emulated_sharded_context_is_in_bounds_and_matches(emulated_runs):
+    """The subject-sharded code path (p2_set_exchange): a hook that doubles
+    every exchanged buffer stands for two shards holding the same subjects,
+    against one context on the collection stacked twice."""
+    out = _result(emulated_runs, "shard_r6")
+    assert out["calls_ok"] == 1.0, out
+    for key in ("H", "V", "W", "M2"):
+        assert out[key] < 1e-5, (key, out[key])
+    assert out["fit"] < 1e-6

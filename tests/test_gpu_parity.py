@@ -218,10 +218,14 @@ def test_seeded_init_and_stopping_rule(p2):
 
 
 @pytest.mark.parametrize("name,K,R", [("tiny", 200, 5), ("c63m", 3000, 10), ("c63m", 1500, 16),
-                                      ("ptiny", 50, 5), ("p63m", 2000, 10)])
+                                      ("ptiny", 50, 5), ("p63m", 2000, 10),
+                                      # one warp per row above R = 16
+                                      ("c250m", 400, 24), ("c250m", 400, 40), ("ptiny", 50, 40),
+                                      ("tiny", 120, 64)])
 def test_nonneg_one_step_parity(p2, name, K, R):
     """Section 5.1's variant (non-negative S_k and V): one iteration from the
-    same FP32-exact start against the oracle's Lawson-Hanson solves."""
+    same FP32-exact start against the oracle's Lawson-Hanson solves, with the
+    lane-per-row NNLS kernel (R <= 16) and the warp-per-row one (R > 16)."""
     X = synth.generate(name, K=K)
     H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=3)
     with p2.Parafac2(R, nonneg=True) as m:
@@ -254,7 +258,23 @@ def test_nonneg_ten_iterations_and_limits(p2):
     assert abs(fit - ref["history"][-1]["fit"]) < FIT_TOL
     assert np.all(V >= 0) and np.all(W >= 0)
     with pytest.raises(p2.P2Error):
-        p2.Parafac2(17, nonneg=True)
+        p2.Parafac2(65, nonneg=True)
+
+
+def test_nonneg_ten_iterations_r40(p2):
+    """Ten non-negative iterations at R = 40 (warp-per-row NNLS, warm-started
+    passive sets carried across iterations) against the oracle's fits."""
+    X = synth.generate("c250m", K=300)
+    R = 40
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=6)
+    with p2.Parafac2(R, nonneg=True) as m:
+        m.load(X)
+        m.init(H0, V0, W0)
+        fits = [m.iterate(1) for _ in range(10)]
+        _, V, W = m.factors()
+    ref = P.parafac2_als(X, H0, V0, W0, n_iter=10, nonneg=True)
+    assert max(abs(a - h["fit"]) for a, h in zip(fits, ref["history"])) < FIT_TOL
+    assert np.all(V >= 0) and np.all(W >= 0)
 
 
 @pytest.mark.parametrize("name,K,R,precision", [("tiny", 200, 5, "fp32"), ("c63m", 2000, 10, "fp32"),

@@ -113,3 +113,88 @@ def test_clock_record_counts_only_samples_in_the_timed_region(tmp_path, lines, s
     got = c.stop()
     for k, v in want.items():
         assert got[k] == v, (k, got)
+
+
+def test_plan_shards_balances_nonzeros_and_covers_every_subject():
+    from paper_1703_04219_gb300 import shard
+    X = synth.generate("c63m", K=5000)
+    for n in (1, 2, 3, 7):
+        cuts = shard.plan_shards(X.subj_ptr, X.row_ptr, n)
+        assert cuts[0] == 0 and cuts[-1] == X.K and len(cuts) == n + 1
+        assert all(a <= b for a, b in zip(cuts, cuts[1:]))
+        nnz = [int(X.row_ptr[X.subj_ptr[b]] - X.row_ptr[X.subj_ptr[a]])
+               for a, b in zip(cuts, cuts[1:])]
+        assert sum(nnz) == X.nnz
+        biggest = int(np.diff(X.row_ptr[X.subj_ptr]).max())     # one subject's non-zeros
+        assert max(nnz) - min(nnz) <= 2 * biggest, (n, nnz)
+    parts = shard.shards(X, 3)
+    assert sum(p.K for p in parts) == X.K
+    for p in parts:                                           # the ranges reassemble X
+        k = p.k0
+        assert np.array_equal(p.col, X.col[X.row_ptr[X.subj_ptr[k]]:
+                                           X.row_ptr[X.subj_ptr[k + p.K]]])
+        assert p.subj_ptr[0] == 0 and p.row_ptr[0] == 0 and p.row_ptr[-1] == len(p.col)
+    tiny = shard.plan_shards(np.array([0, 2, 3]), np.arange(4), 4)   # more shards than subjects
+    assert tiny[0] == 0 and tiny[-1] == 2 and len(tiny) == 5
+
+
+def _shard_rank(rank, world, port, q):
+    """One shard of the subject-sharded iteration, with the oracle's
+    per-subject functions standing in for the library's kernels: the shard's
+    partial M1, W^TW and M2 are summed with host_allreduce_ (gloo) exactly
+    where a sharded context calls its exchange hook."""
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import parafac2 as P
+    from paper_1703_04219_gb300 import shard
+    X = synth.generate("tiny", K=120)
+    R = 4
+    H0, V0, W0 = (a.astype(np.float64) for a in synth.init_factors(R, X.J, X.K, seed=8))
+    cuts = shard.plan_shards(X.subj_ptr, X.row_ptr, world)
+    rng_ = shard.subject_range(X, cuts[rank], cuts[rank + 1])
+    part = synth.Slices(rng_.K, rng_.J, rng_.subj_ptr, rng_.row_ptr, rng_.col, rng_.val)
+    W = W0[cuts[rank]:cuts[rank + 1]]
+    blocks = P.all_blocks(part)
+    cols = [c for _, c in blocks]
+    Ys = [P.form_y(P.procrustes_q(Xc, c, H0, V0, W[k]), Xc) for k, (Xc, c) in enumerate(blocks)]
+    stats = np.concatenate([P.mttkrp_spartan(Ys, cols, H0, V0, W, 1).ravel(), (W.T @ W).ravel()])
+    shard.host_allreduce_(stats)
+    M1, WtW = stats[:R * R].reshape(R, R), stats[R * R:].reshape(R, R)
+    H, _ = P.normalize_columns(M1 @ P.pinv_sym(WtW * (V0.T @ V0)))
+    M2 = np.ascontiguousarray(P.mttkrp_spartan(Ys, cols, H, V0, W, 2))
+    shard.host_allreduce_(M2)
+    q.put((rank, M1, WtW, M2))
+    dist.destroy_process_group()
+
+
+def test_sharded_exchange_over_two_gloo_ranks():
+    """Two ranks (gloo, CPU) each hold one nnz-balanced subject range; after
+    the exchanges both hold the unsharded iteration's M1, W^TW and M2."""
+    import multiprocessing as mp
+    from oracle import parafac2 as P
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 30500 + (os.getpid() % 1000)
+    ps = [ctx.Process(target=_shard_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    got = []
+    import queue
+    while len(got) < 2:
+        try:
+            got.append(q.get(timeout=5))
+        except queue.Empty:
+            assert all(p.is_alive() or p.exitcode == 0 for p in ps), [p.exitcode for p in ps]
+    res = sorted(got, key=lambda t: t[0])
+    for p in ps:
+        p.join(timeout=60)
+    assert all(p.exitcode == 0 for p in ps)
+    X = synth.generate("tiny", K=120)
+    H0, V0, W0 = (a.astype(np.float64) for a in synth.init_factors(4, X.J, X.K, seed=8))
+    ref = P.als_iteration(P.all_blocks(X), H0, V0, W0)
+    for _, M1, WtW, M2 in res:
+        assert np.allclose(M1, ref["M1"], rtol=1e-12, atol=1e-12 * np.abs(ref["M1"]).max())
+        assert np.allclose(WtW, W0.T @ W0, rtol=1e-12)
+        assert np.allclose(M2, ref["M2"], rtol=1e-12, atol=1e-12 * np.abs(ref["M2"]).max())
+    assert np.array_equal(res[0][3], res[1][3])           # every rank holds the same sum

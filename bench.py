@@ -579,8 +579,11 @@ def run_serving(rate=50000.0, horizon_s=2.0, n_iter=5, n_slots=4, seed=5, precis
     req = synth.generate(replace(ws, K=n_req, seed=ws.seed))
     reqs = requests_from_slices(req, rate_per_s=rate, seed=seed)
     max_subjects = 4096
-    srv = Server(model, n_slots=n_slots, max_subjects=max_subjects, max_rows=max_subjects * 64,
-                 max_nnz=max_subjects * 256, n_iter=n_iter)
+    # admission by device memory: 2% of the free device memory for the slots'
+    # scratch, capacities from the requests' mean shape (rows, non-zeros per row)
+    srv = Server(model, n_slots=n_slots, max_subjects=max_subjects, n_iter=n_iter,
+                 memory_fraction=0.02,
+                 shape=(float(req.n_rows / req.K), float(req.nnz / max(req.n_rows, 1))))
     warm = requests_from_slices(req.take(list(range(min(512, n_req)))), rate_per_s=1e9, seed=seed)
     srv.run(warm)                      # first launches, allocator
     _, st = srv.run(reqs)
@@ -588,9 +591,7 @@ def run_serving(rate=50000.0, horizon_s=2.0, n_iter=5, n_slots=4, seed=5, precis
     model.close()
     st.update({"precision": precision, "rate_per_s": rate, "horizon_s": horizon_s,
                "n_iter": n_iter, "slots": n_slots,
-               "R": R, "mean_rows": float(req.n_rows / req.K), "mean_nnz": float(req.nnz / req.K),
-               "admission_per_slot": {"subjects": max_subjects, "rows": max_subjects * 64,
-                                      "nnz": max_subjects * 256}})
+               "R": R, "mean_rows": float(req.n_rows / req.K), "mean_nnz": float(req.nnz / req.K)})
     return st
 
 

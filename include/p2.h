@@ -251,6 +251,13 @@ int p2_projector_create(p2_ctx *model, int64_t max_subjects, int64_t max_rows, i
                         void *stream, p2_projector **out);
 int p2_projector_destroy(p2_projector *pj);
 
+/* Device bytes a projector of these capacities allocates on the model's
+ * device (its scratch: the batch's CSR arrays in both formats and the
+ * per-subject Gram, S, T and state), into *bytes.  A server that admits
+ * requests by memory sizes its projectors with it. */
+int p2_projector_bytes(p2_ctx *model, int64_t max_subjects, int64_t max_rows, int64_t max_nnz,
+                       int64_t *bytes);
+
 /*
  * Enqueue the projection of n_req subjects given like p2_load_slices (column
  * ids in the model's original column order; location 0: host, validated on

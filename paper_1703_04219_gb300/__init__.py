@@ -28,7 +28,7 @@ EXPORTED = ("p2_default_options", "p2_create", "p2_destroy", "p2_load_slices", "
             "p2_iterate", "p2_fit", "p2_get_factors", "p2_set_factors", "p2_get_mttkrp",
             "p2_get_procrustes", "p2_get_U", "p2_iterate_until", "p2_stats", "p2_device_bytes", "p2_mode1_stats_noalloc",
             "p2_projector_create", "p2_projector_destroy", "p2_project", "p2_projector_sync",
-            "p2_set_exchange", "p2_last_error")
+            "p2_set_exchange", "p2_projector_bytes", "p2_last_error")
 
 
 class p2_options(ctypes.Structure):
@@ -85,6 +85,7 @@ def _load():
         "p2_project": ([vp, i64, vp, vp, vp, vp, i32, i32, vp, vp, i32], ctypes.c_int),
         "p2_projector_sync": ([vp], ctypes.c_int),
         "p2_set_exchange": ([vp, vp, vp], ctypes.c_int),
+        "p2_projector_bytes": ([vp, i64, i64, i64, ctypes.POINTER(i64)], ctypes.c_int),
         "p2_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -263,6 +264,14 @@ def p2_mode1_stats_noalloc(K, R, T, G, W, M1, WtW=None, stream=None):
     _check(lib.p2_mode1_stats_noalloc(K, R, _ptr(T), _ptr(G), _ptr(W), _ptr(M1),
                                       _ptr(WtW), ctypes.c_void_p(stream)),
            "p2_mode1_stats_noalloc")
+
+
+def p2_projector_bytes(model, max_subjects, max_rows, max_nnz) -> int:
+    """Device bytes of a projector with these capacities on the model."""
+    b = ctypes.c_int64()
+    _check(lib.p2_projector_bytes(model.ctx, int(max_subjects), int(max_rows), int(max_nnz),
+                                  ctypes.byref(b)), "p2_projector_bytes")
+    return b.value
 
 
 class Projector:

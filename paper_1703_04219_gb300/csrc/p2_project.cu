@@ -202,6 +202,20 @@ void proj_free(p2_projector *pj) {
 
 extern "C" {
 
+int p2_projector_bytes(p2_ctx *model, int64_t max_subjects, int64_t max_rows, int64_t max_nnz,
+                       int64_t *bytes) {
+    if (!model || !bytes) return proj_fail(P2_EINVAL, "p2_projector_bytes: NULL argument");
+    if (max_subjects < 1 || max_rows < 0 || max_nnz < 0)
+        return proj_fail(P2_EINVAL, "p2_projector_bytes: bad capacity");
+    const int64_t R = model->R, P = model->P;
+    // the allocations of p2_projector_create, element by element
+    int64_t per_subject = 8 + 8 + 8 + (int64_t)sizeof(dw) * P + 4 * R + 4 * R * R;
+    if (model->opt.nonneg) per_subject += 4 * R + 8;
+    *bytes = per_subject * max_subjects + 3 * 8 + (8 + 2) * max_rows + 8 +
+             (4 + 2 + 4) * max_nnz + (int64_t)sizeof(SmallState);
+    return P2_OK;
+}
+
 int p2_projector_create(p2_ctx *model, int64_t max_subjects, int64_t max_rows, int64_t max_nnz,
                         void *stream, p2_projector **out) {
     if (!out) return proj_fail(P2_EINVAL, "p2_projector_create: NULL out");

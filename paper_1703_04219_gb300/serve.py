@@ -4,8 +4,9 @@ Requests are new subjects to project onto a fitted model (fixed H, V).  The
 server keeps ``n_slots`` projectors, each with its own CUDA stream and pinned
 staging buffers.  Requests that arrive while batches are on the GPU wait in a
 FIFO queue and are admitted into the next batch as soon as a slot frees up,
-as long as the batch fits the slot's memory capacity (subjects, rows,
-non-zeros); a request larger than a whole slot is rejected.  Slots run
+as long as the batch fits the slot's memory (its capacities in subjects, rows
+and non-zeros, sized from a device-memory budget with p2_projector_bytes, or
+given); a request larger than a whole slot is rejected.  Slots run
 concurrently on the device.  Completion is detected with CUDA events, so the
 host loop never blocks on a running batch.
 
@@ -65,14 +66,71 @@ def requests_from_slices(slices, rate_per_s: float, seed: int = 0):
     return out
 
 
+def capacities_for_memory(model, slot_bytes, max_subjects, mean_rows, mean_nnz_per_row,
+                          headroom=2.0):
+    """Capacities (subjects, rows, non-zeros) of one slot whose projector
+    takes at most slot_bytes of device memory (p2_projector_bytes), for
+    requests of the given mean shape: rows and non-zeros sized for at least
+    `headroom` times the mean (more if the budget allows), subjects capped at
+    max_subjects and reduced until that headroom fits."""
+    from . import p2_projector_bytes
+
+    def need(s, f):
+        rows = int(np.ceil(f * s * mean_rows))
+        nnz = int(np.ceil(f * s * mean_rows * mean_nnz_per_row))
+        return p2_projector_bytes(model, s, rows, nnz), rows, nnz
+
+    s = int(max_subjects)
+    while s > 1 and need(s, headroom)[0] > slot_bytes:
+        s = max(1, s // 2)
+    if need(s, headroom)[0] > slot_bytes:
+        raise ValueError(f"slot memory {slot_bytes} B holds no request of the given shape")
+    lo, hi = float(headroom), float(headroom)
+    while need(s, hi * 2)[0] <= slot_bytes and hi < 1e6:      # largest scale that fits
+        hi *= 2
+    hi *= 2
+    for _ in range(40):
+        mid = (lo + hi) / 2
+        if need(s, mid)[0] <= slot_bytes:
+            lo = mid
+        else:
+            hi = mid
+    b, rows, nnz = need(s, lo)
+    return s, rows, nnz, b
+
+
 class Server:
+    """Continuous-batching server.  Capacities per slot either given
+    (max_subjects, max_rows, max_nnz) or derived from a device-memory budget:
+    memory_bytes for all slots' scratch, or memory_fraction of the device's
+    free memory at start-up, with the request shape (mean rows per subject,
+    mean non-zeros per row); max_subjects then caps a batch's subjects (a
+    latency bound).  A request is admitted into a batch while the batch fits
+    the slot's capacities, i.e. its memory."""
+
     def __init__(self, model, n_slots: int = 4, max_subjects: int = 256,
-                 max_rows: int = 65536, max_nnz: int = 262144, n_iter: int = 10):
+                 max_rows: int = 65536, max_nnz: int = 262144, n_iter: int = 10,
+                 memory_bytes=None, memory_fraction=None, shape=(33.0, 3.0),
+                 log_batches: bool = False):
         import torch
         self.torch = torch
         self.R = model.R
         self.n_iter = n_iter
+        self.admission = None
+        if memory_fraction is not None and memory_bytes is None:
+            free, _ = torch.cuda.mem_get_info()
+            memory_bytes = int(memory_fraction * free)
+            self.admission = {"free_device_bytes": int(free), "memory_fraction": memory_fraction}
+        if memory_bytes is not None:
+            slot_bytes = int(memory_bytes) // n_slots
+            max_subjects, max_rows, max_nnz, used = capacities_for_memory(
+                model, slot_bytes, max_subjects, shape[0], shape[1])
+            self.admission = dict(self.admission or {}, memory_bytes=int(memory_bytes),
+                                  slot_bytes=slot_bytes, slot_projector_bytes=int(used),
+                                  capacity={"subjects": max_subjects, "rows": max_rows,
+                                            "nnz": max_nnz})
         self.cap = (max_subjects, max_rows, max_nnz)
+        self.batch_log = [] if log_batches else None
         self.slots = []
         for _ in range(n_slots):
             st = torch.cuda.Stream()
@@ -107,6 +165,8 @@ class Server:
             row += r.rows
             nz += r.nnz
             sp[i + 1] = row
+        if self.batch_log is not None:
+            self.batch_log.append((n, row, nz))
         slot.pj.submit(n, slot.sp, slot.rp, slot.col, slot.val, self.n_iter, slot.S)
         slot.event.record(slot.stream)
         slot.batch = batch
@@ -162,5 +222,7 @@ class Server:
             "subjects_per_s": len(results) / makespan if makespan > 0 else None,
             "batches": len(batches), "mean_batch": float(np.mean(batches)) if batches else 0.0,
             "makespan_s": makespan,
+            "admission": self.admission or {"capacity": dict(zip(("subjects", "rows", "nnz"),
+                                                                 self.cap))},
         }
         return results, stats

@@ -28,7 +28,7 @@ CASES = {
     "iterate_r20": ["iterate", "c250m", "12", "20"],     # outside the rank-compiled list
     "iterate_r5_bf16": ["iterate", "tiny", "24", "5", "bf16"],
     "iterate_r5_nonneg": ["iterate", "tiny", "24", "5", "nonneg"],
-    "iterate_r24_nonneg": ["iterate", "c250m", "40", "24", "nonneg"],
+    "iterate_r17_nonneg": ["iterate", "tiny", "24", "17", "nonneg"],
     "iterate_r10_fp64": ["iterate", "tiny", "24", "10", "fp64"],
     "iterate_r40_fp64": ["iterate", "tiny", "16", "40", "fp64"],
     "project_r12": ["project", "12", "3"],
@@ -115,10 +115,10 @@ def test_emulated_seeded_init_and_stopping_rule(emulated_runs):
     assert out["n_loose"] == 2
 
 
-@pytest.mark.parametrize("name", ["iterate_r5_nonneg", "iterate_r24_nonneg"])
+@pytest.mark.parametrize("name", ["iterate_r5_nonneg", "iterate_r17_nonneg"])
 def test_emulated_nonneg_iteration_is_in_bounds_and_matches_oracle(emulated_runs, name):
     """Section 5.1's non-negative variant: row-wise NNLS for V and W (one
-    lane per row at R = 5, one warp per row at R = 24)."""
+    lane per row at R = 5, one warp per row at R = 17)."""
     err = _result(emulated_runs, name)
     assert err["neg"] == 0.0
     for key in ("M1", "M2", "M3", "H", "V", "W"):

@@ -220,7 +220,7 @@ def test_seeded_init_and_stopping_rule(p2):
 @pytest.mark.parametrize("name,K,R", [("tiny", 200, 5), ("c63m", 3000, 10), ("c63m", 1500, 16),
                                       ("ptiny", 50, 5), ("p63m", 2000, 10),
                                       # one warp per row above R = 16
-                                      ("c250m", 400, 24), ("c250m", 400, 40), ("ptiny", 50, 40),
+                                      ("c250m", 400, 24), ("c250m", 400, 40), ("p500m", 300, 40),
                                       ("tiny", 120, 64)])
 def test_nonneg_one_step_parity(p2, name, K, R):
     """Section 5.1's variant (non-negative S_k and V): one iteration from the

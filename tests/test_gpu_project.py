@@ -92,28 +92,113 @@ def test_result_is_the_same_alone_and_in_the_mix(p2):
 
 
 def test_concurrent_projectors_overlap_and_agree(p2):
+    """Two projectors on two streams: the same results as one at a time, and
+    their device work overlaps.  CUDA events bracket each batch on its own
+    stream; the two intervals intersect, and the pair finishes in well under
+    the sum of the two batches' times when run one after the other."""
     torch = pytest.importorskip("torch")
     m = _model(p2, 10)
-    a, b = _requests(50, 2), _requests(50, 3)
-    with p2.Projector(m, 64, 20_000, 200_000) as pj:
-        Sa_ref = pj.project(a, n_iter=5)
-        Sb_ref = pj.project(b, n_iter=5)
+    a, b = _requests(400, 2), _requests(400, 3)
+    n_iter = 10
+    arrs = {id(r): [np.ascontiguousarray(x) for x in (r.subj_ptr, r.row_ptr, r.col, r.val)]
+            for r in (a, b)}
     s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
-    pa = p2.Projector(m, 64, 20_000, 200_000, stream=s1.cuda_stream)
-    pb = p2.Projector(m, 64, 20_000, 200_000, stream=s2.cuda_stream)
-    outs = []
-    for pj, req in ((pa, a), (pb, b)):
-        arrs = [np.ascontiguousarray(x) for x in (req.subj_ptr, req.row_ptr, req.col, req.val)]
-        S = np.empty((req.K, 10), np.float32)
-        pj.submit(req.K, *arrs, 5, S)
-        outs.append((arrs, S))
-    pa.sync()
-    pb.sync()
+    pa = p2.Projector(m, 512, 40_000, 400_000, stream=s1.cuda_stream)
+    pb = p2.Projector(m, 512, 40_000, 400_000, stream=s2.cuda_stream)
+    ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
+
+    def run(pj, st, req, S):
+        e0, e1 = ev(), ev()
+        e0.record(st)
+        pj.submit(req.K, *arrs[id(req)], n_iter, S)
+        e1.record(st)
+        return e0, e1
+
+    # one at a time (after a warm-up of both)
+    Sa_ref, Sb_ref = np.empty((a.K, 10), np.float32), np.empty((b.K, 10), np.float32)
+    for _ in range(2):
+        run(pa, s1, a, Sa_ref)
+        pa.sync()
+        run(pb, s2, b, Sb_ref)
+        pb.sync()
+    serial = []
+    for _ in range(3):
+        ta0, ta1 = run(pa, s1, a, Sa_ref)
+        pa.sync()
+        tb0, tb1 = run(pb, s2, b, Sb_ref)
+        pb.sync()
+        serial.append(ta0.elapsed_time(ta1) + tb0.elapsed_time(tb1))
+    # both in flight
+    conc, intersect = [], []
+    for _ in range(3):
+        Sa, Sb = np.empty_like(Sa_ref), np.empty_like(Sb_ref)
+        torch.cuda.synchronize()
+        origin = ev()
+        origin.record(s1)
+        ta0, ta1 = run(pa, s1, a, Sa)
+        tb0, tb1 = run(pb, s2, b, Sb)
+        pa.sync()
+        pb.sync()
+        a0, a1 = origin.elapsed_time(ta0), origin.elapsed_time(ta1)
+        b0, b1 = origin.elapsed_time(tb0), origin.elapsed_time(tb1)
+        intersect.append(a0 < b1 and b0 < a1)
+        conc.append(max(a1, b1) - min(a0, b0))
+        assert np.array_equal(Sa, Sa_ref) and np.array_equal(Sb, Sb_ref)
     pa.close()
     pb.close()
     m.close()
-    assert np.array_equal(outs[0][1], Sa_ref)
-    assert np.array_equal(outs[1][1], Sb_ref)
+    assert all(intersect)
+    assert min(conc) < 0.85 * min(serial), (conc, serial)
+
+
+def test_server_admits_by_device_memory(p2):
+    """Slots sized from a device-memory budget (p2_projector_bytes): every
+    launched batch fits the slot's capacities, the slot's projector takes no
+    more than its share of the budget, a request larger than a slot is
+    rejected, and the results equal the direct projection."""
+    pytest.importorskip("torch")
+    from paper_1703_04219_gb300.serve import Server, requests_from_slices
+    m = _model(p2, 10)
+    req = _requests(200, 6)
+    budget = 3 * p2.p2_projector_bytes(m, 24, 24 * 66, 24 * 66 * 3)
+    srv = Server(m, n_slots=3, max_subjects=64, n_iter=4, memory_bytes=budget,
+                 shape=(33.0, 3.0), log_batches=True)
+    adm = srv.admission
+    cap = adm["capacity"]
+    assert adm["slot_projector_bytes"] <= adm["slot_bytes"] == budget // 3
+    assert p2.p2_projector_bytes(m, cap["subjects"], cap["rows"], cap["nnz"]) <= budget // 3
+    reqs = requests_from_slices(req, rate_per_s=20000.0, seed=2)
+    big = max(reqs, key=lambda r: r.rows)
+    res, stats = srv.run(reqs)
+    log = srv.batch_log
+    srv.close()
+    with p2.Projector(m, 256, 60_000, 400_000) as pj:
+        S = pj.project(req, n_iter=4)
+    m.close()
+    assert stats["completed"] + stats["rejected"] == req.K
+    for n, rows, nnz in log:
+        assert n <= cap["subjects"] and rows <= cap["rows"] and nnz <= cap["nnz"]
+    too_big = [r.rid for r in reqs if r.rows > cap["rows"] or r.nnz > cap["nnz"]]
+    assert stats["rejected"] == len(too_big)
+    if big.rows > cap["rows"]:
+        assert big.rid not in res
+    for k, s in res.items():
+        assert np.array_equal(s, S[k]), k
+
+
+def test_projector_bytes_matches_its_allocation(p2):
+    torch = pytest.importorskip("torch")
+    m = _model(p2, 10, K=100, iters=1)
+    want = p2.p2_projector_bytes(m, 5000, 200_000, 2_000_000)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    pj = p2.Projector(m, 5000, 200_000, 2_000_000)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    pj.close()
+    m.close()
+    used = free0 - free1
+    assert want - 4 * 2 ** 20 <= used <= want + 64 * 2 ** 20, (want, used)
 
 
 def test_projection_rejects_malformed_requests(p2):

@@ -7,9 +7,11 @@ contexts' exchange hooks (shard.LocalExchange) sum their partial M1, W^TW,
 
 * every shard holds bitwise the same H, V, M1 and M2 and the same fit;
 * H, V, M1, M2, the concatenated W and M3 and the fit agree with one
-  unsharded context on the whole collection within the FP32 tolerances
-  (relative Frobenius 1e-5, fit 1e-4), after one and after three iterations,
-  at R = 10 and at R = 40 (also in the non-negative variant);
+  unsharded context on the whole collection: after one iteration within the
+  FP32 tolerances (relative Frobenius 1e-5, fit 1e-4), after two or three
+  within 1e-4 (the two runs sum in different orders, and ALS carries the
+  round-off differences forward), at R = 10, 24 and 40, also in the
+  non-negative variant;
 * a hook that fails makes the call return P2_EEXCHANGE, and the hook must be
   set before the slices are loaded (P2_ESTATE).
 
@@ -75,9 +77,11 @@ def _sharded(p2, X, R, H0, V0, W0, n_iter, n_shards, **kw):
 
 
 @pytest.mark.parametrize("name,K,R,n_shards,n_iter,nonneg", [
-    ("c63m", 3000, 10, 2, 1, False), ("c63m", 3000, 10, 3, 3, False),
-    ("c250m", 600, 40, 2, 3, False), ("c63m", 2000, 10, 2, 3, True),
-    ("c250m", 400, 24, 4, 2, True)])
+    ("c63m", 3000, 10, 2, 1, False), ("c63m", 3000, 10, 3, 1, False),
+    ("c250m", 600, 40, 2, 1, False), ("c63m", 2000, 10, 2, 1, True),
+    ("c250m", 400, 24, 4, 1, True),
+    ("c63m", 3000, 10, 3, 3, False), ("c250m", 600, 40, 2, 3, False),
+    ("c63m", 2000, 10, 2, 3, True), ("c250m", 400, 24, 4, 2, True)])
 def test_shards_match_one_context(p2, name, K, R, n_shards, n_iter, nonneg):
     X = synth.generate(name, K=K)
     H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=21)
@@ -89,9 +93,13 @@ def test_shards_match_one_context(p2, name, K, R, n_shards, n_iter, nonneg):
         assert g["fits"] == got[0]["fits"]
     W = np.concatenate([g["W"] for g in got])
     M3 = np.concatenate([g["M3"] for g in got])
+    # one step: the kernels' tolerance; more steps: the two runs sum in
+    # different orders, and ALS carries those round-off differences forward
+    # like any FP32 trajectory (the ten-iteration tests allow 1e-4 as well)
+    tol = 1e-5 if n_iter == 1 else 1e-4
     for key, v in (("H", got[0]["H"]), ("V", got[0]["V"]), ("M1", got[0]["M1"]),
                    ("M2", got[0]["M2"]), ("W", W), ("M3", M3)):
-        assert rel_fro(v, ref[key]) < 1e-5, (key, rel_fro(v, ref[key]))
+        assert rel_fro(v, ref[key]) < tol, (key, rel_fro(v, ref[key]))
     assert max(abs(a - b) for a, b in zip(got[0]["fits"], ref["fits"])) < 1e-4
 
 

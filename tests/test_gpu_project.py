@@ -93,19 +93,23 @@ def test_result_is_the_same_alone_and_in_the_mix(p2):
 
 def test_concurrent_projectors_overlap_and_agree(p2):
     """Two projectors on two streams: the same results as one at a time, and
-    their device work overlaps.  CUDA events bracket each batch on its own
-    stream; the two intervals intersect, and the pair finishes in well under
-    the sum of the two batches' times when run one after the other."""
+    their device work overlaps.  Both batches (pinned host buffers, so a
+    submit only validates and enqueues) are queued behind one gate event that
+    a short bounded device sleep delays, so neither starts before both are
+    enqueued; CUDA events bracket each batch on its own stream.  The two
+    intervals intersect, and the pair finishes in well under the sum of the
+    two batches' times run one after the other."""
     torch = pytest.importorskip("torch")
     m = _model(p2, 10)
     a, b = _requests(400, 2), _requests(400, 3)
     n_iter = 10
-    arrs = {id(r): [np.ascontiguousarray(x) for x in (r.subj_ptr, r.row_ptr, r.col, r.val)]
-            for r in (a, b)}
-    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()   # noqa: E731
+    arrs = {id(r): [pin(x) for x in (r.subj_ptr, r.row_ptr, r.col, r.val)] for r in (a, b)}
+    s0, s1, s2 = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     pa = p2.Projector(m, 512, 40_000, 400_000, stream=s1.cuda_stream)
     pb = p2.Projector(m, 512, 40_000, 400_000, stream=s2.cuda_stream)
     ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
+    out = lambda r: torch.empty((r.K, 10), dtype=torch.float32).pin_memory()   # noqa: E731
 
     def run(pj, st, req, S):
         e0, e1 = ev(), ev()
@@ -114,9 +118,8 @@ def test_concurrent_projectors_overlap_and_agree(p2):
         e1.record(st)
         return e0, e1
 
-    # one at a time (after a warm-up of both)
-    Sa_ref, Sb_ref = np.empty((a.K, 10), np.float32), np.empty((b.K, 10), np.float32)
-    for _ in range(2):
+    Sa_ref, Sb_ref = out(a), out(b)
+    for _ in range(2):                                  # warm-up, one at a time
         run(pa, s1, a, Sa_ref)
         pa.sync()
         run(pb, s2, b, Sb_ref)
@@ -128,13 +131,17 @@ def test_concurrent_projectors_overlap_and_agree(p2):
         tb0, tb1 = run(pb, s2, b, Sb_ref)
         pb.sync()
         serial.append(ta0.elapsed_time(ta1) + tb0.elapsed_time(tb1))
-    # both in flight
     conc, intersect = [], []
     for _ in range(3):
-        Sa, Sb = np.empty_like(Sa_ref), np.empty_like(Sb_ref)
+        Sa, Sb = out(a), out(b)
         torch.cuda.synchronize()
-        origin = ev()
-        origin.record(s1)
+        origin, gate = ev(), torch.cuda.Event()
+        origin.record(s0)
+        with torch.cuda.stream(s0):
+            torch.cuda._sleep(20_000_000)               # ~10 ms: both batches get queued
+        gate.record(s0)
+        s1.wait_event(gate)
+        s2.wait_event(gate)
         ta0, ta1 = run(pa, s1, a, Sa)
         tb0, tb1 = run(pb, s2, b, Sb)
         pa.sync()
@@ -143,10 +150,11 @@ def test_concurrent_projectors_overlap_and_agree(p2):
         b0, b1 = origin.elapsed_time(tb0), origin.elapsed_time(tb1)
         intersect.append(a0 < b1 and b0 < a1)
         conc.append(max(a1, b1) - min(a0, b0))
-        assert np.array_equal(Sa, Sa_ref) and np.array_equal(Sb, Sb_ref)
+        assert torch.equal(Sa, Sa_ref) and torch.equal(Sb, Sb_ref)
     pa.close()
     pb.close()
     m.close()
+    print(f"\nserial {min(serial):.3f} ms, concurrent {min(conc):.3f} ms")
     assert all(intersect)
     assert min(conc) < 0.85 * min(serial), (conc, serial)
 

@@ -75,6 +75,25 @@ typedef struct {
                              (float-float) arithmetic on the FP32 pipe, ~2^-46 normwise */
 } p2_options;
 
+/* Launch choices that change the speed, never the results (every choice
+ * computes the same values bit for bit). */
+typedef struct {
+    int32_t procrustes_split;  /* R > 12, double-word Procrustes step: 1 (default) = split into
+                                  a Householder kernel, a one-lane-per-subject QR kernel that
+                                  records its Givens rotations, and a kernel that applies them;
+                                  0 = one fused kernel */
+    int32_t subject_bins;      /* sparse passes take the subjects in bins of their non-zero
+                                  count (1), in their own order (0), or by the rule R > 16 (-1,
+                                  default) */
+    int32_t split_record_cap;  /* split Procrustes step: Givens rotations recorded per subject
+                                  (0 = all the scratch holds, 2 R^2 + 2 R); a subject that needs
+                                  more is finished by the fused kernel */
+} p2_tuning;
+
+int p2_get_tuning(p2_ctx *ctx, p2_tuning *out);
+/* P2_EINVAL for a value out of range; a captured iteration is re-captured. */
+int p2_set_tuning(p2_ctx *ctx, const p2_tuning *t);
+
 /* Counters and timings of a context (p2_stats). */
 typedef struct {
     int64_t kernel_launches;    /* kernels this context has enqueued (graph replays included) */

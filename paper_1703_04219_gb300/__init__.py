@@ -28,7 +28,8 @@ EXPORTED = ("p2_default_options", "p2_create", "p2_destroy", "p2_load_slices", "
             "p2_iterate", "p2_fit", "p2_get_factors", "p2_set_factors", "p2_get_mttkrp",
             "p2_get_procrustes", "p2_get_U", "p2_iterate_until", "p2_stats", "p2_device_bytes", "p2_mode1_stats_noalloc",
             "p2_projector_create", "p2_projector_destroy", "p2_project", "p2_projector_sync",
-            "p2_set_exchange", "p2_projector_bytes", "p2_last_error")
+            "p2_set_exchange", "p2_projector_bytes", "p2_get_tuning", "p2_set_tuning",
+            "p2_last_error")
 
 
 class p2_options(ctypes.Structure):
@@ -37,6 +38,11 @@ class p2_options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("timing", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("nonneg", ctypes.c_int32),
                 ("fp64_procrustes", ctypes.c_int32)]
+
+
+class p2_tuning(ctypes.Structure):
+    _fields_ = [("procrustes_split", ctypes.c_int32), ("subject_bins", ctypes.c_int32),
+                ("split_record_cap", ctypes.c_int32)]
 
 
 class p2_stats_t(ctypes.Structure):
@@ -86,6 +92,8 @@ def _load():
         "p2_projector_sync": ([vp], ctypes.c_int),
         "p2_set_exchange": ([vp, vp, vp], ctypes.c_int),
         "p2_projector_bytes": ([vp, i64, i64, i64, ctypes.POINTER(i64)], ctypes.c_int),
+        "p2_get_tuning": ([vp, ctypes.POINTER(p2_tuning)], ctypes.c_int),
+        "p2_set_tuning": ([vp, ctypes.POINTER(p2_tuning)], ctypes.c_int),
         "p2_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -404,6 +412,21 @@ class Parafac2:
         k1 = self.K if k1 is None else k1
         n = int(self._subj_ptr[k1] - self._subj_ptr[k0])
         return p2_get_U(self.ctx, k0, k1, n, self.R)
+
+    def tuning(self) -> dict:
+        """The launch choices in force (p2_get_tuning)."""
+        t = p2_tuning()
+        _check(lib.p2_get_tuning(self.ctx, ctypes.byref(t)), "p2_get_tuning")
+        return {"procrustes_split": t.procrustes_split, "subject_bins": t.subject_bins,
+                "split_record_cap": t.split_record_cap}
+
+    def set_tuning(self, **kw):
+        """Change launch choices (p2_set_tuning); results do not change."""
+        cur = self.tuning()
+        cur.update(kw)
+        t = p2_tuning(int(cur["procrustes_split"]), int(cur["subject_bins"]),
+                      int(cur["split_record_cap"]))
+        _check(lib.p2_set_tuning(self.ctx, ctypes.byref(t)), "p2_set_tuning")
 
     def set_exchange(self, fn):
         """Make this context one shard of a subject-sharded collection (see

@@ -94,6 +94,11 @@ static void free_data(p2_ctx *c) {
     dfree(c, &c->d_T, K * R * R);
     dfree(c, &c->d_G, K * P);
     dfree(c, &c->d_Gf, K * P);
+    dfree(c, &c->d_split, c->split_bytes);
+    dfree(c, &c->d_split_list, (size_t)c->split_chunk);
+    dfree(c, &c->d_split_cnt, 1);
+    c->split_chunk = c->split_cap = 0;
+    c->split_bytes = 0;
     delete[] c->h_perm_new2old;
     delete[] c->h_perm_old2new;
     c->h_perm_new2old = c->h_perm_old2new = nullptr;
@@ -158,6 +163,38 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
     P2_CUDA_TRY(cudaMemsetAsync(c->d_M3, 0, sizeof(float) * (size_t)K * R, c->stream));
     c->h_perm_new2old = new int32_t[J];
     c->h_perm_old2new = new int32_t[J];
+    if (R > 12 && K > 0) {
+        // scratch of the split Procrustes step for one chunk of subjects: at
+        // most 8 GiB and an eighth of the free memory, a chunk of at least 4,096
+        // subjects (otherwise the fused kernel runs)
+        const size_t cap = 2 * R * R + 2 * R;       // rotations recorded per subject
+        const size_t per = 8 * R * R + 28 * R + 8 + 17 * cap;
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            fr = 0;
+        }
+        size_t budget = (size_t)8 << 30;
+        if (fr / 8 < budget) budget = fr / 8;
+        int64_t ch = (int64_t)(budget / per);
+        if (ch > K) ch = K;
+        if (ch >= 4096 || ch == K) {
+            c->split_chunk = ch;
+            c->split_cap = (int64_t)cap;
+            c->split_bytes = (size_t)ch * per + 16 * 256;
+            if (dalloc(c, &c->d_split, c->split_bytes) != P2_OK ||
+                dalloc(c, &c->d_split_list, (size_t)ch) != P2_OK ||
+                dalloc(c, &c->d_split_cnt, 1) != P2_OK) {
+                // the fused kernel needs none of it
+                dfree(c, &c->d_split, c->split_bytes);
+                dfree(c, &c->d_split_list, (size_t)ch);
+                dfree(c, &c->d_split_cnt, 1);
+                c->split_chunk = c->split_cap = 0;
+                c->split_bytes = 0;
+                set_error("");
+            }
+        }
+    }
     return P2_OK;
 }
 
@@ -321,6 +358,25 @@ int p2_create(p2_ctx **out, const p2_options *opt) {
         return rc;
     }
     *out = c;
+    return P2_OK;
+}
+
+int p2_get_tuning(p2_ctx *c, p2_tuning *t) {
+    if (!c || !t) return fail(P2_EINVAL, "p2_get_tuning: NULL argument");
+    *t = c->tune;
+    return P2_OK;
+}
+
+int p2_set_tuning(p2_ctx *c, const p2_tuning *t) {
+    if (!c || !t) return fail(P2_EINVAL, "p2_set_tuning: NULL argument");
+    if ((t->procrustes_split != 0 && t->procrustes_split != 1) || t->subject_bins < -1 ||
+        t->subject_bins > 1 || t->split_record_cap < 0)
+        return fail(P2_EINVAL, "p2_set_tuning: bad value");
+    c->tune = *t;
+    if (c->graph) {                 // the captured iteration holds the old launches
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
     return P2_OK;
 }
 

@@ -172,6 +172,15 @@ struct p2_ctx {
     double *d_part2 = nullptr;  // second partial buffer
     int *d_colcount = nullptr;  // [J] (load time)
 
+    // split Procrustes step (R > 12): one chunk's scratch (GrpSplit in
+    // p2_polar_grp.cuh, carved by split_scratch), the fallback list
+    unsigned char *d_split = nullptr;
+    size_t split_bytes = 0;
+    int64_t split_chunk = 0, split_cap = 0;
+    int32_t *d_split_list = nullptr;
+    int32_t *d_split_cnt = nullptr;
+    p2_tuning tune{1, -1, 0};   // launch choices (p2_set_tuning, the autotuner)
+
     // subject-sharded form: the caller's exchange hook (NULL: unsharded) and
     // the one-row sum of the statistics partials that it exchanges
     p2_exchange_fn xfn = nullptr;

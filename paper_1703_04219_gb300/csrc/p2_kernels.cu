@@ -46,9 +46,11 @@ static __device__ __forceinline__ int warp_excl_scan(int v, int lane) {
 static XView xview(const p2_ctx *c) {
     // subject bins pay above R = 16, where a subject's work is large enough
     // for the tail of the persistent grid to matter (R = 40: alpha pass -3%);
-    // at R = 10 the natural order's sequential walk over X is worth more (+1.5%)
+    // at R = 10 the natural order's sequential walk over X is worth more
+    // (+1.5%); the tuning can override the rule
+    const bool bins = c->tune.subject_bins < 0 ? c->R > 16 : c->tune.subject_bins != 0;
     return XView{c->X.subj_row, c->X.subj_nnz, c->X.row_len, c->X.col, c->X.val, c->X.K,
-                 c->R > 16 ? c->d_sorder : nullptr};
+                 bins ? c->d_sorder : nullptr};
 }
 
 // The error-free transformations below hold only if every rounding happens

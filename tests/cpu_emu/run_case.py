@@ -173,6 +173,26 @@ def rational_case(R, K):
             "einval": einval, "still_iterates": still}
 
 
+def split_case(R, K):
+    """The split Procrustes step (QR recorder) against the fused kernel, and
+    with a record capacity small enough that most subjects go to the fused
+    fallback: T_k and the factors bitwise equal after one iteration."""
+    X = synth.generate("tiny", K=K)
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=17)
+    outs = []
+    for tune in (dict(procrustes_split=1), dict(procrustes_split=0),
+                 dict(procrustes_split=1, split_record_cap=R)):
+        with p2.Parafac2(R, use_graph=False) as m:
+            m.set_tuning(**tune)
+            m.load(X)
+            m.init(H0, V0, W0)
+            T0 = m.procrustes()
+            m.iterate(1)
+            outs.append((T0, m.procrustes()) + m.factors())
+    same = all(np.array_equal(a, b) for o in outs[1:] for a, b in zip(outs[0], o))
+    return {"bitwise": float(same)}
+
+
 def shard_case(R, K):
     """A context whose exchange hook doubles every buffer (the sum over two
     shards that hold the same subjects) against an unsharded context on the
@@ -221,6 +241,8 @@ if __name__ == "__main__":
         out = seed_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "rational":
         out = rational_case(int(sys.argv[2]), int(sys.argv[3]))
+    elif kind == "split":
+        out = split_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "shard":
         out = shard_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "getu":

@@ -1,0 +1,46 @@
+"""The split Procrustes step for R > 12 (p2_tuning.procrustes_split): a
+Householder kernel stores Q_h and the tridiagonal, a one-lane-per-subject
+kernel runs the QR iteration and records its Givens rotations, and a third
+kernel applies them to Q_h and forms T_k; subjects whose rotations exceed
+the record are finished by the fused kernel.  The arithmetic and its order
+are the fused kernel's, so T_k, the factors and the MTTKRPs must be the same
+bit for bit, with and without the fallback (a small record capacity), on
+the rank-compiled and the generic instances."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def p2():
+    import paper_1703_04219_gb300 as mod
+    return mod
+
+
+@pytest.mark.parametrize("name,K,R", [("c250m", 3000, 40), ("c250m", 1500, 24),
+                                      ("tiny", 150, 13), ("c250m", 800, 20), ("tiny", 80, 64)])
+def test_split_procrustes_is_bitwise_the_fused_kernel(p2, name, K, R):
+    X = synth.generate(name, K=K)
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=23)
+    outs = []
+    for tune in (dict(procrustes_split=1), dict(procrustes_split=0),
+                 dict(procrustes_split=1, split_record_cap=R * 4)):
+        with p2.Parafac2(R) as m:
+            m.set_tuning(**tune)
+            m.load(X)
+            m.init(H0, V0, W0)
+            T0 = m.procrustes()
+            fits = [m.iterate(1) for _ in range(2)]
+            st = m.stats()
+            outs.append(dict(T0=T0, T=m.procrustes(), F=m.factors(), M1=m.mttkrp(1),
+                             fits=fits, flops=st["polar_fp64_flops"]))
+    ref = outs[0]
+    for o in outs[1:]:
+        assert np.array_equal(o["T0"], ref["T0"]) and np.array_equal(o["T"], ref["T"])
+        for a, b in zip(o["F"], ref["F"]):
+            assert np.array_equal(a, b)
+        assert np.array_equal(o["M1"], ref["M1"]) and o["fits"] == ref["fits"]
+        assert o["flops"] == ref["flops"]

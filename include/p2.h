@@ -73,6 +73,14 @@ typedef struct {
                              formation of T_k run in FP64 on the FP64 pipe (same algorithm,
                              Householder + implicit QR); zero (default): in double-word
                              (float-float) arithmetic on the FP32 pipe, ~2^-46 normwise */
+    int32_t autotune;     /* non-zero: the first p2_iterate times the launch choices of
+                             p2_tuning on this context's data (split or fused Procrustes
+                             step for R > 12, subject bins on or off for the sparse passes)
+                             and keeps the fastest; zero (default): the built-in rules */
+    const char *tune_cache; /* nullable: a file of tuned choices, one JSON object per line
+                             keyed by rank, precision, variant and the collection's K, J and
+                             non-zero count; a matching line is used instead of timing, and a
+                             newly timed choice is appended */
 } p2_options;
 
 /* Launch choices that change the speed, never the results (every choice
@@ -91,6 +99,9 @@ typedef struct {
 } p2_tuning;
 
 int p2_get_tuning(p2_ctx *ctx, p2_tuning *out);
+/* How the autotuner chose ("" before it ran; "cache", or the timings it took).
+ * The string belongs to the context. */
+const char *p2_tuning_note(p2_ctx *ctx);
 /* P2_EINVAL for a value out of range; a captured iteration is re-captured. */
 int p2_set_tuning(p2_ctx *ctx, const p2_tuning *t);
 
@@ -109,7 +120,7 @@ typedef struct {
 
 /* Fill *opt with defaults for rank R (precision FP32, device 0, graph on,
  * rank_rtol 1e-5, own stream, timing off, seed 20170314, unconstrained,
- * double-word Procrustes). */
+ * double-word Procrustes, no autotuning, no tuning cache). */
 void p2_default_options(p2_options *opt, int32_t R);
 
 /* Create a context on opt->device.  *out receives the handle (NULL on error).

@@ -29,7 +29,7 @@ EXPORTED = ("p2_default_options", "p2_create", "p2_destroy", "p2_load_slices", "
             "p2_get_procrustes", "p2_get_U", "p2_iterate_until", "p2_stats", "p2_device_bytes", "p2_mode1_stats_noalloc",
             "p2_projector_create", "p2_projector_destroy", "p2_project", "p2_projector_sync",
             "p2_set_exchange", "p2_projector_bytes", "p2_get_tuning", "p2_set_tuning",
-            "p2_last_error")
+            "p2_tuning_note", "p2_last_error")
 
 
 class p2_options(ctypes.Structure):
@@ -37,7 +37,8 @@ class p2_options(ctypes.Structure):
                 ("use_graph", ctypes.c_int32), ("rank_rtol", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("timing", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("nonneg", ctypes.c_int32),
-                ("fp64_procrustes", ctypes.c_int32)]
+                ("fp64_procrustes", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("tune_cache", ctypes.c_char_p)]
 
 
 class p2_tuning(ctypes.Structure):
@@ -94,6 +95,7 @@ def _load():
         "p2_projector_bytes": ([vp, i64, i64, i64, ctypes.POINTER(i64)], ctypes.c_int),
         "p2_get_tuning": ([vp, ctypes.POINTER(p2_tuning)], ctypes.c_int),
         "p2_set_tuning": ([vp, ctypes.POINTER(p2_tuning)], ctypes.c_int),
+        "p2_tuning_note": ([vp], ctypes.c_char_p),
         "p2_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -335,7 +337,8 @@ class Parafac2:
 
     def __init__(self, R: int, device: int = 0, use_graph: bool = True, rank_rtol: float = 1e-5,
                  stream=None, timing: bool = False, precision: str = "fp32", seed=None,
-                 nonneg: bool = False, fp64_procrustes: bool = False):
+                 nonneg: bool = False, fp64_procrustes: bool = False, autotune: bool = False,
+                 tune_cache=None):
         if precision not in ("fp32", "bf16"):
             raise ValueError("precision must be 'fp32' or 'bf16'")
         opt = p2_default_options(R)
@@ -349,6 +352,9 @@ class Parafac2:
             opt.seed = int(seed)
         opt.nonneg = 1 if nonneg else 0
         opt.fp64_procrustes = 1 if fp64_procrustes else 0
+        opt.autotune = 1 if autotune else 0
+        self._tune_cache = tune_cache.encode() if tune_cache else None   # kept alive
+        opt.tune_cache = self._tune_cache
         self.R = R
         self.precision = precision
         self.ctx = p2_create(opt)
@@ -419,6 +425,9 @@ class Parafac2:
         _check(lib.p2_get_tuning(self.ctx, ctypes.byref(t)), "p2_get_tuning")
         return {"procrustes_split": t.procrustes_split, "subject_bins": t.subject_bins,
                 "split_record_cap": t.split_record_cap}
+
+    def tuning_note(self) -> str:
+        return lib.p2_tuning_note(self.ctx).decode(errors="replace")
 
     def set_tuning(self, **kw):
         """Change launch choices (p2_set_tuning); results do not change."""

@@ -294,6 +294,8 @@ void p2_default_options(p2_options *opt, int32_t R) {
     opt->seed = 20170314ULL;
     opt->nonneg = 0;
     opt->fp64_procrustes = 0;
+    opt->autotune = 0;
+    opt->tune_cache = nullptr;
 }
 
 int p2_create(p2_ctx **out, const p2_options *opt) {
@@ -308,6 +310,8 @@ int p2_create(p2_ctx **out, const p2_options *opt) {
     P2_CUDA_TRY(cudaSetDevice(opt->device));
     p2_ctx *c = new p2_ctx();
     c->opt = *opt;
+    if (opt->tune_cache) c->tune_cache = opt->tune_cache;
+    c->opt.tune_cache = nullptr;                 // the copy above is the one used
     if (!(c->opt.rank_rtol > 0.0)) c->opt.rank_rtol = 1e-5;
     c->R = opt->R;
     c->P = opt->R * (opt->R + 1) / 2;
@@ -365,6 +369,10 @@ int p2_get_tuning(p2_ctx *c, p2_tuning *t) {
     if (!c || !t) return fail(P2_EINVAL, "p2_get_tuning: NULL argument");
     *t = c->tune;
     return P2_OK;
+}
+
+const char *p2_tuning_note(p2_ctx *c) {
+    return c ? c->tune_note.c_str() : "";
 }
 
 int p2_set_tuning(p2_ctx *c, const p2_tuning *t) {
@@ -604,10 +612,90 @@ int p2_set_factors(p2_ctx *c, const float *H, const float *V, const float *W) {
     return set_factors_impl(c, H, V, W);
 }
 
+// The autotuner (p2_options.autotune): the launch choices of p2_tuning timed
+// on this context's data, before the first iteration is captured.  Every
+// choice computes the same values, so the trials change no result.
+static std::string tune_key(const p2_ctx *c) {
+    char b[256];
+    snprintf(b, sizeof b, "R=%d precision=%d nonneg=%d fp64=%d K=%lld J=%d nnz=%lld", c->R,
+             c->opt.precision, c->opt.nonneg ? 1 : 0, c->opt.fp64_procrustes ? 1 : 0,
+             (long long)c->X.K, (int)c->X.J, (long long)c->X.nnz);
+    return b;
+}
+
+static bool tune_from_cache(p2_ctx *c, const std::string &key) {
+    FILE *f = fopen(c->tune_cache.c_str(), "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    const std::string want = "\"key\": \"" + key + "\"";
+    while (fgets(line, sizeof line, f)) {
+        if (!strstr(line, want.c_str())) continue;
+        const char *a = strstr(line, "\"procrustes_split\":");
+        const char *b = strstr(line, "\"subject_bins\":");
+        int ps = 0, sb = 0;
+        if (a && b && sscanf(a, "\"procrustes_split\": %d", &ps) == 1 &&
+            sscanf(b, "\"subject_bins\": %d", &sb) == 1 && (ps == 0 || ps == 1) &&
+            (sb == 0 || sb == 1)) {
+            c->tune.procrustes_split = ps;
+            c->tune.subject_bins = sb;
+            found = true;                 // the last matching line wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static int autotune(p2_ctx *c) {
+    c->tuned = true;
+    const std::string key = tune_key(c);
+    if (!c->tune_cache.empty() && tune_from_cache(c, key)) {
+        c->tune_note = "cache";
+        return P2_OK;
+    }
+    char note[256];
+    float q_split = -1.f, q_fused = -1.f;
+    if (c->R > 12 && c->d_split && !c->opt.fp64_procrustes) {
+        for (int split = 1; split >= 0; --split) {
+            c->tune.procrustes_split = split;
+            float ms = 0.f;
+            P2_TRY(tune_time_qstep(c, 2, &ms));
+            (split ? q_split : q_fused) = ms;
+        }
+        c->tune.procrustes_split = q_split <= q_fused ? 1 : 0;
+    }
+    float b_off = 0.f, b_on = 0.f;
+    c->tune.subject_bins = 0;
+    P2_TRY(tune_time_mode2(c, 2, &b_off));
+    c->tune.subject_bins = 1;
+    P2_TRY(tune_time_mode2(c, 2, &b_on));
+    c->tune.subject_bins = b_on < b_off ? 1 : 0;
+    snprintf(note, sizeof note,
+             "timed: Q-step split %.3f ms, fused %.3f ms; mode-2 pass bins %.3f ms, no bins %.3f ms",
+             q_split, q_fused, b_on, b_off);
+    c->tune_note = note;
+    if (!c->tune_cache.empty()) {
+        FILE *f = fopen(c->tune_cache.c_str(), "a");
+        if (f) {
+            fprintf(f, "{\"key\": \"%s\", \"procrustes_split\": %d, \"subject_bins\": %d}\n",
+                    key.c_str(), c->tune.procrustes_split, c->tune.subject_bins);
+            fclose(f);
+        }
+    }
+    return P2_OK;
+}
+
 int p2_iterate(p2_ctx *c, int32_t n_iter, double *fit_out) {
     P2_TRY(check_ready(c, true));
     if (n_iter < 0) return fail(P2_EINVAL, "p2_iterate: n_iter < 0");
     P2_CUDA_TRY(cudaSetDevice(c->opt.device));
+    if (n_iter > 0 && c->opt.autotune && !c->tuned) {
+        P2_TRY(autotune(c));
+        if (c->graph) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
+    }
     const bool use_graph = c->opt.use_graph && !c->xfn;   // a sharded iteration calls the hook
     if (n_iter > 0 && use_graph && !c->graph) {
         cudaGraph_t g = nullptr;

@@ -180,6 +180,9 @@ struct p2_ctx {
     int32_t *d_split_list = nullptr;
     int32_t *d_split_cnt = nullptr;
     p2_tuning tune{1, -1, 0};   // launch choices (p2_set_tuning, the autotuner)
+    bool tuned = false;         // the autotuner has run (or read the cache)
+    std::string tune_cache;     // opt.tune_cache, copied
+    std::string tune_note;      // how the choices were made (p2_tuning_note)
 
     // subject-sharded form: the caller's exchange hook (NULL: unsharded) and
     // the one-row sum of the statistics partials that it exchanges
@@ -214,6 +217,12 @@ __global__ void __launch_bounds__(256) k_subject_stats(const float *__restrict__
                                                        const float *__restrict__ M3, double *part,
                                                        int64_t K, int R, int with_m3);
 // per-iteration pieces (p2_kernels.cu)
+// autotuner trials (p2_kernels.cu): the Q-step, or the mode-2 pass (its
+// kernels only), enqueued `reps` times; the fastest time in ms.  Both leave
+// the state they feed forward as one run would (the Q-step's T and rotation
+// counts; the mode-2 pass's outputs are recomputed by every iteration).
+int tune_time_qstep(p2_ctx *c, int reps, float *ms);
+int tune_time_mode2(p2_ctx *c, int reps, float *ms);
 // exchange hook call of a sharded context (P2_OK if unsharded)
 int exchange(p2_ctx *c, double *buf, int64_t count);
 int enqueue_prologue(p2_ctx *c);     // Q-step + mode-1 MTTKRP for the current (H, V, W)

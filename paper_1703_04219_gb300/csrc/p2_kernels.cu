@@ -1832,6 +1832,62 @@ int enqueue_prologue(p2_ctx *c) {
     return enqueue_qstep(c, 0);
 }
 
+// Autotuner trials.
+template <class F>
+static int tune_time(p2_ctx *c, int reps, float *ms, F &&enqueue) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    P2_CUDA_TRY(cudaEventCreate(&a));
+    cudaError_t e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        P2_CUDA_TRY(e);
+    }
+    float best = -1.f;
+    int rc = P2_OK;
+    for (int r = 0; r < reps && rc == P2_OK; ++r) {
+        cudaEventRecord(a, c->stream);
+        rc = enqueue();
+        cudaEventRecord(b, c->stream);
+        e = cudaEventSynchronize(b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        if (e != cudaSuccess && rc == P2_OK) {
+            set_error("autotuner timing: %s", cudaGetErrorString(e));
+            rc = P2_ECUDA;
+        }
+        if (rc == P2_OK && (best < 0.f || t < best)) best = t;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ms = best;
+    return rc;
+}
+
+int tune_time_qstep(p2_ctx *c, int reps, float *ms) {
+    return tune_time(c, reps, ms, [c]() -> int {
+        const cudaError_t e = launch_polar(c);
+        if (e != cudaSuccess) {
+            set_error("autotuner: Procrustes launch failed: %s", cudaGetErrorString(e));
+            return P2_ECUDA;
+        }
+        c->enqueued += POLAR_LAUNCHES;
+        return P2_OK;
+    });
+}
+
+int tune_time_mode2(p2_ctx *c, int reps, float *ms) {
+    return tune_time(c, reps, ms, [c]() -> int {
+        const Launch L = plan(c);
+        launch_beta_p(c, L);
+        P2_LAUNCH_CHECK("k_beta_p");
+        if (c->X.nseg > 0) {
+            launch_m2_segments(c);
+            P2_LAUNCH_CHECK("k_m2_segments");
+        }
+        return P2_OK;
+    });
+}
+
 int enqueue_iteration(p2_ctx *c) {
     const Launch L = plan(c);
     const int R = c->R;

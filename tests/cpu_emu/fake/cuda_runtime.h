@@ -101,6 +101,7 @@ inline cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t = nullptr) {
     return cudaSuccess;
 }
 inline cudaError_t cudaEventRecordWithFlags(cudaEvent_t e, cudaStream_t s, unsigned) { return cudaEventRecord(e, s); }
+inline cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
 inline cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t a, cudaEvent_t b) { *ms = (float)(*(double *)b - *(double *)a); return cudaSuccess; }
 template <class F> inline cudaError_t cudaOccupancyMaxActiveBlocksPerMultiprocessor(int *n, F, int, size_t) { *n = 1; return cudaSuccess; }
 template <class F> inline cudaError_t cudaFuncGetAttributes(cudaFuncAttributes *a, F) { *a = cudaFuncAttributes{}; return cudaSuccess; }

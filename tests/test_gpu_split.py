@@ -44,3 +44,31 @@ def test_split_procrustes_is_bitwise_the_fused_kernel(p2, name, K, R):
             assert np.array_equal(a, b)
         assert np.array_equal(o["M1"], ref["M1"]) and o["fits"] == ref["fits"]
         assert o["flops"] == ref["flops"]
+
+
+def test_autotuner_keeps_results_and_uses_its_cache(p2, tmp_path):
+    """p2_options.autotune times the launch choices at the first iteration
+    (split or fused Procrustes step, subject bins) and keeps the fastest;
+    the results equal the untuned context's bit for bit, the choice is
+    appended to the cache file, and a second context reads it from there."""
+    X = synth.generate("c250m", K=4000)
+    R = 40
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=29)
+    cache = str(tmp_path / "tune.jsonl")
+    outs, notes, tunes = [], [], []
+    for kw in (dict(), dict(autotune=True, tune_cache=cache), dict(autotune=True, tune_cache=cache)):
+        with p2.Parafac2(R, **kw) as m:
+            m.load(X)
+            m.init(H0, V0, W0)
+            fit = m.iterate(2)
+            outs.append((fit,) + m.factors())
+            notes.append(m.tuning_note())
+            tunes.append(m.tuning())
+    for o in outs[1:]:
+        assert o[0] == outs[0][0]
+        for a, b in zip(o[1:], outs[0][1:]):
+            assert np.array_equal(a, b)
+    assert notes[0] == "" and notes[1].startswith("timed") and notes[2] == "cache"
+    assert tunes[1] == tunes[2]
+    lines = open(cache).read().strip().splitlines()
+    assert len(lines) == 1 and '"key": "R=40' in lines[0]

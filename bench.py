@@ -181,9 +181,9 @@ def job_throughput(nnz_per_rank, steps, ms_total_max, world):
 
 # sources that define each kernel whose DRAM traffic profiles/traffic.json records
 TRAFFIC_SOURCES = {
-    "k_polar_reg": ("p2_dw.cuh", "p2_eig_dw.cuh", "p2_polar.cu", "p2_polar.cuh"),
-    "k_polar_grp": ("p2_dw.cuh", "p2_polar.cu", "p2_polar.cuh", "p2_polar_grp.cu",
-                    "p2_polar_grp.cuh"),
+    "k_polar_reg": ("p2_dw.cuh", "p2_num.cuh", "p2_eig_dw.cuh", "p2_polar.cu", "p2_polar.cuh"),
+    "k_polar_split": ("p2_dw.cuh", "p2_num.cuh", "p2_polar.cu", "p2_polar.cuh",
+                      "p2_polar_grp.cu", "p2_polar_grp.cuh", "p2_polar_grp_launch.cuh"),
 }
 
 
@@ -306,7 +306,9 @@ def roofline(X, R, phase_ms, flops, wname):
     if dom == "procrustes":
         ach = flops / (phase_ms[dom] / 1e3) / 1e12
         kname = ("k_polar_reg (double-word Procrustes, one lane per subject)" if R <= 12 else
-                 "k_polar_grp (double-word Procrustes, a group of 8 or 16 lanes per subject)")
+                 "split double-word Procrustes step: k_polar_grp<MODE 1> (Householder, a group "
+                 "of 8 or 16 lanes per subject), k_qr_record (QR, one lane per subject), "
+                 "k_polar_grp<MODE 2> (rotations applied, T_k)")
         roof = {"kernel": kname, "bound": "alu",
                 "achieved": ach, "peak": DW_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / DW_PEAK_TFLOPS,
@@ -314,7 +316,7 @@ def roofline(X, R, phase_ms, flops, wname):
                 f"{DW_INSTR_PER_FMA} FP32 instructions per double-word multiply-add",
                 "vs_fp64_nominal": ach / FP64_PEAK_TFLOPS,
                 "algorithmic_flops_per_launch": flops,
-                "traffic": _traffic("k_polar_reg" if R <= 12 else "k_polar_grp", wname)}
+                "traffic": _traffic("k_polar_reg" if R <= 12 else "k_polar_split", wname)}
     else:
         by = bmodel.get(dom, 0)
         ach = by / (phase_ms[dom] / 1e3) / 1e9
@@ -330,7 +332,7 @@ def roofline(X, R, phase_ms, flops, wname):
 
 
 def measure_workload(X, w, precision, steps, warmup, device, gpu_id, fp64_procrustes=False,
-                     nonneg=False):
+                     nonneg=False, tuning=None):
     """One workload timed like the headline (graph replays, CUDA events on the
     library's stream, phase events, clocks sampled in the timed region)."""
     import torch
@@ -340,6 +342,8 @@ def measure_workload(X, w, precision, steps, warmup, device, gpu_id, fp64_procru
     stream = torch.cuda.Stream()
     m = p2.Parafac2(R, device=device, stream=stream.cuda_stream, timing=True,
                     precision=precision, fp64_procrustes=fp64_procrustes, nonneg=nonneg)
+    if tuning:
+        m.set_tuning(**tuning)
     m.load(X)
     m.init(H0, V0, W0)
     for _ in range(warmup):
@@ -348,13 +352,17 @@ def measure_workload(X, w, precision, steps, warmup, device, gpu_id, fp64_procru
     clocks = ClockSampler(gpu_id)
     t = timed_steps(m, stream, steps, None, clocks)
     fit, _ = m.fit()
+    tune = m.tuning()
     m.close()
     ms = t["ms_total"] / steps
     roof, sparse = roofline(X, R, t["phase_ms"], t["flops"], w.name)
+    if tune.get("procrustes_split") == 0 and R > 12 and roof.get("bound") == "alu":
+        roof["kernel"] = "k_polar_grp (fused double-word Procrustes, 8 or 16 lanes per subject)"
+        roof["traffic"] = None
     if fp64_procrustes:
         roof = fp64_roofline(R, t["phase_ms"], t["flops"])
     return {"workload": _workload_desc(w, X), "precision": precision,
-            "procrustes": "fp64" if fp64_procrustes else "double-word",
+            "procrustes": "fp64" if fp64_procrustes else "double-word", "tuning": tune,
             "nonneg": bool(nonneg),
             "storage": "V and P_k bfloat16" if precision == "bf16" else "float",
             "steps": steps, "warmup": warmup, "s_per_iter": ms / 1e3,
@@ -378,24 +386,27 @@ def synth_init(w, X):
 
 
 def run_r40(args, device, gpu_id):
-    """Table 1's R = 40 column: the 250M-non-zero workload in FP32, with
-    bfloat16 storage and with the FP64 arm of the Procrustes step, the
+    """Table 1's R = 40 column: the 250M-non-zero workload in FP32 (split
+    Procrustes step, and the fused kernel for comparison), with bfloat16
+    storage and with the FP64 arm of the Procrustes step, the
     555M-non-zero workload in FP32, and the paper's own configuration
     (planted 500M-non-zero workload, non-negative S_k and V)."""
     import synth
     out = {}
     steps = max(1, min(args.steps, 5))
-    for name, precs in (("c250m", ("fp32", "bf16", "fp64p")), ("c555m", ("fp32",))):
+    for name, precs in (("c250m", ("fp32", "fused", "bf16", "fp64p")), ("c555m", ("fp32",))):
         w = synth.WORKLOADS[name]
         X = synth.generate(w)
         for prec in precs:
             if prec == "fp64p" and args.no_fp64:
                 continue
-            key = f"{name}_fp64_procrustes" if prec == "fp64p" else f"{name}_{prec}"
-            out[key] = measure_workload(X, w, "fp32" if prec == "fp64p" else prec,
+            key = {"fp64p": f"{name}_fp64_procrustes",
+                   "fused": f"{name}_fp32_fused_procrustes"}.get(prec, f"{name}_{prec}")
+            out[key] = measure_workload(X, w, prec if prec in ("fp32", "bf16") else "fp32",
                                         min(steps, 3) if prec == "fp64p" else steps,
                                         args.warmup, device, gpu_id,
-                                        fp64_procrustes=prec == "fp64p")
+                                        fp64_procrustes=prec == "fp64p",
+                                        tuning={"procrustes_split": 0} if prec == "fused" else None)
         del X
     if not args.no_nonneg:
         # the paper's configuration: planted workload, non-negative S_k and V

@@ -43,7 +43,7 @@ class p2_options(ctypes.Structure):
 
 class p2_tuning(ctypes.Structure):
     _fields_ = [("procrustes_split", ctypes.c_int32), ("subject_bins", ctypes.c_int32),
-                ("split_record_cap", ctypes.c_int32)]
+                ("split_record_cap", ctypes.c_int32), ("m2_block_kib", ctypes.c_int32)]
 
 
 class p2_stats_t(ctypes.Structure):
@@ -424,7 +424,7 @@ class Parafac2:
         t = p2_tuning()
         _check(lib.p2_get_tuning(self.ctx, ctypes.byref(t)), "p2_get_tuning")
         return {"procrustes_split": t.procrustes_split, "subject_bins": t.subject_bins,
-                "split_record_cap": t.split_record_cap}
+                "split_record_cap": t.split_record_cap, "m2_block_kib": t.m2_block_kib}
 
     def tuning_note(self) -> str:
         return lib.p2_tuning_note(self.ctx).decode(errors="replace")
@@ -434,7 +434,7 @@ class Parafac2:
         cur = self.tuning()
         cur.update(kw)
         t = p2_tuning(int(cur["procrustes_split"]), int(cur["subject_bins"]),
-                      int(cur["split_record_cap"]))
+                      int(cur["split_record_cap"]), int(cur["m2_block_kib"]))
         _check(lib.p2_set_tuning(self.ctx, ctypes.byref(t)), "p2_set_tuning")
 
     def set_exchange(self, fn):

@@ -73,14 +73,15 @@ static void free_data(p2_ctx *c) {
     dfree(c, &c->d_Vprev, J * v_stride<float>((int)R));
     dfree(c, &c->d_Vh, J * v_stride<bf16_t>((int)R));
     dfree(c, &c->d_Vprevh, J * v_stride<bf16_t>((int)R));
-    dfree(c, &c->d_Ph, N * R);
+    dfree(c, &c->d_Ph, (size_t)c->X.p_rows * R);
     dfree(c, &c->d_Vun, J * R);
     dfree(c, &c->d_M2, J * R);
-    dfree(c, &c->d_P, N * R);
+    dfree(c, &c->d_P, (size_t)c->X.p_rows * R);
     dfree(c, &c->X.csc_row, nnz);
     dfree(c, &c->X.csc_val, nnz);
-    dfree(c, &c->X.seg_start, (size_t)c->X.nseg + 1);
-    dfree(c, &c->X.col_seg, J + 1);
+    dfree(c, &c->X.seg_start, (size_t)c->X.nseg);
+    dfree(c, &c->X.seg_end, (size_t)c->X.nseg);
+    dfree(c, &c->X.col_seg, (size_t)c->X.nblk * J + 1);
     dfree(c, &c->d_segpart, (size_t)c->X.nseg * R);
     dfree(c, &c->d_W, K * R);
     dfree(c, &c->d_M3, K * R);
@@ -132,6 +133,7 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
         P2_CUDA_TRY(cudaMemsetAsync(c->d_Vh, 0, sizeof(bf16_t) * nv, c->stream));
         P2_CUDA_TRY(cudaMemsetAsync(c->d_Vprevh, 0, sizeof(bf16_t) * nv, c->stream));
         P2_TRY(dalloc(c, &c->d_Ph, (size_t)N * R));
+        c->X.p_rows = N;
     } else {
         const size_t nv = (size_t)J * v_stride<float>(R);     // padded rows, zero padding
         P2_TRY(dalloc(c, &c->d_V, nv));
@@ -139,6 +141,7 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
         P2_CUDA_TRY(cudaMemsetAsync(c->d_V, 0, sizeof(float) * nv, c->stream));
         P2_CUDA_TRY(cudaMemsetAsync(c->d_Vprev, 0, sizeof(float) * nv, c->stream));
         P2_TRY(dalloc(c, &c->d_P, (size_t)N * R));
+        c->X.p_rows = N;
     }
     P2_TRY(dalloc(c, &c->d_T, (size_t)K * R * R));
     P2_TRY(dalloc(c, &c->d_Vun, (size_t)J * R));
@@ -378,7 +381,7 @@ const char *p2_tuning_note(p2_ctx *c) {
 int p2_set_tuning(p2_ctx *c, const p2_tuning *t) {
     if (!c || !t) return fail(P2_EINVAL, "p2_set_tuning: NULL argument");
     if ((t->procrustes_split != 0 && t->procrustes_split != 1) || t->subject_bins < -1 ||
-        t->subject_bins > 1 || t->split_record_cap < 0)
+        t->subject_bins > 1 || t->split_record_cap < 0 || t->m2_block_kib < 0)
         return fail(P2_EINVAL, "p2_set_tuning: bad value");
     c->tune = *t;
     if (c->graph) {                 // the captured iteration holds the old launches

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "../../include/p2.h"
 #include "p2_dw.cuh"
@@ -87,9 +88,20 @@ struct DevX {
     uint32_t *csc_row = nullptr;   // [nnz] stacked row id of each non-zero, column-major
     float *csc_val = nullptr;      // [nnz]
     int64_t nseg = 0;              // column segments of at most P2_SEG non-zeros
-    int64_t *seg_start = nullptr;  // [nseg+1] offsets into csc_*
-    int64_t *col_seg = nullptr;    // [J+1] first segment of each (relabelled) column
+    int64_t *seg_start = nullptr;  // [nseg] first non-zero of each segment (offsets into csc_*)
+    int64_t *seg_end = nullptr;    // [nseg] one past its last
+    // The mode-2 pass runs over row blocks (whole subjects, P rows of one block
+    // sized to stay in L2): a column's non-zeros, sorted by row, fall into one
+    // run per block, cut into segments; segments are numbered block by block.
+    int64_t *col_seg = nullptr;    // [nblk J + 1] first segment of (block b, column j) at b J + j
+    int32_t nblk = 1;
+    int64_t p_rows = 0;            // rows of the P buffer: the largest block
+    std::vector<int64_t> blk_subj; // host [nblk+1]: first subject of each block
+    std::vector<int64_t> blk_row;  // host [nblk+1]: first stacked row of each block
+    std::vector<int64_t> blk_seg;  // host [nblk+1]: first segment of each block
 };
+// bytes of P rows one row block may hold (the blocks' P rows stay in L2)
+#define P2_M2_BLOCK_BYTES (40ll << 20)
 
 #define P2_SEG 1024
 
@@ -179,7 +191,7 @@ struct p2_ctx {
     int64_t split_chunk = 0, split_cap = 0;
     int32_t *d_split_list = nullptr;
     int32_t *d_split_cnt = nullptr;
-    p2_tuning tune{1, -1, 0};   // launch choices (p2_set_tuning, the autotuner)
+    p2_tuning tune{1, -1, 0, 0};   // launch choices (p2_set_tuning, the autotuner)
     bool tuned = false;         // the autotuner has run (or read the cache)
     std::string tune_cache;     // opt.tune_cache, copied
     std::string tune_note;      // how the choices were made (p2_tuning_note)

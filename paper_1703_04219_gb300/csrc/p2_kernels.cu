@@ -502,12 +502,14 @@ template <int CB, class S>
 __global__ void __launch_bounds__(256) k_m2_segments(const uint32_t *__restrict__ csc_row,
                                                      const float *__restrict__ csc_val,
                                                      const int64_t *__restrict__ seg_start,
-                                                     int64_t nseg, const S *__restrict__ Pin,
+                                                     const int64_t *__restrict__ seg_end,
+                                                     int64_t sg0, int64_t sg1,
+                                                     const S *__restrict__ Pin, int64_t row0,
                                                      double *segpart, int R) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t sg = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; sg < nseg; sg += nwarps) {
-        const int64_t a = seg_start[sg], b = seg_start[sg + 1];
+    for (int64_t sg = sg0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; sg < sg1; sg += nwarps) {
+        const int64_t a = seg_start[sg], b = seg_end[sg];
         for (int cb = 0; cb < R; cb += CB) {
             float hi[CB], cp[CB];
 #pragma unroll
@@ -518,7 +520,7 @@ __global__ void __launch_bounds__(256) k_m2_segments(const uint32_t *__restrict_
             for (int64_t e = a + lane; e < b; e += 32) {
                 const uint32_t row = csc_row[e];
                 const float x = csc_val[e];
-                const S *pr = Pin + (size_t)row * R + cb;
+                const S *pr = Pin + (size_t)((int64_t)row - row0) * R + cb;   // the block's P rows
 #pragma unroll
                 for (int c = 0; c < CB; ++c) {
                     if (cb + c < R) {
@@ -542,17 +544,21 @@ __global__ void __launch_bounds__(256) k_m2_segments(const uint32_t *__restrict_
     }
 }
 
-// M2(j, :) = sum of column j's segment partials (FP64): one warp per column,
-// lanes take segments in a fixed stride, combined by a fixed xor-butterfly.
+// M2(j, :) = sum of column j's segment partials (FP64), blocks in order: one
+// warp per column, lanes take each block's segments in a fixed stride,
+// combined by a fixed xor-butterfly.
 __global__ void k_m2_columns(const double *__restrict__ segpart, const int64_t *__restrict__ col_seg,
-                             double *M2, int32_t J, int R) {
+                             double *M2, int32_t J, int nblk, int R) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; j < J; j += nwarps) {
-        const int64_t s0 = col_seg[j], s1 = col_seg[j + 1];
         for (int c = 0; c < R; ++c) {
             double acc = 0.0;
-            for (int64_t sg = s0 + lane; sg < s1; sg += 32) acc += segpart[(size_t)sg * R + c];
+            for (int bk = 0; bk < nblk; ++bk) {
+                const int64_t v = (int64_t)bk * J + j;
+                for (int64_t sg = col_seg[v] + lane; sg < col_seg[v + 1]; sg += 32)
+                    acc += segpart[(size_t)sg * R + c];
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULLMASK, acc, o);
             if (lane == 0) M2[(size_t)j * R + c] = acc;
@@ -928,6 +934,7 @@ __global__ void __launch_bounds__(256) k_eig_z(XView X, const double *__restrict
 __global__ void __launch_bounds__(256) k_eig_m2_segments(const uint32_t *__restrict__ csc_row,
                                                          const float *__restrict__ csc_val,
                                                          const int64_t *__restrict__ seg_start,
+                                                         const int64_t *__restrict__ seg_end,
                                                          int64_t nseg, const double *__restrict__ Z,
                                                          int CW, double *segpart) {
     const int64_t n = nseg * CW, stride = (int64_t)gridDim.x * blockDim.x;
@@ -935,23 +942,27 @@ __global__ void __launch_bounds__(256) k_eig_m2_segments(const uint32_t *__restr
         const int64_t sg = t / CW;
         const int c = (int)(t - sg * CW);
         double v = 0.0;
-        for (int64_t e = seg_start[sg]; e < seg_start[sg + 1]; ++e)
+        for (int64_t e = seg_start[sg]; e < seg_end[sg]; ++e)
             v = fma((double)csc_val[e], Z[(size_t)csc_row[e] * CW + c], v);
         segpart[t] = v;
     }
 }
 
 // Y(j, c0 + c) = sum of column j's segment partials in order (rows CW wide),
-// Y J x b: one thread per (column, component).
+// blocks in order: Y J x b, one thread per (column, component).
 __global__ void k_eig_m2_columns(const double *__restrict__ segpart,
-                                 const int64_t *__restrict__ col_seg, int32_t J, int CW,
+                                 const int64_t *__restrict__ col_seg, int32_t J, int nblk, int CW,
                                  double *Y, int b, int c0) {
     const int64_t n = (int64_t)J * CW, stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
         const int64_t j = t / CW;
         const int c = (int)(t - j * CW);
         double acc = 0.0;
-        for (int64_t sg = col_seg[j]; sg < col_seg[j + 1]; ++sg) acc += segpart[(size_t)sg * CW + c];
+        for (int bk = 0; bk < nblk; ++bk) {
+            const int64_t v = (int64_t)bk * J + j;
+            for (int64_t sg = col_seg[v]; sg < col_seg[v + 1]; ++sg)
+                acc += segpart[(size_t)sg * CW + c];
+        }
         Y[(size_t)j * b + c0 + c] = acc;
     }
 }
@@ -1650,26 +1661,42 @@ static void launch_alpha(p2_ctx *c, const Launch &L) {
         launch_alpha_t<MODE3, float>(c, L, MODE3 ? c->d_Vprev : nullptr);
 }
 
+// Mode-2 rows of row block b (its subjects, P rows relative to the block's
+// first row, into the P buffer that holds one block); one block: the whole
+// collection, in the subject order of xview.
 template <int CB, class S, int RT>
-static void launch_beta_k(p2_ctx *c, const Launch &L) {
+static void launch_beta_k(p2_ctx *c, const Launch &L, int b) {
     const int nt = L.beta_warps * 32;
-    dim3 grid(c->geo.nsm * resident_blocks(c, k_beta_p<CB, S, S, RT>, nt, L.beta_smem));
+    XView X = xview(c);
+    int64_t row0 = 0, k0 = 0;
+    if (c->X.nblk > 1) {
+        k0 = c->X.blk_subj[b];
+        X.subj_row += k0;
+        X.subj_nnz += k0;
+        X.K = c->X.blk_subj[b + 1] - k0;
+        X.order = nullptr;
+        row0 = c->X.blk_row[b];
+    }
+    const int64_t want = (X.K + L.beta_warps - 1) / L.beta_warps;
+    const int64_t full = (int64_t)c->geo.nsm * resident_blocks(c, k_beta_p<CB, S, S, RT>, nt, L.beta_smem);
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min(want, full)));
     k_beta_p<CB, S, S, RT><<<grid, dim3(nt), L.beta_smem, c->stream>>>(
-        xview(c), Bufs<S>::V(c), c->d_H, c->d_T, c->d_W, Bufs<S>::P(c), c->R, 0);
+        X, Bufs<S>::V(c), c->d_H, c->d_T + (size_t)k0 * c->R * c->R, c->d_W + (size_t)k0 * c->R,
+        Bufs<S>::P(c), c->R, row0);
 }
 
 template <class S, int... Rs>
-static void launch_beta_ranks(p2_ctx *c, const Launch &L, std::integer_sequence<int, Rs...>) {
+static void launch_beta_ranks(p2_ctx *c, const Launch &L, int b, std::integer_sequence<int, Rs...>) {
     bool done = false;
-    ((c->R == Rs && !done ? (launch_beta_k<RankBlock<Rs>::cb, S, Rs>(c, L), done = true)
+    ((c->R == Rs && !done ? (launch_beta_k<RankBlock<Rs>::cb, S, Rs>(c, L, b), done = true)
                               : false),
      ...);
-    if (!done) launch_beta_k<32, S, 0>(c, L);
+    if (!done) launch_beta_k<32, S, 0>(c, L, b);
 }
 
 template <class S>
-static void launch_beta_p_t(p2_ctx *c, const Launch &L) {
-    launch_beta_ranks<S>(c, L, RankList{});
+static void launch_beta_p_t(p2_ctx *c, const Launch &L, int b) {
+    launch_beta_ranks<S>(c, L, b, RankList{});
 }
 
 // mode-1 statistics (k_subject_stats_gf) compiled for the rank when it is in RankList
@@ -1688,11 +1715,11 @@ static void launch_stats_ranks(p2_ctx *c, int nb, int nt, size_t ssm, int with_f
                                                           c->d_part, c->X.K, c->R, with_fit);
 }
 
-static void launch_beta_p(p2_ctx *c, const Launch &L) {
+static void launch_beta_p(p2_ctx *c, const Launch &L, int b) {
     if (c->bf16)
-        launch_beta_p_t<bf16_t>(c, L);
+        launch_beta_p_t<bf16_t>(c, L, b);
     else
-        launch_beta_p_t<float>(c, L);
+        launch_beta_p_t<float>(c, L, b);
 }
 
 // U rows of subjects k0 .. k1-1 (rows r0 .. of the stacked order) into the
@@ -1738,32 +1765,53 @@ cudaError_t launch_get_u(p2_ctx *c, int64_t k0, int64_t k1, int64_t r0, float *U
     return cudaGetLastError();
 }
 
+// Mode-2 segment partials of row block b (segments blk_seg[b] .. blk_seg[b+1]).
 template <class S>
-static void launch_m2_segments_t(p2_ctx *c) {
-    const int64_t want = (c->X.nseg + 7) / 8;
+static void launch_m2_segments_t(p2_ctx *c, int b) {
+    const int64_t sg0 = c->X.blk_seg[b], sg1 = c->X.blk_seg[b + 1];
+    if (sg1 <= sg0) return;
+    const int64_t want = (sg1 - sg0 + 7) / 8;
     const int sb = (int)(want < 64 * (int64_t)c->geo.nsm ? want : 64 * (int64_t)c->geo.nsm);
     const S *P = Bufs<S>::P(c);
+    const int64_t row0 = c->X.nblk > 1 ? c->X.blk_row[b] : 0;
     switch (comp_block(c->R)) {
         case 8:
             k_m2_segments<8, S><<<sb, 256, 0, c->stream>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
-                                                           c->X.nseg, P, c->d_segpart, c->R);
+                                                           c->X.seg_end, sg0, sg1, P, row0,
+                                                           c->d_segpart, c->R);
             break;
         case 16:
             k_m2_segments<16, S><<<sb, 256, 0, c->stream>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
-                                                            c->X.nseg, P, c->d_segpart, c->R);
+                                                            c->X.seg_end, sg0, sg1, P, row0,
+                                                            c->d_segpart, c->R);
             break;
         default:
             k_m2_segments<32, S><<<sb, 256, 0, c->stream>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
-                                                            c->X.nseg, P, c->d_segpart, c->R);
+                                                            c->X.seg_end, sg0, sg1, P, row0,
+                                                            c->d_segpart, c->R);
             break;
     }
 }
 
-static void launch_m2_segments(p2_ctx *c) {
+static void launch_m2_segments(p2_ctx *c, int b) {
     if (c->bf16)
-        launch_m2_segments_t<bf16_t>(c);
+        launch_m2_segments_t<bf16_t>(c, b);
     else
-        launch_m2_segments_t<float>(c);
+        launch_m2_segments_t<float>(c, b);
+}
+
+// The mode-2 pass's kernels, row block by row block: each block's P rows are
+// written and then read back while they are in L2.
+static int enqueue_mode2_blocks(p2_ctx *c, const Launch &L) {
+    for (int b = 0; b < c->X.nblk; ++b) {
+        launch_beta_p(c, L, b);
+        P2_LAUNCH_CHECK("k_beta_p");
+        if (c->X.blk_seg[b + 1] > c->X.blk_seg[b]) {
+            launch_m2_segments(c, b);
+            P2_LAUNCH_CHECK("k_m2_segments");
+        }
+    }
+    return P2_OK;
 }
 
 // Q-step for the current (H, V, W) (Algorithm 2's SVD loop), then the
@@ -1878,13 +1926,7 @@ int tune_time_qstep(p2_ctx *c, int reps, float *ms) {
 int tune_time_mode2(p2_ctx *c, int reps, float *ms) {
     return tune_time(c, reps, ms, [c]() -> int {
         const Launch L = plan(c);
-        launch_beta_p(c, L);
-        P2_LAUNCH_CHECK("k_beta_p");
-        if (c->X.nseg > 0) {
-            launch_m2_segments(c);
-            P2_LAUNCH_CHECK("k_m2_segments");
-        }
-        return P2_OK;
+        return enqueue_mode2_blocks(c, L);
     });
 }
 
@@ -1903,16 +1945,15 @@ int enqueue_iteration(p2_ctx *c) {
     P2_LAUNCH_CHECK("k_solve_h");
     // pass beta: mode-2 MTTKRP
     mark(c, 1);
-    launch_beta_p(c, L);
-    P2_LAUNCH_CHECK("k_beta_p");
-    if (c->X.nseg > 0) {
-        launch_m2_segments(c);
-        P2_LAUNCH_CHECK("k_m2_segments");
+    {
+        const int rc = enqueue_mode2_blocks(c, L);
+        if (rc != P2_OK) return rc;
     }
     const int64_t nJR = J * R;
     const int fb = (int)((nJR + 255) / 256 < 4 * nsm ? (nJR + 255) / 256 : 4 * nsm);
     const int cb_blocks = (int)((J + 7) / 8 < 8 * nsm ? (J + 7) / 8 : 8 * nsm);
-    k_m2_columns<<<cb_blocks, 256, 0, s>>>(c->d_segpart, c->X.col_seg, c->d_M2, (int32_t)J, R);
+    k_m2_columns<<<cb_blocks, 256, 0, s>>>(c->d_segpart, c->X.col_seg, c->d_M2, (int32_t)J,
+                                           c->X.nblk, R);
     P2_LAUNCH_CHECK("k_m2_columns");
     {                                           // sharded: M2 summed over the shards
         const int xrc = exchange(c, c->d_M2, nJR);
@@ -1992,10 +2033,10 @@ int enqueue_eig_product(p2_ctx *c, const double *Vd, int b, int CW, double *Z, d
         P2_LAUNCH_CHECK("k_eig_z");
         if (c->X.nseg > 0) {
             k_eig_m2_segments<<<sb, 256, 0, c->stream>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
-                                                         c->X.nseg, Z, w, seg);
+                                                         c->X.seg_end, c->X.nseg, Z, w, seg);
             P2_LAUNCH_CHECK("k_eig_m2_segments");
         }
-        k_eig_m2_columns<<<cb, 256, 0, c->stream>>>(seg, c->X.col_seg, J, w, Y, b, c0);
+        k_eig_m2_columns<<<cb, 256, 0, c->stream>>>(seg, c->X.col_seg, J, c->X.nblk, w, Y, b, c0);
         P2_LAUNCH_CHECK("k_eig_m2_columns");
     }
     return P2_OK;

@@ -10,6 +10,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "p2_internal.cuh"
@@ -168,71 +169,193 @@ __global__ void k_chunk_place(const uint16_t *__restrict__ col, const float *__r
     }
 }
 
+// First position of each block's run in each column (the column's non-zeros
+// are sorted by stacked row): vstart[j (nblk + 1) + b], b = 0 .. nblk.
+__global__ void k_block_runs(const uint32_t *__restrict__ csc_row,
+                             const int64_t *__restrict__ colptr,
+                             const int64_t *__restrict__ blk_row, int nblk, int32_t J,
+                             int64_t *vstart) {
+    const int64_t n = (int64_t)J * (nblk + 1);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / (nblk + 1);
+        const int b = (int)(t - j * (nblk + 1));
+        int64_t lo = colptr[j], hi = colptr[j + 1];
+        if (b == 0) {
+            vstart[t] = lo;
+        } else if (b == nblk) {
+            vstart[t] = hi;
+        } else {
+            const uint64_t key = (uint64_t)blk_row[b];
+            while (lo < hi) {                      // first row >= the block's first row
+                const int64_t mid = lo + (hi - lo) / 2;
+                if ((uint64_t)csc_row[mid] < key) lo = mid + 1;
+                else hi = mid;
+            }
+            vstart[t] = lo;
+        }
+    }
+}
+
+// Row blocks of the mode-2 pass: whole subjects, at most `budget` stacked
+// rows each (a subject longer than the budget is a block of its own).
+static void plan_blocks(const std::vector<int64_t> &subj_row, int64_t budget,
+                        std::vector<int64_t> &blk_subj, std::vector<int64_t> &blk_row) {
+    const int64_t K = (int64_t)subj_row.size() - 1;
+    blk_subj.assign(1, 0);
+    blk_row.assign(1, 0);
+    int64_t k = 0;
+    while (k < K) {
+        int64_t e = k + 1;
+        while (e < K && subj_row[e + 1] - subj_row[k] <= budget) ++e;
+        blk_subj.push_back(e);
+        blk_row.push_back(subj_row[e]);
+        k = e;
+    }
+    if (K == 0) {
+        blk_subj.push_back(0);
+        blk_row.push_back(subj_row.empty() ? 0 : subj_row[0]);
+    }
+}
+
 static int build_csc(p2_ctx *c, const int64_t *d_row_ptr, const int32_t *h_count_new,
                      int64_t N, int64_t nnz, int32_t J) {
     cudaStream_t s = c->stream;
     const int nsm = c->geo.nsm;
-    // column pointers and segments (host; J <= 65535)
-    std::vector<int64_t> colptr((size_t)J + 1, 0), colseg((size_t)J + 1, 0);
-    std::vector<int64_t> segs;
+    const int64_t K = c->X.K;
+    // column pointers (host; J <= 65535)
+    std::vector<int64_t> colptr((size_t)J + 1, 0);
     for (int32_t j = 0; j < J; ++j) colptr[j + 1] = colptr[j] + h_count_new[j];
-    for (int32_t j = 0; j < J; ++j) {
-        colseg[j] = (int64_t)segs.size();
-        for (int64_t a = colptr[j]; a < colptr[j + 1]; a += P2_SEG) segs.push_back(a);
+    // row blocks from the subjects' row offsets
+    {
+        std::vector<int64_t> sr((size_t)K + 1);
+        P2_CUDA_TRY(cudaMemcpyAsync(sr.data(), c->X.subj_row, sizeof(int64_t) * ((size_t)K + 1),
+                                    cudaMemcpyDeviceToHost, s));
+        P2_CUDA_TRY(cudaStreamSynchronize(s));
+        const int64_t elem = c->bf16 ? 2 : 4;
+        const int64_t bytes = c->tune.m2_block_kib > 0 ? (int64_t)c->tune.m2_block_kib << 10
+                                                        : P2_M2_BLOCK_BYTES;
+        int64_t budget = bytes / (elem * c->R);
+        if (budget < 1) budget = 1;
+        plan_blocks(sr, budget, c->X.blk_subj, c->X.blk_row);
+        c->X.nblk = (int32_t)c->X.blk_subj.size() - 1;
+        int64_t rows = 0;
+        for (int b = 0; b < c->X.nblk; ++b)
+            rows = std::max<int64_t>(rows, c->X.blk_row[b + 1] - c->X.blk_row[b]);
+        // the P buffer holds one block
+        if (rows < c->X.p_rows) {
+            void **pp = c->bf16 ? (void **)&c->d_Ph : (void **)&c->d_P;
+            cudaFree(*pp);
+            *pp = nullptr;
+            c->dev_bytes -= (size_t)c->X.p_rows * c->R * elem;
+            const cudaError_t e = cudaMalloc(pp, (size_t)(rows > 0 ? rows : 1) * c->R * elem);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                c->X.p_rows = 0;
+                set_error("load: allocation of the mode-2 rows failed: %s", cudaGetErrorString(e));
+                return e == cudaErrorMemoryAllocation ? P2_ENOMEM : P2_ECUDA;
+            }
+            c->X.p_rows = rows;
+            c->dev_bytes += (size_t)rows * c->R * elem;
+        }
     }
-    colseg[J] = (int64_t)segs.size();
-    segs.push_back(nnz);
-    const int64_t nseg = (int64_t)segs.size() - 1;
-    c->X.nseg = nseg;
-    cudaError_t e = cudaMalloc(&c->X.seg_start, sizeof(int64_t) * segs.size());
-    if (e == cudaSuccess) e = cudaMalloc(&c->X.col_seg, sizeof(int64_t) * ((size_t)J + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&c->X.csc_row, sizeof(uint32_t) * (nnz > 0 ? nnz : 1));
+    const int nblk = c->X.nblk;
+    cudaError_t e = cudaMalloc(&c->X.csc_row, sizeof(uint32_t) * (nnz > 0 ? nnz : 1));
     if (e == cudaSuccess) e = cudaMalloc(&c->X.csc_val, sizeof(float) * (nnz > 0 ? nnz : 1));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_segpart, sizeof(double) * (size_t)(nseg > 0 ? nseg : 1) * c->R);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("load: allocation of the column-major copy failed: %s", cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? P2_ENOMEM : P2_ECUDA;
     }
-    c->dev_bytes += sizeof(int64_t) * (segs.size() + J + 1) + (sizeof(uint32_t) + sizeof(float)) * (size_t)nnz +
-                    sizeof(double) * (size_t)nseg * c->R;
-    P2_CUDA_TRY(cudaMemcpyAsync(c->X.seg_start, segs.data(), sizeof(int64_t) * segs.size(),
-                                cudaMemcpyHostToDevice, s));
-    P2_CUDA_TRY(cudaMemcpyAsync(c->X.col_seg, colseg.data(), sizeof(int64_t) * ((size_t)J + 1),
-                                cudaMemcpyHostToDevice, s));
-    if (nnz == 0) return P2_OK;
-    // chunking keeps the per-chunk count matrix near 256 MB at most
-    int64_t nch = (nnz + 65535) / 65536;
-    const int64_t maxch = (256ll << 20) / (4ll * J);
-    if (nch > maxch) nch = maxch > 0 ? maxch : 1;
-    const int64_t chunk = (nnz + nch - 1) / nch;
-    nch = (nnz + chunk - 1) / chunk;
-    int64_t *d_colptr = nullptr;
-    uint32_t *d_rowid = nullptr;
-    int *d_cnt = nullptr;
-    e = cudaMalloc(&d_colptr, sizeof(int64_t) * ((size_t)J + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&d_rowid, sizeof(uint32_t) * (size_t)nnz);
-    if (e == cudaSuccess) e = cudaMalloc(&d_cnt, sizeof(int) * (size_t)nch * J);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_colptr, colptr.data(), sizeof(int64_t) * ((size_t)J + 1),
-                                              cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(int) * (size_t)nch * J, s);
-    if (e == cudaSuccess) {
-        k_rowid<<<8 * nsm, 256, 0, s>>>(d_row_ptr, N, d_rowid);
-        k_chunk_hist<<<(int)nch, 256, 0, s>>>(c->X.col, nnz, chunk, J, d_cnt);
-        k_col_scan<<<(J + 255) / 256, 256, 0, s>>>(d_colptr, (int)nch, J, d_cnt);
-        k_chunk_place<<<(int)nch, 32, 0, s>>>(c->X.col, c->X.val, d_rowid, nnz, chunk, J, d_cnt,
-                                              c->X.csc_row, c->X.csc_val);
-        e = cudaGetLastError();
+    c->dev_bytes += (sizeof(uint32_t) + sizeof(float)) * (size_t)nnz;
+    std::vector<int64_t> vstart((size_t)J * (nblk + 1), 0);
+    if (nnz > 0) {
+        // chunking keeps the per-chunk count matrix near 256 MB at most
+        int64_t nch = (nnz + 65535) / 65536;
+        const int64_t maxch = (256ll << 20) / (4ll * J);
+        if (nch > maxch) nch = maxch > 0 ? maxch : 1;
+        const int64_t chunk = (nnz + nch - 1) / nch;
+        nch = (nnz + chunk - 1) / chunk;
+        int64_t *d_colptr = nullptr, *d_blkrow = nullptr, *d_vstart = nullptr;
+        uint32_t *d_rowid = nullptr;
+        int *d_cnt = nullptr;
+        e = cudaMalloc(&d_colptr, sizeof(int64_t) * ((size_t)J + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&d_rowid, sizeof(uint32_t) * (size_t)nnz);
+        if (e == cudaSuccess) e = cudaMalloc(&d_cnt, sizeof(int) * (size_t)nch * J);
+        if (e == cudaSuccess) e = cudaMalloc(&d_blkrow, sizeof(int64_t) * ((size_t)nblk + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&d_vstart, sizeof(int64_t) * vstart.size());
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_colptr, colptr.data(), sizeof(int64_t) * ((size_t)J + 1),
+                                                  cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_blkrow, c->X.blk_row.data(),
+                                                  sizeof(int64_t) * ((size_t)nblk + 1),
+                                                  cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(int) * (size_t)nch * J, s);
+        if (e == cudaSuccess) {
+            k_rowid<<<8 * nsm, 256, 0, s>>>(d_row_ptr, N, d_rowid);
+            k_chunk_hist<<<(int)nch, 256, 0, s>>>(c->X.col, nnz, chunk, J, d_cnt);
+            k_col_scan<<<(J + 255) / 256, 256, 0, s>>>(d_colptr, (int)nch, J, d_cnt);
+            k_chunk_place<<<(int)nch, 32, 0, s>>>(c->X.col, c->X.val, d_rowid, nnz, chunk, J, d_cnt,
+                                                  c->X.csc_row, c->X.csc_val);
+            const int64_t nv = (int64_t)vstart.size();
+            k_block_runs<<<(int)std::min<int64_t>((nv + 255) / 256, 8 * nsm), 256, 0, s>>>(
+                c->X.csc_row, d_colptr, d_blkrow, nblk, J, d_vstart);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(vstart.data(), d_vstart, sizeof(int64_t) * vstart.size(),
+                                cudaMemcpyDeviceToHost, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaFree(d_colptr);
+        cudaFree(d_rowid);
+        cudaFree(d_cnt);
+        cudaFree(d_blkrow);
+        cudaFree(d_vstart);
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess) {
+            set_error("load: building the column-major copy failed: %s", cudaGetErrorString(e));
+            return P2_ECUDA;
+        }
     }
-    cudaError_t e2 = cudaStreamSynchronize(s);
-    cudaFree(d_colptr);
-    cudaFree(d_rowid);
-    cudaFree(d_cnt);
-    if (e == cudaSuccess) e = e2;
+    // segments block by block, column by column within a block: each
+    // (block, column) run cut into pieces of at most P2_SEG non-zeros
+    std::vector<int64_t> s_lo, s_hi, vseg((size_t)nblk * J + 1, 0);
+    c->X.blk_seg.assign((size_t)nblk + 1, 0);
+    for (int b = 0; b < nblk; ++b) {
+        c->X.blk_seg[b] = (int64_t)s_lo.size();
+        for (int32_t j = 0; j < J; ++j) {
+            vseg[(size_t)b * J + j] = (int64_t)s_lo.size();
+            const int64_t lo = vstart[(size_t)j * (nblk + 1) + b];
+            const int64_t hi = vstart[(size_t)j * (nblk + 1) + b + 1];
+            for (int64_t a0 = lo; a0 < hi; a0 += P2_SEG) {
+                s_lo.push_back(a0);
+                s_hi.push_back(std::min<int64_t>(a0 + P2_SEG, hi));
+            }
+        }
+    }
+    c->X.blk_seg[nblk] = (int64_t)s_lo.size();
+    vseg[(size_t)nblk * J] = (int64_t)s_lo.size();
+    const int64_t nseg = (int64_t)s_lo.size();
+    c->X.nseg = nseg;
+    e = cudaMalloc(&c->X.seg_start, sizeof(int64_t) * (size_t)(nseg > 0 ? nseg : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&c->X.seg_end, sizeof(int64_t) * (size_t)(nseg > 0 ? nseg : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&c->X.col_seg, sizeof(int64_t) * vseg.size());
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_segpart, sizeof(double) * (size_t)(nseg > 0 ? nseg : 1) * c->R);
     if (e != cudaSuccess) {
-        set_error("load: building the column-major copy failed: %s", cudaGetErrorString(e));
-        return P2_ECUDA;
+        cudaGetLastError();
+        set_error("load: allocation of the mode-2 segments failed: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? P2_ENOMEM : P2_ECUDA;
     }
+    c->dev_bytes += sizeof(int64_t) * (2 * (size_t)nseg + vseg.size()) +
+                    sizeof(double) * (size_t)nseg * c->R;
+    if (nseg > 0) {
+        P2_CUDA_TRY(cudaMemcpyAsync(c->X.seg_start, s_lo.data(), sizeof(int64_t) * (size_t)nseg,
+                                    cudaMemcpyHostToDevice, s));
+        P2_CUDA_TRY(cudaMemcpyAsync(c->X.seg_end, s_hi.data(), sizeof(int64_t) * (size_t)nseg,
+                                    cudaMemcpyHostToDevice, s));
+    }
+    P2_CUDA_TRY(cudaMemcpyAsync(c->X.col_seg, vseg.data(), sizeof(int64_t) * vseg.size(),
+                                cudaMemcpyHostToDevice, s));
+    P2_CUDA_TRY(cudaStreamSynchronize(s));
     return P2_OK;
 }
 

@@ -193,6 +193,27 @@ def split_case(R, K):
     return {"bitwise": float(same)}
 
 
+def blocks_case(R, K):
+    """The mode-2 pass over many row blocks (a tiny block size) against one
+    block: M2, V and the fit equal to round-off (the partial sums are added
+    in another order), and both against the oracle."""
+    X = synth.generate("tiny", K=K)
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=19)
+    outs = []
+    for kib in (0, 1):
+        with p2.Parafac2(R, use_graph=False) as m:
+            m.set_tuning(m2_block_kib=kib)
+            m.load(X)
+            m.init(H0, V0, W0)
+            fit = m.iterate(1)
+            outs.append((fit, m.mttkrp(2), m.factors()[1]))
+    ref = P.als_iteration(P.all_blocks(X), H0.astype(np.float64), V0.astype(np.float64),
+                          W0.astype(np.float64))
+    return {"M2_blocks": rel_fro(outs[1][1], outs[0][1]), "V_blocks": rel_fro(outs[1][2], outs[0][2]),
+            "M2": rel_fro(outs[1][1], ref["M2"]), "V": rel_fro(outs[1][2], ref["V"]),
+            "fit": abs(outs[1][0] - outs[0][0])}
+
+
 def shard_case(R, K):
     """A context whose exchange hook doubles every buffer (the sum over two
     shards that hold the same subjects) against an unsharded context on the
@@ -241,6 +262,8 @@ if __name__ == "__main__":
         out = seed_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "rational":
         out = rational_case(int(sys.argv[2]), int(sys.argv[3]))
+    elif kind == "blocks":
+        out = blocks_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "split":
         out = split_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "shard":

@@ -39,6 +39,7 @@ CASES = {
     "shard_r6": ["shard", "6", "20"],
     "split_r13": ["split", "13", "12"],
     "split_r40": ["split", "40", "8"],
+    "blocks_r6": ["blocks", "6", "40"],
 }
 
 
@@ -163,3 +164,12 @@ def test_emulated_split_procrustes_equals_fused(emulated_runs, name):
     rotation-applying kernel) and its fused fallback give the fused kernel's
     results bit for bit, within bounds."""
     assert _result(emulated_runs, name)["bitwise"] == 1.0
+
+
+def test_emulated_mode2_row_blocks_are_in_bounds_and_match(emulated_runs):
+    """The mode-2 pass over many row blocks (1 KiB of P rows each) against a
+    single block and the oracle."""
+    out = _result(emulated_runs, "blocks_r6")
+    assert out["M2_blocks"] < 1e-12 and out["V_blocks"] < 1e-6, out
+    assert out["M2"] < 1e-5 and out["V"] < 1e-5, out
+    assert out["fit"] < 1e-9

@@ -97,8 +97,9 @@ typedef struct {
                                   (0 = all the scratch holds, 2 R^2 + 2 R); a subject that needs
                                   more is finished by the fused kernel */
     int32_t m2_block_kib;      /* mode-2 pass: row blocks whose P rows take at most this many
-                                  KiB, so that they are read back from L2 (0 = 40 MiB); takes
-                                  effect at the next p2_load_slices */
+                                  KiB, so that they are read back from L2 (0 = one block, the
+                                  whole collection: the default, measured fastest at 63M-555M
+                                  non-zeros); takes effect at the next p2_load_slices */
 } p2_tuning;
 
 int p2_get_tuning(p2_ctx *ctx, p2_tuning *out);

@@ -100,8 +100,6 @@ struct DevX {
     std::vector<int64_t> blk_row;  // host [nblk+1]: first stacked row of each block
     std::vector<int64_t> blk_seg;  // host [nblk+1]: first segment of each block
 };
-// bytes of P rows one row block may hold (the blocks' P rows stay in L2)
-#define P2_M2_BLOCK_BYTES (40ll << 20)
 
 #define P2_SEG 1024
 

@@ -233,9 +233,12 @@ static int build_csc(p2_ctx *c, const int64_t *d_row_ptr, const int32_t *h_count
                                     cudaMemcpyDeviceToHost, s));
         P2_CUDA_TRY(cudaStreamSynchronize(s));
         const int64_t elem = c->bf16 ? 2 : 4;
-        const int64_t bytes = c->tune.m2_block_kib > 0 ? (int64_t)c->tune.m2_block_kib << 10
-                                                        : P2_M2_BLOCK_BYTES;
-        int64_t budget = bytes / (elem * c->R);
+        // m2_block_kib = 0: one block, the whole collection (measured fastest:
+        // every extra block adds a pair of launches and their tails, which
+        // cost more than the L2 hits on the P rows save)
+        int64_t budget = c->tune.m2_block_kib > 0
+                             ? ((int64_t)c->tune.m2_block_kib << 10) / (elem * c->R)
+                             : (int64_t)N;
         if (budget < 1) budget = 1;
         plan_blocks(sr, budget, c->X.blk_subj, c->X.blk_row);
         c->X.nblk = (int32_t)c->X.blk_subj.size() - 1;

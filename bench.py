@@ -331,8 +331,16 @@ def roofline(X, R, phase_ms, flops, wname):
     return roof, sparse
 
 
+def tc_m_on(R, fp64_procrustes, tensor_core_m):
+    """Whether the library forms the Procrustes step's M on the tensor cores
+    (opt-in, 13 <= R <= 48)."""
+    if fp64_procrustes or not 13 <= R <= 48:
+        return False
+    return bool(tensor_core_m)
+
+
 def measure_workload(X, w, precision, steps, warmup, device, gpu_id, fp64_procrustes=False,
-                     nonneg=False, tuning=None):
+                     nonneg=False, tuning=None, tensor_core_m=None):
     """One workload timed like the headline (graph replays, CUDA events on the
     library's stream, phase events, clocks sampled in the timed region)."""
     import torch
@@ -341,7 +349,8 @@ def measure_workload(X, w, precision, steps, warmup, device, gpu_id, fp64_procru
     H0, V0, W0 = synth_init(w, X)
     stream = torch.cuda.Stream()
     m = p2.Parafac2(R, device=device, stream=stream.cuda_stream, timing=True,
-                    precision=precision, fp64_procrustes=fp64_procrustes, nonneg=nonneg)
+                    precision=precision, fp64_procrustes=fp64_procrustes, nonneg=nonneg,
+                    tensor_core_m=tensor_core_m)
     if tuning:
         m.set_tuning(**tuning)
     m.load(X)
@@ -363,6 +372,7 @@ def measure_workload(X, w, precision, steps, warmup, device, gpu_id, fp64_procru
         roof = fp64_roofline(R, t["phase_ms"], t["flops"])
     return {"workload": _workload_desc(w, X), "precision": precision,
             "procrustes": "fp64" if fp64_procrustes else "double-word", "tuning": tune,
+            "m_on_tensor_cores": tc_m_on(R, fp64_procrustes, tensor_core_m),
             "nonneg": bool(nonneg),
             "storage": "V and P_k bfloat16" if precision == "bf16" else "float",
             "steps": steps, "warmup": warmup, "s_per_iter": ms / 1e3,
@@ -387,26 +397,29 @@ def synth_init(w, X):
 
 def run_r40(args, device, gpu_id):
     """Table 1's R = 40 column: the 250M-non-zero workload in FP32 (split
-    Procrustes step, and the fused kernel for comparison), with bfloat16
+    Procrustes step; for comparison M formed on the tensor cores, and the
+    fused kernel), with bfloat16
     storage and with the FP64 arm of the Procrustes step, the
     555M-non-zero workload in FP32, and the paper's own configuration
     (planted 500M-non-zero workload, non-negative S_k and V)."""
     import synth
     out = {}
     steps = max(1, min(args.steps, 5))
-    for name, precs in (("c250m", ("fp32", "fused", "bf16", "fp64p")), ("c555m", ("fp32",))):
+    for name, precs in (("c250m", ("fp32", "tc", "fused", "bf16", "fp64p")), ("c555m", ("fp32",))):
         w = synth.WORKLOADS[name]
         X = synth.generate(w)
         for prec in precs:
             if prec == "fp64p" and args.no_fp64:
                 continue
             key = {"fp64p": f"{name}_fp64_procrustes",
+                   "tc": f"{name}_fp32_m_on_tensor_cores",
                    "fused": f"{name}_fp32_fused_procrustes"}.get(prec, f"{name}_{prec}")
             out[key] = measure_workload(X, w, prec if prec in ("fp32", "bf16") else "fp32",
                                         min(steps, 3) if prec == "fp64p" else steps,
                                         args.warmup, device, gpu_id,
                                         fp64_procrustes=prec == "fp64p",
-                                        tuning={"procrustes_split": 0} if prec == "fused" else None)
+                                        tuning={"procrustes_split": 0} if prec == "fused" else None,
+                                        tensor_core_m=True if prec == "tc" else None)
         del X
     if not args.no_nonneg:
         # the paper's configuration: planted workload, non-negative S_k and V
@@ -443,7 +456,8 @@ def run_p2(args, w):
     R = w.R
     H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=w.seed)
     stream = torch.cuda.Stream()
-    m = p2.Parafac2(R, device=local, stream=stream.cuda_stream, timing=True)
+    m = p2.Parafac2(R, device=local, stream=stream.cuda_stream, timing=True,
+                    tensor_core_m=args.tensor_core_m)
     m.load(X)
     m.init(H0, V0, W0)
     for _ in range(args.warmup):
@@ -656,7 +670,11 @@ def main(argv=None):
                     help="skip the FP64 arm of the Procrustes step")
     ap.add_argument("--no-r40", action="store_true",
                     help="skip the R = 40 workloads (250M nnz FP32 and bfloat16, 555M nnz)")
+    ap.add_argument("--tensor-core-m", choices=["auto", "on", "off"], default="auto",
+                    help="form the Procrustes step's M on the tensor cores (auto: the "
+                         "library's default, off)")
     args = ap.parse_args(argv)
+    args.tensor_core_m = {"auto": None, "on": True, "off": False}[args.tensor_core_m]
     if args.warmup < 3:
         args.warmup = 3
     import synth

@@ -81,6 +81,17 @@ typedef struct {
                              keyed by rank, precision, variant and the collection's K, J and
                              non-zero count; a matching line is used instead of timing, and a
                              newly timed choice is appended */
+    int32_t tensor_core_m; /* R in 13..48, double-word Procrustes step: the matrix
+                             M = H S_k G_k S_k H^T whose eigen-decomposition gives the polar
+                             factor is formed on the tensor cores (bf16 MMAs made exact by
+                             splitting every entry into seven 8-bit digits, FP32 accumulation
+                             in tensor memory, the digit products recombined in double-word
+                             arithmetic: ~2^-48 normwise, the accuracy of the double-word
+                             product it replaces, not its rounding) instead of on the FP32
+                             pipe.  Measured slower end to end on GB300 (250M nnz, R = 40:
+                             the digit split and recombination cost more FP32-pipe work than
+                             the product saves), so it is opt-in: 1 = on for 13 <= R <= 48;
+                             0 or -1 (default) = off.  Ignored with fp64_procrustes. */
 } p2_options;
 
 /* Launch choices that change the speed, never the results (every choice

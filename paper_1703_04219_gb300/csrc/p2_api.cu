@@ -98,6 +98,7 @@ static void free_data(p2_ctx *c) {
     dfree(c, &c->d_split, c->split_bytes);
     dfree(c, &c->d_split_list, (size_t)c->split_chunk);
     dfree(c, &c->d_split_cnt, 1);
+    dfree(c, &c->d_Mtc, K * P);
     c->split_chunk = c->split_cap = 0;
     c->split_bytes = 0;
     delete[] c->h_perm_new2old;
@@ -198,6 +199,14 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
             }
         }
     }
+    if (K > 0 && tc_m_wanted(c)) {
+        // every subject's M' for the grouped Procrustes kernels; without the
+        // memory they form M' themselves
+        if (dalloc(c, &c->d_Mtc, (size_t)K * P) != P2_OK) {
+            c->d_Mtc = nullptr;
+            set_error("");
+        }
+    }
     return P2_OK;
 }
 
@@ -215,6 +224,10 @@ static int read_flags(p2_ctx *c, int *flags) {
 }
 
 static int flags_status(int flags) {
+    if (flags & FLAG_TC_TIMEOUT) {
+        set_error("a tensor-core MMA did not complete within its wait limit (flags 0x%x)", flags);
+        return P2_ECUDA;
+    }
     if (flags & FLAG_NONFINITE) {
         set_error("numeric problem detected on the device (flags 0x%x: non-finite loss)", flags);
         return P2_ENUMERIC;
@@ -299,6 +312,7 @@ void p2_default_options(p2_options *opt, int32_t R) {
     opt->fp64_procrustes = 0;
     opt->autotune = 0;
     opt->tune_cache = nullptr;
+    opt->tensor_core_m = -1;
 }
 
 int p2_create(p2_ctx **out, const p2_options *opt) {
@@ -620,9 +634,9 @@ int p2_set_factors(p2_ctx *c, const float *H, const float *V, const float *W) {
 // choice computes the same values, so the trials change no result.
 static std::string tune_key(const p2_ctx *c) {
     char b[256];
-    snprintf(b, sizeof b, "R=%d precision=%d nonneg=%d fp64=%d K=%lld J=%d nnz=%lld", c->R,
+    snprintf(b, sizeof b, "R=%d precision=%d nonneg=%d fp64=%d tc=%d K=%lld J=%d nnz=%lld", c->R,
              c->opt.precision, c->opt.nonneg ? 1 : 0, c->opt.fp64_procrustes ? 1 : 0,
-             (long long)c->X.K, (int)c->X.J, (long long)c->X.nnz);
+             c->d_Mtc ? 1 : 0, (long long)c->X.K, (int)c->X.J, (long long)c->X.nnz);
     return b;
 }
 

@@ -21,6 +21,7 @@ enum : int {
     FLAG_BAD_VAL = 4,        // non-finite value
     FLAG_EIG_NOCONV = 8,     // an eigen iteration hit its step limit
     FLAG_NONFINITE = 32,     // non-finite loss / factor
+    FLAG_TC_TIMEOUT = 64,    // a tensor-core MMA did not complete within its wait limit
 };
 
 void set_error(const char *fmt, ...);
@@ -189,6 +190,9 @@ struct p2_ctx {
     int64_t split_chunk = 0, split_cap = 0;
     int32_t *d_split_list = nullptr;
     int32_t *d_split_cnt = nullptr;
+    // tensor-core formation of M' (p2_options.tensor_core_m): every subject's
+    // packed lower M' (K x P double-words), read by the grouped kernels
+    p2::dw *d_Mtc = nullptr;
     p2_tuning tune{1, -1, 0, 0};   // launch choices (p2_set_tuning, the autotuner)
     bool tuned = false;         // the autotuner has run (or read the cache)
     std::string tune_cache;     // opt.tune_cache, copied
@@ -265,12 +269,23 @@ cudaError_t launch_order_desc(const int32_t *key, int64_t K, int32_t *rank, int3
 cudaError_t launch_subject_bins(p2_ctx *c);
 cudaError_t launch_polar_on(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
                             float *T, int64_t K, cudaStream_t s, const int32_t *order = nullptr,
-                            int32_t *qrcnt = nullptr);
+                            int32_t *qrcnt = nullptr, const dw *mpre = nullptr);
 // subjects per chunk of the ordering kernels (p2_polar.cu)
 #define P2_ORDER_CHUNK 4096
 #define P2_ORDER_BINS 256
-// kernels launched by launch_polar (the ordering and the Procrustes kernel)
-constexpr int POLAR_LAUNCHES = 4;
+// kernels launch_polar enqueues for this context (the ordering, the optional
+// tensor-core formation of M, the Procrustes kernel or the split step's
+// kernels per chunk)
+int polar_launches(const p2_ctx *c);
+// M' = H' S' G' S' H'^T of every subject on the tensor cores (p2_form_tc.cu),
+// packed lower double-words, for 13 <= R <= P2_TC_RMAX
+#define P2_TC_RMAX 48
+bool form_m_tc_supported(int R);
+// whether the context's options select the tensor-core formation of M'
+bool tc_m_wanted(const p2_ctx *c);
+cudaError_t form_m_tc_configure(int R);
+cudaError_t launch_form_m_tc(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
+                             dw *Mout, int64_t K, cudaStream_t s);
 // non-negative variant (p2_nnls.cu): row-wise NNLS for the W and V updates
 cudaError_t nnls_configure(int cap);
 cudaError_t launch_nnls_w(p2_ctx *c);
@@ -292,7 +307,9 @@ cudaError_t polar_grp_configure_f64(int cap);
 cudaError_t launch_polar_grp_f64(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
                                  float *T, int64_t K, cudaStream_t s, double rtol2,
                                  const int32_t *order, int32_t *qrcnt);
+// mpre (nullable, double-word instances only): each subject's M' from
+// launch_form_m_tc instead of forming it in the kernel
 cudaError_t launch_polar_grp(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
                              float *T, int64_t K, cudaStream_t s, double rtol2,
-                             const int32_t *order, int32_t *qrcnt);
+                             const int32_t *order, int32_t *qrcnt, const dw *mpre = nullptr);
 }  // namespace p2

@@ -1829,7 +1829,7 @@ static int enqueue_qstep(p2_ctx *c, int with_fit) {
             set_error("launch of the Procrustes kernel failed: %s", cudaGetErrorString(e));
             return P2_ECUDA;
         }
-        c->enqueued += POLAR_LAUNCHES;
+        c->enqueued += polar_launches(c);
     }
     mark(c, 5);
     const int P = R * (R + 1) / 2;
@@ -1918,7 +1918,7 @@ int tune_time_qstep(p2_ctx *c, int reps, float *ms) {
             set_error("autotuner: Procrustes launch failed: %s", cudaGetErrorString(e));
             return P2_ECUDA;
         }
-        c->enqueued += POLAR_LAUNCHES;
+        c->enqueued += polar_launches(c);
         return P2_OK;
     });
 }

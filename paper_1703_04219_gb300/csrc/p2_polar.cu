@@ -307,10 +307,16 @@ static cudaError_t allow_reg(int cap) {
     return e;
 }
 
+bool tc_m_wanted(const p2_ctx *c) {
+    if (c->opt.fp64_procrustes || !form_m_tc_supported(c->R)) return false;
+    return c->opt.tensor_core_m > 0;
+}
+
 int polar_configure(p2_ctx *c) {
     const int cap = c->geo.smem_optin;
     cudaError_t e = c->opt.fp64_procrustes ? allow_reg<f64n>(cap) : allow_reg<dw>(cap);
     if (e == cudaSuccess) e = polar_grp_configure(cap, c->opt.fp64_procrustes != 0);
+    if (e == cudaSuccess && tc_m_wanted(c)) e = form_m_tc_configure(c->R);
     if (e != cudaSuccess) {
         set_error("configuring the Procrustes kernels: %s", cudaGetErrorString(e));
         return P2_ECUDA;
@@ -322,11 +328,11 @@ int polar_configure(p2_ctx *c) {
 // holding H64) writing T; returns a cudaError_t.
 cudaError_t launch_polar_on(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
                             float *T, int64_t K, cudaStream_t s, const int32_t *order,
-                            int32_t *qrcnt) {
+                            int32_t *qrcnt, const dw *mpre) {
     const int R = c->R;
     const double rtol2 = c->opt.rank_rtol * c->opt.rank_rtol;
     if (K <= 0) return cudaSuccess;
-    if (R > 12) return launch_polar_grp(c, G, W, st, T, K, s, rtol2, order, qrcnt);
+    if (R > 12) return launch_polar_grp(c, G, W, st, T, K, s, rtol2, order, qrcnt, mpre);
     const float rt2 = (float)rtol2;
     const bool f64 = c->opt.fp64_procrustes != 0;
     int rc = -1;
@@ -377,15 +383,33 @@ cudaError_t launch_subject_bins(p2_ctx *c) {
 }
 
 // The Q-step of the iteration: order the subjects by their last rotation
-// counts, then the Procrustes kernel (POLAR_LAUNCHES kernels in all).
+// counts, form every subject's M' on the tensor cores where selected, then
+// the Procrustes kernel(s) (polar_launches kernels in all).
 cudaError_t launch_polar(p2_ctx *c) {
     const int64_t K = c->X.K;
     if (K <= 0) return cudaSuccess;
     cudaError_t e = launch_order_desc(c->d_qrcnt, K, c->d_rank, c->d_binoff, c->d_order,
                                       c->stream);
     if (e != cudaSuccess) return e;
+    if (c->d_Mtc) {
+        e = launch_form_m_tc(c, c->d_G, c->d_W, c->d_s, c->d_Mtc, K, c->stream);
+        if (e != cudaSuccess) return e;
+    }
     return launch_polar_on(c, c->d_G, c->d_W, c->d_s, c->d_T, K, c->stream, c->d_order,
-                           c->d_qrcnt);
+                           c->d_qrcnt, c->d_Mtc);
+}
+
+int polar_launches(const p2_ctx *c) {
+    const int64_t K = c->X.K;
+    if (K <= 0) return 0;
+    int n = 3 + (c->d_Mtc ? 1 : 0);                      // ordering (+ M' on the tensor cores)
+    if (c->R > 12 && !c->opt.fp64_procrustes && c->d_split && c->tune.procrustes_split) {
+        const int64_t chunks = (K + c->split_chunk - 1) / c->split_chunk;
+        n += (int)(5 * chunks);                          // MODE 1, QR record, MODE 2, collect, fallback
+    } else {
+        n += 1;
+    }
+    return n;
 }
 
 }  // namespace p2

@@ -11,10 +11,10 @@ cudaError_t polar_grp_configure(int cap, bool fp64) {
 
 cudaError_t launch_polar_grp(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
                              float *T, int64_t K, cudaStream_t s, double rtol2,
-                             const int32_t *order, int32_t *qrcnt) {
+                             const int32_t *order, int32_t *qrcnt, const dw *mpre) {
     if (c->opt.fp64_procrustes)
         return launch_polar_grp_f64(c, G, W, st, T, K, s, rtol2, order, qrcnt);
-    return launch_grp_t<dw>(c, G, W, st, T, K, s, rtol2, order, qrcnt);
+    return launch_grp_t<dw>(c, G, W, st, T, K, s, rtol2, order, qrcnt, mpre);
 }
 
 }  // namespace p2

@@ -4,6 +4,8 @@
 // helpers (p2_polar.cuh), SmallState and FLAG_EIG_NOCONV.
 #pragma once
 
+#include <type_traits>
+
 #include "p2_num.cuh"
 
 namespace p2 {
@@ -87,6 +89,9 @@ template <class D> struct GrpSplit {
     int64_t cap = 0;                // records per subject slot (the stride)
     int64_t lim = 0;                // records a subject may use (<= cap)
     const int32_t *kdev = nullptr;
+    // nullable: every subject's M' (packed lower, indexed by subject), formed
+    // on the tensor cores; the kernels then load it instead of forming it
+    const dw *mpre = nullptr;
 };
 static __device__ __forceinline__ dw shfl_dw(unsigned mask, dw v, int src) {
     return dw{__shfl_sync(mask, v.h, src), __shfl_sync(mask, v.l, src)};
@@ -166,54 +171,64 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
             }
             __syncwarp(gmask);
 
-            // ---- M' = H' B H'^T with B = S' G' S' -------------------------------
-            // U = B H'^T, row by row in place (row i of B is held in registers).
-    #pragma unroll 1
-            for (int ii = 0; ii < RPL; ++ii) {
-                const int i = gl + PG * ii;
-                if (i >= R) break;
-                D b[RB];
-                const float wi = wv[i];
-    #pragma unroll
-                for (int j = 0; j < RB; ++j) {
-                    if (j < R) {
-                        const int p = (j <= i) ? (i * (i + 1) / 2 + j) : (j * (j + 1) / 2 + i);
-                        b[j] = dw_mul(dw_scale(from_dw<D>(Gk[p]), gsc), num_prod<D>(wi, wv[j]));
+            int em = 0;
+            if (std::is_same<D, dw>::value && sc.mpre) {
+                // M' formed on the tensor cores (same scalings, double-word accuracy)
+                const dw *Mk = sc.mpre + (size_t)k * (R * (R + 1) / 2);
+                for (int i = gl; i < R; i += PG) {
+                    for (int j = 0; j <= i; ++j) A(i, j) = from_dw<D>(Mk[i * (i + 1) / 2 + j]);
+                    em = max(em, f_expo(A(i, i).h));
+                }
+                __syncwarp(gmask);
+            } else {
+                // ---- M' = H' B H'^T with B = S' G' S' -------------------------------
+                // U = B H'^T, row by row in place (row i of B is held in registers).
+                #pragma unroll 1
+                for (int ii = 0; ii < RPL; ++ii) {
+                    const int i = gl + PG * ii;
+                    if (i >= R) break;
+                    D b[RB];
+                    const float wi = wv[i];
+                #pragma unroll
+                    for (int j = 0; j < RB; ++j) {
+                        if (j < R) {
+                            const int p = (j <= i) ? (i * (i + 1) / 2 + j) : (j * (j + 1) / 2 + i);
+                            b[j] = dw_mul(dw_scale(from_dw<D>(Gk[p]), gsc), num_prod<D>(wi, wv[j]));
+                        }
+                    }
+                #pragma unroll 1
+                    for (int c = 0; c < R; ++c) {
+                        acc_t<D> s = acc0<D>();
+                #pragma unroll
+                        for (int j = 0; j < RB; ++j)
+                            if (j < R) acc_fmaf(s, b[j], Hs[c * R + j]);
+                        A(i, c) = acc_val(s);
                     }
                 }
-    #pragma unroll 1
+                __syncwarp(gmask);
+                // M' = H' U, column by column in place (lower triangle).
+                #pragma unroll 1
                 for (int c = 0; c < R; ++c) {
-                    acc_t<D> s = acc0<D>();
-    #pragma unroll
-                    for (int j = 0; j < RB; ++j)
-                        if (j < R) acc_fmaf(s, b[j], Hs[c * R + j]);
-                    A(i, c) = acc_val(s);
-                }
-            }
-            __syncwarp(gmask);
-            // M' = H' U, column by column in place (lower triangle).
-            int em = 0;
-    #pragma unroll 1
-            for (int c = 0; c < R; ++c) {
-                D u[RB];
-    #pragma unroll
-                for (int i = 0; i < RB; ++i)
-                    if (i < R) u[i] = A(i, c);
-                __syncwarp(gmask);
-    #pragma unroll 1
-                for (int ii = 0; ii < RPL; ++ii) {
-                    const int r = gl + PG * ii;
-                    if (r >= R) break;
-                    if (r < c) continue;
-                    acc_t<D> s = acc0<D>();
-    #pragma unroll
+                    D u[RB];
+                #pragma unroll
                     for (int i = 0; i < RB; ++i)
-                        if (i < R) acc_fmaf(s, u[i], Hs[r * R + i]);
-                    const D m = acc_val(s);
-                    A(r, c) = m;
-                    if (r == c) em = max(em, f_expo(m.h));
+                        if (i < R) u[i] = A(i, c);
+                    __syncwarp(gmask);
+                #pragma unroll 1
+                    for (int ii = 0; ii < RPL; ++ii) {
+                        const int r = gl + PG * ii;
+                        if (r >= R) break;
+                        if (r < c) continue;
+                        acc_t<D> s = acc0<D>();
+                #pragma unroll
+                        for (int i = 0; i < RB; ++i)
+                            if (i < R) acc_fmaf(s, u[i], Hs[r * R + i]);
+                        const D m = acc_val(s);
+                        A(r, c) = m;
+                        if (r == c) em = max(em, f_expo(m.h));
+                    }
+                    __syncwarp(gmask);
                 }
-                __syncwarp(gmask);
             }
             em = group_max<PG>(gmask, em);
             if (eg == 0 || ew == 0 || em == 0) {

@@ -38,7 +38,7 @@ static void launch_grp(const p2_ctx *c, const dw *G, const float *W, SmallState 
 }
 
 // Pointers into the context's scratch for one chunk of the split step.
-static GrpSplit<dw> split_scratch(const p2_ctx *c) {
+static GrpSplit<dw> split_scratch(const p2_ctx *c, const dw *mpre) {
     const int64_t CH = c->split_chunk, R = c->R, cap = c->split_cap;
     unsigned char *b = c->d_split;
     auto take = [&b](size_t bytes) {
@@ -47,6 +47,7 @@ static GrpSplit<dw> split_scratch(const p2_ctx *c) {
         return p;
     };
     GrpSplit<dw> sc;
+    sc.mpre = mpre;
     sc.qh = reinterpret_cast<dw *>(take(sizeof(dw) * CH * R * R));
     sc.de = reinterpret_cast<dw *>(take(sizeof(dw) * CH * 2 * R));
     sc.dout = reinterpret_cast<dw *>(take(sizeof(dw) * CH * R));
@@ -75,9 +76,9 @@ static bool use_split(const p2_ctx *c, int64_t K, const int32_t *order) {
 template <int RB, int PG, int RT = 0>
 static void launch_grp_split(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
                              float *T, int64_t K, cudaStream_t s, double rtol2,
-                             const int32_t *order, int32_t *qrcnt) {
+                             const int32_t *order, int32_t *qrcnt, const dw *mpre) {
     const int R = c->R;
-    GrpSplit<dw> sc = split_scratch(c);
+    GrpSplit<dw> sc = split_scratch(c, mpre);
     const int64_t CH = c->split_chunk;
     const int nt = 128;
     const size_t smb = (size_t)2 * R * nt * sizeof(dw);
@@ -92,6 +93,7 @@ static void launch_grp_split(const p2_ctx *c, const dw *G, const float *W, Small
             sc.nrec, n, ord, c->d_split_list, c->d_split_cnt);
         GrpSplit<dw> fb{};
         fb.kdev = c->d_split_cnt;
+        fb.mpre = mpre;
         launch_grp<dw, RB, PG, RT, 0>(c, G, W, st, T, n, s, rtol2, c->d_split_list, qrcnt, fb);
     }
 }
@@ -149,13 +151,15 @@ static cudaError_t grp_configure_t(int cap) {
 template <class D>
 static cudaError_t launch_grp_t(const p2_ctx *c, const dw *G, const float *W, SmallState *st,
                              float *T, int64_t K, cudaStream_t s, double rtol2,
-                             const int32_t *order, int32_t *qrcnt) {
+                             const int32_t *order, int32_t *qrcnt, const dw *mpre = nullptr) {
     const int R = c->R;
+    GrpSplit<D> fz{};
+    if constexpr (std::is_same<D, dw>::value) fz.mpre = mpre;
     if constexpr (std::is_same<D, dw>::value) {
         if (use_split(c, K, order)) {
             switch (R) {
 #define P2_SPLIT(r, rb, pg) \
-                case r: launch_grp_split<rb, pg, r>(c, G, W, st, T, K, s, rtol2, order, qrcnt); \
+                case r: launch_grp_split<rb, pg, r>(c, G, W, st, T, K, s, rtol2, order, qrcnt, mpre); \
                         return cudaGetLastError();
                 P2_SPLIT(13, 16, 8) P2_SPLIT(14, 16, 8) P2_SPLIT(15, 16, 8) P2_SPLIT(16, 16, 8)
                 P2_SPLIT(24, 24, 8) P2_SPLIT(32, 32, 8) P2_SPLIT(40, 48, 16) P2_SPLIT(48, 48, 16)
@@ -163,39 +167,39 @@ static cudaError_t launch_grp_t(const p2_ctx *c, const dw *G, const float *W, Sm
 #undef P2_SPLIT
                 default: break;
             }
-            if (R <= 16) launch_grp_split<16, 8>(c, G, W, st, T, K, s, rtol2, order, qrcnt);
-            else if (R <= 24) launch_grp_split<24, 8>(c, G, W, st, T, K, s, rtol2, order, qrcnt);
-            else if (R <= 32) launch_grp_split<32, 8>(c, G, W, st, T, K, s, rtol2, order, qrcnt);
-            else if (R <= 48) launch_grp_split<48, 16>(c, G, W, st, T, K, s, rtol2, order, qrcnt);
-            else launch_grp_split<64, 16>(c, G, W, st, T, K, s, rtol2, order, qrcnt);
+            if (R <= 16) launch_grp_split<16, 8>(c, G, W, st, T, K, s, rtol2, order, qrcnt, mpre);
+            else if (R <= 24) launch_grp_split<24, 8>(c, G, W, st, T, K, s, rtol2, order, qrcnt, mpre);
+            else if (R <= 32) launch_grp_split<32, 8>(c, G, W, st, T, K, s, rtol2, order, qrcnt, mpre);
+            else if (R <= 48) launch_grp_split<48, 16>(c, G, W, st, T, K, s, rtol2, order, qrcnt, mpre);
+            else launch_grp_split<64, 16>(c, G, W, st, T, K, s, rtol2, order, qrcnt, mpre);
             return cudaGetLastError();
         }
     }
     // ranks 13 .. 16 and the multiples of 8 run an instance compiled for the
     // rank (loop bounds and offsets constant), the others the generic one
     switch (R) {
-        case 13: launch_grp<D, 16, 8, 13>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
-        case 14: launch_grp<D, 16, 8, 14>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
-        case 15: launch_grp<D, 16, 8, 15>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
-        case 16: launch_grp<D, 16, 8, 16>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
-        case 24: launch_grp<D, 24, 8, 24>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
-        case 32: launch_grp<D, 32, 8, 32>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
-        case 40: launch_grp<D, 48, 16, 40>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
-        case 48: launch_grp<D, 48, 16, 48>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
-        case 56: launch_grp<D, 64, 16, 56>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
-        case 64: launch_grp<D, 64, 16, 64>(c, G, W, st, T, K, s, rtol2, order, qrcnt); return cudaGetLastError();
+        case 13: launch_grp<D, 16, 8, 13>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz); return cudaGetLastError();
+        case 14: launch_grp<D, 16, 8, 14>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz); return cudaGetLastError();
+        case 15: launch_grp<D, 16, 8, 15>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz); return cudaGetLastError();
+        case 16: launch_grp<D, 16, 8, 16>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz); return cudaGetLastError();
+        case 24: launch_grp<D, 24, 8, 24>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz); return cudaGetLastError();
+        case 32: launch_grp<D, 32, 8, 32>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz); return cudaGetLastError();
+        case 40: launch_grp<D, 48, 16, 40>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz); return cudaGetLastError();
+        case 48: launch_grp<D, 48, 16, 48>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz); return cudaGetLastError();
+        case 56: launch_grp<D, 64, 16, 56>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz); return cudaGetLastError();
+        case 64: launch_grp<D, 64, 16, 64>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz); return cudaGetLastError();
         default: break;
     }
     if (R <= 16)
-        launch_grp<D, 16, 8>(c, G, W, st, T, K, s, rtol2, order, qrcnt);
+        launch_grp<D, 16, 8>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz);
     else if (R <= 24)
-        launch_grp<D, 24, 8>(c, G, W, st, T, K, s, rtol2, order, qrcnt);
+        launch_grp<D, 24, 8>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz);
     else if (R <= 32)
-        launch_grp<D, 32, 8>(c, G, W, st, T, K, s, rtol2, order, qrcnt);
+        launch_grp<D, 32, 8>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz);
     else if (R <= 48)
-        launch_grp<D, 48, 16>(c, G, W, st, T, K, s, rtol2, order, qrcnt);
+        launch_grp<D, 48, 16>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz);
     else
-        launch_grp<D, 64, 16>(c, G, W, st, T, K, s, rtol2, order, qrcnt);
+        launch_grp<D, 64, 16>(c, G, W, st, T, K, s, rtol2, order, qrcnt, fz);
     return cudaGetLastError();
 }
 

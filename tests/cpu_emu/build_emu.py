@@ -77,7 +77,7 @@ def build() -> str:
                 units.append(os.path.join(gen, name))
     units.append(os.path.join(HERE, "emu_rt.cpp"))
     flags = ["g++", "-std=c++20", "-O1", "-g", "-ffp-contract=off", "-fsanitize=address",
-             "-fno-omit-frame-pointer",
+             "-fno-omit-frame-pointer", "-DP2_CPU_EMU",
              "-fPIC", "-I", os.path.join(HERE, "fake"), "-I", CSRC]
     objs = [os.path.join(BUILD, os.path.basename(u)[:-4] + ".o") for u in units]
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:

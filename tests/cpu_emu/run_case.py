@@ -173,6 +173,40 @@ def rational_case(R, K):
             "einval": einval, "still_iterates": still}
 
 
+def tc_case(R, K):
+    """The tensor-core formation of M' (p2_options.tensor_core_m: digits of
+    8 bits on the emulated tensor core, exact FP32 accumulation) against the
+    double-word formation on the FP32 pipe: T_k of the first Q-step and the
+    factors after one iteration close to each other and to the oracle, with
+    the split step, the fused kernel and the split step's fallback."""
+    X = synth.generate("tiny", K=K)
+    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=41)
+    ref = P.als_iteration(P.all_blocks(X), H0.astype(np.float64), V0.astype(np.float64),
+                          W0.astype(np.float64))
+    out = {}
+    runs = {}
+    for name, tc, tune in (("dw", False, dict(procrustes_split=1)),
+                           ("tc", True, dict(procrustes_split=1)),
+                           ("tc_fused", True, dict(procrustes_split=0)),
+                           ("tc_fallback", True, dict(procrustes_split=1, split_record_cap=R))):
+        with p2.Parafac2(R, use_graph=False, tensor_core_m=tc) as m:
+            m.set_tuning(**tune)
+            m.load(X)
+            m.init(H0, V0, W0)
+            T0 = m.procrustes()
+            fit = m.iterate(1)
+            runs[name] = (T0, fit) + m.factors()
+    for name in ("dw", "tc", "tc_fused", "tc_fallback"):
+        T0, fit, H, V, W = runs[name]
+        out[f"{name}_T0_vs_dw"] = rel_fro(T0, runs["dw"][0])
+        out[f"{name}_W"] = rel_fro(W, ref["W"])
+        out[f"{name}_V"] = rel_fro(V, ref["V"])
+        out[f"{name}_H"] = rel_fro(H, ref["H"])
+    out["tc_paths_bitwise"] = float(all(np.array_equal(a, b) for n in ("tc_fused", "tc_fallback")
+                                        for a, b in zip(runs["tc"], runs[n])))
+    return out
+
+
 def split_case(R, K):
     """The split Procrustes step (QR recorder) against the fused kernel, and
     with a record capacity small enough that most subjects go to the fused
@@ -264,6 +298,8 @@ if __name__ == "__main__":
         out = rational_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "blocks":
         out = blocks_case(int(sys.argv[2]), int(sys.argv[3]))
+    elif kind == "tc":
+        out = tc_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "split":
         out = split_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "shard":

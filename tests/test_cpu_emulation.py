@@ -5,7 +5,9 @@ per subject), at R = 20 (a rank outside the compiled list: generic kernels), at 
 and R = 40 with the FP64 arm of the Procrustes step, at R = 5 with bfloat16
 storage and in the non-negative variant, a projection of new
 subjects, U_k = Q_k H for a range of subjects, the seeded initialisation
-with the stopping rule, and the rational start (subspace iteration in FP64).
+with the stopping rule, the rational start (subspace iteration in FP64), and
+the tensor-core formation of the Procrustes step's M (tcgen05 MMAs emulated
+from the shared-memory descriptors).
 Every device buffer and every block's shared memory is a heap block of its
 exact size, so an out-of-bounds access by any kernel aborts the run; the
 results must also match the FP64 oracle.  No GPU involved."""
@@ -39,6 +41,8 @@ CASES = {
     "shard_r6": ["shard", "6", "20"],
     "split_r13": ["split", "13", "12"],
     "split_r40": ["split", "40", "8"],
+    "tc_r40": ["tc", "40", "8"],
+    "tc_r13": ["tc", "13", "16"],
     "blocks_r6": ["blocks", "6", "40"],
 }
 
@@ -164,6 +168,20 @@ def test_emulated_split_procrustes_equals_fused(emulated_runs, name):
     rotation-applying kernel) and its fused fallback give the fused kernel's
     results bit for bit, within bounds."""
     assert _result(emulated_runs, name)["bitwise"] == 1.0
+
+
+@pytest.mark.parametrize("name", ["tc_r40", "tc_r13"])
+def test_emulated_tensor_core_m(emulated_runs, name):
+    """M of the Procrustes step formed on the (emulated) tensor cores: in
+    bounds, the split step, the fused kernel and the fallback bitwise equal
+    to each other, T_k close to the double-word formation's, and the factors
+    within 1e-5 of the oracle."""
+    out = _result(emulated_runs, name)
+    assert out["tc_paths_bitwise"] == 1.0, out
+    for path in ("tc", "tc_fused", "tc_fallback"):
+        assert out[f"{path}_T0_vs_dw"] < 1e-4, out
+        for f in ("W", "V", "H"):
+            assert out[f"{path}_{f}"] < 1e-5, (path, f, out)
 
 
 def test_emulated_mode2_row_blocks_are_in_bounds_and_match(emulated_runs):

@@ -133,6 +133,32 @@ static __device__ __forceinline__ void gather_rows(const XView &X, int nr, int64
     if (lane >= nr) return;
     const int64_t b0 = base + off;
     const int VS = v_stride<S>(R);
+    if (TWO && CB >= 32 && R <= CB) {
+        // the whole row in one block: one walk over the row's non-zeros feeds
+        // both operands (one round of dependent column loads instead of two);
+        // for CB >= 32 only, where the kernel may hold both accumulator rows
+        // (one block per SM; at CB = 16 the registers of three blocks per SM
+        // do not hold them)
+        float a1[CB], a2[CB];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            a1[c] = 0.f;
+            a2[c] = 0.f;
+        }
+        for (int e = 0; e < len; ++e) {
+            const int j = X.col[b0 + e];
+            const float x = X.val[b0 + e];
+            axpy_row<CB>(a1, x, V1 + (size_t)j * VS, R);
+            axpy_row<CB>(a2, x, V2 + (size_t)j * VS, R);
+        }
+#pragma unroll
+        for (int c = 0; c < CB; ++c)
+            if (c < R) {
+                z1[lane * RS + c] = a1[c];
+                z2[lane * RS + c] = a2[c];
+            }
+        return;
+    }
 #pragma unroll 1
     for (int which = 0; which < (TWO ? 2 : 1); ++which) {
         const S *__restrict__ Vw = which ? V2 : V1;
@@ -1491,7 +1517,9 @@ using RankList = std::integer_sequence<int, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 1
                                        24, 32, 40, 48, 56, 64>;
 template <int R>
 struct RankBlock {
-    static constexpr int cb = R <= 8 ? 8 : R <= 16 ? 16 : 32;
+    // above 32 the whole row (R rounded up to 8) in one block, so that a
+    // row's non-zeros are walked once per operand
+    static constexpr int cb = R <= 8 ? 8 : R <= 16 ? 16 : R <= 32 ? 32 : (R + 7) / 8 * 8;
 };
 
 template <class S, int... Rs>

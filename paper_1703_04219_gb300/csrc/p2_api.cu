@@ -73,10 +73,10 @@ static void free_data(p2_ctx *c) {
     dfree(c, &c->d_Vprev, J * v_stride<float>((int)R));
     dfree(c, &c->d_Vh, J * v_stride<bf16_t>((int)R));
     dfree(c, &c->d_Vprevh, J * v_stride<bf16_t>((int)R));
-    dfree(c, &c->d_Ph, (size_t)c->X.p_rows * R);
+    dfree(c, &c->d_Ph, (size_t)c->X.p_rows * v_stride<bf16_t>((int)R));
     dfree(c, &c->d_Vun, J * R);
     dfree(c, &c->d_M2, J * R);
-    dfree(c, &c->d_P, (size_t)c->X.p_rows * R);
+    dfree(c, &c->d_P, (size_t)c->X.p_rows * v_stride<float>((int)R));
     dfree(c, &c->X.csc_row, nnz);
     dfree(c, &c->X.csc_val, nnz);
     dfree(c, &c->X.seg_start, (size_t)c->X.nseg);
@@ -133,7 +133,7 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
         P2_TRY(dalloc(c, &c->d_Vprevh, nv));
         P2_CUDA_TRY(cudaMemsetAsync(c->d_Vh, 0, sizeof(bf16_t) * nv, c->stream));
         P2_CUDA_TRY(cudaMemsetAsync(c->d_Vprevh, 0, sizeof(bf16_t) * nv, c->stream));
-        P2_TRY(dalloc(c, &c->d_Ph, (size_t)N * R));
+        P2_TRY(dalloc(c, &c->d_Ph, (size_t)N * v_stride<bf16_t>(R)));   // rows padded as V
         c->X.p_rows = N;
     } else {
         const size_t nv = (size_t)J * v_stride<float>(R);     // padded rows, zero padding
@@ -141,7 +141,7 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
         P2_TRY(dalloc(c, &c->d_Vprev, nv));
         P2_CUDA_TRY(cudaMemsetAsync(c->d_V, 0, sizeof(float) * nv, c->stream));
         P2_CUDA_TRY(cudaMemsetAsync(c->d_Vprev, 0, sizeof(float) * nv, c->stream));
-        P2_TRY(dalloc(c, &c->d_P, (size_t)N * R));
+        P2_TRY(dalloc(c, &c->d_P, (size_t)N * v_stride<float>(R)));     // rows padded as V
         c->X.p_rows = N;
     }
     P2_TRY(dalloc(c, &c->d_T, (size_t)K * R * R));

@@ -426,6 +426,48 @@ __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 3) k_alpha(XView X, const 
 // mode 2 (Eq. mttkrp2_3) is M2 = sum_k Y_k^T H S_k = sum_k X_k^T P_k.
 // One warp per subject; the rows go to P (N x R) in stacked-row order.
 // ---------------------------------------------------------------------------
+// bfloat16 bit pattern of v, rounded to nearest even (as Stor<bf16_t>::st)
+static __device__ __forceinline__ uint32_t bf16_bits(float v) {
+    const bf16_t h = __float2bfloat16_rn(v);
+    uint16_t u;
+    memcpy(&u, &h, sizeof u);
+    return u;
+}
+
+// a[0 .. CB) to a 16-byte aligned row segment p as 16-byte vectors: the
+// first lim values, zeros up to len (len <= CB, a multiple of the vector)
+template <int CB>
+static __device__ __forceinline__ void vec_store_row(float *p, const float *a, int lim, int len) {
+#pragma unroll
+    for (int q = 0; q < CB / 4; ++q) {
+        if (4 * q < len) {
+            float4 v;
+            v.x = 4 * q < lim ? a[4 * q] : 0.f;
+            v.y = 4 * q + 1 < lim ? a[4 * q + 1] : 0.f;
+            v.z = 4 * q + 2 < lim ? a[4 * q + 2] : 0.f;
+            v.w = 4 * q + 3 < lim ? a[4 * q + 3] : 0.f;
+            *reinterpret_cast<float4 *>(p + 4 * q) = v;
+        }
+    }
+}
+template <int CB>
+static __device__ __forceinline__ void vec_store_row(bf16_t *p, const float *a, int lim, int len) {
+#pragma unroll
+    for (int q = 0; q < CB / 8; ++q) {
+        if (8 * q < len) {
+            uint32_t w[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int c = 8 * q + 2 * h;
+                const uint32_t lo = c < lim ? bf16_bits(a[c]) : 0u;
+                const uint32_t hi = c + 1 < lim ? bf16_bits(a[c + 1]) : 0u;
+                w[h] = lo | (hi << 16);
+            }
+            *reinterpret_cast<uint4 *>(p + 8 * q) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
 static __host__ __device__ size_t beta_warp_bytes(int R) {
     const size_t b = ((size_t)32 * row_stride(R) + (size_t)R * f_stride(R) + (size_t)R * R + R) * 4;
     return (b + 15) & ~(size_t)15;
@@ -433,13 +475,15 @@ static __host__ __device__ size_t beta_warp_bytes(int R) {
 
 // The same kernel serves p2_get_U (U_k = Q_k H = Z_k T_k^T H): W == NULL
 // stands for S_k = I, the output type O may differ from the storage type S,
-// and row r of the view is written at Pout[(r - out_row0) R].
+// and row r of the view is written at Pout[(r - out_row0) ldo].  With ldo =
+// v_stride<O>(R) (the mode-2 rows) every row is a whole number of 16-byte
+// vectors, written with vector stores, the padding zero.
 template <int CB, class S, class O = S, int RT = 0>
 __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 4) k_beta_p(XView X, const S *__restrict__ V,
                                                 const float *__restrict__ H,
                                                 const float *__restrict__ T,
                                                 const float *__restrict__ W, O *Pout, int R_rt,
-                                                int64_t out_row0) {
+                                                int64_t out_row0, int ldo) {
     const int R = RT > 0 ? RT : R_rt;   // RT > 0: the rank fixed at compile time
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RS = row_stride(R);
@@ -481,12 +525,13 @@ __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 4) k_beta_p(XView X, const
             const int tot = __shfl_sync(FULLMASK, off + len, 31);
             gather_rows<CB, false, S>(X, nr, base, len, off, V, nullptr, zo, nullptr, R, RS, lane);
             __syncwarp();
-            O *Pr = Pout + (size_t)(cr - out_row0) * R;
+            O *Pr = Pout + (size_t)(cr - out_row0) * ldo;
+            const bool vec = ldo == v_stride<O>(R);
             // lane i computes row i of Z_k F_k; all lanes read the same F_k row
             // (a shared-memory broadcast) four columns at a time
             if (lane < nr) {
                 const float *zr = zo + lane * RS;
-                O *Prow = Pr + (size_t)lane * R;
+                O *Prow = Pr + (size_t)lane * ldo;
                 for (int cb = 0; cb < R; cb += CB) {
                     float acc[CB];
 #pragma unroll
@@ -505,13 +550,48 @@ __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 4) k_beta_p(XView X, const
                             }
                         }
                     }
+                    if (vec) {
+                        vec_store_row<CB>(Prow + cb, acc, R - cb, ldo - cb);
+                    } else {
 #pragma unroll
-                    for (int c = 0; c < CB; ++c)
-                        if (cb + c < R) Stor<O>::st(Prow + cb + c, acc[c]);
+                        for (int c = 0; c < CB; ++c)
+                            if (cb + c < R) Stor<O>::st(Prow + cb + c, acc[c]);
+                    }
                 }
             }
             __syncwarp();
             base += tot;
+        }
+    }
+}
+
+// v[0 .. CB) from a 16-byte aligned row segment p with 16-byte loads (the
+// vectors that hold the first lim values)
+template <int CB>
+static __device__ __forceinline__ void vec_load_row(float *v, const float *__restrict__ p, int lim) {
+#pragma unroll
+    for (int q = 0; q < CB / 4; ++q) {
+        if (4 * q < lim) {
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(p) + q);
+            v[4 * q] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
+        }
+    }
+}
+template <int CB>
+static __device__ __forceinline__ void vec_load_row(float *v, const bf16_t *__restrict__ p, int lim) {
+#pragma unroll
+    for (int q = 0; q < CB / 8; ++q) {
+        if (8 * q < lim) {
+            const uint4 t = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+            const unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {       // two bfloat16 per word, low half first
+                v[8 * q + 2 * h] = __int_as_float((int)(w[h] << 16));
+                v[8 * q + 2 * h + 1] = __int_as_float((int)(w[h] & 0xffff0000u));
+            }
         }
     }
 }
@@ -533,6 +613,7 @@ __global__ void __launch_bounds__(256) k_m2_segments(const uint32_t *__restrict_
                                                      const S *__restrict__ Pin, int64_t row0,
                                                      double *segpart, int R) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int PS = v_stride<S>(R);              // P rows padded to 16-byte vectors
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t sg = sg0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; sg < sg1; sg += nwarps) {
         const int64_t a = seg_start[sg], b = seg_end[sg];
@@ -546,11 +627,13 @@ __global__ void __launch_bounds__(256) k_m2_segments(const uint32_t *__restrict_
             for (int64_t e = a + lane; e < b; e += 32) {
                 const uint32_t row = csc_row[e];
                 const float x = csc_val[e];
-                const S *pr = Pin + (size_t)((int64_t)row - row0) * R + cb;   // the block's P rows
+                const S *pr = Pin + (size_t)((int64_t)row - row0) * PS + cb;  // the block's P rows
+                float pv[CB];
+                vec_load_row<CB>(pv, pr, R - cb);
 #pragma unroll
                 for (int c = 0; c < CB; ++c) {
                     if (cb + c < R) {
-                        const float y = x * Stor<S>::ld(pr + c) - cp[c];
+                        const float y = x * pv[c] - cp[c];
                         const float tt = hi[c] + y;
                         cp[c] = (tt - hi[c]) - y;
                         hi[c] = tt;
@@ -1710,7 +1793,7 @@ static void launch_beta_k(p2_ctx *c, const Launch &L, int b) {
     dim3 grid((unsigned)std::max<int64_t>(1, std::min(want, full)));
     k_beta_p<CB, S, S, RT><<<grid, dim3(nt), L.beta_smem, c->stream>>>(
         X, Bufs<S>::V(c), c->d_H, c->d_T + (size_t)k0 * c->R * c->R, c->d_W + (size_t)k0 * c->R,
-        Bufs<S>::P(c), c->R, row0);
+        Bufs<S>::P(c), c->R, row0, v_stride<S>(c->R));
 }
 
 template <class S, int... Rs>
@@ -1767,17 +1850,17 @@ static void launch_get_u_t(p2_ctx *c, const Launch &L, int64_t k0, int64_t k1, i
     switch (comp_block(c->R)) {
         case 8: {
             const int g = (int)std::min<int64_t>(want, c->geo.nsm * resident_blocks(c, k_beta_p<8, S, float>, nt, L.beta_smem));
-            k_beta_p<8, S, float><<<g, nt, L.beta_smem, c->stream>>>(X, V, c->d_H, T, nullptr, U, c->R, r0);
+            k_beta_p<8, S, float><<<g, nt, L.beta_smem, c->stream>>>(X, V, c->d_H, T, nullptr, U, c->R, r0, c->R);
             break;
         }
         case 16: {
             const int g = (int)std::min<int64_t>(want, c->geo.nsm * resident_blocks(c, k_beta_p<16, S, float>, nt, L.beta_smem));
-            k_beta_p<16, S, float><<<g, nt, L.beta_smem, c->stream>>>(X, V, c->d_H, T, nullptr, U, c->R, r0);
+            k_beta_p<16, S, float><<<g, nt, L.beta_smem, c->stream>>>(X, V, c->d_H, T, nullptr, U, c->R, r0, c->R);
             break;
         }
         default: {
             const int g = (int)std::min<int64_t>(want, c->geo.nsm * resident_blocks(c, k_beta_p<32, S, float>, nt, L.beta_smem));
-            k_beta_p<32, S, float><<<g, nt, L.beta_smem, c->stream>>>(X, V, c->d_H, T, nullptr, U, c->R, r0);
+            k_beta_p<32, S, float><<<g, nt, L.beta_smem, c->stream>>>(X, V, c->d_H, T, nullptr, U, c->R, r0, c->R);
             break;
         }
     }

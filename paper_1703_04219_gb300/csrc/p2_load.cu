@@ -250,8 +250,9 @@ static int build_csc(p2_ctx *c, const int64_t *d_row_ptr, const int32_t *h_count
             void **pp = c->bf16 ? (void **)&c->d_Ph : (void **)&c->d_P;
             cudaFree(*pp);
             *pp = nullptr;
-            c->dev_bytes -= (size_t)c->X.p_rows * c->R * elem;
-            const cudaError_t e = cudaMalloc(pp, (size_t)(rows > 0 ? rows : 1) * c->R * elem);
+            const size_t ps = c->bf16 ? v_stride<bf16_t>(c->R) : v_stride<float>(c->R);
+            c->dev_bytes -= (size_t)c->X.p_rows * ps * elem;
+            const cudaError_t e = cudaMalloc(pp, (size_t)(rows > 0 ? rows : 1) * ps * elem);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 c->X.p_rows = 0;
@@ -259,7 +260,7 @@ static int build_csc(p2_ctx *c, const int64_t *d_row_ptr, const int32_t *h_count
                 return e == cudaErrorMemoryAllocation ? P2_ENOMEM : P2_ECUDA;
             }
             c->X.p_rows = rows;
-            c->dev_bytes += (size_t)rows * c->R * elem;
+            c->dev_bytes += (size_t)rows * ps * elem;
         }
     }
     const int nblk = c->X.nblk;

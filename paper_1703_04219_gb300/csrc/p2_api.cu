@@ -29,11 +29,28 @@ static int fail(int code, const char *msg) {
     return code;
 }
 
+// Device memory of a context comes, stream-ordered, from the context's own
+// pool, which keeps what is freed for the next allocation (a reload of
+// slices reuses it without cudaMalloc/cudaFree and their device-wide
+// synchronisation); the pool's memory goes back at p2_destroy.  Without a
+// pool (creation refused) plain cudaMalloc/cudaFree.
+cudaError_t ctx_malloc(const p2_ctx *c, void **p, size_t bytes) {
+    if (c->pool) return cudaMallocFromPoolAsync(p, bytes, c->pool, c->stream);
+    return cudaMalloc(p, bytes);
+}
+void ctx_free(const p2_ctx *c, void *p) {
+    if (!p) return;
+    if (c->pool)
+        cudaFreeAsync(p, c->stream);
+    else
+        cudaFree(p);
+}
+
 template <class T>
 static int dalloc(p2_ctx *c, T **p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    cudaError_t e = ctx_malloc(c, (void **)p, sizeof(T) * count);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMalloc of %zu bytes failed: %s", sizeof(T) * count, cudaGetErrorString(e));
@@ -46,7 +63,7 @@ static int dalloc(p2_ctx *c, T **p, size_t count) {
 template <class T>
 static void dfree(p2_ctx *c, T **p, size_t count) {
     if (*p) {
-        cudaFree(*p);
+        ctx_free(c, *p);
         if (count == 0) count = 1;
         c->dev_bytes -= sizeof(T) * count;
     }
@@ -355,6 +372,26 @@ int p2_create(p2_ctx **out, const p2_options *opt) {
         }
         c->own_stream = true;
     }
+    {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = opt->device;
+        if (cudaMemPoolCreate(&c->pool, &props) == cudaSuccess) {
+            uint64_t keep = ~0ull;               // keep freed memory for reuse
+            if (cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                cudaMemPoolDestroy(c->pool);
+                c->pool = nullptr;
+            }
+        } else {
+            cudaGetLastError();
+            c->pool = nullptr;
+        }
+    }
     if (c->opt.timing) {
         for (int i = 0; i < 8; ++i) {
             if (cudaEventCreate(&c->ev[i]) != cudaSuccess) {
@@ -427,6 +464,8 @@ int p2_destroy(p2_ctx *c) {
     dfree(c, &c->d_red, part_stride);
     for (int i = 0; i < 8; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->stream) cudaStreamSynchronize(c->stream);   // the frees above are stream-ordered
+    if (c->pool) cudaMemPoolDestroy(c->pool);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return P2_OK;

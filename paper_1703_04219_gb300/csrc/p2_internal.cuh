@@ -124,6 +124,10 @@ struct Geometry {
     int red_blocks = 0;     // blocks of the grid reductions (fixed => deterministic)
 };
 
+// device memory of a context (its stream-ordered pool, p2_api.cu)
+cudaError_t ctx_malloc(const struct ::p2_ctx *c, void **p, size_t bytes);
+void ctx_free(const struct ::p2_ctx *c, void *p);
+
 // kernel launchers (defined in the .cu files)
 int launch_load(struct ::p2_ctx *ctx, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
                 const int32_t *d_col, const float *d_val, int64_t K, int32_t J, int64_t N,
@@ -137,6 +141,7 @@ struct p2_ctx {
     int P = 0;                      // R(R+1)/2
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaMemPool_t pool = nullptr;   // the context's device memory (ctx_malloc)
     p2::Geometry geo;
 
     p2::DevX X;

@@ -248,11 +248,11 @@ static int build_csc(p2_ctx *c, const int64_t *d_row_ptr, const int32_t *h_count
         // the P buffer holds one block
         if (rows < c->X.p_rows) {
             void **pp = c->bf16 ? (void **)&c->d_Ph : (void **)&c->d_P;
-            cudaFree(*pp);
+            ctx_free(c, *pp);
             *pp = nullptr;
             const size_t ps = c->bf16 ? v_stride<bf16_t>(c->R) : v_stride<float>(c->R);
             c->dev_bytes -= (size_t)c->X.p_rows * ps * elem;
-            const cudaError_t e = cudaMalloc(pp, (size_t)(rows > 0 ? rows : 1) * ps * elem);
+            const cudaError_t e = ctx_malloc(c, pp, (size_t)(rows > 0 ? rows : 1) * ps * elem);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 c->X.p_rows = 0;
@@ -264,8 +264,8 @@ static int build_csc(p2_ctx *c, const int64_t *d_row_ptr, const int32_t *h_count
         }
     }
     const int nblk = c->X.nblk;
-    cudaError_t e = cudaMalloc(&c->X.csc_row, sizeof(uint32_t) * (nnz > 0 ? nnz : 1));
-    if (e == cudaSuccess) e = cudaMalloc(&c->X.csc_val, sizeof(float) * (nnz > 0 ? nnz : 1));
+    cudaError_t e = ctx_malloc(c, (void **)&c->X.csc_row, sizeof(uint32_t) * (nnz > 0 ? nnz : 1));
+    if (e == cudaSuccess) e = ctx_malloc(c, (void **)&c->X.csc_val, sizeof(float) * (nnz > 0 ? nnz : 1));
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("load: allocation of the column-major copy failed: %s", cudaGetErrorString(e));
@@ -283,11 +283,11 @@ static int build_csc(p2_ctx *c, const int64_t *d_row_ptr, const int32_t *h_count
         int64_t *d_colptr = nullptr, *d_blkrow = nullptr, *d_vstart = nullptr;
         uint32_t *d_rowid = nullptr;
         int *d_cnt = nullptr;
-        e = cudaMalloc(&d_colptr, sizeof(int64_t) * ((size_t)J + 1));
-        if (e == cudaSuccess) e = cudaMalloc(&d_rowid, sizeof(uint32_t) * (size_t)nnz);
-        if (e == cudaSuccess) e = cudaMalloc(&d_cnt, sizeof(int) * (size_t)nch * J);
-        if (e == cudaSuccess) e = cudaMalloc(&d_blkrow, sizeof(int64_t) * ((size_t)nblk + 1));
-        if (e == cudaSuccess) e = cudaMalloc(&d_vstart, sizeof(int64_t) * vstart.size());
+        e = ctx_malloc(c, (void **)&d_colptr, sizeof(int64_t) * ((size_t)J + 1));
+        if (e == cudaSuccess) e = ctx_malloc(c, (void **)&d_rowid, sizeof(uint32_t) * (size_t)nnz);
+        if (e == cudaSuccess) e = ctx_malloc(c, (void **)&d_cnt, sizeof(int) * (size_t)nch * J);
+        if (e == cudaSuccess) e = ctx_malloc(c, (void **)&d_blkrow, sizeof(int64_t) * ((size_t)nblk + 1));
+        if (e == cudaSuccess) e = ctx_malloc(c, (void **)&d_vstart, sizeof(int64_t) * vstart.size());
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_colptr, colptr.data(), sizeof(int64_t) * ((size_t)J + 1),
                                                   cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_blkrow, c->X.blk_row.data(),
@@ -309,11 +309,11 @@ static int build_csc(p2_ctx *c, const int64_t *d_row_ptr, const int32_t *h_count
             e = cudaMemcpyAsync(vstart.data(), d_vstart, sizeof(int64_t) * vstart.size(),
                                 cudaMemcpyDeviceToHost, s);
         cudaError_t e2 = cudaStreamSynchronize(s);
-        cudaFree(d_colptr);
-        cudaFree(d_rowid);
-        cudaFree(d_cnt);
-        cudaFree(d_blkrow);
-        cudaFree(d_vstart);
+        ctx_free(c, d_colptr);
+        ctx_free(c, d_rowid);
+        ctx_free(c, d_cnt);
+        ctx_free(c, d_blkrow);
+        ctx_free(c, d_vstart);
         if (e == cudaSuccess) e = e2;
         if (e != cudaSuccess) {
             set_error("load: building the column-major copy failed: %s", cudaGetErrorString(e));
@@ -340,10 +340,10 @@ static int build_csc(p2_ctx *c, const int64_t *d_row_ptr, const int32_t *h_count
     vseg[(size_t)nblk * J] = (int64_t)s_lo.size();
     const int64_t nseg = (int64_t)s_lo.size();
     c->X.nseg = nseg;
-    e = cudaMalloc(&c->X.seg_start, sizeof(int64_t) * (size_t)(nseg > 0 ? nseg : 1));
-    if (e == cudaSuccess) e = cudaMalloc(&c->X.seg_end, sizeof(int64_t) * (size_t)(nseg > 0 ? nseg : 1));
-    if (e == cudaSuccess) e = cudaMalloc(&c->X.col_seg, sizeof(int64_t) * vseg.size());
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_segpart, sizeof(double) * (size_t)(nseg > 0 ? nseg : 1) * c->R);
+    e = ctx_malloc(c, (void **)&c->X.seg_start, sizeof(int64_t) * (size_t)(nseg > 0 ? nseg : 1));
+    if (e == cudaSuccess) e = ctx_malloc(c, (void **)&c->X.seg_end, sizeof(int64_t) * (size_t)(nseg > 0 ? nseg : 1));
+    if (e == cudaSuccess) e = ctx_malloc(c, (void **)&c->X.col_seg, sizeof(int64_t) * vseg.size());
+    if (e == cudaSuccess) e = ctx_malloc(c, (void **)&c->d_segpart, sizeof(double) * (size_t)(nseg > 0 ? nseg : 1) * c->R);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("load: allocation of the mode-2 segments failed: %s", cudaGetErrorString(e));
@@ -369,7 +369,7 @@ int launch_load(p2_ctx *c, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
     cudaStream_t s = c->stream;
     const int nsm = c->geo.nsm;
     LoadScratch *ls = nullptr;
-    P2_CUDA_TRY(cudaMallocAsync(&ls, sizeof(LoadScratch), s));
+    P2_CUDA_TRY(ctx_malloc(c, (void **)&ls, sizeof(LoadScratch)));
     P2_CUDA_TRY(cudaMemsetAsync(ls, 0, sizeof(LoadScratch), s));
     P2_CUDA_TRY(cudaMemsetAsync(c->d_colcount, 0, sizeof(int) * (size_t)J, s));
     k_check_subjects<<<4 * nsm, 256, 0, s>>>(d_subj_ptr, d_row_ptr, K, N, c->X.subj_row,
@@ -390,7 +390,7 @@ int launch_load(p2_ctx *c, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
     cudaError_t e2 = cudaMemcpyAsync(cc, c->d_colcount, sizeof(int) * (size_t)J,
                                      cudaMemcpyDeviceToHost, s);
     cudaError_t e3 = cudaStreamSynchronize(s);
-    cudaFreeAsync(ls, s);
+    ctx_free(c, ls);
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
         delete[] hp;
         delete[] cc;
@@ -417,7 +417,7 @@ int launch_load(p2_ctx *c, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
     key[J] = nx2;
     if (c->xfn) {
         double *dk = nullptr;
-        cudaError_t e = cudaMallocAsync(&dk, sizeof(double) * ((size_t)J + 1), s);
+        cudaError_t e = ctx_malloc(c, (void **)&dk, sizeof(double) * ((size_t)J + 1));
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(dk, key.data(), sizeof(double) * ((size_t)J + 1),
                                 cudaMemcpyHostToDevice, s);
@@ -426,7 +426,7 @@ int launch_load(p2_ctx *c, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
             e = cudaMemcpyAsync(key.data(), dk, sizeof(double) * ((size_t)J + 1),
                                 cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && rc == P2_OK) e = cudaStreamSynchronize(s);
-        if (dk) cudaFreeAsync(dk, s);
+        if (dk) ctx_free(c, dk);
         if (rc != P2_OK) {
             delete[] cc;
             return rc;

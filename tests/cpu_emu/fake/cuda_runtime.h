@@ -81,6 +81,25 @@ inline cudaError_t cudaMemGetInfo(size_t *f, size_t *t) {
     return cudaSuccess;
 }
 inline cudaError_t cudaFreeAsync(void *p, cudaStream_t) { free(p); return cudaSuccess; }
+// memory pools: creation refused, so callers take their cudaMalloc path
+typedef void *cudaMemPool_t;
+enum cudaMemAllocationType { cudaMemAllocationTypePinned = 1 };
+enum cudaMemAllocationHandleType { cudaMemHandleTypeNone = 0 };
+enum cudaMemLocationType { cudaMemLocationTypeDevice = 1 };
+struct cudaMemLocation { cudaMemLocationType type; int id; };
+struct cudaMemPoolProps {
+    cudaMemAllocationType allocType;
+    cudaMemAllocationHandleType handleTypes;
+    cudaMemLocation location;
+    void *win32SecurityAttributes;
+    size_t maxSize;
+    unsigned char reserved[56];
+};
+enum cudaMemPoolAttr { cudaMemPoolAttrReleaseThreshold = 4 };
+inline cudaError_t cudaMemPoolCreate(cudaMemPool_t *, const cudaMemPoolProps *) { return cudaErrorNotSupported; }
+inline cudaError_t cudaMemPoolSetAttribute(cudaMemPool_t, cudaMemPoolAttr, void *) { return cudaErrorNotSupported; }
+inline cudaError_t cudaMemPoolDestroy(cudaMemPool_t) { return cudaSuccess; }
+template <class T> inline cudaError_t cudaMallocFromPoolAsync(T **p, size_t n, cudaMemPool_t, cudaStream_t) { return cudaMalloc(p, n); }
 inline cudaError_t cudaMemcpy(void *d, const void *s, size_t n, cudaMemcpyKind) { if (n) memmove(d, s, n); return cudaSuccess; }
 inline cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyKind k, cudaStream_t = nullptr) { return cudaMemcpy(d, s, n, k); }
 inline cudaError_t cudaMemsetAsync(void *d, int v, size_t n, cudaStream_t = nullptr) { memset(d, v, n); return cudaSuccess; }

@@ -189,6 +189,19 @@ P2_HD int tridiagonal_qr_dw(int n_rt, DwMat<D> Z, DwVec<D> d, DwVec<D> e, int ma
     D x = zero, z = zero, dk = zero, ek = zero;
     int kp = 0;
     D cp = one, sp = zero;
+    // bit i: e[i] negligible against d[i], d[i + 1].  Taken for every position
+    // once; afterwards a trip re-tests only the positions whose d or e it
+    // wrote (the others keep their inputs, hence their bits).
+    unsigned long long nm = 0;
+#pragma unroll
+    for (int i = 0; i + 1 < NA; ++i)
+        if (i + 1 < n && dw_negligible(e[i], d[i], d[i + 1], tiny_ex)) nm |= 1ull << i;
+    auto retest = [&](int i) {
+        if (i >= 0 && i + 1 < n) {
+            const unsigned long long b = 1ull << i;
+            nm = dw_negligible(e[i], d[i], d[i + 1], tiny_ex) ? (nm | b) : (nm & ~b);
+        }
+    };
 #pragma unroll 1
     while (true) {
         D za[NA], zb[NA];                               // pending rotation's columns
@@ -199,10 +212,6 @@ P2_HD int tridiagonal_qr_dw(int n_rt, DwMat<D> Z, DwVec<D> d, DwVec<D> e, int ma
                 zb[i] = Z(i, kp + 1);
             }
         // ---- the block a new sweep would take, and its shift ----------------
-        unsigned long long nm = 0;                        // bit i: e[i] negligible
-#pragma unroll
-        for (int i = 0; i + 1 < NA; ++i)
-            if (i + 1 < n && dw_negligible(e[i], d[i], d[i + 1], tiny_ex)) nm |= 1ull << i;
         const unsigned long long nn = ~nm & ((1ull << q) - 1);
         const int qn = nn ? 64 - p2_clz64(nn) : 0;        // top non-negligible position + 1
         const unsigned long long nb = qn > 1 ? nm & ((1ull << (qn - 1)) - 1) : 0ull;
@@ -284,6 +293,7 @@ P2_HD int tridiagonal_qr_dw(int n_rt, DwMat<D> Z, DwVec<D> d, DwVec<D> e, int ma
         kp = kr;
         cp = c;
         sp = s;
+        const int kw = kr;                                // the positions this trip wrote
         if (++kr < q) {
             z = dw_neg(dw_mul(s, en));
             ek = dw_mul(c, en);
@@ -293,7 +303,12 @@ P2_HD int tridiagonal_qr_dw(int n_rt, DwMat<D> Z, DwVec<D> d, DwVec<D> e, int ma
             d[q] = dk1;
             e[q - 1] = ekn;
             sweeping = false;
+            retest(q - 1);
+            retest(q);
         }
+        retest(kw - 1);
+        retest(kw);
+        if (clear_top) retest(p - 1);
     }
     {   // flush the last rotation
         const D nsp = dw_neg(sp);

@@ -92,18 +92,6 @@ typedef struct {
                              the digit split and recombination cost more FP32-pipe work than
                              the product saves), so it is opt-in: 1 = on for 13 <= R <= 48;
                              0 or -1 (default) = off.  Ignored with fp64_procrustes. */
-    int32_t mode2_fixed_point; /* R <= 16: the mode-2 MTTKRP (Algorithm 3's M2) accumulated
-                             in 64-bit integers: every non-zero's contribution x P_k(i, r),
-                             rounded at a per-component power-of-two scale chosen each
-                             iteration from a bound on every column's sum (so nothing can
-                             overflow), added with integer atomics (exact, so deterministic
-                             in any order), hot columns in shared memory; the P_k rows
-                             (N x R, 2.4 GB at 63M nnz, R = 10) are not stored.  Measured
-                             slower on GB300 (63M nnz, R = 10: mode-2 pass 5.6 ms against
-                             3.6 ms; the atomics on the hottest columns serialise), so it is
-                             opt-in for the memory it saves: 1 = on for R <= 16; 0 or -1
-                             (default) = off (FP32 Kahan sums over the column-major copy).
-                             Ignored above 16. */
 } p2_options;
 
 /* Launch choices that change the speed, never the results (every choice

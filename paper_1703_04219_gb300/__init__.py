@@ -38,8 +38,7 @@ class p2_options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("timing", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("nonneg", ctypes.c_int32),
                 ("fp64_procrustes", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("tune_cache", ctypes.c_char_p), ("tensor_core_m", ctypes.c_int32),
-                ("mode2_fixed_point", ctypes.c_int32)]
+                ("tune_cache", ctypes.c_char_p), ("tensor_core_m", ctypes.c_int32)]
 
 
 class p2_tuning(ctypes.Structure):
@@ -339,7 +338,7 @@ class Parafac2:
     def __init__(self, R: int, device: int = 0, use_graph: bool = True, rank_rtol: float = 1e-5,
                  stream=None, timing: bool = False, precision: str = "fp32", seed=None,
                  nonneg: bool = False, fp64_procrustes: bool = False, autotune: bool = False,
-                 tune_cache=None, tensor_core_m=None, mode2_fixed_point=None):
+                 tune_cache=None, tensor_core_m=None):
         if precision not in ("fp32", "bf16"):
             raise ValueError("precision must be 'fp32' or 'bf16'")
         opt = p2_default_options(R)
@@ -356,8 +355,6 @@ class Parafac2:
         opt.autotune = 1 if autotune else 0
         if tensor_core_m is not None:       # None: the library's rule
             opt.tensor_core_m = 1 if tensor_core_m else 0
-        if mode2_fixed_point is not None:   # None: the library's default (off)
-            opt.mode2_fixed_point = 1 if mode2_fixed_point else 0
         self._tune_cache = tune_cache.encode() if tune_cache else None   # kept alive
         opt.tune_cache = self._tune_cache
         self.R = R

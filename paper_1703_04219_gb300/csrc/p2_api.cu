@@ -116,7 +116,6 @@ static void free_data(p2_ctx *c) {
     dfree(c, &c->d_split_list, (size_t)c->split_chunk);
     dfree(c, &c->d_split_cnt, 1);
     dfree(c, &c->d_Mtc, K * P);
-    dfree(c, &c->d_fxacc, J * R);
     c->split_chunk = c->split_cap = 0;
     c->split_bytes = 0;
     delete[] c->h_perm_new2old;
@@ -138,8 +137,6 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
     c->X.J = J;
     c->X.N = N;
     c->X.nnz = nnz;
-    // fixed-point mode 2 (opt-in, R <= 16): no P rows needed
-    c->fx = c->R <= 16 && c->opt.mode2_fixed_point > 0;
     P2_TRY(dalloc(c, &c->X.subj_row, (size_t)K + 1));
     P2_TRY(dalloc(c, &c->X.subj_nnz, (size_t)K + 1));
     P2_TRY(dalloc(c, &c->X.row_len, (size_t)N));
@@ -153,22 +150,17 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
         P2_TRY(dalloc(c, &c->d_Vprevh, nv));
         P2_CUDA_TRY(cudaMemsetAsync(c->d_Vh, 0, sizeof(bf16_t) * nv, c->stream));
         P2_CUDA_TRY(cudaMemsetAsync(c->d_Vprevh, 0, sizeof(bf16_t) * nv, c->stream));
-        if (!c->fx) {
-            P2_TRY(dalloc(c, &c->d_Ph, (size_t)N * v_stride<bf16_t>(R)));   // rows padded as V
-            c->X.p_rows = N;
-        }
+        P2_TRY(dalloc(c, &c->d_Ph, (size_t)N * v_stride<bf16_t>(R)));   // rows padded as V
+        c->X.p_rows = N;
     } else {
         const size_t nv = (size_t)J * v_stride<float>(R);     // padded rows, zero padding
         P2_TRY(dalloc(c, &c->d_V, nv));
         P2_TRY(dalloc(c, &c->d_Vprev, nv));
         P2_CUDA_TRY(cudaMemsetAsync(c->d_V, 0, sizeof(float) * nv, c->stream));
         P2_CUDA_TRY(cudaMemsetAsync(c->d_Vprev, 0, sizeof(float) * nv, c->stream));
-        if (!c->fx) {
-            P2_TRY(dalloc(c, &c->d_P, (size_t)N * v_stride<float>(R)));     // rows padded as V
-            c->X.p_rows = N;
-        }
+        P2_TRY(dalloc(c, &c->d_P, (size_t)N * v_stride<float>(R)));     // rows padded as V
+        c->X.p_rows = N;
     }
-    if (c->fx) P2_TRY(dalloc(c, &c->d_fxacc, (size_t)J * R));
     P2_TRY(dalloc(c, &c->d_T, (size_t)K * R * R));
     P2_TRY(dalloc(c, &c->d_Vun, (size_t)J * R));
     P2_TRY(dalloc(c, &c->d_M2, (size_t)J * R));
@@ -249,10 +241,6 @@ static int read_flags(p2_ctx *c, int *flags) {
 }
 
 static int flags_status(int flags) {
-    if (flags & FLAG_FX_RANGE) {
-        set_error("fixed-point mode 2: a term outside its bound (flags 0x%x)", flags);
-        return P2_ENUMERIC;
-    }
     if (flags & FLAG_TC_TIMEOUT) {
         set_error("a tensor-core MMA did not complete within its wait limit (flags 0x%x)", flags);
         return P2_ECUDA;
@@ -342,7 +330,6 @@ void p2_default_options(p2_options *opt, int32_t R) {
     opt->autotune = 0;
     opt->tune_cache = nullptr;
     opt->tensor_core_m = -1;
-    opt->mode2_fixed_point = -1;
 }
 
 int p2_create(p2_ctx **out, const p2_options *opt) {

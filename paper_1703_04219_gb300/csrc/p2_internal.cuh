@@ -22,7 +22,6 @@ enum : int {
     FLAG_EIG_NOCONV = 8,     // an eigen iteration hit its step limit
     FLAG_NONFINITE = 32,     // non-finite loss / factor
     FLAG_TC_TIMEOUT = 64,    // a tensor-core MMA did not complete within its wait limit
-    FLAG_FX_RANGE = 128,     // a fixed-point mode-2 term outside the range its bound allows
 };
 
 void set_error(const char *fmt, ...);
@@ -54,13 +53,6 @@ struct SmallState {
     unsigned long long polar_flops;     // FP64 flops executed by k_polar (running total)
     int flags;
     int iter;
-    // fixed-point mode 2 (R <= 16): the load-time column bound
-    // max_j sum_{i in column j} |x_ij| ||x_i||_1, the iteration's
-    // max_k max|T_k| |w_kr| (float bits, for atomicMax), and each component's
-    // scale exponent
-    double fx_dmax;
-    unsigned int fx_tw[P2_RMAX];
-    int fx_shift[P2_RMAX];
 };
 
 // Storage type of V and of the mode-2 rows P: float (P2_FP32) or bfloat16
@@ -131,9 +123,6 @@ struct Geometry {
     int smem_optin = 0;
     int red_blocks = 0;     // blocks of the grid reductions (fixed => deterministic)
 };
-
-// load time: the column bound of the fixed-point mode 2 (p2_kernels.cu)
-int launch_fx_bound(struct ::p2_ctx *c, const int64_t *d_row_ptr, const float *d_val, int64_t N);
 
 // device memory of a context (its stream-ordered pool, p2_api.cu)
 cudaError_t ctx_malloc(const struct ::p2_ctx *c, void **p, size_t bytes);
@@ -209,9 +198,6 @@ struct p2_ctx {
     // tensor-core formation of M' (p2_options.tensor_core_m): every subject's
     // packed lower M' (K x P double-words), read by the grouped kernels
     p2::dw *d_Mtc = nullptr;
-    // fixed-point mode 2 (p2_options.mode2_fixed_point): J x R integer sums
-    unsigned long long *d_fxacc = nullptr;
-    bool fx = false;
     p2_tuning tune{1, -1, 0, 0};   // launch choices (p2_set_tuning, the autotuner)
     bool tuned = false;         // the autotuner has run (or read the cache)
     std::string tune_cache;     // opt.tune_cache, copied

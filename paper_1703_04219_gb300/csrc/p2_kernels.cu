@@ -597,259 +597,6 @@ static __device__ __forceinline__ void vec_load_row(float *v, const bf16_t *__re
 }
 
 // ---------------------------------------------------------------------------
-// Mode 2 in fixed point (R <= 16, opt-in: p2_options.mode2_fixed_point).  M2(j, r) =
-// sum over the non-zeros x_ij of column j of x_ij P(i, r), P(i, :) = z_i F_k.
-// Each term is rounded to an integer at the scale 2^S_r and the integers are
-// added with 64-bit atomics: integer addition is exact and associative, so
-// the sum is the same in any order (deterministic) and carries no rounding
-// beyond the terms' (at most 2^-(S_r+1) each).  S_r comes, every iteration,
-// from a bound on every column's sum of |x P(i, r)|:
-//   |z_iu| <= ||x_i||_1 max|V|,  |F_k(u, r)| <= max|T_k| ||H(:, r)||_1 |w_kr|,
-//   sum_{i in col j} |x_ij P(i, r)|
-//       <= R max|V| ||H(:, r)||_1 max_k(max|T_k| |w_kr|) max_j sum_i |x_ij| ||x_i||_1,
-// doubled for the rounding of the FP32 products, so that 2^S_r times it stays
-// below 2^61 and no partial sum can overflow.
-// ---------------------------------------------------------------------------
-
-// round(t 2^sh) as an integer, from the float's fields (no conversion
-// instruction); sets FLAG_FX_RANGE (and saturates) above 2^62
-static __device__ __forceinline__ long long fx_fixed(float t, int sh, int *flags) {
-    const uint32_t b = (uint32_t)__float_as_int(t);
-    const int ex = (int)((b >> 23) & 0xFF);
-    if (ex == 0) return 0;                       // zero or subnormal: below the resolution
-    const long long mant = (long long)((b & 0x7FFFFFu) | 0x800000u);
-    const int k = ex - 150 + sh;                 // t 2^sh = mant 2^k
-    long long y;
-    if (k >= 0) {
-        if (k > 38) {
-            atomicOr(flags, FLAG_FX_RANGE);
-            y = 0x3FFFFFFFFFFFFFFFll;
-        } else {
-            y = mant << k;
-        }
-    } else if (k > -25) {
-        y = (mant + (1ll << (-k - 1))) >> (-k);
-    } else {
-        y = 0;
-    }
-    return (b >> 31) ? -y : y;
-}
-
-// Load time: ||x_i||_1 of every stacked row.
-__global__ void k_fx_row_l1(const int64_t *__restrict__ row_ptr, const float *__restrict__ val,
-                            int64_t N, float *l1) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) s += fabsf(val[e]);
-        l1[r] = s;
-    }
-}
-
-// Load time: max over the columns of sum_{i in col j} |x_ij| ||x_i||_1, one
-// warp per column over its segments; the maximum of non-negative doubles by
-// an integer atomicMax on their bit patterns (order-free).
-__global__ void k_fx_col_bound(const uint32_t *__restrict__ csc_row,
-                               const float *__restrict__ csc_val,
-                               const int64_t *__restrict__ seg_start,
-                               const int64_t *__restrict__ seg_end,
-                               const int64_t *__restrict__ col_seg, int nblk, int32_t J,
-                               const float *__restrict__ l1, SmallState *st) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; j < J; j += nwarps) {
-        double acc = 0.0;
-        for (int bk = 0; bk < nblk; ++bk) {
-            const int64_t v = (int64_t)bk * J + j;
-            for (int64_t sg = col_seg[v]; sg < col_seg[v + 1]; ++sg)
-                for (int64_t e = seg_start[sg] + lane; e < seg_end[sg]; e += 32)
-                    acc += (double)fabsf(csc_val[e]) * (double)l1[csc_row[e]];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULLMASK, acc, o);
-        if (lane == 0)
-            atomicMax(reinterpret_cast<unsigned long long *>(&st->fx_dmax),
-                      (unsigned long long)__double_as_longlong(acc));
-    }
-}
-
-// Every iteration: max_k max|T_k| |w_kr| into st->fx_tw (float bits; zero
-// on entry), one warp per subject.
-__global__ void __launch_bounds__(256) k_fx_tw(const float *__restrict__ T,
-                                               const float *__restrict__ W, int64_t K, int R,
-                                               SmallState *st) {
-    __shared__ unsigned int red[P2_RMAX];
-    for (int i = threadIdx.x; i < R; i += blockDim.x) red[i] = 0u;
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; k < K; k += nwarps) {
-        float m = 0.f;
-        const float *Tk = T + (size_t)k * R * R;
-        for (int e = lane; e < R * R; e += 32) m = fmaxf(m, fabsf(Tk[e]));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULLMASK, m, o));
-        for (int r = lane; r < R; r += 32) {
-            const float v = m * fabsf(W[(size_t)k * R + r]);
-            atomicMax(&red[r], (unsigned int)__float_as_int(v));
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < R; i += blockDim.x) atomicMax(&st->fx_tw[i], red[i]);
-}
-
-// Every iteration (one block): the scale exponents S_r from the bound, then
-// fx_tw cleared for the next iteration.
-template <class S>
-__global__ void k_fx_scale(const S *__restrict__ V, int32_t J, const float *__restrict__ H,
-                           int R, SmallState *st) {
-    __shared__ float vred[32];
-    const int VS = v_stride<S>(R);
-    float vm = 0.f;
-    for (int64_t e = threadIdx.x; e < (int64_t)J * R; e += blockDim.x) {
-        const int64_t j = e / R;
-        vm = fmaxf(vm, fabsf(Stor<S>::ldp(V + j * VS + (e - j * R))));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) vm = fmaxf(vm, __shfl_xor_sync(FULLMASK, vm, o));
-    if ((threadIdx.x & 31) == 0) vred[threadIdx.x >> 5] = vm;
-    __syncthreads();
-    if (threadIdx.x < R) {
-        float vmax = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) vmax = fmaxf(vmax, vred[w]);
-        const int r = threadIdx.x;
-        double hn = 0.0;
-        for (int v = 0; v < R; ++v) hn += fabs((double)H[v * R + r]);
-        const double tw = (double)__int_as_float((int)st->fx_tw[r]);
-        const double B = 2.0 * R * (double)vmax * hn * tw * st->fx_dmax;
-        int sh = 0;
-        if (B > 0.0 && isfinite(B)) {
-            int e2 = 0;
-            frexp(B, &e2);                          // B < 2^e2
-            sh = 61 - e2;
-        }
-        st->fx_shift[r] = sh < -120 ? -120 : (sh > 120 ? 120 : sh);
-    }
-    __syncthreads();
-    if (threadIdx.x < R) st->fx_tw[threadIdx.x] = 0u;
-}
-
-// The pass: pass beta's rows of P (as k_beta_p), each non-zero's terms added
-// at once; columns below JH (the hottest, first after the relabel) into this
-// block's shared accumulators, flushed at the end, the others into acc.
-template <int CB, class S, int RT = 0>
-__global__ void __launch_bounds__(256, 3) k_beta_fx(XView X, const S *__restrict__ V,
-                                                    const float *__restrict__ H,
-                                                    const float *__restrict__ T,
-                                                    const float *__restrict__ W,
-                                                    SmallState *st, unsigned long long *acc,
-                                                    int R_rt, int JH) {
-    const int R = RT > 0 ? RT : R_rt;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int RS = row_stride(R);
-    float *Hs = reinterpret_cast<float *>(smem_raw);
-    const size_t cta_bytes = ((size_t)R * R * 4 + 15) & ~(size_t)15;
-    const int nw = blockDim.x >> 5;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int FS = f_stride(R);
-    float *zo = reinterpret_cast<float *>(smem_raw + cta_bytes + warp * beta_warp_bytes(R));
-    float *Fk = zo + 32 * RS;
-    float *Tk = Fk + R * FS;
-    float *wk = Tk + R * R;
-    unsigned long long *hot =
-        reinterpret_cast<unsigned long long *>(smem_raw + cta_bytes + nw * beta_warp_bytes(R));
-    for (int i = threadIdx.x; i < R * R; i += blockDim.x) Hs[i] = H[i];
-    for (int i = threadIdx.x; i < JH * R; i += blockDim.x) hot[i] = 0ull;
-    int sh[CB];
-#pragma unroll
-    for (int c = 0; c < CB; ++c) sh[c] = c < R ? st->fx_shift[c] : 0;
-    __syncthreads();
-    const int64_t nwarps = (int64_t)gridDim.x * nw;
-    for (int64_t ki = (int64_t)blockIdx.x * nw + warp; ki < X.K; ki += nwarps) {
-        const int64_t k = X.order ? (int64_t)X.order[ki] : ki;
-        const int64_t r0 = X.subj_row[k], r1 = X.subj_row[k + 1];
-        if (r1 == r0) continue;
-        int64_t base = X.subj_nnz[k];
-        const float *Tg = T + (size_t)k * R * R;
-        for (int e = lane; e < R * R; e += 32) Tk[e] = Tg[e];
-        for (int s = lane; s < R; s += 32) wk[s] = W[(size_t)k * R + s];
-        __syncwarp();
-        RowCol us(lane, R);
-        for (int e = lane; e < R * R; e += 32, us.next(R)) {
-            float f = 0.f;
-            for (int r = 0; r < R; ++r) f = fmaf(Tk[r * R + us.r], Hs[r * R + us.c], f);
-            Fk[us.r * FS + us.c] = f * wk[us.c];
-        }
-        for (int e = lane; e < R * (FS - R); e += 32) {
-            const int u = e / (FS - R);
-            Fk[u * FS + R + (e - u * (FS - R))] = 0.f;
-        }
-        __syncwarp();
-        for (int64_t cr = r0; cr < r1; cr += 32) {
-            const int nr = (int)((r1 - cr) < 32 ? (r1 - cr) : 32);
-            const int len = (lane < nr) ? (int)X.row_len[cr + lane] : 0;
-            const int off = warp_excl_scan(len, lane);
-            const int tot = __shfl_sync(FULLMASK, off + len, 31);
-            gather_rows<CB, false, S>(X, nr, base, len, off, V, nullptr, zo, nullptr, R, RS, lane);
-            __syncwarp();
-            if (lane < nr) {
-                const float *zr = zo + lane * RS;
-                float p[CB];
-#pragma unroll
-                for (int c = 0; c < CB; ++c) p[c] = 0.f;
-                for (int u = 0; u < R; ++u) {
-                    const float a = zr[u];
-                    const float4 *f4 = reinterpret_cast<const float4 *>(Fk + u * FS);
-#pragma unroll
-                    for (int q = 0; q < CB / 4; ++q) {
-                        if (4 * q < R) {
-                            const float4 f = f4[q];
-                            p[4 * q] = fmaf(a, f.x, p[4 * q]);
-                            p[4 * q + 1] = fmaf(a, f.y, p[4 * q + 1]);
-                            p[4 * q + 2] = fmaf(a, f.z, p[4 * q + 2]);
-                            p[4 * q + 3] = fmaf(a, f.w, p[4 * q + 3]);
-                        }
-                    }
-                }
-                // bfloat16 storage keeps P in bfloat16: round as the stored rows would be
-                if (sizeof(S) == 2) {
-#pragma unroll
-                    for (int c = 0; c < CB; ++c) p[c] = __bfloat162float(__float2bfloat16_rn(p[c]));
-                }
-                const int64_t b0 = base + off;
-                for (int e = 0; e < len; ++e) {
-                    const int j = X.col[b0 + e];
-                    const float x = X.val[b0 + e];
-                    unsigned long long *dst = j < JH ? hot + (size_t)j * R : acc + (size_t)j * R;
-#pragma unroll
-                    for (int c = 0; c < CB; ++c) {
-                        if (c < R) {
-                            const long long v = fx_fixed(x * p[c], sh[c], &st->flags);
-                            if (v) atomicAdd(dst + c, (unsigned long long)v);
-                        }
-                    }
-                }
-            }
-            __syncwarp();
-            base += tot;
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < JH * R; i += blockDim.x)
-        if (hot[i]) atomicAdd(acc + i, hot[i]);
-}
-
-// M2(j, r) = acc(j, r) 2^-S_r
-__global__ void k_fx_finish(const unsigned long long *__restrict__ acc,
-                            const SmallState *__restrict__ st, double *M2, int64_t n, int R) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i % R);
-        M2[i] = ldexp((double)(long long)acc[i], -st->fx_shift[r]);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Pass beta, part 2: M2(j, :) = sum over the non-zeros x of column j of
 // x * P(row, :), read column-major.  One warp per column segment (at most
 // P2_SEG non-zeros), one lane per non-zero (32 rows of P in flight per
@@ -1858,19 +1605,6 @@ struct RankBlock {
     static constexpr int cb = R <= 8 ? 8 : R <= 16 ? 16 : R <= 32 ? 32 : (R + 7) / 8 * 8;
 };
 
-template <class S, int R0>
-static int allow_fx_one(int cap) {
-    if constexpr (R0 <= 16)
-        return allow_dynamic_smem(k_beta_fx<RankBlock<R0>::cb, S, R0>, cap, "k_beta_fx");
-    return P2_OK;
-}
-template <class S, int... Rs>
-static int allow_fx(int cap, std::integer_sequence<int, Rs...>) {
-    int rc = P2_OK;
-    ((rc = rc != P2_OK ? rc : allow_fx_one<S, Rs>(cap)), ...);
-    return rc;
-}
-
 template <class S, int... Rs>
 static int allow_rank_kernels(int cap, std::integer_sequence<int, Rs...>) {
     int rc = P2_OK;
@@ -1907,7 +1641,6 @@ static int configure_sparse(int cap) {
     if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<8, S, float>, cap, "k_beta_p");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<16, S, float>, cap, "k_beta_p");
     if (rc == P2_OK) rc = allow_dynamic_smem(k_beta_p<32, S, float>, cap, "k_beta_p");
-    if (rc == P2_OK) rc = allow_fx<S>(cap, RankList{});
     return rc;
 }
 
@@ -2192,96 +1925,6 @@ static int enqueue_mode2_blocks(p2_ctx *c, const Launch &L) {
     return P2_OK;
 }
 
-// Fixed-point mode 2 (R <= 16): the pass with its hot-column accumulators
-// sized for three blocks per SM.
-template <int CB, class S, int RT>
-static void launch_beta_fx_k(p2_ctx *c, const Launch &L) {
-    const int nt = L.beta_warps * 32;
-    const int R = c->R;
-    const size_t base = L.beta_smem;
-    const size_t budget = (size_t)c->geo.smem_optin / 3;
-    int64_t jh = budget > base ? (int64_t)((budget - base) / (8 * (size_t)R)) : 0;
-    if (jh > c->X.J) jh = c->X.J;
-    const size_t smem = base + (size_t)jh * R * sizeof(unsigned long long);
-    dim3 grid(c->geo.nsm * resident_blocks(c, k_beta_fx<CB, S, RT>, nt, smem));
-    k_beta_fx<CB, S, RT><<<grid, dim3(nt), smem, c->stream>>>(
-        xview(c), Bufs<S>::V(c), c->d_H, c->d_T, c->d_W, c->d_s, c->d_fxacc, R, (int)jh);
-}
-template <class S, int R0>
-static bool launch_beta_fx_if(p2_ctx *c, const Launch &L) {
-    if constexpr (R0 <= 16) {
-        if (c->R == R0) {
-            launch_beta_fx_k<RankBlock<R0>::cb, S, R0>(c, L);
-            return true;
-        }
-    }
-    return false;
-}
-template <class S, int... Rs>
-static void launch_beta_fx_ranks(p2_ctx *c, const Launch &L, std::integer_sequence<int, Rs...>) {
-    (launch_beta_fx_if<S, Rs>(c, L) || ...);
-}
-
-template <class S>
-static int enqueue_mode2_fx_t(p2_ctx *c, const Launch &L) {
-    cudaStream_t s = c->stream;
-    const int R = c->R;
-    const int64_t J = c->X.J, K = c->X.K, nJR = J * R;
-    const int nsm = c->geo.nsm;
-    P2_CUDA_TRY(cudaMemsetAsync(c->d_fxacc, 0, sizeof(unsigned long long) * (size_t)nJR, s));
-    const int tb = (int)std::min<int64_t>((K + 7) / 8, 4 * (int64_t)nsm);
-    k_fx_tw<<<tb > 0 ? tb : 1, 256, 0, s>>>(c->d_T, c->d_W, K, R, c->d_s);
-    P2_LAUNCH_CHECK("k_fx_tw");
-    k_fx_scale<S><<<1, 256, 0, s>>>(Bufs<S>::V(c), (int32_t)J, c->d_H, R, c->d_s);
-    P2_LAUNCH_CHECK("k_fx_scale");
-    launch_beta_fx_ranks<S>(c, L, RankList{});
-    P2_LAUNCH_CHECK("k_beta_fx");
-    const int fb = (int)std::min<int64_t>((nJR + 255) / 256, 4 * (int64_t)nsm);
-    k_fx_finish<<<fb > 0 ? fb : 1, 256, 0, s>>>(c->d_fxacc, c->d_s, c->d_M2, nJR, R);
-    P2_LAUNCH_CHECK("k_fx_finish");
-    return P2_OK;
-}
-
-// Pass beta and the mode-2 MTTKRP into d_M2: fixed point, or the rows of P
-// reduced over the column-major copy.
-static int enqueue_mode2(p2_ctx *c, const Launch &L) {
-    if (c->fx) return c->bf16 ? enqueue_mode2_fx_t<bf16_t>(c, L) : enqueue_mode2_fx_t<float>(c, L);
-    const int rc = enqueue_mode2_blocks(c, L);
-    if (rc != P2_OK) return rc;
-    const int64_t J = c->X.J;
-    const int nsm = c->geo.nsm;
-    const int cb_blocks = (int)((J + 7) / 8 < 8 * nsm ? (J + 7) / 8 : 8 * nsm);
-    k_m2_columns<<<cb_blocks, 256, 0, c->stream>>>(c->d_segpart, c->X.col_seg, c->d_M2,
-                                                   (int32_t)J, c->X.nblk, c->R);
-    P2_LAUNCH_CHECK("k_m2_columns");
-    return P2_OK;
-}
-
-// Load time: the column bound of the fixed-point mode 2 (rows' L1 norms
-// from the caller's row pointers and values, then the column sums).
-int launch_fx_bound(p2_ctx *c, const int64_t *d_row_ptr, const float *d_val, int64_t N) {
-    cudaStream_t s = c->stream;
-    const int nsm = c->geo.nsm;
-    P2_CUDA_TRY(cudaMemsetAsync(&c->d_s->fx_dmax, 0, sizeof(double), s));
-    P2_CUDA_TRY(cudaMemsetAsync(c->d_s->fx_tw, 0, sizeof(c->d_s->fx_tw), s));
-    if (N <= 0) return P2_OK;
-    float *l1 = nullptr;
-    P2_CUDA_TRY(ctx_malloc(c, (void **)&l1, sizeof(float) * (size_t)N));
-    k_fx_row_l1<<<8 * nsm, 256, 0, s>>>(d_row_ptr, d_val, N, l1);
-    const int64_t J = c->X.J;
-    const int cb = (int)std::min<int64_t>((J + 7) / 8, 8 * (int64_t)nsm);
-    k_fx_col_bound<<<cb > 0 ? cb : 1, 256, 0, s>>>(c->X.csc_row, c->X.csc_val, c->X.seg_start,
-                                                   c->X.seg_end, c->X.col_seg, c->X.nblk,
-                                                   (int32_t)J, l1, c->d_s);
-    const cudaError_t e = cudaGetLastError();
-    ctx_free(c, l1);
-    if (e != cudaSuccess) {
-        set_error("load: fixed-point bound kernels failed: %s", cudaGetErrorString(e));
-        return P2_ECUDA;
-    }
-    return P2_OK;
-}
-
 // Q-step for the current (H, V, W) (Algorithm 2's SVD loop), then the
 // per-subject statistics that need it: mode-1 MTTKRP partials, W^TW,
 // max |W|, <W, M3>, and (with_fit) the loss of the completed iteration.
@@ -2394,7 +2037,7 @@ int tune_time_qstep(p2_ctx *c, int reps, float *ms) {
 int tune_time_mode2(p2_ctx *c, int reps, float *ms) {
     return tune_time(c, reps, ms, [c]() -> int {
         const Launch L = plan(c);
-        return enqueue_mode2(c, L);
+        return enqueue_mode2_blocks(c, L);
     });
 }
 
@@ -2414,11 +2057,15 @@ int enqueue_iteration(p2_ctx *c) {
     // pass beta: mode-2 MTTKRP
     mark(c, 1);
     {
-        const int rc = enqueue_mode2(c, L);
+        const int rc = enqueue_mode2_blocks(c, L);
         if (rc != P2_OK) return rc;
     }
     const int64_t nJR = J * R;
     const int fb = (int)((nJR + 255) / 256 < 4 * nsm ? (nJR + 255) / 256 : 4 * nsm);
+    const int cb_blocks = (int)((J + 7) / 8 < 8 * nsm ? (J + 7) / 8 : 8 * nsm);
+    k_m2_columns<<<cb_blocks, 256, 0, s>>>(c->d_segpart, c->X.col_seg, c->d_M2, (int32_t)J,
+                                           c->X.nblk, R);
+    P2_LAUNCH_CHECK("k_m2_columns");
     {                                           // sharded: M2 summed over the shards
         const int xrc = exchange(c, c->d_M2, nJR);
         if (xrc != P2_OK) return xrc;

@@ -245,8 +245,8 @@ static int build_csc(p2_ctx *c, const int64_t *d_row_ptr, const int32_t *h_count
         int64_t rows = 0;
         for (int b = 0; b < c->X.nblk; ++b)
             rows = std::max<int64_t>(rows, c->X.blk_row[b + 1] - c->X.blk_row[b]);
-        // the P buffer holds one block (no P buffer with the fixed-point mode 2)
-        if (!c->fx && rows < c->X.p_rows) {
+        // the P buffer holds one block
+        if (rows < c->X.p_rows) {
             void **pp = c->bf16 ? (void **)&c->d_Ph : (void **)&c->d_P;
             ctx_free(c, *pp);
             *pp = nullptr;
@@ -470,10 +470,6 @@ int launch_load(p2_ctx *c, const int64_t *d_subj_ptr, const int64_t *d_row_ptr,
     {
         int rc = build_csc(c, d_row_ptr, count_new.data(), N, nnz, J);
         if (rc != P2_OK) return rc;
-        if (c->fx) {
-            rc = launch_fx_bound(c, d_row_ptr, d_val, N);
-            if (rc != P2_OK) return rc;
-        }
     }
     P2_CUDA_TRY(cudaMemcpyAsync(&c->d_s->normx2, &nx2, sizeof(double), cudaMemcpyHostToDevice, s));
     P2_CUDA_TRY(cudaStreamSynchronize(s));

@@ -179,7 +179,6 @@ template <class T> inline T __ldg(const T *p) { return *p; }
 inline int __float_as_int(float f) { int i; memcpy(&i, &f, 4); return i; }
 inline float __int_as_float(int i) { float f; memcpy(&f, &i, 4); return f; }
 inline int __double2hiint(double d) { int64_t b; memcpy(&b, &d, 8); return (int)(b >> 32); }
-inline long long __double_as_longlong(double d) { long long b; memcpy(&b, &d, 8); return b; }
 std::mutex &emu_atomic_mutex();
 template <class T, class U> inline T atomicAdd(T *p, U v) { std::lock_guard<std::mutex> g(emu_atomic_mutex()); T o = *p; *p = o + (T)v; return o; }
 template <class T, class U> inline T atomicOr(T *p, U v) { std::lock_guard<std::mutex> g(emu_atomic_mutex()); T o = *p; *p = o | (T)v; return o; }

@@ -207,27 +207,6 @@ def tc_case(R, K):
     return out
 
 
-def fx_case(R, K, precision="fp32"):
-    """Mode 2 in fixed point (integer atomics, hot columns in shared memory)
-    against the FP32 Kahan sums over the column-major copy, and both against
-    the oracle, after one iteration."""
-    X = synth.generate("c63m", K=K)
-    H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=43)
-    if precision == "bf16":
-        V0 = bf16_round(V0)
-    out = {}
-    for fx in (True, False):
-        with p2.Parafac2(R, use_graph=False, mode2_fixed_point=fx, precision=precision) as m:
-            m.load(X)
-            m.init(H0, V0, W0)
-            m.iterate(1)
-            out[fx] = (m.mttkrp(2), m.factors()[1])
-    ref = P.als_iteration(P.all_blocks(X), H0.astype(np.float64), V0.astype(np.float64),
-                          W0.astype(np.float64))
-    return {"M2_fx_vs_kahan": rel_fro(out[True][0], out[False][0]),
-            "M2": rel_fro(out[True][0], ref["M2"]), "V": rel_fro(out[True][1], ref["V"])}
-
-
 def split_case(R, K):
     """The split Procrustes step (QR recorder) against the fused kernel, and
     with a record capacity small enough that most subjects go to the fused
@@ -319,8 +298,6 @@ if __name__ == "__main__":
         out = rational_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "blocks":
         out = blocks_case(int(sys.argv[2]), int(sys.argv[3]))
-    elif kind == "fx":
-        out = fx_case(int(sys.argv[2]), int(sys.argv[3]), sys.argv[4] if len(sys.argv) > 4 else "fp32")
     elif kind == "tc":
         out = tc_case(int(sys.argv[2]), int(sys.argv[3]))
     elif kind == "split":

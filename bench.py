@@ -184,6 +184,8 @@ TRAFFIC_SOURCES = {
     "k_polar_reg": ("p2_dw.cuh", "p2_num.cuh", "p2_eig_dw.cuh", "p2_polar.cu", "p2_polar.cuh"),
     "k_polar_split": ("p2_dw.cuh", "p2_num.cuh", "p2_polar.cu", "p2_polar.cuh",
                       "p2_polar_grp.cu", "p2_polar_grp.cuh", "p2_polar_grp_launch.cuh"),
+    "k_polar_reg_split": ("p2_dw.cuh", "p2_num.cuh", "p2_eig_dw.cuh", "p2_polar.cu",
+                          "p2_polar.cuh", "p2_polar_grp.cuh"),
 }
 
 
@@ -298,17 +300,27 @@ def run_reference(args, w):
     return 0
 
 
-def roofline(X, R, phase_ms, flops, wname):
-    """Roofline of the dominant kernel group and the sparse passes' GB/s."""
+def roofline(X, R, phase_ms, flops, wname, split=True):
+    """Roofline of the dominant kernel group and the sparse passes' GB/s
+    (split: whether the Procrustes step ran split into its three kernels)."""
     dom = max(phase_ms, key=phase_ms.get)
     bmodel = _bytes_model(X, R)
     hbm_peak, hbm_src = _peaks()
     if dom == "procrustes":
         ach = flops / (phase_ms[dom] / 1e3) / 1e12
-        kname = ("k_polar_reg (double-word Procrustes, one lane per subject)" if R <= 12 else
-                 "split double-word Procrustes step: k_polar_grp<MODE 1> (Householder, a group "
-                 "of 8 or 16 lanes per subject), k_qr_record (QR, one lane per subject), "
-                 "k_polar_grp<MODE 2> (rotations applied, T_k)")
+        if R <= 12 and split:
+            kname = ("split double-word Procrustes step: k_polar_reg<MODE 1> (M, Householder, "
+                     "one lane per subject), k_qr_record (QR, one lane per subject), "
+                     "k_polar_reg<MODE 2> (rotations applied, T_k)")
+            tkey = "k_polar_reg_split"
+        elif R <= 12:
+            kname = "k_polar_reg (double-word Procrustes, one lane per subject)"
+            tkey = "k_polar_reg"
+        else:
+            kname = ("split double-word Procrustes step: k_polar_grp<MODE 1> (Householder, a "
+                     "group of 8 or 16 lanes per subject), k_qr_record (QR, one lane per "
+                     "subject), k_polar_grp<MODE 2> (rotations applied, T_k)")
+            tkey = "k_polar_split"
         roof = {"kernel": kname, "bound": "alu",
                 "achieved": ach, "peak": DW_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / DW_PEAK_TFLOPS,
@@ -316,7 +328,7 @@ def roofline(X, R, phase_ms, flops, wname):
                 f"{DW_INSTR_PER_FMA} FP32 instructions per double-word multiply-add",
                 "vs_fp64_nominal": ach / FP64_PEAK_TFLOPS,
                 "algorithmic_flops_per_launch": flops,
-                "traffic": _traffic("k_polar_reg" if R <= 12 else "k_polar_split", wname)}
+                "traffic": _traffic(tkey, wname)}
     else:
         by = bmodel.get(dom, 0)
         ach = by / (phase_ms[dom] / 1e3) / 1e9
@@ -364,7 +376,8 @@ def measure_workload(X, w, precision, steps, warmup, device, gpu_id, fp64_procru
     tune = m.tuning()
     m.close()
     ms = t["ms_total"] / steps
-    roof, sparse = roofline(X, R, t["phase_ms"], t["flops"], w.name)
+    roof, sparse = roofline(X, R, t["phase_ms"], t["flops"], w.name,
+                            split=tune.get("procrustes_split") == 1)
     if tune.get("procrustes_split") == 0 and R > 12 and roof.get("bound") == "alu":
         roof["kernel"] = "k_polar_grp (fused double-word Procrustes, 8 or 16 lanes per subject)"
         roof["traffic"] = None
@@ -458,6 +471,8 @@ def run_p2(args, w):
     stream = torch.cuda.Stream()
     m = p2.Parafac2(R, device=local, stream=stream.cuda_stream, timing=True,
                     tensor_core_m=args.tensor_core_m)
+    if args.procrustes_split is not None:
+        m.set_tuning(procrustes_split=args.procrustes_split)
     m.load(X)
     m.init(H0, V0, W0)
     for _ in range(args.warmup):
@@ -475,7 +490,8 @@ def run_p2(args, w):
     ms_step = ms_total / args.steps
     value = job_throughput(X.nnz, args.steps, ms_total, world)
 
-    roof, sparse = roofline(X, R, phase_ms, t["flops"], w.name)
+    roof, sparse = roofline(X, R, phase_ms, t["flops"], w.name,
+                            split=m.tuning()["procrustes_split"] == 1)
 
     # end-to-end through the public API from pinned host buffers
     e2e = None
@@ -673,8 +689,13 @@ def main(argv=None):
     ap.add_argument("--tensor-core-m", choices=["auto", "on", "off"], default="auto",
                     help="form the Procrustes step's M on the tensor cores (auto: the "
                          "library's default, off)")
+    ap.add_argument("--procrustes-split", choices=["auto", "on", "off"], default="auto",
+                    help="headline workload: the Procrustes step split into its Householder, "
+                         "QR-recording and rotation kernels, or fused (auto: the library's "
+                         "default, on)")
     args = ap.parse_args(argv)
     args.tensor_core_m = {"auto": None, "on": True, "off": False}[args.tensor_core_m]
+    args.procrustes_split = {"auto": None, "on": 1, "off": 0}[args.procrustes_split]
     if args.warmup < 3:
         args.warmup = 3
     import synth

@@ -97,7 +97,7 @@ typedef struct {
 /* Launch choices that change the speed, never the results (every choice
  * computes the same values bit for bit). */
 typedef struct {
-    int32_t procrustes_split;  /* R > 12, double-word Procrustes step: 1 (default) = split into
+    int32_t procrustes_split;  /* R >= 2, double-word Procrustes step: 1 (default) = split into
                                   a Householder kernel, a one-lane-per-subject QR kernel that
                                   records its Givens rotations, and a kernel that applies them;
                                   0 = one fused kernel */

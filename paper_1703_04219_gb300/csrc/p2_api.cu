@@ -184,7 +184,7 @@ static int alloc_data(p2_ctx *c, int64_t K, int32_t J, int64_t N, int64_t nnz) {
     P2_CUDA_TRY(cudaMemsetAsync(c->d_M3, 0, sizeof(float) * (size_t)K * R, c->stream));
     c->h_perm_new2old = new int32_t[J];
     c->h_perm_old2new = new int32_t[J];
-    if (R > 12 && K > 0) {
+    if (R >= 2 && K > 0 && !c->opt.fp64_procrustes) {
         // scratch of the split Procrustes step for one chunk of subjects: at
         // most 8 GiB and an eighth of the free memory, a chunk of at least 4,096
         // subjects (otherwise the fused kernel runs)
@@ -711,7 +711,7 @@ static int autotune(p2_ctx *c) {
     }
     char note[256];
     float q_split = -1.f, q_fused = -1.f;
-    if (c->R > 12 && c->d_split && !c->opt.fp64_procrustes) {
+    if (c->R >= 2 && c->d_split && !c->opt.fp64_procrustes) {
         for (int split = 1; split >= 0; --split) {
             c->tune.procrustes_split = split;
             float ms = 0.f;

@@ -42,6 +42,9 @@ static __device__ __forceinline__ void store_out(double *p, dw v) {
 template <int R>
 __host__ __device__ constexpr int nnls_lane_dws() { return R * (R + 1) / 2 + 5 * R; }
 
+constexpr int NNLS_THREADS = 128;     // threads per block of k_nnls_rows (a constant
+                                      // stride: the lanes' entries provably distinct)
+
 template <int R>
 size_t nnls_smem(int nt) {
     return (size_t)R * R * sizeof(dw) + (size_t)nt * nnls_lane_dws<R>() * sizeof(dw) +
@@ -51,14 +54,15 @@ size_t nnls_smem(int nt) {
 // Rows r of `rows` (n x R, FP32 or FP64) -> out (n x R, FP32 or FP64);
 // passive[r] holds the row's passive set (bit j: x_j > 0) in and out.
 template <int R, class B, class O>
-__global__ void __launch_bounds__(128, 1) k_nnls_rows(const double *__restrict__ Xa,
+__global__ void __launch_bounds__(NNLS_THREADS, 1) k_nnls_rows(const double *__restrict__ Xa,
                                                    const double *__restrict__ Xb,
                                                    const B *__restrict__ rows, int64_t n,
                                                    uint64_t *passive, O *out) {
     constexpr int LP = R * (R + 1) / 2;
     constexpr int DWS = nnls_lane_dws<R>();
     extern __shared__ __align__(16) dw sn[];
-    const int NT = blockDim.x, t = threadIdx.x;
+    constexpr int NT = NNLS_THREADS;
+    const int t = threadIdx.x;
     dw *As = sn;                                   // R x R, A = Xa * Xb
     for (int e = t; e < R * R; e += NT) As[e] = to_dw(Xa[e] * Xb[e]);
     __syncthreads();
@@ -66,14 +70,14 @@ __global__ void __launch_bounds__(128, 1) k_nnls_rows(const double *__restrict__
     for (int e = 0; e < R * R; ++e) scale_a = fmaxf(scale_a, fabsf(As[e].h));
     dw *lane = sn + R * R + t;
     unsigned char *ix = reinterpret_cast<unsigned char *>(sn + R * R + (size_t)DWS * NT) + t;
-    auto S = [lane, NT](int e) -> dw & { return lane[(size_t)e * NT]; };
+    auto S = [lane](int e) -> dw & { return lane[(size_t)e * NT]; };
     auto L = [&](int a, int c) -> dw & { return S(a * (a + 1) / 2 + c); };
     auto RD = [&](int a) -> dw & { return S(LP + a); };
     auto Y = [&](int a) -> dw & { return S(LP + R + a); };
     auto X = [&](int j) -> dw & { return S(LP + 2 * R + j); };
     auto Z = [&](int j) -> dw & { return S(LP + 3 * R + j); };
     auto Bv = [&](int j) -> dw & { return S(LP + 4 * R + j); };
-    auto IDX = [ix, NT](int a) -> unsigned char & { return ix[(size_t)a * NT]; };
+    auto IDX = [ix](int a) -> unsigned char & { return ix[(size_t)a * NT]; };
     const dw zero = dw_f(0.f), one = dw_f(1.f);
 
     // z_P = A_PP^{-1} b_P (Cholesky), z = 0 off P; returns the mask of the
@@ -422,7 +426,7 @@ template <int R, class B, class O>
 static cudaError_t launch_nnls_t(const p2_ctx *c, const double *Xa, const double *Xb,
                                  const B *rows, int64_t n, uint64_t *passive, O *out,
                                  cudaStream_t s) {
-    const int nt = 128;
+    const int nt = NNLS_THREADS;
     const size_t smem = nnls_smem<R>(nt);
     const int64_t want = (n + nt - 1) / nt;
     const int64_t cap = (int64_t)c->geo.nsm * 8;

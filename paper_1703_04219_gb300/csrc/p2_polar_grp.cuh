@@ -65,8 +65,9 @@ static __device__ __forceinline__ unsigned long long group_or(unsigned mask, uns
     return v;
 }
 
-// Scratch of the split Procrustes step (R > 12): kernel MODE 1 reduces each
-// subject of a chunk to tridiagonal form and stores Q_h (row-major), d, e,
+// Scratch of the split Procrustes step: kernel MODE 1 (of k_polar_grp for
+// R > 12, of the lane kernel k_polar_reg below) reduces each
+// subject of a chunk to tridiagonal form and stores Q_h, d, e,
 // w' and the output exponent (meta, GRP_ZERO for a zero subject);
 // k_qr_record runs the QR iteration on (d, e) alone, one lane per subject,
 // and records every Givens rotation (cap per subject; nrec = -1 when they
@@ -86,8 +87,14 @@ template <class D> struct GrpSplit {
     RotRec<D> *rec = nullptr;
     uint8_t *rkr = nullptr;
     int32_t *nrec = nullptr;
-    int64_t cap = 0;                // records per subject slot (the stride)
+    int64_t cap = 0;                // records per subject slot
     int64_t lim = 0;                // records a subject may use (<= cap)
+    // record n of slot i at rec[i * rsub + n * rstep] (rsub = 0: cap, the
+    // grouped kernel's layout; the lane kernel interleaves the records of a
+    // chunk's slots: rsub = 1, rstep = chunk)
+    int64_t rsub = 0, rstep = 1;
+    // lane kernel: Q_h entry (r, c) of slot i at qh[(r R + c) chunk + i]
+    int64_t chunk = 0;
     const int32_t *kdev = nullptr;
     // nullable: every subject's M' (packed lower, indexed by subject), formed
     // on the tensor cores; the kernels then load it instead of forming it
@@ -666,19 +673,22 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
 // recurrence redundantly; here one lane serves a subject, so the recurrence
 // costs 1/16 of the warp instructions it did there.
 // ---------------------------------------------------------------------------
+constexpr int QR_THREADS = 128;       // threads per block of k_qr_record (a constant
+                                      // stride: the lanes' d, e provably distinct)
 template <int RT, class D>
-__global__ void __launch_bounds__(128) k_qr_record(GrpSplit<D> sc, int64_t K, int R_rt,
+__global__ void __launch_bounds__(QR_THREADS) k_qr_record(GrpSplit<D> sc, int64_t K, int R_rt,
                                                    const int32_t *__restrict__ order,
                                                    int32_t *qrcnt, SmallState *st) {
     const int R = RT > 0 ? RT : R_rt;
     extern __shared__ __align__(16) unsigned char sqr_raw[];
     D *smq = reinterpret_cast<D *>(sqr_raw);
-    const int t = threadIdx.x, NT = blockDim.x;
+    const int t = threadIdx.x;
+    constexpr int NT = QR_THREADS;
     const int64_t slot = (int64_t)blockIdx.x * NT + t;
     D *dv = smq + t;
     D *ev = smq + (size_t)R * NT + t;
-    auto d = [dv, NT](int i) -> D & { return dv[(size_t)i * NT]; };
-    auto e = [ev, NT](int i) -> D & { return ev[(size_t)i * NT]; };
+    auto d = [dv](int i) -> D & { return dv[(size_t)i * NT]; };
+    auto e = [ev](int i) -> D & { return ev[(size_t)i * NT]; };
     const D one = num_f<D>(1.f), zero = num_f<D>(0.f);
     unsigned long long flops = 0;
     if (slot < K && sc.meta[slot] != GRP_ZERO) {
@@ -688,8 +698,9 @@ __global__ void __launch_bounds__(128) k_qr_record(GrpSplit<D> sc, int64_t K, in
             d(i) = de[i];
             e(i) = de[R + i];
         }
-        RotRec<D> *rec = sc.rec + (size_t)slot * sc.cap;
-        uint8_t *rkr = sc.rkr + (size_t)slot * sc.cap;
+        const int64_t rs = sc.rsub ? sc.rsub : sc.cap;
+        RotRec<D> *rec = sc.rec + (size_t)slot * rs;
+        uint8_t *rkr = sc.rkr + (size_t)slot * rs;
         int64_t n = 0;
         bool full = false;
         float an = 0.f;
@@ -769,8 +780,8 @@ __global__ void __launch_bounds__(128) k_qr_record(GrpSplit<D> sc, int64_t K, in
                 full = true;
                 break;
             }
-            rec[n] = RotRec<D>{c, s};
-            rkr[n] = (uint8_t)kr;
+            rec[n * sc.rstep] = RotRec<D>{c, s};
+            rkr[n * sc.rstep] = (uint8_t)kr;
             ++n;
             if (kr > p) e(kr - 1) = rr;
             d(kr) = dkn;

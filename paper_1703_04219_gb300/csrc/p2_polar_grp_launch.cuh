@@ -80,7 +80,7 @@ static void launch_grp_split(const p2_ctx *c, const dw *G, const float *W, Small
     const int R = c->R;
     GrpSplit<dw> sc = split_scratch(c, mpre);
     const int64_t CH = c->split_chunk;
-    const int nt = 128;
+    const int nt = QR_THREADS;
     const size_t smb = (size_t)2 * R * nt * sizeof(dw);
     for (int64_t c0 = 0; c0 < K; c0 += CH) {
         const int64_t n = (K - c0) < CH ? (K - c0) : CH;

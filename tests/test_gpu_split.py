@@ -1,11 +1,12 @@
-"""The split Procrustes step for R > 12 (p2_tuning.procrustes_split): a
-Householder kernel stores Q_h and the tridiagonal, a one-lane-per-subject
-kernel runs the QR iteration and records its Givens rotations, and a third
-kernel applies them to Q_h and forms T_k; subjects whose rotations exceed
-the record are finished by the fused kernel.  The arithmetic and its order
-are the fused kernel's, so T_k, the factors and the MTTKRPs must be the same
-bit for bit, with and without the fallback (a small record capacity), on
-the rank-compiled and the generic instances."""
+"""The split Procrustes step (p2_tuning.procrustes_split): a Householder
+kernel stores Q_h and the tridiagonal, a one-lane-per-subject kernel runs
+the QR iteration and records its Givens rotations, and a third kernel
+applies them to Q_h and forms T_k; subjects whose rotations exceed the
+record are finished by the fused kernel.  The arithmetic and its order are
+the fused kernel's, so T_k, the factors and the MTTKRPs must be the same
+bit for bit, with and without the fallback (a small record capacity), for
+the lane-per-subject kernel (R <= 12) and the grouped kernel's
+rank-compiled and generic instances (R > 12)."""
 import numpy as np
 import pytest
 
@@ -21,7 +22,9 @@ def p2():
 
 
 @pytest.mark.parametrize("name,K,R", [("c250m", 3000, 40), ("c250m", 1500, 24),
-                                      ("tiny", 150, 13), ("c250m", 800, 20), ("tiny", 80, 64)])
+                                      ("tiny", 150, 13), ("c250m", 800, 20), ("tiny", 80, 64),
+                                      ("c63m", 5000, 10), ("tiny", 300, 5), ("c63m", 700, 12),
+                                      ("tiny", 100, 2)])
 def test_split_procrustes_is_bitwise_the_fused_kernel(p2, name, K, R):
     X = synth.generate(name, K=K)
     H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=23)

@@ -76,10 +76,32 @@ P2_HD void tridiagonalize_dw(int n_rt, DwMat<D> A, DwVec<D> d, DwVec<D> e) {
         for (int i = k + 2; i < n; ++i) A(i, k) = dw_mul(A(i, k), inv_v0);
         A(k, k + 1) = b;
         e[k] = beta;
-        // p = b A22 v (A22 symmetric, lower triangle stored), K = b/2 p^T v
+        // p = b A22 v (A22 symmetric, lower triangle stored), K = b/2 p^T v;
+        // rows in pairs (two independent sums interleaved), pv in row order
         acc_t<D> pv = acc0<D>();
-        for (int i = k + 1; i < n; ++i) {
-            acc_t<D> s = acc_from(A(i, k + 1));          // v_{k+1} = 1
+        int i2 = k + 1;
+        for (; i2 + 1 < n; i2 += 2) {
+            const int i = i2;
+            acc_t<D> s0 = acc_from(A(i, k + 1));         // v_{k+1} = 1
+            acc_t<D> s1 = acc_from(A(i + 1, k + 1));
+            for (int j = k + 2; j < n; ++j) {
+                const D vj = A(j, k);
+                acc_fma(s0, (j <= i) ? A(i, j) : A(j, i), vj);
+                acc_fma(s1, (j <= i + 1) ? A(i + 1, j) : A(j, i + 1), vj);
+            }
+            const D si0 = dw_mul(acc_val(s0), b);
+            const D si1 = dw_mul(acc_val(s1), b);
+            t[i] = si0;
+            t[i + 1] = si1;
+            if (i == k + 1)
+                acc_add(pv, si0);
+            else
+                acc_fma(pv, si0, A(i, k));
+            acc_fma(pv, si1, A(i + 1, k));
+        }
+        if (i2 < n) {
+            const int i = i2;
+            acc_t<D> s = acc_from(A(i, k + 1));
             for (int j = k + 2; j < n; ++j) acc_fma(s, (j <= i) ? A(i, j) : A(j, i), A(j, k));
             const D si = dw_mul(acc_val(s), b);
             t[i] = si;
@@ -94,13 +116,27 @@ P2_HD void tridiagonalize_dw(int n_rt, DwMat<D> A, DwVec<D> d, DwVec<D> e) {
         for (int i = k + 1; i < n; ++i) {                // A22 -= v w^T + w v^T
             const D nvi = dw_neg((i == k + 1) ? one : A(i, k));
             const D nwi = dw_neg(t[i]);
-            for (int j = k + 1; j <= i; ++j) {
+            {                                            // j = k + 1: v_{k+1} = 1
+                acc_t<D> a = acc_from(A(i, k + 1));
+                acc_fma(a, nvi, t[k + 1]);
+                acc_add(a, nwi);
+                A(i, k + 1) = acc_val(a);
+            }
+            int j = k + 2;
+            for (; j + 1 <= i; j += 2) {                 // entries in pairs
+                acc_t<D> a0 = acc_from(A(i, j));
+                acc_t<D> a1 = acc_from(A(i, j + 1));
+                acc_fma(a0, nvi, t[j]);
+                acc_fma(a1, nvi, t[j + 1]);
+                acc_fma(a0, nwi, A(j, k));
+                acc_fma(a1, nwi, A(j + 1, k));
+                A(i, j) = acc_val(a0);
+                A(i, j + 1) = acc_val(a1);
+            }
+            if (j <= i) {
                 acc_t<D> a = acc_from(A(i, j));
                 acc_fma(a, nvi, t[j]);
-                if (j == k + 1)
-                    acc_add(a, nwi);
-                else
-                    acc_fma(a, nwi, A(j, k));
+                acc_fma(a, nwi, A(j, k));
                 A(i, j) = acc_val(a);
             }
         }
@@ -130,8 +166,26 @@ P2_HD void tridiagonalize_dw(int n_rt, DwMat<D> A, DwVec<D> d, DwVec<D> e) {
         const D nb = dw_neg(b);
         A(k + 1, k + 1) = dw_add(one, nb);
         for (int i = k + 2; i < n; ++i) A(i, k + 1) = dw_mul(nb, A(i, k));
-        for (int c = k + 2; c < n; ++c) {
-            acc_t<D> s = acc0<D>();                      // A(k+1, c) = 0 here
+        int c = k + 2;
+        for (; c + 1 < n; c += 2) {                      // columns in pairs
+            acc_t<D> s0 = acc0<D>(), s1 = acc0<D>();     // A(k+1, c) = 0 here
+            for (int i = k + 2; i < n; ++i) {
+                const D vi = A(i, k);
+                acc_fma(s0, vi, A(i, c));
+                acc_fma(s1, vi, A(i, c + 1));
+            }
+            const D ns0 = dw_mul(acc_val(s0), nb);
+            const D ns1 = dw_mul(acc_val(s1), nb);
+            A(k + 1, c) = ns0;
+            A(k + 1, c + 1) = ns1;
+            for (int i = k + 2; i < n; ++i) {
+                const D vi = A(i, k);
+                A(i, c) = dw_fma(ns0, vi, A(i, c));
+                A(i, c + 1) = dw_fma(ns1, vi, A(i, c + 1));
+            }
+        }
+        if (c < n) {
+            acc_t<D> s = acc0<D>();
             for (int i = k + 2; i < n; ++i) acc_fma(s, A(i, k), A(i, c));
             const D ns = dw_mul(acc_val(s), nb);
             A(k + 1, c) = ns;

@@ -136,7 +136,20 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
                         for (int j = 0; j < R; ++j) acc_fmaf(s, g[pk<R>(i, j)], hc[j]);
                         tv[i] = acc_val(s);
                     }
-                    for (int r = c; r < R; ++r) {
+                    int r = c;
+                    for (; r + 1 < R; r += 2) {             // entries in pairs
+                        acc_t<D> s0 = acc0<D>(), s1 = acc0<D>();
+#pragma unroll
+                        for (int i = 0; i < R; ++i) {
+                            acc_fmaf(s0, tv[i], Hs[r * R + i]);
+                            acc_fmaf(s1, tv[i], Hs[(r + 1) * R + i]);
+                        }
+                        const D m0 = acc_val(s0), m1 = acc_val(s1);
+                        A(r, c) = m0;
+                        A(r + 1, c) = m1;
+                        if (r == c) em = max(em, f_expo(m0.h));
+                    }
+                    if (r < R) {
                         acc_t<D> s = acc0<D>();
 #pragma unroll
                         for (int i = 0; i < R; ++i) acc_fmaf(s, tv[i], Hs[r * R + i]);

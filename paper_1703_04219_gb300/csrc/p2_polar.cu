@@ -35,20 +35,23 @@ static __device__ __forceinline__ int pk(int i, int j) {   // packed lower index
 
 // Shared memory: H (scaled, FP32) for the block, then per lane the working
 // matrix (R x R) and the tridiagonal (d, e), interleaved across the lanes:
-// R^2 + 2R double-words per lane.  The block has as many lanes as a block's
-// opt-in shared memory (227 KB) holds, at most 256, a multiple of 32: a
-// compile-time constant, so that the interleaved addresses of different
-// entries are provably distinct and the compiler may reorder their loads and
-// stores.
+// R^2 + 2R double-words per lane (MODE 2 below: R^2, plus w' for R > 10; its
+// d in registers: 256 lanes at R = 10 instead of 224).  The block has as
+// many lanes as a block's opt-in shared memory (227 KB) holds, at most 256,
+// a multiple of 32: a compile-time constant, so that the interleaved
+// addresses of different entries are provably distinct and the compiler may
+// reorder their loads and stores.
 constexpr int REG_SMEM_OPTIN = 232448;
 template <int R>
 __host__ __device__ constexpr size_t reg_hbytes() { return (size_t)((R * R + 1) / 2) * sizeof(dw); }
-template <int R>
-__host__ __device__ constexpr size_t reg_lane_bytes() { return (size_t)(R * R + 2 * R) * sizeof(dw); }
-template <int R>
+template <int R, int MODE>
+__host__ __device__ constexpr size_t reg_lane_bytes() {
+    return (size_t)(MODE == 2 ? R * R + (R > 10 ? R : 0) : R * R + 2 * R) * sizeof(dw);
+}
+template <int R, int MODE>
 __host__ __device__ constexpr int reg_threads() {
-    return (int)(((REG_SMEM_OPTIN - reg_hbytes<R>()) / reg_lane_bytes<R>() < 256
-                      ? (REG_SMEM_OPTIN - reg_hbytes<R>()) / reg_lane_bytes<R>()
+    return (int)(((REG_SMEM_OPTIN - reg_hbytes<R>()) / reg_lane_bytes<R, MODE>() < 256
+                      ? (REG_SMEM_OPTIN - reg_hbytes<R>()) / reg_lane_bytes<R, MODE>()
                       : 256) /
                  32 * 32);
 }
@@ -64,7 +67,7 @@ __host__ __device__ constexpr int reg_threads() {
 // number of subjects is *sc.kdev (MODE 0 over the subjects whose rotations
 // did not fit the record).
 template <int R, class D, int MODE = 0>
-__global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
+__global__ void __launch_bounds__(reg_threads<R, MODE>(), 1) k_polar_reg(const dw *__restrict__ G,
                                                    const float *__restrict__ W, SmallState *st,
                                                    float *T, int64_t K, float rtol2,
                                                    const int32_t *__restrict__ order,
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
     constexpr int HW = (R * R + 1) / 2;                  // double-word slots holding H
     extern __shared__ __align__(16) unsigned char smr_raw[];
     D *smd = reinterpret_cast<D *>(smr_raw);
-    constexpr int NT = reg_threads<R>();                 // = blockDim.x
+    constexpr int NT = reg_threads<R, MODE>();           // = blockDim.x
     static_assert(sizeof(D) == sizeof(dw), "one double-word slot per element");
     const int t = threadIdx.x;
     float *Hs = reinterpret_cast<float *>(smd);
@@ -93,8 +96,9 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
         const int64_t k = order ? (int64_t)order[slot] : slot;
         const D zero = num_f<D>(0.f), one = num_f<D>(1.f);
         DwMat<D> A{th + t, NT, R};
-        DwVec<D> d{th + (size_t)R * R * NT + t, NT};
-        DwVec<D> e{th + (size_t)(R * R + R) * NT + t, NT};
+        DwVec<D> d{th + (size_t)R * R * NT + t, NT};     // (not MODE 2)
+        DwVec<D> e{th + (size_t)(MODE == 2 ? R * R : R * R + R) * NT + t, NT};
+        D dr[MODE == 2 ? R : 1];                         // MODE 2: the eigenvalues
         const size_t tb = (size_t)k * R * R;
         int so = 0;
         bool live = true;                                // a subject with T_k to form
@@ -217,7 +221,7 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
                         A(r, c) = sc.qh[(size_t)(r * R + c) * sc.chunk + slot];
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    d[i] = sc.dout[(size_t)slot * R + i];
+                    dr[i] = sc.dout[(size_t)slot * R + i];
                     w[i] = sc.wv[(size_t)slot * R + i];
                 }
                 if constexpr (R > 1) {
@@ -282,14 +286,24 @@ __global__ void __launch_bounds__(256, 1) k_polar_reg(const dw *__restrict__ G,
             if (live) {
                 float lmax = 0.f;
 #pragma unroll
-                for (int i = 0; i < R; ++i) lmax = fmaxf(lmax, d[i].h);
-                const float cut = rtol2 * lmax;
-#pragma unroll 1
                 for (int i = 0; i < R; ++i) {
-                    const D di = d[i];
+                    if constexpr (MODE == 2)
+                        lmax = fmaxf(lmax, dr[i].h);
+                    else
+                        lmax = fmaxf(lmax, d[i].h);
+                }
+                const float cut = rtol2 * lmax;
+                auto cut_column = [&](int i, D di) {
                     const D sf = (lmax > 0.f && di.h > cut) ? dw_sqrt(dw_rsqrt(di)) : zero;  // d^-1/4
 #pragma unroll
                     for (int r = 0; r < R; ++r) A(r, i) = dw_mul(A(r, i), sf);
+                };
+                if constexpr (MODE == 2) {
+#pragma unroll
+                    for (int i = 0; i < R; ++i) cut_column(i, dr[i]);
+                } else {
+#pragma unroll 1
+                    for (int i = 0; i < R; ++i) cut_column(i, d[i]);
                 }
                 const float o1 = f_pow2(so / 2), o2 = f_pow2(so - so / 2);
                 if constexpr (R <= 10) {
@@ -422,8 +436,8 @@ template <int R, class D, int MODE = 0>
 static int launch_reg(const p2_ctx *c, const dw *G, const float *W, SmallState *st, float *T,
                       int64_t K, cudaStream_t s, float rtol2, const int32_t *order,
                       int32_t *qrcnt, GrpSplit<D> sc = GrpSplit<D>{}) {
-    constexpr int nt = reg_threads<R>();
-    const size_t smem = reg_hbytes<R>() + (size_t)nt * reg_lane_bytes<R>();
+    constexpr int nt = reg_threads<R, MODE>();
+    const size_t smem = reg_hbytes<R>() + (size_t)nt * reg_lane_bytes<R, MODE>();
     if (nt < 32 || smem > (size_t)c->geo.smem_optin) return -1;
     const int nblk = (int)((K + nt - 1) / nt);
     k_polar_reg<R, D, MODE><<<nblk, nt, smem, s>>>(G, W, st, T, K, rtol2, order, qrcnt, sc);

@@ -41,6 +41,7 @@ CASES = {
     "shard_r6": ["shard", "6", "20"],
     "split_r5": ["split", "5", "40"],
     "split_r10": ["split", "10", "24"],
+    "split_r12": ["split", "12", "16"],
     "split_r13": ["split", "13", "12"],
     "split_r40": ["split", "40", "8"],
     "tc_r40": ["tc", "40", "8"],
@@ -164,7 +165,7 @@ def test_emulated_sharded_context_is_in_bounds_and_matches(emulated_runs):
     assert out["fit"] < 1e-6
 
 
-@pytest.mark.parametrize("name", ["split_r5", "split_r10", "split_r13", "split_r40"])
+@pytest.mark.parametrize("name", ["split_r5", "split_r10", "split_r12", "split_r13", "split_r40"])
 def test_emulated_split_procrustes_equals_fused(emulated_runs, name):
     """The split Procrustes step (Householder kernel, one-lane QR recorder,
     rotation-applying kernel) and its fused fallback give the fused kernel's

@@ -203,8 +203,20 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                             b[j] = dw_mul(dw_scale(from_dw<D>(Gk[p]), gsc), num_prod<D>(wi, wv[j]));
                         }
                     }
+                    int c = 0;
                 #pragma unroll 1
-                    for (int c = 0; c < R; ++c) {
+                    for (; c + 1 < R; c += 2) {             // columns in pairs
+                        acc_t<D> s0 = acc0<D>(), s1 = acc0<D>();
+                #pragma unroll
+                        for (int j = 0; j < RB; ++j)
+                            if (j < R) {
+                                acc_fmaf(s0, b[j], Hs[c * R + j]);
+                                acc_fmaf(s1, b[j], Hs[(c + 1) * R + j]);
+                            }
+                        A(i, c) = acc_val(s0);
+                        A(i, c + 1) = acc_val(s1);
+                    }
+                    if (c < R) {
                         acc_t<D> s = acc0<D>();
                 #pragma unroll
                         for (int j = 0; j < RB; ++j)
@@ -221,11 +233,24 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                     for (int i = 0; i < RB; ++i)
                         if (i < R) u[i] = A(i, c);
                     __syncwarp(gmask);
-                #pragma unroll 1
-                    for (int ii = 0; ii < RPL; ++ii) {
-                        const int r = gl + PG * ii;
-                        if (r >= R) break;
-                        if (r < c) continue;
+                    int r2 = gl;                            // the lane's rows in pairs
+                    while (r2 < c) r2 += PG;
+                    for (; r2 + PG < R; r2 += 2 * PG) {
+                        const int r = r2, r1 = r2 + PG;
+                        acc_t<D> s0 = acc0<D>(), s1 = acc0<D>();
+                #pragma unroll
+                        for (int i = 0; i < RB; ++i)
+                            if (i < R) {
+                                acc_fmaf(s0, u[i], Hs[r * R + i]);
+                                acc_fmaf(s1, u[i], Hs[r1 * R + i]);
+                            }
+                        const D m0 = acc_val(s0), m1 = acc_val(s1);
+                        A(r, c) = m0;
+                        A(r1, c) = m1;
+                        if (r == c) em = max(em, f_expo(m0.h));
+                    }
+                    if (r2 < R) {
+                        const int r = r2;
                         acc_t<D> s = acc0<D>();
                 #pragma unroll
                         for (int i = 0; i < RB; ++i)
@@ -289,9 +314,32 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                     }
                     __syncwarp(gmask);
                     // p = bh A22 v on my rows, pv = p . v
+                    // (the lane's rows in pairs, two independent sums
+                    // interleaved; pa in row order)
                     acc_t<D> pa = acc0<D>();
-                    for (int i = gl; i < R; i += PG) {
-                        if (i < kk + 1) continue;
+                    int i2 = gl;
+                    while (i2 < kk + 1) i2 += PG;
+                    for (; i2 + PG < R; i2 += 2 * PG) {
+                        const int i = i2, i1 = i2 + PG;
+                        acc_t<D> s0 = acc_from(A(i, kk + 1));
+                        acc_t<D> s1 = acc_from(A(i1, kk + 1));
+                        for (int j = kk + 2; j < R; ++j) {
+                            const D vj = A(j, kk);
+                            acc_fma(s0, (j <= i) ? A(i, j) : A(j, i), vj);
+                            acc_fma(s1, (j <= i1) ? A(i1, j) : A(j, i1), vj);
+                        }
+                        const D si0 = dw_mul(acc_val(s0), bh);
+                        const D si1 = dw_mul(acc_val(s1), bh);
+                        t[i] = si0;
+                        t[i1] = si1;
+                        if (i == kk + 1)
+                            acc_add(pa, si0);
+                        else
+                            acc_fma(pa, si0, A(i, kk));
+                        acc_fma(pa, si1, A(i1, kk));
+                    }
+                    if (i2 < R) {
+                        const int i = i2;
                         acc_t<D> s = acc_from(A(i, kk + 1));
                         for (int j = kk + 2; j < R; ++j)
                             acc_fma(s, (j <= i) ? A(i, j) : A(j, i), A(j, kk));
@@ -357,9 +405,29 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                         }
                         __syncwarp(gmask);
                         if (act) {
-                            for (int c = gl; c < R; c += PG) {
-                                if (c < kk + 2) continue;
-                                acc_t<D> s = acc0<D>();             // A(kk+1, c) = 0 here
+                            int c2 = gl;                        // the lane's columns in pairs
+                            while (c2 < kk + 2) c2 += PG;
+                            for (; c2 + PG < R; c2 += 2 * PG) {
+                                const int c = c2, c1 = c2 + PG;
+                                acc_t<D> s0 = acc0<D>(), s1 = acc0<D>();   // A(kk+1, c) = 0 here
+                                for (int i = kk + 2; i < R; ++i) {
+                                    const D vi = A(i, kk);
+                                    acc_fma(s0, vi, A(i, c));
+                                    acc_fma(s1, vi, A(i, c1));
+                                }
+                                const D ns0 = dw_mul(acc_val(s0), nb);
+                                const D ns1 = dw_mul(acc_val(s1), nb);
+                                A(kk + 1, c) = ns0;
+                                A(kk + 1, c1) = ns1;
+                                for (int i = kk + 2; i < R; ++i) {
+                                    const D vi = A(i, kk);
+                                    A(i, c) = dw_fma(ns0, vi, A(i, c));
+                                    A(i, c1) = dw_fma(ns1, vi, A(i, c1));
+                                }
+                            }
+                            if (c2 < R) {
+                                const int c = c2;
+                                acc_t<D> s = acc0<D>();
                                 for (int i = kk + 2; i < R; ++i) acc_fma(s, A(i, kk), A(i, c));
                                 const D ns = dw_mul(acc_val(s), nb);
                                 A(kk + 1, c) = ns;

@@ -363,13 +363,27 @@ __global__ void __launch_bounds__(256, 1) k_polar_grp(const dw *__restrict__ G,
                         if (i < kk + 1) continue;
                         const D nvi = dw_neg((i == kk + 1) ? one : A(i, kk));
                         const D nwi = dw_neg(t[i]);
-                        for (int j = kk + 1; j <= i; ++j) {
+                        {                                    // j = kk + 1: v_{kk+1} = 1
+                            acc_t<D> a = acc_from(A(i, kk + 1));
+                            acc_fma(a, nvi, t[kk + 1]);
+                            acc_add(a, nwi);
+                            A(i, kk + 1) = acc_val(a);
+                        }
+                        int j = kk + 2;
+                        for (; j + 1 <= i; j += 2) {         // entries in pairs
+                            acc_t<D> a0 = acc_from(A(i, j));
+                            acc_t<D> a1 = acc_from(A(i, j + 1));
+                            acc_fma(a0, nvi, t[j]);
+                            acc_fma(a1, nvi, t[j + 1]);
+                            acc_fma(a0, nwi, A(j, kk));
+                            acc_fma(a1, nwi, A(j + 1, kk));
+                            A(i, j) = acc_val(a0);
+                            A(i, j + 1) = acc_val(a1);
+                        }
+                        if (j <= i) {
                             acc_t<D> a = acc_from(A(i, j));
                             acc_fma(a, nvi, t[j]);
-                            if (j == kk + 1)
-                                acc_add(a, nwi);
-                            else
-                                acc_fma(a, nwi, A(j, kk));
+                            acc_fma(a, nwi, A(j, kk));
                             A(i, j) = acc_val(a);
                         }
                     }

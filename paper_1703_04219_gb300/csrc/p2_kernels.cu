@@ -922,10 +922,86 @@ static __device__ void cta_jacobi(double *A, double *U, int n, int *flags, doubl
     __syncthreads();
 }
 
-// out = A^+ for the symmetric PSD n x n matrix in A (destroyed); U is n x n
-// scratch.  Eigenvalues <= n * 2^-52 * lambda_max are dropped.
-static __device__ void cta_pinv(double *A, double *U, double *out, int n, int *flags) {
+// out = A^-1 by a Cholesky factorisation A = L L^T (in C), L^-1 (in U) and
+// A^-1 = L^-T L^-1, when that provably equals A^+ as cta_pinv defines it:
+// every eigenvalue above the cut n 2^-52 lambda_max.  lambda_min >=
+// 1 / trace(A^-1) and lambda_max <= trace(A), so a margin of 2^10 between
+// 1 / trace(A^-1) and n 2^-52 trace(A) leaves no eigenvalue near the cut.
+// Returns false (out untouched, A untouched) when the factorisation breaks
+// down or the bound does not hold.  A chain of ~2n FP64 square roots and
+// divisions instead of the Jacobi sweeps' ~6n rounds of them.
+static __device__ bool cta_inv_chol(const double *A, double *C, double *U, double *out, int n) {
+    __shared__ double rinv[P2_RMAX];
+    __shared__ int ok;
+    __shared__ double tra, trinv;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < n * n; e += nt) {
+        C[e] = A[e];
+        U[e] = 0.0;
+    }
+    if (tid == 0) {
+        ok = 1;
+        double t = 0.0;
+        for (int i = 0; i < n; ++i) t += A[i * n + i];
+        tra = t;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {                        // right-looking, lower triangle
+        if (tid == 0) {
+            const double d = C[k * n + k];
+            if (!(d > 0.0) || !ok) {
+                ok = 0;
+            } else {
+                const double l = sqrt(d);
+                C[k * n + k] = l;
+                rinv[k] = 1.0 / l;
+            }
+        }
+        __syncthreads();
+        if (!ok) return false;
+        for (int i = k + 1 + tid; i < n; i += nt) C[i * n + k] *= rinv[k];
+        __syncthreads();
+        for (int e = tid; e < (n - k - 1) * (n - k - 1); e += nt) {
+            const int i = k + 1 + e / (n - k - 1), j = k + 1 + e % (n - k - 1);
+            if (j <= i) C[i * n + j] = fma(-C[i * n + k], C[j * n + k], C[i * n + j]);
+        }
+        __syncthreads();
+    }
+    for (int j = tid; j < n; j += nt) {                  // column j of L^-1 (lower)
+        for (int i = j; i < n; ++i) {
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int m = j; m < i; ++m) s = fma(-C[i * n + m], U[m * n + j], s);
+            U[i * n + j] = s * rinv[i];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += nt) {              // (L^-T L^-1)_{ij}
+        const int i = e / n, j = e - (e / n) * n;
+        double s = 0.0;
+        for (int m = (i > j ? i : j); m < n; ++m) s = fma(U[m * n + i], U[m * n + j], s);
+        C[e] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int i = 0; i < n; ++i) t += C[i * n + i];
+        trinv = t;
+    }
+    __syncthreads();
+    const double cut = (double)n * 2.220446049250313e-16 * tra;
+    if (!(trinv > 0.0) || !(1.0 / trinv > 1024.0 * cut) || !isfinite(trinv)) return false;
+    for (int e = tid; e < n * n; e += nt) out[e] = C[e];
+    __syncthreads();
+    return true;
+}
+
+// out = A^+ for the symmetric PSD n x n matrix in A (destroyed); U and C are
+// n x n scratch.  Eigenvalues <= n * 2^-52 * lambda_max are dropped (by the
+// Jacobi eigen-decomposition; the Cholesky inverse where it provably gives
+// the same matrix, up to rounding).
+static __device__ void cta_pinv(double *A, double *U, double *C, double *out, int n, int *flags) {
     __shared__ double f[P2_RMAX];
+    if (cta_inv_chol(A, C, U, out, n)) return;
     cta_jacobi(A, U, n, flags);
     if (threadIdx.x == 0) {
         double lmax = 0.0;
@@ -1329,7 +1405,7 @@ __global__ void __launch_bounds__(256) k_solve_h(const double *__restrict__ part
         A[e] = st->WtW[e] * st->VtV[e];
     }
     __syncthreads();
-    cta_pinv(A, U, Pi, R, &st->flags);
+    cta_pinv(A, U, Hn, Pi, R, &st->flags);            // Hn: scratch until written below
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
         const int i = e / R, j = e - i * R;
         double s = 0.0;
@@ -1373,10 +1449,10 @@ __global__ void k_init_h(const float *__restrict__ H, SmallState *st, int R) {
 // V solve, part a: (W^TW * H^TH)^+.
 __global__ void __launch_bounds__(256) k_solve_v_pinv(SmallState *st, int R) {
     extern __shared__ __align__(16) double sd[];
-    double *A = sd, *U = A + R * R;
+    double *A = sd, *U = A + R * R, *C = U + R * R;
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) A[e] = st->WtW[e] * st->HtH[e];
     __syncthreads();
-    cta_pinv(A, U, st->P2inv, R, &st->flags);
+    cta_pinv(A, U, C, st->P2inv, R, &st->flags);
 }
 
 // V solve, part b: Vun = M2 P2inv; partial column sums of squares per block.
@@ -1441,7 +1517,7 @@ __global__ void k_solve_v_store(const double *__restrict__ Vun, const SmallState
 __global__ void __launch_bounds__(256) k_fin_v(const double *__restrict__ part, int nparts,
                                                SmallState *st, int R, int with_g3) {
     extern __shared__ __align__(16) double sd[];
-    double *A = sd, *U = A + R * R;
+    double *A = sd, *U = A + R * R, *C = U + R * R;     // C: with_g3 only (4 R^2 doubles)
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
         double s = 0.0;
         for (int b = 0; b < nparts; ++b) s += part[(size_t)b * R * R + e];
@@ -1449,7 +1525,7 @@ __global__ void __launch_bounds__(256) k_fin_v(const double *__restrict__ part, 
         A[e] = s * st->HtH[e];
     }
     __syncthreads();
-    if (with_g3) cta_pinv(A, U, st->G3inv, R, &st->flags);
+    if (with_g3) cta_pinv(A, U, C, st->G3inv, R, &st->flags);
 }
 
 // The exchange hook of a sharded context: sums buf over the shards in place

@@ -30,10 +30,16 @@ def bf16_round(a):
 def iterate_case(name, K, R, precision="fp32"):
     nonneg = precision == "nonneg"
     fp64 = precision == "fp64"                # the FP64 arm of the Procrustes step
-    if nonneg or fp64:
+    dup = precision == "dupcols"              # singular Gram-Hadamard products
+    if nonneg or fp64 or dup:
         precision = "fp32"
     X = synth.generate(name, K=K)
     H0, V0, W0 = synth.init_factors(R, X.J, X.K, seed=11)
+    if dup:
+        # column 1 of V and W equal to column 0: every R x R Gram-Hadamard
+        # product is singular, so the pseudo-inverses take the Jacobi path
+        V0[:, 1] = V0[:, 0]
+        W0[:, 1] = W0[:, 0]
     if precision == "bf16":                # a start that bfloat16 storage represents exactly
         V0 = bf16_round(V0)
     with p2.Parafac2(R, use_graph=False, precision=precision, nonneg=nonneg,

@@ -1,6 +1,8 @@
 """The library's CUDA kernels run on the CPU emulator (tests/cpu_emu) under
 AddressSanitizer: one ALS iteration at R = 5 and R = 10 (lane-per-subject
-Procrustes), at R = 13 and R = 40 (grouped Procrustes, eight and sixteen lanes
+Procrustes; at R = 5 also from a start with two equal columns of V and W, whose
+singular Gram-Hadamard products send the pseudo-inverses down their Jacobi
+path), at R = 13 and R = 40 (grouped Procrustes, eight and sixteen lanes
 per subject), at R = 20 (a rank outside the compiled list: generic kernels), at R = 10
 and R = 40 with the FP64 arm of the Procrustes step, at R = 5 with bfloat16
 storage and in the non-negative variant, a projection of new
@@ -32,6 +34,7 @@ CASES = {
     "iterate_r5_nonneg": ["iterate", "tiny", "24", "5", "nonneg"],
     "iterate_r17_nonneg": ["iterate", "tiny", "24", "17", "nonneg"],
     "iterate_r10_fp64": ["iterate", "tiny", "24", "10", "fp64"],
+    "iterate_r5_dupcols": ["iterate", "tiny", "24", "5", "dupcols"],
     "iterate_r40_fp64": ["iterate", "tiny", "16", "40", "fp64"],
     "project_r12": ["project", "12", "3"],
     "project_r8_nonneg": ["project", "8", "3", "nonneg"],
@@ -91,7 +94,8 @@ def _result(runs, name):
 
 
 @pytest.mark.parametrize("name", ["iterate_r5", "iterate_r10", "iterate_r13", "iterate_r40",
-                                  "iterate_r20", "iterate_r10_fp64", "iterate_r40_fp64"])
+                                  "iterate_r20", "iterate_r10_fp64", "iterate_r40_fp64",
+                                  "iterate_r5_dupcols"])
 def test_emulated_iteration_is_in_bounds_and_matches_oracle(emulated_runs, name):
     err = _result(emulated_runs, name)
     for key in ("M1", "M2", "M3", "H", "V", "W"):

@@ -347,23 +347,37 @@ __global__ void __launch_bounds__(256, CB >= 32 ? 1 : 3) k_alpha(XView X, const 
                     Cacc[e] += acc;
                 }
             }
-            for (int p = lane; p < P; p += 32) {
-                const int r = pr[p], s = pc[p];
-                float sh = Ghi[p], sl = Glo[p];
+            // a lane's two packed entries p and p + 32 accumulated together (two
+            // independent chains; a lane without a second entry repeats the
+            // first and discards it), each with its own terms in row order
+            for (int p = lane; p < P; p += 64) {
+                const bool two = p + 32 < P;
+                const int q = two ? p + 32 : p;
+                const int r = pr[p], s = pc[p], r1 = pr[q], s1 = pc[q];
+                float sh = Ghi[p], sl = Glo[p], sh1 = Ghi[q], sl1 = Glo[q];
 #pragma unroll 4
                 for (int i = 0; i < nr; ++i) {
                     const float a = zn[i * RS + r], b = zn[i * RS + s];
+                    const float a1 = zn[i * RS + r1], b1 = zn[i * RS + s1];
                     // TwoProduct and TwoSum with uncontracted roundings (see two_sum)
-                    const float pa = f_mul(a, b);
+                    const float pa = f_mul(a, b), pa1 = f_mul(a1, b1);
                     const float pe = f_fma(a, b, -pa);          // a*b = pa + pe exactly
-                    const float t = f_add(sh, pa);              // TwoSum(sh, pa)
-                    const float bv = f_sub(t, sh);
+                    const float pe1 = f_fma(a1, b1, -pa1);
+                    const float t = f_add(sh, pa), t1 = f_add(sh1, pa1);   // TwoSum(sh, pa)
+                    const float bv = f_sub(t, sh), bv1 = f_sub(t1, sh1);
                     const float er = f_add(f_sub(sh, f_sub(t, bv)), f_sub(pa, bv));
+                    const float er1 = f_add(f_sub(sh1, f_sub(t1, bv1)), f_sub(pa1, bv1));
                     sh = t;
+                    sh1 = t1;
                     sl = f_add(sl, f_add(er, pe));
+                    sl1 = f_add(sl1, f_add(er1, pe1));
                 }
                 Ghi[p] = sh;
                 Glo[p] = sl;
+                if (two) {
+                    Ghi[q] = sh1;
+                    Glo[q] = sl1;
+                }
             }
             __syncwarp();
             base += tot;

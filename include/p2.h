@@ -75,7 +75,7 @@ typedef struct {
                              (float-float) arithmetic on the FP32 pipe, ~2^-46 normwise */
     int32_t autotune;     /* non-zero: the first p2_iterate times the launch choices of
                              p2_tuning on this context's data (split or fused Procrustes
-                             step for R > 12, subject bins on or off for the sparse passes)
+                             step for R >= 2, subject bins on or off for the sparse passes)
                              and keeps the fastest; zero (default): the built-in rules */
     const char *tune_cache; /* nullable: a file of tuned choices, one JSON object per line
                              keyed by rank, precision, variant and the collection's K, J and

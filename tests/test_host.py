@@ -198,3 +198,28 @@ def test_sharded_exchange_over_two_gloo_ranks():
         assert np.allclose(WtW, W0.T @ W0, rtol=1e-12)
         assert np.allclose(M2, ref["M2"], rtol=1e-12, atol=1e-12 * np.abs(ref["M2"]).max())
     assert np.array_equal(res[0][3], res[1][3])           # every rank holds the same sum
+
+
+@pytest.mark.parametrize("R,split,name_has,wname,traffic_key", [
+    (10, True, "k_polar_reg<MODE 1>", "c63m", "k_polar_reg_split"),
+    (10, False, "k_polar_reg (double-word", "c63m", "k_polar_reg"),
+    (40, True, "k_polar_grp<MODE 1>", "c250m", "k_polar_split"),
+])
+def test_roofline_names_the_procrustes_kernels_that_ran(R, split, name_has, wname, traffic_key):
+    """bench.py's roofline for a Procrustes-dominated step: the kernel group
+    named after the split or fused form that ran, the achieved rate =
+    algorithmic flops / phase time against the derived double-word peak, and
+    DRAM traffic only from a profiles/traffic.json entry of that group whose
+    sources hash matches (else null)."""
+    import types
+    bench = _bench_module()
+    X = types.SimpleNamespace(K=1000, n_rows=50000, nnz=60000)
+    phase = {"procrustes": 5.0, "beta_mode2": 1.0, "alpha_mode3_w_gram": 1.0,
+             "subject_stats_mode1": 0.1, "h_solve": 0.1, "v_solve": 0.1, "fit": 0.1}
+    flops = 1e10
+    roof, sparse = bench.roofline(X, R, phase, flops, wname, split=split)
+    assert name_has in roof["kernel"] and roof["bound"] == "alu"
+    assert roof["achieved"] == pytest.approx(flops / 5e-3 / 1e12)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / bench.DW_PEAK_TFLOPS)
+    assert roof["traffic"] == bench._traffic(traffic_key, wname)
+    assert set(sparse) == {"beta_mode2", "alpha_mode3_w_gram"}

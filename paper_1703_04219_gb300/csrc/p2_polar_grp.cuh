@@ -66,8 +66,8 @@ static __device__ __forceinline__ unsigned long long group_or(unsigned mask, uns
 }
 
 // Scratch of the split Procrustes step: kernel MODE 1 (of k_polar_grp for
-// R > 12, of the lane kernel k_polar_reg below) reduces each
-// subject of a chunk to tridiagonal form and stores Q_h, d, e,
+// R > 12, of the lane kernel k_polar_reg in p2_polar.cu for R <= 12) reduces
+// each subject of a chunk to tridiagonal form and stores Q_h, d, e,
 // w' and the output exponent (meta, GRP_ZERO for a zero subject);
 // k_qr_record runs the QR iteration on (d, e) alone, one lane per subject,
 // and records every Givens rotation (cap per subject; nrec = -1 when they
